@@ -1,0 +1,139 @@
+"""P0 Galerkin boundary-element oracle for the direct formulation.
+
+Test infrastructure only.
+
+Discretisation (Sec. "An introduction to Bempp"): piecewise-constant (P0)
+trial and test functions on flat triangles, A_ij = int_Ti int_Tj k(x,y),
+b_i = int_Ti f.  Regular pairs use the product of the nq-point triangle rule
+(the G entries of Eq. bempp_fmm_matvec); identical or vertex-sharing pairs use
+a semi-analytic rule (analytic inner integral, fine outer rule), see oracle.c.
+
+Direct formulation (Eq. direct), Galerkin form with M the P0 mass matrix
+(diagonal of the triangle areas):
+    [ M/2 + K_L        -V_L          ] [phi ]   [ b ]
+    [ M/2 - K_Y   (eps1/eps2) V_Y    ] [dphi] = [ 0 ],
+    b_i = int_Ti sum_k q_k / (4 pi eps1 |x - r_k|).
+Reaction potential (Eq. phi_reac): phi_reac(r) = -K_L[phi](r) + V_L[dphi](r),
+energy (Eq. energy): dG = 1/2 sum_k q_k phi_reac(r_k), times 4 pi C for
+kcal/mol (C = 332.0637).
+
+Readings: the 3-point rule is the interior degree-2 rule (2/3,1/6,1/6),
+the 6-point rule is Dunavant's degree-4 rule; "adjacent" means sharing at
+least one vertex.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from ._lib import lib
+from .kernels import LAPLACE, direct_sum
+from .closed_forms import KCAL
+
+
+def _p(a):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def geometry(verts, tris):
+    """Unit normals n = (v1-v0)x(v2-v0)/|.| and areas of each triangle."""
+    V = np.asarray(verts, dtype=np.float64)
+    F = np.asarray(tris)
+    e1 = V[F[:, 1]] - V[F[:, 0]]
+    e2 = V[F[:, 2]] - V[F[:, 0]]
+    c = np.cross(e1, e2)
+    a = np.linalg.norm(c, axis=1)
+    return c / a[:, None], 0.5 * a
+
+
+def regular_rule(nq):
+    L = np.zeros(3 * nq)
+    W = np.zeros(nq)
+    if lib().or_regular_rule(int(nq), _p(L), _p(W)) != 0:
+        raise ValueError("nq must be 1, 3 or 6")
+    return L.reshape(nq, 3), W
+
+
+def quad_points(verts, tris, nq):
+    """Quadrature points x_a (a = i*nq + k), their weights w_k |T_i|, normals
+    of their triangle, and the triangle index."""
+    V = np.asarray(verts, dtype=np.float64)
+    F = np.asarray(tris)
+    L, W = regular_rule(nq)
+    n, area = geometry(V, F)
+    P = np.einsum("kc,icd->ikd", L, V[F]).reshape(-1, 3)
+    w = (W[None, :] * area[:, None]).ravel()
+    nrm = np.repeat(n, nq, axis=0)
+    tri = np.repeat(np.arange(len(F)), nq)
+    return P, w, nrm, tri
+
+
+def assemble_p0(verts, tris, nq, kappa, L_outer=6, n_outer=4, n_inner=4):
+    """Dense P0 Galerkin matrices (V_L, K_L, V_Y, K_Y), each [nt, nt]."""
+    V = np.ascontiguousarray(verts, dtype=np.float64)
+    F = np.ascontiguousarray(tris, dtype=np.int32)
+    nt = len(F)
+    mats = [np.zeros((nt, nt)) for _ in range(4)]
+    rc = lib().or_assemble_p0(len(V), _p(V), nt, _p(F), int(nq), float(kappa),
+                              int(L_outer), int(n_outer), int(n_inner), *[_p(m) for m in mats])
+    if rc != 0:
+        raise ValueError("assembly failed")
+    return tuple(mats)
+
+
+def direct_matrix(mats, area, eps_in, eps_out):
+    """The 2x2 block matrix of Eq. direct in P0 Galerkin form."""
+    VL, KL, VY, KY = mats
+    M = np.diag(area)
+    return np.block([[0.5 * M + KL, -VL], [0.5 * M - KY, (eps_in / eps_out) * VY]])
+
+
+def rhs(verts, tris, nq, atoms, charges, eps_in):
+    """b_i = int_Ti sum_k q_k/(4 pi eps1 |x - r_k|) with the nq-point rule."""
+    P, w, _, tri = quad_points(verts, tris, nq)
+    f = direct_sum(LAPLACE, 0.0, atoms, q=np.asarray(charges, dtype=np.float64) / eps_in, tgt=P)
+    b = np.zeros(len(tris))
+    np.add.at(b, tri, w * f)
+    return b
+
+
+def solve_direct(verts, tris, nq, atoms, charges, eps_in, eps_out, kappa, mats=None):
+    """Dense LU solve of Eq. direct; returns (phi, dphi, mats)."""
+    _, area = geometry(verts, tris)
+    if mats is None:
+        mats = assemble_p0(verts, tris, nq, kappa)
+    A = direct_matrix(mats, area, eps_in, eps_out)
+    nt = len(tris)
+    b = np.concatenate([rhs(verts, tris, nq, atoms, charges, eps_in), np.zeros(nt)])
+    x = np.linalg.solve(A, b)
+    return x[:nt], x[nt:], mats
+
+
+def phi_reac(verts, tris, nq, phi, dphi, atoms):
+    """Eq. phi_reac at the atoms: -K_L[phi] + V_L[dphi] with the nq-point rule."""
+    P, w, nrm, tri = quad_points(verts, tris, nq)
+    return direct_sum(LAPLACE, 0.0, P, q=w * np.asarray(dphi)[tri], dip=-w * np.asarray(phi)[tri],
+                      src_n=nrm, tgt=atoms)
+
+
+def kahan_sum(v):
+    s = 0.0
+    c = 0.0
+    for x in np.asarray(v, dtype=np.float64).ravel():
+        y = x - c
+        t = s + y
+        c = (t - s) - y
+        s = t
+    return s
+
+
+def solvation_energy(charges, phir):
+    """Eq. energy in kcal/mol: 1/2 sum q phi_reac * 4 pi C (Kahan sum)."""
+    return 0.5 * kahan_sum(np.asarray(charges) * phir) * 4.0 * np.pi * KCAL
+
+
+def solve_energy(verts, tris, nq, atoms, charges, eps_in, eps_out, kappa, mats=None):
+    phi, dphi, mats = solve_direct(verts, tris, nq, atoms, charges, eps_in, eps_out, kappa, mats)
+    pr = phi_reac(verts, tris, nq, phi, dphi, atoms)
+    return solvation_energy(charges, pr), phi, dphi, mats
