@@ -1,0 +1,302 @@
+#!/usr/bin/env python
+"""Benchmark of the FMM-BEM hot path on GB300.
+
+Workload (one step): the two FMM passes of one direct-formulation mat-vec
+on a 4,000,000-point bumpy-sphere surface point set -- a Laplace apply and a
+Yukawa (kappa = 0.125) apply, each with single-layer (monopole) and
+double-layer (dipole, per-point unit normals) sources, expansion order
+p = 6, ncrit = 128, FP32 arithmetic (PB_MIXED).  Metric: FMM apply
+points/s = targets evaluated per apply per second (2 applies per step).
+
+Lines printed (one JSON line on rank 0):
+  --impl ours       (default) the CUDA path through the C-ABI
+  --impl reference  the FP64 direct-sum oracle on the host cores, on a
+                    bounded target sample per step (this run's reference arm)
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_POINTS = 4_000_000
+P_ORDER = 6
+NCRIT = 128
+KAPPA = 0.125
+METRIC = "FMM apply points/s (4M-point surface, Laplace+Yukawa SL+DL, p=6)"
+UNIT = "points/s"
+SM_COUNT = 152
+FP32_LANES = 128
+SM_MAX_MHZ = 2070.0
+# FLOPs per pair (FMA = 2): Laplace SL+DL 19, Yukawa SL+DL 27; monopole-only
+# evaluations of equivalent densities (M2P, L2P): Laplace 10, Yukawa 18.
+FLOPS_PAIR = {"lap_sd": 19, "yuk_sd": 27, "lap_m": 10, "yuk_m": 18}
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=N_POINTS)
+    ap.add_argument("--p", type=int, default=P_ORDER)
+    ap.add_argument("--ncrit", type=int, default=NCRIT)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def inputs(n):
+    import synthetic
+    x, nrm = synthetic.bumpy_sphere_points(n, seed=0)
+    q = synthetic.uniform_densities(n, seed=1)
+    d = synthetic.uniform_densities(n, seed=2)
+    return x, nrm, q, d
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def cpu_model():
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
+
+
+def oracle_sample(x, nrm, q, d, ntgt, seed=5):
+    """FP64 direct sums (the oracle as it stands) for a target sample; returns seconds."""
+    import synthetic
+    from oracle.kernels import LAPLACE, YUKAWA, direct_sum
+    idx = synthetic.random_subsample(len(x), ntgt, seed=seed)
+    t0 = time.perf_counter()
+    direct_sum(LAPLACE, 0.0, x, q=q, dip=d, src_n=nrm, tgt=x[idx])
+    direct_sum(YUKAWA, KAPPA, x, q=q, dip=d, src_n=nrm, tgt=x[idx])
+    return time.perf_counter() - t0
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self, index):
+        self.index = index
+        self.samples = []
+        self.proc = None
+
+    def __enter__(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.samples.append([s.strip() for s in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            time.sleep(0.3)
+            self.proc.terminate()
+            self.proc.wait()
+            self.thread.join(timeout=2)
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(s[1]) for s in self.samples if len(s) > 2 and s[1].replace('.', '', 1).isdigit()]
+        mx = [float(s[2]) for s in self.samples if len(s) > 2 and s[2].replace('.', '', 1).isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for s in self.samples:
+            for k, nm in enumerate(names):
+                if len(s) > 5 + k and s[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(self.samples)}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    x, nrm, q, d = inputs(args.n)
+    ntgt = 400
+    for _ in range(args.warmup):
+        oracle_sample(x, nrm, q, d, ntgt)
+    ts = [oracle_sample(x, nrm, q, d, ntgt, seed=100 + k) for k in range(args.steps)]
+    t = float(np.mean(ts))
+    value = 2 * ntgt / t
+    cores = host_cores()
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"fmm_apply {args.n} bumpy-sphere points, Laplace+Yukawa SL+DL, "
+                                   f"FP64 direct sum on {ntgt} sampled targets per step",
+                       "global_batch": args.n, "seq_len": None, "parallelism": "host cores"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{ntgt} targets x {args.n} sources x 2 kernels per step",
+                             "cpu": cpu_model()},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    import paper_2103_01048_gb300 as pb
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU")
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    # the CPU baseline runs before any GPU work on rank 0 (bounded sample)
+    x, nrm, q, d = inputs(args.n)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        ntgt = 2000
+        t = oracle_sample(x, nrm, q, d, ntgt)
+        cpu = {"value": 2 * ntgt / t, "unit": UNIT, "cores": host_cores(), "kind": "oracle",
+               "sample": f"{ntgt} targets x {args.n} sources, FP64 direct sum, Laplace+Yukawa SL+DL "
+                         f"({t:.1f} s)", "cpu": cpu_model()}
+
+    stream = torch.cuda.Stream()
+    ctx = pb.pb_create(local, stream)
+    X = torch.from_numpy(x).cuda()
+    Nr = torch.from_numpy(nrm).cuda()
+    Q = torch.from_numpy(q).cuda()
+    D = torch.from_numpy(d).cuda()
+    tree = pb.fmm_tree_build(ctx, X, args.ncrit)
+    info = pb.fmm_tree_info(tree)
+    out_l = torch.empty(args.n, device="cuda")
+    out_y = torch.empty(args.n, device="cuda")
+    flush = torch.empty(256 * 1024 * 1024 // 4, device="cuda")
+
+    def step():
+        pb.fmm_apply(ctx, tree, pb.FMM_LAPLACE, 0.0, args.p, out_l, q=Q, dip=D, src_n=Nr)
+        pb.fmm_apply(ctx, tree, pb.FMM_YUKAWA, KAPPA, args.p, out_y, q=Q, dip=D, src_n=Nr)
+
+    # warm-up (also builds and caches the operators)
+    for _ in range(max(args.warmup, 3)):
+        step()
+    pb.pb_sync(ctx)
+    torch.cuda.synchronize()
+
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    pb.pb_profile(ctx, True)
+    with Clocks(local) as clk:
+        for k in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.fill_(float(k))            # L2 flush between timed steps (untimed)
+                ev[k][0].record(stream)
+                step()
+                ev[k][1].record(stream)
+        torch.cuda.synchronize()
+    prof = pb.pb_profile_read(ctx)
+    pb.pb_profile(ctx, False)
+    if dist:
+        dist.barrier()
+    ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
+    if dist:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * 2 * args.n / (ms * 1e-3)
+
+    # e2e through the C-ABI with pinned host buffers (H2D of inputs, D2H of results inside)
+    hq = torch.from_numpy(q).pin_memory()
+    hd = torch.from_numpy(d).pin_memory()
+    hn = torch.from_numpy(nrm).pin_memory()
+    ho_l = torch.empty(args.n).pin_memory()
+    ho_y = torch.empty(args.n).pin_memory()
+
+    def step_host():
+        pb.fmm_apply(ctx, tree, pb.FMM_LAPLACE, 0.0, args.p, ho_l, q=hq, dip=hd, src_n=hn)
+        pb.fmm_apply(ctx, tree, pb.FMM_YUKAWA, KAPPA, args.p, ho_y, q=hq, dip=hd, src_n=hn)
+
+    step_host()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step_host()
+    torch.cuda.synchronize()
+    e2e_ms = (time.perf_counter() - t0) * 1e3 / args.steps
+    h2d = 2 * (q.nbytes + d.nbytes + nrm.nbytes)
+    d2h = 2 * 4 * args.n
+
+    # roofline of the dominant phase (per-launch averages from the library's event timers)
+    phases = {k: v for k, v in prof.items() if k != "launches" and v[1] > 0}
+    dom = max(phases, key=lambda k: phases[k][0])
+    leaf_ms = phases["leaf"][0] / phases["leaf"][1]     # per apply (one leaf launch per apply)
+    p = args.p
+    ne = 6 * (p - 1) ** 2 + 2
+    far = (info.m2p_targets + info.l2p_targets) * ne
+    leaf_flops = (info.p2p_pairs * (FLOPS_PAIR["lap_sd"] + FLOPS_PAIR["yuk_sd"])
+                  + far * (FLOPS_PAIR["lap_m"] + FLOPS_PAIR["yuk_m"])) / 2.0   # average per apply
+    peak = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    achieved = leaf_flops / (leaf_ms * 1e-3) / 1e12
+    roof = {"kernel": "k_leaf_eval (P2P+M2P+L2P)", "bound": "alu", "achieved": achieved, "peak": peak,
+            "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+            "peak_note": "FP32 FMA pipe: 152 SMs x 128 lanes x 2 flop x 2070 MHz (derived, not measured)",
+            "dominant_phase": dom}
+    launches = prof["launches"]
+
+    clocks = clk.summary()
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": f"fmm_apply {args.n} bumpy-sphere points (amp 0.05), Laplace+Yukawa "
+                                       f"(kappa {KAPPA}) SL+DL, p={p}, ncrit={args.ncrit}, tree cached",
+                           "global_batch": args.n * world, "seq_len": None,
+                           "parallelism": "replicas" if world > 1 else "single GPU",
+                           "l2": "flushed between steps (256 MB write)",
+                           "tree": {"boxes": info.n_box, "leaves": info.n_leaf, "levels": info.n_levels,
+                                    "v_pairs": info.n_v, "p2p_pairs": info.p2p_pairs}},
+                "roofline": roof, "cpu_baseline": cpu,
+                "e2e": {"value": world * 2 * args.n / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                        "d2h_bytes_per_step": d2h},
+                "gpu_launches": int(launches), "clocks": clocks,
+                "phases_ms_per_step": {k: v[0] / args.steps for k, v in phases.items()}}
+        print(json.dumps(line), flush=True)
+    pb.fmm_tree_destroy(tree)
+    pb.pb_destroy(ctx)
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,189 @@
+/*
+ * pbfmm — C-ABI of a GB300-native (sm_103a) fast-multipole boundary-element
+ * solver for the linearised Poisson–Boltzmann equation, after the method of
+ * Wang, Cooper, Betcke & Barba, "High-productivity, high-performance workflow
+ * for virus-scale electrostatic simulations with Bempp-Exafmm" (arXiv
+ * 2103.01048).
+ *
+ * Conventions for every entry point
+ *   - Return value: PB_OK (0) on success, else one of the PB_E* codes below;
+ *     no C++ exception crosses the ABI.  pb_last_error(ctx) gives a message.
+ *   - Pointers are plain host or device pointers.  Where an argument says
+ *     "host or device", the library inspects it with cudaPointerGetAttributes
+ *     and stages host data through its own device buffers.
+ *   - Work is ordered on the stream given to pb_create.  Calls documented as
+ *     "asynchronous" return before the GPU finishes; read results after a
+ *     stream synchronisation.
+ *   - Objects returned through `out` parameters are owned by the library and
+ *     released by the matching *_destroy call.  Caller buffers stay caller
+ *     owned; the library never keeps a pointer to them after the call.
+ *   - Coordinates are array-of-structures [n][3]; lengths in Angstrom,
+ *     charges in e, energies in kcal/mol.
+ */
+#ifndef PBFMM_H
+#define PBFMM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* status codes */
+enum {
+    PB_OK = 0,
+    PB_EINVAL = 1,    /* invalid argument (null, size, unsupported option) */
+    PB_ENOMEM = 2,    /* device allocation failed */
+    PB_ECUDA = 3,     /* a CUDA runtime call failed */
+    PB_EMESH = 4,     /* degenerate or non-manifold mesh */
+    PB_ENOCONV = 5,   /* GMRES reached max_iter; last iterate kept */
+    PB_ETIMEOUT = 6   /* a bounded device-side wait gave up */
+};
+
+/* Green's function families (Eq. single_double):
+ * FMM_LAPLACE g = 1/(4 pi r), FMM_YUKAWA g = exp(-kappa r)/(4 pi r). */
+enum { FMM_LAPLACE = 0, FMM_YUKAWA = 1 };
+
+/* arithmetic of the FMM passes */
+enum { PB_MIXED = 0 /* FP32 kernels */, PB_FP64 = 1 /* all-FP64 kernels */ };
+
+typedef struct pb_ctx pb_ctx;
+typedef struct fmm_tree fmm_tree;
+
+/* ------------------------------------------------------------------------ */
+/* Context                                                                   */
+/* ------------------------------------------------------------------------ */
+
+/* Create a context on CUDA device `device`; `cuda_stream` (a cudaStream_t,
+ * may be NULL for the legacy default stream) orders every later call.  The
+ * library owns *out; free it with pb_destroy. */
+int pb_create(pb_ctx** out, int device, void* cuda_stream);
+
+/* Synchronise the context stream and free every library-owned resource of
+ * the context.  Trees created on it must be destroyed first. */
+int pb_destroy(pb_ctx* ctx);
+
+/* Message of the last failing call on this context (static storage owned by
+ * the context; valid until the next call).  Never NULL. */
+const char* pb_last_error(pb_ctx* ctx);
+
+/* Wait for all work queued on the context stream. */
+int pb_sync(pb_ctx* ctx);
+
+/* Per-phase device timers (CUDA events on the context stream).
+ * pb_profile(ctx, 1) enables and resets them, pb_profile(ctx, 0) disables.
+ * pb_profile_read returns, for phase `phase` (PB_PH_*), the accumulated
+ * device milliseconds and the number of timed phase executions; phase
+ * PB_PH_LAUNCHES returns in *calls the number of kernels the library
+ * launched since the reset (ms unused).  Reading synchronises the stream. */
+enum {
+    PB_PH_GATHER = 0,  /* densities into Morton order                  */
+    PB_PH_P2M = 1,     /* leaf sources -> upward check -> UC2UE        */
+    PB_PH_M2M = 2,
+    PB_PH_P2L = 3,
+    PB_PH_M2L = 4,
+    PB_PH_DOWN = 5,    /* L2L + DC2DE per level                        */
+    PB_PH_LEAF = 6,    /* P2P + M2P + L2P                              */
+    PB_PH_SCATTER = 7,
+    PB_PH_BEM = 8,     /* sparse Galerkin glue around the FMM          */
+    PB_PH_GMRES = 9,   /* FP64 Arnoldi / Givens                        */
+    PB_PH_COUNT = 10,
+    PB_PH_LAUNCHES = 100
+};
+int pb_profile(pb_ctx* ctx, int enable);
+int pb_profile_read(pb_ctx* ctx, int phase, double* ms, int64_t* calls);
+
+/* ------------------------------------------------------------------------ */
+/* Octree and interaction lists (Sec. "Fast multipole method": enclosing     */
+/* cube, recursive subdivision until each leaf holds at most ncrit points;   */
+/* near field N(B) and interaction list I(B); adaptive U/V/W/X lists of the  */
+/* kernel-independent FMM the paper cites).                                  */
+/* ------------------------------------------------------------------------ */
+
+/* Build the tree over sources `src_xyz` (device, float [n_src][3]) and, if
+ * `tgt_xyz` is non-NULL, a distinct target set (device, float [n_tgt][3]);
+ * with tgt_xyz NULL the targets are the sources (n_tgt ignored).
+ * ncrit >= 1 is the maximum point count of a leaf (sources plus targets when
+ * the sets differ).  Cube, Morton keys (63-bit, FP64 quantisation with
+ * correctly rounded operations), stable key sort, split rule and list
+ * definitions are documented in the library's DESIGN notes and reproduced
+ * bit for bit by the oracle.  Synchronous (returns when the tree is built).
+ * Errors: PB_EINVAL for n_src < 1, ncrit < 1 or NULL src_xyz. */
+int fmm_tree_build(pb_ctx* ctx, const float* src_xyz, int64_t n_src,
+                   const float* tgt_xyz, int64_t n_tgt, int ncrit, fmm_tree** out);
+
+int fmm_tree_destroy(fmm_tree* tree);
+
+typedef struct {
+    int64_t n_src, n_tgt, n_box, n_leaf;
+    int32_t n_levels;      /* deepest level + 1 */
+    int32_t same;          /* 1 if targets are the sources */
+    int64_t n_u, n_v, n_w, n_x;   /* total entries of each list */
+    double center[3], half_width; /* the enclosing cube */
+    /* algorithmic work of one apply on this tree (exact, from the lists) */
+    int64_t p2p_pairs;     /* point pairs of the U lists (near field)      */
+    int64_t m2p_targets;   /* sum over leaves of targets x |W list|        */
+    int64_t p2l_sources;   /* sum over boxes of X-list source points       */
+    int64_t l2p_targets;   /* targets in leaves at level >= 2              */
+    int64_t p2m_sources;   /* sources in leaves                            */
+    int64_t n_dense_box;   /* boxes at level >= 2 (UC2UE/DC2DE/M2M/L2L)    */
+} fmm_tree_info_t;
+
+int fmm_tree_info(const fmm_tree* tree, fmm_tree_info_t* info);
+
+/* Copy the sorted order out to HOST buffers (any may be NULL):
+ * perm_*[k] = original index of the k-th point in Morton order; keys_* are
+ * the sorted 63-bit keys.  Synchronous. */
+int fmm_tree_export_points(const fmm_tree* tree, int32_t* perm_src, uint64_t* keys_src,
+                           int32_t* perm_tgt, uint64_t* keys_tgt);
+
+/* Copy the boxes out to HOST buffers [n_box] (anchor is [n_box][3]); boxes
+ * are numbered level by level in Morton order, children of a box are
+ * contiguous.  src_begin/src_end index the Morton-sorted sources. */
+int fmm_tree_export_boxes(const fmm_tree* tree, int32_t* level, int32_t* parent,
+                          int32_t* first_child, int32_t* nchild, int32_t* anchor,
+                          int32_t* src_begin, int32_t* src_end,
+                          int32_t* tgt_begin, int32_t* tgt_end);
+
+/* Copy one interaction list out as CSR to HOST buffers: which = 0 (U), 1 (V),
+ * 2 (W), 3 (X); off [n_box + 1], ids [off[n_box]] in ascending box order. */
+int fmm_tree_export_list(const fmm_tree* tree, int which, int64_t* off, int32_t* ids);
+
+/* ------------------------------------------------------------------------ */
+/* FMM matrix-vector product (Eq. nbody_sum through the KIFMM of Sec. "Fast   */
+/* multipole method": P2M, M2M, M2L, L2L, L2P, P2P; equivalent densities      */
+/* matched on check surfaces, Eq. multipole_local).                          */
+/* ------------------------------------------------------------------------ */
+
+/* out[i] = sum_j g(x_i, y_j) q[j] + dg/dn_y(x_i, y_j) dip[j]        (r > 0)
+ * out_dn[i] = sum_j dg/dn_x(x_i, y_j) q[j]     (adjoint double layer, K')
+ * for every target x_i of the tree, approximated by the KIFMM with
+ * expansion order p (points per edge of the equivalent/check surfaces,
+ * n_e = 6(p-1)^2 + 2 surface points; 2 <= p <= 12).
+ *   kernel    FMM_LAPLACE or FMM_YUKAWA (kappa > 0 for Yukawa).
+ *   q         source monopole densities [n_src] or NULL (single layer).
+ *   dip       source dipole densities [n_src] or NULL (double layer); needs
+ *             src_n, the source unit normals [n_src][3].
+ *   tgt_n     target unit normals [n_tgt][3]; needed iff out_dn != NULL.
+ *   out       [n_tgt] potentials in ORIGINAL target order (required).
+ *   out_dn    [n_tgt] target-normal derivatives or NULL.  With out_dn the
+ *             dipole term must be absent (the hypersingular kernel is not
+ *             provided).
+ *   precision PB_MIXED (FP32 arithmetic, FP32 buffers: pass float*) or
+ *             PB_FP64 (FP64 arithmetic, every density/normal/output buffer
+ *             is double*).
+ * Buffers may be host or device memory (see conventions).  With device
+ * buffers the call is asynchronous; with any host buffer it synchronises.
+ * Operators for (kernel, kappa, p, tree size) are precomputed on first use
+ * and cached in the tree.
+ * Errors: PB_EINVAL for missing normals, p out of range, kappa <= 0 with
+ * FMM_YUKAWA, dip together with out_dn. */
+int fmm_apply(pb_ctx* ctx, fmm_tree* tree, int kernel, double kappa, int p, int precision,
+              const void* q, const void* dip, const void* src_n, const void* tgt_n,
+              void* out, void* out_dn);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PBFMM_H */

@@ -1,0 +1,182 @@
+"""Thin Python binding of the pbfmm C-ABI (include/pbfmm.h).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library libpbfmm.so built from csrc/.  Buffers may be torch tensors (device
+or host) or numpy arrays (host); their raw pointers are passed through.
+There is no fallback: importing this package fails if the library is absent.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIBPATH = os.path.join(_HERE, "libpbfmm.so")
+
+if not os.path.exists(_LIBPATH):
+    raise ImportError(f"libpbfmm.so not built ({_LIBPATH}); run paper_2103_01048_gb300.build.build()")
+
+_lib = ctypes.CDLL(_LIBPATH)
+
+PB_OK, PB_EINVAL, PB_ENOMEM, PB_ECUDA, PB_EMESH, PB_ENOCONV, PB_ETIMEOUT = range(7)
+FMM_LAPLACE, FMM_YUKAWA = 0, 1
+PB_MIXED, PB_FP64 = 0, 1
+_ERRNAMES = {1: "PB_EINVAL", 2: "PB_ENOMEM", 3: "PB_ECUDA", 4: "PB_EMESH", 5: "PB_ENOCONV", 6: "PB_ETIMEOUT"}
+
+_P = ctypes.c_void_p
+_I64 = ctypes.c_int64
+
+
+class fmm_tree_info_t(ctypes.Structure):
+    _fields_ = [("n_src", _I64), ("n_tgt", _I64), ("n_box", _I64), ("n_leaf", _I64),
+                ("n_levels", ctypes.c_int32), ("same", ctypes.c_int32),
+                ("n_u", _I64), ("n_v", _I64), ("n_w", _I64), ("n_x", _I64),
+                ("center", ctypes.c_double * 3), ("half_width", ctypes.c_double),
+                ("p2p_pairs", _I64), ("m2p_targets", _I64), ("p2l_sources", _I64), ("l2p_targets", _I64),
+                ("p2m_sources", _I64), ("n_dense_box", _I64)]
+
+
+def _sig(name, args, res=ctypes.c_int):
+    f = getattr(_lib, name)
+    f.argtypes = args
+    f.restype = res
+    return f
+
+
+_sig("pb_create", [ctypes.POINTER(_P), ctypes.c_int, _P])
+_sig("pb_destroy", [_P])
+_sig("pb_last_error", [_P], ctypes.c_char_p)
+_sig("pb_sync", [_P])
+_sig("pb_profile", [_P, ctypes.c_int])
+_sig("pb_profile_read", [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_I64)])
+_sig("fmm_tree_build", [_P, _P, _I64, _P, _I64, ctypes.c_int, ctypes.POINTER(_P)])
+_sig("fmm_tree_destroy", [_P])
+_sig("fmm_tree_info", [_P, ctypes.POINTER(fmm_tree_info_t)])
+_sig("fmm_tree_export_points", [_P, _P, _P, _P, _P])
+_sig("fmm_tree_export_boxes", [_P] + [_P] * 9)
+_sig("fmm_tree_export_list", [_P, ctypes.c_int, _P, _P])
+_sig("fmm_apply", [_P, _P, ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int, _P, _P, _P, _P, _P, _P])
+
+
+class PBError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{_ERRNAMES.get(code, code)}: {msg}")
+        self.code = code
+
+
+def lib_path():
+    return _LIBPATH
+
+
+def exported_symbols():
+    """Names this binding resolves in the library."""
+    return ["pb_create", "pb_destroy", "pb_last_error", "pb_sync", "pb_profile", "pb_profile_read", "fmm_tree_build", "fmm_tree_destroy",
+            "fmm_tree_info", "fmm_tree_export_points", "fmm_tree_export_boxes", "fmm_tree_export_list",
+            "fmm_apply"]
+
+
+def ptr(x):
+    """Raw pointer of a torch tensor / numpy array (None -> NULL)."""
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        if not x.flags.c_contiguous:
+            raise ValueError("array must be C-contiguous")
+        return x.ctypes.data
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return x.data_ptr()
+    raise TypeError(f"unsupported buffer type {type(x)}")
+
+
+def _check(rc, ctx):
+    if rc != PB_OK:
+        raise PBError(rc, _lib.pb_last_error(ctx).decode() if ctx else "")
+
+
+def pb_create(device=0, stream=None):
+    """Context on `device`; `stream` is a torch.cuda.Stream, a raw handle or None."""
+    h = _P()
+    s = None
+    if stream is not None:
+        s = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+    _check(_lib.pb_create(ctypes.byref(h), int(device), s), None)
+    return h
+
+
+def pb_destroy(ctx):
+    _check(_lib.pb_destroy(ctx), None)
+
+
+def pb_sync(ctx):
+    _check(_lib.pb_sync(ctx), ctx)
+
+
+PHASES = ["gather", "p2m", "m2m", "p2l", "m2l", "down", "leaf", "scatter", "bem", "gmres"]
+PB_PH_LAUNCHES = 100
+
+
+def pb_profile(ctx, enable=True):
+    _check(_lib.pb_profile(ctx, 1 if enable else 0), ctx)
+
+
+def pb_profile_read(ctx):
+    """{phase: (ms, calls)} for every phase, plus 'launches'."""
+    res = {}
+    ms = ctypes.c_double()
+    n = _I64()
+    for i, name in enumerate(PHASES):
+        _check(_lib.pb_profile_read(ctx, i, ctypes.byref(ms), ctypes.byref(n)), ctx)
+        res[name] = (ms.value, n.value)
+    _check(_lib.pb_profile_read(ctx, PB_PH_LAUNCHES, ctypes.byref(ms), ctypes.byref(n)), ctx)
+    res["launches"] = n.value
+    return res
+
+
+def fmm_tree_build(ctx, src_xyz, ncrit, tgt_xyz=None):
+    n = int(np.prod(src_xyz.shape)) // 3
+    nt = 0 if tgt_xyz is None else int(np.prod(tgt_xyz.shape)) // 3
+    h = _P()
+    _check(_lib.fmm_tree_build(ctx, ptr(src_xyz), n, ptr(tgt_xyz), nt, int(ncrit), ctypes.byref(h)), ctx)
+    return h
+
+
+def fmm_tree_destroy(tree):
+    _check(_lib.fmm_tree_destroy(tree), None)
+
+
+def fmm_tree_info(tree):
+    info = fmm_tree_info_t()
+    _check(_lib.fmm_tree_info(tree, ctypes.byref(info)), None)
+    return info
+
+
+def fmm_tree_export(ctx, tree):
+    """All tree arrays as numpy (for bit-exact comparison with the oracle)."""
+    info = fmm_tree_info(tree)
+    ns, nt, nb = info.n_src, info.n_tgt, info.n_box
+    out = dict(perm_src=np.zeros(ns, np.int32), keys_src=np.zeros(ns, np.uint64),
+               perm_tgt=np.zeros(nt, np.int32), keys_tgt=np.zeros(nt, np.uint64))
+    _check(_lib.fmm_tree_export_points(tree, *[ptr(out[k]) for k in ("perm_src", "keys_src", "perm_tgt", "keys_tgt")]), ctx)
+    names = ["level", "parent", "first_child", "nchild", "anchor", "src_begin", "src_end", "tgt_begin", "tgt_end"]
+    for k in names:
+        out[k] = np.zeros(nb * 3 if k == "anchor" else nb, np.int32)
+    _check(_lib.fmm_tree_export_boxes(tree, *[ptr(out[k]) for k in names]), ctx)
+    out["anchor"] = out["anchor"].reshape(nb, 3)
+    for which, name in enumerate("UVWX"):
+        off = np.zeros(nb + 1, np.int64)
+        _check(_lib.fmm_tree_export_list(tree, which, ptr(off), None), ctx)
+        ids = np.zeros(max(int(off[-1]), 1), np.int32)
+        _check(_lib.fmm_tree_export_list(tree, which, ptr(off), ptr(ids)), ctx)
+        out[name] = (off, ids[:off[-1]])
+    out["info"] = info
+    return out
+
+
+def fmm_apply(ctx, tree, kernel, kappa, p, out, q=None, dip=None, src_n=None, tgt_n=None, out_dn=None,
+              precision=PB_MIXED):
+    _check(_lib.fmm_apply(ctx, tree, int(kernel), float(kappa), int(p), int(precision), ptr(q), ptr(dip),
+                          ptr(src_n), ptr(tgt_n), ptr(out), ptr(out_dn)), ctx)

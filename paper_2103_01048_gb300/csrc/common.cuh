@@ -1,0 +1,135 @@
+// Shared internals of the pbfmm library (device helpers, context, errors).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string>
+#include <vector>
+#include <cstdio>
+#include <cstring>
+#include <stdexcept>
+
+#include "../../include/pbfmm.h"
+
+namespace pbfmm {
+
+constexpr int kMaxLevel = 21;      // 21 bits per axis in a 63-bit Morton key
+constexpr int kCollCap = 27;       // same-level adjacent boxes, self included
+constexpr int kCoarseCap = 26;     // coarser adjacent leaves (disjoint cubes touching a cube)
+constexpr int kVCap = 189;         // 6^3 - 3^3 children of the parent's colleagues
+constexpr int kXCap = 26;
+constexpr int kNumOffsets = 343;   // 7^3 relative offsets of a V-list pair (27 unused)
+
+// Error carried through the C-ABI: every internal failure throws this and the
+// entry point converts it to a status code + message.
+struct Error : std::runtime_error {
+    int code;
+    Error(int c, const std::string& m) : std::runtime_error(m), code(c) {}
+};
+
+#define PB_CUDA(call)                                                              \
+    do {                                                                           \
+        cudaError_t e_ = (call);                                                   \
+        if (e_ != cudaSuccess)                                                     \
+            throw ::pbfmm::Error(PB_ECUDA, std::string(#call) + ": " +             \
+                                               cudaGetErrorString(e_));            \
+    } while (0)
+
+// Counts the library's kernel launches (reported by pb_profile_read); called
+// once after every launch.
+extern thread_local long long g_launch_count;
+#define PB_CHECK_LAUNCH()                         \
+    do {                                          \
+        ++::pbfmm::g_launch_count;                \
+        PB_CUDA(cudaGetLastError());              \
+    } while (0)
+
+#define PB_REQUIRE(cond, code, msg)                                                \
+    do {                                                                           \
+        if (!(cond)) throw ::pbfmm::Error(code, msg);                              \
+    } while (0)
+
+// Owning device buffer (stream-ordered allocations on the context stream).
+template <typename T>
+struct DBuf {
+    T* p = nullptr;
+    size_t n = 0;
+    cudaStream_t s = nullptr;
+    DBuf() = default;
+    DBuf(const DBuf&) = delete;
+    DBuf& operator=(const DBuf&) = delete;
+    ~DBuf() { release(); }
+    void release() {
+        if (p) cudaFreeAsync(p, s);
+        p = nullptr;
+        n = 0;
+    }
+    void alloc(size_t count, cudaStream_t stream) {
+        release();
+        s = stream;
+        n = count;
+        if (count) {
+            cudaError_t e = cudaMallocAsync((void**)&p, count * sizeof(T), stream);
+            if (e != cudaSuccess) {
+                p = nullptr;
+                n = 0;
+                throw Error(PB_ENOMEM, std::string("device allocation failed: ") + cudaGetErrorString(e));
+            }
+        }
+    }
+    // grow keeping contents
+    void grow(size_t count, cudaStream_t stream) {
+        if (count <= n) return;
+        T* q = nullptr;
+        cudaError_t e = cudaMallocAsync((void**)&q, count * sizeof(T), stream);
+        if (e != cudaSuccess) throw Error(PB_ENOMEM, "device allocation failed");
+        if (n) PB_CUDA(cudaMemcpyAsync(q, p, n * sizeof(T), cudaMemcpyDeviceToDevice, stream));
+        if (p) cudaFreeAsync(p, s);
+        p = q;
+        n = count;
+        s = stream;
+    }
+    void zero(cudaStream_t stream) {
+        if (n) PB_CUDA(cudaMemsetAsync(p, 0, n * sizeof(T), stream));
+    }
+};
+
+inline int div_up(long long a, long long b) { return (int)((a + b - 1) / b); }
+
+}  // namespace pbfmm
+
+// The opaque context of the C-ABI.
+struct pb_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    std::string last_error;
+    int sm_count = 0;
+    // per-phase device timers
+    bool profile = false;
+    double prof_ms[PB_PH_COUNT] = {};
+    long long prof_calls[PB_PH_COUNT] = {};
+    long long launch_base = 0;
+    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> pending;
+};
+
+namespace pbfmm {
+// Scoped phase timer: records an event pair around a phase when profiling.
+struct PhaseTimer {
+    pb_ctx* ctx;
+    int phase;
+    cudaEvent_t a = nullptr, b = nullptr;
+    PhaseTimer(pb_ctx* c, int ph) : ctx(c), phase(ph) {
+        if (ctx->profile) {
+            cudaEventCreate(&a);
+            cudaEventCreate(&b);
+            cudaEventRecord(a, ctx->stream);
+        }
+    }
+    ~PhaseTimer() {
+        if (a) {
+            cudaEventRecord(b, ctx->stream);
+            ctx->pending.push_back({phase, {a, b}});
+        }
+    }
+};
+void profile_collect(pb_ctx* ctx);
+}  // namespace pbfmm

@@ -1,0 +1,561 @@
+// KIFMM apply (Sec. "Fast multipole method"): upward pass (P2M at leaves,
+// M2M in post-order), M2L over the interaction lists, downward pass (L2L in
+// pre-order), then L2P + P2P at the leaves.  Adaptive-tree extras: M2P for
+// the W list and P2L for the X list.
+//
+// Layout in HBM: Morton-sorted sources as float4 (x, y, z, q) plus float4
+// (d n_x, d n_y, d n_z, 0) for double-layer sources; equivalent densities
+// and check potentials box-major [n_box][npad].  Everything here is templated
+// on the arithmetic type: float (mixed path) and double (all-FP64 path).
+#include "fmm.cuh"
+#include <algorithm>
+#include <memory>
+
+namespace pbfmm {
+
+constexpr double kInv4PiD = 0.07957747154594767;
+
+template <typename T> struct V4;
+template <> struct V4<float> { using type = float4; };
+template <> struct V4<double> { using type = double4; };
+
+template <typename T> __device__ __forceinline__ T rsqrt_t(T x);
+template <> __device__ __forceinline__ float rsqrt_t<float>(float x) { return rsqrtf(x); }
+template <> __device__ __forceinline__ double rsqrt_t<double>(double x) { return rsqrt(x); }
+template <typename T> __device__ __forceinline__ T exp_t(T x);
+template <> __device__ __forceinline__ float exp_t<float>(float x) { return __expf(x); }
+template <> __device__ __forceinline__ double exp_t<double>(double x) { return exp(x); }
+
+// One source-target interaction, without the 1/(4 pi) factor:
+//   pot += g q + (d.m) f,   dn += -(d.n_t) f q,   d = x_t - y_s,
+//   g = e/r, f = e (1 + kappa r)/r^3, e = exp(-kappa r) (Yukawa) or 1.
+template <typename T, bool YUK, bool DL, bool DN>
+__device__ __forceinline__ void interact(T dx, T dy, T dz, T q, T mx, T my, T mz, T nx, T ny, T nz, T kappa,
+                                         T& pot, T& dn) {
+    T r2 = dx * dx + dy * dy + dz * dz;
+    T rinv = r2 > T(0) ? rsqrt_t<T>(r2) : T(0);
+    T g = rinv, f = rinv * rinv * rinv;
+    if (YUK) {
+        T r = r2 * rinv;
+        T e = exp_t<T>(-kappa * r);
+        g *= e;
+        f *= e * (T(1) + kappa * r);
+    }
+    pot += g * q;
+    if (DL) pot += (dx * mx + dy * my + dz * mz) * f;
+    if (DN) dn -= (dx * nx + dy * ny + dz * nz) * f * q;
+}
+
+// ---------------------------------------------------------------------------
+// gather of the densities into Morton order
+// ---------------------------------------------------------------------------
+template <typename T, typename In>
+__global__ void k_gather_src(long long n, const int* __restrict__ perm, const float4* __restrict__ pos,
+                             const In* __restrict__ q, const In* __restrict__ dip, const In* __restrict__ nrm,
+                             typename V4<T>::type* __restrict__ sq, typename V4<T>::type* __restrict__ sm) {
+    long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    long long i = perm[k];
+    float4 p = pos[k];
+    T qq = q ? (T)q[i] : T(0);
+    sq[k] = {(T)p.x, (T)p.y, (T)p.z, qq};
+    if (sm) {
+        T d = (T)dip[i];
+        sm[k] = {d * (T)nrm[3 * i], d * (T)nrm[3 * i + 1], d * (T)nrm[3 * i + 2], T(0)};
+    }
+}
+
+template <typename T, typename In>
+__global__ void k_gather_tn(long long n, const int* __restrict__ perm, const In* __restrict__ nrm,
+                            typename V4<T>::type* __restrict__ tn) {
+    long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    long long i = perm[k];
+    tn[k] = {(T)nrm[3 * i], (T)nrm[3 * i + 1], (T)nrm[3 * i + 2], T(0)};
+}
+
+template <typename T, typename Out>
+__global__ void k_scatter(long long n, const int* __restrict__ perm, const T* __restrict__ v, Out* __restrict__ out) {
+    long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    out[perm[k]] = (Out)v[k];
+}
+
+// ---------------------------------------------------------------------------
+// P2M / P2L: source points -> check surface of a box.
+// One CTA per box.  Sources are taken relative to the box centre (FP64
+// subtraction) so the surface geometry keeps full relative precision.
+// mode 0 (P2M): sources = the box's own points, check surface at 2.95 r.
+// mode 1 (P2L): sources = points of the X-list leaves, check surface at 1.05 r.
+// ---------------------------------------------------------------------------
+template <typename T, bool YUK, bool DL>
+__global__ void __launch_bounds__(128) k_p2check(int nbox, const int* __restrict__ boxes, int mode,
+                                                 const double4* __restrict__ center, const int* __restrict__ sb,
+                                                 const int* __restrict__ se, const int* __restrict__ X,
+                                                 const int* __restrict__ X_n,
+                                                 const typename V4<T>::type* __restrict__ sq,
+                                                 const typename V4<T>::type* __restrict__ sm,
+                                                 const float4* __restrict__ surf, int ne, int npad, T kappa,
+                                                 T* __restrict__ chk) {
+    using V = typename V4<T>::type;
+    constexpr int CH = 128;
+    constexpr int MAXP = 4;   // check points per thread (ne <= 512)
+    __shared__ V s_q[CH];
+    __shared__ V s_m[DL ? CH : 1];
+    int bi = blockIdx.x;
+    if (bi >= nbox) return;
+    int b = boxes[bi];
+    double4 c = center[b];
+    T alpha = T(mode == 0 ? kAlphaOuter : kAlphaInner) * (T)c.w;
+    T px[MAXP], py[MAXP], pz[MAXP], acc[MAXP];
+#pragma unroll
+    for (int m = 0; m < MAXP; ++m) {
+        int i = threadIdx.x + m * CH;
+        float4 s = (i < ne) ? surf[i] : make_float4(0, 0, 0, 0);
+        px[m] = alpha * (T)s.x; py[m] = alpha * (T)s.y; pz[m] = alpha * (T)s.z;
+        acc[m] = T(0);
+    }
+    int nlist = (mode == 0) ? 1 : X_n[b];
+    T dummy = T(0);
+    for (int li = 0; li < nlist; ++li) {
+        int a = (mode == 0) ? b : X[(long long)b * kXCap + li];
+        int j0 = sb[a], j1 = se[a];
+        for (int jc = j0; jc < j1; jc += CH) {
+            int j = jc + threadIdx.x;
+            __syncthreads();
+            if (j < j1) {
+                V v = sq[j];
+                s_q[threadIdx.x] = {(T)((double)v.x - c.x), (T)((double)v.y - c.y), (T)((double)v.z - c.z), v.w};
+                if (DL) s_m[threadIdx.x] = sm[j];
+            }
+            __syncthreads();
+            int cnt = min(CH, j1 - jc);
+            for (int t = 0; t < cnt; ++t) {
+                V s = s_q[t];
+                T mx = 0, my = 0, mz = 0;
+                if (DL) { V mm = s_m[t]; mx = mm.x; my = mm.y; mz = mm.z; }
+#pragma unroll
+                for (int m = 0; m < MAXP; ++m)
+                    interact<T, YUK, DL, false>(px[m] - s.x, py[m] - s.y, pz[m] - s.z, s.w, mx, my, mz, 0, 0, 0,
+                                                kappa, acc[m], dummy);
+            }
+        }
+    }
+#pragma unroll
+    for (int m = 0; m < MAXP; ++m) {
+        int i = threadIdx.x + m * CH;
+        if (i < npad) chk[(long long)b * npad + i] = (i < ne) ? acc[m] * T(kInv4PiD) : T(0);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Dense operator x box-vector products (UC2UE, DC2DE, M2M, L2L, M2L), SIMT.
+// A CTA computes C[npad x 32 boxes] = sum over terms of Op_term x X_gathered,
+// 256 threads as 16 row groups x 16 column pairs, K chunks of 16 in smem.
+// ---------------------------------------------------------------------------
+constexpr int kTC = 32;    // boxes per tile (= kM2LTile)
+static_assert(kTC == kM2LTile, "M2L tile width");
+
+enum GemmMode { G_DENSE = 0, G_M2M = 1, G_L2L = 2, G_M2L = 3 };
+
+struct GemmArgs {
+    int mode;
+    int ncols;                 // number of column boxes (modes 0-2)
+    const int* cols;           // column box ids (modes 0-2); NULL: col_base + i
+    int col_base;
+    const int* first_child;
+    const int* nchild;
+    const int4* anchor;
+    const int* parent;
+    // M2L schedule
+    const int* tile_box;
+    const int* tile_level;
+    const int* entry_off;
+    const int* entry_oidx;
+    const int* entry_src;
+    int level;                 // operator level (modes 0-2)
+    int accumulate;            // mode 0: Y += (else Y =)
+};
+
+template <typename T, int NPAD>
+__global__ void __launch_bounds__(256) k_box_gemm(GemmArgs a, const T* __restrict__ ops, const T* __restrict__ Xv,
+                                                  T* __restrict__ Yv) {
+    constexpr int KC = (sizeof(T) * NPAD * 16 > 40000) ? 8 : 16;
+    constexpr int RPT = NPAD / 16;
+    __shared__ T s_op[KC][NPAD + 1];
+    __shared__ T s_x[KC][kTC + 1];
+    __shared__ int s_src[kTC];
+    __shared__ int s_dst[kTC];
+    const int tid = threadIdx.x;
+    const int ty = tid / 16, tx = tid % 16;   // row group, column pair
+    const int tile = blockIdx.x;
+    const size_t m2 = (size_t)NPAD * NPAD;
+    int nterm, level;
+    if (a.mode == G_M2L) {
+        nterm = a.entry_off[tile + 1] - a.entry_off[tile];
+        level = a.tile_level[tile];
+    } else {
+        nterm = (a.mode == G_DENSE) ? 1 : 8;
+        level = a.level;
+    }
+    T acc[RPT][2];
+#pragma unroll
+    for (int r = 0; r < RPT; ++r) acc[r][0] = acc[r][1] = T(0);
+    for (int term = 0; term < nterm; ++term) {
+        // columns: source box for this term, destination box
+        __syncthreads();
+        if (tid < kTC) {
+            int src = -1, dst = -1;
+            if (a.mode == G_M2L) {
+                int e = a.entry_off[tile] + term;
+                src = a.entry_src[(long long)e * kTC + tid];
+                dst = a.tile_box[(long long)tile * kTC + tid];
+            } else {
+                int ci = tile * kTC + tid;
+                int b = ci < a.ncols ? (a.cols ? a.cols[ci] : a.col_base + ci) : -1;
+                if (b >= 0) {
+                    if (a.mode == G_DENSE) { src = b; dst = b; }
+                    else {
+                        // child of b in octant `term` (M2M: source; L2L: destination)
+                        int ch = -1;
+                        int f = a.first_child[b], nc = a.nchild[b];
+                        for (int k = 0; k < nc; ++k) {
+                            int4 an = a.anchor[f + k];
+                            int oct = ((an.x & 1) << 2) | ((an.y & 1) << 1) | (an.z & 1);
+                            if (oct == term) ch = f + k;
+                        }
+                        if (a.mode == G_M2M) { src = ch; dst = nc > 0 ? b : -1; }
+                        else { src = (ch >= 0) ? b : -1; dst = ch; }
+                    }
+                }
+            }
+            s_src[tid] = src;
+            s_dst[tid] = dst;
+        }
+        __syncthreads();
+        bool any = false;
+        for (int c = 0; c < kTC; ++c) any |= (s_src[c] >= 0);
+        if (!any) continue;
+        const T* op;
+        if (a.mode == G_M2L) op = ops + ((size_t)level * kNumOffsets + a.entry_oidx[a.entry_off[tile] + term]) * m2;
+        else if (a.mode == G_DENSE) op = ops + (size_t)level * m2;
+        else op = ops + ((size_t)level * 8 + term) * m2;
+        for (int k0 = 0; k0 < NPAD; k0 += KC) {
+            __syncthreads();
+            for (int i = tid; i < NPAD * KC; i += 256) {
+                int row = i / KC, kk = i % KC;
+                s_op[kk][row] = op[(size_t)row * NPAD + k0 + kk];
+            }
+            for (int i = tid; i < kTC * KC; i += 256) {
+                int c = i / KC, kk = i % KC;
+                int s = s_src[c];
+                s_x[kk][c] = (s >= 0) ? Xv[(size_t)s * NPAD + k0 + kk] : T(0);
+            }
+            __syncthreads();
+#pragma unroll
+            for (int kk = 0; kk < KC; ++kk) {
+                T x0 = s_x[kk][2 * tx], x1 = s_x[kk][2 * tx + 1];
+#pragma unroll
+                for (int r = 0; r < RPT; ++r) {
+                    T o = s_op[kk][ty + 16 * r];
+                    acc[r][0] += o * x0;
+                    acc[r][1] += o * x1;
+                }
+            }
+        }
+        if (a.mode == G_L2L) {
+#pragma unroll
+            for (int cc = 0; cc < 2; ++cc) {
+                int d = s_dst[2 * tx + cc];
+                if (d >= 0) {
+#pragma unroll
+                    for (int r = 0; r < RPT; ++r) Yv[(size_t)d * NPAD + ty + 16 * r] += acc[r][cc];
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < RPT; ++r) acc[r][0] = acc[r][1] = T(0);
+        }
+    }
+    if (a.mode == G_L2L) return;
+#pragma unroll
+    for (int cc = 0; cc < 2; ++cc) {
+        int d = s_dst[2 * tx + cc];
+        if (d < 0) continue;
+        bool add = (a.mode == G_M2L) || (a.mode == G_DENSE && a.accumulate);
+#pragma unroll
+        for (int r = 0; r < RPT; ++r) {
+            size_t o = (size_t)d * NPAD + ty + 16 * r;
+            Yv[o] = add ? Yv[o] + acc[r][cc] : acc[r][cc];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Leaf evaluation: P2P over U(B), M2P over W(B), L2P of B's own downward
+// equivalent density, at every target of leaf B.  One CTA per target leaf.
+// ---------------------------------------------------------------------------
+template <typename T, bool YUK, bool DL, bool DN>
+__global__ void __launch_bounds__(128) k_leaf_eval(const int* __restrict__ leaves, int nleaf,
+                                                   const int* __restrict__ tb, const int* __restrict__ te,
+                                                   const int* __restrict__ sb, const int* __restrict__ se,
+                                                   const int* __restrict__ U_off, const int* __restrict__ U_ids,
+                                                   const int* __restrict__ W_off, const int* __restrict__ W_ids,
+                                                   const int* __restrict__ level, const double4* __restrict__ center,
+                                                   const float4* __restrict__ tpos,
+                                                   const typename V4<T>::type* __restrict__ tn,
+                                                   const typename V4<T>::type* __restrict__ sq,
+                                                   const typename V4<T>::type* __restrict__ sm,
+                                                   const T* __restrict__ Qu, const T* __restrict__ Qd,
+                                                   const float4* __restrict__ surf, int ne, int npad, T kappa,
+                                                   T* __restrict__ pot_out, T* __restrict__ dn_out) {
+    using V = typename V4<T>::type;
+    constexpr int CH = 128;
+    __shared__ V s_q[CH];
+    __shared__ V s_m[DL ? CH : 1];
+    int li = blockIdx.x;
+    if (li >= nleaf) return;
+    int b = leaves[li];
+    int t0 = tb[b], t1 = te[b];
+    for (int tc = t0; tc < t1; tc += CH) {
+        int t = tc + threadIdx.x;
+        bool valid = t < t1;
+        float4 xp = valid ? tpos[t] : make_float4(0, 0, 0, 0);
+        T x = xp.x, y = xp.y, z = xp.z;
+        T nx = 0, ny = 0, nz = 0;
+        if (DN && valid) { V nn = tn[t]; nx = nn.x; ny = nn.y; nz = nn.z; }
+        T pot = 0, dn = 0;
+        // P2P
+        for (int ui = U_off[b]; ui < U_off[b + 1]; ++ui) {
+            int a = U_ids[ui];
+            int j0 = sb[a], j1 = se[a];
+            for (int jc = j0; jc < j1; jc += CH) {
+                int j = jc + threadIdx.x;
+                __syncthreads();
+                if (j < j1) {
+                    s_q[threadIdx.x] = sq[j];
+                    if (DL) s_m[threadIdx.x] = sm[j];
+                }
+                __syncthreads();
+                int cnt = min(CH, j1 - jc);
+                for (int k = 0; k < cnt; ++k) {
+                    V s = s_q[k];
+                    T mx = 0, my = 0, mz = 0;
+                    if (DL) { V mm = s_m[k]; mx = mm.x; my = mm.y; mz = mm.z; }
+                    interact<T, YUK, DL, DN>(x - s.x, y - s.y, z - s.z, s.w, mx, my, mz, nx, ny, nz, kappa, pot, dn);
+                }
+            }
+        }
+        // M2P (W list) and L2P (own downward equivalent): monopole equivalent densities
+        int nw = W_off[b + 1] - W_off[b];
+        int nsrcbox = nw + (level[b] >= 2 ? 1 : 0);
+        for (int wi = 0; wi < nsrcbox; ++wi) {
+            int a = (wi < nw) ? W_ids[W_off[b] + wi] : b;
+            const T* Q = (wi < nw) ? Qu : Qd;
+            double4 ca = center[a];
+            T alpha = T(wi < nw ? kAlphaInner : kAlphaOuter) * (T)ca.w;
+            T rx = (T)((double)xp.x - ca.x), ry = (T)((double)xp.y - ca.y), rz = (T)((double)xp.z - ca.z);
+            for (int jc = 0; jc < ne; jc += CH) {
+                int j = jc + threadIdx.x;
+                __syncthreads();
+                if (j < ne) {
+                    float4 s = surf[j];
+                    s_q[threadIdx.x] = {alpha * (T)s.x, alpha * (T)s.y, alpha * (T)s.z, Q[(size_t)a * npad + j]};
+                }
+                __syncthreads();
+                int cnt = min(CH, ne - jc);
+                for (int k = 0; k < cnt; ++k) {
+                    V s = s_q[k];
+                    interact<T, YUK, false, DN>(rx - s.x, ry - s.y, rz - s.z, s.w, 0, 0, 0, nx, ny, nz, kappa, pot, dn);
+                }
+            }
+        }
+        if (valid) {
+            pot_out[t] = pot * T(kInv4PiD);
+            if (DN) dn_out[t] = dn * T(kInv4PiD);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// host driver
+// ---------------------------------------------------------------------------
+template <typename T>
+struct Work {
+    DBuf<typename V4<T>::type> sq, sm, tn;
+    DBuf<T> Qu, Qd, chk, pot, dn;
+};
+
+template <typename T, int NPAD>
+static void gemm_launch(cudaStream_t st, int nblocks, const GemmArgs& a, const T* ops, const T* X, T* Y) {
+    if (nblocks <= 0) return;
+    k_box_gemm<T, NPAD><<<nblocks, 256, 0, st>>>(a, ops, X, Y);
+    PB_CHECK_LAUNCH();
+}
+
+template <typename T>
+static void gemm_dispatch(int npad, cudaStream_t st, int nblocks, const GemmArgs& a, const T* ops, const T* X, T* Y) {
+    switch (npad) {
+        case 16: gemm_launch<T, 16>(st, nblocks, a, ops, X, Y); break;
+        case 32: gemm_launch<T, 32>(st, nblocks, a, ops, X, Y); break;
+        case 64: gemm_launch<T, 64>(st, nblocks, a, ops, X, Y); break;
+        case 112: gemm_launch<T, 112>(st, nblocks, a, ops, X, Y); break;
+        case 160: gemm_launch<T, 160>(st, nblocks, a, ops, X, Y); break;
+        case 208: gemm_launch<T, 208>(st, nblocks, a, ops, X, Y); break;
+        case 304: gemm_launch<T, 304>(st, nblocks, a, ops, X, Y); break;
+        case 400: gemm_launch<T, 400>(st, nblocks, a, ops, X, Y); break;
+        case 496: gemm_launch<T, 496>(st, nblocks, a, ops, X, Y); break;
+        default: throw Error(PB_EINVAL, "unsupported expansion order");
+    }
+}
+
+template <typename T, bool YUK, bool DL>
+static void launch_p2check(cudaStream_t st, int nbox, const int* boxes, int mode, fmm_tree* Tr, Work<T>& W,
+                           const Operators& O, T kappa) {
+    if (nbox <= 0) return;
+    k_p2check<T, YUK, DL><<<nbox, 128, 0, st>>>(nbox, boxes, mode, Tr->center.p, Tr->sb.p, Tr->se.p, Tr->X.p,
+                                                Tr->X_n.p, W.sq.p, W.sm.p, (const float4*)O.surf_f.p, O.ne, O.npad, kappa, W.chk.p);
+    PB_CHECK_LAUNCH();
+}
+
+template <typename T, bool YUK, bool DL, bool DN>
+static void launch_leaf(cudaStream_t st, fmm_tree* Tr, Work<T>& W, const Operators& O, T kappa) {
+    if (Tr->n_tleaf <= 0) return;
+    const float4* tpos = Tr->same ? Tr->pos_s.p : Tr->pos_t.p;
+    const int* tb = Tr->same ? Tr->sb.p : Tr->tb.p;
+    const int* te = Tr->same ? Tr->se.p : Tr->te.p;
+    k_leaf_eval<T, YUK, DL, DN><<<Tr->n_tleaf, 128, 0, st>>>(
+        Tr->leaf_ids.p, Tr->n_tleaf, tb, te, Tr->sb.p, Tr->se.p, Tr->U_off.p, Tr->U_ids.p, Tr->W_off.p, Tr->W_ids.p,
+        Tr->level.p, Tr->center.p, tpos, W.tn.p, W.sq.p, W.sm.p, W.Qu.p, W.Qd.p, (const float4*)O.surf_f.p, O.ne, O.npad, kappa,
+        W.pot.p, W.dn.p);
+    PB_CHECK_LAUNCH();
+}
+
+template <typename T>
+static const T* opsel(const Operators& O, const DBuf<float>& f, const DBuf<double>& d);
+template <>
+const float* opsel<float>(const Operators&, const DBuf<float>& f, const DBuf<double>&) { return f.p; }
+template <>
+const double* opsel<double>(const Operators&, const DBuf<float>&, const DBuf<double>& d) { return d.p; }
+
+template <typename T, typename In, bool YUK>
+static void apply_t(fmm_tree* Tr, const Operators& O, double kappa_d, const In* q, const In* dip, const In* src_n,
+                    const In* tgt_n, In* out, In* out_dn) {
+    cudaStream_t st = Tr->ctx->stream;
+    const long long ns = Tr->ns, nt = Tr->same ? Tr->ns : Tr->nt;
+    const int npad = O.npad, nb = Tr->nbox;
+    const T kappa = (T)kappa_d;
+    const bool DL = dip != nullptr, DN = out_dn != nullptr;
+    Work<T> W;
+    W.sq.alloc(ns, st);
+    if (DL) W.sm.alloc(ns, st);
+    W.Qu.alloc((size_t)nb * npad, st);
+    W.Qd.alloc((size_t)nb * npad, st);
+    W.chk.alloc((size_t)nb * npad, st);
+    W.pot.alloc(nt, st);
+    if (DN) { W.dn.alloc(nt, st); W.tn.alloc(nt, st); }
+    W.Qu.zero(st);
+    W.Qd.zero(st);
+    W.chk.zero(st);
+    pb_ctx* ctx = Tr->ctx;
+    auto ph = std::make_unique<PhaseTimer>(ctx, PB_PH_GATHER);
+    k_gather_src<T, In><<<div_up(ns, 256), 256, 0, st>>>(ns, Tr->perm_s.p, Tr->pos_s.p, q, dip, src_n, W.sq.p,
+                                                          DL ? W.sm.p : nullptr);
+    PB_CHECK_LAUNCH();
+    if (DN) {
+        const int* pt = Tr->same ? Tr->perm_s.p : Tr->perm_t.p;
+        k_gather_tn<T, In><<<div_up(nt, 256), 256, 0, st>>>(nt, pt, tgt_n, W.tn.p);
+        PB_CHECK_LAUNCH();
+    }
+    const T* uc2ue = opsel<T>(O, O.uc2ue, O.uc2ue_d);
+    const T* dc2de = opsel<T>(O, O.dc2de, O.dc2de_d);
+    const T* m2m = opsel<T>(O, O.m2m, O.m2m_d);
+    const T* l2l = opsel<T>(O, O.l2l, O.l2l_d);
+    const T* m2l = opsel<T>(O, O.m2l, O.m2l_d);
+    GemmArgs ga{};
+    ga.first_child = Tr->first_child.p;
+    ga.nchild = Tr->nchild.p;
+    ga.anchor = Tr->anchor.p;
+    ga.parent = Tr->parent.p;
+    const int nsl = Tr->sleaf_lvl_off[Tr->nlev];
+    ph.reset(); ph = std::make_unique<PhaseTimer>(ctx, PB_PH_P2M);
+    // ---- upward pass: P2M at leaves with sources, then UC2UE per level
+    if (DL) launch_p2check<T, YUK, true>(st, nsl, Tr->sleaf_ids.p, 0, Tr, W, O, kappa);
+    else launch_p2check<T, YUK, false>(st, nsl, Tr->sleaf_ids.p, 0, Tr, W, O, kappa);
+    for (int l = 0; l < Tr->nlev; ++l) {
+        int a0 = Tr->sleaf_lvl_off[l], a1 = Tr->sleaf_lvl_off[l + 1];
+        if (a1 <= a0) continue;
+        ga.mode = G_DENSE; ga.ncols = a1 - a0; ga.cols = Tr->sleaf_ids.p + a0; ga.col_base = 0;
+        ga.level = l; ga.accumulate = 0;
+        gemm_dispatch<T>(npad, st, div_up(a1 - a0, kTC), ga, uc2ue, W.chk.p, W.Qu.p);
+    }
+    ph.reset(); ph = std::make_unique<PhaseTimer>(ctx, PB_PH_M2M);
+    // M2M, post-order: parents at level l from children at level l + 1
+    // (leaves of level l keep their P2M result: the kernel skips them)
+    for (int l = Tr->nlev - 2; l >= 2; --l) {
+        int a0 = Tr->lvl_off[l], a1 = Tr->lvl_off[l + 1];
+        ga.mode = G_M2M; ga.ncols = a1 - a0; ga.cols = nullptr; ga.col_base = a0; ga.level = l + 1;
+        gemm_dispatch<T>(npad, st, div_up(a1 - a0, kTC), ga, m2m, W.Qu.p, W.Qu.p);
+    }
+    ph.reset(); ph = std::make_unique<PhaseTimer>(ctx, PB_PH_P2L);
+    // ---- far field into downward check potentials: P2L (X list), M2L (V list)
+    W.chk.zero(st);
+    if (Tr->n_xbox > 0) {
+        if (DL) launch_p2check<T, YUK, true>(st, Tr->n_xbox, Tr->xbox_ids.p, 1, Tr, W, O, kappa);
+        else launch_p2check<T, YUK, false>(st, Tr->n_xbox, Tr->xbox_ids.p, 1, Tr, W, O, kappa);
+    }
+    ph.reset(); ph = std::make_unique<PhaseTimer>(ctx, PB_PH_M2L);
+    if (Tr->m2l.ntile > 0) {
+        ga.mode = G_M2L;
+        ga.tile_box = Tr->m2l.tile_box.p;
+        ga.tile_level = Tr->m2l.tile_level.p;
+        ga.entry_off = Tr->m2l.entry_off.p;
+        ga.entry_oidx = Tr->m2l.entry_offset_idx.p;
+        ga.entry_src = Tr->m2l.entry_src.p;
+        gemm_dispatch<T>(npad, st, Tr->m2l.ntile, ga, m2l, W.Qu.p, W.chk.p);
+    }
+    ph.reset(); ph = std::make_unique<PhaseTimer>(ctx, PB_PH_DOWN);
+    // ---- downward pass, pre-order: L2L from the parent (levels >= 3), then DC2DE
+    for (int l = 2; l < Tr->nlev; ++l) {
+        int a0 = Tr->lvl_off[l], a1 = Tr->lvl_off[l + 1];
+        if (l >= 3) {
+            int p0 = Tr->lvl_off[l - 1], p1 = Tr->lvl_off[l];
+            ga.mode = G_L2L; ga.ncols = p1 - p0; ga.cols = nullptr; ga.col_base = p0; ga.level = l;
+            gemm_dispatch<T>(npad, st, div_up(p1 - p0, kTC), ga, l2l, W.Qd.p, W.chk.p);
+        }
+        ga.mode = G_DENSE; ga.ncols = a1 - a0; ga.cols = nullptr; ga.col_base = a0; ga.level = l; ga.accumulate = 0;
+        gemm_dispatch<T>(npad, st, div_up(a1 - a0, kTC), ga, dc2de, W.chk.p, W.Qd.p);
+    }
+    ph.reset(); ph = std::make_unique<PhaseTimer>(ctx, PB_PH_LEAF);
+    // ---- leaves: P2P + M2P + L2P
+    if (DL) {
+        if (DN) throw Error(PB_EINVAL, "double layer with target-normal derivative is not provided");
+        launch_leaf<T, YUK, true, false>(st, Tr, W, O, kappa);
+    } else {
+        if (DN) launch_leaf<T, YUK, false, true>(st, Tr, W, O, kappa);
+        else launch_leaf<T, YUK, false, false>(st, Tr, W, O, kappa);
+    }
+    ph.reset(); ph = std::make_unique<PhaseTimer>(ctx, PB_PH_SCATTER);
+    const int* pt = Tr->same ? Tr->perm_s.p : Tr->perm_t.p;
+    k_scatter<T, In><<<div_up(nt, 256), 256, 0, st>>>(nt, pt, W.pot.p, out);
+    PB_CHECK_LAUNCH();
+    if (DN) k_scatter<T, In><<<div_up(nt, 256), 256, 0, st>>>(nt, pt, W.dn.p, out_dn);
+    if (DN) PB_CHECK_LAUNCH();
+    ph.reset();
+}
+
+void fmm_apply_impl(fmm_tree* Tr, int kernel, double kappa, int p, int precision, const void* q, const void* dip,
+                    const void* src_n, const void* tgt_n, void* out, void* out_dn) {
+    auto O = get_operators(Tr, kernel, kappa, p, precision == PB_FP64);
+    bool yuk = kernel == FMM_YUKAWA;
+    if (precision == PB_FP64) {
+        auto f = yuk ? apply_t<double, double, true> : apply_t<double, double, false>;
+        f(Tr, *O, kappa, (const double*)q, (const double*)dip, (const double*)src_n, (const double*)tgt_n,
+          (double*)out, (double*)out_dn);
+    } else {
+        auto f = yuk ? apply_t<float, float, true> : apply_t<float, float, false>;
+        f(Tr, *O, kappa, (const float*)q, (const float*)dip, (const float*)src_n, (const float*)tgt_n, (float*)out,
+          (float*)out_dn);
+    }
+}
+
+}  // namespace pbfmm

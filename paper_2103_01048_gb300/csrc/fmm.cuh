@@ -1,0 +1,36 @@
+// KIFMM operators and apply (Sec. "Fast multipole method").
+#pragma once
+#include "tree.cuh"
+
+namespace pbfmm {
+
+// Surface radii relative to the box half-width (kernel-independent FMM of
+// Ying, Biros & Zorin, cited by the paper): upward equivalent surface close
+// to the box, upward check surface outside it; the downward pair swapped.
+constexpr double kAlphaInner = 1.05;
+constexpr double kAlphaOuter = 2.95;
+
+inline int surface_count(int p) { return 6 * (p - 1) * (p - 1) + 2; }
+inline int pad16(int n) { return (n + 15) / 16 * 16; }
+
+// Translation operators for one (kernel, kappa, p) on one tree, per level.
+// Matrices are row-major [npad][npad] (row = output point, column = input
+// point), zero-padded beyond ne.
+struct Operators {
+    int kernel = 0;
+    double kappa = 0.0;
+    int p = 0, ne = 0, npad = 0, nlev = 0;
+    DBuf<double> surf;            // [ne][3] unit surface points
+    DBuf<float> surf_f;           // [ne][4] float copy (x, y, z, 0)
+    // FP32 copies
+    DBuf<float> uc2ue, dc2de;     // [nlev][npad^2]
+    DBuf<float> m2m, l2l;         // [nlev][8][npad^2]  (child level index)
+    DBuf<float> m2l;              // [nlev][343][npad^2]
+    // FP64 copies (all-FP64 path)
+    DBuf<double> uc2ue_d, dc2de_d, m2m_d, l2l_d, m2l_d;
+    bool have_d = false;
+};
+
+std::shared_ptr<Operators> get_operators(fmm_tree* T, int kernel, double kappa, int p, bool need_fp64);
+
+}  // namespace pbfmm

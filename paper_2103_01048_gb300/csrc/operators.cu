@@ -1,0 +1,235 @@
+// Precomputation of the KIFMM translation operators (the "invariant
+// matrices" the paper pre-computes and caches, Sec. "Fast multipole method"
+// and the assembly-time discussion of the performance study).
+//
+// For each level l (box half-width r_l = R / 2^l), all in FP64 on the GPU:
+//   UC2UE_l = pinv(K(upward check, upward equivalent))      [Eq. multipole_local]
+//   DC2DE_l = pinv(K(downward check, downward equivalent))
+//   M2M_l[c] = UC2UE_{l-1} K(parent upward check, child-c upward equivalent)
+//   L2L_l[c] = K(child-c downward check, parent downward equivalent)
+//   M2L_l[o] = K(downward check of B, upward equivalent of the box at offset o)
+// The paper says only "solve the linear systems"; the regularised solve used
+// here is Tikhonov: pinv(K) = (K^T K + lam I)^{-1} K^T with
+// lam = (1e-7 ||K||_F)^2, by a Cholesky factorisation.
+#include "fmm.cuh"
+#include <cmath>
+
+namespace pbfmm {
+
+constexpr double kInv4Pi = 0.07957747154594767;   // 1/(4 pi)
+
+__global__ void k_kernel_matrix(int ne, int kernel, double kappa, const double* __restrict__ surf,
+                                double tcx, double tcy, double tcz, double ts,
+                                double scx, double scy, double scz, double ss, double* __restrict__ out) {
+    int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= ne * ne) return;
+    int i = idx / ne, j = idx % ne;
+    double dx = (tcx + ts * surf[3 * i]) - (scx + ss * surf[3 * j]);
+    double dy = (tcy + ts * surf[3 * i + 1]) - (scy + ss * surf[3 * j + 1]);
+    double dz = (tcz + ts * surf[3 * i + 2]) - (scz + ss * surf[3 * j + 2]);
+    double r = sqrt(dx * dx + dy * dy + dz * dz);
+    double g = kInv4Pi / r;
+    if (kernel == FMM_YUKAWA) g *= exp(-kappa * r);
+    out[idx] = g;
+}
+
+__global__ void k_sumsq(int n, const double* a, double* out) {
+    __shared__ double red[1024];
+    double s = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) s += a[i] * a[i];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[0] = red[0];
+}
+
+// G = K^T K + lam I,  lam = eps^2 * sumsq(K)
+__global__ void k_gram(int n, const double* __restrict__ K, const double* sumsq, double eps2, double* __restrict__ G) {
+    int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= n * n) return;
+    int i = idx / n, j = idx % n;
+    double s = 0.0;
+    for (int k = 0; k < n; ++k) s += K[k * n + i] * K[k * n + j];
+    if (i == j) s += eps2 * sumsq[0];
+    G[idx] = s;
+}
+
+// In-place lower Cholesky factor of G (one CTA).
+__global__ void k_cholesky(int n, double* G) {
+    __shared__ double piv;
+    for (int k = 0; k < n; ++k) {
+        if (threadIdx.x == 0) {
+            double d = G[k * n + k];
+            piv = sqrt(d > 0.0 ? d : 1e-300);
+            G[k * n + k] = piv;
+        }
+        __syncthreads();
+        for (int i = k + 1 + threadIdx.x; i < n; i += blockDim.x) G[i * n + k] /= piv;
+        __syncthreads();
+        int m = n - k - 1;
+        for (int t = threadIdx.x; t < m * m; t += blockDim.x) {
+            int i = k + 1 + t / m, j = k + 1 + t % m;
+            if (j <= i) G[i * n + j] -= G[i * n + k] * G[j * n + k];
+        }
+        __syncthreads();
+    }
+}
+
+// X = G^{-1} K^T with G = L L^T: column j of X solves G x = (row j of K)^T.
+__global__ void k_chol_solve(int n, const double* __restrict__ L, const double* __restrict__ K, double* __restrict__ X) {
+    int j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    for (int k = 0; k < n; ++k) {                 // L y = b
+        double s = K[j * n + k];
+        for (int m = 0; m < k; ++m) s -= L[k * n + m] * X[m * n + j];
+        X[k * n + j] = s / L[k * n + k];
+    }
+    for (int k = n - 1; k >= 0; --k) {            // L^T x = y
+        double s = X[k * n + j];
+        for (int m = k + 1; m < n; ++m) s -= L[m * n + k] * X[m * n + j];
+        X[k * n + j] = s / L[k * n + k];
+    }
+}
+
+__global__ void k_matmul(int n, const double* __restrict__ A, const double* __restrict__ B, double* __restrict__ C) {
+    int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= n * n) return;
+    int i = idx / n, j = idx % n;
+    double s = 0.0;
+    for (int k = 0; k < n; ++k) s += A[i * n + k] * B[k * n + j];
+    C[idx] = s;
+}
+
+__global__ void k_store_padded(int n, int npad, const double* __restrict__ src, float* __restrict__ dst_f,
+                               double* __restrict__ dst_d) {
+    int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= npad * npad) return;
+    int i = idx / npad, j = idx % npad;
+    double v = (i < n && j < n) ? src[i * n + j] : 0.0;
+    dst_f[idx] = (float)v;
+    if (dst_d) dst_d[idx] = v;
+}
+
+namespace {
+
+struct Builder {
+    cudaStream_t st;
+    int n, kernel;
+    double kappa;
+    const double* surf;
+    DBuf<double> A, B, C, G, ss;
+    Builder(cudaStream_t s, int ne, int k, double kap, const double* su) : st(s), n(ne), kernel(k), kappa(kap), surf(su) {
+        A.alloc((size_t)n * n, st); B.alloc((size_t)n * n, st); C.alloc((size_t)n * n, st);
+        G.alloc((size_t)n * n, st); ss.alloc(1, st);
+    }
+    void kmat(double* out, const double tc[3], double ts, const double sc[3], double sscale) {
+        k_kernel_matrix<<<div_up((long long)n * n, 256), 256, 0, st>>>(n, kernel, kappa, surf, tc[0], tc[1], tc[2], ts,
+                                                                      sc[0], sc[1], sc[2], sscale, out);
+        PB_CHECK_LAUNCH();
+    }
+    // out = pinv(Kin)  (Kin is destroyed)
+    void pinv(const double* Kin, double* out) {
+        k_sumsq<<<1, 1024, 0, st>>>(n * n, Kin, ss.p);
+        k_gram<<<div_up((long long)n * n, 256), 256, 0, st>>>(n, Kin, ss.p, 1e-14, G.p);
+        k_cholesky<<<1, 1024, 0, st>>>(n, G.p);
+        k_chol_solve<<<div_up(n, 64), 64, 0, st>>>(n, G.p, Kin, out);
+        PB_CHECK_LAUNCH();
+    }
+    void store(const double* src, float* f, double* d, int npad) {
+        k_store_padded<<<div_up((long long)npad * npad, 256), 256, 0, st>>>(n, npad, src, f, d);
+        PB_CHECK_LAUNCH();
+    }
+};
+
+}  // namespace
+
+std::shared_ptr<Operators> get_operators(fmm_tree* T, int kernel, double kappa, int p, bool need_fp64) {
+    auto key = std::make_tuple(kernel, kernel == FMM_YUKAWA ? kappa : 0.0, p, T->nlev);
+    auto it = T->ops.find(key);
+    if (it != T->ops.end() && (!need_fp64 || it->second->have_d)) return it->second;
+    cudaStream_t st = T->ctx->stream;
+    auto O = std::make_shared<Operators>();
+    O->kernel = kernel;
+    O->kappa = kappa;
+    O->p = p;
+    O->ne = surface_count(p);
+    O->npad = pad16(O->ne);
+    O->nlev = T->nlev;
+    const int n = O->ne, np = O->npad, L = T->nlev;
+    // unit surface: boundary points of the p x p x p grid on [-1, 1]^3
+    std::vector<double> s;
+    std::vector<float> sf;
+    for (int i = 0; i < p; ++i)
+        for (int j = 0; j < p; ++j)
+            for (int k = 0; k < p; ++k) {
+                if (i == 0 || j == 0 || k == 0 || i == p - 1 || j == p - 1 || k == p - 1) {
+                    double x = -1.0 + 2.0 * i / (p - 1), y = -1.0 + 2.0 * j / (p - 1), z = -1.0 + 2.0 * k / (p - 1);
+                    s.push_back(x); s.push_back(y); s.push_back(z);
+                    sf.push_back((float)x); sf.push_back((float)y); sf.push_back((float)z); sf.push_back(0.f);
+                }
+            }
+    O->surf.alloc(s.size(), st);
+    O->surf_f.alloc(sf.size(), st);
+    PB_CUDA(cudaMemcpyAsync(O->surf.p, s.data(), s.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+    PB_CUDA(cudaMemcpyAsync(O->surf_f.p, sf.data(), sf.size() * sizeof(float), cudaMemcpyHostToDevice, st));
+    const size_t m2 = (size_t)np * np;
+    O->uc2ue.alloc(L * m2, st); O->dc2de.alloc(L * m2, st);
+    O->m2m.alloc(L * 8 * m2, st); O->l2l.alloc(L * 8 * m2, st);
+    O->m2l.alloc(L * (size_t)kNumOffsets * m2, st);
+    O->m2m.zero(st); O->l2l.zero(st); O->m2l.zero(st);
+    if (need_fp64) {
+        O->uc2ue_d.alloc(L * m2, st); O->dc2de_d.alloc(L * m2, st);
+        O->m2m_d.alloc(L * 8 * m2, st); O->l2l_d.alloc(L * 8 * m2, st);
+        O->m2l_d.alloc(L * (size_t)kNumOffsets * m2, st);
+        O->m2m_d.zero(st); O->l2l_d.zero(st); O->m2l_d.zero(st);
+        O->have_d = true;
+    }
+    Builder Bd(st, n, kernel, kappa, O->surf.p);
+    DBuf<double> uc2ue_prev;
+    uc2ue_prev.alloc((size_t)n * n, st);
+    const double zero[3] = {0, 0, 0};
+    for (int l = 0; l < L; ++l) {
+        const double r = std::ldexp(T->R, -l);
+        // UC2UE_l, DC2DE_l
+        Bd.kmat(Bd.A.p, zero, kAlphaOuter * r, zero, kAlphaInner * r);
+        Bd.pinv(Bd.A.p, Bd.B.p);
+        Bd.store(Bd.B.p, O->uc2ue.p + l * m2, need_fp64 ? O->uc2ue_d.p + l * m2 : nullptr, np);
+        if (l > 0) {
+            // M2M_l[c] = UC2UE_{l-1} K(parent uc, child ue); parent half-width 2r
+            for (int c = 0; c < 8; ++c) {
+                const double cc[3] = {((c >> 2) & 1) ? r : -r, ((c >> 1) & 1) ? r : -r, (c & 1) ? r : -r};
+                Bd.kmat(Bd.C.p, zero, kAlphaOuter * 2 * r, cc, kAlphaInner * r);
+                k_matmul<<<div_up((long long)n * n, 256), 256, 0, st>>>(n, uc2ue_prev.p, Bd.C.p, Bd.A.p);
+                Bd.store(Bd.A.p, O->m2m.p + ((size_t)l * 8 + c) * m2,
+                         need_fp64 ? O->m2m_d.p + ((size_t)l * 8 + c) * m2 : nullptr, np);
+                // L2L_l[c] = K(child dc, parent de)
+                Bd.kmat(Bd.C.p, cc, kAlphaInner * r, zero, kAlphaOuter * 2 * r);
+                Bd.store(Bd.C.p, O->l2l.p + ((size_t)l * 8 + c) * m2,
+                         need_fp64 ? O->l2l_d.p + ((size_t)l * 8 + c) * m2 : nullptr, np);
+            }
+        }
+        PB_CUDA(cudaMemcpyAsync(uc2ue_prev.p, Bd.B.p, (size_t)n * n * sizeof(double), cudaMemcpyDeviceToDevice, st));
+        Bd.kmat(Bd.A.p, zero, kAlphaInner * r, zero, kAlphaOuter * r);
+        Bd.pinv(Bd.A.p, Bd.B.p);
+        Bd.store(Bd.B.p, O->dc2de.p + l * m2, need_fp64 ? O->dc2de_d.p + l * m2 : nullptr, np);
+        // M2L_l[o]
+        if (l >= 2) {
+            for (int o = 0; o < kNumOffsets; ++o) {
+                int ox = o / 49 - 3, oy = (o / 7) % 7 - 3, oz = o % 7 - 3;
+                if (std::abs(ox) <= 1 && std::abs(oy) <= 1 && std::abs(oz) <= 1) continue;
+                const double sc[3] = {2 * r * ox, 2 * r * oy, 2 * r * oz};
+                Bd.kmat(Bd.C.p, zero, kAlphaInner * r, sc, kAlphaInner * r);
+                Bd.store(Bd.C.p, O->m2l.p + ((size_t)l * kNumOffsets + o) * m2,
+                         need_fp64 ? O->m2l_d.p + ((size_t)l * kNumOffsets + o) * m2 : nullptr, np);
+            }
+        }
+    }
+    PB_CUDA(cudaStreamSynchronize(st));
+    T->ops[key] = O;
+    return O;
+}
+
+}  // namespace pbfmm

@@ -1,0 +1,67 @@
+// Device octree of the KIFMM (Sec. "Fast multipole method").
+#pragma once
+#include "common.cuh"
+#include <map>
+#include <memory>
+#include <tuple>
+
+namespace pbfmm {
+
+struct Operators;   // fmm.cu: precomputed translation operators per level
+
+// Per-tile M2L schedule for the target-stationary M2L: each tile is up to
+// kM2LTile boxes of one level; for every relative offset used by any box of
+// the tile, one entry lists the source box of each tile column (-1 = none).
+constexpr int kM2LTile = 32;
+
+struct M2LSchedule {
+    int ntile = 0;
+    std::vector<int> tile_level_h;     // level of each tile
+    DBuf<int> tile_box;                // [ntile][kM2LTile] target box ids (-1 pad)
+    DBuf<int> tile_level;              // [ntile]
+    DBuf<int> entry_off;               // [ntile + 1] CSR over entries
+    DBuf<int> entry_offset_idx;        // [nentry] offset index 0..342
+    DBuf<int> entry_src;               // [nentry][kM2LTile] source box ids (-1 = none)
+    long long nentry = 0;
+    long long npairs = 0;              // total V-list pairs (algorithmic work)
+};
+
+}  // namespace pbfmm
+
+struct fmm_tree {
+    pb_ctx* ctx = nullptr;
+    int64_t ns = 0, nt = 0;
+    bool same = true;
+    int ncrit = 0;
+    double c[3] = {0, 0, 0}, R = 1.0;
+
+    pbfmm::DBuf<uint64_t> keys_s, keys_t;
+    pbfmm::DBuf<int> perm_s, perm_t;
+    pbfmm::DBuf<float4> pos_s, pos_t;        // Morton-sorted (x, y, z, 0)
+
+    int nbox = 0, nlev = 0, nleaf = 0;
+    std::vector<int> lvl_off;                // boxes of level l: [lvl_off[l], lvl_off[l+1])
+    pbfmm::DBuf<int> level, parent, first_child, nchild, sb, se, tb, te;
+    pbfmm::DBuf<int4> anchor;                // (ax, ay, az, level)
+    pbfmm::DBuf<double4> center;             // (cx, cy, cz, half-width)
+
+    pbfmm::DBuf<int> coll, coll_n, cn, cn_n, V, V_n, X, X_n;
+    pbfmm::DBuf<int> U_off, U_ids, W_off, W_ids;
+    long long n_u = 0, n_v = 0, n_w = 0, n_x = 0;
+    // algorithmic work counters of one apply (see fmm_tree_info_t)
+    long long work[6] = {0, 0, 0, 0, 0, 0};
+    pbfmm::DBuf<int> leaf_ids;               // leaves with at least one target
+    int n_tleaf = 0;
+    std::vector<int> leaf_level_h;           // per level: leaves with sources (host lists built on demand)
+
+    // leaves with sources, grouped by level (for P2M + UC2UE)
+    pbfmm::DBuf<int> sleaf_ids;              // sorted by level
+    std::vector<int> sleaf_lvl_off;          // [nlev + 1]
+    // boxes with a non-empty X list
+    pbfmm::DBuf<int> xbox_ids;
+    int n_xbox = 0;
+    // non-leaf boxes per level (M2M parents) and all boxes per level for L2L
+    pbfmm::M2LSchedule m2l;
+
+    std::map<std::tuple<int, double, int, int>, std::shared_ptr<pbfmm::Operators>> ops;
+};

@@ -1,0 +1,201 @@
+"""GPU parity of the octree and the FMM apply against the oracle.
+
+Tree, keys, boxes and all four interaction lists are compared bit for bit
+with oracle/tree.py; fmm_apply is compared with the FP64 direct sum
+(oracle/kernels.py) in relative L2 over all targets (small sizes) or over a
+seeded target sample (the 4M-point workload).  Tolerance: 1e-5 relative L2,
+the bound the FMM apply must meet at an expansion order chosen for it.
+"""
+import numpy as np
+import pytest
+
+import synthetic
+from oracle import tree as ot
+from oracle.kernels import LAPLACE, YUKAWA, direct_sum, rel_l2
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-5
+
+
+@pytest.fixture(scope="module")
+def pb():
+    import paper_2103_01048_gb300 as pb
+    return pb
+
+
+@pytest.fixture(scope="module")
+def ctx(pb):
+    assert torch.cuda.is_available()
+    c = pb.pb_create(0, None)
+    yield c
+    pb.pb_destroy(c)
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def tree_cases():
+    rng = np.random.default_rng(11)
+    x, _ = synthetic.bumpy_sphere_points(20000, seed=3)
+    yield "sphere20k", x, None, 64
+    cl = np.concatenate([rng.normal(0, 0.01, (3000, 3)), rng.uniform(-1, 1, (7000, 3))]).astype(np.float32)
+    yield "clustered", cl, None, 25
+    s = rng.uniform(-1, 1, (6000, 3)).astype(np.float32)
+    t = rng.normal(0.3, 0.2, (5000, 3)).astype(np.float32)
+    yield "separate", s, t, 30
+    dup = np.repeat(rng.uniform(0, 1, (5, 3)).astype(np.float32), 20, axis=0)
+    yield "duplicates", dup, None, 8
+    yield "single", np.array([[0.5, -1.0, 2.0]], np.float32), None, 1
+    yield "tiny_ncrit_big", x[:500], None, 1000
+
+
+@pytest.mark.parametrize("name,src,tgt,ncrit", list(tree_cases()))
+def test_tree_bit_exact(pb, ctx, name, src, tgt, ncrit):
+    ref = ot.build_tree(src, ncrit, tgt)
+    T = ref["tree"]
+    L = ot.build_lists(T)
+    h = pb.fmm_tree_build(ctx, dev(src), ncrit, None if tgt is None else dev(tgt))
+    try:
+        g = pb.fmm_tree_export(ctx, h)
+    finally:
+        pb.fmm_tree_destroy(h)
+    info = g["info"]
+    assert np.allclose(info.center, ref["c"], rtol=0, atol=0)
+    assert info.half_width == ref["R"]
+    assert np.array_equal(g["keys_src"], ref["keys_src"])
+    assert np.array_equal(g["perm_src"], ref["perm_src"])
+    if tgt is not None:
+        assert np.array_equal(g["keys_tgt"], ref["keys_tgt"])
+        assert np.array_equal(g["perm_tgt"], ref["perm_tgt"])
+    assert info.n_box == T.nbox
+    for k, r in [("level", T.level), ("parent", T.parent), ("nchild", T.nchild), ("src_begin", T.sb),
+                 ("src_end", T.se)]:
+        assert np.array_equal(g[k], r), k
+    assert np.array_equal(g["anchor"], T.anchor)
+    fc = np.where(T.nchild > 0, T.first_child, -1)
+    assert np.array_equal(g["first_child"], fc)
+    if tgt is not None:
+        assert np.array_equal(g["tgt_begin"], T.tb) and np.array_equal(g["tgt_end"], T.te)
+    for name_l in "UVWX":
+        off, ids = g[name_l]
+        roff, rids = ot.to_csr(L[name_l])
+        assert np.array_equal(off, roff), name_l
+        assert np.array_equal(ids, rids), name_l
+
+
+def fmm_case(n, seed=0):
+    x, nrm = synthetic.bumpy_sphere_points(n, seed=seed)
+    q = synthetic.uniform_densities(n, seed=seed + 1)
+    d = synthetic.uniform_densities(n, seed=seed + 2)
+    return x, nrm, q, d
+
+
+def run_apply(pb, ctx, tree, kernel, kappa, p, q=None, d=None, sn=None, tn=None, nt=None, fp64=False, dn=False):
+    dt = torch.float64 if fp64 else torch.float32
+    cv = (lambda a: None if a is None else dev(np.asarray(a, np.float64 if fp64 else np.float32)))
+    out = torch.zeros(nt, dtype=dt, device="cuda")
+    odn = torch.zeros(nt, dtype=dt, device="cuda") if dn else None
+    pb.fmm_apply(ctx, tree, kernel, kappa, p, out, q=cv(q), dip=cv(d), src_n=cv(sn), tgt_n=cv(tn), out_dn=odn,
+                 precision=pb.PB_FP64 if fp64 else pb.PB_MIXED)
+    torch.cuda.synchronize()
+    return out.cpu().numpy(), (odn.cpu().numpy() if dn else None)
+
+
+@pytest.fixture(scope="module")
+def case20k(pb, ctx):
+    x, nrm, q, d = fmm_case(20000)
+    h = pb.fmm_tree_build(ctx, dev(x), 64)
+    yield x, nrm, q, d, h
+    pb.fmm_tree_destroy(h)
+
+
+@pytest.mark.parametrize("kernel,kappa", [(LAPLACE, 0.0), (YUKAWA, 0.125), (YUKAWA, 4.0)])
+@pytest.mark.parametrize("layer", ["SL", "DL", "SL+DL", "DN"])
+def test_fmm_vs_direct(pb, ctx, case20k, kernel, kappa, layer):
+    x, nrm, q, d, h = case20k
+    qq = q if layer in ("SL", "SL+DL", "DN") else None
+    dd = d if layer in ("DL", "SL+DL") else None
+    out, dn = run_apply(pb, ctx, h, kernel, kappa, 6, q=qq, d=dd, sn=nrm, tn=nrm if layer == "DN" else None,
+                        nt=len(x), dn=layer == "DN")
+    ref = direct_sum(kernel, kappa, x, q=qq, dip=dd, src_n=nrm, tgt_n=nrm if layer == "DN" else None,
+                     want_dn=layer == "DN")
+    if layer == "DN":
+        ref, rdn = ref
+        assert rel_l2(dn, rdn) < TOL
+    assert rel_l2(out, ref) < TOL
+
+
+def test_fmm_error_decreases_with_p(pb, ctx, case20k):
+    x, nrm, q, d, h = case20k
+    ref = direct_sum(YUKAWA, 0.125, x, q=q, dip=d, src_n=nrm)
+    errs = []
+    for p in (3, 4, 6):
+        out, _ = run_apply(pb, ctx, h, YUKAWA, 0.125, p, q=q, d=d, sn=nrm, nt=len(x))
+        errs.append(rel_l2(out, ref))
+    assert errs[0] > errs[1] > errs[2]
+
+
+def test_fp64_path(pb, ctx, case20k):
+    x, nrm, q, d, h = case20k
+    ref = direct_sum(LAPLACE, 0.0, x, q=q, dip=d, src_n=nrm)
+    out, _ = run_apply(pb, ctx, h, LAPLACE, 0.0, 8, q=q, d=d, sn=nrm, nt=len(x), fp64=True)
+    assert rel_l2(out, ref) < 1e-6
+
+
+def test_single_leaf_is_direct_sum(pb, ctx):
+    x, nrm, q, d = fmm_case(3000, seed=7)
+    h = pb.fmm_tree_build(ctx, dev(x), 100000)
+    try:
+        out, _ = run_apply(pb, ctx, h, YUKAWA, 0.3, 4, q=q, d=d, sn=nrm, nt=len(x))
+    finally:
+        pb.fmm_tree_destroy(h)
+    ref = direct_sum(YUKAWA, 0.3, x, q=q, dip=d, src_n=nrm)
+    assert rel_l2(out, ref) < 2e-6
+
+
+def test_separate_targets_and_host_buffers(pb, ctx):
+    rng = np.random.default_rng(4)
+    x, nrm, q, d = fmm_case(12000, seed=9)
+    tgt = (rng.standard_normal((5000, 3)) * 0.4).astype(np.float32)
+    h = pb.fmm_tree_build(ctx, dev(x), 48, dev(tgt))
+    try:
+        out, _ = run_apply(pb, ctx, h, LAPLACE, 0.0, 6, q=q, d=d, sn=nrm, nt=len(tgt))
+        host_out = np.zeros(len(tgt), np.float32)
+        pb.fmm_apply(ctx, h, LAPLACE, 0.0, 6, host_out, q=q, dip=d, src_n=nrm)
+    finally:
+        pb.fmm_tree_destroy(h)
+    ref = direct_sum(LAPLACE, 0.0, x, q=q, dip=d, src_n=nrm, tgt=tgt)
+    assert rel_l2(out, ref) < TOL
+    assert np.array_equal(out, host_out)
+
+
+def test_invalid_arguments(pb, ctx, case20k):
+    x, nrm, q, d, h = case20k
+    out = torch.zeros(len(x), device="cuda")
+    with pytest.raises(pb.PBError) as e:
+        pb.fmm_apply(ctx, h, YUKAWA, 0.0, 6, out, q=dev(q))
+    assert e.value.code == pb.PB_EINVAL
+    with pytest.raises(pb.PBError):
+        pb.fmm_apply(ctx, h, LAPLACE, 0.0, 6, out, dip=dev(d))          # no normals
+    with pytest.raises(pb.PBError):
+        pb.fmm_apply(ctx, h, LAPLACE, 0.0, 1, out, q=dev(q))            # p < 2
+
+
+def test_full_size_sampled(pb, ctx):
+    """The 4M-point workload at the bench's launch configuration, checked on
+    a seeded sample of targets against the FP64 direct sum over all sources."""
+    n = 4_000_000
+    x, nrm, q, d = fmm_case(n)
+    h = pb.fmm_tree_build(ctx, dev(x), 128)
+    try:
+        for kernel, kappa in [(LAPLACE, 0.0), (YUKAWA, 0.125)]:
+            out, _ = run_apply(pb, ctx, h, kernel, kappa, 6, q=q, d=d, sn=nrm, nt=n)
+            idx = synthetic.random_subsample(n, 300, seed=5)
+            ref = direct_sum(kernel, kappa, x, q=q, dip=d, src_n=nrm, tgt=x[idx])
+            # the direct sum at a target excludes only r = 0; same in both
+            assert rel_l2(out[idx], ref) < TOL
+    finally:
+        pb.fmm_tree_destroy(h)
