@@ -16,7 +16,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _LIBPATH = os.path.join(_HERE, "libpbfmm.so")
 
 if not os.path.exists(_LIBPATH):
-    raise ImportError(f"libpbfmm.so not built ({_LIBPATH}); run paper_2103_01048_gb300.build.build()")
+    raise ImportError(f"libpbfmm.so not built ({_LIBPATH}); run __graft_entry__.build()")
 
 _lib = ctypes.CDLL(_LIBPATH)
 

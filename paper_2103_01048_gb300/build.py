@@ -26,7 +26,14 @@ def _stale(obj, deps):
 
 
 def build(verbose=False, force=False):
+    import platform
     os.makedirs(BUILD, exist_ok=True)
+    stamp = os.path.join(BUILD, "arch.txt")
+    arch = platform.machine()
+    if not os.path.exists(LIB) or not os.path.exists(stamp) or open(stamp).read() != arch:
+        force = True          # objects from another host architecture or a partial build
+    with open(stamp, "w") as f:
+        f.write(arch)
     nvcc = os.environ.get("NVCC", "nvcc")
     headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))]
     headers.append(os.path.join(ROOT, "include", "pbfmm.h"))
