@@ -177,13 +177,15 @@ struct GemmArgs {
     int accumulate;            // mode 0: Y += (else Y =)
 };
 
-template <typename T, int NPAD>
-__global__ void __launch_bounds__(256) k_box_gemm(GemmArgs a, const T* __restrict__ ops, const T* __restrict__ Xv,
+// T: type of the box vectors; TO: type of the operator and the accumulation
+// (double for the ill-conditioned check-to-equivalent solves).
+template <typename T, typename TO, int NPAD>
+__global__ void __launch_bounds__(256) k_box_gemm(GemmArgs a, const TO* __restrict__ ops, const T* __restrict__ Xv,
                                                   T* __restrict__ Yv) {
-    constexpr int KC = (sizeof(T) * NPAD * 16 > 40000) ? 8 : 16;
+    constexpr int KC = (sizeof(TO) * NPAD * 16 > 40000) ? 8 : 16;
     constexpr int RPT = NPAD / 16;
-    __shared__ T s_op[KC][NPAD + 1];
-    __shared__ T s_x[KC][kTC + 1];
+    __shared__ TO s_op[KC][NPAD + 1];
+    __shared__ TO s_x[KC][kTC + 1];
     __shared__ int s_src[kTC];
     __shared__ int s_dst[kTC];
     const int tid = threadIdx.x;
@@ -198,9 +200,9 @@ __global__ void __launch_bounds__(256) k_box_gemm(GemmArgs a, const T* __restric
         nterm = (a.mode == G_DENSE) ? 1 : 8;
         level = a.level;
     }
-    T acc[RPT][2];
+    TO acc[RPT][2];
 #pragma unroll
-    for (int r = 0; r < RPT; ++r) acc[r][0] = acc[r][1] = T(0);
+    for (int r = 0; r < RPT; ++r) acc[r][0] = acc[r][1] = TO(0);
     for (int term = 0; term < nterm; ++term) {
         // columns: source box for this term, destination box
         __syncthreads();
@@ -236,7 +238,7 @@ __global__ void __launch_bounds__(256) k_box_gemm(GemmArgs a, const T* __restric
         bool any = false;
         for (int c = 0; c < kTC; ++c) any |= (s_src[c] >= 0);
         if (!any) continue;
-        const T* op;
+        const TO* op;
         if (a.mode == G_M2L) op = ops + ((size_t)level * kNumOffsets + a.entry_oidx[a.entry_off[tile] + term]) * m2;
         else if (a.mode == G_DENSE) op = ops + (size_t)level * m2;
         else op = ops + ((size_t)level * 8 + term) * m2;
@@ -249,15 +251,15 @@ __global__ void __launch_bounds__(256) k_box_gemm(GemmArgs a, const T* __restric
             for (int i = tid; i < kTC * KC; i += 256) {
                 int c = i / KC, kk = i % KC;
                 int s = s_src[c];
-                s_x[kk][c] = (s >= 0) ? Xv[(size_t)s * NPAD + k0 + kk] : T(0);
+                s_x[kk][c] = (s >= 0) ? (TO)Xv[(size_t)s * NPAD + k0 + kk] : TO(0);
             }
             __syncthreads();
 #pragma unroll
             for (int kk = 0; kk < KC; ++kk) {
-                T x0 = s_x[kk][2 * tx], x1 = s_x[kk][2 * tx + 1];
+                TO x0 = s_x[kk][2 * tx], x1 = s_x[kk][2 * tx + 1];
 #pragma unroll
                 for (int r = 0; r < RPT; ++r) {
-                    T o = s_op[kk][ty + 16 * r];
+                    TO o = s_op[kk][ty + 16 * r];
                     acc[r][0] += o * x0;
                     acc[r][1] += o * x1;
                 }
@@ -269,11 +271,11 @@ __global__ void __launch_bounds__(256) k_box_gemm(GemmArgs a, const T* __restric
                 int d = s_dst[2 * tx + cc];
                 if (d >= 0) {
 #pragma unroll
-                    for (int r = 0; r < RPT; ++r) Yv[(size_t)d * NPAD + ty + 16 * r] += acc[r][cc];
+                    for (int r = 0; r < RPT; ++r) Yv[(size_t)d * NPAD + ty + 16 * r] += (T)acc[r][cc];
                 }
             }
 #pragma unroll
-            for (int r = 0; r < RPT; ++r) acc[r][0] = acc[r][1] = T(0);
+            for (int r = 0; r < RPT; ++r) acc[r][0] = acc[r][1] = TO(0);
         }
     }
     if (a.mode == G_L2L) return;
@@ -285,7 +287,7 @@ __global__ void __launch_bounds__(256) k_box_gemm(GemmArgs a, const T* __restric
 #pragma unroll
         for (int r = 0; r < RPT; ++r) {
             size_t o = (size_t)d * NPAD + ty + 16 * r;
-            Yv[o] = add ? Yv[o] + acc[r][cc] : acc[r][cc];
+            Yv[o] = add ? Yv[o] + (T)acc[r][cc] : (T)acc[r][cc];
         }
     }
 }
@@ -385,25 +387,25 @@ struct Work {
     DBuf<T> Qu, Qd, chk, pot, dn;
 };
 
-template <typename T, int NPAD>
-static void gemm_launch(cudaStream_t st, int nblocks, const GemmArgs& a, const T* ops, const T* X, T* Y) {
+template <typename T, typename TO, int NPAD>
+static void gemm_launch(cudaStream_t st, int nblocks, const GemmArgs& a, const TO* ops, const T* X, T* Y) {
     if (nblocks <= 0) return;
-    k_box_gemm<T, NPAD><<<nblocks, 256, 0, st>>>(a, ops, X, Y);
+    k_box_gemm<T, TO, NPAD><<<nblocks, 256, 0, st>>>(a, ops, X, Y);
     PB_CHECK_LAUNCH();
 }
 
-template <typename T>
-static void gemm_dispatch(int npad, cudaStream_t st, int nblocks, const GemmArgs& a, const T* ops, const T* X, T* Y) {
+template <typename T, typename TO>
+static void gemm_dispatch(int npad, cudaStream_t st, int nblocks, const GemmArgs& a, const TO* ops, const T* X, T* Y) {
     switch (npad) {
-        case 16: gemm_launch<T, 16>(st, nblocks, a, ops, X, Y); break;
-        case 32: gemm_launch<T, 32>(st, nblocks, a, ops, X, Y); break;
-        case 64: gemm_launch<T, 64>(st, nblocks, a, ops, X, Y); break;
-        case 112: gemm_launch<T, 112>(st, nblocks, a, ops, X, Y); break;
-        case 160: gemm_launch<T, 160>(st, nblocks, a, ops, X, Y); break;
-        case 208: gemm_launch<T, 208>(st, nblocks, a, ops, X, Y); break;
-        case 304: gemm_launch<T, 304>(st, nblocks, a, ops, X, Y); break;
-        case 400: gemm_launch<T, 400>(st, nblocks, a, ops, X, Y); break;
-        case 496: gemm_launch<T, 496>(st, nblocks, a, ops, X, Y); break;
+        case 16: gemm_launch<T, TO, 16>(st, nblocks, a, ops, X, Y); break;
+        case 32: gemm_launch<T, TO, 32>(st, nblocks, a, ops, X, Y); break;
+        case 64: gemm_launch<T, TO, 64>(st, nblocks, a, ops, X, Y); break;
+        case 112: gemm_launch<T, TO, 112>(st, nblocks, a, ops, X, Y); break;
+        case 160: gemm_launch<T, TO, 160>(st, nblocks, a, ops, X, Y); break;
+        case 208: gemm_launch<T, TO, 208>(st, nblocks, a, ops, X, Y); break;
+        case 304: gemm_launch<T, TO, 304>(st, nblocks, a, ops, X, Y); break;
+        case 400: gemm_launch<T, TO, 400>(st, nblocks, a, ops, X, Y); break;
+        case 496: gemm_launch<T, TO, 496>(st, nblocks, a, ops, X, Y); break;
         default: throw Error(PB_EINVAL, "unsupported expansion order");
     }
 }
@@ -466,8 +468,8 @@ static void apply_t(fmm_tree* Tr, const Operators& O, double kappa_d, const In* 
         k_gather_tn<T, In><<<div_up(nt, 256), 256, 0, st>>>(nt, pt, tgt_n, W.tn.p);
         PB_CHECK_LAUNCH();
     }
-    const T* uc2ue = opsel<T>(O, O.uc2ue, O.uc2ue_d);
-    const T* dc2de = opsel<T>(O, O.dc2de, O.dc2de_d);
+    const double* uc2ue = O.uc2ue_d.p;      // FP64 always (ill-conditioned solves)
+    const double* dc2de = O.dc2de_d.p;
     const T* m2m = opsel<T>(O, O.m2m, O.m2m_d);
     const T* l2l = opsel<T>(O, O.l2l, O.l2l_d);
     const T* m2l = opsel<T>(O, O.m2l, O.m2l_d);
@@ -486,7 +488,7 @@ static void apply_t(fmm_tree* Tr, const Operators& O, double kappa_d, const In* 
         if (a1 <= a0) continue;
         ga.mode = G_DENSE; ga.ncols = a1 - a0; ga.cols = Tr->sleaf_ids.p + a0; ga.col_base = 0;
         ga.level = l; ga.accumulate = 0;
-        gemm_dispatch<T>(npad, st, div_up(a1 - a0, kTC), ga, uc2ue, W.chk.p, W.Qu.p);
+        gemm_dispatch<T, double>(npad, st, div_up(a1 - a0, kTC), ga, uc2ue, W.chk.p, W.Qu.p);
     }
     ph.reset(); ph = std::make_unique<PhaseTimer>(ctx, PB_PH_M2M);
     // M2M, post-order: parents at level l from children at level l + 1
@@ -494,15 +496,23 @@ static void apply_t(fmm_tree* Tr, const Operators& O, double kappa_d, const In* 
     for (int l = Tr->nlev - 2; l >= 2; --l) {
         int a0 = Tr->lvl_off[l], a1 = Tr->lvl_off[l + 1];
         ga.mode = G_M2M; ga.ncols = a1 - a0; ga.cols = nullptr; ga.col_base = a0; ga.level = l + 1;
-        gemm_dispatch<T>(npad, st, div_up(a1 - a0, kTC), ga, m2m, W.Qu.p, W.Qu.p);
+        gemm_dispatch<T, T>(npad, st, div_up(a1 - a0, kTC), ga, m2m, W.Qu.p, W.Qu.p);
     }
     ph.reset(); ph = std::make_unique<PhaseTimer>(ctx, PB_PH_P2L);
-    // ---- far field into downward check potentials: P2L (X list), M2L (V list)
-    W.chk.zero(st);
+    // ---- far field into downward equivalent densities.
+    // P2L: X-list sources -> downward check -> DC2DE (FP64), per level
     if (Tr->n_xbox > 0) {
         if (DL) launch_p2check<T, YUK, true>(st, Tr->n_xbox, Tr->xbox_ids.p, 1, Tr, W, O, kappa);
         else launch_p2check<T, YUK, false>(st, Tr->n_xbox, Tr->xbox_ids.p, 1, Tr, W, O, kappa);
+        for (int l = 0; l < Tr->nlev; ++l) {
+            int a0 = Tr->xbox_lvl_off[l], a1 = Tr->xbox_lvl_off[l + 1];
+            if (a1 <= a0) continue;
+            ga.mode = G_DENSE; ga.ncols = a1 - a0; ga.cols = Tr->xbox_ids.p + a0; ga.col_base = 0;
+            ga.level = l; ga.accumulate = 0;
+            gemm_dispatch<T, double>(npad, st, div_up(a1 - a0, kTC), ga, dc2de, W.chk.p, W.Qd.p);
+        }
     }
+    // M2L (V list) with DC2DE folded into the operators: accumulate into Qd
     ph.reset(); ph = std::make_unique<PhaseTimer>(ctx, PB_PH_M2L);
     if (Tr->m2l.ntile > 0) {
         ga.mode = G_M2L;
@@ -511,19 +521,14 @@ static void apply_t(fmm_tree* Tr, const Operators& O, double kappa_d, const In* 
         ga.entry_off = Tr->m2l.entry_off.p;
         ga.entry_oidx = Tr->m2l.entry_offset_idx.p;
         ga.entry_src = Tr->m2l.entry_src.p;
-        gemm_dispatch<T>(npad, st, Tr->m2l.ntile, ga, m2l, W.Qu.p, W.chk.p);
+        gemm_dispatch<T, T>(npad, st, Tr->m2l.ntile, ga, m2l, W.Qu.p, W.Qd.p);
     }
+    // ---- downward pass, pre-order: L2L (DC2DE folded) from parents at level l - 1
     ph.reset(); ph = std::make_unique<PhaseTimer>(ctx, PB_PH_DOWN);
-    // ---- downward pass, pre-order: L2L from the parent (levels >= 3), then DC2DE
-    for (int l = 2; l < Tr->nlev; ++l) {
-        int a0 = Tr->lvl_off[l], a1 = Tr->lvl_off[l + 1];
-        if (l >= 3) {
-            int p0 = Tr->lvl_off[l - 1], p1 = Tr->lvl_off[l];
-            ga.mode = G_L2L; ga.ncols = p1 - p0; ga.cols = nullptr; ga.col_base = p0; ga.level = l;
-            gemm_dispatch<T>(npad, st, div_up(p1 - p0, kTC), ga, l2l, W.Qd.p, W.chk.p);
-        }
-        ga.mode = G_DENSE; ga.ncols = a1 - a0; ga.cols = nullptr; ga.col_base = a0; ga.level = l; ga.accumulate = 0;
-        gemm_dispatch<T>(npad, st, div_up(a1 - a0, kTC), ga, dc2de, W.chk.p, W.Qd.p);
+    for (int l = 3; l < Tr->nlev; ++l) {
+        int p0 = Tr->lvl_off[l - 1], p1 = Tr->lvl_off[l];
+        ga.mode = G_L2L; ga.ncols = p1 - p0; ga.cols = nullptr; ga.col_base = p0; ga.level = l;
+        gemm_dispatch<T, T>(npad, st, div_up(p1 - p0, kTC), ga, l2l, W.Qd.p, W.Qd.p);
     }
     ph.reset(); ph = std::make_unique<PhaseTimer>(ctx, PB_PH_LEAF);
     // ---- leaves: P2P + M2P + L2P

@@ -6,8 +6,13 @@
 //   UC2UE_l = pinv(K(upward check, upward equivalent))      [Eq. multipole_local]
 //   DC2DE_l = pinv(K(downward check, downward equivalent))
 //   M2M_l[c] = UC2UE_{l-1} K(parent upward check, child-c upward equivalent)
-//   L2L_l[c] = K(child-c downward check, parent downward equivalent)
-//   M2L_l[o] = K(downward check of B, upward equivalent of the box at offset o)
+//   L2L_l[c] = DC2DE_l K(child-c downward check, parent downward equivalent)
+//   M2L_l[o] = DC2DE_l K(downward check of B, upward equivalent of the box at offset o)
+// The pseudo-inverses have norms ~1e6-1e7, so a product with one of them
+// computed in FP32 loses every digit; folded into the translations above
+// (in FP64) the operators have norms of order 1-100 and are stored in FP32.
+// UC2UE / DC2DE themselves are kept in FP64 for the two places where raw
+// check potentials are converted (P2M at leaves, P2L of X lists).
 // The paper says only "solve the linear systems"; the regularised solve used
 // here is Tikhonov: pinv(K) = (K^T K + lam I)^{-1} K^T with
 // lam = (1e-7 ||K||_F)^2, by a Cholesky factorisation.
@@ -177,55 +182,60 @@ std::shared_ptr<Operators> get_operators(fmm_tree* T, int kernel, double kappa, 
     PB_CUDA(cudaMemcpyAsync(O->surf_f.p, sf.data(), sf.size() * sizeof(float), cudaMemcpyHostToDevice, st));
     const size_t m2 = (size_t)np * np;
     O->uc2ue.alloc(L * m2, st); O->dc2de.alloc(L * m2, st);
+    O->uc2ue_d.alloc(L * m2, st); O->dc2de_d.alloc(L * m2, st);
     O->m2m.alloc(L * 8 * m2, st); O->l2l.alloc(L * 8 * m2, st);
     O->m2l.alloc(L * (size_t)kNumOffsets * m2, st);
     O->m2m.zero(st); O->l2l.zero(st); O->m2l.zero(st);
     if (need_fp64) {
-        O->uc2ue_d.alloc(L * m2, st); O->dc2de_d.alloc(L * m2, st);
         O->m2m_d.alloc(L * 8 * m2, st); O->l2l_d.alloc(L * 8 * m2, st);
         O->m2l_d.alloc(L * (size_t)kNumOffsets * m2, st);
         O->m2m_d.zero(st); O->l2l_d.zero(st); O->m2l_d.zero(st);
         O->have_d = true;
     }
     Builder Bd(st, n, kernel, kappa, O->surf.p);
-    DBuf<double> uc2ue_prev;
+    DBuf<double> uc2ue_prev, dc;
     uc2ue_prev.alloc((size_t)n * n, st);
+    dc.alloc((size_t)n * n, st);
     const double zero[3] = {0, 0, 0};
     for (int l = 0; l < L; ++l) {
         const double r = std::ldexp(T->R, -l);
         // UC2UE_l, DC2DE_l
         Bd.kmat(Bd.A.p, zero, kAlphaOuter * r, zero, kAlphaInner * r);
         Bd.pinv(Bd.A.p, Bd.B.p);
-        Bd.store(Bd.B.p, O->uc2ue.p + l * m2, need_fp64 ? O->uc2ue_d.p + l * m2 : nullptr, np);
+        Bd.store(Bd.B.p, O->uc2ue.p + l * m2, O->uc2ue_d.p + l * m2, np);
+        // DC2DE_l (kept in Bd.G's sibling buffer `dc`)
+        Bd.kmat(Bd.A.p, zero, kAlphaInner * r, zero, kAlphaOuter * r);
+        Bd.pinv(Bd.A.p, dc.p);
+        Bd.store(dc.p, O->dc2de.p + l * m2, O->dc2de_d.p + l * m2, np);
         if (l > 0) {
-            // M2M_l[c] = UC2UE_{l-1} K(parent uc, child ue); parent half-width 2r
             for (int c = 0; c < 8; ++c) {
                 const double cc[3] = {((c >> 2) & 1) ? r : -r, ((c >> 1) & 1) ? r : -r, (c & 1) ? r : -r};
+                // M2M_l[c] = UC2UE_{l-1} K(parent uc, child ue); parent half-width 2r
                 Bd.kmat(Bd.C.p, zero, kAlphaOuter * 2 * r, cc, kAlphaInner * r);
                 k_matmul<<<div_up((long long)n * n, 256), 256, 0, st>>>(n, uc2ue_prev.p, Bd.C.p, Bd.A.p);
                 Bd.store(Bd.A.p, O->m2m.p + ((size_t)l * 8 + c) * m2,
                          need_fp64 ? O->m2m_d.p + ((size_t)l * 8 + c) * m2 : nullptr, np);
-                // L2L_l[c] = K(child dc, parent de)
+                // L2L_l[c] = DC2DE_l K(child dc, parent de)
                 Bd.kmat(Bd.C.p, cc, kAlphaInner * r, zero, kAlphaOuter * 2 * r);
-                Bd.store(Bd.C.p, O->l2l.p + ((size_t)l * 8 + c) * m2,
+                k_matmul<<<div_up((long long)n * n, 256), 256, 0, st>>>(n, dc.p, Bd.C.p, Bd.A.p);
+                Bd.store(Bd.A.p, O->l2l.p + ((size_t)l * 8 + c) * m2,
                          need_fp64 ? O->l2l_d.p + ((size_t)l * 8 + c) * m2 : nullptr, np);
             }
         }
         PB_CUDA(cudaMemcpyAsync(uc2ue_prev.p, Bd.B.p, (size_t)n * n * sizeof(double), cudaMemcpyDeviceToDevice, st));
-        Bd.kmat(Bd.A.p, zero, kAlphaInner * r, zero, kAlphaOuter * r);
-        Bd.pinv(Bd.A.p, Bd.B.p);
-        Bd.store(Bd.B.p, O->dc2de.p + l * m2, need_fp64 ? O->dc2de_d.p + l * m2 : nullptr, np);
-        // M2L_l[o]
+        // M2L_l[o] = DC2DE_l K(dc of B, ue of the box at offset o)
         if (l >= 2) {
             for (int o = 0; o < kNumOffsets; ++o) {
                 int ox = o / 49 - 3, oy = (o / 7) % 7 - 3, oz = o % 7 - 3;
                 if (std::abs(ox) <= 1 && std::abs(oy) <= 1 && std::abs(oz) <= 1) continue;
                 const double sc[3] = {2 * r * ox, 2 * r * oy, 2 * r * oz};
                 Bd.kmat(Bd.C.p, zero, kAlphaInner * r, sc, kAlphaInner * r);
-                Bd.store(Bd.C.p, O->m2l.p + ((size_t)l * kNumOffsets + o) * m2,
+                k_matmul<<<div_up((long long)n * n, 256), 256, 0, st>>>(n, dc.p, Bd.C.p, Bd.A.p);
+                Bd.store(Bd.A.p, O->m2l.p + ((size_t)l * kNumOffsets + o) * m2,
                          need_fp64 ? O->m2l_d.p + ((size_t)l * kNumOffsets + o) * m2 : nullptr, np);
             }
         }
+        PB_CHECK_LAUNCH();
     }
     PB_CUDA(cudaStreamSynchronize(st));
     T->ops[key] = O;

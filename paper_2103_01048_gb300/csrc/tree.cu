@@ -599,6 +599,16 @@ void build_tree(fmm_tree* T, const float* src, const float* tgt) {
     k_flag<<<div_up(nb, 256), 256, 0, st>>>(nb, T->X_n.p, flag.p, 2, nullptr, nullptr);
     T->n_xbox = compact(flag.p, nb, T->xbox_ids, st);
     {
+        std::vector<int> ids(std::max(T->n_xbox, 1));
+        if (T->n_xbox)
+            PB_CUDA(cudaMemcpyAsync(ids.data(), T->xbox_ids.p, T->n_xbox * sizeof(int), cudaMemcpyDeviceToHost, st));
+        PB_CUDA(cudaStreamSynchronize(st));
+        T->xbox_lvl_off.assign(T->nlev + 1, 0);
+        for (int l = 0; l <= T->nlev; ++l)
+            T->xbox_lvl_off[l] =
+                (int)(std::lower_bound(ids.begin(), ids.begin() + T->n_xbox, T->lvl_off[l]) - ids.begin());
+    }
+    {
         // number of leaves
         std::vector<int> nch(nb);
         PB_CUDA(cudaMemcpyAsync(nch.data(), T->nchild.p, nb * sizeof(int), cudaMemcpyDeviceToHost, st));

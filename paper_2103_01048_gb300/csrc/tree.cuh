@@ -58,8 +58,9 @@ struct fmm_tree {
     pbfmm::DBuf<int> sleaf_ids;              // sorted by level
     std::vector<int> sleaf_lvl_off;          // [nlev + 1]
     // boxes with a non-empty X list
-    pbfmm::DBuf<int> xbox_ids;
+    pbfmm::DBuf<int> xbox_ids;              // in box (= level) order
     int n_xbox = 0;
+    std::vector<int> xbox_lvl_off;           // [nlev + 1]
     // non-leaf boxes per level (M2M parents) and all boxes per level for L2L
     pbfmm::M2LSchedule m2l;
 
