@@ -159,7 +159,7 @@ int fmm_tree_export_list(const fmm_tree* tree, int which, int64_t* off, int32_t*
  * out_dn[i] = sum_j dg/dn_x(x_i, y_j) q[j]     (adjoint double layer, K')
  * for every target x_i of the tree, approximated by the KIFMM with
  * expansion order p (points per edge of the equivalent/check surfaces,
- * n_e = 6(p-1)^2 + 2 surface points; 2 <= p <= 12).
+ * n_e = 6(p-1)^2 + 2 surface points; 2 <= p <= 10).
  *   kernel    FMM_LAPLACE or FMM_YUKAWA (kappa > 0 for Yukawa).
  *   q         source monopole densities [n_src] or NULL (single layer).
  *   dip       source dipole densities [n_src] or NULL (double layer); needs

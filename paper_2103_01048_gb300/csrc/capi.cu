@@ -278,7 +278,7 @@ int fmm_apply(pb_ctx* ctx, fmm_tree* T, int kernel, double kappa, int p, int pre
     PB_API_BEGIN
     PB_REQUIRE(kernel == FMM_LAPLACE || kernel == FMM_YUKAWA, PB_EINVAL, "fmm_apply: unknown kernel");
     PB_REQUIRE(kernel == FMM_LAPLACE || kappa > 0.0, PB_EINVAL, "fmm_apply: Yukawa needs kappa > 0");
-    PB_REQUIRE(p >= 2 && p <= 12, PB_EINVAL, "fmm_apply: p must be in [2, 12]");
+    PB_REQUIRE(p >= 2 && p <= 10, PB_EINVAL, "fmm_apply: p must be in [2, 10]");
     PB_REQUIRE(precision == PB_MIXED || precision == PB_FP64, PB_EINVAL, "fmm_apply: unknown precision");
     PB_REQUIRE(out != nullptr, PB_EINVAL, "fmm_apply: out is required");
     PB_REQUIRE(!dip || src_n, PB_EINVAL, "fmm_apply: double layer needs source normals");

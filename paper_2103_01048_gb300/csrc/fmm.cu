@@ -180,8 +180,8 @@ struct GemmArgs {
 // T: type of the box vectors; TO: type of the operator and the accumulation
 // (double for the ill-conditioned check-to-equivalent solves).
 template <typename T, typename TO, int NPAD>
-__global__ void __launch_bounds__(256) k_box_gemm(GemmArgs a, const TO* __restrict__ ops, const T* __restrict__ Xv,
-                                                  T* __restrict__ Yv) {
+__device__ __forceinline__ void box_gemm_body(const GemmArgs& a, const TO* __restrict__ ops, const T* __restrict__ Xv,
+                                              T* __restrict__ Yv) {
     constexpr int KC = (sizeof(TO) * NPAD * 16 > 40000) ? 8 : 16;
     constexpr int RPT = NPAD / 16;
     __shared__ TO s_op[KC][NPAD + 1];
@@ -292,6 +292,22 @@ __global__ void __launch_bounds__(256) k_box_gemm(GemmArgs a, const TO* __restri
     }
 }
 
+// One kernel name per use so launch lists and profiles separate them.
+template <typename T, typename TO, int NPAD>
+__global__ void __launch_bounds__(256) k_m2l_simt(GemmArgs a, const TO* __restrict__ ops, const T* __restrict__ X,
+                                                  T* __restrict__ Y) { box_gemm_body<T, TO, NPAD>(a, ops, X, Y); }
+template <typename T, typename TO, int NPAD>
+__global__ void __launch_bounds__(256) k_m2m(GemmArgs a, const TO* __restrict__ ops, const T* __restrict__ X,
+                                             T* __restrict__ Y) { box_gemm_body<T, TO, NPAD>(a, ops, X, Y); }
+template <typename T, typename TO, int NPAD>
+__global__ void __launch_bounds__(256) k_l2l(GemmArgs a, const TO* __restrict__ ops, const T* __restrict__ X,
+                                             T* __restrict__ Y) { box_gemm_body<T, TO, NPAD>(a, ops, X, Y); }
+template <typename T, typename TO, int NPAD>
+__global__ void __launch_bounds__(256) k_check2equiv(GemmArgs a, const TO* __restrict__ ops,
+                                                     const T* __restrict__ X, T* __restrict__ Y) {
+    box_gemm_body<T, TO, NPAD>(a, ops, X, Y);
+}
+
 // ---------------------------------------------------------------------------
 // Leaf evaluation: P2P over U(B), M2P over W(B), L2P of B's own downward
 // equivalent density, at every target of leaf B.  One CTA per target leaf.
@@ -390,7 +406,12 @@ struct Work {
 template <typename T, typename TO, int NPAD>
 static void gemm_launch(cudaStream_t st, int nblocks, const GemmArgs& a, const TO* ops, const T* X, T* Y) {
     if (nblocks <= 0) return;
-    k_box_gemm<T, TO, NPAD><<<nblocks, 256, 0, st>>>(a, ops, X, Y);
+    switch (a.mode) {
+        case G_M2L: k_m2l_simt<T, TO, NPAD><<<nblocks, 256, 0, st>>>(a, ops, X, Y); break;
+        case G_M2M: k_m2m<T, TO, NPAD><<<nblocks, 256, 0, st>>>(a, ops, X, Y); break;
+        case G_L2L: k_l2l<T, TO, NPAD><<<nblocks, 256, 0, st>>>(a, ops, X, Y); break;
+        default: k_check2equiv<T, TO, NPAD><<<nblocks, 256, 0, st>>>(a, ops, X, Y); break;
+    }
     PB_CHECK_LAUNCH();
 }
 
@@ -402,7 +423,7 @@ static void gemm_dispatch(int npad, cudaStream_t st, int nblocks, const GemmArgs
         case 64: gemm_launch<T, TO, 64>(st, nblocks, a, ops, X, Y); break;
         case 112: gemm_launch<T, TO, 112>(st, nblocks, a, ops, X, Y); break;
         case 160: gemm_launch<T, TO, 160>(st, nblocks, a, ops, X, Y); break;
-        case 208: gemm_launch<T, TO, 208>(st, nblocks, a, ops, X, Y); break;
+        case 224: gemm_launch<T, TO, 224>(st, nblocks, a, ops, X, Y); break;
         case 304: gemm_launch<T, TO, 304>(st, nblocks, a, ops, X, Y); break;
         case 400: gemm_launch<T, TO, 400>(st, nblocks, a, ops, X, Y); break;
         case 496: gemm_launch<T, TO, 496>(st, nblocks, a, ops, X, Y); break;
