@@ -49,6 +49,16 @@ enum { PB_MIXED = 0 /* FP32 kernels */, PB_FP64 = 1 /* all-FP64 kernels */ };
 
 typedef struct pb_ctx pb_ctx;
 typedef struct fmm_tree fmm_tree;
+typedef struct pb_mesh pb_mesh;
+typedef struct pb_result pb_result;
+
+/* trial/test spaces (Sec. "An introduction to Bempp") */
+enum { PB_P0 = 0 /* piecewise constant */ };
+
+typedef struct {
+    int p;        /* FMM expansion order, 2..10 */
+    int ncrit;    /* maximum points per octree leaf */
+} pb_fmm_params;
 
 /* ------------------------------------------------------------------------ */
 /* Context                                                                   */
@@ -181,6 +191,64 @@ int fmm_tree_export_list(const fmm_tree* tree, int which, int64_t* off, int32_t*
 int fmm_apply(pb_ctx* ctx, fmm_tree* tree, int kernel, double kappa, int p, int precision,
               const void* q, const void* dip, const void* src_n, const void* tgt_n,
               void* out, void* out_dn);
+
+/* ------------------------------------------------------------------------ */
+/* Boundary-element mesh and the direct formulation (Eq. direct).            */
+/* ------------------------------------------------------------------------ */
+
+/* Set up a closed triangulated surface: verts (host or device, double
+ * [nv][3]), tris (host or device, int32 [nt][3], counter-clockwise seen from
+ * outside so that normals point out of the solute, Eq. pde).  basis must be
+ * PB_P0; nquad (3 or 6) is the regular quadrature rule per triangle (3: the
+ * interior degree-2 rule (2/3,1/6,1/6); 6: Dunavant degree 4).  Builds
+ * normals, areas, quadrature points, the vertex-sharing adjacency (the
+ * pairs that need singular quadrature) and the octree over the quadrature
+ * points.  Copies the inputs; synchronous.
+ * Errors: PB_EMESH for invalid indices or a triangle with area below
+ * 1e-12 times the mean area; PB_EINVAL for other bad arguments. */
+int pb_mesh_setup(pb_ctx* ctx, const double* verts, int64_t nv, const int32_t* tris, int64_t nt,
+                  int basis, int nquad, const pb_fmm_params* params, pb_mesh** out);
+int pb_mesh_destroy(pb_mesh* mesh);
+
+/* Sizes of a mesh: triangles, quadrature points, vertex-sharing pairs. */
+int pb_mesh_info(const pb_mesh* mesh, int64_t* nt, int64_t* nquad_points, int64_t* nadj);
+
+/* Singular Galerkin entries for Yukawa parameter kappa, to HOST buffers:
+ * adj_off [nt + 1] and adj_ids [nadj] (CSR of the pairs, ascending), and
+ * S [nadj][4] = (V_L, K_L, V_Y, K_Y) entries int_Ti int_Tj of the kernels of
+ * Eq. single_double (identical or vertex-sharing triangle pairs).
+ * Synchronous; assembles S on first use for this kappa. */
+int pb_mesh_export_singular(pb_ctx* ctx, pb_mesh* mesh, double kappa, int64_t* adj_off, int32_t* adj_ids,
+                            double* S);
+
+/* y = A x for the Galerkin matrix of Eq. direct (precond = 0), or
+ * y = P^{-1} A x with the block-diagonal preconditioner (precond = 1),
+ * through the split A x = P2^T (G - C) P1 x + S x (Eq. bempp_fmm_matvec).
+ * x, y: double [2 nt] (phi, then dphi/dn), host or device.  precision
+ * PB_MIXED runs the FMM and the corrections in FP32, PB_FP64 in FP64.
+ * Synchronous when a host buffer is given. */
+int pb_mesh_matvec(pb_ctx* ctx, pb_mesh* mesh, double eps_in, double eps_out, double kappa, int precision,
+                   int precond, const double* x, double* y);
+
+/* Solve Eq. direct for point charges q (double [na], e) at atoms (double
+ * [na][3]) inside the surface, eps_in / eps_out relative permittivities,
+ * kappa the inverse Debye length (1/A).  Full GMRES (no restart, x0 = 0,
+ * left block-diagonal preconditioning) in FP64 until the preconditioned
+ * relative residual is <= tol or max_iter (1..2000) iterations.  Returns PB_OK, or
+ * PB_ENOCONV with *out still holding the last iterate.  Synchronous. */
+int pb_solve(pb_ctx* ctx, pb_mesh* mesh, const double* atoms, const double* q, int64_t na, double eps_in,
+             double eps_out, double kappa, double tol, int max_iter, int precision, pb_result** out);
+int pb_result_destroy(pb_result* res);
+
+/* Iterations, final relative residual, and (if x != NULL) the solution to a
+ * HOST buffer double [2 nt]: phi on the triangles, then dphi/dn. */
+int pb_result_get(const pb_result* res, int* iterations, double* residual, double* x);
+
+/* Polar solvation energy (Eq. energy) of a solved system, kcal/mol:
+ * dG = 1/2 sum_k q_k phi_reac(r_k) * 4 pi * 332.0637, with the reaction
+ * potential of Eq. phi_reac evaluated at the atoms by the regular rule.
+ * phi_reac (HOST, double [na]) may be NULL.  Synchronous. */
+int pb_solvation_energy(pb_ctx* ctx, pb_result* res, double* dG_kcal_per_mol, double* phi_reac);
 
 #ifdef __cplusplus
 }

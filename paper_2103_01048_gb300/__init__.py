@@ -60,6 +60,23 @@ _sig("fmm_tree_export_list", [_P, ctypes.c_int, _P, _P])
 _sig("fmm_apply", [_P, _P, ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int, _P, _P, _P, _P, _P, _P])
 
 
+class pb_fmm_params(ctypes.Structure):
+    _fields_ = [("p", ctypes.c_int), ("ncrit", ctypes.c_int)]
+
+
+_D = ctypes.c_double
+_sig("pb_mesh_setup", [_P, _P, _I64, _P, _I64, ctypes.c_int, ctypes.c_int, ctypes.POINTER(pb_fmm_params),
+                       ctypes.POINTER(_P)])
+_sig("pb_mesh_destroy", [_P])
+_sig("pb_mesh_info", [_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64), ctypes.POINTER(_I64)])
+_sig("pb_mesh_export_singular", [_P, _P, _D, _P, _P, _P])
+_sig("pb_mesh_matvec", [_P, _P, _D, _D, _D, ctypes.c_int, ctypes.c_int, _P, _P])
+_sig("pb_solve", [_P, _P, _P, _P, _I64, _D, _D, _D, _D, ctypes.c_int, ctypes.c_int, ctypes.POINTER(_P)])
+_sig("pb_result_destroy", [_P])
+_sig("pb_result_get", [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(_D), _P])
+_sig("pb_solvation_energy", [_P, _P, ctypes.POINTER(_D), _P])
+
+
 class PBError(RuntimeError):
     def __init__(self, code, msg):
         super().__init__(f"{_ERRNAMES.get(code, code)}: {msg}")
@@ -74,7 +91,8 @@ def exported_symbols():
     """Names this binding resolves in the library."""
     return ["pb_create", "pb_destroy", "pb_last_error", "pb_sync", "pb_profile", "pb_profile_read", "fmm_tree_build", "fmm_tree_destroy",
             "fmm_tree_info", "fmm_tree_export_points", "fmm_tree_export_boxes", "fmm_tree_export_list",
-            "fmm_apply"]
+            "fmm_apply", "pb_mesh_setup", "pb_mesh_destroy", "pb_mesh_info", "pb_mesh_export_singular",
+            "pb_mesh_matvec", "pb_solve", "pb_result_destroy", "pb_result_get", "pb_solvation_energy"]
 
 
 def ptr(x):
@@ -180,3 +198,75 @@ def fmm_apply(ctx, tree, kernel, kappa, p, out, q=None, dip=None, src_n=None, tg
               precision=PB_MIXED):
     _check(_lib.fmm_apply(ctx, tree, int(kernel), float(kappa), int(p), int(precision), ptr(q), ptr(dip),
                           ptr(src_n), ptr(tgt_n), ptr(out), ptr(out_dn)), ctx)
+
+
+PB_P0 = 0
+
+
+def pb_mesh_setup(ctx, verts, tris, nquad=3, p=6, ncrit=128, basis=PB_P0):
+    """verts float64 [nv,3], tris int32 [nt,3] (host numpy or device tensors)."""
+    nv = int(np.prod(verts.shape)) // 3
+    nt = int(np.prod(tris.shape)) // 3
+    prm = pb_fmm_params(int(p), int(ncrit))
+    h = _P()
+    _check(_lib.pb_mesh_setup(ctx, ptr(verts), nv, ptr(tris), nt, int(basis), int(nquad), ctypes.byref(prm),
+                              ctypes.byref(h)), ctx)
+    return h
+
+
+def pb_mesh_destroy(mesh):
+    _check(_lib.pb_mesh_destroy(mesh), None)
+
+
+def pb_mesh_info(mesh):
+    a, b, c = _I64(), _I64(), _I64()
+    _check(_lib.pb_mesh_info(mesh, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)), None)
+    return a.value, b.value, c.value
+
+
+def pb_mesh_export_singular(ctx, mesh, kappa):
+    nt, _, nadj = pb_mesh_info(mesh)
+    off = np.zeros(nt + 1, np.int64)
+    ids = np.zeros(nadj, np.int32)
+    S = np.zeros((nadj, 4))
+    _check(_lib.pb_mesh_export_singular(ctx, mesh, float(kappa), ptr(off), ptr(ids), ptr(S)), ctx)
+    return off, ids, S
+
+
+def pb_mesh_matvec(ctx, mesh, x, y, eps_in, eps_out, kappa, precision=PB_MIXED, precond=False):
+    _check(_lib.pb_mesh_matvec(ctx, mesh, float(eps_in), float(eps_out), float(kappa), int(precision),
+                               1 if precond else 0, ptr(x), ptr(y)), ctx)
+
+
+def pb_solve(ctx, mesh, atoms, charges, eps_in, eps_out, kappa, tol, max_iter=500, precision=PB_MIXED):
+    """Returns (result handle, status); status PB_OK or PB_ENOCONV (handle valid in both)."""
+    atoms = np.ascontiguousarray(atoms, dtype=np.float64) if isinstance(atoms, np.ndarray) else atoms
+    charges = np.ascontiguousarray(charges, dtype=np.float64) if isinstance(charges, np.ndarray) else charges
+    na = int(np.prod(charges.shape))
+    h = _P()
+    rc = _lib.pb_solve(ctx, mesh, ptr(atoms), ptr(charges), na, float(eps_in), float(eps_out), float(kappa),
+                       float(tol), int(max_iter), int(precision), ctypes.byref(h))
+    if rc not in (PB_OK, PB_ENOCONV) or not h:
+        _check(rc, ctx)
+    return h, rc
+
+
+def pb_result_get(res, nt=None):
+    it = ctypes.c_int()
+    rr = _D()
+    x = None
+    if nt is not None:
+        x = np.zeros(2 * nt)
+    _check(_lib.pb_result_get(res, ctypes.byref(it), ctypes.byref(rr), ptr(x)), None)
+    return it.value, rr.value, x
+
+
+def pb_result_destroy(res):
+    _check(_lib.pb_result_destroy(res), None)
+
+
+def pb_solvation_energy(ctx, res, na=None):
+    e = _D()
+    phir = np.zeros(na) if na else None
+    _check(_lib.pb_solvation_energy(ctx, res, ctypes.byref(e), ptr(phir)), ctx)
+    return (e.value, phir) if na else e.value

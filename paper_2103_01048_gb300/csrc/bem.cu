@@ -1,0 +1,874 @@
+// Galerkin BEM of the direct formulation on the GPU.
+//
+// Mat-vec (Eq. bempp_fmm_matvec): A x = P2^T (G - C) P1 x + S x, with
+//   P1  quadrature-point densities from the P0 coefficients,
+//   G   applied by one Laplace and one Yukawa FMM pass that carry the
+//       single-layer (monopole) and double-layer (dipole) sources together,
+//   C   the G entries of identical / vertex-sharing triangle pairs, removed
+//       on the fly,
+//   S   the singular Galerkin entries of those pairs (assembled once),
+// combined into the 2x2 block system of Eq. direct, then the block-diagonal
+// preconditioner (per element the 2x2 matrix of diagonal entries).
+// Solve: full GMRES in FP64 (classical Gram-Schmidt twice), Givens rotations
+// on the device.  RHS (charge -> surface), reaction potential (Eq. phi_reac,
+// surface -> charge) and the FP64 energy sum (Eq. energy).
+#include "bem.cuh"
+#include <cub/cub.cuh>
+#include <algorithm>
+#include <cmath>
+
+namespace pbfmm {
+
+void fmm_apply_impl(fmm_tree* Tr, int kernel, double kappa, int p, int precision, const void* q, const void* dip,
+                    const void* src_n, const void* tgt_n, void* out, void* out_dn);
+void build_tree(fmm_tree* T, const float* src, const float* tgt);
+
+constexpr double kInv4PiB = 0.07957747154594767;
+constexpr double kKcal = 332.0637;     // kcal A / (mol e^2)
+
+// ---------------------------------------------------------------------------
+// quadrature rules
+// ---------------------------------------------------------------------------
+// regular rules, barycentric (l0, l1, l2) and weight (sum 1): the interior
+// degree-2 3-point rule and Dunavant's degree-4 6-point rule
+static void regular_rule(int nq, std::vector<double>& L, std::vector<double>& W) {
+    L.clear(); W.clear();
+    if (nq == 3) {
+        const double a = 2.0 / 3.0, b = 1.0 / 6.0;
+        double pts[3][3] = {{a, b, b}, {b, a, b}, {b, b, a}};
+        for (auto& p : pts) { L.insert(L.end(), p, p + 3); W.push_back(1.0 / 3.0); }
+    } else if (nq == 6) {
+        const double a1 = 0.445948490915965, w1 = 0.223381589678011;
+        const double a2 = 0.091576213509771, w2 = 0.109951743655322;
+        for (int k = 0; k < 3; ++k) {
+            double p[3] = {a1, a1, a1};
+            p[k] = 1.0 - 2.0 * a1;
+            L.insert(L.end(), p, p + 3); W.push_back(w1);
+        }
+        for (int k = 0; k < 3; ++k) {
+            double p[3] = {a2, a2, a2};
+            p[k] = 1.0 - 2.0 * a2;
+            L.insert(L.end(), p, p + 3); W.push_back(w2);
+        }
+    } else {
+        throw Error(PB_EINVAL, "nquad must be 3 or 6");
+    }
+}
+
+// Gauss-Legendre on [0,1] (Newton on the Legendre recurrence)
+static void gauss01(int n, std::vector<double>& x, std::vector<double>& w) {
+    x.resize(n); w.resize(n);
+    for (int i = 0; i < n; ++i) {
+        double z = std::cos(M_PI * (i + 0.75) / (n + 0.5)), dp = 1.0;
+        for (int it = 0; it < 100; ++it) {
+            double p0 = 1.0, p1 = z;
+            for (int k = 2; k <= n; ++k) { double p2 = ((2 * k - 1) * z * p1 - (k - 1) * p0) / k; p0 = p1; p1 = p2; }
+            if (n == 1) { p1 = z; p0 = 1.0; }
+            dp = n * (z * p1 - p0) / (z * z - 1.0);
+            double dz = p1 / dp;
+            z -= dz;
+            if (std::fabs(dz) < 1e-16) break;
+        }
+        x[i] = 0.5 * (1.0 - z);
+        w[i] = 1.0 / ((1.0 - z * z) * dp * dp);
+    }
+}
+
+// collapsed Gauss rule on the reference triangle (l1, l2, weight), weights sum to 1
+constexpr int kSingOuterN = 3, kSingInnerN = 4, kSingDepth = 4;
+__constant__ double c_out_l[kSingOuterN * kSingOuterN][3];
+__constant__ double c_in_l[kSingInnerN * kSingInnerN][3];
+
+static void collapsed_rule(int n, std::vector<double>& out) {
+    std::vector<double> x, w;
+    gauss01(n, x, w);
+    out.clear();
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) {
+            out.push_back(x[i] * (1.0 - x[j]));
+            out.push_back(x[i] * x[j]);
+            out.push_back(2.0 * x[i] * w[i] * w[j]);
+        }
+}
+
+// ---------------------------------------------------------------------------
+// geometry, quadrature points
+// ---------------------------------------------------------------------------
+__global__ void k_geometry(int nt, int nv, const double* __restrict__ V, const int* __restrict__ F, int nq,
+                           const double* __restrict__ rl, const double* __restrict__ rw, double* nrm, double* area,
+                           double* qp_d, double* qn_d, double* qw_d, float* qp_f, float* qn_f, float* qw_f, int* bad) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nt) return;
+    int f0 = F[3 * i], f1 = F[3 * i + 1], f2 = F[3 * i + 2];
+    if (f0 < 0 || f1 < 0 || f2 < 0 || f0 >= nv || f1 >= nv || f2 >= nv || f0 == f1 || f1 == f2 || f0 == f2) {
+        atomicExch(bad, 1);
+        f0 = f1 = f2 = 0;
+    }
+    double a[3], b[3], c[3];
+    for (int k = 0; k < 3; ++k) { a[k] = V[3 * f0 + k]; b[k] = V[3 * f1 + k]; c[k] = V[3 * f2 + k]; }
+    double e1[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]};
+    double e2[3] = {c[0] - a[0], c[1] - a[1], c[2] - a[2]};
+    double n[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2], e1[0] * e2[1] - e1[1] * e2[0]};
+    double nn = sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+    double inv = nn > 0 ? 1.0 / nn : 0.0;
+    for (int k = 0; k < 3; ++k) nrm[3 * i + k] = n[k] * inv;
+    area[i] = 0.5 * nn;
+    for (int q = 0; q < nq; ++q) {
+        long long pidx = (long long)i * nq + q;
+        for (int k = 0; k < 3; ++k) {
+            double x = rl[3 * q] * a[k] + rl[3 * q + 1] * b[k] + rl[3 * q + 2] * c[k];
+            qp_d[3 * pidx + k] = x;
+            qp_f[3 * pidx + k] = (float)x;
+            qn_d[3 * pidx + k] = n[k] * inv;
+            qn_f[3 * pidx + k] = (float)(n[k] * inv);
+        }
+        qw_d[pidx] = rw[q] * 0.5 * nn;
+        qw_f[pidx] = (float)(rw[q] * 0.5 * nn);
+    }
+}
+
+// vertex -> triangle incidence
+__global__ void k_vcount(int nt, const int* F, int* cnt) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nt) return;
+    for (int k = 0; k < 3; ++k) atomicAdd(cnt + F[3 * i + k], 1);
+}
+__global__ void k_vfill(int nt, const int* F, const int* off, int* cur, int* ids) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nt) return;
+    for (int k = 0; k < 3; ++k) {
+        int v = F[3 * i + k];
+        ids[off[v] + atomicAdd(cur + v, 1)] = i;
+    }
+}
+
+constexpr int kAdjCap = 128;
+
+// triangles sharing a vertex with triangle i (self included), ascending;
+// pass 0 counts, pass 1 writes
+__global__ void k_adjacency(int nt, const int* F, const int* voff, const int* vids, int pass, int* cnt,
+                            const int* off, int* ids, int* overflow) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nt) return;
+    int buf[kAdjCap];
+    int n = 0;
+    for (int k = 0; k < 3; ++k) {
+        int v = F[3 * i + k];
+        for (int e = voff[v]; e < voff[v + 1]; ++e) {
+            int t = vids[e];
+            bool dup = false;
+            for (int m = 0; m < n; ++m) dup |= (buf[m] == t);
+            if (!dup) {
+                if (n >= kAdjCap) { atomicExch(overflow, 1); break; }
+                buf[n++] = t;
+            }
+        }
+    }
+    for (int a = 1; a < n; ++a) {
+        int v = buf[a], b = a - 1;
+        while (b >= 0 && buf[b] > v) { buf[b + 1] = buf[b]; --b; }
+        buf[b + 1] = v;
+    }
+    if (pass == 0) cnt[i] = n;
+    else for (int m = 0; m < n; ++m) ids[off[i] + m] = buf[m];
+}
+
+// ---------------------------------------------------------------------------
+// singular Galerkin entries (identical or vertex-sharing pairs)
+// Inner integrals: analytic for 1/r (uniform-density triangle potential,
+// Wilton et al. 1984) and for (x-y).n/r^3 (solid angle, Van Oosterom &
+// Strackee 1983); bounded Yukawa remainders by a collapsed Gauss rule.
+// Outer integral: collapsed Gauss rule on a subdivision of T_i refined
+// geometrically toward the edges of T_j, kSingDepth levels deep.
+// ---------------------------------------------------------------------------
+struct D3 { double x, y, z; };
+__device__ __forceinline__ D3 operator-(D3 a, D3 b) { return {a.x - b.x, a.y - b.y, a.z - b.z}; }
+__device__ __forceinline__ D3 operator+(D3 a, D3 b) { return {a.x + b.x, a.y + b.y, a.z + b.z}; }
+__device__ __forceinline__ D3 operator*(double s, D3 a) { return {s * a.x, s * a.y, s * a.z}; }
+__device__ __forceinline__ double dot(D3 a, D3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+__device__ __forceinline__ D3 cross(D3 a, D3 b) { return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x}; }
+__device__ __forceinline__ double len(D3 a) { return sqrt(dot(a, a)); }
+
+// int_T 1/|x-y| dA_y
+__device__ double pot_uniform_triangle(D3 x, const D3* v) {
+    D3 n = cross(v[1] - v[0], v[2] - v[0]);
+    n = (1.0 / len(n)) * n;
+    double h = dot(x - v[0], n);
+    double ah = fabs(h);
+    D3 xp = x - h * n;                       // projection on the plane
+    double scale = len(v[1] - v[0]) + len(v[2] - v[0]);
+    double total = 0.0;
+    for (int e = 0; e < 3; ++e) {
+        D3 p = v[e], q = v[(e + 1) % 3];
+        D3 t = q - p;
+        t = (1.0 / len(t)) * t;
+        D3 m = cross(t, n);                   // in-plane, outward
+        double d0 = dot(p - xp, m);           // signed distance to the edge line
+        if (fabs(d0) <= 1e-14 * scale) continue;
+        double s0 = dot(p - xp, t), s1 = dot(q - xp, t);
+        double r0 = len(x - p), r1 = len(x - q);
+        double w2 = d0 * d0 + h * h;
+        double f1 = s1 >= 0 ? r1 + s1 : w2 / (r1 - s1);
+        double f0 = s0 >= 0 ? r0 + s0 : w2 / (r0 - s0);
+        total += d0 * log(f1 / f0);
+        if (ah > 0.0) total -= ah * (atan(d0 * s1 / (w2 + ah * r1)) - atan(d0 * s0 / (w2 + ah * r0)));
+    }
+    return total;
+}
+
+// int_T (x-y).n_y/|x-y|^3 dA_y = signed solid angle of T seen from x
+__device__ double solid_angle(D3 x, const D3* v) {
+    D3 a = v[0] - x, b = v[1] - x, c = v[2] - x;
+    double la = len(a), lb = len(b), lc = len(c);
+    double num = dot(a, cross(b, c));
+    double den = la * lb * lc + dot(a, b) * lc + dot(a, c) * lb + dot(b, c) * la;
+    return -2.0 * atan2(num, den);
+}
+
+__device__ double dist_point_segment(D3 p, D3 a, D3 b) {
+    D3 ab = b - a;
+    double t = dot(p - a, ab) / dot(ab, ab);
+    t = t < 0 ? 0 : (t > 1 ? 1 : t);
+    return len(a + t * ab - p);
+}
+
+struct SubTri { D3 v[3]; int depth; };
+
+__global__ void k_singular(int nt, const double* __restrict__ V, const int* __restrict__ F,
+                           const int* __restrict__ adj_off, const int* __restrict__ adj_ids, double kappa,
+                           double* __restrict__ S) {
+    int i = blockIdx.x;
+    if (i >= nt) return;
+    D3 Ti[3];
+    for (int k = 0; k < 3; ++k) Ti[k] = {V[3 * F[3 * i + k]], V[3 * F[3 * i + k] + 1], V[3 * F[3 * i + k] + 2]};
+    for (int e = adj_off[i] + threadIdx.x; e < adj_off[i + 1]; e += blockDim.x) {
+        int j = adj_ids[e];
+        D3 Tj[3];
+        for (int k = 0; k < 3; ++k) Tj[k] = {V[3 * F[3 * j + k]], V[3 * F[3 * j + k] + 1], V[3 * F[3 * j + k] + 2]};
+        const bool same = (i == j);
+        D3 nj = cross(Tj[1] - Tj[0], Tj[2] - Tj[0]);
+        double aj = 0.5 * len(nj);
+        nj = (1.0 / (2.0 * aj)) * nj;
+        double tol = 1e-10 * sqrt(aj);
+        double vl = 0, kl = 0, vy = 0, ky = 0;
+        SubTri stack[3 * kSingDepth + 2];
+        int sp = 0;
+        stack[sp++] = {{Ti[0], Ti[1], Ti[2]}, 0};
+        while (sp > 0) {
+            SubTri s = stack[--sp];
+            bool touch = false;
+            for (int a = 0; a < 3 && !touch; ++a)
+                for (int ed = 0; ed < 3 && !touch; ++ed)
+                    touch = dist_point_segment(s.v[a], Tj[ed], Tj[(ed + 1) % 3]) < tol;
+            if (touch && s.depth < kSingDepth) {
+                D3 m01 = 0.5 * (s.v[0] + s.v[1]), m12 = 0.5 * (s.v[1] + s.v[2]), m20 = 0.5 * (s.v[2] + s.v[0]);
+                stack[sp++] = {{s.v[0], m01, m20}, s.depth + 1};
+                stack[sp++] = {{m01, s.v[1], m12}, s.depth + 1};
+                stack[sp++] = {{m20, m12, s.v[2]}, s.depth + 1};
+                stack[sp++] = {{m12, m20, m01}, s.depth + 1};
+                continue;
+            }
+            double as = 0.5 * len(cross(s.v[1] - s.v[0], s.v[2] - s.v[0]));
+            for (int k = 0; k < kSingOuterN * kSingOuterN; ++k) {
+                double l1 = c_out_l[k][0], l2 = c_out_l[k][1], w = c_out_l[k][2] * as;
+                D3 x = (1.0 - l1 - l2) * s.v[0] + l1 * s.v[1] + l2 * s.v[2];
+                double sl = pot_uniform_triangle(x, Tj);
+                double dl = same ? 0.0 : solid_angle(x, Tj);
+                double rs = 0.0, rd = 0.0;
+                if (kappa > 0.0) {
+                    for (int m = 0; m < kSingInnerN * kSingInnerN; ++m) {
+                        double m1 = c_in_l[m][0], m2 = c_in_l[m][1], wm = c_in_l[m][2];
+                        D3 y = (1.0 - m1 - m2) * Tj[0] + m1 * Tj[1] + m2 * Tj[2];
+                        D3 d = x - y;
+                        double r = len(d);
+                        double t = kappa * r;
+                        if (r > 1e-300) {
+                            double em1 = expm1(-t);
+                            rs += wm * em1 / r;
+                            rd += wm * dot(d, nj) * (em1 + t * exp(-t)) / (r * r * r);
+                        } else {
+                            rs += wm * (-kappa);
+                        }
+                    }
+                }
+                vl += w * sl;
+                kl += w * dl;
+                vy += w * (sl + aj * rs);
+                ky += w * (same ? 0.0 : dl + aj * rd);
+            }
+        }
+        S[4 * (long long)e + 0] = kInv4PiB * vl;
+        S[4 * (long long)e + 1] = kInv4PiB * kl;
+        S[4 * (long long)e + 2] = kInv4PiB * vy;
+        S[4 * (long long)e + 3] = kInv4PiB * ky;
+    }
+}
+
+__global__ void k_to_float(long long n, const double* a, float* b) {
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i < n) b[i] = (float)a[i];
+}
+
+// ---------------------------------------------------------------------------
+// mat-vec pieces
+// ---------------------------------------------------------------------------
+// P1: quadrature-point densities of both FMM passes from x = [phi; dphi]
+//   Laplace: q = -w dphi, d = w phi;  Yukawa: q = (eps1/eps2) w dphi, d = -w phi
+template <typename T>
+__global__ void k_p1(int nt, int nq, const double* __restrict__ x, const T* __restrict__ qw, double er,
+                     T* qL, T* dL, T* qY, T* dY) {
+    long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (a >= (long long)nt * nq) return;
+    int i = (int)(a / nq);
+    T w = qw[a];
+    T phi = (T)x[i], dphi = (T)x[nt + i];
+    qL[a] = -w * dphi;
+    dL[a] = w * phi;
+    qY[a] = (T)er * w * dphi;
+    dY[a] = -w * phi;
+}
+
+template <typename T> __device__ __forceinline__ T rsq(T x);
+template <> __device__ __forceinline__ float rsq<float>(float x) { return rsqrtf(x); }
+template <> __device__ __forceinline__ double rsq<double>(double x) { return rsqrt(x); }
+template <typename T> __device__ __forceinline__ T ex(T x);
+template <> __device__ __forceinline__ float ex<float>(float x) { return __expf(x); }
+template <> __device__ __forceinline__ double ex<double>(double x) { return exp(x); }
+
+// P2^T (pot - C) + S x + M/2 phi, then the 2x2 block-diagonal preconditioner
+// (if precond).  One thread per triangle.
+template <typename T>
+__global__ void k_combine(int nt, int nq, const double* __restrict__ x, const T* __restrict__ potL,
+                          const T* __restrict__ potY, const T* __restrict__ qp, const T* __restrict__ qn,
+                          const T* __restrict__ qw, const int* __restrict__ adj_off, const int* __restrict__ adj_ids,
+                          const T* __restrict__ S, const double* __restrict__ area, double er, double kappa_d,
+                          int precond, double* __restrict__ y) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nt) return;
+    const T kappa = (T)kappa_d;
+    const T c4 = (T)kInv4PiB;
+    T r1 = 0, r2 = 0;
+    for (int a = 0; a < nq; ++a) {
+        long long pa = (long long)i * nq + a;
+        T wa = qw[pa];
+        T xa = qp[3 * pa], ya = qp[3 * pa + 1], za = qp[3 * pa + 2];
+        T cL = 0, cY = 0;      // C: G entries of adjacent pairs, removed
+        for (int e = adj_off[i]; e < adj_off[i + 1]; ++e) {
+            int j = adj_ids[e];
+            T phi = (T)x[j], dphi = (T)x[nt + j];
+            for (int b = 0; b < nq; ++b) {
+                long long pb = (long long)j * nq + b;
+                if (pb == pa) continue;
+                T dx = xa - qp[3 * pb], dy = ya - qp[3 * pb + 1], dz = za - qp[3 * pb + 2];
+                T r2s = dx * dx + dy * dy + dz * dz;
+                if (r2s <= T(0)) continue;
+                T rinv = rsq<T>(r2s);
+                T r = r2s * rinv;
+                T rn = (dx * qn[3 * pb] + dy * qn[3 * pb + 1] + dz * qn[3 * pb + 2]) * rinv * rinv * rinv;
+                T wb = qw[pb];
+                cL += wb * (rinv * (-dphi) + rn * phi);
+                T e1 = ex<T>(-kappa * r);
+                cY += wb * (e1 * rinv * ((T)er * dphi) - e1 * (T(1) + kappa * r) * rn * phi);
+            }
+        }
+        r1 += wa * (potL[pa] - c4 * cL);
+        r2 += wa * (potY[pa] - c4 * cY);
+    }
+    double R1 = (double)r1, R2 = (double)r2;
+    double phi_i = x[i];
+    double d11 = 0.5 * area[i], d12 = 0, d21 = 0.5 * area[i], d22 = 0;
+    for (int e = adj_off[i]; e < adj_off[i + 1]; ++e) {
+        int j = adj_ids[e];
+        double vl = S[4 * (long long)e], kl = S[4 * (long long)e + 1], vy = S[4 * (long long)e + 2],
+               ky = S[4 * (long long)e + 3];
+        double phi = x[j], dphi = x[nt + j];
+        R1 += kl * phi - vl * dphi;
+        R2 += -ky * phi + er * vy * dphi;
+        if (j == i) { d11 += kl; d12 = -vl; d21 -= ky; d22 = er * vy; }
+    }
+    R1 += 0.5 * area[i] * phi_i;
+    R2 += 0.5 * area[i] * phi_i;
+    if (precond) {
+        double det = d11 * d22 - d12 * d21;
+        double a1 = (d22 * R1 - d12 * R2) / det;
+        double a2 = (-d21 * R1 + d11 * R2) / det;
+        R1 = a1;
+        R2 = a2;
+    }
+    y[i] = R1;
+    y[nt + i] = R2;
+}
+
+// Coulomb potential of the charges at the quadrature points, FP64:
+//   f(x_a) = sum_k q_k / (4 pi eps1 |x_a - r_k|)           (RHS of Eq. direct)
+__global__ void k_coulomb(long long np, const double* __restrict__ qp, int na, const double4* __restrict__ atoms,
+                          double inv_eps, double* __restrict__ f) {
+    __shared__ double4 s[256];
+    long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    double x = 0, y = 0, z = 0;
+    if (a < np) { x = qp[3 * a]; y = qp[3 * a + 1]; z = qp[3 * a + 2]; }
+    double acc = 0.0;
+    for (int k0 = 0; k0 < na; k0 += 256) {
+        __syncthreads();
+        if (k0 + threadIdx.x < na) s[threadIdx.x] = atoms[k0 + threadIdx.x];
+        __syncthreads();
+        int cnt = min(256, na - k0);
+        for (int k = 0; k < cnt; ++k) {
+            double dx = x - s[k].x, dy = y - s[k].y, dz = z - s[k].z;
+            double r2 = dx * dx + dy * dy + dz * dz;
+            if (r2 > 0) acc += s[k].w * rsqrt(r2);
+        }
+    }
+    if (a < np) f[a] = acc * kInv4PiB * inv_eps;
+}
+
+// b_i = sum_{a in T_i} w_a f_a, then [b; 0] through the preconditioner
+__global__ void k_rhs(int nt, int nq, const double* __restrict__ f, const double* __restrict__ qw,
+                      const int* __restrict__ adj_off, const int* __restrict__ adj_ids, const double* __restrict__ S,
+                      const double* __restrict__ area, double er, int precond, double* __restrict__ b) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nt) return;
+    double s = 0.0;
+    for (int a = 0; a < nq; ++a) s += qw[(long long)i * nq + a] * f[(long long)i * nq + a];
+    double R1 = s, R2 = 0.0;
+    if (precond) {
+        double d11 = 0.5 * area[i], d12 = 0, d21 = 0.5 * area[i], d22 = 0;
+        for (int e = adj_off[i]; e < adj_off[i + 1]; ++e) {
+            if (adj_ids[e] != i) continue;
+            d11 += S[4 * (long long)e + 1]; d12 = -S[4 * (long long)e];
+            d21 -= S[4 * (long long)e + 3]; d22 = er * S[4 * (long long)e + 2];
+        }
+        double det = d11 * d22 - d12 * d21;
+        double a1 = (d22 * R1 - d12 * R2) / det, a2 = (-d21 * R1 + d11 * R2) / det;
+        R1 = a1; R2 = a2;
+    }
+    b[i] = R1;
+    b[nt + i] = R2;
+}
+
+// phi_reac(r_k) = -K_L[phi](r_k) + V_L[dphi](r_k)   (Eq. phi_reac), FP64;
+// one block per 128 atoms, quadrature points staged in shared memory
+__global__ void k_phi_reac(int na, const double4* __restrict__ atoms, long long np, int nq, int nt,
+                           const double* __restrict__ qp, const double* __restrict__ qn, const double* __restrict__ qw,
+                           const double* __restrict__ x, double* __restrict__ out) {
+    __shared__ double s_p[128][4];
+    __shared__ double s_n[128][4];
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    double px = 0, py = 0, pz = 0;
+    if (k < na) { px = atoms[k].x; py = atoms[k].y; pz = atoms[k].z; }
+    double acc = 0.0;
+    for (long long b0 = 0; b0 < np; b0 += 128) {
+        __syncthreads();
+        long long b = b0 + threadIdx.x;
+        if (b < np) {
+            int t = (int)(b / nq);
+            double w = qw[b];
+            s_p[threadIdx.x][0] = qp[3 * b]; s_p[threadIdx.x][1] = qp[3 * b + 1]; s_p[threadIdx.x][2] = qp[3 * b + 2];
+            s_p[threadIdx.x][3] = w * x[nt + t];                 // monopole w dphi
+            double d = -w * x[t];                                // dipole -w phi
+            s_n[threadIdx.x][0] = d * qn[3 * b]; s_n[threadIdx.x][1] = d * qn[3 * b + 1];
+            s_n[threadIdx.x][2] = d * qn[3 * b + 2];
+        }
+        __syncthreads();
+        int cnt = (int)min((long long)128, np - b0);
+        for (int m = 0; m < cnt; ++m) {
+            double dx = px - s_p[m][0], dy = py - s_p[m][1], dz = pz - s_p[m][2];
+            double r2 = dx * dx + dy * dy + dz * dz;
+            double rinv = r2 > 0 ? rsqrt(r2) : 0.0;
+            acc += rinv * s_p[m][3] + (dx * s_n[m][0] + dy * s_n[m][1] + dz * s_n[m][2]) * rinv * rinv * rinv;
+        }
+    }
+    if (k < na) out[k] = acc * kInv4PiB;
+}
+
+// dG = 1/2 sum q phi_reac * 4 pi C, FP64 with a fixed reduction order
+__global__ void k_energy(int na, const double4* __restrict__ atoms, const double* __restrict__ phir, double* out) {
+    __shared__ double red[1024];
+    double s = 0.0, c = 0.0;
+    for (int k = threadIdx.x; k < na; k += blockDim.x) {
+        double v = atoms[k].w * phir[k] - c;     // Kahan
+        double t = s + v;
+        c = (t - s) - v;
+        s = t;
+    }
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) out[0] = 0.5 * red[0] * 4.0 * M_PI * kKcal;
+}
+
+// ---------------------------------------------------------------------------
+// FP64 GMRES kernels
+// ---------------------------------------------------------------------------
+constexpr int kDotBlocks = 304;
+
+// partial[blk][k] = sum over the block's rows of V[k][i] w[i], k < nk
+__global__ void k_dots(long long n, const double* __restrict__ V, long long ld, int nk, const double* __restrict__ w,
+                       double* __restrict__ partial, int kmax) {
+    __shared__ double red[256];
+    long long chunk = (n + gridDim.x - 1) / gridDim.x;
+    long long i0 = blockIdx.x * chunk, i1 = min(n, i0 + chunk);
+    for (int k = 0; k < nk; ++k) {
+        double s = 0.0;
+        const double* v = V + (long long)k * ld;
+        for (long long i = i0 + threadIdx.x; i < i1; i += blockDim.x) s += v[i] * w[i];
+        red[threadIdx.x] = s;
+        __syncthreads();
+        for (int o = 128; o > 0; o >>= 1) {
+            if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) partial[(long long)blockIdx.x * kmax + k] = red[0];
+        __syncthreads();
+    }
+}
+
+__global__ void k_dots_reduce(int nblk, int nk, const double* __restrict__ partial, int kmax, double* __restrict__ h,
+                              int accumulate) {
+    int k = threadIdx.x + blockIdx.x * blockDim.x;
+    if (k >= nk) return;
+    double s = 0.0;
+    for (int b = 0; b < nblk; ++b) s += partial[(long long)b * kmax + k];
+    h[k] = accumulate ? h[k] + s : s;
+}
+
+// w -= sum_k h[k] V[k]
+__global__ void k_update(long long n, const double* __restrict__ V, long long ld, int nk, const double* __restrict__ h,
+                         double* __restrict__ w) {
+    extern __shared__ double sh[];
+    for (int k = threadIdx.x; k < nk; k += blockDim.x) sh[k] = h[k];
+    __syncthreads();
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        double s = w[i];
+        for (int k = 0; k < nk; ++k) s -= sh[k] * V[(long long)k * ld + i];
+        w[i] = s;
+    }
+}
+
+// out = w / nrm  (nrm = sqrt(*nrm2)); used for V[j+1]
+__global__ void k_scale(long long n, const double* __restrict__ w, const double* __restrict__ nrm2, double* __restrict__ out) {
+    double inv = 1.0 / sqrt(*nrm2);
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        out[i] = w[i] * inv;
+}
+
+// Hessenberg column j (h[0..j], h[j+1] = ||w||^2 on input) -> Givens update.
+// H is column-major [kmax+1][kmax]; g, cs, sn of length kmax+1.
+__global__ void k_givens(int j, int kmax, const double* __restrict__ h, const double* __restrict__ nrm2,
+                         double* H, double* cs, double* sn, double* g, double* resid) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double* col = H + (long long)j * (kmax + 1);
+    for (int k = 0; k <= j; ++k) col[k] = h[k];
+    col[j + 1] = sqrt(*nrm2);
+    for (int k = 0; k < j; ++k) {
+        double a = col[k], b = col[k + 1];
+        col[k] = cs[k] * a + sn[k] * b;
+        col[k + 1] = -sn[k] * a + cs[k] * b;
+    }
+    double a = col[j], b = col[j + 1];
+    double r = hypot(a, b);
+    double c = r > 0 ? a / r : 1.0, s = r > 0 ? b / r : 0.0;
+    cs[j] = c;
+    sn[j] = s;
+    col[j] = r;
+    col[j + 1] = 0.0;
+    g[j + 1] = -s * g[j];
+    g[j] = c * g[j];
+    resid[0] = fabs(g[j + 1]);
+}
+
+__global__ void k_backsolve(int m, int kmax, const double* __restrict__ H, const double* __restrict__ g, double* y) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    for (int k = m - 1; k >= 0; --k) {
+        double s = g[k];
+        for (int c = k + 1; c < m; ++c) s -= H[(long long)c * (kmax + 1) + k] * y[c];
+        y[k] = s / H[(long long)k * (kmax + 1) + k];
+    }
+}
+
+// x += sum_k y[k] V[k]
+__global__ void k_axpy_basis(long long n, const double* __restrict__ V, long long ld, int m, const double* __restrict__ y,
+                             double* __restrict__ x) {
+    extern __shared__ double sh[];
+    for (int k = threadIdx.x; k < m; k += blockDim.x) sh[k] = y[k];
+    __syncthreads();
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        double s = x[i];
+        for (int k = 0; k < m; ++k) s += sh[k] * V[(long long)k * ld + i];
+        x[i] = s;
+    }
+}
+
+__global__ void k_set_g0(const double* nrm2, double* g) { g[0] = sqrt(*nrm2); }
+
+__global__ void k_vadd(int n, const double* a, double* b) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) b[i] += a[i];
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+static void ensure_singular(pb_mesh* M, double kappa) {
+    if (M->kappa_S == kappa) return;
+    cudaStream_t st = M->ctx->stream;
+    std::vector<double> ro, ri;
+    collapsed_rule(kSingOuterN, ro);
+    collapsed_rule(kSingInnerN, ri);
+    PB_CUDA(cudaMemcpyToSymbolAsync(c_out_l, ro.data(), ro.size() * sizeof(double), 0, cudaMemcpyHostToDevice, st));
+    PB_CUDA(cudaMemcpyToSymbolAsync(c_in_l, ri.data(), ri.size() * sizeof(double), 0, cudaMemcpyHostToDevice, st));
+    M->S_d.alloc(4 * M->nadj, st);
+    M->S_f.alloc(4 * M->nadj, st);
+    PhaseTimer ph(M->ctx, PB_PH_BEM);
+    k_singular<<<(int)M->nt, 32, 0, st>>>((int)M->nt, M->verts.p, M->tris.p, M->adj_off.p, M->adj_ids.p, kappa,
+                                          M->S_d.p);
+    PB_CHECK_LAUNCH();
+    k_to_float<<<div_up(4 * M->nadj, 256), 256, 0, st>>>(4 * M->nadj, M->S_d.p, M->S_f.p);
+    PB_CHECK_LAUNCH();
+    M->kappa_S = kappa;
+}
+
+void ensure_singular_public(pb_mesh* M, double kappa) { ensure_singular(M, kappa); }
+
+void mesh_setup(pb_mesh* M, const double* verts, const int* tris) {
+    cudaStream_t st = M->ctx->stream;
+    const int nt = (int)M->nt, nv = (int)M->nv, nq = M->nq;
+    M->verts.alloc(3 * nv, st);
+    M->tris.alloc(3 * nt, st);
+    PB_CUDA(cudaMemcpyAsync(M->verts.p, verts, 3 * nv * sizeof(double), cudaMemcpyDefault, st));
+    PB_CUDA(cudaMemcpyAsync(M->tris.p, tris, 3 * nt * sizeof(int), cudaMemcpyDefault, st));
+    std::vector<double> L, W;
+    regular_rule(nq, L, W);
+    DBuf<double> rl, rw;
+    rl.alloc(L.size(), st); rw.alloc(W.size(), st);
+    PB_CUDA(cudaMemcpyAsync(rl.p, L.data(), L.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+    PB_CUDA(cudaMemcpyAsync(rw.p, W.data(), W.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+    const long long np = (long long)nt * nq;
+    M->nrm.alloc(3 * nt, st); M->area.alloc(nt, st);
+    M->qp_d.alloc(3 * np, st); M->qn_d.alloc(3 * np, st); M->qw_d.alloc(np, st);
+    M->qp_f.alloc(3 * np, st); M->qn_f.alloc(3 * np, st); M->qw_f.alloc(np, st);
+    DBuf<int> bad;
+    bad.alloc(1, st);
+    bad.zero(st);
+    k_geometry<<<div_up(nt, 128), 128, 0, st>>>(nt, nv, M->verts.p, M->tris.p, nq, rl.p, rw.p, M->nrm.p, M->area.p,
+                                                M->qp_d.p, M->qn_d.p, M->qw_d.p, M->qp_f.p, M->qn_f.p, M->qw_f.p, bad.p);
+    PB_CHECK_LAUNCH();
+    int hbad = 0;
+    PB_CUDA(cudaMemcpyAsync(&hbad, bad.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    PB_CUDA(cudaStreamSynchronize(st));
+    PB_REQUIRE(!hbad, PB_EMESH, "pb_mesh_setup: triangle with an invalid or repeated vertex index");
+    {   // degenerate triangles: area < 1e-12 * mean
+        std::vector<double> ar(nt);
+        PB_CUDA(cudaMemcpyAsync(ar.data(), M->area.p, nt * sizeof(double), cudaMemcpyDeviceToHost, st));
+        PB_CUDA(cudaStreamSynchronize(st));
+        double mean = 0;
+        for (double a : ar) mean += a;
+        mean /= nt;
+        for (double a : ar) PB_REQUIRE(a >= 1e-12 * mean && a > 0, PB_EMESH, "pb_mesh_setup: degenerate triangle");
+    }
+    // adjacency through the vertex -> triangle incidence
+    DBuf<int> vcnt, voff, vcur, vids;
+    vcnt.alloc(nv + 1, st); vcnt.zero(st);
+    voff.alloc(nv + 1, st); vcur.alloc(nv, st); vcur.zero(st);
+    vids.alloc(3 * nt, st);
+    k_vcount<<<div_up(nt, 256), 256, 0, st>>>(nt, M->tris.p, vcnt.p);
+    PB_CHECK_LAUNCH();
+    {
+        size_t tmp = 0;
+        cub::DeviceScan::ExclusiveSum(nullptr, tmp, vcnt.p, voff.p, nv + 1, st);
+        DBuf<char> t;
+        t.alloc(std::max<size_t>(tmp, 1), st);
+        cub::DeviceScan::ExclusiveSum(t.p, tmp, vcnt.p, voff.p, nv + 1, st);
+    }
+    k_vfill<<<div_up(nt, 256), 256, 0, st>>>(nt, M->tris.p, voff.p, vcur.p, vids.p);
+    PB_CHECK_LAUNCH();
+    DBuf<int> acnt, ovf;
+    acnt.alloc(nt + 1, st); acnt.zero(st);
+    ovf.alloc(1, st); ovf.zero(st);
+    M->adj_off.alloc(nt + 1, st);
+    k_adjacency<<<div_up(nt, 128), 128, 0, st>>>(nt, M->tris.p, voff.p, vids.p, 0, acnt.p, nullptr, nullptr, ovf.p);
+    PB_CHECK_LAUNCH();
+    {
+        size_t tmp = 0;
+        cub::DeviceScan::ExclusiveSum(nullptr, tmp, acnt.p, M->adj_off.p, nt + 1, st);
+        DBuf<char> t;
+        t.alloc(std::max<size_t>(tmp, 1), st);
+        cub::DeviceScan::ExclusiveSum(t.p, tmp, acnt.p, M->adj_off.p, nt + 1, st);
+    }
+    int last = 0, hovf = 0;
+    PB_CUDA(cudaMemcpyAsync(&last, M->adj_off.p + nt, sizeof(int), cudaMemcpyDeviceToHost, st));
+    PB_CUDA(cudaMemcpyAsync(&hovf, ovf.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+    PB_CUDA(cudaStreamSynchronize(st));
+    PB_REQUIRE(!hovf, PB_EMESH, "pb_mesh_setup: a triangle has more than 128 vertex neighbours");
+    M->nadj = last;
+    M->adj_ids.alloc(std::max(last, 1), st);
+    k_adjacency<<<div_up(nt, 128), 128, 0, st>>>(nt, M->tris.p, voff.p, vids.p, 1, nullptr, M->adj_off.p,
+                                                 M->adj_ids.p, ovf.p);
+    PB_CHECK_LAUNCH();
+    // FMM tree over the quadrature points
+    M->tree = new fmm_tree();
+    M->tree->ctx = M->ctx;
+    M->tree->ns = np;
+    M->tree->nt = np;
+    M->tree->same = true;
+    M->tree->ncrit = M->ncrit;
+    build_tree(M->tree, M->qp_f.p, nullptr);
+    PB_CUDA(cudaStreamSynchronize(st));
+}
+
+// y = A x (precond = 0) or P^{-1} A x (precond = 1), x, y FP64 device [2 nt]
+template <typename T>
+static void matvec_t(pb_mesh* M, double eps_in, double eps_out, double kappa, const double* x, double* y, int precond) {
+    cudaStream_t st = M->ctx->stream;
+    const int nt = (int)M->nt, nq = M->nq;
+    const long long np = (long long)nt * nq;
+    const double er = eps_in / eps_out;
+    const int prec = std::is_same<T, float>::value ? PB_MIXED : PB_FP64;
+    DBuf<T> qL, dL, qY, dY, pL, pY;
+    qL.alloc(np, st); dL.alloc(np, st); qY.alloc(np, st); dY.alloc(np, st); pL.alloc(np, st); pY.alloc(np, st);
+    const T* qw = std::is_same<T, float>::value ? (const T*)M->qw_f.p : (const T*)M->qw_d.p;
+    const T* qp = std::is_same<T, float>::value ? (const T*)M->qp_f.p : (const T*)M->qp_d.p;
+    const T* qn = std::is_same<T, float>::value ? (const T*)M->qn_f.p : (const T*)M->qn_d.p;
+    const T* S = std::is_same<T, float>::value ? (const T*)M->S_f.p : (const T*)M->S_d.p;
+    {
+        PhaseTimer ph(M->ctx, PB_PH_BEM);
+        k_p1<T><<<div_up(np, 256), 256, 0, st>>>(nt, nq, x, qw, er, qL.p, dL.p, qY.p, dY.p);
+        PB_CHECK_LAUNCH();
+    }
+    fmm_apply_impl(M->tree, FMM_LAPLACE, 0.0, M->p, prec, qL.p, dL.p, qn, nullptr, pL.p, nullptr);
+    fmm_apply_impl(M->tree, FMM_YUKAWA, kappa, M->p, prec, qY.p, dY.p, qn, nullptr, pY.p, nullptr);
+    {
+        PhaseTimer ph(M->ctx, PB_PH_BEM);
+        // S in FP64 for the combine (both paths): the singular entries are exact data
+        k_combine<T><<<div_up(nt, 128), 128, 0, st>>>(nt, nq, x, pL.p, pY.p, qp, qn, qw, M->adj_off.p, M->adj_ids.p,
+                                                      (const T*)S, M->area.p, er, kappa, precond, y);
+        PB_CHECK_LAUNCH();
+    }
+}
+
+void mesh_matvec(pb_mesh* M, double eps_in, double eps_out, double kappa, int precision, const double* x, double* y,
+                 int precond) {
+    ensure_singular(M, kappa);
+    if (precision == PB_FP64) matvec_t<double>(M, eps_in, eps_out, kappa, x, y, precond);
+    else matvec_t<float>(M, eps_in, eps_out, kappa, x, y, precond);
+}
+
+template <typename T>
+static T read_scalar(const T* d, cudaStream_t st) {
+    T h;
+    PB_CUDA(cudaMemcpyAsync(&h, d, sizeof(T), cudaMemcpyDeviceToHost, st));
+    PB_CUDA(cudaStreamSynchronize(st));
+    return h;
+}
+
+// Full GMRES (x0 = 0, left preconditioned, CGS2), FP64.
+static int gmres(pb_mesh* M, pb_result* R, const double* b, double tol, int max_iter) {
+    cudaStream_t st = M->ctx->stream;
+    const long long n = 2 * M->nt;
+    const int kmax = std::max(1, max_iter);
+    DBuf<double> V, w, partial, h, h2, H, cs, sn, g, nrm2, resid, yv;
+    V.alloc((size_t)(kmax + 1) * n, st);
+    w.alloc(n, st);
+    partial.alloc((size_t)kDotBlocks * (kmax + 1), st);
+    h.alloc(kmax + 2, st);
+    h2.alloc(kmax + 2, st);
+    H.alloc((size_t)(kmax + 1) * kmax, st);
+    cs.alloc(kmax + 1, st); sn.alloc(kmax + 1, st); g.alloc(kmax + 2, st);
+    nrm2.alloc(1, st); resid.alloc(1, st); yv.alloc(kmax + 1, st);
+    g.zero(st);
+    R->x.alloc(n, st);
+    R->x.zero(st);
+    const int nb = std::min<long long>(kDotBlocks, (n + 255) / 256);
+    auto dots = [&](const double* Vb, int nk, const double* vec, double* out, int acc) {
+        k_dots<<<nb, 256, 0, st>>>(n, Vb, n, nk, vec, partial.p, kmax + 1);
+        PB_CHECK_LAUNCH();
+        k_dots_reduce<<<div_up(nk, 128), 128, 0, st>>>(nb, nk, partial.p, kmax + 1, out, acc);
+        PB_CHECK_LAUNCH();
+    };
+    const int ub = std::min<long long>(4 * M->ctx->sm_count, (n + 255) / 256);
+    // r0 = P^{-1} b (b is already preconditioned), beta = ||r0||
+    dots(b, 1, b, nrm2.p, 0);
+    double beta = std::sqrt(read_scalar(nrm2.p, st));
+    if (beta == 0.0) { R->iterations = 0; R->residual = 0.0; return PB_OK; }
+    k_scale<<<ub, 256, 0, st>>>(n, b, nrm2.p, V.p);
+    k_set_g0<<<1, 1, 0, st>>>(nrm2.p, g.p);
+    PB_CHECK_LAUNCH();
+    int j = 0;
+    double rel = 1.0;
+    int status = PB_ENOCONV;
+    for (j = 0; j < kmax; ++j) {
+        mesh_matvec(M, R->eps_in, R->eps_out, R->kappa, R->precision, V.p + (long long)j * n, w.p, 1);
+        PhaseTimer ph(M->ctx, PB_PH_GMRES);
+        // CGS2: two passes of classical Gram-Schmidt
+        dots(V.p, j + 1, w.p, h.p, 0);
+        k_update<<<ub, 256, (j + 1) * sizeof(double), st>>>(n, V.p, n, j + 1, h.p, w.p);
+        PB_CHECK_LAUNCH();
+        dots(V.p, j + 1, w.p, h2.p, 0);
+        k_update<<<ub, 256, (j + 1) * sizeof(double), st>>>(n, V.p, n, j + 1, h2.p, w.p);
+        PB_CHECK_LAUNCH();
+        k_vadd<<<div_up(j + 1, 128), 128, 0, st>>>(j + 1, h2.p, h.p);
+        PB_CHECK_LAUNCH();
+        dots(w.p, 1, w.p, nrm2.p, 0);
+        k_givens<<<1, 1, 0, st>>>(j, kmax, h.p, nrm2.p, H.p, cs.p, sn.p, g.p, resid.p);
+        PB_CHECK_LAUNCH();
+        k_scale<<<ub, 256, 0, st>>>(n, w.p, nrm2.p, V.p + (long long)(j + 1) * n);
+        PB_CHECK_LAUNCH();
+        rel = read_scalar(resid.p, st) / beta;
+        if (rel <= tol) { ++j; status = PB_OK; break; }
+    }
+    int m = std::min(j, kmax);
+    k_backsolve<<<1, 1, 0, st>>>(m, kmax, H.p, g.p, yv.p);
+    k_axpy_basis<<<ub, 256, m * sizeof(double), st>>>(n, V.p, n, m, yv.p, R->x.p);
+    PB_CHECK_LAUNCH();
+    PB_CUDA(cudaStreamSynchronize(st));
+    R->iterations = m;
+    R->residual = rel;
+    return status;
+}
+
+int solve(pb_mesh* M, pb_result* R, double tol, int max_iter) {
+    cudaStream_t st = M->ctx->stream;
+    ensure_singular(M, R->kappa);
+    const int nt = (int)M->nt, nq = M->nq;
+    const long long np = (long long)nt * nq;
+    DBuf<double> f, b;
+    f.alloc(np, st);
+    b.alloc(2 * nt, st);
+    {
+        PhaseTimer ph(M->ctx, PB_PH_BEM);
+        k_coulomb<<<div_up(np, 256), 256, 0, st>>>(np, M->qp_d.p, (int)R->na, (const double4*)R->atoms.p,
+                                                   1.0 / R->eps_in, f.p);
+        PB_CHECK_LAUNCH();
+        k_rhs<<<div_up(nt, 128), 128, 0, st>>>(nt, nq, f.p, M->qw_d.p, M->adj_off.p, M->adj_ids.p, M->S_d.p,
+                                               M->area.p, R->eps_in / R->eps_out, 1, b.p);
+        PB_CHECK_LAUNCH();
+    }
+    // The FP64 path needs the FP64 operators: gmres -> mesh_matvec selects them
+    int status = gmres(M, R, b.p, tol, max_iter);
+    R->status = status;
+    return status;
+}
+
+void reaction_energy(pb_result* R, double* phir_host, double* dG) {
+    pb_mesh* M = R->mesh;
+    cudaStream_t st = M->ctx->stream;
+    const int nt = (int)M->nt, nq = M->nq;
+    const long long np = (long long)nt * nq;
+    DBuf<double> phir, e;
+    phir.alloc(std::max<int64_t>(R->na, 1), st);
+    e.alloc(1, st);
+    PhaseTimer ph(M->ctx, PB_PH_BEM);
+    k_phi_reac<<<div_up(R->na, 128), 128, 0, st>>>((int)R->na, (const double4*)R->atoms.p, np, nq, nt, M->qp_d.p,
+                                                  M->qn_d.p, M->qw_d.p, R->x.p, phir.p);
+    PB_CHECK_LAUNCH();
+    k_energy<<<1, 1024, 0, st>>>((int)R->na, (const double4*)R->atoms.p, phir.p, e.p);
+    PB_CHECK_LAUNCH();
+    if (phir_host) PB_CUDA(cudaMemcpyAsync(phir_host, phir.p, R->na * sizeof(double), cudaMemcpyDeviceToHost, st));
+    PB_CUDA(cudaMemcpyAsync(dG, e.p, sizeof(double), cudaMemcpyDeviceToHost, st));
+    PB_CUDA(cudaStreamSynchronize(st));
+}
+
+}  // namespace pbfmm

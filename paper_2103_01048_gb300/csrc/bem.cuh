@@ -1,0 +1,40 @@
+// Galerkin BEM data of the direct formulation (Sec. "An introduction to
+// Bempp", Eq. bempp_fmm_matvec, Eq. direct).
+#pragma once
+#include "fmm.cuh"
+
+struct pb_mesh {
+    pb_ctx* ctx = nullptr;
+    int64_t nv = 0, nt = 0;
+    int nq = 3;              // regular quadrature points per triangle
+    int p = 6, ncrit = 128;  // FMM parameters
+    pbfmm::DBuf<double> verts;        // [nv][3]
+    pbfmm::DBuf<int> tris;            // [nt][3]
+    pbfmm::DBuf<double> nrm, area;    // [nt][3], [nt]
+    // quadrature points a = i*nq + k (FP64 and FP32 copies)
+    pbfmm::DBuf<double> qp_d, qn_d, qw_d;   // [N_Q][3], [N_Q][3], [N_Q] (w_k |T_i|)
+    pbfmm::DBuf<float> qp_f, qn_f, qw_f;
+    // triangles sharing at least one vertex (self included), CSR, ascending
+    pbfmm::DBuf<int> adj_off, adj_ids;
+    int64_t nadj = 0;
+    // singular Galerkin entries of the adjacent pairs, per CSR entry:
+    // [V_L, K_L, V_Y, K_Y] for kappa_S
+    pbfmm::DBuf<double> S_d;
+    pbfmm::DBuf<float> S_f;
+    double kappa_S = -1.0;
+    fmm_tree* tree = nullptr;
+};
+
+struct pb_result {
+    pb_mesh* mesh = nullptr;
+    int64_t nt = 0, na = 0;
+    double eps_in = 4, eps_out = 80, kappa = 0.125;
+    int precision = PB_MIXED;
+    int iterations = 0;
+    double residual = 0.0;
+    int status = PB_OK;
+    pbfmm::DBuf<double> x;            // [2 nt]: phi, then dphi/dn
+    pbfmm::DBuf<double> atoms, charges;
+    double energy = 0.0;
+    bool have_energy = false;
+};

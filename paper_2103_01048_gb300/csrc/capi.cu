@@ -1,12 +1,18 @@
 // C-ABI entry points (declared in include/pbfmm.h).  Every entry point turns
 // internal exceptions into a status code and a message on the context.
-#include "fmm.cuh"
+#include "bem.cuh"
 #include <new>
 
 namespace pbfmm {
 void build_tree(fmm_tree* T, const float* src, const float* tgt);
 void fmm_apply_impl(fmm_tree* Tr, int kernel, double kappa, int p, int precision, const void* q, const void* dip,
                     const void* src_n, const void* tgt_n, void* out, void* out_dn);
+void mesh_setup(pb_mesh* M, const double* verts, const int* tris);
+void mesh_matvec(pb_mesh* M, double eps_in, double eps_out, double kappa, int precision, const double* x, double* y,
+                 int precond);
+int solve(pb_mesh* M, pb_result* R, double tol, int max_iter);
+void reaction_energy(pb_result* R, double* phir_host, double* dG);
+void ensure_singular_public(pb_mesh* M, double kappa);
 
 thread_local long long g_launch_count = 0;
 
@@ -302,6 +308,168 @@ int fmm_apply(pb_ctx* ctx, fmm_tree* T, int kernel, double kappa, int p, int pre
     if (out_host) PB_CUDA(cudaMemcpyAsync(out, o, T->nt * es, cudaMemcpyDeviceToHost, st));
     if (dn_host) PB_CUDA(cudaMemcpyAsync(out_dn, od, T->nt * es, cudaMemcpyDeviceToHost, st));
     if (out_host || dn_host || sq.buf.p || sd.buf.p || sn.buf.p || tn.buf.p) PB_CUDA(cudaStreamSynchronize(st));
+    PB_API_END(ctx)
+}
+
+int pb_mesh_setup(pb_ctx* ctx, const double* verts, int64_t nv, const int32_t* tris, int64_t nt, int basis,
+                  int nquad, const pb_fmm_params* params, pb_mesh** out) {
+    if (!ctx || !out) return PB_EINVAL;
+    *out = nullptr;
+    pb_mesh* M = nullptr;
+    PB_API_BEGIN
+    PB_REQUIRE(verts && tris && nv >= 3 && nt >= 1, PB_EINVAL, "pb_mesh_setup: empty mesh");
+    PB_REQUIRE(basis == PB_P0, PB_EINVAL, "pb_mesh_setup: only the P0 basis is provided");
+    PB_REQUIRE(nquad == 3 || nquad == 6, PB_EINVAL, "pb_mesh_setup: nquad must be 3 or 6");
+    PB_REQUIRE(nt * nquad < (1LL << 31) - 1, PB_EINVAL, "pb_mesh_setup: too many quadrature points");
+    PB_CUDA(cudaSetDevice(ctx->device));
+    M = new pb_mesh();
+    M->ctx = ctx;
+    M->nv = nv;
+    M->nt = nt;
+    M->nq = nquad;
+    if (params) {
+        PB_REQUIRE(params->p >= 2 && params->p <= 10 && params->ncrit >= 1, PB_EINVAL, "pb_mesh_setup: bad FMM params");
+        M->p = params->p;
+        M->ncrit = params->ncrit;
+    }
+    mesh_setup(M, verts, tris);
+    *out = M;
+    M = nullptr;
+    }
+    catch (const pbfmm::Error& e) {
+        if (M) { delete M->tree; delete M; }
+        ctx->last_error = e.what();
+        return e.code;
+    }
+    catch (const std::exception& e) {
+        if (M) { delete M->tree; delete M; }
+        ctx->last_error = e.what();
+        return PB_EINVAL;
+    }
+    ctx->last_error.clear();
+    return PB_OK;
+}
+
+int pb_mesh_destroy(pb_mesh* M) {
+    if (!M) return PB_EINVAL;
+    cudaSetDevice(M->ctx->device);
+    cudaStreamSynchronize(M->ctx->stream);
+    delete M->tree;
+    delete M;
+    return PB_OK;
+}
+
+int pb_mesh_info(const pb_mesh* M, int64_t* nt, int64_t* nqp, int64_t* nadj) {
+    if (!M) return PB_EINVAL;
+    if (nt) *nt = M->nt;
+    if (nqp) *nqp = M->nt * M->nq;
+    if (nadj) *nadj = M->nadj;
+    return PB_OK;
+}
+
+int pb_mesh_export_singular(pb_ctx* ctx, pb_mesh* M, double kappa, int64_t* adj_off, int32_t* adj_ids, double* S) {
+    if (!ctx || !M) return PB_EINVAL;
+    PB_API_BEGIN
+    PB_REQUIRE(kappa > 0, PB_EINVAL, "pb_mesh_export_singular: kappa must be > 0");
+    cudaStream_t st = ctx->stream;
+    ensure_singular_public(M, kappa);
+    if (adj_off) {
+        std::vector<int> o(M->nt + 1);
+        PB_CUDA(cudaMemcpyAsync(o.data(), M->adj_off.p, (M->nt + 1) * 4, cudaMemcpyDeviceToHost, st));
+        PB_CUDA(cudaStreamSynchronize(st));
+        for (int64_t i = 0; i <= M->nt; ++i) adj_off[i] = o[i];
+    }
+    if (adj_ids) PB_CUDA(cudaMemcpyAsync(adj_ids, M->adj_ids.p, M->nadj * 4, cudaMemcpyDeviceToHost, st));
+    if (S) PB_CUDA(cudaMemcpyAsync(S, M->S_d.p, M->nadj * 4 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    PB_CUDA(cudaStreamSynchronize(st));
+    PB_API_END(ctx)
+}
+
+int pb_mesh_matvec(pb_ctx* ctx, pb_mesh* M, double eps_in, double eps_out, double kappa, int precision, int precond,
+                   const double* x, double* y) {
+    if (!ctx || !M) return PB_EINVAL;
+    PB_API_BEGIN
+    PB_REQUIRE(x && y && eps_in > 0 && eps_out > 0 && kappa > 0, PB_EINVAL, "pb_mesh_matvec: bad arguments");
+    PB_REQUIRE(precision == PB_MIXED || precision == PB_FP64, PB_EINVAL, "pb_mesh_matvec: unknown precision");
+    PB_CUDA(cudaSetDevice(ctx->device));
+    cudaStream_t st = ctx->stream;
+    const size_t nb = 2 * M->nt * sizeof(double);
+    Staged sx;
+    sx.in(x, nb, st);
+    bool yh = !is_device_ptr(y);
+    DBuf<char> yb;
+    double* yd = y;
+    if (yh) { yb.alloc(nb, st); yd = (double*)yb.p; }
+    mesh_matvec(M, eps_in, eps_out, kappa, precision, (const double*)sx.dev, yd, precond);
+    if (yh) PB_CUDA(cudaMemcpyAsync(y, yd, nb, cudaMemcpyDeviceToHost, st));
+    PB_CUDA(cudaStreamSynchronize(st));
+    PB_API_END(ctx)
+}
+
+int pb_solve(pb_ctx* ctx, pb_mesh* M, const double* atoms, const double* q, int64_t na, double eps_in, double eps_out,
+             double kappa, double tol, int max_iter, int precision, pb_result** out) {
+    if (!ctx || !M || !out) return PB_EINVAL;
+    *out = nullptr;
+    int status = PB_OK;
+    PB_API_BEGIN
+    PB_REQUIRE(atoms && q && na >= 1, PB_EINVAL, "pb_solve: need at least one charge");
+    PB_REQUIRE(eps_in > 0 && eps_out > 0 && kappa > 0, PB_EINVAL, "pb_solve: eps and kappa must be > 0");
+    PB_REQUIRE(tol >= 0 && max_iter >= 1 && max_iter <= 2000, PB_EINVAL, "pb_solve: tol >= 0 and 1 <= max_iter <= 2000");
+    PB_REQUIRE(precision == PB_MIXED || precision == PB_FP64, PB_EINVAL, "pb_solve: unknown precision");
+    PB_CUDA(cudaSetDevice(ctx->device));
+    cudaStream_t st = ctx->stream;
+    auto* R = new pb_result();
+    R->mesh = M;
+    R->nt = M->nt;
+    R->na = na;
+    R->eps_in = eps_in;
+    R->eps_out = eps_out;
+    R->kappa = kappa;
+    R->precision = precision;
+    // atoms as (x, y, z, q) double4 on the device
+    std::vector<double> a4(4 * na);
+    std::vector<double> ha(3 * na), hq(na);
+    PB_CUDA(cudaMemcpy(ha.data(), atoms, 3 * na * sizeof(double), cudaMemcpyDefault));
+    PB_CUDA(cudaMemcpy(hq.data(), q, na * sizeof(double), cudaMemcpyDefault));
+    for (int64_t k = 0; k < na; ++k) {
+        a4[4 * k] = ha[3 * k]; a4[4 * k + 1] = ha[3 * k + 1]; a4[4 * k + 2] = ha[3 * k + 2]; a4[4 * k + 3] = hq[k];
+    }
+    R->atoms.alloc(4 * na, st);
+    PB_CUDA(cudaMemcpyAsync(R->atoms.p, a4.data(), 4 * na * sizeof(double), cudaMemcpyHostToDevice, st));
+    *out = R;
+    status = solve(M, R, tol, max_iter);
+    if (status != PB_OK) {
+        ctx->last_error = "pb_solve: GMRES did not reach tol within max_iter";
+        return status;
+    }
+    PB_API_END(ctx)
+}
+
+int pb_result_destroy(pb_result* R) {
+    if (!R) return PB_EINVAL;
+    cudaStreamSynchronize(R->mesh->ctx->stream);
+    delete R;
+    return PB_OK;
+}
+
+int pb_result_get(const pb_result* R, int* iterations, double* residual, double* x) {
+    if (!R) return PB_EINVAL;
+    if (iterations) *iterations = R->iterations;
+    if (residual) *residual = R->residual;
+    if (x) {
+        cudaError_t e = cudaMemcpy(x, R->x.p, 2 * R->nt * sizeof(double), cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) return PB_ECUDA;
+    }
+    return PB_OK;
+}
+
+int pb_solvation_energy(pb_ctx* ctx, pb_result* R, double* dG, double* phir) {
+    if (!ctx || !R || !dG) return PB_EINVAL;
+    PB_API_BEGIN
+    PB_CUDA(cudaSetDevice(ctx->device));
+    reaction_energy(R, phir, dG);
+    R->energy = *dG;
+    R->have_energy = true;
     PB_API_END(ctx)
 }
 

@@ -1,0 +1,154 @@
+"""GPU parity of the Galerkin BEM path (direct formulation) against the
+dense P0 oracle (oracle/bem.py).
+
+* singular entries S (identical / vertex-sharing pairs) vs the oracle's
+  dense matrices at those pairs;
+* the FMM mat-vec P2^T (G - C) P1 x + S x vs the dense matrix times x;
+* pb_solve + pb_solvation_energy vs the oracle's dense-LU energy
+  (1e-4 relative, the bound on the solvation energy), mixed and FP64;
+* the Born ion of radius 2 A on the 5,120-triangle icosphere (the full
+  Born-ion configuration) against the oracle and the closed form;
+* error paths: non-convergence and degenerate meshes.
+"""
+import numpy as np
+import pytest
+
+import synthetic
+from oracle import bem, closed_forms as cf
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+EPS_IN, EPS_OUT, KAPPA = 4.0, 80.0, 0.125
+
+
+@pytest.fixture(scope="module")
+def pb():
+    import paper_2103_01048_gb300 as pb
+    return pb
+
+
+@pytest.fixture(scope="module")
+def ctx(pb):
+    c = pb.pb_create(0, None)
+    yield c
+    pb.pb_destroy(c)
+
+
+@pytest.fixture(scope="module")
+def sphere3():
+    V, F = synthetic.icosphere(3, 2.0)
+    mats = bem.assemble_p0(V, F, 3, KAPPA)
+    return V, F, mats
+
+
+def test_singular_entries(pb, ctx, sphere3):
+    V, F, mats = sphere3
+    m = pb.pb_mesh_setup(ctx, V, F.astype(np.int32), 3, 6, 64)
+    try:
+        off, ids, S = pb.pb_mesh_export_singular(ctx, m, KAPPA)
+    finally:
+        pb.pb_mesh_destroy(m)
+    nt = len(F)
+    rows = np.repeat(np.arange(nt), np.diff(off))
+    # adjacency = triangles sharing a vertex, self included, ascending
+    for i in (0, 17, nt - 1):
+        ref = sorted(j for j in range(nt) if set(F[i]) & set(F[j]))
+        assert list(ids[off[i]:off[i + 1]]) == ref
+    for k, M in enumerate(mats):
+        ref = M[rows, ids]
+        err = np.abs(S[:, k] - ref).max() / np.abs(ref).max()
+        assert err < 2e-5, (k, err)
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_matvec_vs_dense(pb, ctx, sphere3, precision):
+    V, F, mats = sphere3
+    _, area = bem.geometry(V, F)
+    A = bem.direct_matrix(mats, area, EPS_IN, EPS_OUT)
+    rng = np.random.default_rng(3)
+    x = rng.uniform(-1, 1, 2 * len(F))
+    m = pb.pb_mesh_setup(ctx, V, F.astype(np.int32), 3, 6 if precision == "mixed" else 8, 64)
+    try:
+        y = np.zeros_like(x)
+        pb.pb_mesh_matvec(ctx, m, x, y, EPS_IN, EPS_OUT, KAPPA,
+                          precision=pb.PB_MIXED if precision == "mixed" else pb.PB_FP64)
+    finally:
+        pb.pb_mesh_destroy(m)
+    ref = A @ x
+    err = np.linalg.norm(y - ref) / np.linalg.norm(ref)
+    assert err < 2e-5, err
+
+
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_solve_energy_vs_oracle(pb, ctx, sphere3, precision):
+    V, F, mats = sphere3
+    atoms = np.array([[0.3, -0.2, 0.5], [-0.6, 0.1, -0.2], [0.0, 0.7, 0.1]])
+    q = np.array([0.7, -0.4, 0.5])
+    E_ref, phi_ref, dphi_ref, _ = bem.solve_energy(V, F, 3, atoms, q, EPS_IN, EPS_OUT, KAPPA, mats=mats)
+    m = pb.pb_mesh_setup(ctx, V, F.astype(np.int32), 3, 6 if precision == "mixed" else 8, 64)
+    try:
+        res, st = pb.pb_solve(ctx, m, atoms, q, EPS_IN, EPS_OUT, KAPPA, 1e-7, 300,
+                              precision=pb.PB_MIXED if precision == "mixed" else pb.PB_FP64)
+        assert st == pb.PB_OK
+        it, rr, x = pb.pb_result_get(res, len(F))
+        E, phir = pb.pb_solvation_energy(ctx, res, len(q))
+        pb.pb_result_destroy(res)
+    finally:
+        pb.pb_mesh_destroy(m)
+    assert rr <= 1e-7 and it > 0
+    assert abs(E - E_ref) / abs(E_ref) < 1e-4
+    nt = len(F)
+    assert np.linalg.norm(x[:nt] - phi_ref) / np.linalg.norm(phi_ref) < 1e-4
+    pr_ref = bem.phi_reac(V, F, 3, phi_ref, dphi_ref, atoms)
+    assert np.allclose(phir, pr_ref, rtol=2e-4, atol=1e-8)
+
+
+def test_born_ion_full(pb, ctx):
+    """Born ion, radius 2 A, 5,120-triangle icosphere, 3-point rule, P0,
+    GMRES tol 1e-6 (the Born-ion configuration), mixed and FP64 paths."""
+    V, F = synthetic.icosphere(4, 2.0)
+    atoms, q = np.zeros((1, 3)), np.array([1.0])
+    E_ref, *_ = bem.solve_energy(V, F, 3, atoms, q, EPS_IN, EPS_OUT, KAPPA)
+    born = cf.born_energy(1.0, 2.0, EPS_IN, EPS_OUT, KAPPA)
+    for prec, p in [(pb.PB_MIXED, 6), (pb.PB_FP64, 8)]:
+        m = pb.pb_mesh_setup(ctx, V, F.astype(np.int32), 3, p, 128)
+        try:
+            res, st = pb.pb_solve(ctx, m, atoms, q, EPS_IN, EPS_OUT, KAPPA, 1e-6, 300, precision=prec)
+            assert st == pb.PB_OK
+            E = pb.pb_solvation_energy(ctx, res)
+            pb.pb_result_destroy(res)
+        finally:
+            pb.pb_mesh_destroy(m)
+        assert abs(E - E_ref) / abs(E_ref) < 1e-4
+        assert abs(E - born) / abs(born) < 2e-3
+
+
+def test_nonconvergence_returns_last_iterate(pb, ctx, sphere3):
+    V, F, _ = sphere3
+    m = pb.pb_mesh_setup(ctx, V, F.astype(np.int32), 3, 4, 64)
+    try:
+        res, st = pb.pb_solve(ctx, m, np.zeros((1, 3)), np.ones(1), EPS_IN, EPS_OUT, KAPPA, 0.0, 3)
+        assert st == pb.PB_ENOCONV
+        it, rr, x = pb.pb_result_get(res, len(F))
+        assert it == 3 and rr > 0 and np.all(np.isfinite(x))
+        pb.pb_result_destroy(res)
+    finally:
+        pb.pb_mesh_destroy(m)
+
+
+def test_degenerate_mesh_rejected(pb, ctx):
+    V, F = synthetic.icosphere(1, 1.0)
+    V = V.copy()
+    F = F.astype(np.int32).copy()
+    F[0, 2] = F[0, 1]               # repeated vertex
+    with pytest.raises(pb.PBError) as e:
+        pb.pb_mesh_setup(ctx, V, F, 3, 4, 64)
+    assert e.value.code == pb.PB_EMESH
+    F2 = synthetic.icosphere(1, 1.0)[1].astype(np.int32)
+    V2 = V.copy()
+    a, b, c = F2[5]
+    V2[c] = 0.5 * (V2[a] + V2[b])   # zero-area triangle
+    with pytest.raises(pb.PBError) as e:
+        pb.pb_mesh_setup(ctx, V2, F2, 3, 4, 64)
+    assert e.value.code == pb.PB_EMESH
