@@ -75,7 +75,7 @@ static void gauss01(int n, std::vector<double>& x, std::vector<double>& w) {
 }
 
 // collapsed Gauss rule on the reference triangle (l1, l2, weight), weights sum to 1
-constexpr int kSingOuterN = 3, kSingInnerN = 4, kSingDepth = 4;
+constexpr int kSingOuterN = 4, kSingInnerN = 4, kSingDepth = 5;
 __constant__ double c_out_l[kSingOuterN * kSingOuterN][3];
 __constant__ double c_in_l[kSingInnerN * kSingInnerN][3];
 
