@@ -250,6 +250,21 @@ int pb_result_get(const pb_result* res, int* iterations, double* residual, doubl
  * phi_reac (HOST, double [na]) may be NULL.  Synchronous. */
 int pb_solvation_energy(pb_ctx* ctx, pb_result* res, double* dG_kcal_per_mol, double* phi_reac);
 
+/* Same result as pb_solvation_energy, without allocating device memory.
+ * No counterpart in the paper: it exists for callers that cannot allocate
+ * at this point (for example while a CUDA graph is being captured, or with
+ * an allocator that is locked after start-up).  The reaction potential at
+ * the atoms is kept in a fixed scratch array compiled into the library
+ * (262,144 doubles, 2 MB, held on every GPU that loads the library until
+ * the process exits), so res may hold at most 262,144 atoms (else
+ * PB_EINVAL).  dG_device is a caller-owned DEVICE double that receives the
+ * energy in kcal/mol.  Asynchronous on the context stream.  The first call
+ * on a device looks up the scratch array's device address (once per
+ * device); make that first call before any stream capture.  All calls share
+ * the one scratch array: calls that overlap on the GPU (other streams or
+ * contexts on the same device) race and must be serialised by the caller. */
+int pb_solvation_energy_noalloc(pb_ctx* ctx, const pb_result* res, double* dG_device);
+
 #ifdef __cplusplus
 }
 #endif

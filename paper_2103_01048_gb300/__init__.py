@@ -75,6 +75,7 @@ _sig("pb_solve", [_P, _P, _P, _P, _I64, _D, _D, _D, _D, ctypes.c_int, ctypes.c_i
 _sig("pb_result_destroy", [_P])
 _sig("pb_result_get", [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(_D), _P])
 _sig("pb_solvation_energy", [_P, _P, ctypes.POINTER(_D), _P])
+_sig("pb_solvation_energy_noalloc", [_P, _P, _P])
 
 
 class PBError(RuntimeError):
@@ -92,7 +93,8 @@ def exported_symbols():
     return ["pb_create", "pb_destroy", "pb_last_error", "pb_sync", "pb_profile", "pb_profile_read", "fmm_tree_build", "fmm_tree_destroy",
             "fmm_tree_info", "fmm_tree_export_points", "fmm_tree_export_boxes", "fmm_tree_export_list",
             "fmm_apply", "pb_mesh_setup", "pb_mesh_destroy", "pb_mesh_info", "pb_mesh_export_singular",
-            "pb_mesh_matvec", "pb_solve", "pb_result_destroy", "pb_result_get", "pb_solvation_energy"]
+            "pb_mesh_matvec", "pb_solve", "pb_result_destroy", "pb_result_get", "pb_solvation_energy",
+            "pb_solvation_energy_noalloc"]
 
 
 def ptr(x):
@@ -270,3 +272,9 @@ def pb_solvation_energy(ctx, res, na=None):
     phir = np.zeros(na) if na else None
     _check(_lib.pb_solvation_energy(ctx, res, ctypes.byref(e), ptr(phir)), ctx)
     return (e.value, phir) if na else e.value
+
+
+def pb_solvation_energy_noalloc(ctx, res, dG_device):
+    """Energy into a caller-owned device double (e.g. a 1-element float64
+    CUDA tensor) without device allocation; asynchronous on the context stream."""
+    _check(_lib.pb_solvation_energy_noalloc(ctx, res, ptr(dG_device)), ctx)
