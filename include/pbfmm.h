@@ -77,7 +77,8 @@ int pb_destroy(pb_ctx* ctx);
  * the context; valid until the next call).  Never NULL. */
 const char* pb_last_error(pb_ctx* ctx);
 
-/* Wait for all work queued on the context stream. */
+/* Wait for all work queued on the context stream; PB_ETIMEOUT if a kernel
+ * with a bounded device-side wait gave up since the last check. */
 int pb_sync(pb_ctx* ctx);
 
 /* Per-phase device timers (CUDA events on the context stream).
@@ -185,7 +186,11 @@ int fmm_tree_export_list(const fmm_tree* tree, int which, int64_t* off, int32_t*
  * Buffers may be host or device memory (see conventions).  With device
  * buffers the call is asynchronous; with any host buffer it synchronises.
  * Operators for (kernel, kappa, p, tree size) are precomputed on first use
- * and cached in the tree.
+ * and cached in the tree.  With PB_MIXED and p <= 6 the M2L runs on the
+ * tensor cores (TF32 split into hi + lo parts, three products per step);
+ * its row reductions make the summation order run-dependent at the 1e-7
+ * level.  Its waits are bounded: a timeout is reported as PB_ETIMEOUT by the
+ * next synchronising call (pb_sync, or this call when it synchronises).
  * Errors: PB_EINVAL for missing normals, p out of range, kappa <= 0 with
  * FMM_YUKAWA, dip together with out_dn. */
 int fmm_apply(pb_ctx* ctx, fmm_tree* tree, int kernel, double kappa, int p, int precision,

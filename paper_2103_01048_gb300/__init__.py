@@ -278,3 +278,19 @@ def pb_solvation_energy_noalloc(ctx, res, dG_device):
     """Energy into a caller-owned device double (e.g. a 1-element float64
     CUDA tensor) without device allocation; asynchronous on the context stream."""
     _check(_lib.pb_solvation_energy_noalloc(ctx, res, ptr(dG_device)), ctx)
+
+
+# internal self-test hook of the tensor-core M2L kernel (not part of the ABI)
+_lib.pbfmm_selftest_m2l_tc.argtypes = [ctypes.c_int, ctypes.c_int, _P, _P, _P]
+_lib.pbfmm_selftest_m2l_tc.restype = ctypes.c_int
+
+
+def _selftest_m2l_tc(Q, Op):
+    """D = Q Op^T through the tcgen05 M2L kernel (float32 host arrays)."""
+    Q = np.ascontiguousarray(Q, np.float32)
+    Op = np.ascontiguousarray(Op, np.float32)
+    D = np.zeros_like(Q)
+    rc = _lib.pbfmm_selftest_m2l_tc(Q.shape[0], Q.shape[1], ptr(Q), ptr(Op), ptr(D))
+    if rc != PB_OK:
+        raise PBError(rc, "tensor-core M2L self-test failed")
+    return D

@@ -88,6 +88,8 @@ int pb_create(pb_ctx** out, int device, void* cuda_stream) {
     PB_CUDA(cudaDeviceGetDefaultMemPool(&pool, device));
     uint64_t thr = UINT64_MAX;
     PB_CUDA(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr));
+    PB_CUDA(cudaMalloc((void**)&ctx->dev_err, sizeof(int)));
+    PB_CUDA(cudaMemset(ctx->dev_err, 0, sizeof(int)));
     *out = ctx;
     PB_API_END(ctx)
 }
@@ -95,6 +97,7 @@ int pb_create(pb_ctx** out, int device, void* cuda_stream) {
 int pb_destroy(pb_ctx* ctx) {
     if (!ctx) return PB_EINVAL;
     cudaStreamSynchronize(ctx->stream);
+    if (ctx->dev_err) cudaFree(ctx->dev_err);
     delete ctx;
     return PB_OK;
 }
@@ -104,11 +107,23 @@ const char* pb_last_error(pb_ctx* ctx) {
     return ctx->last_error.c_str();
 }
 
+// Read and clear the device error flag (after a stream synchronisation).
+void check_device_error(pb_ctx* ctx) {
+    int h = 0;
+    PB_CUDA(cudaMemcpyAsync(&h, ctx->dev_err, sizeof(int), cudaMemcpyDeviceToHost, ctx->stream));
+    PB_CUDA(cudaStreamSynchronize(ctx->stream));
+    if (h) {
+        PB_CUDA(cudaMemsetAsync(ctx->dev_err, 0, sizeof(int), ctx->stream));
+        throw Error(PB_ETIMEOUT, "a device-side wait timed out (tensor-core M2L); results of the affected call are invalid");
+    }
+}
+
 int pb_sync(pb_ctx* ctx) {
     if (!ctx) return PB_EINVAL;
     PB_API_BEGIN
     PB_CUDA(cudaSetDevice(ctx->device));
     PB_CUDA(cudaStreamSynchronize(ctx->stream));
+    check_device_error(ctx);
     PB_API_END(ctx)
 }
 
@@ -307,7 +322,10 @@ int fmm_apply(pb_ctx* ctx, fmm_tree* T, int kernel, double kappa, int p, int pre
     fmm_apply_impl(T, kernel, kappa, p, precision, sq.dev, sd.dev, sn.dev, tn.dev, o, od);
     if (out_host) PB_CUDA(cudaMemcpyAsync(out, o, T->nt * es, cudaMemcpyDeviceToHost, st));
     if (dn_host) PB_CUDA(cudaMemcpyAsync(out_dn, od, T->nt * es, cudaMemcpyDeviceToHost, st));
-    if (out_host || dn_host || sq.buf.p || sd.buf.p || sn.buf.p || tn.buf.p) PB_CUDA(cudaStreamSynchronize(st));
+    if (out_host || dn_host || sq.buf.p || sd.buf.p || sn.buf.p || tn.buf.p) {
+        PB_CUDA(cudaStreamSynchronize(st));
+        check_device_error(ctx);
+    }
     PB_API_END(ctx)
 }
 
@@ -403,6 +421,7 @@ int pb_mesh_matvec(pb_ctx* ctx, pb_mesh* M, double eps_in, double eps_out, doubl
     mesh_matvec(M, eps_in, eps_out, kappa, precision, (const double*)sx.dev, yd, precond);
     if (yh) PB_CUDA(cudaMemcpyAsync(y, yd, nb, cudaMemcpyDeviceToHost, st));
     PB_CUDA(cudaStreamSynchronize(st));
+    check_device_error(ctx);
     PB_API_END(ctx)
 }
 
@@ -438,6 +457,7 @@ int pb_solve(pb_ctx* ctx, pb_mesh* M, const double* atoms, const double* q, int6
     PB_CUDA(cudaMemcpyAsync(R->atoms.p, a4.data(), 4 * na * sizeof(double), cudaMemcpyHostToDevice, st));
     *out = R;
     status = solve(M, R, tol, max_iter);
+    check_device_error(ctx);
     if (status != PB_OK) {
         ctx->last_error = "pb_solve: GMRES did not reach tol within max_iter";
         return status;

@@ -109,6 +109,9 @@ struct pb_ctx {
     long long prof_calls[PB_PH_COUNT] = {};
     long long launch_base = 0;
     std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> pending;
+    // device-side error flag of kernels with bounded waits (0 = fine); read
+    // and cleared by the next synchronising call, reported as PB_ETIMEOUT
+    int* dev_err = nullptr;
 };
 
 namespace pbfmm {

@@ -10,8 +10,11 @@
 #include "fmm.cuh"
 #include <algorithm>
 #include <memory>
+#include <type_traits>
 
 namespace pbfmm {
+
+bool m2l_tc_launch(const fmm_tree* T, const Operators& O, const float* Qu, float* Qd, int* err, cudaStream_t st);
 
 constexpr double kInv4PiD = 0.07957747154594767;
 
@@ -418,15 +421,14 @@ static void gemm_launch(cudaStream_t st, int nblocks, const GemmArgs& a, const T
 template <typename T, typename TO>
 static void gemm_dispatch(int npad, cudaStream_t st, int nblocks, const GemmArgs& a, const TO* ops, const T* X, T* Y) {
     switch (npad) {
-        case 16: gemm_launch<T, TO, 16>(st, nblocks, a, ops, X, Y); break;
         case 32: gemm_launch<T, TO, 32>(st, nblocks, a, ops, X, Y); break;
         case 64: gemm_launch<T, TO, 64>(st, nblocks, a, ops, X, Y); break;
-        case 112: gemm_launch<T, TO, 112>(st, nblocks, a, ops, X, Y); break;
+        case 128: gemm_launch<T, TO, 128>(st, nblocks, a, ops, X, Y); break;
         case 160: gemm_launch<T, TO, 160>(st, nblocks, a, ops, X, Y); break;
         case 224: gemm_launch<T, TO, 224>(st, nblocks, a, ops, X, Y); break;
-        case 304: gemm_launch<T, TO, 304>(st, nblocks, a, ops, X, Y); break;
-        case 400: gemm_launch<T, TO, 400>(st, nblocks, a, ops, X, Y); break;
-        case 496: gemm_launch<T, TO, 496>(st, nblocks, a, ops, X, Y); break;
+        case 320: gemm_launch<T, TO, 320>(st, nblocks, a, ops, X, Y); break;
+        case 416: gemm_launch<T, TO, 416>(st, nblocks, a, ops, X, Y); break;
+        case 512: gemm_launch<T, TO, 512>(st, nblocks, a, ops, X, Y); break;
         default: throw Error(PB_EINVAL, "unsupported expansion order");
     }
 }
@@ -535,7 +537,11 @@ static void apply_t(fmm_tree* Tr, const Operators& O, double kappa_d, const In* 
     }
     // M2L (V list) with DC2DE folded into the operators: accumulate into Qd
     ph.reset(); ph = std::make_unique<PhaseTimer>(ctx, PB_PH_M2L);
-    if (Tr->m2l.ntile > 0) {
+    bool tc_done = false;
+    if constexpr (std::is_same<T, float>::value) {
+        if (Tr->m2l_pairs.nitems > 0) tc_done = m2l_tc_launch(Tr, O, W.Qu.p, W.Qd.p, ctx->dev_err, st);
+    }
+    if (!tc_done && Tr->m2l.ntile > 0) {
         ga.mode = G_M2L;
         ga.tile_box = Tr->m2l.tile_box.p;
         ga.tile_level = Tr->m2l.tile_level.p;

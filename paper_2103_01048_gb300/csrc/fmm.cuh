@@ -11,7 +11,7 @@ constexpr double kAlphaInner = 1.05;
 constexpr double kAlphaOuter = 2.95;
 
 inline int surface_count(int p) { return 6 * (p - 1) * (p - 1) + 2; }
-inline int pad16(int n) { return (n + 15) / 16 * 16; }
+inline int pad32(int n) { return (n + 31) / 32 * 32; }
 
 // Translation operators for one (kernel, kappa, p) on one tree, per level.
 // Matrices are row-major [npad][npad] (row = output point, column = input
@@ -26,6 +26,11 @@ struct Operators {
     DBuf<float> uc2ue, dc2de;     // [nlev][npad^2]
     DBuf<float> m2m, l2l;         // [nlev][8][npad^2]  (child level index)
     DBuf<float> m2l;              // [nlev][343][npad^2]
+    // tensor-core M2L (p <= 6): per level and offset, the operator split into
+    // TF32 hi + lo parts, pre-swizzled (128B swizzle, K-major) per N half:
+    // [level][343][half][hi|lo][K/32][npad/2 rows][128 B]
+    DBuf<float> m2l_tc;
+    bool have_tc = false;
     // FP64 copies (all-FP64 path)
     DBuf<double> uc2ue_d, dc2de_d, m2m_d, l2l_d, m2l_d;
     bool have_d = false;

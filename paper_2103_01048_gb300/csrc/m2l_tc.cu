@@ -1,0 +1,457 @@
+// M2L on the 5th-generation tensor cores (tcgen05, TMEM accumulators).
+//
+// The V-list pairs (Sec. "Fast multipole method": interaction list I(B)) are
+// grouped by (level, relative offset): all pairs of a group share one M2L
+// operator (with the DC2DE solve folded in, FP64-built, FP32-stored).  A CTA
+// owns one group chunk and one half of the operator's output rows:
+//   * the operator half, split into TF32 hi + lo parts and pre-swizzled in
+//     global memory (128B swizzle, K-major), is copied into shared memory
+//     once with cp.async.bulk and stays resident;
+//   * 128-pair row tiles stream through: the producer threads gather the
+//     source boxes' upward densities (Qu rows), split them into TF32 hi + lo
+//     and write them swizzled into a double-buffered A stage;
+//   * one thread issues tcgen05.mma kind::tf32 (M = 128 pairs, N = npad/2,
+//     K = 8 per instruction), three products per k-step (hi*hi + hi*lo +
+//     lo*hi: FP32-level accuracy), accumulating in TMEM;
+//   * the epilogue reads the accumulator with tcgen05.ld and adds each row
+//     into the target box's downward density with red.global.add.v4.f32
+//     (targets of one group are distinct; groups overlap, hence the
+//     reduction).  Summation order across groups is not fixed.
+// Every wait is bounded (~1 s); on a timeout the kernel records an error
+// code, drains its own MMAs, frees TMEM and returns.
+#include "fmm.cuh"
+#include <cub/cub.cuh>
+#include <algorithm>
+
+namespace pbfmm {
+
+constexpr int kTcRows = 128;           // pairs per row tile (MMA M)
+constexpr int kTcItemPairs = 1024;     // pairs per work item
+constexpr int kTcMaxNpad = 160;        // resident operator half must fit in shared memory
+
+// ---------------------------------------------------------------------------
+// PTX helpers
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// bounded wait (about one second at the boost clock); false on timeout
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+    long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity)) {
+        if (clock64() - t0 > 2000000000LL) return false;
+    }
+    return true;
+}
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_alloc(uint32_t* slot, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)),
+                 "r"(ncols)
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_relinquish() {
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void mma_tf32(uint32_t dt, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(dt),
+        "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+        : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+__device__ __forceinline__ void red_add_v4(float* p, float a, float b, float c, float d) {
+    asm volatile("red.global.add.v4.f32 [%0], {%1,%2,%3,%4};" ::"l"(p), "f"(a), "f"(b), "f"(c), "f"(d) : "memory");
+}
+
+// UMMA shared-memory descriptor: K-major, 128B swizzle, 8-row atoms of 1024 B
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr >> 4) & 0x3FFF);      // start address
+    d |= (uint64_t)1 << 16;                      // leading byte offset (unused with swizzle)
+    d |= (uint64_t)(1024 >> 4) << 32;            // stride byte offset: next 8-row atom
+    d |= (uint64_t)1 << 46;                      // descriptor version
+    d |= (uint64_t)2 << 61;                      // 128B swizzle
+    return d;
+}
+// instruction descriptor: D f32, A/B tf32, K-major both, M = 128, N = n
+__host__ __device__ constexpr uint32_t idesc_tf32(int n) {
+    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+}
+
+// byte offset of element (row, k) of a [rows][32] fp32 K-block in the 128B-swizzled layout
+__host__ __device__ __forceinline__ uint32_t sw128_off(int row, int k) {
+    int c = k >> 2, w = k & 3;
+    return (uint32_t)((row >> 3) * 1024 + (row & 7) * 128 + ((c ^ (row & 7)) << 4) + (w << 2));
+}
+
+__device__ __forceinline__ float tf32_hi(float x) { return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u); }
+
+// ---------------------------------------------------------------------------
+// operator packing: [level][343][half][hi|lo][kb][nh rows][32] swizzled
+// ---------------------------------------------------------------------------
+__global__ void k_pack_m2l_tc(int npad, long long nmat, const float* __restrict__ m2l, float* __restrict__ out) {
+    long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const long long m2 = (long long)npad * npad;
+    if (idx >= nmat * m2) return;
+    long long mat = idx / m2;
+    int n = (int)((idx % m2) / npad), k = (int)(idx % npad);
+    const int nh = npad / 2, kb_n = npad / 32;
+    int half = n / nh, nr = n % nh, kb = k / 32, kk = k % 32;
+    float x = m2l[idx];
+    float hi = tf32_hi(x), lo = x - hi;
+    const long long half_bytes = 2LL * kb_n * nh * 128;
+    char* base = (char*)out + mat * 2 * half_bytes + half * half_bytes;
+    uint32_t off = (uint32_t)kb * nh * 128 + sw128_off(nr, kk);
+    *(float*)(base + off) = hi;
+    *(float*)(base + (long long)kb_n * nh * 128 + off) = lo;
+}
+
+void pack_m2l_tc(Operators& O, cudaStream_t st) {
+    if (O.npad > kTcMaxNpad || O.npad % 32 != 0) { O.have_tc = false; return; }
+    const long long nmat = (long long)O.nlev * kNumOffsets;
+    const long long m2 = (long long)O.npad * O.npad;
+    O.m2l_tc.alloc(nmat * m2 * 2, st);
+    k_pack_m2l_tc<<<div_up(nmat * m2, 256), 256, 0, st>>>(O.npad, nmat, O.m2l.p, O.m2l_tc.p);
+    PB_CHECK_LAUNCH();
+    O.have_tc = true;
+}
+
+// ---------------------------------------------------------------------------
+// V-list pairs grouped by (level, offset)
+// ---------------------------------------------------------------------------
+__global__ void k_pairs_emit(int nbox, const int* V, const int* V_n, const int* V_off, const int4* anchor,
+                             int* key, int* tgt, int* src) {
+    int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= nbox) return;
+    int4 ab = anchor[b];
+    for (int i = 0; i < V_n[b]; ++i) {
+        int s = V[(long long)b * kVCap + i];
+        int4 as = anchor[s];
+        int o = (as.x - ab.x + 3) * 49 + (as.y - ab.y + 3) * 7 + (as.z - ab.z + 3);
+        int e = V_off[b] + i;
+        key[e] = ab.w * kNumOffsets + o;
+        tgt[e] = b;
+        src[e] = s;
+    }
+}
+
+__global__ void k_gather_int(int n, const int* idx, const int* a, int* out) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = a[idx[i]];
+}
+
+void build_m2l_pairs(fmm_tree* T) {
+    cudaStream_t st = T->ctx->stream;
+    const int nb = T->nbox;
+    const long long np = T->n_v;
+    auto& P = T->m2l_pairs;
+    P.npairs = np;
+    P.nitems = 0;
+    if (np == 0) return;
+    DBuf<int> voff, key, tgt, src, idx, key_s, idx_s;
+    voff.alloc(nb + 1, st);
+    {
+        size_t tmp = 0;
+        cub::DeviceScan::ExclusiveSum(nullptr, tmp, T->V_n.p, voff.p, nb, st);
+        DBuf<char> t;
+        t.alloc(std::max<size_t>(tmp, 1), st);
+        cub::DeviceScan::ExclusiveSum(t.p, tmp, T->V_n.p, voff.p, nb, st);
+    }
+    key.alloc(np, st); tgt.alloc(np, st); src.alloc(np, st);
+    k_pairs_emit<<<div_up(nb, 128), 128, 0, st>>>(nb, T->V.p, T->V_n.p, voff.p, T->anchor.p, key.p, tgt.p, src.p);
+    PB_CHECK_LAUNCH();
+    idx.alloc(np, st); key_s.alloc(np, st); idx_s.alloc(np, st);
+    std::vector<int> hidx(np);
+    for (long long i = 0; i < np; ++i) hidx[i] = (int)i;
+    PB_CUDA(cudaMemcpyAsync(idx.p, hidx.data(), np * sizeof(int), cudaMemcpyHostToDevice, st));
+    {
+        size_t tmp = 0;
+        cub::DeviceRadixSort::SortPairs(nullptr, tmp, key.p, key_s.p, idx.p, idx_s.p, (int)np, 0, 32, st);
+        DBuf<char> t;
+        t.alloc(std::max<size_t>(tmp, 1), st);
+        cub::DeviceRadixSort::SortPairs(t.p, tmp, key.p, key_s.p, idx.p, idx_s.p, (int)np, 0, 32, st);
+    }
+    P.tgt.alloc(np, st);
+    P.src.alloc(np, st);
+    k_gather_int<<<div_up(np, 256), 256, 0, st>>>((int)np, idx_s.p, tgt.p, P.tgt.p);
+    k_gather_int<<<div_up(np, 256), 256, 0, st>>>((int)np, idx_s.p, src.p, P.src.p);
+    PB_CHECK_LAUNCH();
+    std::vector<int> hk(np);
+    PB_CUDA(cudaMemcpyAsync(hk.data(), key_s.p, np * sizeof(int), cudaMemcpyDeviceToHost, st));
+    PB_CUDA(cudaStreamSynchronize(st));
+    // work items: (first pair, pair count <= kTcItemPairs, level, offset)
+    std::vector<int4> items;
+    long long i = 0;
+    while (i < np) {
+        long long j = i;
+        while (j < np && hk[j] == hk[i]) ++j;
+        for (long long a = i; a < j; a += kTcItemPairs)
+            items.push_back(make_int4((int)a, (int)std::min<long long>(kTcItemPairs, j - a), hk[i] / kNumOffsets,
+                                      hk[i] % kNumOffsets));
+        i = j;
+    }
+    P.nitems = (int)items.size();
+    P.items.alloc(items.size(), st);
+    PB_CUDA(cudaMemcpyAsync(P.items.p, items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice, st));
+    PB_CUDA(cudaStreamSynchronize(st));
+}
+
+// ---------------------------------------------------------------------------
+// the kernel
+// ---------------------------------------------------------------------------
+struct TcSmem {
+    uint64_t barB, barMMA[2];
+    uint32_t tmem_slot;
+    int failed;
+    int src[kTcRows], tgt[kTcRows];
+};
+
+template <int NPAD>
+__global__ void __launch_bounds__(128, 1) k_m2l_tc(const int4* __restrict__ items, const int* __restrict__ ptgt,
+                                                   const int* __restrict__ psrc, const float* __restrict__ ops,
+                                                   const float* __restrict__ Qu, float* __restrict__ Qd,
+                                                   int* __restrict__ err) {
+    constexpr int NH = NPAD / 2;                     // output rows of this CTA (MMA N)
+    constexpr int KB = NPAD / 32;                    // K blocks of 32 tf32 (128 B)
+    constexpr uint32_t B_SPLIT = KB * NH * 128;      // bytes of one of hi / lo
+    constexpr uint32_t A_SPLIT = kTcRows * 128;      // 16 KB
+    constexpr uint32_t TCOLS = NH <= 32 ? 32 : (NH <= 64 ? 64 : (NH <= 128 ? 128 : 256));
+    constexpr uint32_t IDESC = idesc_tf32(NH);
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t* sB = smem;                               // [hi|lo][KB][NH][128]
+    uint8_t* sA = smem + 2 * B_SPLIT;                 // [stage][hi|lo][128][128]
+    TcSmem* S = (TcSmem*)(sA + 2 * 2 * A_SPLIT);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int4 it = items[blockIdx.x];
+    const int half = blockIdx.y;
+    const int first = it.x, npairs = it.y, level = it.z, offs = it.w;
+
+    if (tid == 0) {
+        mbar_init(&S->barB, 1);
+        mbar_init(&S->barMMA[0], 1);
+        mbar_init(&S->barMMA[1], 1);
+        S->failed = 0;
+        fence_mbar_init();
+    }
+    if (warp == 0) {
+        tmem_alloc(&S->tmem_slot, TCOLS);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t taddr = S->tmem_slot;
+
+    // resident operator half: hi and lo, one bulk copy each
+    const uint8_t* gB = (const uint8_t*)ops + (((long long)level * kNumOffsets + offs) * 2 + half) * (2LL * B_SPLIT);
+    if (tid == 0) {
+        mbar_arrive_expect_tx(&S->barB, 2 * B_SPLIT);
+        bulk_g2s(sB, gB, B_SPLIT, &S->barB);
+        bulk_g2s(sB + B_SPLIT, gB + B_SPLIT, B_SPLIT, &S->barB);
+    }
+    bool ok = mbar_wait(&S->barB, 0);
+    uint32_t commits[2] = {0, 0};
+    int last_stage = -1;
+    const int ntile = (npairs + kTcRows - 1) / kTcRows;
+    if (__syncthreads_or(!ok)) goto fail;
+
+    for (int tile = 0; tile < ntile; ++tile) {
+        const int row0 = first + tile * kTcRows;
+        const int nrow = min(kTcRows, npairs - tile * kTcRows);
+        S->src[tid] = tid < nrow ? psrc[row0 + tid] : -1;
+        S->tgt[tid] = tid < nrow ? ptgt[row0 + tid] : -1;
+        for (int kb = 0; kb < KB; ++kb) {
+            const int s = (tile * KB + kb) & 1;
+            if (commits[s] > 0) ok = mbar_wait(&S->barMMA[s], (commits[s] - 1) & 1);
+            if (__syncthreads_or(!ok)) goto fail;
+            // gather row tid of the A tile: Qu[src][kb*32 .. +32), split hi / lo
+            uint8_t* aHi = sA + (size_t)s * 2 * A_SPLIT;
+            uint8_t* aLo = aHi + A_SPLIT;
+            const int sbox = S->src[tid];
+            const float4* q4 = sbox >= 0 ? (const float4*)(Qu + (size_t)sbox * NPAD + kb * 32) : nullptr;
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+                float4 v = q4 ? q4[c] : make_float4(0.f, 0.f, 0.f, 0.f);
+                float4 h = make_float4(tf32_hi(v.x), tf32_hi(v.y), tf32_hi(v.z), tf32_hi(v.w));
+                float4 l = make_float4(v.x - h.x, v.y - h.y, v.z - h.z, v.w - h.w);
+                uint32_t off = sw128_off(tid, c * 4);
+                *(float4*)(aHi + off) = h;
+                *(float4*)(aLo + off) = l;
+            }
+            fence_proxy_async();
+            __syncthreads();
+            if (tid == 0) {
+                tc_fence_after();
+                const uint32_t aH = smem_u32(aHi), aL = smem_u32(aLo);
+                const uint32_t bH = smem_u32(sB) + kb * NH * 128, bL = bH + B_SPLIT;
+#pragma unroll
+                for (int ks = 0; ks < 4; ++ks) {
+                    const uint32_t acc0 = (kb > 0 || ks > 0) ? 1u : 0u;
+                    mma_tf32(taddr, sw128_desc(aH + ks * 32), sw128_desc(bH + ks * 32), IDESC, acc0);
+                    mma_tf32(taddr, sw128_desc(aH + ks * 32), sw128_desc(bL + ks * 32), IDESC, 1u);
+                    mma_tf32(taddr, sw128_desc(aL + ks * 32), sw128_desc(bH + ks * 32), IDESC, 1u);
+                }
+                mma_commit(&S->barMMA[s]);
+            }
+            commits[s]++;
+            last_stage = s;
+        }
+        // accumulator complete once the last commit of the tile has arrived
+        ok = mbar_wait(&S->barMMA[last_stage], (commits[last_stage] - 1) & 1);
+        if (__syncthreads_or(!ok)) goto fail;
+        tc_fence_after();
+        {
+            const int row = warp * 32 + lane;
+            const int t = S->tgt[row];
+            float* dst = t >= 0 ? Qd + (size_t)t * NPAD + half * NH : nullptr;
+#pragma unroll 1
+            for (int c0 = 0; c0 < NH; c0 += 16) {
+                float v[16];
+                tmem_ld16(taddr + ((uint32_t)(warp * 32) << 16) + c0, v);
+                if (dst) {
+#pragma unroll
+                    for (int q = 0; q < 16; q += 4) red_add_v4(dst + c0 + q, v[q], v[q + 1], v[q + 2], v[q + 3]);
+                }
+            }
+        }
+        tc_fence_before();
+        __syncthreads();
+    }
+    goto done;
+
+fail:
+    if (tid == 0) atomicExch(err, 1);
+    // drain: every MMA this CTA issued has been committed; wait (bounded) for the last
+    if (last_stage >= 0) mbar_wait(&S->barMMA[last_stage], (commits[last_stage] - 1) & 1);
+    mbar_wait(&S->barB, 0);
+done:
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (warp == 0) tmem_dealloc(taddr, TCOLS);
+}
+
+template <int NPAD>
+static size_t tc_smem_bytes() {
+    return 1024 + 2 * (size_t)(NPAD / 32) * (NPAD / 2) * 128 + 4 * (size_t)kTcRows * 128 + sizeof(TcSmem);
+}
+
+template <int NPAD>
+static void launch_tc(const fmm_tree* T, const Operators& O, const float* Qu, float* Qd, int* err, cudaStream_t st) {
+    const size_t sm = tc_smem_bytes<NPAD>();
+    PB_CUDA(cudaFuncSetAttribute(k_m2l_tc<NPAD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    dim3 grid(T->m2l_pairs.nitems, 2);
+    k_m2l_tc<NPAD><<<grid, kTcRows, sm, st>>>(T->m2l_pairs.items.p, T->m2l_pairs.tgt.p, T->m2l_pairs.src.p,
+                                              O.m2l_tc.p, Qu, Qd, err);
+    PB_CHECK_LAUNCH();
+}
+
+// returns false when the tensor-core path does not apply (caller uses SIMT)
+bool m2l_tc_launch(const fmm_tree* T, const Operators& O, const float* Qu, float* Qd, int* err, cudaStream_t st) {
+    if (!O.have_tc || T->m2l_pairs.nitems == 0) return T->m2l_pairs.nitems == 0 && O.have_tc;
+    switch (O.npad) {
+        case 32: launch_tc<32>(T, O, Qu, Qd, err, st); return true;
+        case 64: launch_tc<64>(T, O, Qu, Qd, err, st); return true;
+        case 128: launch_tc<128>(T, O, Qu, Qd, err, st); return true;
+        case 160: launch_tc<160>(T, O, Qu, Qd, err, st); return true;
+        default: return false;
+    }
+}
+
+}  // namespace pbfmm
+
+// ---------------------------------------------------------------------------
+// Self-test hook (not part of the documented ABI): D = Q Op^T for one
+// operator through the tensor-core M2L kernel, host buffers.
+// ---------------------------------------------------------------------------
+using namespace pbfmm;
+extern "C" int pbfmm_selftest_m2l_tc(int nrows, int npad, const float* Q, const float* Op, float* D) {
+    try {
+        if (nrows < 1 || (npad != 32 && npad != 64 && npad != 128 && npad != 160)) return PB_EINVAL;
+        cudaStream_t st = nullptr;
+        fmm_tree T;
+        Operators O;
+        O.npad = npad;
+        O.nlev = 1;
+        DBuf<float> m2l, q, d;
+        DBuf<int> e;
+        m2l.alloc((size_t)kNumOffsets * npad * npad, st);
+        m2l.zero(st);
+        PB_CUDA(cudaMemcpyAsync(m2l.p, Op, (size_t)npad * npad * 4, cudaMemcpyHostToDevice, st));   // offset slot 0
+        O.m2l.p = m2l.p;
+        pack_m2l_tc(O, st);
+        O.m2l.p = nullptr;
+        q.alloc((size_t)nrows * npad, st);
+        d.alloc((size_t)nrows * npad, st);
+        d.zero(st);
+        e.alloc(1, st);
+        e.zero(st);
+        PB_CUDA(cudaMemcpyAsync(q.p, Q, (size_t)nrows * npad * 4, cudaMemcpyHostToDevice, st));
+        std::vector<int> id(nrows);
+        for (int i = 0; i < nrows; ++i) id[i] = i;
+        T.m2l_pairs.tgt.alloc(nrows, st);
+        T.m2l_pairs.src.alloc(nrows, st);
+        PB_CUDA(cudaMemcpyAsync(T.m2l_pairs.tgt.p, id.data(), nrows * 4, cudaMemcpyHostToDevice, st));
+        PB_CUDA(cudaMemcpyAsync(T.m2l_pairs.src.p, id.data(), nrows * 4, cudaMemcpyHostToDevice, st));
+        std::vector<int4> items;
+        for (int a = 0; a < nrows; a += kTcItemPairs) items.push_back(make_int4(a, std::min(kTcItemPairs, nrows - a), 0, 0));
+        T.m2l_pairs.nitems = (int)items.size();
+        T.m2l_pairs.items.alloc(items.size(), st);
+        PB_CUDA(cudaMemcpyAsync(T.m2l_pairs.items.p, items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice, st));
+        m2l_tc_launch(&T, O, q.p, d.p, e.p, st);
+        int herr = 0;
+        PB_CUDA(cudaMemcpyAsync(&herr, e.p, 4, cudaMemcpyDeviceToHost, st));
+        PB_CUDA(cudaMemcpyAsync(D, d.p, (size_t)nrows * npad * 4, cudaMemcpyDeviceToHost, st));
+        PB_CUDA(cudaStreamSynchronize(st));
+        return herr ? PB_ETIMEOUT : PB_OK;
+    } catch (const Error& e) {
+        return e.code;
+    }
+}

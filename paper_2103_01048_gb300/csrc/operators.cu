@@ -151,6 +151,8 @@ struct Builder {
 
 }  // namespace
 
+void pack_m2l_tc(Operators& O, cudaStream_t st);
+
 std::shared_ptr<Operators> get_operators(fmm_tree* T, int kernel, double kappa, int p, bool need_fp64) {
     auto key = std::make_tuple(kernel, kernel == FMM_YUKAWA ? kappa : 0.0, p, T->nlev);
     auto it = T->ops.find(key);
@@ -161,7 +163,7 @@ std::shared_ptr<Operators> get_operators(fmm_tree* T, int kernel, double kappa, 
     O->kappa = kappa;
     O->p = p;
     O->ne = surface_count(p);
-    O->npad = pad16(O->ne);
+    O->npad = pad32(O->ne);
     O->nlev = T->nlev;
     const int n = O->ne, np = O->npad, L = T->nlev;
     // unit surface: boundary points of the p x p x p grid on [-1, 1]^3
@@ -237,6 +239,7 @@ std::shared_ptr<Operators> get_operators(fmm_tree* T, int kernel, double kappa, 
         }
         PB_CHECK_LAUNCH();
     }
+    pack_m2l_tc(*O, st);
     PB_CUDA(cudaStreamSynchronize(st));
     T->ops[key] = O;
     return O;

@@ -404,6 +404,8 @@ static T read1(const T* d, cudaStream_t st) {
     return h;
 }
 
+void build_m2l_pairs(fmm_tree* T);
+
 void build_tree(fmm_tree* T, const float* src, const float* tgt) {
     cudaStream_t st = T->ctx->stream;
     const long long ns = T->ns, nt = T->same ? T->ns : T->nt;
@@ -657,6 +659,8 @@ void build_tree(fmm_tree* T, const float* src, const float* tgt) {
             PB_CHECK_LAUNCH();
         }
     }
+    // 9. V-list pairs grouped by (level, offset) for the tensor-core M2L
+    build_m2l_pairs(T);
     PB_CUDA(cudaStreamSynchronize(st));
 }
 

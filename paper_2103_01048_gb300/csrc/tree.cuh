@@ -26,6 +26,15 @@ struct M2LSchedule {
     long long npairs = 0;              // total V-list pairs (algorithmic work)
 };
 
+// V-list pairs sorted by (level, offset) for the tensor-core M2L, cut into
+// work items (first pair, count <= 1024, level, offset).
+struct M2LPairs {
+    DBuf<int> tgt, src;
+    DBuf<int4> items;
+    int nitems = 0;
+    long long npairs = 0;
+};
+
 }  // namespace pbfmm
 
 struct fmm_tree {
@@ -63,6 +72,7 @@ struct fmm_tree {
     std::vector<int> xbox_lvl_off;           // [nlev + 1]
     // non-leaf boxes per level (M2M parents) and all boxes per level for L2L
     pbfmm::M2LSchedule m2l;
+    pbfmm::M2LPairs m2l_pairs;
 
     std::map<std::tuple<int, double, int, int>, std::shared_ptr<pbfmm::Operators>> ops;
 };

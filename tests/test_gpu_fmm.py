@@ -86,6 +86,19 @@ def test_tree_bit_exact(pb, ctx, name, src, tgt, ncrit):
         assert np.array_equal(ids, rids), name_l
 
 
+@pytest.mark.parametrize("npad,nrows", [(32, 130), (64, 1), (128, 257), (160, 2500)])
+def test_tcgen05_m2l_kernel(pb, npad, nrows):
+    """The tensor-core M2L kernel alone: D = Q Op^T with TF32 hi/lo splitting
+    matches the FP64 product to FP32-level accuracy (ragged row tiles,
+    several work items)."""
+    rng = np.random.default_rng(npad + nrows)
+    Q = rng.uniform(-1, 1, (nrows, npad)).astype(np.float32)
+    Op = rng.uniform(-1, 1, (npad, npad)).astype(np.float32)
+    D = pb._selftest_m2l_tc(Q, Op)
+    ref = Q.astype(np.float64) @ Op.astype(np.float64).T
+    assert np.abs(D - ref).max() / np.abs(ref).max() < 2e-6
+
+
 def fmm_case(n, seed=0):
     x, nrm = synthetic.bumpy_sphere_points(n, seed=seed)
     q = synthetic.uniform_densities(n, seed=seed + 1)
