@@ -182,7 +182,8 @@ def test_separate_targets_and_host_buffers(pb, ctx):
         pb.fmm_tree_destroy(h)
     ref = direct_sum(LAPLACE, 0.0, x, q=q, dip=d, src_n=nrm, tgt=tgt)
     assert rel_l2(out, ref) < TOL
-    assert np.array_equal(out, host_out)
+    # the tensor-core M2L reduces rows in a run-dependent order
+    assert rel_l2(host_out, out) < 1e-6
 
 
 def test_invalid_arguments(pb, ctx, case20k):
