@@ -130,7 +130,10 @@ __host__ __device__ __forceinline__ uint32_t sw128_off(int row, int k) {
     return (uint32_t)((row >> 3) * 1024 + (row & 7) * 128 + ((c ^ (row & 7)) << 4) + (w << 2));
 }
 
-__device__ __forceinline__ float tf32_hi(float x) { return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u); }
+// TF32 part of x, rounded to nearest (ties away from zero); x - hi is exact in FP32
+__device__ __forceinline__ float tf32_hi(float x) {
+    return __uint_as_float((__float_as_uint(x) + 0x1000u) & 0xFFFFE000u);
+}
 
 // ---------------------------------------------------------------------------
 // operator packing: [level][343][half][hi|lo][kb][nh rows][32] swizzled

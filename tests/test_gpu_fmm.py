@@ -96,7 +96,7 @@ def test_tcgen05_m2l_kernel(pb, npad, nrows):
     Op = rng.uniform(-1, 1, (npad, npad)).astype(np.float32)
     D = pb._selftest_m2l_tc(Q, Op)
     ref = Q.astype(np.float64) @ Op.astype(np.float64).T
-    assert np.abs(D - ref).max() / np.abs(ref).max() < 2e-6
+    assert np.abs(D - ref).max() / np.abs(ref).max() < 5e-6
 
 
 def fmm_case(n, seed=0):
