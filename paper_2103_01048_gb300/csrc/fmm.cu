@@ -17,6 +17,8 @@ namespace pbfmm {
 bool m2l_tc_launch(const fmm_tree* T, const Operators& O, const float* Qu, float* Qd, int* err, cudaStream_t st);
 
 constexpr double kInv4PiD = 0.07957747154594767;
+constexpr int kTC = 32;    // boxes per tile of the dense box-vector products (= kM2LTile)
+static_assert(kTC == kM2LTile, "M2L tile width");
 
 template <typename T> struct V4;
 template <> struct V4<float> { using type = float4; };
@@ -91,8 +93,8 @@ __global__ void k_scatter(long long n, const int* __restrict__ perm, const T* __
 // mode 0 (P2M): sources = the box's own points, check surface at 2.95 r.
 // mode 1 (P2L): sources = points of the X-list leaves, check surface at 1.05 r.
 // ---------------------------------------------------------------------------
-template <typename T, bool YUK, bool DL>
-__global__ void __launch_bounds__(128) k_p2check(int nbox, const int* __restrict__ boxes, int mode,
+template <typename T, bool YUK, bool DL, int MAXP>
+__global__ void __launch_bounds__(256) k_p2check(int nbox, const int* __restrict__ boxes, int mode,
                                                  const double4* __restrict__ center, const int* __restrict__ sb,
                                                  const int* __restrict__ se, const int* __restrict__ X,
                                                  const int* __restrict__ X_n,
@@ -100,11 +102,11 @@ __global__ void __launch_bounds__(128) k_p2check(int nbox, const int* __restrict
                                                  const typename V4<T>::type* __restrict__ sm,
                                                  const float4* __restrict__ surf, int ne, int npad, T kappa,
                                                  T* __restrict__ chk) {
+    // one (MAXP = 1) or two check points per thread; blockDim.x <= 256
     using V = typename V4<T>::type;
-    constexpr int CH = 128;
-    constexpr int MAXP = 4;   // check points per thread (ne <= 512)
-    __shared__ V s_q[CH];
-    __shared__ V s_m[DL ? CH : 1];
+    __shared__ V s_q[256];
+    __shared__ V s_m[DL ? 256 : 1];
+    const int CH = blockDim.x;
     int bi = blockIdx.x;
     if (bi >= nbox) return;
     int b = boxes[bi];
@@ -151,13 +153,78 @@ __global__ void __launch_bounds__(128) k_p2check(int nbox, const int* __restrict
     }
 }
 
+// Check potential -> equivalent density, X (float) -> Y (float), with the
+// ill-conditioned operator (UC2UE or DC2DE, norm ~1e6) held as an FP32 pair
+// op = hi + lo and every product and sum carried in double-float
+// (error-free product by FMA, TwoSum accumulation): ~48-bit arithmetic on
+// the FP32 pipes instead of the FP64 units.
+template <int NPAD>
+__global__ void __launch_bounds__(256) k_check2equiv_df(int ncols, const int* __restrict__ cols, int col_base,
+                                                        const float* __restrict__ op_hi,
+                                                        const float* __restrict__ op_lo, const float* __restrict__ Xv,
+                                                        float* __restrict__ Yv) {
+    constexpr int KC = NPAD > 256 ? 8 : 16;
+    constexpr int RPT = NPAD / 16;
+    __shared__ float s_h[KC][NPAD + 1];
+    __shared__ float s_l[KC][NPAD + 1];
+    __shared__ float s_x[KC][kTC + 1];
+    __shared__ int s_box[kTC];
+    const int tid = threadIdx.x, ty = tid / 16, tx = tid % 16;
+    if (tid < kTC) {
+        int ci = blockIdx.x * kTC + tid;
+        s_box[tid] = ci < ncols ? (cols ? cols[ci] : col_base + ci) : -1;
+    }
+    float sum[RPT][2], cmp[RPT][2];
+#pragma unroll
+    for (int r = 0; r < RPT; ++r) sum[r][0] = sum[r][1] = cmp[r][0] = cmp[r][1] = 0.f;
+    for (int k0 = 0; k0 < NPAD; k0 += KC) {
+        __syncthreads();
+        for (int i = tid; i < NPAD * KC; i += 256) {
+            int row = i / KC, kk = i % KC;
+            s_h[kk][row] = op_hi[(size_t)row * NPAD + k0 + kk];
+            s_l[kk][row] = op_lo[(size_t)row * NPAD + k0 + kk];
+        }
+        for (int i = tid; i < kTC * KC; i += 256) {
+            int c = i / KC, kk = i % KC;
+            int s = s_box[c];
+            s_x[kk][c] = (s >= 0) ? Xv[(size_t)s * NPAD + k0 + kk] : 0.f;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < KC; ++kk) {
+            float x[2] = {s_x[kk][2 * tx], s_x[kk][2 * tx + 1]};
+#pragma unroll
+            for (int r = 0; r < RPT; ++r) {
+                float oh = s_h[kk][ty + 16 * r], ol = s_l[kk][ty + 16 * r];
+#pragma unroll
+                for (int cc = 0; cc < 2; ++cc) {
+                    float p = __fmul_rn(oh, x[cc]);
+                    float e = fmaf(oh, x[cc], -p);          // exact error of oh * x
+                    e = fmaf(ol, x[cc], e);
+                    float s = sum[r][cc];
+                    float t = __fadd_rn(s, p);               // TwoSum(s, p)
+                    float bp = __fsub_rn(t, s);
+                    float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(p, bp));
+                    sum[r][cc] = t;
+                    cmp[r][cc] += err + e;
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int cc = 0; cc < 2; ++cc) {
+        int d = s_box[2 * tx + cc];
+        if (d < 0) continue;
+#pragma unroll
+        for (int r = 0; r < RPT; ++r) Yv[(size_t)d * NPAD + ty + 16 * r] = sum[r][cc] + cmp[r][cc];
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Dense operator x box-vector products (UC2UE, DC2DE, M2M, L2L, M2L), SIMT.
 // A CTA computes C[npad x 32 boxes] = sum over terms of Op_term x X_gathered,
 // 256 threads as 16 row groups x 16 column pairs, K chunks of 16 in smem.
 // ---------------------------------------------------------------------------
-constexpr int kTC = 32;    // boxes per tile (= kM2LTile)
-static_assert(kTC == kM2LTile, "M2L tile width");
 
 enum GemmMode { G_DENSE = 0, G_M2M = 1, G_L2L = 2, G_M2L = 3 };
 
@@ -313,7 +380,12 @@ __global__ void __launch_bounds__(256) k_check2equiv(GemmArgs a, const TO* __res
 
 // ---------------------------------------------------------------------------
 // Leaf evaluation: P2P over U(B), M2P over W(B), L2P of B's own downward
-// equivalent density, at every target of leaf B.  One CTA per target leaf.
+// equivalent density, at every target of leaf B.  One CTA (128 threads) per
+// target leaf.  A leaf holds at most ncrit targets, usually fewer than 128:
+// the CTA is split into G = 128 / slots groups (slots = the smallest power of
+// two >= the target count, at least 16); group g takes every G-th source of
+// each staged chunk and the G partial sums are added at the end, so no
+// thread idles.
 // ---------------------------------------------------------------------------
 template <typename T, bool YUK, bool DL, bool DN>
 __global__ void __launch_bounds__(128) k_leaf_eval(const int* __restrict__ leaves, int nleaf,
@@ -333,12 +405,17 @@ __global__ void __launch_bounds__(128) k_leaf_eval(const int* __restrict__ leave
     constexpr int CH = 128;
     __shared__ V s_q[CH];
     __shared__ V s_m[DL ? CH : 1];
+    __shared__ T s_red[2][CH];
     int li = blockIdx.x;
     if (li >= nleaf) return;
     int b = leaves[li];
     int t0 = tb[b], t1 = te[b];
-    for (int tc = t0; tc < t1; tc += CH) {
-        int t = tc + threadIdx.x;
+    int slots = CH;
+    while (slots > 16 && slots / 2 >= t1 - t0) slots /= 2;
+    const int G = CH / slots;
+    const int tloc = threadIdx.x % slots, g = threadIdx.x / slots;
+    for (int tc = t0; tc < t1; tc += slots) {
+        int t = tc + tloc;
         bool valid = t < t1;
         float4 xp = valid ? tpos[t] : make_float4(0, 0, 0, 0);
         T x = xp.x, y = xp.y, z = xp.z;
@@ -358,7 +435,7 @@ __global__ void __launch_bounds__(128) k_leaf_eval(const int* __restrict__ leave
                 }
                 __syncthreads();
                 int cnt = min(CH, j1 - jc);
-                for (int k = 0; k < cnt; ++k) {
+                for (int k = g; k < cnt; k += G) {
                     V s = s_q[k];
                     T mx = 0, my = 0, mz = 0;
                     if (DL) { V mm = s_m[k]; mx = mm.x; my = mm.y; mz = mm.z; }
@@ -384,15 +461,24 @@ __global__ void __launch_bounds__(128) k_leaf_eval(const int* __restrict__ leave
                 }
                 __syncthreads();
                 int cnt = min(CH, ne - jc);
-                for (int k = 0; k < cnt; ++k) {
+                for (int k = g; k < cnt; k += G) {
                     V s = s_q[k];
                     interact<T, YUK, false, DN>(rx - s.x, ry - s.y, rz - s.z, s.w, 0, 0, 0, nx, ny, nz, kappa, pot, dn);
                 }
             }
         }
-        if (valid) {
-            pot_out[t] = pot * T(kInv4PiD);
-            if (DN) dn_out[t] = dn * T(kInv4PiD);
+        // combine the G partial sums of each target
+        s_red[0][threadIdx.x] = pot;
+        if (DN) s_red[1][threadIdx.x] = dn;
+        __syncthreads();
+        if (g == 0 && valid) {
+            T p = 0, d = 0;
+            for (int q = 0; q < G; ++q) {
+                p += s_red[0][tloc + q * slots];
+                if (DN) d += s_red[1][tloc + q * slots];
+            }
+            pot_out[t] = p * T(kInv4PiD);
+            if (DN) dn_out[t] = d * T(kInv4PiD);
         }
     }
 }
@@ -437,9 +523,59 @@ template <typename T, bool YUK, bool DL>
 static void launch_p2check(cudaStream_t st, int nbox, const int* boxes, int mode, fmm_tree* Tr, Work<T>& W,
                            const Operators& O, T kappa) {
     if (nbox <= 0) return;
-    k_p2check<T, YUK, DL><<<nbox, 128, 0, st>>>(nbox, boxes, mode, Tr->center.p, Tr->sb.p, Tr->se.p, Tr->X.p,
-                                                Tr->X_n.p, W.sq.p, W.sm.p, (const float4*)O.surf_f.p, O.ne, O.npad, kappa, W.chk.p);
+    if (O.npad <= 256)
+        k_p2check<T, YUK, DL, 1><<<nbox, O.npad, 0, st>>>(nbox, boxes, mode, Tr->center.p, Tr->sb.p, Tr->se.p,
+                                                          Tr->X.p, Tr->X_n.p, W.sq.p, W.sm.p,
+                                                          (const float4*)O.surf_f.p, O.ne, O.npad, kappa, W.chk.p);
+    else
+        k_p2check<T, YUK, DL, 2><<<nbox, 256, 0, st>>>(nbox, boxes, mode, Tr->center.p, Tr->sb.p, Tr->se.p, Tr->X.p,
+                                                       Tr->X_n.p, W.sq.p, W.sm.p, (const float4*)O.surf_f.p, O.ne,
+                                                       O.npad, kappa, W.chk.p);
     PB_CHECK_LAUNCH();
+}
+
+template <int NPAD>
+static void launch_df(cudaStream_t st, int ncols, const int* cols, int base, const float* hi, const float* lo,
+                      const float* X, float* Y) {
+    k_check2equiv_df<NPAD><<<div_up(ncols, kTC), 256, 0, st>>>(ncols, cols, base, hi, lo, X, Y);
+    PB_CHECK_LAUNCH();
+}
+
+// Y[col] = (hi + lo) X[col] for ncols boxes (double-float accumulation)
+static void check2equiv_df(int npad, cudaStream_t st, int ncols, const int* cols, int base, const float* hi,
+                           const float* lo, const float* X, float* Y) {
+    if (ncols <= 0) return;
+    switch (npad) {
+        case 32: launch_df<32>(st, ncols, cols, base, hi, lo, X, Y); break;
+        case 64: launch_df<64>(st, ncols, cols, base, hi, lo, X, Y); break;
+        case 128: launch_df<128>(st, ncols, cols, base, hi, lo, X, Y); break;
+        case 160: launch_df<160>(st, ncols, cols, base, hi, lo, X, Y); break;
+        case 224: launch_df<224>(st, ncols, cols, base, hi, lo, X, Y); break;
+        case 320: launch_df<320>(st, ncols, cols, base, hi, lo, X, Y); break;
+        case 416: launch_df<416>(st, ncols, cols, base, hi, lo, X, Y); break;
+        case 512: launch_df<512>(st, ncols, cols, base, hi, lo, X, Y); break;
+        default: throw Error(PB_EINVAL, "unsupported expansion order");
+    }
+}
+
+// the two check -> equivalent conversions: FP64 for the FP64 path,
+// double-float for the FP32 path
+template <typename T>
+static void check2equiv(const Operators& O, int level, bool up, cudaStream_t st, GemmArgs ga, int ncols,
+                        const int* cols, const T* X, T* Y);
+template <>
+void check2equiv<float>(const Operators& O, int level, bool up, cudaStream_t st, GemmArgs, int ncols,
+                        const int* cols, const float* X, float* Y) {
+    const size_t m2 = (size_t)O.npad * O.npad;
+    const float* hi = (up ? O.uc2ue_hi.p : O.dc2de_hi.p) + level * m2;
+    const float* lo = (up ? O.uc2ue_lo.p : O.dc2de_lo.p) + level * m2;
+    check2equiv_df(O.npad, st, ncols, cols, 0, hi, lo, X, Y);
+}
+template <>
+void check2equiv<double>(const Operators& O, int level, bool up, cudaStream_t st, GemmArgs ga, int ncols,
+                         const int* cols, const double* X, double* Y) {
+    ga.mode = G_DENSE; ga.ncols = ncols; ga.cols = cols; ga.col_base = 0; ga.level = level; ga.accumulate = 0;
+    gemm_dispatch<double, double>(O.npad, st, div_up(ncols, kTC), ga, up ? O.uc2ue_d.p : O.dc2de_d.p, X, Y);
 }
 
 template <typename T, bool YUK, bool DL, bool DN>
@@ -491,8 +627,6 @@ static void apply_t(fmm_tree* Tr, const Operators& O, double kappa_d, const In* 
         k_gather_tn<T, In><<<div_up(nt, 256), 256, 0, st>>>(nt, pt, tgt_n, W.tn.p);
         PB_CHECK_LAUNCH();
     }
-    const double* uc2ue = O.uc2ue_d.p;      // FP64 always (ill-conditioned solves)
-    const double* dc2de = O.dc2de_d.p;
     const T* m2m = opsel<T>(O, O.m2m, O.m2m_d);
     const T* l2l = opsel<T>(O, O.l2l, O.l2l_d);
     const T* m2l = opsel<T>(O, O.m2l, O.m2l_d);
@@ -509,9 +643,7 @@ static void apply_t(fmm_tree* Tr, const Operators& O, double kappa_d, const In* 
     for (int l = 0; l < Tr->nlev; ++l) {
         int a0 = Tr->sleaf_lvl_off[l], a1 = Tr->sleaf_lvl_off[l + 1];
         if (a1 <= a0) continue;
-        ga.mode = G_DENSE; ga.ncols = a1 - a0; ga.cols = Tr->sleaf_ids.p + a0; ga.col_base = 0;
-        ga.level = l; ga.accumulate = 0;
-        gemm_dispatch<T, double>(npad, st, div_up(a1 - a0, kTC), ga, uc2ue, W.chk.p, W.Qu.p);
+        check2equiv<T>(O, l, true, st, ga, a1 - a0, Tr->sleaf_ids.p + a0, W.chk.p, W.Qu.p);
     }
     ph.reset(); ph = std::make_unique<PhaseTimer>(ctx, PB_PH_M2M);
     // M2M, post-order: parents at level l from children at level l + 1
@@ -530,9 +662,7 @@ static void apply_t(fmm_tree* Tr, const Operators& O, double kappa_d, const In* 
         for (int l = 0; l < Tr->nlev; ++l) {
             int a0 = Tr->xbox_lvl_off[l], a1 = Tr->xbox_lvl_off[l + 1];
             if (a1 <= a0) continue;
-            ga.mode = G_DENSE; ga.ncols = a1 - a0; ga.cols = Tr->xbox_ids.p + a0; ga.col_base = 0;
-            ga.level = l; ga.accumulate = 0;
-            gemm_dispatch<T, double>(npad, st, div_up(a1 - a0, kTC), ga, dc2de, W.chk.p, W.Qd.p);
+            check2equiv<T>(O, l, false, st, ga, a1 - a0, Tr->xbox_ids.p + a0, W.chk.p, W.Qd.p);
         }
     }
     // M2L (V list) with DC2DE folded into the operators: accumulate into Qd

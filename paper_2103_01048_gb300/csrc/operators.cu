@@ -108,6 +108,16 @@ __global__ void k_matmul(int n, const double* __restrict__ A, const double* __re
     C[idx] = s;
 }
 
+__global__ void k_split_pair(long long n, const double* __restrict__ src, float* __restrict__ hi,
+                             float* __restrict__ lo) {
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double v = src[i];
+    float h = (float)v;
+    hi[i] = h;
+    lo[i] = (float)(v - (double)h);
+}
+
 __global__ void k_store_padded(int n, int npad, const double* __restrict__ src, float* __restrict__ dst_f,
                                double* __restrict__ dst_d) {
     int idx = blockIdx.x * blockDim.x + threadIdx.x;
@@ -239,6 +249,11 @@ std::shared_ptr<Operators> get_operators(fmm_tree* T, int kernel, double kappa, 
         }
         PB_CHECK_LAUNCH();
     }
+    O->uc2ue_hi.alloc(L * m2, st); O->uc2ue_lo.alloc(L * m2, st);
+    O->dc2de_hi.alloc(L * m2, st); O->dc2de_lo.alloc(L * m2, st);
+    k_split_pair<<<div_up(L * m2, 256), 256, 0, st>>>(L * m2, O->uc2ue_d.p, O->uc2ue_hi.p, O->uc2ue_lo.p);
+    k_split_pair<<<div_up(L * m2, 256), 256, 0, st>>>(L * m2, O->dc2de_d.p, O->dc2de_hi.p, O->dc2de_lo.p);
+    PB_CHECK_LAUNCH();
     pack_m2l_tc(*O, st);
     PB_CUDA(cudaStreamSynchronize(st));
     T->ops[key] = O;
