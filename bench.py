@@ -50,6 +50,7 @@ def parse():
     ap.add_argument("--p", type=int, default=P_ORDER)
     ap.add_argument("--ncrit", type=int, default=NCRIT)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-solve", action="store_true")
     return ap.parse_args()
 
 
@@ -275,6 +276,35 @@ def main():
     launches = prof["launches"]
 
     clocks = clk.summary()
+
+    # PB solve ms per mesh, mixed vs all-FP64 GPU path: the Born ion
+    # (5,120-triangle icosphere of radius 2 A, +1e at the centre, P0,
+    # 3-point rule, GMRES tol 1e-6), setup excluded (as the paper's
+    # assembly/solve split)
+    solve = None
+    if rank == 0 and not args.no_solve:
+        import synthetic as syn
+        V, F = syn.icosphere(4, 2.0)
+        atoms, qa = np.zeros((1, 3)), np.array([1.0])
+        solve = {"workload": "Born ion r=2 A, 5120 triangles, 3-pt rule, P0, tol 1e-6, eps 4/80, kappa 0.125"}
+        for name, prec, p in [("mixed", pb.PB_MIXED, 6), ("fp64", pb.PB_FP64, 8)]:
+            mesh = pb.pb_mesh_setup(ctx, V, F.astype(np.int32), 3, p, 128)
+            res, st = pb.pb_solve(ctx, mesh, atoms, qa, 4.0, 80.0, 0.125, 1e-6, 300, precision=prec)
+            pb.pb_result_destroy(res)
+            ts = []
+            for _ in range(3):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                res, st = pb.pb_solve(ctx, mesh, atoms, qa, 4.0, 80.0, 0.125, 1e-6, 300, precision=prec)
+                e = pb.pb_solvation_energy(ctx, res)
+                ts.append((time.perf_counter() - t0) * 1e3)
+                it, rr, _ = pb.pb_result_get(res)
+                pb.pb_result_destroy(res)
+            pb.pb_mesh_destroy(mesh)
+            solve[name] = {"ms_per_mesh": float(np.median(ts)), "iterations": it, "dG_kcal_mol": e, "p": p}
+        solve["mixed_vs_fp64_rel_dG"] = abs(solve["mixed"]["dG_kcal_mol"] - solve["fp64"]["dG_kcal_mol"]) / abs(
+            solve["fp64"]["dG_kcal_mol"])
+        solve["speedup_mixed_over_fp64"] = solve["fp64"]["ms_per_mesh"] / solve["mixed"]["ms_per_mesh"]
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -285,11 +315,13 @@ def main():
                            "parallelism": "replicas" if world > 1 else "single GPU",
                            "l2": "flushed between steps (256 MB write)",
                            "tree": {"boxes": info.n_box, "leaves": info.n_leaf, "levels": info.n_levels,
-                                    "v_pairs": info.n_v, "p2p_pairs": info.p2p_pairs}},
+                                    "v_pairs": info.n_v, "p2p_pairs": info.p2p_pairs,
+                                    "m2p_targets": info.m2p_targets, "p2l_sources": info.p2l_sources,
+                                    "l2p_targets": info.l2p_targets}},
                 "roofline": roof, "cpu_baseline": cpu,
                 "e2e": {"value": world * 2 * args.n / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                         "d2h_bytes_per_step": d2h},
-                "gpu_launches": int(launches), "clocks": clocks,
+                "gpu_launches": int(launches), "clocks": clocks, "pb_solve": solve,
                 "phases_ms_per_step": {k: v[0] / args.steps for k, v in phases.items()}}
         print(json.dumps(line), flush=True)
     pb.fmm_tree_destroy(tree)
