@@ -287,8 +287,8 @@ def main():
         V, F = syn.icosphere(4, 2.0)
         atoms, qa = np.zeros((1, 3)), np.array([1.0])
         solve = {"workload": "Born ion r=2 A, 5120 triangles, 3-pt rule, P0, tol 1e-6, eps 4/80, kappa 0.125"}
-        for name, prec, p in [("mixed", pb.PB_MIXED, 6), ("fp64", pb.PB_FP64, 8)]:
-            mesh = pb.pb_mesh_setup(ctx, V, F.astype(np.int32), 3, p, 128)
+        for name, prec, p_s in [("mixed", pb.PB_MIXED, 6), ("fp64", pb.PB_FP64, 8)]:
+            mesh = pb.pb_mesh_setup(ctx, V, F.astype(np.int32), 3, p_s, 128)
             res, st = pb.pb_solve(ctx, mesh, atoms, qa, 4.0, 80.0, 0.125, 1e-6, 300, precision=prec)
             pb.pb_result_destroy(res)
             ts = []
@@ -301,7 +301,7 @@ def main():
                 it, rr, _ = pb.pb_result_get(res)
                 pb.pb_result_destroy(res)
             pb.pb_mesh_destroy(mesh)
-            solve[name] = {"ms_per_mesh": float(np.median(ts)), "iterations": it, "dG_kcal_mol": e, "p": p}
+            solve[name] = {"ms_per_mesh": float(np.median(ts)), "iterations": it, "dG_kcal_mol": e, "p": p_s}
         solve["mixed_vs_fp64_rel_dG"] = abs(solve["mixed"]["dG_kcal_mol"] - solve["fp64"]["dG_kcal_mol"]) / abs(
             solve["fp64"]["dG_kcal_mol"])
         solve["speedup_mixed_over_fp64"] = solve["fp64"]["ms_per_mesh"] / solve["mixed"]["ms_per_mesh"]
