@@ -255,6 +255,17 @@ int pb_result_get(const pb_result* res, int* iterations, double* residual, doubl
  * phi_reac (HOST, double [na]) may be NULL.  Synchronous. */
 int pb_solvation_energy(pb_ctx* ctx, pb_result* res, double* dG_kcal_per_mol, double* phi_reac);
 
+/* Gradient of the polar solvation energy of a solved system (kcal/mol per e
+ * and per A) with respect to the atomic charges and positions, by one
+ * adjoint GMRES solve with A^T (the transposed double layer is the adjoint
+ * double layer K', Eq. adj_hyp) in the precision of `res`, to relative
+ * residual tol (max_iter 1..2000).  The surface mesh is held fixed.
+ *   dEdq  HOST double [na]        dE/dq_k
+ *   dEdx  HOST double [na][3]     dE/dr_k
+ * Either may be NULL.  Returns PB_OK or PB_ENOCONV (gradients from the last
+ * adjoint iterate).  Synchronous. */
+int pb_energy_grad(pb_ctx* ctx, pb_result* res, double tol, int max_iter, double* dEdq, double* dEdx);
+
 /* Same result as pb_solvation_energy, without allocating device memory.
  * No counterpart in the paper: it exists for callers that cannot allocate
  * at this point (for example while a CUDA graph is being captured, or with

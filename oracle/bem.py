@@ -137,3 +137,50 @@ def solve_energy(verts, tris, nq, atoms, charges, eps_in, eps_out, kappa, mats=N
     phi, dphi, mats = solve_direct(verts, tris, nq, atoms, charges, eps_in, eps_out, kappa, mats)
     pr = phi_reac(verts, tris, nq, phi, dphi, atoms)
     return solvation_energy(charges, pr), phi, dphi, mats
+
+
+def charge_response(verts, tris, nq, atoms, eps_in, eps_out, kappa, mats):
+    """Matrix R with phi_reac(r_k) = sum_l R_kl q_l (Eq. phi_reac after
+    Eq. direct), built column by column from its definition
+    R = E A^{-1} B: B maps charges to the right-hand side, E maps the surface
+    solution to the reaction potential at the atoms."""
+    atoms = np.asarray(atoms, dtype=np.float64).reshape(-1, 3)
+    na = len(atoms)
+    nt = len(tris)
+    P, w, nrm, tri = quad_points(verts, tris, nq)
+    _, area = geometry(verts, tris)
+    A = direct_matrix(mats, area, eps_in, eps_out)
+    B = np.zeros((2 * nt, na))
+    E = np.zeros((na, 2 * nt))
+    for k in range(na):
+        d = P - atoms[k]
+        r = np.linalg.norm(d, axis=1)
+        g = 1.0 / (4 * np.pi * r)
+        np.add.at(B[:nt, k], tri, w * g / eps_in)
+        # dg/dn_y at y = x_b for target r_k: (r_k - x_b).n_b / (4 pi r^3)
+        dgdn = ((atoms[k] - P) * nrm).sum(axis=1) / (4 * np.pi * r ** 3)
+        np.add.at(E[k, :nt], tri, -w * dgdn)
+        np.add.at(E[k, nt:], tri, w * g)
+    return E @ np.linalg.solve(A, B)
+
+
+def energy_grad_q(verts, tris, nq, atoms, charges, eps_in, eps_out, kappa, mats):
+    """dE/dq = 1/2 (R + R^T) q in kcal/mol/e (E = 1/2 q^T R q * 4 pi C)."""
+    R = charge_response(verts, tris, nq, atoms, eps_in, eps_out, kappa, mats)
+    q = np.asarray(charges, dtype=np.float64)
+    return 0.5 * (R + R.T) @ q * 4.0 * np.pi * KCAL
+
+
+def energy_grad_x_fd(verts, tris, nq, atoms, charges, eps_in, eps_out, kappa, mats, h=1e-4, idx=None):
+    """dE/dr_k by central finite differences of the dense-LU energy, the
+    surface held fixed; idx selects (atom, axis) components (default all)."""
+    atoms = np.asarray(atoms, dtype=np.float64).reshape(-1, 3)
+    comps = idx if idx is not None else [(k, c) for k in range(len(atoms)) for c in range(3)]
+    out = {}
+    for k, c in comps:
+        ap = atoms.copy(); ap[k, c] += h
+        am = atoms.copy(); am[k, c] -= h
+        ep, *_ = solve_energy(verts, tris, nq, ap, charges, eps_in, eps_out, kappa, mats=mats)
+        em, *_ = solve_energy(verts, tris, nq, am, charges, eps_in, eps_out, kappa, mats=mats)
+        out[(k, c)] = (ep - em) / (2 * h)
+    return out

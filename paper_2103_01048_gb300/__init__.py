@@ -76,6 +76,7 @@ _sig("pb_result_destroy", [_P])
 _sig("pb_result_get", [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(_D), _P])
 _sig("pb_solvation_energy", [_P, _P, ctypes.POINTER(_D), _P])
 _sig("pb_solvation_energy_noalloc", [_P, _P, _P])
+_sig("pb_energy_grad", [_P, _P, _D, ctypes.c_int, _P, _P])
 
 
 class PBError(RuntimeError):
@@ -94,7 +95,7 @@ def exported_symbols():
             "fmm_tree_info", "fmm_tree_export_points", "fmm_tree_export_boxes", "fmm_tree_export_list",
             "fmm_apply", "pb_mesh_setup", "pb_mesh_destroy", "pb_mesh_info", "pb_mesh_export_singular",
             "pb_mesh_matvec", "pb_solve", "pb_result_destroy", "pb_result_get", "pb_solvation_energy",
-            "pb_solvation_energy_noalloc"]
+            "pb_solvation_energy_noalloc", "pb_energy_grad"]
 
 
 def ptr(x):
@@ -278,6 +279,16 @@ def pb_solvation_energy_noalloc(ctx, res, dG_device):
     """Energy into a caller-owned device double (e.g. a 1-element float64
     CUDA tensor) without device allocation; asynchronous on the context stream."""
     _check(_lib.pb_solvation_energy_noalloc(ctx, res, ptr(dG_device)), ctx)
+
+
+def pb_energy_grad(ctx, res, na, tol=1e-8, max_iter=500):
+    """(dE/dq [na], dE/dx [na,3]) in kcal/mol/e and kcal/mol/A; raises on failure."""
+    gq = np.zeros(na)
+    gx = np.zeros((na, 3))
+    rc = _lib.pb_energy_grad(ctx, res, float(tol), int(max_iter), ptr(gq), ptr(gx))
+    if rc not in (PB_OK, PB_ENOCONV):
+        _check(rc, ctx)
+    return gq, gx, rc
 
 
 # internal self-test hook of the tensor-core M2L kernel (not part of the ABI)

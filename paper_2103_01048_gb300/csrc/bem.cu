@@ -16,6 +16,7 @@
 #include <cub/cub.cuh>
 #include <algorithm>
 #include <cmath>
+#include <functional>
 
 namespace pbfmm {
 
@@ -764,8 +765,10 @@ static T read_scalar(const T* d, cudaStream_t st) {
     return h;
 }
 
-// Full GMRES (x0 = 0, left preconditioned, CGS2), FP64.
-static int gmres(pb_mesh* M, pb_result* R, const double* b, double tol, int max_iter) {
+// Full GMRES (x0 = 0, left preconditioned, CGS2), FP64.  `matvec(v, w)`
+// writes w = P^{-1} A v for device vectors of length 2 nt.
+int gmres(pb_mesh* M, const std::function<void(const double*, double*)>& matvec, const double* b,
+          DBuf<double>& x, double tol, int max_iter, int* iterations, double* residual) {
     cudaStream_t st = M->ctx->stream;
     const long long n = 2 * M->nt;
     const int kmax = std::max(1, max_iter);
@@ -779,8 +782,8 @@ static int gmres(pb_mesh* M, pb_result* R, const double* b, double tol, int max_
     cs.alloc(kmax + 1, st); sn.alloc(kmax + 1, st); g.alloc(kmax + 2, st);
     nrm2.alloc(1, st); resid.alloc(1, st); yv.alloc(kmax + 1, st);
     g.zero(st);
-    R->x.alloc(n, st);
-    R->x.zero(st);
+    x.alloc(n, st);
+    x.zero(st);
     const int nb = std::min<long long>(kDotBlocks, (n + 255) / 256);
     auto dots = [&](const double* Vb, int nk, const double* vec, double* out, int acc) {
         k_dots<<<nb, 256, 0, st>>>(n, Vb, n, nk, vec, partial.p, kmax + 1);
@@ -792,7 +795,7 @@ static int gmres(pb_mesh* M, pb_result* R, const double* b, double tol, int max_
     // r0 = P^{-1} b (b is already preconditioned), beta = ||r0||
     dots(b, 1, b, nrm2.p, 0);
     double beta = std::sqrt(read_scalar(nrm2.p, st));
-    if (beta == 0.0) { R->iterations = 0; R->residual = 0.0; return PB_OK; }
+    if (beta == 0.0) { *iterations = 0; *residual = 0.0; return PB_OK; }
     k_scale<<<ub, 256, 0, st>>>(n, b, nrm2.p, V.p);
     k_set_g0<<<1, 1, 0, st>>>(nrm2.p, g.p);
     PB_CHECK_LAUNCH();
@@ -800,7 +803,7 @@ static int gmres(pb_mesh* M, pb_result* R, const double* b, double tol, int max_
     double rel = 1.0;
     int status = PB_ENOCONV;
     for (j = 0; j < kmax; ++j) {
-        mesh_matvec(M, R->eps_in, R->eps_out, R->kappa, R->precision, V.p + (long long)j * n, w.p, 1);
+        matvec(V.p + (long long)j * n, w.p);
         PhaseTimer ph(M->ctx, PB_PH_GMRES);
         // CGS2: two passes of classical Gram-Schmidt
         dots(V.p, j + 1, w.p, h.p, 0);
@@ -821,11 +824,11 @@ static int gmres(pb_mesh* M, pb_result* R, const double* b, double tol, int max_
     }
     int m = std::min(j, kmax);
     k_backsolve<<<1, 1, 0, st>>>(m, kmax, H.p, g.p, yv.p);
-    k_axpy_basis<<<ub, 256, m * sizeof(double), st>>>(n, V.p, n, m, yv.p, R->x.p);
+    k_axpy_basis<<<ub, 256, m * sizeof(double), st>>>(n, V.p, n, m, yv.p, x.p);
     PB_CHECK_LAUNCH();
     PB_CUDA(cudaStreamSynchronize(st));
-    R->iterations = m;
-    R->residual = rel;
+    *iterations = m;
+    *residual = rel;
     return status;
 }
 
@@ -846,8 +849,10 @@ int solve(pb_mesh* M, pb_result* R, double tol, int max_iter) {
                                                M->area.p, R->eps_in / R->eps_out, 1, b.p);
         PB_CHECK_LAUNCH();
     }
-    // The FP64 path needs the FP64 operators: gmres -> mesh_matvec selects them
-    int status = gmres(M, R, b.p, tol, max_iter);
+    auto mv = [&](const double* v, double* w) {
+        mesh_matvec(M, R->eps_in, R->eps_out, R->kappa, R->precision, v, w, 1);
+    };
+    int status = gmres(M, mv, b.p, R->x, tol, max_iter, &R->iterations, &R->residual);
     R->status = status;
     return status;
 }

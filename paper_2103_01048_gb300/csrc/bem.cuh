@@ -2,6 +2,7 @@
 // Bempp", Eq. bempp_fmm_matvec, Eq. direct).
 #pragma once
 #include "fmm.cuh"
+#include <functional>
 
 struct pb_mesh {
     pb_ctx* ctx = nullptr;
@@ -22,8 +23,19 @@ struct pb_mesh {
     pbfmm::DBuf<double> S_d;
     pbfmm::DBuf<float> S_f;
     double kappa_S = -1.0;
+    pbfmm::DBuf<int> adj_tr;          // for CSR entry (i, j): the index of entry (j, i)
     fmm_tree* tree = nullptr;
 };
+
+namespace pbfmm {
+int gmres(pb_mesh* M, const std::function<void(const double*, double*)>& matvec, const double* b, DBuf<double>& x,
+          double tol, int max_iter, int* iterations, double* residual);
+void ensure_singular_public(pb_mesh* M, double kappa);
+void mesh_matvec(pb_mesh* M, double eps_in, double eps_out, double kappa, int precision, const double* x, double* y,
+                 int precond);
+void fmm_apply_impl(fmm_tree* Tr, int kernel, double kappa, int p, int precision, const void* q, const void* dip,
+                    const void* src_n, const void* tgt_n, void* out, void* out_dn);
+}  // namespace pbfmm
 
 struct pb_result {
     pb_mesh* mesh = nullptr;
@@ -37,4 +49,8 @@ struct pb_result {
     pbfmm::DBuf<double> atoms, charges;
     double energy = 0.0;
     bool have_energy = false;
+    // adjoint solve (gradients)
+    pbfmm::DBuf<double> lambda;       // [2 nt]
+    int adj_iterations = 0;
+    double adj_residual = 0.0;
 };

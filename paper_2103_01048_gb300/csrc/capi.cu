@@ -13,6 +13,7 @@ void mesh_matvec(pb_mesh* M, double eps_in, double eps_out, double kappa, int pr
 int solve(pb_mesh* M, pb_result* R, double tol, int max_iter);
 void reaction_energy(pb_result* R, double* phir_host, double* dG);
 void ensure_singular_public(pb_mesh* M, double kappa);
+int energy_gradient(pb_result* R, double tol, int max_iter, double* dEdq_host, double* dEdx_host);
 
 thread_local long long g_launch_count = 0;
 
@@ -490,6 +491,21 @@ int pb_solvation_energy(pb_ctx* ctx, pb_result* R, double* dG, double* phir) {
     reaction_energy(R, phir, dG);
     R->energy = *dG;
     R->have_energy = true;
+    PB_API_END(ctx)
+}
+
+int pb_energy_grad(pb_ctx* ctx, pb_result* R, double tol, int max_iter, double* dEdq, double* dEdx) {
+    if (!ctx || !R) return PB_EINVAL;
+    int status = PB_OK;
+    PB_API_BEGIN
+    PB_REQUIRE(tol >= 0 && max_iter >= 1 && max_iter <= 2000, PB_EINVAL, "pb_energy_grad: bad tol or max_iter");
+    PB_CUDA(cudaSetDevice(ctx->device));
+    status = energy_gradient(R, tol, max_iter, dEdq, dEdx);
+    check_device_error(ctx);
+    if (status != PB_OK) {
+        ctx->last_error = "pb_energy_grad: adjoint GMRES did not reach tol within max_iter";
+        return status;
+    }
     PB_API_END(ctx)
 }
 
