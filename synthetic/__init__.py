@@ -143,3 +143,118 @@ def fcc_ball_atoms(natoms: int, ball_radius: float, nn_dist: float,
     q = rng.uniform(-qmax, qmax, natoms)
     q -= q.mean()
     return xyz, radii, q
+
+
+def gaussian_surface(xyz, radii, spacing, level=1.0, cutoff=3.0, pad=None):
+    """Closed triangulation of the isosurface F(x) = level of the Gaussian
+    density F(x) = sum_k exp(-(|x - r_k|^2 / R_k^2 - 1)), terms cut off beyond
+    cutoff * R_k, by marching tetrahedra on a regular grid of the given
+    spacing (each cube split into six tetrahedra around its main diagonal, so
+    neighbouring cubes share faces and the surface is watertight).  Grid
+    values within 1e-6 of `level` are nudged off it so that no vertex sits on
+    a grid node.  Triangles are oriented with normals pointing to lower F
+    (out of the molecule).  Returns (verts float64 [nv,3], tris int32 [nt,3]).
+    """
+    xyz = np.asarray(xyz, dtype=np.float64)
+    radii = np.asarray(radii, dtype=np.float64)
+    if pad is None:
+        pad = 2.0 * radii.max() + 2 * spacing
+    lo = xyz.min(axis=0) - pad
+    hi = xyz.max(axis=0) + pad
+    n = np.ceil((hi - lo) / spacing).astype(int) + 1
+    gx = [lo[a] + spacing * np.arange(n[a]) for a in range(3)]
+    F = np.zeros(tuple(n))
+    for k in range(len(xyz)):
+        rc = cutoff * radii[k]
+        sl = []
+        for a in range(3):
+            i0 = max(0, int(np.floor((xyz[k, a] - rc - lo[a]) / spacing)))
+            i1 = min(n[a], int(np.ceil((xyz[k, a] + rc - lo[a]) / spacing)) + 1)
+            sl.append(slice(i0, i1))
+        X, Y, Z = np.meshgrid(gx[0][sl[0]], gx[1][sl[1]], gx[2][sl[2]], indexing="ij")
+        d2 = (X - xyz[k, 0]) ** 2 + (Y - xyz[k, 1]) ** 2 + (Z - xyz[k, 2]) ** 2
+        term = np.exp(-(d2 / radii[k] ** 2 - 1.0))
+        term[d2 > rc * rc] = 0.0
+        F[sl[0], sl[1], sl[2]] += term
+    G = F - level
+    G[np.abs(G) < 1e-6] = 1e-6
+    inside = G > 0
+    # six tetrahedra of the unit cube sharing the diagonal (0,0,0)-(1,1,1)
+    corners = np.array([[0, 0, 0], [1, 0, 0], [0, 1, 0], [1, 1, 0],
+                        [0, 0, 1], [1, 0, 1], [0, 1, 1], [1, 1, 1]])
+    tets = [(0, 1, 3, 7), (0, 3, 2, 7), (0, 2, 6, 7), (0, 6, 4, 7), (0, 4, 5, 7), (0, 5, 1, 7)]
+    ci = np.stack(np.meshgrid(np.arange(n[0] - 1), np.arange(n[1] - 1), np.arange(n[2] - 1),
+                              indexing="ij"), axis=-1).reshape(-1, 3)
+    # keep cubes crossed by the surface
+    cin = np.stack([inside[ci[:, 0] + c[0], ci[:, 1] + c[1], ci[:, 2] + c[2]] for c in corners], axis=1)
+    cross = cin.any(axis=1) & ~cin.all(axis=1)
+    ci = ci[cross]
+    stride = np.array([n[1] * n[2], n[2], 1])
+    vert_of_edge = {}
+    verts = []
+    tris = []
+
+    def edge_vertex(a, b):
+        key = (a, b) if a < b else (b, a)
+        v = vert_of_edge.get(key)
+        if v is None:
+            ia = np.array(np.unravel_index(a, n))
+            ib = np.array(np.unravel_index(b, n))
+            ga, gb = G[tuple(ia)], G[tuple(ib)]
+            # linear interpolation, kept off the grid nodes (no sliver triangles)
+            t = min(0.98, max(0.02, ga / (ga - gb)))
+            p = lo + spacing * (ia + t * (ib - ia))
+            v = len(verts)
+            verts.append(p)
+            vert_of_edge[key] = v
+        return v
+
+    flat = G.ravel()
+    for c in ci:
+        base = c @ stride
+        ids = [base + corners[m] @ stride for m in range(8)]
+        for tet in tets:
+            node = [ids[m] for m in tet]
+            ins = [flat[v] > 0 for v in node]
+            m = sum(ins)
+            if m == 0 or m == 4:
+                continue
+            I = [v for v, s in zip(node, ins) if s]
+            O = [v for v, s in zip(node, ins) if not s]
+            if m == 1:
+                faces = [(edge_vertex(I[0], O[0]), edge_vertex(I[0], O[1]), edge_vertex(I[0], O[2]))]
+                ref = [(I[0], O[0])]
+            elif m == 3:
+                faces = [(edge_vertex(O[0], I[0]), edge_vertex(O[0], I[1]), edge_vertex(O[0], I[2]))]
+                ref = [(I[0], O[0])]
+            else:
+                a, b = edge_vertex(I[0], O[0]), edge_vertex(I[0], O[1])
+                c2, d = edge_vertex(I[1], O[1]), edge_vertex(I[1], O[0])
+                faces = [(a, b, c2), (a, c2, d)]
+                ref = [(I[0], O[0])]
+            ia = np.array(np.unravel_index(ref[0][0], n), dtype=float)
+            io = np.array(np.unravel_index(ref[0][1], n), dtype=float)
+            outward = io - ia                      # from inside to outside
+            for f in faces:
+                p0, p1, p2 = verts[f[0]], verts[f[1]], verts[f[2]]
+                nr = np.cross(p1 - p0, p2 - p0)
+                tris.append(f if nr @ outward >= 0 else (f[0], f[2], f[1]))
+    V = np.array(verts)
+    T = np.array(tris, dtype=np.int32)
+    return V, T
+
+
+def synthetic_protein(natoms=2000, target_tris=80000, seed=3, ball_radius=20.0):
+    """Atoms (jittered FCC in a ball, radii U[1.2, 2.0], charges U[-0.8, 0.8]
+    with zero net charge) and their Gaussian surface with the grid spacing
+    tuned so the triangle count is within 10% of target_tris.  Returns
+    (verts, tris, xyz, radii, q, spacing)."""
+    xyz, radii, q = fcc_ball_atoms(natoms, ball_radius, 2.85, 0.1, seed=seed)
+    h = 0.7 * (80000.0 / target_tris) ** 0.5 * (ball_radius / 20.0)
+    for _ in range(6):
+        V, T = gaussian_surface(xyz, radii, h)
+        ratio = len(T) / target_tris
+        if 0.9 <= ratio <= 1.1:
+            break
+        h *= ratio ** 0.5
+    return V, T, xyz, radii, q, h
