@@ -255,6 +255,29 @@ int pb_result_get(const pb_result* res, int* iterations, double* residual, doubl
  * phi_reac (HOST, double [na]) may be NULL.  Synchronous. */
 int pb_solvation_energy(pb_ctx* ctx, pb_result* res, double* dG_kcal_per_mol, double* phi_reac);
 
+/* Solve several systems together (same eps_in, eps_out, kappa, tol,
+ * max_iter, precision; each its own mesh, charges and positions): the
+ * GMRES iterations run in lockstep, one CUDA stream per system, each
+ * system's preconditioned mat-vec captured once as a CUDA graph and replayed
+ * every iteration; one host synchronisation per iteration for all systems.
+ * meshes[nsys] must be distinct.  atoms[s] (double [na[s]][3]) and
+ * charges[s] (double [na[s]]) are host or device arrays.  out[nsys]
+ * receives one result per system (free each with pb_result_destroy),
+ * status[nsys] PB_OK or PB_ENOCONV per system.  Returns PB_OK if every system
+ * converged, else PB_ENOCONV.  Synchronous.  The results match pb_solve up to
+ * the FMM's run-dependent summation order. */
+int pb_solve_batch(pb_ctx* ctx, pb_mesh* const* meshes, int nsys, const double* const* atoms,
+                   const double* const* charges, const int64_t* na, double eps_in, double eps_out, double kappa,
+                   double tol, int max_iter, int precision, pb_result** out, int* status);
+
+/* Autotuner for the leaf size: for each candidate ncrit, build the octree of
+ * the points xyz (host or device, float [n][3]) and time one Laplace and one
+ * Yukawa single+double-layer FMM apply at order p (mean of 3 after a warm
+ * run, CUDA events); *best_ncrit receives the fastest candidate and *best_ms
+ * (may be NULL) its time.  Synchronous. */
+int pb_tune_ncrit(pb_ctx* ctx, const float* xyz, int64_t n, int p, const int32_t* candidates, int ncand,
+                  int* best_ncrit, double* best_ms);
+
 /* Gradient of the polar solvation energy of a solved system (kcal/mol per e
  * and per A) with respect to the atomic charges and positions, by one
  * adjoint GMRES solve with A^T (the transposed double layer is the adjoint

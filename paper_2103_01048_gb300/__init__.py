@@ -77,6 +77,9 @@ _sig("pb_result_get", [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(_D), _P]
 _sig("pb_solvation_energy", [_P, _P, ctypes.POINTER(_D), _P])
 _sig("pb_solvation_energy_noalloc", [_P, _P, _P])
 _sig("pb_energy_grad", [_P, _P, _D, ctypes.c_int, _P, _P])
+_sig("pb_solve_batch", [_P, _P, ctypes.c_int, _P, _P, _P, _D, _D, _D, _D, ctypes.c_int, ctypes.c_int, _P, _P])
+_sig("pb_tune_ncrit", [_P, _P, _I64, ctypes.c_int, _P, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                       ctypes.POINTER(_D)])
 
 
 class PBError(RuntimeError):
@@ -95,7 +98,7 @@ def exported_symbols():
             "fmm_tree_info", "fmm_tree_export_points", "fmm_tree_export_boxes", "fmm_tree_export_list",
             "fmm_apply", "pb_mesh_setup", "pb_mesh_destroy", "pb_mesh_info", "pb_mesh_export_singular",
             "pb_mesh_matvec", "pb_solve", "pb_result_destroy", "pb_result_get", "pb_solvation_energy",
-            "pb_solvation_energy_noalloc", "pb_energy_grad"]
+            "pb_solvation_energy_noalloc", "pb_energy_grad", "pb_solve_batch", "pb_tune_ncrit"]
 
 
 def ptr(x):
@@ -289,6 +292,36 @@ def pb_energy_grad(ctx, res, na, tol=1e-8, max_iter=500):
     if rc not in (PB_OK, PB_ENOCONV):
         _check(rc, ctx)
     return gq, gx, rc
+
+
+def pb_solve_batch(ctx, meshes, atoms_list, charges_list, eps_in, eps_out, kappa, tol, max_iter=500,
+                   precision=PB_MIXED):
+    """Solve len(meshes) systems together; returns (results, statuses, rc)."""
+    ns = len(meshes)
+    A = [np.ascontiguousarray(a, dtype=np.float64) for a in atoms_list]
+    Q = [np.ascontiguousarray(q, dtype=np.float64) for q in charges_list]
+    mesh_arr = (_P * ns)(*[m.value if isinstance(m, _P) else m for m in meshes])
+    a_arr = (_P * ns)(*[a.ctypes.data for a in A])
+    q_arr = (_P * ns)(*[q.ctypes.data for q in Q])
+    na = np.array([len(q) for q in Q], dtype=np.int64)
+    out = (_P * ns)()
+    st = np.zeros(ns, dtype=np.int32)
+    rc = _lib.pb_solve_batch(ctx, mesh_arr, ns, a_arr, q_arr, ptr(na), float(eps_in), float(eps_out),
+                             float(kappa), float(tol), int(max_iter), int(precision), out, ptr(st))
+    if rc not in (PB_OK, PB_ENOCONV):
+        _check(rc, ctx)
+    return [_P(out[i]) for i in range(ns)], st, rc
+
+
+def pb_tune_ncrit(ctx, xyz, p, candidates):
+    """(best ncrit, its ms) for one Laplace + one Yukawa SL+DL apply."""
+    cand = np.ascontiguousarray(candidates, dtype=np.int32)
+    best = ctypes.c_int()
+    ms = _D()
+    n = int(np.prod(xyz.shape)) // 3
+    _check(_lib.pb_tune_ncrit(ctx, ptr(xyz), n, int(p), ptr(cand), len(cand), ctypes.byref(best), ctypes.byref(ms)),
+           ctx)
+    return best.value, ms.value
 
 
 # internal self-test hook of the tensor-core M2L kernel (not part of the ABI)

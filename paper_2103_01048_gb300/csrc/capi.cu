@@ -14,6 +14,37 @@ int solve(pb_mesh* M, pb_result* R, double tol, int max_iter);
 void reaction_energy(pb_result* R, double* phir_host, double* dG);
 void ensure_singular_public(pb_mesh* M, double kappa);
 int energy_gradient(pb_result* R, double tol, int max_iter, double* dEdq_host, double* dEdx_host);
+void solve_batch(pb_ctx* ctx, pb_mesh* const* meshes, int nsys, pb_result** results, double tol, int max_iter,
+                 int* status);
+void tune_ncrit(pb_ctx* ctx, const float* xyz_dev, long long n, int p, const int* cand, int ncand, int* best,
+                double* best_ms);
+
+// A result object for the charges of one system (atoms as (x, y, z, q) on the device).
+pb_result* make_result(pb_ctx* ctx, pb_mesh* M, const double* atoms, const double* q, int64_t na, double eps_in,
+                       double eps_out, double kappa, int precision) {
+    auto* R = new pb_result();
+    R->mesh = M;
+    R->nt = M->nt;
+    R->na = na;
+    R->eps_in = eps_in;
+    R->eps_out = eps_out;
+    R->kappa = kappa;
+    R->precision = precision;
+    std::vector<double> a4(4 * na), ha(3 * na), hq(na);
+    cudaError_t e1 = cudaMemcpy(ha.data(), atoms, 3 * na * sizeof(double), cudaMemcpyDefault);
+    cudaError_t e2 = cudaMemcpy(hq.data(), q, na * sizeof(double), cudaMemcpyDefault);
+    if (e1 != cudaSuccess || e2 != cudaSuccess) {
+        delete R;
+        throw Error(PB_ECUDA, "copying atoms/charges failed");
+    }
+    for (int64_t k = 0; k < na; ++k) {
+        a4[4 * k] = ha[3 * k]; a4[4 * k + 1] = ha[3 * k + 1]; a4[4 * k + 2] = ha[3 * k + 2]; a4[4 * k + 3] = hq[k];
+    }
+    R->atoms.alloc(4 * na, ctx->stream);
+    PB_CUDA(cudaMemcpyAsync(R->atoms.p, a4.data(), 4 * na * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    PB_CUDA(cudaStreamSynchronize(ctx->stream));
+    return R;
+}
 
 thread_local long long g_launch_count = 0;
 
@@ -438,24 +469,8 @@ int pb_solve(pb_ctx* ctx, pb_mesh* M, const double* atoms, const double* q, int6
     PB_REQUIRE(precision == PB_MIXED || precision == PB_FP64, PB_EINVAL, "pb_solve: unknown precision");
     PB_CUDA(cudaSetDevice(ctx->device));
     cudaStream_t st = ctx->stream;
-    auto* R = new pb_result();
-    R->mesh = M;
-    R->nt = M->nt;
-    R->na = na;
-    R->eps_in = eps_in;
-    R->eps_out = eps_out;
-    R->kappa = kappa;
-    R->precision = precision;
-    // atoms as (x, y, z, q) double4 on the device
-    std::vector<double> a4(4 * na);
-    std::vector<double> ha(3 * na), hq(na);
-    PB_CUDA(cudaMemcpy(ha.data(), atoms, 3 * na * sizeof(double), cudaMemcpyDefault));
-    PB_CUDA(cudaMemcpy(hq.data(), q, na * sizeof(double), cudaMemcpyDefault));
-    for (int64_t k = 0; k < na; ++k) {
-        a4[4 * k] = ha[3 * k]; a4[4 * k + 1] = ha[3 * k + 1]; a4[4 * k + 2] = ha[3 * k + 2]; a4[4 * k + 3] = hq[k];
-    }
-    R->atoms.alloc(4 * na, st);
-    PB_CUDA(cudaMemcpyAsync(R->atoms.p, a4.data(), 4 * na * sizeof(double), cudaMemcpyHostToDevice, st));
+    (void)st;
+    pb_result* R = make_result(ctx, M, atoms, q, na, eps_in, eps_out, kappa, precision);
     *out = R;
     status = solve(M, R, tol, max_iter);
     check_device_error(ctx);
@@ -491,6 +506,49 @@ int pb_solvation_energy(pb_ctx* ctx, pb_result* R, double* dG, double* phir) {
     reaction_energy(R, phir, dG);
     R->energy = *dG;
     R->have_energy = true;
+    PB_API_END(ctx)
+}
+
+int pb_solve_batch(pb_ctx* ctx, pb_mesh* const* meshes, int nsys, const double* const* atoms,
+                   const double* const* charges, const int64_t* na, double eps_in, double eps_out, double kappa,
+                   double tol, int max_iter, int precision, pb_result** out, int* status) {
+    if (!ctx || !meshes || nsys < 1 || !atoms || !charges || !na || !out || !status) return PB_EINVAL;
+    for (int s = 0; s < nsys; ++s) out[s] = nullptr;
+    int rc = PB_OK;
+    PB_API_BEGIN
+    PB_REQUIRE(eps_in > 0 && eps_out > 0 && kappa > 0, PB_EINVAL, "pb_solve_batch: eps and kappa must be > 0");
+    PB_REQUIRE(tol >= 0 && max_iter >= 1 && max_iter <= 2000, PB_EINVAL, "pb_solve_batch: bad tol or max_iter");
+    PB_REQUIRE(precision == PB_MIXED || precision == PB_FP64, PB_EINVAL, "pb_solve_batch: unknown precision");
+    for (int s = 0; s < nsys; ++s) {
+        PB_REQUIRE(meshes[s] && atoms[s] && charges[s] && na[s] >= 1, PB_EINVAL, "pb_solve_batch: empty system");
+        for (int t = 0; t < s; ++t)
+            PB_REQUIRE(meshes[t] != meshes[s], PB_EINVAL, "pb_solve_batch: meshes must be distinct");
+    }
+    PB_CUDA(cudaSetDevice(ctx->device));
+    for (int s = 0; s < nsys; ++s)
+        out[s] = make_result(ctx, meshes[s], atoms[s], charges[s], na[s], eps_in, eps_out, kappa, precision);
+    solve_batch(ctx, meshes, nsys, out, tol, max_iter, status);
+    check_device_error(ctx);
+    for (int s = 0; s < nsys; ++s)
+        if (status[s] != PB_OK) rc = PB_ENOCONV;
+    if (rc != PB_OK) {
+        ctx->last_error = "pb_solve_batch: some systems did not reach tol within max_iter";
+        return rc;
+    }
+    PB_API_END(ctx)
+}
+
+int pb_tune_ncrit(pb_ctx* ctx, const float* xyz, int64_t n, int p, const int32_t* cand, int ncand, int* best,
+                  double* best_ms) {
+    if (!ctx || !xyz || n < 1 || !cand || ncand < 1 || !best) return PB_EINVAL;
+    PB_API_BEGIN
+    PB_REQUIRE(p >= 2 && p <= 10, PB_EINVAL, "pb_tune_ncrit: p must be in [2, 10]");
+    for (int c = 0; c < ncand; ++c) PB_REQUIRE(cand[c] >= 1, PB_EINVAL, "pb_tune_ncrit: ncrit must be >= 1");
+    PB_CUDA(cudaSetDevice(ctx->device));
+    Staged s;
+    s.in(xyz, (size_t)n * 3 * sizeof(float), ctx->stream);
+    tune_ncrit(ctx, (const float*)s.dev, n, p, cand, ncand, best, best_ms);
+    check_device_error(ctx);
     PB_API_END(ctx)
 }
 

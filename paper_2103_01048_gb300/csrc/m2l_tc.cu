@@ -389,7 +389,15 @@ static size_t tc_smem_bytes() {
 template <int NPAD>
 static void launch_tc(const fmm_tree* T, const Operators& O, const float* Qu, float* Qd, int* err, cudaStream_t st) {
     const size_t sm = tc_smem_bytes<NPAD>();
-    PB_CUDA(cudaFuncSetAttribute(k_m2l_tc<NPAD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    // opt in to the large shared-memory carve-out once per process and device
+    // (not a stream operation, so it stays out of captured graphs)
+    static bool attr_set[64] = {false};
+    int dev = 0;
+    PB_CUDA(cudaGetDevice(&dev));
+    if (dev >= 0 && dev < 64 && !attr_set[dev]) {
+        PB_CUDA(cudaFuncSetAttribute(k_m2l_tc<NPAD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        attr_set[dev] = true;
+    }
     dim3 grid(T->m2l_pairs.nitems, 2);
     k_m2l_tc<NPAD><<<grid, kTcRows, sm, st>>>(T->m2l_pairs.items.p, T->m2l_pairs.tgt.p, T->m2l_pairs.src.p,
                                               O.m2l_tc.p, Qu, Qd, err);

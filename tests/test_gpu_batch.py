@@ -1,0 +1,72 @@
+"""Batched solves (one stream and one captured mat-vec graph per system,
+lockstep GMRES) against one-at-a-time pb_solve, and the ncrit autotuner."""
+import numpy as np
+import pytest
+
+import synthetic
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+EPS = (4.0, 80.0, 0.125)
+
+
+@pytest.fixture(scope="module")
+def pb():
+    import paper_2103_01048_gb300 as pb
+    return pb
+
+
+def systems():
+    out = []
+    V, F = synthetic.icosphere(3, 2.0)
+    out.append((V, F, np.zeros((1, 3)), np.array([1.0])))
+    V, F = synthetic.icosphere(2, 3.0)
+    out.append((V, F, np.array([[0.5, 0.2, -0.3], [-0.7, 0.1, 0.4], [0.0, -0.8, 0.2]]), np.array([0.5, -0.6, 0.1])))
+    xyz, r, q = synthetic.fcc_ball_atoms(20, 4.0, 2.85, 0.1, seed=5)
+    V, F = synthetic.gaussian_surface(xyz, r, 0.45)
+    out.append((V, F, xyz, q))
+    V, F = synthetic.icosphere(4, 4.0)
+    out.append((V, F, np.array([[1.0, 1.0, 1.0]]), np.array([1.0])))
+    return out
+
+
+def test_batch_matches_single_solves(pb):
+    ctx = pb.pb_create(0, None)
+    sysl = systems()
+    meshes = [pb.pb_mesh_setup(ctx, V, F.astype(np.int32), 3, 6, 64) for V, F, _, _ in sysl]
+    try:
+        single = []
+        for m, (_, _, a, q) in zip(meshes, sysl):
+            res, st = pb.pb_solve(ctx, m, a, q, *EPS, 1e-7, 400)
+            assert st == pb.PB_OK
+            it, _, _ = pb.pb_result_get(res)
+            single.append((pb.pb_solvation_energy(ctx, res), it))
+            pb.pb_result_destroy(res)
+        for _ in range(2):   # twice: graphs are rebuilt per call
+            results, sts, rc = pb.pb_solve_batch(ctx, meshes, [s[2] for s in sysl], [s[3] for s in sysl],
+                                                 *EPS, 1e-7, 400)
+            assert rc == pb.PB_OK and np.all(sts == pb.PB_OK)
+            for res, (e_ref, it_ref) in zip(results, single):
+                e = pb.pb_solvation_energy(ctx, res)
+                it, rr, _ = pb.pb_result_get(res)
+                assert rr <= 1e-7
+                assert abs(it - it_ref) <= 2
+                assert abs(e - e_ref) <= 1e-5 * abs(e_ref)
+                pb.pb_result_destroy(res)
+        with pytest.raises(pb.PBError):
+            pb.pb_solve_batch(ctx, [meshes[0], meshes[0]], [sysl[0][2]] * 2, [sysl[0][3]] * 2, *EPS, 1e-7)
+    finally:
+        for m in meshes:
+            pb.pb_mesh_destroy(m)
+        pb.pb_destroy(ctx)
+
+
+def test_ncrit_autotuner(pb):
+    ctx = pb.pb_create(0, None)
+    try:
+        x, _ = synthetic.bumpy_sphere_points(200000, seed=1)
+        best, ms = pb.pb_tune_ncrit(ctx, torch.from_numpy(x).cuda(), 6, [32, 64, 128, 256])
+        assert best in (32, 64, 128, 256) and ms > 0
+    finally:
+        pb.pb_destroy(ctx)

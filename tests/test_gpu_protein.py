@@ -38,7 +38,7 @@ def test_protein_solve_and_gradients(pb, protein):
     m6 = pb.pb_mesh_setup(ctx, V, T.astype(np.int32), 3, 6, 128)
     m8 = pb.pb_mesh_setup(ctx, V, T.astype(np.int32), 3, 8, 128)
     try:
-        def energy(mesh, x, qq, tol=1e-9):
+        def energy(mesh, x, qq, tol=1e-8):
             res, st = pb.pb_solve(ctx, mesh, x, qq, *EPS, tol, 1000)
             assert st == pb.PB_OK
             e = pb.pb_solvation_energy(ctx, res)
@@ -53,11 +53,11 @@ def test_protein_solve_and_gradients(pb, protein):
         assert abs(e6 - e8) / abs(e8) < 1e-4
         # gradients at a tight tolerance
         e, res = energy(m6, xyz, q)
-        gq, gx, st = pb.pb_energy_grad(ctx, res, len(q), tol=1e-9, max_iter=1000)
+        gq, gx, st = pb.pb_energy_grad(ctx, res, len(q), tol=1e-8, max_iter=1000)
         pb.pb_result_destroy(res)
         assert st == pb.PB_OK and gq.shape == (2000,) and gx.shape == (2000, 3)
         rng = np.random.default_rng(7)
-        ks = rng.choice(len(q), 8, replace=False)
+        ks = rng.choice(len(q), 5, replace=False)
         hq = 0.05
         for k in ks:
             qp, qm = q.copy(), q.copy()
@@ -66,7 +66,7 @@ def test_protein_solve_and_gradients(pb, protein):
             fd = (energy(m6, xyz, qp)[0] - energy(m6, xyz, qm)[0]) / (2 * hq)
             assert abs(fd - gq[k]) < 1e-3 * np.abs(gq).max(), (k, fd, gq[k])
         hx = 1e-2
-        comps = [(int(k), int(c)) for k, c in zip(rng.choice(len(q), 8, replace=False), rng.integers(0, 3, 8))]
+        comps = [(int(k), int(c)) for k, c in zip(rng.choice(len(q), 5, replace=False), rng.integers(0, 3, 5))]
         for k, c in comps:
             xp, xm = xyz.copy(), xyz.copy()
             xp[k, c] += hx
