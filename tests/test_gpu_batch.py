@@ -23,7 +23,7 @@ def systems():
     out.append((V, F, np.zeros((1, 3)), np.array([1.0])))
     V, F = synthetic.icosphere(2, 3.0)
     out.append((V, F, np.array([[0.5, 0.2, -0.3], [-0.7, 0.1, 0.4], [0.0, -0.8, 0.2]]), np.array([0.5, -0.6, 0.1])))
-    xyz, r, q = synthetic.fcc_ball_atoms(20, 4.0, 2.85, 0.1, seed=5)
+    xyz, r, q = synthetic.fcc_ball_atoms(20, 5.5, 2.85, 0.1, seed=5)
     V, F = synthetic.gaussian_surface(xyz, r, 0.45)
     out.append((V, F, xyz, q))
     V, F = synthetic.icosphere(4, 4.0)
