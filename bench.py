@@ -305,6 +305,55 @@ def main():
         solve["mixed_vs_fp64_rel_dG"] = abs(solve["mixed"]["dG_kcal_mol"] - solve["fp64"]["dG_kcal_mol"]) / abs(
             solve["fp64"]["dG_kcal_mol"])
         solve["speedup_mixed_over_fp64"] = solve["fp64"]["ms_per_mesh"] / solve["mixed"]["ms_per_mesh"]
+
+    # batched binding energies: complexes -> (complex, receptor, ligand)
+    # meshes solved together by pb_solve_batch vs one at a time
+    batch = None
+    if rank == 0 and not args.no_solve:
+        import synthetic as syn
+        C = 332.0637
+        meshes, atoms_l, q_l, tags = [], [], [], []
+        ncx = 3
+        for c in range(ncx):
+            cx = syn.binding_complex(150 + 60 * c, 15 + 5 * c, seed=10 + c)
+            for k in ("cplx", "rec", "lig"):
+                V, T = cx["surf"][k]
+                meshes.append(pb.pb_mesh_setup(ctx, V, T.astype(np.int32), 3, 6, 64))
+                atoms_l.append(cx[k][0]); q_l.append(cx[k][2]); tags.append((c, k))
+            xr, xl = cx["rec"][0], cx["lig"][0]
+            r = np.linalg.norm(xr[:, None, :] - xl[None, :, :], axis=2)
+            tags.append(("coul", c, C * (cx["rec"][2][:, None] * cx["lig"][2][None, :] / (4.0 * r)).sum()))
+        ntri = [pb.pb_mesh_info(m)[0] for m in meshes]
+        # warm (operators, singular entries)
+        res_l, _, _ = pb.pb_solve_batch(ctx, meshes, atoms_l, q_l, 4.0, 80.0, 0.125, 1e-5, 500)
+        for r_ in res_l:
+            pb.pb_result_destroy(r_)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        res_l, sts, rc = pb.pb_solve_batch(ctx, meshes, atoms_l, q_l, 4.0, 80.0, 0.125, 1e-5, 500)
+        t_batch = (time.perf_counter() - t0) * 1e3
+        eb = [pb.pb_solvation_energy(ctx, r_) for r_ in res_l]
+        for r_ in res_l:
+            pb.pb_result_destroy(r_)
+        t0 = time.perf_counter()
+        es = []
+        for m, a_, q_ in zip(meshes, atoms_l, q_l):
+            r_, _ = pb.pb_solve(ctx, m, a_, q_, 4.0, 80.0, 0.125, 1e-5, 500)
+            es.append(pb.pb_solvation_energy(ctx, r_))
+            pb.pb_result_destroy(r_)
+        t_seq = (time.perf_counter() - t0) * 1e3
+        coul = {t[1]: t[2] for t in tags if t[0] == "coul"}
+        # Eq. bind: dG_bind = dG_complex - dG_receptor - dG_ligand - dG_coul
+        dgb = [eb[3 * c] - eb[3 * c + 1] - eb[3 * c + 2] - coul[c] for c in range(ncx)]
+        batch = {"workload": f"{ncx} synthetic complexes x (complex, receptor, ligand) = {len(meshes)} meshes, "
+                             f"{min(ntri)}-{max(ntri)} triangles, mixed, tol 1e-5",
+                 "batched_ms_per_mesh": t_batch / len(meshes), "sequential_ms_per_mesh": t_seq / len(meshes),
+                 "speedup": t_seq / t_batch,
+                 "max_rel_dG_batched_vs_sequential": float(max(abs(a - b) / abs(b) for a, b in zip(eb, es))),
+                 "dG_bind_kcal_mol": dgb,
+                 "dG_coul_eps_in_kcal_mol": [coul[c] for c in range(ncx)]}
+        for m in meshes:
+            pb.pb_mesh_destroy(m)
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
@@ -321,7 +370,7 @@ def main():
                 "roofline": roof, "cpu_baseline": cpu,
                 "e2e": {"value": world * 2 * args.n / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                         "d2h_bytes_per_step": d2h},
-                "gpu_launches": int(launches), "clocks": clocks, "pb_solve": solve,
+                "gpu_launches": int(launches), "clocks": clocks, "pb_solve": solve, "pb_solve_batch": batch,
                 "phases_ms_per_step": {k: v[0] / args.steps for k, v in phases.items()}}
         print(json.dumps(line), flush=True)
     pb.fmm_tree_destroy(tree)

@@ -258,3 +258,34 @@ def synthetic_protein(natoms=2000, target_tris=80000, seed=3, ball_radius=20.0):
             break
         h *= ratio ** 0.5
     return V, T, xyz, radii, q, h
+
+
+def binding_complex(n_rec, n_lig, seed=0, gap=4.5, spacing=0.7):
+    """A synthetic receptor-ligand complex: receptor atoms on a jittered FCC
+    lattice in a ball sized for n_rec atoms, ligand in a small ball placed
+    along a seeded random direction so that the closest receptor-ligand
+    atom-centre distance is `gap` A.  Returns dict with the atoms, radii and
+    charges of the receptor, the ligand and the complex, and the three
+    Gaussian surfaces (verts, tris)."""
+    rng = np.random.default_rng(seed)
+    per_atom = 2.85 ** 3 / 2 ** 0.5          # FCC volume per site
+    rr = (3 * n_rec * per_atom / (4 * np.pi)) ** (1 / 3) * 1.1 + 1.0
+    rl = (3 * n_lig * per_atom / (4 * np.pi)) ** (1 / 3) * 1.1 + 1.0
+    xr, radr, qr = fcc_ball_atoms(n_rec, rr, 2.85, 0.1, seed=seed + 1)
+    xl, radl, ql = fcc_ball_atoms(n_lig, rl, 2.85, 0.1, seed=seed + 2)
+    u = rng.standard_normal(3)
+    u /= np.linalg.norm(u)
+    shift = rr + rl
+    for _ in range(60):
+        d = np.min(np.linalg.norm((xl + shift * u)[:, None, :] - xr[None, :, :], axis=2))
+        shift += gap - d
+        if abs(gap - d) < 1e-3:
+            break
+    xl = xl + shift * u
+    xc = np.concatenate([xr, xl])
+    radc = np.concatenate([radr, radl])
+    qc = np.concatenate([qr, ql])
+    out = dict(rec=(xr, radr, qr), lig=(xl, radl, ql), cplx=(xc, radc, qc))
+    out["surf"] = {k: gaussian_surface(v[0], v[1], spacing) for k, v in
+                   (("rec", out["rec"]), ("lig", out["lig"]), ("cplx", out["cplx"]))}
+    return out
