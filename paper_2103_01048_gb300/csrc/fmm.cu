@@ -34,11 +34,13 @@ template <> __device__ __forceinline__ double exp_t<double>(double x) { return e
 // One source-target interaction, without the 1/(4 pi) factor:
 //   pot += g q + (d.m) f,   dn += -(d.n_t) f q,   d = x_t - y_s,
 //   g = e/r, f = e (1 + kappa r)/r^3, e = exp(-kappa r) (Yukawa) or 1.
-template <typename T, bool YUK, bool DL, bool DN>
+// GUARD: the pair may coincide (r = 0 contributes nothing).  Coincident
+// points share a Morton key, hence a leaf, so only a leaf's own box needs it.
+template <typename T, bool YUK, bool DL, bool DN, bool GUARD = true>
 __device__ __forceinline__ void interact(T dx, T dy, T dz, T q, T mx, T my, T mz, T nx, T ny, T nz, T kappa,
                                          T& pot, T& dn) {
     T r2 = dx * dx + dy * dy + dz * dz;
-    T rinv = r2 > T(0) ? rsqrt_t<T>(r2) : T(0);
+    T rinv = GUARD ? (r2 > T(0) ? rsqrt_t<T>(r2) : T(0)) : rsqrt_t<T>(r2);
     T g = rinv, f = rinv * rinv * rinv;
     if (YUK) {
         T r = r2 * rinv;
@@ -381,11 +383,12 @@ __global__ void __launch_bounds__(256) k_check2equiv(GemmArgs a, const TO* __res
 // ---------------------------------------------------------------------------
 // Leaf evaluation: P2P over U(B), M2P over W(B), L2P of B's own downward
 // equivalent density, at every target of leaf B.  One CTA (128 threads) per
-// target leaf.  A leaf holds at most ncrit targets, usually fewer than 128:
-// the CTA is split into G = 128 / slots groups (slots = the smallest power of
-// two >= the target count, at least 16); group g takes every G-th source of
-// each staged chunk and the G partial sums are added at the end, so no
-// thread idles.
+// target leaf; each thread carries two targets (t and t + slots) so every
+// staged source is loaded once for two pairs.  A leaf holds at most ncrit
+// targets, usually fewer than 256: the CTA is split into G = 128 / slots
+// groups (slots = the smallest power of two >= half the target count, at
+// least 8); group g takes every G-th source of each staged chunk and the G
+// partial sums are added at the end, so no thread idles.
 // ---------------------------------------------------------------------------
 template <typename T, bool YUK, bool DL, bool DN>
 __global__ void __launch_bounds__(128) k_leaf_eval(const int* __restrict__ leaves, int nleaf,
@@ -405,27 +408,32 @@ __global__ void __launch_bounds__(128) k_leaf_eval(const int* __restrict__ leave
     constexpr int CH = 128;
     __shared__ V s_q[CH];
     __shared__ V s_m[DL ? CH : 1];
-    __shared__ T s_red[2][CH];
+    __shared__ T s_red[2][2 * CH];
     int li = blockIdx.x;
     if (li >= nleaf) return;
-    int b = leaves[li];
-    int t0 = tb[b], t1 = te[b];
+    const int b = leaves[li];
+    const int t0 = tb[b], t1 = te[b];
     int slots = CH;
-    while (slots > 16 && slots / 2 >= t1 - t0) slots /= 2;
+    while (slots > 8 && 2 * (slots / 2) >= t1 - t0) slots /= 2;
     const int G = CH / slots;
     const int tloc = threadIdx.x % slots, g = threadIdx.x / slots;
-    for (int tc = t0; tc < t1; tc += slots) {
-        int t = tc + tloc;
-        bool valid = t < t1;
-        float4 xp = valid ? tpos[t] : make_float4(0, 0, 0, 0);
-        T x = xp.x, y = xp.y, z = xp.z;
-        T nx = 0, ny = 0, nz = 0;
-        if (DN && valid) { V nn = tn[t]; nx = nn.x; ny = nn.y; nz = nn.z; }
-        T pot = 0, dn = 0;
+    const int nw = W_off[b + 1] - W_off[b];
+    const int nsrcbox = nw + (level[b] >= 2 ? 1 : 0);
+    for (int tc = t0; tc < t1; tc += 2 * slots) {
+        const int ta = tc + tloc, tb2 = ta + slots;
+        const bool va = ta < t1, vb = tb2 < t1;
+        const float4 xa = va ? tpos[ta] : make_float4(0, 0, 0, 0);
+        const float4 xb = vb ? tpos[tb2] : make_float4(0, 0, 0, 0);
+        T nxa = 0, nya = 0, nza = 0, nxb = 0, nyb = 0, nzb = 0;
+        if (DN) {
+            if (va) { V nn = tn[ta]; nxa = nn.x; nya = nn.y; nza = nn.z; }
+            if (vb) { V nn = tn[tb2]; nxb = nn.x; nyb = nn.y; nzb = nn.z; }
+        }
+        T pa = 0, da = 0, pb = 0, db = 0;
         // P2P
         for (int ui = U_off[b]; ui < U_off[b + 1]; ++ui) {
-            int a = U_ids[ui];
-            int j0 = sb[a], j1 = se[a];
+            const int a = U_ids[ui];
+            const int j0 = sb[a], j1 = se[a];
             for (int jc = j0; jc < j1; jc += CH) {
                 int j = jc + threadIdx.x;
                 __syncthreads();
@@ -434,24 +442,39 @@ __global__ void __launch_bounds__(128) k_leaf_eval(const int* __restrict__ leave
                     if (DL) s_m[threadIdx.x] = sm[j];
                 }
                 __syncthreads();
-                int cnt = min(CH, j1 - jc);
-                for (int k = g; k < cnt; k += G) {
-                    V s = s_q[k];
-                    T mx = 0, my = 0, mz = 0;
-                    if (DL) { V mm = s_m[k]; mx = mm.x; my = mm.y; mz = mm.z; }
-                    interact<T, YUK, DL, DN>(x - s.x, y - s.y, z - s.z, s.w, mx, my, mz, nx, ny, nz, kappa, pot, dn);
+                const int cnt = min(CH, j1 - jc);
+                if (a == b) {
+                    for (int k = g; k < cnt; k += G) {
+                        V s = s_q[k];
+                        T mx = 0, my = 0, mz = 0;
+                        if (DL) { V mm = s_m[k]; mx = mm.x; my = mm.y; mz = mm.z; }
+                        interact<T, YUK, DL, DN, true>((T)xa.x - s.x, (T)xa.y - s.y, (T)xa.z - s.z, s.w, mx, my, mz,
+                                                       nxa, nya, nza, kappa, pa, da);
+                        interact<T, YUK, DL, DN, true>((T)xb.x - s.x, (T)xb.y - s.y, (T)xb.z - s.z, s.w, mx, my, mz,
+                                                       nxb, nyb, nzb, kappa, pb, db);
+                    }
+                } else {
+#pragma unroll 2
+                    for (int k = g; k < cnt; k += G) {
+                        V s = s_q[k];
+                        T mx = 0, my = 0, mz = 0;
+                        if (DL) { V mm = s_m[k]; mx = mm.x; my = mm.y; mz = mm.z; }
+                        interact<T, YUK, DL, DN, false>((T)xa.x - s.x, (T)xa.y - s.y, (T)xa.z - s.z, s.w, mx, my, mz,
+                                                        nxa, nya, nza, kappa, pa, da);
+                        interact<T, YUK, DL, DN, false>((T)xb.x - s.x, (T)xb.y - s.y, (T)xb.z - s.z, s.w, mx, my, mz,
+                                                        nxb, nyb, nzb, kappa, pb, db);
+                    }
                 }
             }
         }
         // M2P (W list) and L2P (own downward equivalent): monopole equivalent densities
-        int nw = W_off[b + 1] - W_off[b];
-        int nsrcbox = nw + (level[b] >= 2 ? 1 : 0);
         for (int wi = 0; wi < nsrcbox; ++wi) {
-            int a = (wi < nw) ? W_ids[W_off[b] + wi] : b;
+            const int a = (wi < nw) ? W_ids[W_off[b] + wi] : b;
             const T* Q = (wi < nw) ? Qu : Qd;
-            double4 ca = center[a];
-            T alpha = T(wi < nw ? kAlphaInner : kAlphaOuter) * (T)ca.w;
-            T rx = (T)((double)xp.x - ca.x), ry = (T)((double)xp.y - ca.y), rz = (T)((double)xp.z - ca.z);
+            const double4 ca = center[a];
+            const T alpha = T(wi < nw ? kAlphaInner : kAlphaOuter) * (T)ca.w;
+            const T rxa = (T)((double)xa.x - ca.x), rya = (T)((double)xa.y - ca.y), rza = (T)((double)xa.z - ca.z);
+            const T rxb = (T)((double)xb.x - ca.x), ryb = (T)((double)xb.y - ca.y), rzb = (T)((double)xb.z - ca.z);
             for (int jc = 0; jc < ne; jc += CH) {
                 int j = jc + threadIdx.x;
                 __syncthreads();
@@ -460,25 +483,32 @@ __global__ void __launch_bounds__(128) k_leaf_eval(const int* __restrict__ leave
                     s_q[threadIdx.x] = {alpha * (T)s.x, alpha * (T)s.y, alpha * (T)s.z, Q[(size_t)a * npad + j]};
                 }
                 __syncthreads();
-                int cnt = min(CH, ne - jc);
+                const int cnt = min(CH, ne - jc);
+#pragma unroll 2
                 for (int k = g; k < cnt; k += G) {
                     V s = s_q[k];
-                    interact<T, YUK, false, DN>(rx - s.x, ry - s.y, rz - s.z, s.w, 0, 0, 0, nx, ny, nz, kappa, pot, dn);
+                    interact<T, YUK, false, DN, false>(rxa - s.x, rya - s.y, rza - s.z, s.w, 0, 0, 0, nxa, nya, nza,
+                                                       kappa, pa, da);
+                    interact<T, YUK, false, DN, false>(rxb - s.x, ryb - s.y, rzb - s.z, s.w, 0, 0, 0, nxb, nyb, nzb,
+                                                       kappa, pb, db);
                 }
             }
         }
         // combine the G partial sums of each target
-        s_red[0][threadIdx.x] = pot;
-        if (DN) s_red[1][threadIdx.x] = dn;
         __syncthreads();
-        if (g == 0 && valid) {
-            T p = 0, d = 0;
+        s_red[0][threadIdx.x] = pa;
+        s_red[0][CH + threadIdx.x] = pb;
+        if (DN) { s_red[1][threadIdx.x] = da; s_red[1][CH + threadIdx.x] = db; }
+        __syncthreads();
+        if (g == 0) {
+            T sa = 0, sb2 = 0, ea = 0, eb = 0;
             for (int q = 0; q < G; ++q) {
-                p += s_red[0][tloc + q * slots];
-                if (DN) d += s_red[1][tloc + q * slots];
+                sa += s_red[0][tloc + q * slots];
+                sb2 += s_red[0][CH + tloc + q * slots];
+                if (DN) { ea += s_red[1][tloc + q * slots]; eb += s_red[1][CH + tloc + q * slots]; }
             }
-            pot_out[t] = p * T(kInv4PiD);
-            if (DN) dn_out[t] = d * T(kInv4PiD);
+            if (va) { pot_out[ta] = sa * T(kInv4PiD); if (DN) dn_out[ta] = ea * T(kInv4PiD); }
+            if (vb) { pot_out[tb2] = sb2 * T(kInv4PiD); if (DN) dn_out[tb2] = eb * T(kInv4PiD); }
         }
     }
 }

@@ -105,6 +105,15 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
 #pragma unroll
     for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
+    uint32_t r[8];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
 __device__ __forceinline__ void red_add_v4(float* p, float a, float b, float c, float d) {
     asm volatile("red.global.add.v4.f32 [%0], {%1,%2,%3,%4};" ::"l"(p), "f"(a), "f"(b), "f"(c), "f"(d) : "memory");
 }
@@ -248,18 +257,21 @@ void build_m2l_pairs(fmm_tree* T) {
 // ---------------------------------------------------------------------------
 // the kernel
 // ---------------------------------------------------------------------------
+constexpr int kTcStages = 3;            // A-tile ring depth
+constexpr int kTcThreads = 256;         // 8 warps: two threads per gathered row
+
 struct TcSmem {
-    uint64_t barB, barMMA[2];
+    uint64_t barB, barMMA[kTcStages];
     uint32_t tmem_slot;
     int failed;
     int src[kTcRows], tgt[kTcRows];
 };
 
 template <int NPAD>
-__global__ void __launch_bounds__(128, 1) k_m2l_tc(const int4* __restrict__ items, const int* __restrict__ ptgt,
-                                                   const int* __restrict__ psrc, const float* __restrict__ ops,
-                                                   const float* __restrict__ Qu, float* __restrict__ Qd,
-                                                   int* __restrict__ err) {
+__global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(const int4* __restrict__ items, const int* __restrict__ ptgt,
+                                                          const int* __restrict__ psrc, const float* __restrict__ ops,
+                                                          const float* __restrict__ Qu, float* __restrict__ Qd,
+                                                          int* __restrict__ err) {
     constexpr int NH = NPAD / 2;                     // output rows of this CTA (MMA N)
     constexpr int KB = NPAD / 32;                    // K blocks of 32 tf32 (128 B)
     constexpr uint32_t B_SPLIT = KB * NH * 128;      // bytes of one of hi / lo
@@ -270,16 +282,16 @@ __global__ void __launch_bounds__(128, 1) k_m2l_tc(const int4* __restrict__ item
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint8_t* sB = smem;                               // [hi|lo][KB][NH][128]
     uint8_t* sA = smem + 2 * B_SPLIT;                 // [stage][hi|lo][128][128]
-    TcSmem* S = (TcSmem*)(sA + 2 * 2 * A_SPLIT);
+    TcSmem* S = (TcSmem*)(sA + kTcStages * 2 * A_SPLIT);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int row = tid & (kTcRows - 1), part = tid >> 7;     // row of the A tile, chunk half
     const int4 it = items[blockIdx.x];
     const int half = blockIdx.y;
     const int first = it.x, npairs = it.y, level = it.z, offs = it.w;
 
     if (tid == 0) {
         mbar_init(&S->barB, 1);
-        mbar_init(&S->barMMA[0], 1);
-        mbar_init(&S->barMMA[1], 1);
+        for (int q = 0; q < kTcStages; ++q) mbar_init(&S->barMMA[q], 1);
         S->failed = 0;
         fence_mbar_init();
     }
@@ -300,31 +312,36 @@ __global__ void __launch_bounds__(128, 1) k_m2l_tc(const int4* __restrict__ item
         bulk_g2s(sB + B_SPLIT, gB + B_SPLIT, B_SPLIT, &S->barB);
     }
     bool ok = mbar_wait(&S->barB, 0);
-    uint32_t commits[2] = {0, 0};
+    uint32_t commits[kTcStages] = {0, 0, 0};
     int last_stage = -1;
+    int step = 0;
     const int ntile = (npairs + kTcRows - 1) / kTcRows;
     if (__syncthreads_or(!ok)) goto fail;
 
     for (int tile = 0; tile < ntile; ++tile) {
         const int row0 = first + tile * kTcRows;
         const int nrow = min(kTcRows, npairs - tile * kTcRows);
-        S->src[tid] = tid < nrow ? psrc[row0 + tid] : -1;
-        S->tgt[tid] = tid < nrow ? ptgt[row0 + tid] : -1;
-        for (int kb = 0; kb < KB; ++kb) {
-            const int s = (tile * KB + kb) & 1;
+        if (part == 0) {
+            S->src[row] = row < nrow ? psrc[row0 + row] : -1;
+            S->tgt[row] = row < nrow ? ptgt[row0 + row] : -1;
+        }
+        for (int kb = 0; kb < KB; ++kb, ++step) {
+            const int s = step % kTcStages;
             if (commits[s] > 0) ok = mbar_wait(&S->barMMA[s], (commits[s] - 1) & 1);
             if (__syncthreads_or(!ok)) goto fail;
-            // gather row tid of the A tile: Qu[src][kb*32 .. +32), split hi / lo
+            // gather half of row `row` of the A tile: Qu[src][kb*32 + part*16 .. +16), split hi / lo
             uint8_t* aHi = sA + (size_t)s * 2 * A_SPLIT;
             uint8_t* aLo = aHi + A_SPLIT;
-            const int sbox = S->src[tid];
+            const int sbox = S->src[row];
             const float4* q4 = sbox >= 0 ? (const float4*)(Qu + (size_t)sbox * NPAD + kb * 32) : nullptr;
+            float4 v[4];
 #pragma unroll
-            for (int c = 0; c < 8; ++c) {
-                float4 v = q4 ? q4[c] : make_float4(0.f, 0.f, 0.f, 0.f);
-                float4 h = make_float4(tf32_hi(v.x), tf32_hi(v.y), tf32_hi(v.z), tf32_hi(v.w));
-                float4 l = make_float4(v.x - h.x, v.y - h.y, v.z - h.z, v.w - h.w);
-                uint32_t off = sw128_off(tid, c * 4);
+            for (int c = 0; c < 4; ++c) v[c] = q4 ? q4[part * 4 + c] : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+            for (int c = 0; c < 4; ++c) {
+                float4 h = make_float4(tf32_hi(v[c].x), tf32_hi(v[c].y), tf32_hi(v[c].z), tf32_hi(v[c].w));
+                float4 l = make_float4(v[c].x - h.x, v[c].y - h.y, v[c].z - h.z, v[c].w - h.w);
+                uint32_t off = sw128_off(row, (part * 4 + c) * 4);
                 *(float4*)(aHi + off) = h;
                 *(float4*)(aLo + off) = l;
             }
@@ -351,16 +368,18 @@ __global__ void __launch_bounds__(128, 1) k_m2l_tc(const int4* __restrict__ item
         if (__syncthreads_or(!ok)) goto fail;
         tc_fence_after();
         {
-            const int row = warp * 32 + lane;
-            const int t = S->tgt[row];
+            // warps w and w + 4 read the same TMEM lane quarter, one column half each
+            const int erow = (warp & 3) * 32 + lane;
+            const int t = S->tgt[erow];
+            const int c_lo = part * (NH / 2);
             float* dst = t >= 0 ? Qd + (size_t)t * NPAD + half * NH : nullptr;
 #pragma unroll 1
-            for (int c0 = 0; c0 < NH; c0 += 16) {
-                float v[16];
-                tmem_ld16(taddr + ((uint32_t)(warp * 32) << 16) + c0, v);
+            for (int c0 = c_lo; c0 < c_lo + NH / 2; c0 += 8) {
+                float v[8];
+                tmem_ld8(taddr + ((uint32_t)((warp & 3) * 32) << 16) + c0, v);
                 if (dst) {
-#pragma unroll
-                    for (int q = 0; q < 16; q += 4) red_add_v4(dst + c0 + q, v[q], v[q + 1], v[q + 2], v[q + 3]);
+                    red_add_v4(dst + c0, v[0], v[1], v[2], v[3]);
+                    red_add_v4(dst + c0 + 4, v[4], v[5], v[6], v[7]);
                 }
             }
         }
@@ -383,7 +402,8 @@ done:
 
 template <int NPAD>
 static size_t tc_smem_bytes() {
-    return 1024 + 2 * (size_t)(NPAD / 32) * (NPAD / 2) * 128 + 4 * (size_t)kTcRows * 128 + sizeof(TcSmem);
+    return 1024 + 2 * (size_t)(NPAD / 32) * (NPAD / 2) * 128 + kTcStages * 2 * (size_t)kTcRows * 128 +
+           sizeof(TcSmem);
 }
 
 template <int NPAD>
@@ -399,7 +419,7 @@ static void launch_tc(const fmm_tree* T, const Operators& O, const float* Qu, fl
         attr_set[dev] = true;
     }
     dim3 grid(T->m2l_pairs.nitems, 2);
-    k_m2l_tc<NPAD><<<grid, kTcRows, sm, st>>>(T->m2l_pairs.items.p, T->m2l_pairs.tgt.p, T->m2l_pairs.src.p,
+    k_m2l_tc<NPAD><<<grid, kTcThreads, sm, st>>>(T->m2l_pairs.items.p, T->m2l_pairs.tgt.p, T->m2l_pairs.src.p,
                                               O.m2l_tc.p, Qu, Qd, err);
     PB_CHECK_LAUNCH();
 }
