@@ -325,22 +325,31 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(const int4* __restrict
             S->src[row] = row < nrow ? psrc[row0 + row] : -1;
             S->tgt[row] = row < nrow ? ptgt[row0 + row] : -1;
         }
+        __syncthreads();
+        // all loads of this thread's half row for every K block at once: one
+        // memory latency per tile instead of one per K block
+        float4 v[KB][4];
+        {
+            const int sbox = S->src[row];
+            const float4* q4 = sbox >= 0 ? (const float4*)(Qu + (size_t)sbox * NPAD) : nullptr;
+#pragma unroll
+            for (int kb = 0; kb < KB; ++kb)
+#pragma unroll
+                for (int c = 0; c < 4; ++c) v[kb][c] = q4 ? q4[kb * 8 + part * 4 + c] : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
         for (int kb = 0; kb < KB; ++kb, ++step) {
             const int s = step % kTcStages;
             if (commits[s] > 0) ok = mbar_wait(&S->barMMA[s], (commits[s] - 1) & 1);
             if (__syncthreads_or(!ok)) goto fail;
-            // gather half of row `row` of the A tile: Qu[src][kb*32 + part*16 .. +16), split hi / lo
+            // split into hi / lo and write swizzled into the stage
             uint8_t* aHi = sA + (size_t)s * 2 * A_SPLIT;
             uint8_t* aLo = aHi + A_SPLIT;
-            const int sbox = S->src[row];
-            const float4* q4 = sbox >= 0 ? (const float4*)(Qu + (size_t)sbox * NPAD + kb * 32) : nullptr;
-            float4 v[4];
-#pragma unroll
-            for (int c = 0; c < 4; ++c) v[c] = q4 ? q4[part * 4 + c] : make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
             for (int c = 0; c < 4; ++c) {
-                float4 h = make_float4(tf32_hi(v[c].x), tf32_hi(v[c].y), tf32_hi(v[c].z), tf32_hi(v[c].w));
-                float4 l = make_float4(v[c].x - h.x, v[c].y - h.y, v[c].z - h.z, v[c].w - h.w);
+                const float4 x = v[kb][c];
+                float4 h = make_float4(tf32_hi(x.x), tf32_hi(x.y), tf32_hi(x.z), tf32_hi(x.w));
+                float4 l = make_float4(x.x - h.x, x.y - h.y, x.z - h.z, x.w - h.w);
                 uint32_t off = sw128_off(row, (part * 4 + c) * 4);
                 *(float4*)(aHi + off) = h;
                 *(float4*)(aLo + off) = l;
