@@ -15,6 +15,8 @@
 namespace pbfmm {
 
 bool m2l_tc_launch(const fmm_tree* T, const Operators& O, const float* Qu, float* Qd, int* err, cudaStream_t st);
+bool pc_tc_launch(const fmm_tree* T, const Operators& O, int child_level, bool up, float* Q, int* err,
+                  cudaStream_t st);
 
 constexpr double kInv4PiD = 0.07957747154594767;
 constexpr int kTC = 32;    // boxes per tile of the dense box-vector products (= kM2LTile)
@@ -679,6 +681,9 @@ static void apply_t(fmm_tree* Tr, const Operators& O, double kappa_d, const In* 
     // M2M, post-order: parents at level l from children at level l + 1
     // (leaves of level l keep their P2M result: the kernel skips them)
     for (int l = Tr->nlev - 2; l >= 2; --l) {
+        if constexpr (std::is_same<T, float>::value) {
+            if (pc_tc_launch(Tr, O, l + 1, true, W.Qu.p, ctx->dev_err, st)) continue;
+        }
         int a0 = Tr->lvl_off[l], a1 = Tr->lvl_off[l + 1];
         ga.mode = G_M2M; ga.ncols = a1 - a0; ga.cols = nullptr; ga.col_base = a0; ga.level = l + 1;
         gemm_dispatch<T, T>(npad, st, div_up(a1 - a0, kTC), ga, m2m, W.Qu.p, W.Qu.p);
@@ -713,6 +718,9 @@ static void apply_t(fmm_tree* Tr, const Operators& O, double kappa_d, const In* 
     // ---- downward pass, pre-order: L2L (DC2DE folded) from parents at level l - 1
     ph.reset(); ph = std::make_unique<PhaseTimer>(ctx, PB_PH_DOWN);
     for (int l = 3; l < Tr->nlev; ++l) {
+        if constexpr (std::is_same<T, float>::value) {
+            if (pc_tc_launch(Tr, O, l, false, W.Qd.p, ctx->dev_err, st)) continue;
+        }
         int p0 = Tr->lvl_off[l - 1], p1 = Tr->lvl_off[l];
         ga.mode = G_L2L; ga.ncols = p1 - p0; ga.cols = nullptr; ga.col_base = p0; ga.level = l;
         gemm_dispatch<T, T>(npad, st, div_up(p1 - p0, kTC), ga, l2l, W.Qd.p, W.Qd.p);

@@ -31,6 +31,7 @@ struct Operators {
     // TF32 hi + lo parts, pre-swizzled (128B swizzle, K-major) per N half:
     // [level][343][half][hi|lo][K/32][npad/2 rows][128 B]
     DBuf<float> m2l_tc;
+    DBuf<float> m2m_tc, l2l_tc;   // same packing, [level][8 octants]
     bool have_tc = false;
     // FP64 copies (all-FP64 path)
     DBuf<double> uc2ue_d, dc2de_d, m2m_d, l2l_d, m2l_d;

@@ -164,13 +164,18 @@ __global__ void k_pack_m2l_tc(int npad, long long nmat, const float* __restrict_
     *(float*)(base + (long long)kb_n * nh * 128 + off) = lo;
 }
 
+static void pack_tc(int npad, long long nmat, const float* src, DBuf<float>& dst, cudaStream_t st) {
+    const long long m2 = (long long)npad * npad;
+    dst.alloc(nmat * m2 * 2, st);
+    k_pack_m2l_tc<<<div_up(nmat * m2, 256), 256, 0, st>>>(npad, nmat, src, dst.p);
+    PB_CHECK_LAUNCH();
+}
+
 void pack_m2l_tc(Operators& O, cudaStream_t st) {
     if (O.npad > kTcMaxNpad || O.npad % 32 != 0) { O.have_tc = false; return; }
-    const long long nmat = (long long)O.nlev * kNumOffsets;
-    const long long m2 = (long long)O.npad * O.npad;
-    O.m2l_tc.alloc(nmat * m2 * 2, st);
-    k_pack_m2l_tc<<<div_up(nmat * m2, 256), 256, 0, st>>>(O.npad, nmat, O.m2l.p, O.m2l_tc.p);
-    PB_CHECK_LAUNCH();
+    pack_tc(O.npad, (long long)O.nlev * kNumOffsets, O.m2l.p, O.m2l_tc, st);
+    if (O.m2m.p) pack_tc(O.npad, (long long)O.nlev * 8, O.m2m.p, O.m2m_tc, st);
+    if (O.l2l.p) pack_tc(O.npad, (long long)O.nlev * 8, O.l2l.p, O.l2l_tc, st);
     O.have_tc = true;
 }
 
@@ -237,19 +242,61 @@ void build_m2l_pairs(fmm_tree* T) {
     std::vector<int> hk(np);
     PB_CUDA(cudaMemcpyAsync(hk.data(), key_s.p, np * sizeof(int), cudaMemcpyDeviceToHost, st));
     PB_CUDA(cudaStreamSynchronize(st));
-    // work items: (first pair, pair count <= kTcItemPairs, level, offset)
+    // work items: (first pair, pair count <= kTcItemPairs, operator index = level * 343 + offset, 0)
     std::vector<int4> items;
     long long i = 0;
     while (i < np) {
         long long j = i;
         while (j < np && hk[j] == hk[i]) ++j;
         for (long long a = i; a < j; a += kTcItemPairs)
-            items.push_back(make_int4((int)a, (int)std::min<long long>(kTcItemPairs, j - a), hk[i] / kNumOffsets,
-                                      hk[i] % kNumOffsets));
+            items.push_back(make_int4((int)a, (int)std::min<long long>(kTcItemPairs, j - a), hk[i], 0));
         i = j;
     }
     P.nitems = (int)items.size();
     P.items.alloc(items.size(), st);
+    PB_CUDA(cudaMemcpyAsync(P.items.p, items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice, st));
+    PB_CUDA(cudaStreamSynchronize(st));
+}
+
+// Parent-child pairs for M2M / L2L on the tensor cores: children of level
+// >= 3 grouped by (level, octant), ascending box order inside a group.
+void build_pc_pairs(fmm_tree* T) {
+    cudaStream_t st = T->ctx->stream;
+    auto& P = T->pc_pairs;
+    const int nb = T->nbox;
+    std::vector<int> par(nb);
+    std::vector<int4> anc(nb);
+    PB_CUDA(cudaMemcpyAsync(par.data(), T->parent.p, nb * sizeof(int), cudaMemcpyDeviceToHost, st));
+    PB_CUDA(cudaMemcpyAsync(anc.data(), T->anchor.p, nb * sizeof(int4), cudaMemcpyDeviceToHost, st));
+    PB_CUDA(cudaStreamSynchronize(st));
+    std::vector<std::vector<int>> bucket((size_t)T->nlev * 8);
+    for (int c = 0; c < nb; ++c) {
+        if (anc[c].w < 3) continue;
+        int oct = ((anc[c].x & 1) << 2) | ((anc[c].y & 1) << 1) | (anc[c].z & 1);
+        bucket[(size_t)anc[c].w * 8 + oct].push_back(c);
+    }
+    std::vector<int> hp, hc;
+    std::vector<int4> items;
+    P.level_item_off.assign(T->nlev + 1, 0);
+    for (int l = 0; l < T->nlev; ++l) {
+        P.level_item_off[l] = (int)items.size();
+        for (int o = 0; o < 8; ++o) {
+            auto& v = bucket[(size_t)l * 8 + o];
+            for (size_t a = 0; a < v.size(); a += kTcItemPairs) {
+                int cnt = (int)std::min<size_t>(kTcItemPairs, v.size() - a);
+                items.push_back(make_int4((int)hc.size(), cnt, l * 8 + o, 0));
+                for (int k = 0; k < cnt; ++k) { hc.push_back(v[a + k]); hp.push_back(par[v[a + k]]); }
+            }
+        }
+    }
+    P.level_item_off[T->nlev] = (int)items.size();
+    P.nitems = (int)items.size();
+    if (items.empty()) return;
+    P.parent.alloc(hp.size(), st);
+    P.child.alloc(hc.size(), st);
+    P.items.alloc(items.size(), st);
+    PB_CUDA(cudaMemcpyAsync(P.parent.p, hp.data(), hp.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+    PB_CUDA(cudaMemcpyAsync(P.child.p, hc.data(), hc.size() * sizeof(int), cudaMemcpyHostToDevice, st));
     PB_CUDA(cudaMemcpyAsync(P.items.p, items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice, st));
     PB_CUDA(cudaStreamSynchronize(st));
 }
@@ -272,6 +319,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(const int4* __restrict
                                                           const int* __restrict__ psrc, const float* __restrict__ ops,
                                                           const float* __restrict__ Qu, float* __restrict__ Qd,
                                                           int* __restrict__ err) {
+    // Generic tensor-core box-operator product: for every pair p of the
+    // item, Qd[tgt[p]] += Op(item) Qu[src[p]] (Op resident for the CTA).
+    // Used for M2L (operator per level and offset) and for M2M / L2L
+    // (operator per child level and octant).
     constexpr int NH = NPAD / 2;                     // output rows of this CTA (MMA N)
     constexpr int KB = NPAD / 32;                    // K blocks of 32 tf32 (128 B)
     constexpr uint32_t B_SPLIT = KB * NH * 128;      // bytes of one of hi / lo
@@ -287,7 +338,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(const int4* __restrict
     const int row = tid & (kTcRows - 1), part = tid >> 7;     // row of the A tile, chunk half
     const int4 it = items[blockIdx.x];
     const int half = blockIdx.y;
-    const int first = it.x, npairs = it.y, level = it.z, offs = it.w;
+    const int first = it.x, npairs = it.y, opi = it.z;
 
     if (tid == 0) {
         mbar_init(&S->barB, 1);
@@ -305,7 +356,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(const int4* __restrict
     const uint32_t taddr = S->tmem_slot;
 
     // resident operator half: hi and lo, one bulk copy each
-    const uint8_t* gB = (const uint8_t*)ops + (((long long)level * kNumOffsets + offs) * 2 + half) * (2LL * B_SPLIT);
+    const uint8_t* gB = (const uint8_t*)ops + ((long long)opi * 2 + half) * (2LL * B_SPLIT);
     if (tid == 0) {
         mbar_arrive_expect_tx(&S->barB, 2 * B_SPLIT);
         bulk_g2s(sB, gB, B_SPLIT, &S->barB);
@@ -416,7 +467,19 @@ static size_t tc_smem_bytes() {
 }
 
 template <int NPAD>
+static void launch_tc_items(const int4* items, int nitems, const int* tgt, const int* src, const float* ops,
+                            const float* X, float* Y, int* err, cudaStream_t st);
+
+template <int NPAD>
 static void launch_tc(const fmm_tree* T, const Operators& O, const float* Qu, float* Qd, int* err, cudaStream_t st) {
+    launch_tc_items<NPAD>(T->m2l_pairs.items.p, T->m2l_pairs.nitems, T->m2l_pairs.tgt.p, T->m2l_pairs.src.p,
+                          O.m2l_tc.p, Qu, Qd, err, st);
+}
+
+template <int NPAD>
+static void launch_tc_items(const int4* items, int nitems, const int* tgt, const int* src, const float* ops,
+                            const float* X, float* Y, int* err, cudaStream_t st) {
+    if (nitems <= 0) return;
     const size_t sm = tc_smem_bytes<NPAD>();
     // opt in to the large shared-memory carve-out once per process and device
     // (not a stream operation, so it stays out of captured graphs)
@@ -427,10 +490,32 @@ static void launch_tc(const fmm_tree* T, const Operators& O, const float* Qu, fl
         PB_CUDA(cudaFuncSetAttribute(k_m2l_tc<NPAD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
         attr_set[dev] = true;
     }
-    dim3 grid(T->m2l_pairs.nitems, 2);
-    k_m2l_tc<NPAD><<<grid, kTcThreads, sm, st>>>(T->m2l_pairs.items.p, T->m2l_pairs.tgt.p, T->m2l_pairs.src.p,
-                                              O.m2l_tc.p, Qu, Qd, err);
+    dim3 grid(nitems, 2);
+    k_m2l_tc<NPAD><<<grid, kTcThreads, sm, st>>>(items, tgt, src, ops, X, Y, err);
     PB_CHECK_LAUNCH();
+}
+
+// M2M (up = true: parents at level l - 1 += M2M children at level l) or L2L
+// (children at level l += L2L parents at level l - 1) on the tensor cores;
+// false when the tensor-core path does not apply
+bool pc_tc_launch(const fmm_tree* T, const Operators& O, int child_level, bool up, float* Q, int* err,
+                  cudaStream_t st) {
+    if (!O.have_tc || !O.m2m_tc.p || !O.l2l_tc.p) return false;
+    const auto& P = T->pc_pairs;
+    if (child_level < 3 || child_level >= T->nlev || (int)P.level_item_off.size() != T->nlev + 1) return false;
+    const int i0 = P.level_item_off[child_level], i1 = P.level_item_off[child_level + 1];
+    if (i1 <= i0) return true;
+    const int4* items = P.items.p + i0;
+    const int* tgt = up ? P.parent.p : P.child.p;
+    const int* src = up ? P.child.p : P.parent.p;
+    const float* ops = up ? O.m2m_tc.p : O.l2l_tc.p;
+    switch (O.npad) {
+        case 32: launch_tc_items<32>(items, i1 - i0, tgt, src, ops, Q, Q, err, st); return true;
+        case 64: launch_tc_items<64>(items, i1 - i0, tgt, src, ops, Q, Q, err, st); return true;
+        case 128: launch_tc_items<128>(items, i1 - i0, tgt, src, ops, Q, Q, err, st); return true;
+        case 160: launch_tc_items<160>(items, i1 - i0, tgt, src, ops, Q, Q, err, st); return true;
+        default: return false;
+    }
 }
 
 // returns false when the tensor-core path does not apply (caller uses SIMT)
@@ -482,6 +567,7 @@ extern "C" int pbfmm_selftest_m2l_tc(int nrows, int npad, const float* Q, const 
         PB_CUDA(cudaMemcpyAsync(T.m2l_pairs.src.p, id.data(), nrows * 4, cudaMemcpyHostToDevice, st));
         std::vector<int4> items;
         for (int a = 0; a < nrows; a += kTcItemPairs) items.push_back(make_int4(a, std::min(kTcItemPairs, nrows - a), 0, 0));
+        // (operator index 0: level 0, offset slot 0)
         T.m2l_pairs.nitems = (int)items.size();
         T.m2l_pairs.items.alloc(items.size(), st);
         PB_CUDA(cudaMemcpyAsync(T.m2l_pairs.items.p, items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice, st));

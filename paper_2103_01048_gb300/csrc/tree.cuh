@@ -35,6 +35,16 @@ struct M2LPairs {
     long long npairs = 0;
 };
 
+// Parent-child pairs (children of level >= 3) grouped by (level, octant) for
+// M2M / L2L on the tensor cores; items of child level l are
+// [level_item_off[l], level_item_off[l + 1]).
+struct PCPairs {
+    DBuf<int> parent, child;
+    DBuf<int4> items;
+    std::vector<int> level_item_off;
+    int nitems = 0;
+};
+
 }  // namespace pbfmm
 
 struct fmm_tree {
@@ -73,6 +83,7 @@ struct fmm_tree {
     // non-leaf boxes per level (M2M parents) and all boxes per level for L2L
     pbfmm::M2LSchedule m2l;
     pbfmm::M2LPairs m2l_pairs;
+    pbfmm::PCPairs pc_pairs;
 
     std::map<std::tuple<int, double, int, int>, std::shared_ptr<pbfmm::Operators>> ops;
 };
