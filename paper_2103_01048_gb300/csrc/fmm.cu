@@ -385,14 +385,14 @@ __global__ void __launch_bounds__(256) k_check2equiv(GemmArgs a, const TO* __res
 // ---------------------------------------------------------------------------
 // Leaf evaluation: P2P over U(B), M2P over W(B), L2P of B's own downward
 // equivalent density, at every target of leaf B.  One CTA (128 threads) per
-// target leaf; each thread carries two targets (t and t + slots) so every
-// staged source is loaded once for two pairs.  A leaf holds at most ncrit
-// targets, usually fewer than 256: the CTA is split into G = 128 / slots
-// groups (slots = the smallest power of two >= half the target count, at
-// least 8); group g takes every G-th source of each staged chunk and the G
-// partial sums are added at the end, so no thread idles.
+// target leaf; each thread carries NT targets (t, t + slots, ...) so every
+// staged source is loaded once for NT pairs.  A leaf holds at most ncrit
+// targets, usually fewer than 128 * NT: the CTA is split into
+// G = 128 / slots groups (slots = the smallest power of two >= the target
+// count / NT, at least 8); group g takes every G-th source of each staged
+// chunk and the G partial sums are added at the end, so no thread idles.
 // ---------------------------------------------------------------------------
-template <typename T, bool YUK, bool DL, bool DN>
+template <typename T, bool YUK, bool DL, bool DN, int NT>
 __global__ void __launch_bounds__(128) k_leaf_eval(const int* __restrict__ leaves, int nleaf,
                                                    const int* __restrict__ tb, const int* __restrict__ te,
                                                    const int* __restrict__ sb, const int* __restrict__ se,
@@ -410,28 +410,31 @@ __global__ void __launch_bounds__(128) k_leaf_eval(const int* __restrict__ leave
     constexpr int CH = 128;
     __shared__ V s_q[CH];
     __shared__ V s_m[DL ? CH : 1];
-    __shared__ T s_red[2][2 * CH];
+    __shared__ T s_red[DN ? 2 : 1][NT * CH];
     int li = blockIdx.x;
     if (li >= nleaf) return;
     const int b = leaves[li];
     const int t0 = tb[b], t1 = te[b];
     int slots = CH;
-    while (slots > 8 && 2 * (slots / 2) >= t1 - t0) slots /= 2;
+    while (slots > 8 && NT * (slots / 2) >= t1 - t0) slots /= 2;
     const int G = CH / slots;
     const int tloc = threadIdx.x % slots, g = threadIdx.x / slots;
     const int nw = W_off[b + 1] - W_off[b];
     const int nsrcbox = nw + (level[b] >= 2 ? 1 : 0);
-    for (int tc = t0; tc < t1; tc += 2 * slots) {
-        const int ta = tc + tloc, tb2 = ta + slots;
-        const bool va = ta < t1, vb = tb2 < t1;
-        const float4 xa = va ? tpos[ta] : make_float4(0, 0, 0, 0);
-        const float4 xb = vb ? tpos[tb2] : make_float4(0, 0, 0, 0);
-        T nxa = 0, nya = 0, nza = 0, nxb = 0, nyb = 0, nzb = 0;
-        if (DN) {
-            if (va) { V nn = tn[ta]; nxa = nn.x; nya = nn.y; nza = nn.z; }
-            if (vb) { V nn = tn[tb2]; nxb = nn.x; nyb = nn.y; nzb = nn.z; }
+    for (int tc = t0; tc < t1; tc += NT * slots) {
+        int ti[NT];
+        bool vt[NT];
+        float4 xt[NT];
+        T nx[NT], ny[NT], nz[NT], pot[NT], dn[NT];
+#pragma unroll
+        for (int u = 0; u < NT; ++u) {
+            ti[u] = tc + tloc + u * slots;
+            vt[u] = ti[u] < t1;
+            xt[u] = vt[u] ? tpos[ti[u]] : make_float4(0, 0, 0, 0);
+            nx[u] = ny[u] = nz[u] = T(0);
+            if (DN && vt[u]) { V nn = tn[ti[u]]; nx[u] = nn.x; ny[u] = nn.y; nz[u] = nn.z; }
+            pot[u] = dn[u] = T(0);
         }
-        T pa = 0, da = 0, pb = 0, db = 0;
         // P2P
         for (int ui = U_off[b]; ui < U_off[b + 1]; ++ui) {
             const int a = U_ids[ui];
@@ -450,21 +453,20 @@ __global__ void __launch_bounds__(128) k_leaf_eval(const int* __restrict__ leave
                         V s = s_q[k];
                         T mx = 0, my = 0, mz = 0;
                         if (DL) { V mm = s_m[k]; mx = mm.x; my = mm.y; mz = mm.z; }
-                        interact<T, YUK, DL, DN, true>((T)xa.x - s.x, (T)xa.y - s.y, (T)xa.z - s.z, s.w, mx, my, mz,
-                                                       nxa, nya, nza, kappa, pa, da);
-                        interact<T, YUK, DL, DN, true>((T)xb.x - s.x, (T)xb.y - s.y, (T)xb.z - s.z, s.w, mx, my, mz,
-                                                       nxb, nyb, nzb, kappa, pb, db);
+#pragma unroll
+                        for (int u = 0; u < NT; ++u)
+                            interact<T, YUK, DL, DN, true>((T)xt[u].x - s.x, (T)xt[u].y - s.y, (T)xt[u].z - s.z, s.w,
+                                                           mx, my, mz, nx[u], ny[u], nz[u], kappa, pot[u], dn[u]);
                     }
                 } else {
-#pragma unroll 2
                     for (int k = g; k < cnt; k += G) {
                         V s = s_q[k];
                         T mx = 0, my = 0, mz = 0;
                         if (DL) { V mm = s_m[k]; mx = mm.x; my = mm.y; mz = mm.z; }
-                        interact<T, YUK, DL, DN, false>((T)xa.x - s.x, (T)xa.y - s.y, (T)xa.z - s.z, s.w, mx, my, mz,
-                                                        nxa, nya, nza, kappa, pa, da);
-                        interact<T, YUK, DL, DN, false>((T)xb.x - s.x, (T)xb.y - s.y, (T)xb.z - s.z, s.w, mx, my, mz,
-                                                        nxb, nyb, nzb, kappa, pb, db);
+#pragma unroll
+                        for (int u = 0; u < NT; ++u)
+                            interact<T, YUK, DL, DN, false>((T)xt[u].x - s.x, (T)xt[u].y - s.y, (T)xt[u].z - s.z,
+                                                            s.w, mx, my, mz, nx[u], ny[u], nz[u], kappa, pot[u], dn[u]);
                     }
                 }
             }
@@ -475,8 +477,13 @@ __global__ void __launch_bounds__(128) k_leaf_eval(const int* __restrict__ leave
             const T* Q = (wi < nw) ? Qu : Qd;
             const double4 ca = center[a];
             const T alpha = T(wi < nw ? kAlphaInner : kAlphaOuter) * (T)ca.w;
-            const T rxa = (T)((double)xa.x - ca.x), rya = (T)((double)xa.y - ca.y), rza = (T)((double)xa.z - ca.z);
-            const T rxb = (T)((double)xb.x - ca.x), ryb = (T)((double)xb.y - ca.y), rzb = (T)((double)xb.z - ca.z);
+            T rx[NT], ry[NT], rz[NT];
+#pragma unroll
+            for (int u = 0; u < NT; ++u) {
+                rx[u] = (T)((double)xt[u].x - ca.x);
+                ry[u] = (T)((double)xt[u].y - ca.y);
+                rz[u] = (T)((double)xt[u].z - ca.z);
+            }
             for (int jc = 0; jc < ne; jc += CH) {
                 int j = jc + threadIdx.x;
                 __syncthreads();
@@ -486,31 +493,36 @@ __global__ void __launch_bounds__(128) k_leaf_eval(const int* __restrict__ leave
                 }
                 __syncthreads();
                 const int cnt = min(CH, ne - jc);
-#pragma unroll 2
                 for (int k = g; k < cnt; k += G) {
                     V s = s_q[k];
-                    interact<T, YUK, false, DN, false>(rxa - s.x, rya - s.y, rza - s.z, s.w, 0, 0, 0, nxa, nya, nza,
-                                                       kappa, pa, da);
-                    interact<T, YUK, false, DN, false>(rxb - s.x, ryb - s.y, rzb - s.z, s.w, 0, 0, 0, nxb, nyb, nzb,
-                                                       kappa, pb, db);
+#pragma unroll
+                    for (int u = 0; u < NT; ++u)
+                        interact<T, YUK, false, DN, false>(rx[u] - s.x, ry[u] - s.y, rz[u] - s.z, s.w, 0, 0, 0,
+                                                           nx[u], ny[u], nz[u], kappa, pot[u], dn[u]);
                 }
             }
         }
         // combine the G partial sums of each target
         __syncthreads();
-        s_red[0][threadIdx.x] = pa;
-        s_red[0][CH + threadIdx.x] = pb;
-        if (DN) { s_red[1][threadIdx.x] = da; s_red[1][CH + threadIdx.x] = db; }
+#pragma unroll
+        for (int u = 0; u < NT; ++u) {
+            s_red[0][u * CH + threadIdx.x] = pot[u];
+            if (DN) s_red[DN ? 1 : 0][u * CH + threadIdx.x] = dn[u];
+        }
         __syncthreads();
         if (g == 0) {
-            T sa = 0, sb2 = 0, ea = 0, eb = 0;
-            for (int q = 0; q < G; ++q) {
-                sa += s_red[0][tloc + q * slots];
-                sb2 += s_red[0][CH + tloc + q * slots];
-                if (DN) { ea += s_red[1][tloc + q * slots]; eb += s_red[1][CH + tloc + q * slots]; }
+#pragma unroll
+            for (int u = 0; u < NT; ++u) {
+                T sp = 0, sd = 0;
+                for (int q = 0; q < G; ++q) {
+                    sp += s_red[0][u * CH + tloc + q * slots];
+                    if (DN) sd += s_red[DN ? 1 : 0][u * CH + tloc + q * slots];
+                }
+                if (vt[u]) {
+                    pot_out[ti[u]] = sp * T(kInv4PiD);
+                    if (DN) dn_out[ti[u]] = sd * T(kInv4PiD);
+                }
             }
-            if (va) { pot_out[ta] = sa * T(kInv4PiD); if (DN) dn_out[ta] = ea * T(kInv4PiD); }
-            if (vb) { pot_out[tb2] = sb2 * T(kInv4PiD); if (DN) dn_out[tb2] = eb * T(kInv4PiD); }
         }
     }
 }
@@ -616,7 +628,8 @@ static void launch_leaf(cudaStream_t st, fmm_tree* Tr, Work<T>& W, const Operato
     const float4* tpos = Tr->same ? Tr->pos_s.p : Tr->pos_t.p;
     const int* tb = Tr->same ? Tr->sb.p : Tr->tb.p;
     const int* te = Tr->same ? Tr->se.p : Tr->te.p;
-    k_leaf_eval<T, YUK, DL, DN><<<Tr->n_tleaf, 128, 0, st>>>(
+    constexpr int NT = std::is_same<T, float>::value ? 4 : 2;
+    k_leaf_eval<T, YUK, DL, DN, NT><<<Tr->n_tleaf, 128, 0, st>>>(
         Tr->leaf_ids.p, Tr->n_tleaf, tb, te, Tr->sb.p, Tr->se.p, Tr->U_off.p, Tr->U_ids.p, Tr->W_off.p, Tr->W_ids.p,
         Tr->level.p, Tr->center.p, tpos, W.tn.p, W.sq.p, W.sm.p, W.Qu.p, W.Qd.p, (const float4*)O.surf_f.p, O.ne, O.npad, kappa,
         W.pot.p, W.dn.p);
