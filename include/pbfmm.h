@@ -102,6 +102,21 @@ enum {
     PB_PH_LAUNCHES = 100
 };
 int pb_profile(pb_ctx* ctx, int enable);
+
+/* Context options.
+ *   PB_OPT_COUPLING       0 (default): charge -> surface right-hand side,
+ *                         surface -> charge reaction potential and the
+ *                         adjoint right-hand side by direct FP64 sums when
+ *                         atoms x quadrature points <= 4e9, else by the FMM
+ *                         (trees over atoms and quadrature points, order p
+ *                         of the mesh); 1: always direct; 2: always FMM.
+ *   PB_OPT_DETERMINISTIC  0 (default): tensor-core M2L/M2M/L2L with row
+ *                         reductions (summation order run-dependent at
+ *                         ~1e-7); 1: CUDA-core kernels with a fixed order,
+ *                         bitwise reproducible results.
+ * Errors: PB_EINVAL for an unknown option or value. */
+enum { PB_OPT_COUPLING = 1, PB_OPT_DETERMINISTIC = 2 };
+int pb_set_option(pb_ctx* ctx, int option, int value);
 int pb_profile_read(pb_ctx* ctx, int phase, double* ms, int64_t* calls);
 
 /* ------------------------------------------------------------------------ */

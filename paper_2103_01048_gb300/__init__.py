@@ -50,6 +50,7 @@ _sig("pb_destroy", [_P])
 _sig("pb_last_error", [_P], ctypes.c_char_p)
 _sig("pb_sync", [_P])
 _sig("pb_profile", [_P, ctypes.c_int])
+_sig("pb_set_option", [_P, ctypes.c_int, ctypes.c_int])
 _sig("pb_profile_read", [_P, ctypes.c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_I64)])
 _sig("fmm_tree_build", [_P, _P, _I64, _P, _I64, ctypes.c_int, ctypes.POINTER(_P)])
 _sig("fmm_tree_destroy", [_P])
@@ -94,7 +95,8 @@ def lib_path():
 
 def exported_symbols():
     """Names this binding resolves in the library."""
-    return ["pb_create", "pb_destroy", "pb_last_error", "pb_sync", "pb_profile", "pb_profile_read", "fmm_tree_build", "fmm_tree_destroy",
+    return ["pb_create", "pb_destroy", "pb_last_error", "pb_sync", "pb_profile", "pb_profile_read", "pb_set_option",
+            "fmm_tree_build", "fmm_tree_destroy",
             "fmm_tree_info", "fmm_tree_export_points", "fmm_tree_export_boxes", "fmm_tree_export_list",
             "fmm_apply", "pb_mesh_setup", "pb_mesh_destroy", "pb_mesh_info", "pb_mesh_export_singular",
             "pb_mesh_matvec", "pb_solve", "pb_result_destroy", "pb_result_get", "pb_solvation_energy",
@@ -141,6 +143,13 @@ def pb_sync(ctx):
 
 PHASES = ["gather", "p2m", "m2m", "p2l", "m2l", "down", "leaf", "scatter", "bem", "gmres"]
 PB_PH_LAUNCHES = 100
+
+
+PB_OPT_COUPLING, PB_OPT_DETERMINISTIC = 1, 2
+
+
+def pb_set_option(ctx, option, value):
+    _check(_lib.pb_set_option(ctx, int(option), int(value)), ctx)
 
 
 def pb_profile(ctx, enable=True):

@@ -105,6 +105,27 @@ __global__ void k_adj_rhs(int nt, int nq, const double* __restrict__ qp, const d
     c[nt + i] = (-d12 * cphi + d11 * cdphi) / det;
 }
 
+// the same right-hand side from FMM outputs at the quadrature points:
+// pot = sum_k q_k g(x_a, r_k), dn = its n_a-derivative (charges as sources)
+__global__ void k_adj_rhs_fmm(int nt, int nq, const double* __restrict__ qw, const float* __restrict__ pot,
+                              const float* __restrict__ dn, double qscale, const int* __restrict__ adj_off,
+                              const int* __restrict__ adj_ids, const double* __restrict__ S,
+                              const double* __restrict__ area, double er, double* __restrict__ c) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= nt) return;
+    double cphi = 0.0, cdphi = 0.0;
+    for (int a = 0; a < nq; ++a) {
+        long long pa = (long long)i * nq + a;
+        cdphi += qw[pa] * (double)pot[pa] * qscale;
+        cphi -= qw[pa] * (double)dn[pa] * qscale;
+    }
+    double d11, d12, d21, d22;
+    diag_block(i, adj_off, adj_ids, S, area, er, d11, d12, d21, d22);
+    double det = d11 * d22 - d12 * d21;
+    c[i] = (d22 * cphi - d21 * cdphi) / det;
+    c[nt + i] = (-d12 * cphi + d11 * cdphi) / det;
+}
+
 template <typename T>
 __global__ void k_p1_adj(int nt, int nq, const double* __restrict__ lam, const T* __restrict__ qw, T* mL, T* mY) {
     long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -270,6 +291,9 @@ void adjoint_matvec(pb_mesh* M, const pb_result* R, const double* lam, double* y
     else adj_matvec_t<float>(M, R, lam, y);
 }
 
+bool use_fmm_coupling(const pb_mesh* M, const pb_result* R);
+void ensure_coupling_trees(pb_mesh* M, pb_result* R);
+
 int energy_gradient(pb_result* R, double tol, int max_iter, double* dEdq_host, double* dEdx_host) {
     pb_mesh* M = R->mesh;
     cudaStream_t st = M->ctx->stream;
@@ -279,7 +303,19 @@ int energy_gradient(pb_result* R, double tol, int max_iter, double* dEdq_host, d
     const long long np = (long long)nt * nq;
     DBuf<double> c, gq, gx;
     c.alloc(2 * nt, st);
-    {
+    if (use_fmm_coupling(M, R)) {
+        // charges (scaled by 1/eps1 in q_f; undone below) -> potential and
+        // normal derivative at the quadrature points
+        ensure_coupling_trees(M, R);
+        DBuf<float> pot, dn;
+        pot.alloc(np, st); dn.alloc(np, st);
+        fmm_apply_impl(R->tree_aq, FMM_LAPLACE, 0.0, M->p, PB_MIXED, R->q_f.p, nullptr, nullptr, M->qn_f.p, pot.p,
+                       dn.p);
+        PhaseTimer ph(M->ctx, PB_PH_BEM);
+        k_adj_rhs_fmm<<<div_up(nt, 128), 128, 0, st>>>(nt, nq, M->qw_d.p, pot.p, dn.p, R->eps_in, M->adj_off.p,
+                                                       M->adj_ids.p, M->S_d.p, M->area.p, R->eps_in / R->eps_out, c.p);
+        PB_CHECK_LAUNCH();
+    } else {
         PhaseTimer ph(M->ctx, PB_PH_BEM);
         k_adj_rhs<<<div_up(nt, 128), 128, 0, st>>>(nt, nq, M->qp_d.p, M->qn_d.p, M->qw_d.p, (int)R->na,
                                                    (const double4*)R->atoms.p, M->adj_off.p, M->adj_ids.p, M->S_d.p,

@@ -42,6 +42,7 @@ __global__ void k_set_g0(const double* nrm2, double* g);
 __global__ void k_vadd(int n, const double* a, double* b);
 
 constexpr int kDotBlocksB = 304;
+void coulomb_at_points(pb_mesh* M, pb_result* R, double* f);
 
 struct BatchSystem {
     pb_mesh* M = nullptr;
@@ -123,9 +124,7 @@ void solve_batch(pb_ctx* ctx, pb_mesh* const* meshes, int nsys, pb_result** resu
         S->xin.zero(main);
         R->x.alloc(S->n, main);
         R->x.zero(main);
-        k_coulomb<<<div_up(np, 256), 256, 0, main>>>(np, M->qp_d.p, (int)R->na, (const double4*)R->atoms.p,
-                                                     1.0 / R->eps_in, S->f.p);
-        PB_CHECK_LAUNCH();
+        coulomb_at_points(M, R, S->f.p);
         k_rhs<<<div_up(nt, 128), 128, 0, main>>>(nt, nq, S->f.p, M->qw_d.p, M->adj_off.p, M->adj_ids.p, M->S_d.p,
                                                  M->area.p, R->eps_in / R->eps_out, 1, S->b.p);
         PB_CHECK_LAUNCH();

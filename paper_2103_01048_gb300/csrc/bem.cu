@@ -832,6 +832,118 @@ int gmres(pb_mesh* M, const std::function<void(const double*, double*)>& matvec,
     return status;
 }
 
+// ---------------------------------------------------------------------------
+// charge <-> surface couplings through the FMM (large atom counts)
+// ---------------------------------------------------------------------------
+__global__ void k_atoms_split(int na, const double4* __restrict__ atoms, double qscale, float* __restrict__ xyz,
+                              float* __restrict__ qf, double* __restrict__ qd) {
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= na) return;
+    double4 a = atoms[k];
+    xyz[3 * k] = (float)a.x; xyz[3 * k + 1] = (float)a.y; xyz[3 * k + 2] = (float)a.z;
+    qf[k] = (float)(a.w * qscale);
+    qd[k] = a.w * qscale;
+}
+
+// surface densities of the reaction potential: monopole w dphi, dipole -w phi
+template <typename T>
+__global__ void k_reac_densities(long long np, int nq, int nt, const double* __restrict__ qw,
+                                 const double* __restrict__ x, T* __restrict__ mono, T* __restrict__ dip) {
+    long long b = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (b >= np) return;
+    int t = (int)(b / nq);
+    mono[b] = (T)(qw[b] * x[nt + t]);
+    dip[b] = (T)(-qw[b] * x[t]);
+}
+
+template <typename T>
+__global__ void k_to_double(long long n, const T* __restrict__ a, double* __restrict__ b) {
+    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i < n) b[i] = (double)a[i];
+}
+
+bool use_fmm_coupling(const pb_mesh* M, const pb_result* R) {
+    const int mode = M->ctx->coupling;
+    if (mode == 1) return false;
+    if (mode == 2) return true;
+    return (double)R->na * (double)M->nt * M->nq > 4e9;
+}
+
+// the two coupling trees of a result (atoms as targets / as sources)
+void ensure_coupling_trees(pb_mesh* M, pb_result* R) {
+    if (R->tree_qa) return;
+    cudaStream_t st = M->ctx->stream;
+    const long long np = M->nt * M->nq;
+    R->atoms_f.alloc(3 * R->na, st);
+    R->q_f.alloc(R->na, st);
+    R->q_d.alloc(R->na, st);
+    k_atoms_split<<<div_up(R->na, 128), 128, 0, st>>>((int)R->na, (const double4*)R->atoms.p, 1.0 / R->eps_in,
+                                                      R->atoms_f.p, R->q_f.p, R->q_d.p);
+    PB_CHECK_LAUNCH();
+    R->tree_qa = new fmm_tree();       // sources = quadrature points, targets = atoms
+    R->tree_qa->ctx = M->ctx;
+    R->tree_qa->ns = np; R->tree_qa->nt = R->na; R->tree_qa->same = false; R->tree_qa->ncrit = M->ncrit;
+    build_tree(R->tree_qa, M->qp_f.p, R->atoms_f.p);
+    R->tree_aq = new fmm_tree();       // sources = atoms, targets = quadrature points
+    R->tree_aq->ctx = M->ctx;
+    R->tree_aq->ns = R->na; R->tree_aq->nt = np; R->tree_aq->same = false; R->tree_aq->ncrit = M->ncrit;
+    build_tree(R->tree_aq, R->atoms_f.p, M->qp_f.p);
+}
+
+// f(x_a) = sum_k q_k / (4 pi eps1 |x_a - r_k|) at every quadrature point
+void coulomb_at_points(pb_mesh* M, pb_result* R, double* f) {
+    cudaStream_t st = M->ctx->stream;
+    const long long np = M->nt * M->nq;
+    if (!use_fmm_coupling(M, R)) {
+        k_coulomb<<<div_up(np, 256), 256, 0, st>>>(np, M->qp_d.p, (int)R->na, (const double4*)R->atoms.p,
+                                                   1.0 / R->eps_in, f);
+        PB_CHECK_LAUNCH();
+        return;
+    }
+    ensure_coupling_trees(M, R);
+    if (R->precision == PB_FP64) {
+        fmm_apply_impl(R->tree_aq, FMM_LAPLACE, 0.0, M->p, PB_FP64, R->q_d.p, nullptr, nullptr, nullptr, f, nullptr);
+    } else {
+        DBuf<float> ff;
+        ff.alloc(np, st);
+        fmm_apply_impl(R->tree_aq, FMM_LAPLACE, 0.0, M->p, PB_MIXED, R->q_f.p, nullptr, nullptr, nullptr, ff.p,
+                       nullptr);
+        k_to_double<float><<<div_up(np, 256), 256, 0, st>>>(np, ff.p, f);
+        PB_CHECK_LAUNCH();
+    }
+}
+
+// phi_reac at every atom (Eq. phi_reac)
+static void reaction_potential(pb_mesh* M, pb_result* R, double* phir) {
+    cudaStream_t st = M->ctx->stream;
+    const int nt = (int)M->nt, nq = M->nq;
+    const long long np = (long long)nt * nq;
+    if (!use_fmm_coupling(M, R)) {
+        k_phi_reac<<<div_up(R->na, 128), 128, 0, st>>>((int)R->na, (const double4*)R->atoms.p, np, nq, nt,
+                                                      M->qp_d.p, M->qn_d.p, M->qw_d.p, R->x.p, phir);
+        PB_CHECK_LAUNCH();
+        return;
+    }
+    ensure_coupling_trees(M, R);
+    if (R->precision == PB_FP64) {
+        DBuf<double> mono, dip;
+        mono.alloc(np, st); dip.alloc(np, st);
+        k_reac_densities<double><<<div_up(np, 256), 256, 0, st>>>(np, nq, nt, M->qw_d.p, R->x.p, mono.p, dip.p);
+        PB_CHECK_LAUNCH();
+        fmm_apply_impl(R->tree_qa, FMM_LAPLACE, 0.0, M->p, PB_FP64, mono.p, dip.p, M->qn_d.p, nullptr, phir,
+                       nullptr);
+    } else {
+        DBuf<float> mono, dip, pf;
+        mono.alloc(np, st); dip.alloc(np, st); pf.alloc(R->na, st);
+        k_reac_densities<float><<<div_up(np, 256), 256, 0, st>>>(np, nq, nt, M->qw_d.p, R->x.p, mono.p, dip.p);
+        PB_CHECK_LAUNCH();
+        fmm_apply_impl(R->tree_qa, FMM_LAPLACE, 0.0, M->p, PB_MIXED, mono.p, dip.p, M->qn_f.p, nullptr, pf.p,
+                       nullptr);
+        k_to_double<float><<<div_up(R->na, 256), 256, 0, st>>>(R->na, pf.p, phir);
+        PB_CHECK_LAUNCH();
+    }
+}
+
 int solve(pb_mesh* M, pb_result* R, double tol, int max_iter) {
     cudaStream_t st = M->ctx->stream;
     ensure_singular(M, R->kappa);
@@ -842,9 +954,7 @@ int solve(pb_mesh* M, pb_result* R, double tol, int max_iter) {
     b.alloc(2 * nt, st);
     {
         PhaseTimer ph(M->ctx, PB_PH_BEM);
-        k_coulomb<<<div_up(np, 256), 256, 0, st>>>(np, M->qp_d.p, (int)R->na, (const double4*)R->atoms.p,
-                                                   1.0 / R->eps_in, f.p);
-        PB_CHECK_LAUNCH();
+        coulomb_at_points(M, R, f.p);
         k_rhs<<<div_up(nt, 128), 128, 0, st>>>(nt, nq, f.p, M->qw_d.p, M->adj_off.p, M->adj_ids.p, M->S_d.p,
                                                M->area.p, R->eps_in / R->eps_out, 1, b.p);
         PB_CHECK_LAUNCH();
@@ -866,9 +976,8 @@ void reaction_energy(pb_result* R, double* phir_host, double* dG) {
     phir.alloc(std::max<int64_t>(R->na, 1), st);
     e.alloc(1, st);
     PhaseTimer ph(M->ctx, PB_PH_BEM);
-    k_phi_reac<<<div_up(R->na, 128), 128, 0, st>>>((int)R->na, (const double4*)R->atoms.p, np, nq, nt, M->qp_d.p,
-                                                  M->qn_d.p, M->qw_d.p, R->x.p, phir.p);
-    PB_CHECK_LAUNCH();
+    (void)np;
+    reaction_potential(M, R, phir.p);
     k_energy<<<1, 1024, 0, st>>>((int)R->na, (const double4*)R->atoms.p, phir.p, e.p);
     PB_CHECK_LAUNCH();
     if (phir_host) PB_CUDA(cudaMemcpyAsync(phir_host, phir.p, R->na * sizeof(double), cudaMemcpyDeviceToHost, st));

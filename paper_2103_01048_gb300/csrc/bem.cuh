@@ -49,6 +49,15 @@ struct pb_result {
     pbfmm::DBuf<double> atoms, charges;
     double energy = 0.0;
     bool have_energy = false;
+    // charge <-> surface couplings through the FMM (large atom counts)
+    fmm_tree* tree_qa = nullptr;      // sources = quadrature points, targets = atoms
+    fmm_tree* tree_aq = nullptr;      // sources = atoms, targets = quadrature points
+    pbfmm::DBuf<float> atoms_f, q_f;  // atom positions [na][3], charges / eps1
+    pbfmm::DBuf<double> q_d;
+    ~pb_result() {
+        delete tree_qa;
+        delete tree_aq;
+    }
     // adjoint solve (gradients)
     pbfmm::DBuf<double> lambda;       // [2 nt]
     int adj_iterations = 0;

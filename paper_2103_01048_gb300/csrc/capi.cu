@@ -169,6 +169,14 @@ int pb_profile(pb_ctx* ctx, int enable) {
     PB_API_END(ctx)
 }
 
+int pb_set_option(pb_ctx* ctx, int option, int value) {
+    if (!ctx) return PB_EINVAL;
+    if (option == PB_OPT_COUPLING && value >= 0 && value <= 2) { ctx->coupling = value; return PB_OK; }
+    if (option == PB_OPT_DETERMINISTIC && (value == 0 || value == 1)) { ctx->deterministic = value; return PB_OK; }
+    ctx->last_error = "pb_set_option: unknown option or value";
+    return PB_EINVAL;
+}
+
 int pb_profile_read(pb_ctx* ctx, int phase, double* ms, int64_t* calls) {
     if (!ctx) return PB_EINVAL;
     PB_API_BEGIN

@@ -112,6 +112,9 @@ struct pb_ctx {
     // device-side error flag of kernels with bounded waits (0 = fine); read
     // and cleared by the next synchronising call, reported as PB_ETIMEOUT
     int* dev_err = nullptr;
+    // options (pb_set_option)
+    int coupling = 0;          // 0 auto, 1 direct sums, 2 FMM
+    int deterministic = 0;     // 1: no run-dependent reductions (SIMT M2L/M2M/L2L)
 };
 
 namespace pbfmm {

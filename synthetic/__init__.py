@@ -289,3 +289,72 @@ def binding_complex(n_rec, n_lig, seed=0, gap=4.5, spacing=0.7):
     out["surf"] = {k: gaussian_surface(v[0], v[1], spacing) for k, v in
                    (("rec", out["rec"]), ("lig", out["lig"]), ("cplx", out["cplx"]))}
     return out
+
+
+def cube_sphere(n, radius, outward=True, amp=0.0, seed=0):
+    """Closed triangulated sphere from a cube with n x n cells per face,
+    vertices projected radially (welded along the cube edges), radius
+    modulated by 1 + amp * f(u) with the bump field of bumpy_sphere_points.
+    12 n^2 triangles; normals point away from the centre if `outward`, else
+    towards it.  Returns (verts float64 [nv,3], tris int32 [nt,3])."""
+    g = np.arange(n + 1)
+    I, J = np.meshgrid(g, g, indexing="ij")
+    I = I.ravel(); J = J.ravel()
+    faces_v = []
+    for axis in range(3):
+        for side in (0, n):
+            v = np.zeros((len(I), 3), dtype=np.int64)
+            a1, a2 = [a for a in range(3) if a != axis]
+            v[:, axis] = side
+            v[:, a1] = I
+            v[:, a2] = J
+            faces_v.append(v)
+    allv = np.concatenate(faces_v)
+    uniq, inv = np.unique(allv, axis=0, return_inverse=True)
+    inv = inv.ravel()
+    tris = []
+    base = 0
+    m = n + 1
+    for f in range(6):
+        idx = inv[base:base + m * m].reshape(m, m)
+        a = idx[:-1, :-1].ravel(); b = idx[1:, :-1].ravel()
+        c = idx[1:, 1:].ravel(); d = idx[:-1, 1:].ravel()
+        tris.append(np.stack([a, b, c], axis=1))
+        tris.append(np.stack([a, c, d], axis=1))
+        base += m * m
+    T = np.concatenate(tris).astype(np.int64)
+    P = uniq.astype(np.float64) * (2.0 / n) - 1.0
+    u = P / np.linalg.norm(P, axis=1, keepdims=True)
+    r = np.full(len(u), float(radius))
+    if amp:
+        rng = np.random.default_rng(seed)
+        c = rng.standard_normal((32, 3))
+        c /= np.linalg.norm(c, axis=1, keepdims=True)
+        w = rng.uniform(-1.0, 1.0, 32)
+        fb = np.zeros(len(u))
+        for k in range(32):
+            fb += w[k] * np.exp(-((u - c[k]) ** 2).sum(axis=1) / (2 * 0.3 * 0.3))
+        fb /= np.abs(fb).max()
+        r = r * (1.0 + amp * fb)
+    V = u * r[:, None]
+    # orient every triangle consistently
+    p0, p1, p2 = V[T[:, 0]], V[T[:, 1]], V[T[:, 2]]
+    s = (np.cross(p1 - p0, p2 - p0) * (p0 + p1 + p2)).sum(axis=1)
+    flip = (s < 0) if outward else (s > 0)
+    T[flip] = T[flip][:, [0, 2, 1]]
+    return np.ascontiguousarray(V), np.ascontiguousarray(T.astype(np.int32))
+
+
+def virus_shell(n_atoms=1_600_000, r_in=230.0, r_out=270.0, n_face=645, seed=7):
+    """Virus-scale capsid stand-in: atoms on a jittered FCC lattice in the
+    shell r_in + 2 <= rho <= r_out - 2 (radii U[1.2, 2], charges U[-0.8, 0.8],
+    zero net charge) inside a two-component closed surface: the outer wall at
+    r_out (normals outward) and the inner wall at r_in (normals towards the
+    centre, i.e. out of the solute), each a cube sphere of 12 n_face^2
+    triangles with a 0.4% bump.  Returns (verts, tris, xyz, radii, q)."""
+    xyz, radii, q = fcc_ball_atoms(n_atoms, r_out, 2.85, 0.1, seed=seed, shell=(r_in + 2.0, r_out - 2.0))
+    Vo, To = cube_sphere(n_face, r_out, outward=True, amp=0.004, seed=seed + 1)
+    Vi, Ti = cube_sphere(n_face, r_in, outward=False, amp=0.004, seed=seed + 2)
+    V = np.concatenate([Vo, Vi])
+    T = np.concatenate([To, Ti + len(Vo)]).astype(np.int32)
+    return V, T, xyz, radii, q
