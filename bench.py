@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-solve", action="store_true")
     ap.add_argument("--virus", action="store_true", help="virus-scale shell solve only (10M triangles, 1.6M atoms)")
+    ap.add_argument("--virus-face", type=int, default=645, help="cube-sphere subdivision (12 n^2 triangles per wall)")
+    ap.add_argument("--virus-atoms", type=int, default=1_600_000)
     return ap.parse_args()
 
 
@@ -170,21 +172,31 @@ def run_virus(args):
     import torch
     import paper_2103_01048_gb300 as pb
     import synthetic
-    t0 = time.perf_counter()
-    V, T, xyz, radii, q = synthetic.virus_shell()
+    def note(msg):
+        print(f"[virus {time.perf_counter() - t_start:8.1f} s] {msg}", file=sys.stderr, flush=True)
+
+    t_start = t0 = time.perf_counter()
+    V, T, xyz, radii, q = synthetic.virus_shell(n_atoms=args.virus_atoms, n_face=args.virus_face)
     t_gen = time.perf_counter() - t0
+    note(f"generated {len(T)} triangles, {len(q)} atoms")
     ctx = pb.pb_create(0, None)
     free0, total = torch.cuda.mem_get_info()
+    pb.pb_profile(ctx, True)
     t0 = time.perf_counter()
     mesh = pb.pb_mesh_setup(ctx, V, T, 3, 4, 128)
     nt = len(T)
     x = np.zeros(2 * nt)
     y = np.zeros(2 * nt)
+    note("mesh set up")
     pb.pb_mesh_matvec(ctx, mesh, x, y, 4.0, 80.0, 0.125)        # assembles S, builds the operators
     t_setup = time.perf_counter() - t0
+    setup_prof = pb.pb_profile_read(ctx)
+    pb.pb_profile(ctx, False)
+    note(f"singular entries + operators + first mat-vec: {t_setup:.1f} s")
     t0 = time.perf_counter()
     res, st = pb.pb_solve(ctx, mesh, xyz, q, 4.0, 80.0, 0.125, 1e-4, 300)
     t_solve = time.perf_counter() - t0
+    note(f"solve: {t_solve:.1f} s")
     t0 = time.perf_counter()
     e = pb.pb_solvation_energy(ctx, res)
     t_energy = time.perf_counter() - t0
@@ -193,7 +205,10 @@ def run_virus(args):
     line = {"metric": "PB solve s per mesh (virus-scale shell)", "value": t_solve + t_energy, "unit": "s",
             "higher_is_better": False, "n_gpus": 1, "dtype": "f32 FMM / f64 GMRES", "data": "synthetic",
             "config": {"workload": f"virus-scale shell: {len(q)} atoms, {nt} triangles ({3 * nt} quadrature "
-                                   f"points), two cube-sphere walls r=230/270 A, p=4, ncrit=128, tol 1e-4"},
+                                   f"points), two cube-sphere walls r=230/270 A, p=4, ncrit=128, tol 1e-4",
+                       "singular_rule": "FP64 5-level" if nt <= 262144 else "FP32 4-level"},
+            "setup_profile_ms": {k: round(v[0], 1) for k, v in setup_prof.items()
+                                 if k != "launches" and v[0] > 0},
             "status": int(st), "iterations": it, "residual": rr, "dG_kcal_mol": e,
             "setup_s": t_setup, "solve_s": t_solve, "energy_s": t_energy, "generate_s": t_gen,
             "ms_per_gmres_iteration": 1e3 * t_solve / max(it, 1),

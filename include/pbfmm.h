@@ -114,8 +114,13 @@ int pb_profile(pb_ctx* ctx, int enable);
  *                         reductions (summation order run-dependent at
  *                         ~1e-7); 1: CUDA-core kernels with a fixed order,
  *                         bitwise reproducible results.
+ *   PB_OPT_SINGULAR       singular Galerkin entries of vertex-sharing pairs
+ *                         (analytic inner integrals, graded outer rule):
+ *                         0 (default): FP64 with a 5-level graded rule up to
+ *                         262,144 triangles, else FP32 with a 4-level rule;
+ *                         1: always FP64; 2: always FP32.
  * Errors: PB_EINVAL for an unknown option or value. */
-enum { PB_OPT_COUPLING = 1, PB_OPT_DETERMINISTIC = 2 };
+enum { PB_OPT_COUPLING = 1, PB_OPT_DETERMINISTIC = 2, PB_OPT_SINGULAR = 3 };
 int pb_set_option(pb_ctx* ctx, int option, int value);
 int pb_profile_read(pb_ctx* ctx, int phase, double* ms, int64_t* calls);
 

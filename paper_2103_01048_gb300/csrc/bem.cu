@@ -76,9 +76,12 @@ static void gauss01(int n, std::vector<double>& x, std::vector<double>& w) {
 }
 
 // collapsed Gauss rule on the reference triangle (l1, l2, weight), weights sum to 1
-constexpr int kSingOuterN = 4, kSingInnerN = 4, kSingDepth = 5;
-__constant__ double c_out_l[kSingOuterN * kSingOuterN][3];
-__constant__ double c_in_l[kSingInnerN * kSingInnerN][3];
+// singular entries: 4x4 collapsed rules; the singular part of the outer rule
+// is graded 5 levels deep in FP64 and 4 in FP32, the smooth Yukawa remainder
+// 2 levels; FP64 up to kSingFp64MaxTris triangles unless chosen otherwise
+constexpr int kSingOuterN = 4, kSingInnerN = 4;
+constexpr int kSingDepth64 = 5, kSingDepth32 = 4, kSingRemDepth = 2;
+constexpr long long kSingFp64MaxTris = 262144;
 
 static void collapsed_rule(int n, std::vector<double>& out) {
     std::vector<double> x, w;
@@ -180,128 +183,171 @@ __global__ void k_adjacency(int nt, const int* F, const int* voff, const int* vi
 // Wilton et al. 1984) and for (x-y).n/r^3 (solid angle, Van Oosterom &
 // Strackee 1983); bounded Yukawa remainders by a collapsed Gauss rule.
 // Outer integral: collapsed Gauss rule on a subdivision of T_i refined
-// geometrically toward the edges of T_j, kSingDepth levels deep.
+// geometrically toward the part of T_i that T_j shares (its whole boundary,
+// the common edge or the common vertex). That part depends only on which
+// local vertices the two triangles share, so the graded outer rules of the
+// eight sharing patterns are built once on the host in the reference frame
+// of T_i (x = v0 + l1 (v1 - v0) + l2 (v2 - v0)) and every pair reads its
+// pattern's points. The smooth Yukawa remainder takes a shallower rule.
 // ---------------------------------------------------------------------------
-struct D3 { double x, y, z; };
-__device__ __forceinline__ D3 operator-(D3 a, D3 b) { return {a.x - b.x, a.y - b.y, a.z - b.z}; }
-__device__ __forceinline__ D3 operator+(D3 a, D3 b) { return {a.x + b.x, a.y + b.y, a.z + b.z}; }
-__device__ __forceinline__ D3 operator*(double s, D3 a) { return {s * a.x, s * a.y, s * a.z}; }
-__device__ __forceinline__ double dot(D3 a, D3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
-__device__ __forceinline__ D3 cross(D3 a, D3 b) { return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x}; }
-__device__ __forceinline__ double len(D3 a) { return sqrt(dot(a, a)); }
+template <typename T> struct V3 { T x, y, z; };
+template <typename T> __device__ __forceinline__ V3<T> operator-(V3<T> a, V3<T> b) { return {a.x - b.x, a.y - b.y, a.z - b.z}; }
+template <typename T> __device__ __forceinline__ V3<T> operator+(V3<T> a, V3<T> b) { return {a.x + b.x, a.y + b.y, a.z + b.z}; }
+template <typename T> __device__ __forceinline__ V3<T> operator*(T s, V3<T> a) { return {s * a.x, s * a.y, s * a.z}; }
+template <typename T> __device__ __forceinline__ T dot(V3<T> a, V3<T> b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+template <typename T> __device__ __forceinline__ V3<T> cross(V3<T> a, V3<T> b) {
+    return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
+}
+template <typename T> __device__ __forceinline__ T len(V3<T> a) { return sqrt(dot(a, a)); }
 
 // int_T 1/|x-y| dA_y
-__device__ double pot_uniform_triangle(D3 x, const D3* v) {
-    D3 n = cross(v[1] - v[0], v[2] - v[0]);
-    n = (1.0 / len(n)) * n;
-    double h = dot(x - v[0], n);
-    double ah = fabs(h);
-    D3 xp = x - h * n;                       // projection on the plane
-    double scale = len(v[1] - v[0]) + len(v[2] - v[0]);
-    double total = 0.0;
+template <typename T>
+__device__ T pot_uniform_triangle(V3<T> x, const V3<T>* v) {
+    const T skip = sizeof(T) == 8 ? T(1e-14) : T(1e-7);
+    V3<T> n = cross(v[1] - v[0], v[2] - v[0]);
+    n = (T(1) / len(n)) * n;
+    T h = dot(x - v[0], n);
+    T ah = fabs(h);
+    V3<T> xp = x - h * n;                    // projection on the plane
+    T scale = len(v[1] - v[0]) + len(v[2] - v[0]);
+    T total = 0;
     for (int e = 0; e < 3; ++e) {
-        D3 p = v[e], q = v[(e + 1) % 3];
-        D3 t = q - p;
-        t = (1.0 / len(t)) * t;
-        D3 m = cross(t, n);                   // in-plane, outward
-        double d0 = dot(p - xp, m);           // signed distance to the edge line
-        if (fabs(d0) <= 1e-14 * scale) continue;
-        double s0 = dot(p - xp, t), s1 = dot(q - xp, t);
-        double r0 = len(x - p), r1 = len(x - q);
-        double w2 = d0 * d0 + h * h;
-        double f1 = s1 >= 0 ? r1 + s1 : w2 / (r1 - s1);
-        double f0 = s0 >= 0 ? r0 + s0 : w2 / (r0 - s0);
+        V3<T> p = v[e], q = v[(e + 1) % 3];
+        V3<T> t = q - p;
+        t = (T(1) / len(t)) * t;
+        V3<T> m = cross(t, n);                // in-plane, outward
+        T d0 = dot(p - xp, m);                // signed distance to the edge line
+        if (fabs(d0) <= skip * scale) continue;
+        T s0 = dot(p - xp, t), s1 = dot(q - xp, t);
+        T r0 = len(x - p), r1 = len(x - q);
+        T w2 = d0 * d0 + h * h;
+        T f1 = s1 >= 0 ? r1 + s1 : w2 / (r1 - s1);
+        T f0 = s0 >= 0 ? r0 + s0 : w2 / (r0 - s0);
         total += d0 * log(f1 / f0);
-        if (ah > 0.0) total -= ah * (atan(d0 * s1 / (w2 + ah * r1)) - atan(d0 * s0 / (w2 + ah * r0)));
+        if (ah > 0) total -= ah * (atan(d0 * s1 / (w2 + ah * r1)) - atan(d0 * s0 / (w2 + ah * r0)));
     }
     return total;
 }
 
 // int_T (x-y).n_y/|x-y|^3 dA_y = signed solid angle of T seen from x
-__device__ double solid_angle(D3 x, const D3* v) {
-    D3 a = v[0] - x, b = v[1] - x, c = v[2] - x;
-    double la = len(a), lb = len(b), lc = len(c);
-    double num = dot(a, cross(b, c));
-    double den = la * lb * lc + dot(a, b) * lc + dot(a, c) * lb + dot(b, c) * la;
-    return -2.0 * atan2(num, den);
+template <typename T>
+__device__ T solid_angle(V3<T> x, const V3<T>* v) {
+    V3<T> a = v[0] - x, b = v[1] - x, c = v[2] - x;
+    T la = len(a), lb = len(b), lc = len(c);
+    T num = dot(a, cross(b, c));
+    T den = la * lb * lc + dot(a, b) * lc + dot(a, c) * lb + dot(b, c) * la;
+    return T(-2) * atan2(num, den);
 }
 
-__device__ double dist_point_segment(D3 p, D3 a, D3 b) {
-    D3 ab = b - a;
-    double t = dot(p - a, ab) / dot(ab, ab);
-    t = t < 0 ? 0 : (t > 1 ? 1 : t);
-    return len(a + t * ab - p);
+// g(t) = e^-t (1 + t) - 1: the Yukawa double-layer kernel minus the Laplace
+// one is (x-y).n g(kr) / r^3. Below t = 1/4 the Taylor series
+// sum_{n>=2} (-1)^n (1 - n) t^n / n! avoids the cancellation of the closed form.
+template <typename T>
+__device__ __forceinline__ T yukawa_dl_factor(T t) {
+    if (t < T(0.25)) {
+        T s = T(-1.0 / 43545600.0);
+        s = s * t + T(1.0 / 3991680.0);
+        s = s * t + T(-1.0 / 403200.0);
+        s = s * t + T(1.0 / 45360.0);
+        s = s * t + T(-1.0 / 5760.0);
+        s = s * t + T(1.0 / 840.0);
+        s = s * t + T(-1.0 / 144.0);
+        s = s * t + T(1.0 / 30.0);
+        s = s * t + T(-1.0 / 8.0);
+        s = s * t + T(1.0 / 3.0);
+        s = s * t + T(-0.5);
+        return s * t * t;
+    }
+    return expm1(-t) + t * exp(-t);
 }
 
-struct SubTri { D3 v[3]; int depth; };
+constexpr int kNumPat = 8;     // 0 identical, 1..3 edge (v_k, v_k+1), 4..6 vertex k, 7 none
+struct SingRule {
+    int s_off[kNumPat + 1];    // singular-part outer points of pattern p: [s_off[p], s_off[p+1])
+    int r_off[kNumPat + 1];    // remainder outer points
+    int in_off;                // kSingInnerN^2 inner points of the remainder
+};
 
-__global__ void k_singular(int nt, const double* __restrict__ V, const int* __restrict__ F,
-                           const int* __restrict__ adj_off, const int* __restrict__ adj_ids, double kappa,
-                           double* __restrict__ S) {
-    int i = blockIdx.x;
-    if (i >= nt) return;
-    D3 Ti[3];
-    for (int k = 0; k < 3; ++k) Ti[k] = {V[3 * F[3 * i + k]], V[3 * F[3 * i + k] + 1], V[3 * F[3 * i + k] + 2]};
-    for (int e = adj_off[i] + threadIdx.x; e < adj_off[i + 1]; e += blockDim.x) {
-        int j = adj_ids[e];
-        D3 Tj[3];
-        for (int k = 0; k < 3; ++k) Tj[k] = {V[3 * F[3 * j + k]], V[3 * F[3 * j + k] + 1], V[3 * F[3 * j + k] + 2]};
-        const bool same = (i == j);
-        D3 nj = cross(Tj[1] - Tj[0], Tj[2] - Tj[0]);
-        double aj = 0.5 * len(nj);
-        nj = (1.0 / (2.0 * aj)) * nj;
-        double tol = 1e-10 * sqrt(aj);
-        double vl = 0, kl = 0, vy = 0, ky = 0;
-        SubTri stack[3 * kSingDepth + 2];
-        int sp = 0;
-        stack[sp++] = {{Ti[0], Ti[1], Ti[2]}, 0};
-        while (sp > 0) {
-            SubTri s = stack[--sp];
-            bool touch = false;
-            for (int a = 0; a < 3 && !touch; ++a)
-                for (int ed = 0; ed < 3 && !touch; ++ed)
-                    touch = dist_point_segment(s.v[a], Tj[ed], Tj[(ed + 1) % 3]) < tol;
-            if (touch && s.depth < kSingDepth) {
-                D3 m01 = 0.5 * (s.v[0] + s.v[1]), m12 = 0.5 * (s.v[1] + s.v[2]), m20 = 0.5 * (s.v[2] + s.v[0]);
-                stack[sp++] = {{s.v[0], m01, m20}, s.depth + 1};
-                stack[sp++] = {{m01, s.v[1], m12}, s.depth + 1};
-                stack[sp++] = {{m20, m12, s.v[2]}, s.depth + 1};
-                stack[sp++] = {{m12, m20, m01}, s.depth + 1};
-                continue;
-            }
-            double as = 0.5 * len(cross(s.v[1] - s.v[0], s.v[2] - s.v[0]));
-            for (int k = 0; k < kSingOuterN * kSingOuterN; ++k) {
-                double l1 = c_out_l[k][0], l2 = c_out_l[k][1], w = c_out_l[k][2] * as;
-                D3 x = (1.0 - l1 - l2) * s.v[0] + l1 * s.v[1] + l2 * s.v[2];
-                double sl = pot_uniform_triangle(x, Tj);
-                double dl = same ? 0.0 : solid_angle(x, Tj);
-                double rs = 0.0, rd = 0.0;
-                if (kappa > 0.0) {
-                    for (int m = 0; m < kSingInnerN * kSingInnerN; ++m) {
-                        double m1 = c_in_l[m][0], m2 = c_in_l[m][1], wm = c_in_l[m][2];
-                        D3 y = (1.0 - m1 - m2) * Tj[0] + m1 * Tj[1] + m2 * Tj[2];
-                        D3 d = x - y;
-                        double r = len(d);
-                        double t = kappa * r;
-                        if (r > 1e-300) {
-                            double em1 = expm1(-t);
-                            rs += wm * em1 / r;
-                            rd += wm * dot(d, nj) * (em1 + t * exp(-t)) / (r * r * r);
-                        } else {
-                            rs += wm * (-kappa);
-                        }
+template <typename T>
+__global__ void __launch_bounds__(256) k_singular(long long nadj, int nt, const double* __restrict__ V,
+                                                  const int* __restrict__ F, const int* __restrict__ adj_off,
+                                                  const int* __restrict__ adj_ids, T kappa, SingRule R,
+                                                  const T* __restrict__ pts, double* __restrict__ S) {
+    const int lane = threadIdx.x & 31;
+    const long long nw = (gridDim.x * (long long)blockDim.x) >> 5;
+    for (long long e = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5; e < nadj; e += nw) {
+        int lo = 0, hi = nt;               // row: adj_off[lo] <= e < adj_off[lo + 1]
+        while (hi - lo > 1) {
+            int mid = (lo + hi) >> 1;
+            if (adj_off[mid] <= e) lo = mid; else hi = mid;
+        }
+        const int i = lo, j = adj_ids[e];
+        int fi[3], fj[3];
+        for (int k = 0; k < 3; ++k) { fi[k] = F[3 * i + k]; fj[k] = F[3 * j + k]; }
+        int shared = 0, mask = 0;
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b)
+                if (fi[a] == fj[b]) { ++shared; mask |= 1 << a; }
+        int pat;
+        if (i == j || shared == 3) pat = 0;
+        else if (shared == 2) pat = mask == 3 ? 1 : (mask == 6 ? 2 : 3);   // {0,1}, {1,2}, {2,0}
+        else if (shared == 1) pat = 4 + (mask == 1 ? 0 : (mask == 2 ? 1 : 2));
+        else pat = 7;
+        // local frame at v0 of T_i: differences in FP64, then T
+        const double ox = V[3 * fi[0]], oy = V[3 * fi[0] + 1], oz = V[3 * fi[0] + 2];
+        auto rel = [&](int v) -> V3<T> {
+            return {(T)(V[3 * v] - ox), (T)(V[3 * v + 1] - oy), (T)(V[3 * v + 2] - oz)};
+        };
+        const V3<T> E1 = rel(fi[1]), E2 = rel(fi[2]);
+        V3<T> Tj[3] = {rel(fj[0]), rel(fj[1]), rel(fj[2])};
+        V3<T> nj = cross(Tj[1] - Tj[0], Tj[2] - Tj[0]);
+        const T aj = T(0.5) * len(nj);
+        nj = (T(1) / (T(2) * aj)) * nj;
+        const T ai = T(0.5) * len(cross(E1, E2));
+        const bool same = pat == 0;
+        T vl = 0, kl = 0, rs = 0, rd = 0;
+        for (int k = R.s_off[pat] + lane; k < R.s_off[pat + 1]; k += 32) {
+            const T l1 = pts[3 * k], l2 = pts[3 * k + 1], w = pts[3 * k + 2];
+            const V3<T> x = l1 * E1 + l2 * E2;
+            vl += w * pot_uniform_triangle(x, Tj);
+            if (!same) kl += w * solid_angle(x, Tj);
+        }
+        if (kappa > 0) {
+            for (int k = R.r_off[pat] + lane; k < R.r_off[pat + 1]; k += 32) {
+                const T l1 = pts[3 * k], l2 = pts[3 * k + 1], w = pts[3 * k + 2];
+                const V3<T> x = l1 * E1 + l2 * E2;
+                T s = 0, d = 0;
+                for (int m = 0; m < kSingInnerN * kSingInnerN; ++m) {
+                    const T m1 = pts[3 * (R.in_off + m)], m2 = pts[3 * (R.in_off + m) + 1];
+                    const T wm = pts[3 * (R.in_off + m) + 2];
+                    const V3<T> y = ((T(1) - m1 - m2) * Tj[0]) + (m1 * Tj[1]) + (m2 * Tj[2]);
+                    const V3<T> dv = x - y;
+                    const T r = len(dv);
+                    if (r > (T)1e-30) {
+                        const T t = kappa * r;
+                        s += wm * expm1(-t) / r;
+                        if (!same) d += wm * dot(dv, nj) * yukawa_dl_factor(t) / (r * r * r);
+                    } else {
+                        s -= wm * kappa;
                     }
                 }
-                vl += w * sl;
-                kl += w * dl;
-                vy += w * (sl + aj * rs);
-                ky += w * (same ? 0.0 : dl + aj * rd);
+                rs += w * s;
+                rd += w * d;
             }
         }
-        S[4 * (long long)e + 0] = kInv4PiB * vl;
-        S[4 * (long long)e + 1] = kInv4PiB * kl;
-        S[4 * (long long)e + 2] = kInv4PiB * vy;
-        S[4 * (long long)e + 3] = kInv4PiB * ky;
+        for (int o = 16; o > 0; o >>= 1) {
+            vl += __shfl_xor_sync(0xffffffffu, vl, o);
+            kl += __shfl_xor_sync(0xffffffffu, kl, o);
+            rs += __shfl_xor_sync(0xffffffffu, rs, o);
+            rd += __shfl_xor_sync(0xffffffffu, rd, o);
+        }
+        if (lane == 0) {
+            const double VLi = (double)ai * (double)vl, KLi = same ? 0.0 : (double)ai * (double)kl;
+            S[4 * e + 0] = kInv4PiB * VLi;
+            S[4 * e + 1] = kInv4PiB * KLi;
+            S[4 * e + 2] = kInv4PiB * (VLi + (double)ai * (double)aj * (double)rs);
+            S[4 * e + 3] = kInv4PiB * (same ? 0.0 : KLi + (double)ai * (double)aj * (double)rd);
+        }
     }
 }
 
@@ -613,23 +659,100 @@ __global__ void k_vadd(int n, const double* a, double* b) {
 // ---------------------------------------------------------------------------
 // host side
 // ---------------------------------------------------------------------------
+// Is the reference-frame point (l1, l2) on the part of T_i shared with T_j?
+// Subdivision vertices are dyadic rationals, so the tests are exact.
+static bool on_shared(int pat, double l1, double l2) {
+    switch (pat) {
+    case 0: return l1 == 0.0 || l2 == 0.0 || l1 + l2 == 1.0;   // identical: the boundary
+    case 1: return l2 == 0.0;                                  // edge v0 v1
+    case 2: return l1 + l2 == 1.0;                             // edge v1 v2
+    case 3: return l1 == 0.0;                                  // edge v2 v0
+    case 4: return l1 == 0.0 && l2 == 0.0;                     // vertex v0
+    case 5: return l1 == 1.0 && l2 == 0.0;                     // vertex v1
+    case 6: return l1 == 0.0 && l2 == 1.0;                     // vertex v2
+    default: return false;
+    }
+}
+
+// Graded outer rule of one sharing pattern: leaves of the midpoint subdivision
+// of the reference triangle, split while one of its vertices is on the shared
+// part and fewer than `depth` levels deep, each carrying the collapsed rule
+// scaled by its area fraction. Appends (l1, l2, w) with sum w = 1.
+static void graded_rule(int pat, int depth, const std::vector<double>& rule, std::vector<double>& out) {
+    struct Sub { double v[3][2]; int d; };
+    std::vector<Sub> st{{{{0.0, 0.0}, {1.0, 0.0}, {0.0, 1.0}}, 0}};
+    while (!st.empty()) {
+        Sub s = st.back();
+        st.pop_back();
+        bool touch = false;
+        for (int a = 0; a < 3; ++a) touch = touch || on_shared(pat, s.v[a][0], s.v[a][1]);
+        if (touch && s.d < depth) {
+            double m[3][2];   // midpoints of v0v1, v1v2, v2v0
+            for (int a = 0; a < 3; ++a)
+                for (int c = 0; c < 2; ++c) m[a][c] = 0.5 * (s.v[a][c] + s.v[(a + 1) % 3][c]);
+            auto push = [&](const double* p, const double* q, const double* r) {
+                st.push_back({{{p[0], p[1]}, {q[0], q[1]}, {r[0], r[1]}}, s.d + 1});
+            };
+            push(s.v[0], m[0], m[2]);
+            push(m[0], s.v[1], m[1]);
+            push(m[2], m[1], s.v[2]);
+            push(m[1], m[2], m[0]);
+            continue;
+        }
+        const double e1[2] = {s.v[1][0] - s.v[0][0], s.v[1][1] - s.v[0][1]};
+        const double e2[2] = {s.v[2][0] - s.v[0][0], s.v[2][1] - s.v[0][1]};
+        const double frac = std::fabs(e1[0] * e2[1] - e1[1] * e2[0]);
+        for (size_t k = 0; k < rule.size(); k += 3) {
+            out.push_back(s.v[0][0] + rule[k] * e1[0] + rule[k + 1] * e2[0]);
+            out.push_back(s.v[0][1] + rule[k] * e1[1] + rule[k + 1] * e2[1]);
+            out.push_back(rule[k + 2] * frac);
+        }
+    }
+}
+
 static void ensure_singular(pb_mesh* M, double kappa) {
-    if (M->kappa_S == kappa) return;
+    const int mode = M->ctx->singular ? M->ctx->singular : (M->nt <= kSingFp64MaxTris ? 1 : 2);
+    if (M->kappa_S == kappa && M->sing_mode == mode) return;
     cudaStream_t st = M->ctx->stream;
-    std::vector<double> ro, ri;
+    const int depth = mode == 1 ? kSingDepth64 : kSingDepth32;
+    std::vector<double> ro, ri, pts;
     collapsed_rule(kSingOuterN, ro);
     collapsed_rule(kSingInnerN, ri);
-    PB_CUDA(cudaMemcpyToSymbolAsync(c_out_l, ro.data(), ro.size() * sizeof(double), 0, cudaMemcpyHostToDevice, st));
-    PB_CUDA(cudaMemcpyToSymbolAsync(c_in_l, ri.data(), ri.size() * sizeof(double), 0, cudaMemcpyHostToDevice, st));
+    SingRule R;
+    for (int pat = 0; pat <= kNumPat; ++pat) {
+        R.s_off[pat] = (int)(pts.size() / 3);
+        if (pat < kNumPat) graded_rule(pat, depth, ro, pts);
+    }
+    for (int pat = 0; pat <= kNumPat; ++pat) {
+        R.r_off[pat] = (int)(pts.size() / 3);
+        if (pat < kNumPat) graded_rule(pat, std::min(depth, kSingRemDepth), ro, pts);
+    }
+    R.in_off = (int)(pts.size() / 3);
+    pts.insert(pts.end(), ri.begin(), ri.end());
     M->S_d.alloc(4 * M->nadj, st);
     M->S_f.alloc(4 * M->nadj, st);
     PhaseTimer ph(M->ctx, PB_PH_BEM);
-    k_singular<<<(int)M->nt, 32, 0, st>>>((int)M->nt, M->verts.p, M->tris.p, M->adj_off.p, M->adj_ids.p, kappa,
-                                          M->S_d.p);
-    PB_CHECK_LAUNCH();
+    const int blocks = (int)std::min<long long>(div_up(M->nadj, 8), 152LL * 64);   // 8 warps per block
+    if (mode == 1) {
+        DBuf<double> rule;
+        rule.alloc(pts.size(), st);
+        PB_CUDA(cudaMemcpyAsync(rule.p, pts.data(), pts.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+        k_singular<double><<<blocks, 256, 0, st>>>(M->nadj, (int)M->nt, M->verts.p, M->tris.p, M->adj_off.p,
+                                                   M->adj_ids.p, kappa, R, rule.p, M->S_d.p);
+        PB_CHECK_LAUNCH();
+    } else {
+        std::vector<float> pf(pts.begin(), pts.end());
+        DBuf<float> rule;
+        rule.alloc(pf.size(), st);
+        PB_CUDA(cudaMemcpyAsync(rule.p, pf.data(), pf.size() * sizeof(float), cudaMemcpyHostToDevice, st));
+        k_singular<float><<<blocks, 256, 0, st>>>(M->nadj, (int)M->nt, M->verts.p, M->tris.p, M->adj_off.p,
+                                                  M->adj_ids.p, (float)kappa, R, rule.p, M->S_d.p);
+        PB_CHECK_LAUNCH();
+    }
     k_to_float<<<div_up(4 * M->nadj, 256), 256, 0, st>>>(4 * M->nadj, M->S_d.p, M->S_f.p);
     PB_CHECK_LAUNCH();
     M->kappa_S = kappa;
+    M->sing_mode = mode;
 }
 
 void ensure_singular_public(pb_mesh* M, double kappa) { ensure_singular(M, kappa); }

@@ -23,6 +23,7 @@ struct pb_mesh {
     pbfmm::DBuf<double> S_d;
     pbfmm::DBuf<float> S_f;
     double kappa_S = -1.0;
+    int sing_mode = 0;                // 1: FP64 rule, 2: FP32 rule
     pbfmm::DBuf<int> adj_tr;          // for CSR entry (i, j): the index of entry (j, i)
     fmm_tree* tree = nullptr;
 };

@@ -173,6 +173,7 @@ int pb_set_option(pb_ctx* ctx, int option, int value) {
     if (!ctx) return PB_EINVAL;
     if (option == PB_OPT_COUPLING && value >= 0 && value <= 2) { ctx->coupling = value; return PB_OK; }
     if (option == PB_OPT_DETERMINISTIC && (value == 0 || value == 1)) { ctx->deterministic = value; return PB_OK; }
+    if (option == PB_OPT_SINGULAR && value >= 0 && value <= 2) { ctx->singular = value; return PB_OK; }
     ctx->last_error = "pb_set_option: unknown option or value";
     return PB_EINVAL;
 }

@@ -115,6 +115,7 @@ struct pb_ctx {
     // options (pb_set_option)
     int coupling = 0;          // 0 auto, 1 direct sums, 2 FMM
     int deterministic = 0;     // 1: no run-dependent reductions (SIMT M2L/M2M/L2L)
+    int singular = 0;          // singular entries: 0 auto, 1 FP64 (depth 5), 2 FP32 (depth 4)
 };
 
 namespace pbfmm {
