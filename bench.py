@@ -35,9 +35,13 @@ UNIT = "points/s"
 SM_COUNT = 152
 FP32_LANES = 128
 SM_MAX_MHZ = 2070.0
-# FLOPs per pair (FMA = 2): Laplace SL+DL 19, Yukawa SL+DL 27; monopole-only
-# evaluations of equivalent densities (M2P, L2P): Laplace 10, Yukawa 18.
-FLOPS_PAIR = {"lap_sd": 19, "yuk_sd": 27, "lap_m": 10, "yuk_m": 18}
+MUFU_PER_SM_CLK = 16
+# Arithmetic of one source-target pair in the paired (Laplace + Yukawa)
+# evaluation, FMA = 2 FLOPs, MUFU counted apart: SL+DL of both kernels
+# 30 FLOPs + 2 MUFU (rsqrt, ex2); monopole-only pairs of equivalent
+# densities (M2P, L2P) 16 FLOPs + 2 MUFU.
+FLOPS_PAIR = {"pair_sd": 30, "pair_m": 16}
+MUFU_PAIR = 2
 
 
 def parse():
@@ -264,6 +268,9 @@ def main():
     flush = torch.empty(256 * 1024 * 1024 // 4, device="cuda")
 
     def step():
+        pb.fmm_apply_pair(ctx, tree, KAPPA, args.p, out_l, out_y, q_lap=Q, q_yuk=Q, dip=D, src_n=Nr)
+
+    def step_two_applies():
         pb.fmm_apply(ctx, tree, pb.FMM_LAPLACE, 0.0, args.p, out_l, q=Q, dip=D, src_n=Nr)
         pb.fmm_apply(ctx, tree, pb.FMM_YUKAWA, KAPPA, args.p, out_y, q=Q, dip=D, src_n=Nr)
 
@@ -297,6 +304,19 @@ def main():
         ms = float(t.item())
     value = world * 2 * args.n / (ms * 1e-3)
 
+    # the same work as two single-kernel applies (for comparison; untimed by the metric)
+    for _ in range(2):
+        step_two_applies()
+    ev2 = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(3)]
+    for k in range(3):
+        with torch.cuda.stream(stream):
+            flush.fill_(float(k))
+            ev2[k][0].record(stream)
+            step_two_applies()
+            ev2[k][1].record(stream)
+    torch.cuda.synchronize()
+    ms_two = sum(a.elapsed_time(b) for a, b in ev2) / 3
+
     # e2e through the C-ABI with pinned host buffers (H2D of inputs, D2H of results inside)
     hq = torch.from_numpy(q).pin_memory()
     hd = torch.from_numpy(d).pin_memory()
@@ -305,8 +325,7 @@ def main():
     ho_y = torch.empty(args.n).pin_memory()
 
     def step_host():
-        pb.fmm_apply(ctx, tree, pb.FMM_LAPLACE, 0.0, args.p, ho_l, q=hq, dip=hd, src_n=hn)
-        pb.fmm_apply(ctx, tree, pb.FMM_YUKAWA, KAPPA, args.p, ho_y, q=hq, dip=hd, src_n=hn)
+        pb.fmm_apply_pair(ctx, tree, KAPPA, args.p, ho_l, ho_y, q_lap=hq, q_yuk=hq, dip=hd, src_n=hn)
 
     step_host()
     torch.cuda.synchronize()
@@ -315,23 +334,30 @@ def main():
         step_host()
     torch.cuda.synchronize()
     e2e_ms = (time.perf_counter() - t0) * 1e3 / args.steps
-    h2d = 2 * (q.nbytes + d.nbytes + nrm.nbytes)
+    h2d = 2 * q.nbytes + d.nbytes + nrm.nbytes          # q_lap and q_yuk are staged separately
     d2h = 2 * 4 * args.n
 
     # roofline of the dominant phase (per-launch averages from the library's event timers)
     phases = {k: v for k, v in prof.items() if k != "launches" and v[1] > 0}
     dom = max(phases, key=lambda k: phases[k][0])
-    leaf_ms = phases["leaf"][0] / phases["leaf"][1]     # per apply (one leaf launch per apply)
+    leaf_ms = phases["leaf"][0] / phases["leaf"][1]     # one paired leaf launch per step
     p = args.p
     ne = 6 * (p - 1) ** 2 + 2
     far = (info.m2p_targets + info.l2p_targets) * ne
-    leaf_flops = (info.p2p_pairs * (FLOPS_PAIR["lap_sd"] + FLOPS_PAIR["yuk_sd"])
-                  + far * (FLOPS_PAIR["lap_m"] + FLOPS_PAIR["yuk_m"])) / 2.0   # average per apply
-    peak = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    leaf_flops = info.p2p_pairs * FLOPS_PAIR["pair_sd"] + far * FLOPS_PAIR["pair_m"]
+    leaf_mufu = (info.p2p_pairs + far) * MUFU_PAIR
+    fma_peak = SM_COUNT * FP32_LANES * 2 * SM_MAX_MHZ * 1e6          # FLOP/s
+    mufu_peak = SM_COUNT * MUFU_PER_SM_CLK * SM_MAX_MHZ * 1e6        # MUFU op/s
+    t_roof = max(leaf_flops / fma_peak, leaf_mufu / mufu_peak)       # s per launch at the ALU roof
     achieved = leaf_flops / (leaf_ms * 1e-3) / 1e12
-    roof = {"kernel": "k_leaf_eval (P2P+M2P+L2P)", "bound": "alu", "achieved": achieved, "peak": peak,
-            "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
-            "peak_note": "FP32 FMA pipe: 152 SMs x 128 lanes x 2 flop x 2070 MHz (derived, not measured)",
+    peak = leaf_flops / t_roof / 1e12
+    roof = {"kernel": "k_leaf_pair (P2P+M2P+L2P, Laplace+Yukawa)", "bound": "alu", "achieved": achieved,
+            "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+            "peak_note": "derived ALU roof of this launch's instruction mix: max(FLOPs / FP32 FMA peak "
+                         "(152 SMs x 128 lanes x 2 x 2070 MHz = 80.5 TFLOP/s), MUFU ops / MUFU peak "
+                         "(152 x 16 x 2070 MHz)); not measured",
+            "fma_frac": leaf_flops / (leaf_ms * 1e-3) / fma_peak,
+            "mufu_frac": leaf_mufu / (leaf_ms * 1e-3) / mufu_peak,
             "dominant_phase": dom}
     launches = prof["launches"]
 
@@ -418,8 +444,9 @@ def main():
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": {"workload": f"fmm_apply {args.n} bumpy-sphere points (amp 0.05), Laplace+Yukawa "
-                                       f"(kappa {KAPPA}) SL+DL, p={p}, ncrit={args.ncrit}, tree cached",
+                "config": {"workload": f"fmm_apply_pair {args.n} bumpy-sphere points (amp 0.05), Laplace+Yukawa "
+                                       f"(kappa {KAPPA}) SL+DL in one traversal, p={p}, ncrit={args.ncrit}, "
+                                       f"tree cached",
                            "global_batch": args.n * world, "seq_len": None,
                            "parallelism": "replicas" if world > 1 else "single GPU",
                            "l2": "flushed between steps (256 MB write)",
@@ -431,7 +458,8 @@ def main():
                 "e2e": {"value": world * 2 * args.n / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
                         "d2h_bytes_per_step": d2h},
                 "gpu_launches": int(launches), "clocks": clocks, "pb_solve": solve, "pb_solve_batch": batch,
-                "phases_ms_per_step": {k: v[0] / args.steps for k, v in phases.items()}}
+                "phases_ms_per_step": {k: v[0] / args.steps for k, v in phases.items()},
+                "two_applies_ms_per_step": ms_two}
         print(json.dumps(line), flush=True)
     pb.fmm_tree_destroy(tree)
     pb.pb_destroy(ctx)

@@ -217,6 +217,24 @@ int fmm_apply(pb_ctx* ctx, fmm_tree* tree, int kernel, double kappa, int p, int 
               const void* q, const void* dip, const void* src_n, const void* tgt_n,
               void* out, void* out_dn);
 
+/* Laplace and Yukawa in one traversal (Eq. bempp_fmm_matvec: the direct
+ * formulation applies both kernels to the same quadrature points in every
+ * mat-vec).  With g_L = 1/(4 pi r), g_Y = e^{-kappa r}/(4 pi r):
+ *   out_lap[i] = sum_j g_L(x_i, y_j) q_lap[j] + dg_L/dn_y(x_i, y_j) dip[j]
+ *   out_yuk[i] = sum_j g_Y(x_i, y_j) q_yuk[j] + dg_Y/dn_y(x_i, y_j) dip[j]
+ *   dn_lap[i]  = sum_j dg_L/dn_x(x_i, y_j) q_lap[j]
+ *   dn_yuk[i]  = sum_j dg_Y/dn_x(x_i, y_j) q_yuk[j]
+ * The two kernels share the dipole densities and the geometry of every
+ * pair (one distance and one reciprocal square root per pair); the far
+ * field keeps one set of operators per kernel.  Arguments as fmm_apply:
+ * q_lap / q_yuk / dip may each be NULL (no such term), dip needs src_n,
+ * dn_lap and dn_yuk are both NULL or both given (then tgt_n is required and
+ * dip must be NULL).  Results equal two fmm_apply calls up to rounding.
+ * Errors: PB_EINVAL as fmm_apply, and kappa <= 0. */
+int fmm_apply_pair(pb_ctx* ctx, fmm_tree* tree, double kappa, int p, int precision,
+                   const void* q_lap, const void* q_yuk, const void* dip, const void* src_n,
+                   const void* tgt_n, void* out_lap, void* out_yuk, void* dn_lap, void* dn_yuk);
+
 /* ------------------------------------------------------------------------ */
 /* Boundary-element mesh and the direct formulation (Eq. direct).            */
 /* ------------------------------------------------------------------------ */

@@ -59,6 +59,7 @@ _sig("fmm_tree_export_points", [_P, _P, _P, _P, _P])
 _sig("fmm_tree_export_boxes", [_P] + [_P] * 9)
 _sig("fmm_tree_export_list", [_P, ctypes.c_int, _P, _P])
 _sig("fmm_apply", [_P, _P, ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int, _P, _P, _P, _P, _P, _P])
+_sig("fmm_apply_pair", [_P, _P, ctypes.c_double, ctypes.c_int, ctypes.c_int, _P, _P, _P, _P, _P, _P, _P, _P, _P])
 
 
 class pb_fmm_params(ctypes.Structure):
@@ -98,7 +99,7 @@ def exported_symbols():
     return ["pb_create", "pb_destroy", "pb_last_error", "pb_sync", "pb_profile", "pb_profile_read", "pb_set_option",
             "fmm_tree_build", "fmm_tree_destroy",
             "fmm_tree_info", "fmm_tree_export_points", "fmm_tree_export_boxes", "fmm_tree_export_list",
-            "fmm_apply", "pb_mesh_setup", "pb_mesh_destroy", "pb_mesh_info", "pb_mesh_export_singular",
+            "fmm_apply", "fmm_apply_pair", "pb_mesh_setup", "pb_mesh_destroy", "pb_mesh_info", "pb_mesh_export_singular",
             "pb_mesh_matvec", "pb_solve", "pb_result_destroy", "pb_result_get", "pb_solvation_energy",
             "pb_solvation_energy_noalloc", "pb_energy_grad", "pb_solve_batch", "pb_tune_ncrit"]
 
@@ -213,6 +214,13 @@ def fmm_apply(ctx, tree, kernel, kappa, p, out, q=None, dip=None, src_n=None, tg
               precision=PB_MIXED):
     _check(_lib.fmm_apply(ctx, tree, int(kernel), float(kappa), int(p), int(precision), ptr(q), ptr(dip),
                           ptr(src_n), ptr(tgt_n), ptr(out), ptr(out_dn)), ctx)
+
+
+def fmm_apply_pair(ctx, tree, kappa, p, out_lap, out_yuk, q_lap=None, q_yuk=None, dip=None, src_n=None,
+                   tgt_n=None, dn_lap=None, dn_yuk=None, precision=PB_MIXED):
+    """Laplace and Yukawa potentials of the same points in one traversal."""
+    _check(_lib.fmm_apply_pair(ctx, tree, float(kappa), int(p), int(precision), ptr(q_lap), ptr(q_yuk), ptr(dip),
+                               ptr(src_n), ptr(tgt_n), ptr(out_lap), ptr(out_yuk), ptr(dn_lap), ptr(dn_yuk)), ctx)
 
 
 PB_P0 = 0

@@ -274,8 +274,7 @@ static void adj_matvec_t(pb_mesh* M, const pb_result* R, const double* lam, doub
         k_p1_adj<T><<<div_up(np, 256), 256, 0, st>>>(nt, nq, lam, qw, mL.p, mY.p);
         PB_CHECK_LAUNCH();
     }
-    fmm_apply_impl(M->tree, FMM_LAPLACE, 0.0, M->p, prec, mL.p, nullptr, nullptr, qn, pL.p, dL.p);
-    fmm_apply_impl(M->tree, FMM_YUKAWA, R->kappa, M->p, prec, mY.p, nullptr, nullptr, qn, pY.p, dY.p);
+    fmm_apply_pair_impl(M->tree, R->kappa, M->p, prec, mL.p, mY.p, nullptr, nullptr, qn, pL.p, pY.p, dL.p, dY.p);
     PhaseTimer ph(M->ctx, PB_PH_BEM);
     k_combine_adj<T><<<div_up(nt, 128), 128, 0, st>>>(nt, nq, lam, pL.p, dL.p, pY.p, dY.p, qp, qn, qw, M->adj_off.p,
                                                       M->adj_ids.p, M->adj_tr.p, M->S_d.p, M->area.p,

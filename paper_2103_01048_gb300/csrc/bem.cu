@@ -22,6 +22,9 @@ namespace pbfmm {
 
 void fmm_apply_impl(fmm_tree* Tr, int kernel, double kappa, int p, int precision, const void* q, const void* dip,
                     const void* src_n, const void* tgt_n, void* out, void* out_dn);
+void fmm_apply_pair_impl(fmm_tree* Tr, double kappa, int p, int precision, const void* qL, const void* qY,
+                         const void* dip, const void* src_n, const void* tgt_n, void* outL, void* outY, void* dnL,
+                         void* dnY);
 void build_tree(fmm_tree* T, const float* src, const float* tgt);
 
 constexpr double kInv4PiB = 0.07957747154594767;
@@ -360,10 +363,12 @@ __global__ void k_to_float(long long n, const double* a, float* b) {
 // mat-vec pieces
 // ---------------------------------------------------------------------------
 // P1: quadrature-point densities of both FMM passes from x = [phi; dphi]
-//   Laplace: q = -w dphi, d = w phi;  Yukawa: q = (eps1/eps2) w dphi, d = -w phi
+//   Laplace: q = -w dphi, d = w phi;  Yukawa: q = (eps1/eps2) w dphi, d = -w phi.
+// The paired apply shares the dipole density, so the Yukawa pass takes
+// (-q, -d) = ((eps1/eps2) qL, dL) and its potential is negated in the combine.
 template <typename T>
 __global__ void k_p1(int nt, int nq, const double* __restrict__ x, const T* __restrict__ qw, double er,
-                     T* qL, T* dL, T* qY, T* dY) {
+                     T* qL, T* dL, T* qYn) {
     long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (a >= (long long)nt * nq) return;
     int i = (int)(a / nq);
@@ -371,8 +376,7 @@ __global__ void k_p1(int nt, int nq, const double* __restrict__ x, const T* __re
     T phi = (T)x[i], dphi = (T)x[nt + i];
     qL[a] = -w * dphi;
     dL[a] = w * phi;
-    qY[a] = (T)er * w * dphi;
-    dY[a] = -w * phi;
+    qYn[a] = -(T)er * w * dphi;
 }
 
 template <typename T> __device__ __forceinline__ T rsq(T x);
@@ -386,7 +390,7 @@ template <> __device__ __forceinline__ double ex<double>(double x) { return exp(
 // (if precond).  One thread per triangle.
 template <typename T>
 __global__ void k_combine(int nt, int nq, const double* __restrict__ x, const T* __restrict__ potL,
-                          const T* __restrict__ potY, const T* __restrict__ qp, const T* __restrict__ qn,
+                          const T* __restrict__ potYn, const T* __restrict__ qp, const T* __restrict__ qn,
                           const T* __restrict__ qw, const int* __restrict__ adj_off, const int* __restrict__ adj_ids,
                           const T* __restrict__ S, const double* __restrict__ area, double er, double kappa_d,
                           int precond, double* __restrict__ y) {
@@ -419,7 +423,7 @@ __global__ void k_combine(int nt, int nq, const double* __restrict__ x, const T*
             }
         }
         r1 += wa * (potL[pa] - c4 * cL);
-        r2 += wa * (potY[pa] - c4 * cY);
+        r2 += wa * (-potYn[pa] - c4 * cY);
     }
     double R1 = (double)r1, R2 = (double)r2;
     double phi_i = x[i];
@@ -851,23 +855,22 @@ static void matvec_t(pb_mesh* M, double eps_in, double eps_out, double kappa, co
     const long long np = (long long)nt * nq;
     const double er = eps_in / eps_out;
     const int prec = std::is_same<T, float>::value ? PB_MIXED : PB_FP64;
-    DBuf<T> qL, dL, qY, dY, pL, pY;
-    qL.alloc(np, st); dL.alloc(np, st); qY.alloc(np, st); dY.alloc(np, st); pL.alloc(np, st); pY.alloc(np, st);
+    DBuf<T> qL, dL, qYn, pL, pYn;
+    qL.alloc(np, st); dL.alloc(np, st); qYn.alloc(np, st); pL.alloc(np, st); pYn.alloc(np, st);
     const T* qw = std::is_same<T, float>::value ? (const T*)M->qw_f.p : (const T*)M->qw_d.p;
     const T* qp = std::is_same<T, float>::value ? (const T*)M->qp_f.p : (const T*)M->qp_d.p;
     const T* qn = std::is_same<T, float>::value ? (const T*)M->qn_f.p : (const T*)M->qn_d.p;
     const T* S = std::is_same<T, float>::value ? (const T*)M->S_f.p : (const T*)M->S_d.p;
     {
         PhaseTimer ph(M->ctx, PB_PH_BEM);
-        k_p1<T><<<div_up(np, 256), 256, 0, st>>>(nt, nq, x, qw, er, qL.p, dL.p, qY.p, dY.p);
+        k_p1<T><<<div_up(np, 256), 256, 0, st>>>(nt, nq, x, qw, er, qL.p, dL.p, qYn.p);
         PB_CHECK_LAUNCH();
     }
-    fmm_apply_impl(M->tree, FMM_LAPLACE, 0.0, M->p, prec, qL.p, dL.p, qn, nullptr, pL.p, nullptr);
-    fmm_apply_impl(M->tree, FMM_YUKAWA, kappa, M->p, prec, qY.p, dY.p, qn, nullptr, pY.p, nullptr);
+    fmm_apply_pair_impl(M->tree, kappa, M->p, prec, qL.p, qYn.p, dL.p, qn, nullptr, pL.p, pYn.p, nullptr, nullptr);
     {
         PhaseTimer ph(M->ctx, PB_PH_BEM);
         // S in FP64 for the combine (both paths): the singular entries are exact data
-        k_combine<T><<<div_up(nt, 128), 128, 0, st>>>(nt, nq, x, pL.p, pY.p, qp, qn, qw, M->adj_off.p, M->adj_ids.p,
+        k_combine<T><<<div_up(nt, 128), 128, 0, st>>>(nt, nq, x, pL.p, pYn.p, qp, qn, qw, M->adj_off.p, M->adj_ids.p,
                                                       (const T*)S, M->area.p, er, kappa, precond, y);
         PB_CHECK_LAUNCH();
     }

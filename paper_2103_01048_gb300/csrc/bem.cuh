@@ -36,6 +36,9 @@ void mesh_matvec(pb_mesh* M, double eps_in, double eps_out, double kappa, int pr
                  int precond);
 void fmm_apply_impl(fmm_tree* Tr, int kernel, double kappa, int p, int precision, const void* q, const void* dip,
                     const void* src_n, const void* tgt_n, void* out, void* out_dn);
+void fmm_apply_pair_impl(fmm_tree* Tr, double kappa, int p, int precision, const void* qL, const void* qY,
+                         const void* dip, const void* src_n, const void* tgt_n, void* outL, void* outY, void* dnL,
+                         void* dnY);
 }  // namespace pbfmm
 
 struct pb_result {

@@ -7,6 +7,9 @@ namespace pbfmm {
 void build_tree(fmm_tree* T, const float* src, const float* tgt);
 void fmm_apply_impl(fmm_tree* Tr, int kernel, double kappa, int p, int precision, const void* q, const void* dip,
                     const void* src_n, const void* tgt_n, void* out, void* out_dn);
+void fmm_apply_pair_impl(fmm_tree* Tr, double kappa, int p, int precision, const void* qL, const void* qY,
+                         const void* dip, const void* src_n, const void* tgt_n, void* outL, void* outY, void* dnL,
+                         void* dnY);
 void mesh_setup(pb_mesh* M, const double* verts, const int* tris);
 void mesh_matvec(pb_mesh* M, double eps_in, double eps_out, double kappa, int precision, const double* x, double* y,
                  int precond);
@@ -331,6 +334,52 @@ int fmm_tree_export_list(const fmm_tree* T, int which, int64_t* off, int32_t* id
         }
     }
     PB_CUDA(cudaStreamSynchronize(st));
+    PB_API_END(ctx)
+}
+
+int fmm_apply_pair(pb_ctx* ctx, fmm_tree* T, double kappa, int p, int precision, const void* q_lap,
+                   const void* q_yuk, const void* dip, const void* src_n, const void* tgt_n, void* out_lap,
+                   void* out_yuk, void* dn_lap, void* dn_yuk) {
+    if (!ctx || !T) return PB_EINVAL;
+    PB_API_BEGIN
+    PB_REQUIRE(kappa > 0.0, PB_EINVAL, "fmm_apply_pair: kappa must be > 0");
+    PB_REQUIRE(p >= 2 && p <= 10, PB_EINVAL, "fmm_apply_pair: p must be in [2, 10]");
+    PB_REQUIRE(precision == PB_MIXED || precision == PB_FP64, PB_EINVAL, "fmm_apply_pair: unknown precision");
+    PB_REQUIRE(out_lap && out_yuk, PB_EINVAL, "fmm_apply_pair: out_lap and out_yuk are required");
+    PB_REQUIRE(!dip || src_n, PB_EINVAL, "fmm_apply_pair: double layer needs source normals");
+    PB_REQUIRE((dn_lap == nullptr) == (dn_yuk == nullptr), PB_EINVAL,
+               "fmm_apply_pair: give both normal-derivative outputs or neither");
+    PB_REQUIRE(!dn_lap || tgt_n, PB_EINVAL, "fmm_apply_pair: normal derivative needs target normals");
+    PB_REQUIRE(!(dip && dn_lap), PB_EINVAL,
+               "fmm_apply_pair: hypersingular kernel (dipole + target derivative) not provided");
+    PB_CUDA(cudaSetDevice(ctx->device));
+    cudaStream_t st = ctx->stream;
+    const size_t es = precision == PB_FP64 ? 8 : 4;
+    Staged sqL, sqY, sd, sn, tn;
+    sqL.in(q_lap, T->ns * es, st);
+    sqY.in(q_yuk, T->ns * es, st);
+    sd.in(dip, T->ns * es, st);
+    sn.in(src_n, T->ns * 3 * es, st);
+    tn.in(tgt_n, T->nt * 3 * es, st);
+    void* outs[4] = {out_lap, out_yuk, dn_lap, dn_yuk};
+    void* dev[4] = {nullptr, nullptr, nullptr, nullptr};
+    DBuf<char> bufs[4];
+    bool any_host = sqL.buf.p || sqY.buf.p || sd.buf.p || sn.buf.p || tn.buf.p;
+    for (int k = 0; k < 4; ++k) {
+        if (!outs[k]) continue;
+        if (is_device_ptr(outs[k])) { dev[k] = outs[k]; continue; }
+        bufs[k].alloc(T->nt * es, st);
+        dev[k] = bufs[k].p;
+        any_host = true;
+    }
+    fmm_apply_pair_impl(T, kappa, p, precision, sqL.dev, sqY.dev, sd.dev, sn.dev, tn.dev, dev[0], dev[1], dev[2],
+                        dev[3]);
+    for (int k = 0; k < 4; ++k)
+        if (bufs[k].p) PB_CUDA(cudaMemcpyAsync(outs[k], dev[k], T->nt * es, cudaMemcpyDeviceToHost, st));
+    if (any_host) {
+        PB_CUDA(cudaStreamSynchronize(st));
+        check_device_error(ctx);
+    }
     PB_API_END(ctx)
 }
 

@@ -19,6 +19,7 @@ bool pc_tc_launch(const fmm_tree* T, const Operators& O, int child_level, bool u
                   cudaStream_t st);
 
 constexpr double kInv4PiD = 0.07957747154594767;
+constexpr double kLog2E = 1.4426950408889634;     // log2(e)
 constexpr int kTC = 32;    // boxes per tile of the dense box-vector products (= kM2LTile)
 static_assert(kTC == kM2LTile, "M2L tile width");
 
@@ -27,10 +28,25 @@ template <> struct V4<float> { using type = float4; };
 template <> struct V4<double> { using type = double4; };
 
 template <typename T> __device__ __forceinline__ T rsqrt_t(T x);
-template <> __device__ __forceinline__ float rsqrt_t<float>(float x) { return rsqrtf(x); }
+// FP32: the MUFU approximations with denormals flushed (distances and
+// exponentials of the far field never reach the denormal range; r = 0 is
+// guarded before use)
+template <> __device__ __forceinline__ float rsqrt_t<float>(float x) {
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
 template <> __device__ __forceinline__ double rsqrt_t<double>(double x) { return rsqrt(x); }
+// 2^x
+template <typename T> __device__ __forceinline__ T exp2_t(T x);
+template <> __device__ __forceinline__ float exp2_t<float>(float x) {
+    float y;
+    asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+template <> __device__ __forceinline__ double exp2_t<double>(double x) { return exp2(x); }
 template <typename T> __device__ __forceinline__ T exp_t(T x);
-template <> __device__ __forceinline__ float exp_t<float>(float x) { return __expf(x); }
+template <> __device__ __forceinline__ float exp_t<float>(float x) { return exp2_t<float>(x * float(kLog2E)); }
 template <> __device__ __forceinline__ double exp_t<double>(double x) { return exp(x); }
 
 // One source-target interaction, without the 1/(4 pi) factor:
@@ -55,6 +71,36 @@ __device__ __forceinline__ void interact(T dx, T dy, T dz, T q, T mx, T my, T mz
     if (DN) dn -= (dx * nx + dy * ny + dz * nz) * f * q;
 }
 
+// The Laplace and the Yukawa interaction of one pair with the geometry
+// shared (the direct formulation applies both kernels to the same points),
+// without the 1/(4 pi) factor; both kernels take the same dipole m:
+//   potL += g qL + (d.m) f,               dnL -= (d.n) f qL,
+//   potY += e (g qY + (d.m) f (1 + kr)),  dnY -= e (1 + kr) (d.n) f qY,
+//   g = 1/r, f = 1/r^3, e = exp(-kappa r) (Sec. "Fast multipole method").
+template <typename T, bool DL, bool DN, bool GUARD>
+__device__ __forceinline__ void interact_pair(T dx, T dy, T dz, T qL, T qY, T mx, T my, T mz, T nx, T ny, T nz,
+                                              T kappa, T& potL, T& potY, T& dnL, T& dnY) {
+    T r2 = dx * dx + dy * dy + dz * dz;
+    T rinv = GUARD ? (r2 > T(0) ? rsqrt_t<T>(r2) : T(0)) : rsqrt_t<T>(r2);
+    T f = rinv * rinv * rinv;
+    T r = r2 * rinv;
+    T e = exp_t<T>(-kappa * r);
+    T fy = f * (T(1) + kappa * r);
+    potL += rinv * qL;
+    T sy = rinv * qY;
+    if (DL) {
+        T dm = dx * mx + dy * my + dz * mz;
+        potL += dm * f;
+        sy += dm * fy;
+    }
+    potY += e * sy;
+    if (DN) {
+        T dn = dx * nx + dy * ny + dz * nz;
+        dnL -= dn * f * qL;
+        dnY -= e * fy * dn * qY;
+    }
+}
+
 // ---------------------------------------------------------------------------
 // gather of the densities into Morton order
 // ---------------------------------------------------------------------------
@@ -72,6 +118,22 @@ __global__ void k_gather_src(long long n, const int* __restrict__ perm, const fl
         T d = (T)dip[i];
         sm[k] = {d * (T)nrm[3 * i], d * (T)nrm[3 * i + 1], d * (T)nrm[3 * i + 2], T(0)};
     }
+}
+
+// paired apply: sq = (x, y, z, q_lap), sm = (d n_x, d n_y, d n_z, q_yuk)
+template <typename T, typename In>
+__global__ void k_gather_pair(long long n, const int* __restrict__ perm, const float4* __restrict__ pos,
+                              const In* __restrict__ qL, const In* __restrict__ qY, const In* __restrict__ dip,
+                              const In* __restrict__ nrm, typename V4<T>::type* __restrict__ sq,
+                              typename V4<T>::type* __restrict__ sm) {
+    long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    long long i = perm[k];
+    float4 p = pos[k];
+    sq[k] = {(T)p.x, (T)p.y, (T)p.z, qL ? (T)qL[i] : T(0)};
+    T d = dip ? (T)dip[i] : T(0);
+    sm[k] = {dip ? d * (T)nrm[3 * i] : T(0), dip ? d * (T)nrm[3 * i + 1] : T(0), dip ? d * (T)nrm[3 * i + 2] : T(0),
+             qY ? (T)qY[i] : T(0)};
 }
 
 template <typename T, typename In>
@@ -154,6 +216,68 @@ __global__ void __launch_bounds__(256) k_p2check(int nbox, const int* __restrict
     for (int m = 0; m < MAXP; ++m) {
         int i = threadIdx.x + m * CH;
         if (i < npad) chk[(long long)b * npad + i] = (i < ne) ? acc[m] * T(kInv4PiD) : T(0);
+    }
+}
+
+// P2M / P2L of the paired apply: Laplace and Yukawa check potentials of the
+// same sources in one pass (sm carries the dipole and the Yukawa monopole).
+template <typename T, bool DL, int MAXP>
+__global__ void __launch_bounds__(256) k_p2check_pair(int nbox, const int* __restrict__ boxes, int mode,
+                                                      const double4* __restrict__ center, const int* __restrict__ sb,
+                                                      const int* __restrict__ se, const int* __restrict__ X,
+                                                      const int* __restrict__ X_n,
+                                                      const typename V4<T>::type* __restrict__ sq,
+                                                      const typename V4<T>::type* __restrict__ sm,
+                                                      const float4* __restrict__ surf, int ne, int npad, T kappa,
+                                                      T* __restrict__ chkL, T* __restrict__ chkY) {
+    using V = typename V4<T>::type;
+    __shared__ V s_q[256];
+    __shared__ V s_m[256];
+    const int CH = blockDim.x;
+    int bi = blockIdx.x;
+    if (bi >= nbox) return;
+    int b = boxes[bi];
+    double4 c = center[b];
+    T alpha = T(mode == 0 ? kAlphaOuter : kAlphaInner) * (T)c.w;
+    T px[MAXP], py[MAXP], pz[MAXP], aL[MAXP], aY[MAXP];
+#pragma unroll
+    for (int m = 0; m < MAXP; ++m) {
+        int i = threadIdx.x + m * CH;
+        float4 s = (i < ne) ? surf[i] : make_float4(0, 0, 0, 0);
+        px[m] = alpha * (T)s.x; py[m] = alpha * (T)s.y; pz[m] = alpha * (T)s.z;
+        aL[m] = aY[m] = T(0);
+    }
+    int nlist = (mode == 0) ? 1 : X_n[b];
+    T d0 = T(0), d1 = T(0);
+    for (int li = 0; li < nlist; ++li) {
+        int a = (mode == 0) ? b : X[(long long)b * kXCap + li];
+        int j0 = sb[a], j1 = se[a];
+        for (int jc = j0; jc < j1; jc += CH) {
+            int j = jc + threadIdx.x;
+            __syncthreads();
+            if (j < j1) {
+                V v = sq[j];
+                s_q[threadIdx.x] = {(T)((double)v.x - c.x), (T)((double)v.y - c.y), (T)((double)v.z - c.z), v.w};
+                s_m[threadIdx.x] = sm[j];
+            }
+            __syncthreads();
+            int cnt = min(CH, j1 - jc);
+            for (int t = 0; t < cnt; ++t) {
+                V s = s_q[t], mm = s_m[t];
+#pragma unroll
+                for (int m = 0; m < MAXP; ++m)
+                    interact_pair<T, DL, false, false>(px[m] - s.x, py[m] - s.y, pz[m] - s.z, s.w, mm.w, mm.x, mm.y,
+                                                       mm.z, 0, 0, 0, kappa, aL[m], aY[m], d0, d1);
+            }
+        }
+    }
+#pragma unroll
+    for (int m = 0; m < MAXP; ++m) {
+        int i = threadIdx.x + m * CH;
+        if (i < npad) {
+            chkL[(long long)b * npad + i] = (i < ne) ? aL[m] * T(kInv4PiD) : T(0);
+            chkY[(long long)b * npad + i] = (i < ne) ? aY[m] * T(kInv4PiD) : T(0);
+        }
     }
 }
 
@@ -527,6 +651,157 @@ __global__ void __launch_bounds__(128) k_leaf_eval(const int* __restrict__ leave
     }
 }
 
+// Leaf evaluation of the paired apply: the same work split as k_leaf_eval,
+// with the Laplace and the Yukawa sums of every pair taken together.
+template <typename T, bool DL, bool DN, int NT>
+__global__ void __launch_bounds__(128) k_leaf_pair(const int* __restrict__ leaves, int nleaf,
+                                                   const int* __restrict__ tb, const int* __restrict__ te,
+                                                   const int* __restrict__ sb, const int* __restrict__ se,
+                                                   const int* __restrict__ U_off, const int* __restrict__ U_ids,
+                                                   const int* __restrict__ W_off, const int* __restrict__ W_ids,
+                                                   const int* __restrict__ level, const double4* __restrict__ center,
+                                                   const float4* __restrict__ tpos,
+                                                   const typename V4<T>::type* __restrict__ tn,
+                                                   const typename V4<T>::type* __restrict__ sq,
+                                                   const typename V4<T>::type* __restrict__ sm,
+                                                   const T* __restrict__ QuL, const T* __restrict__ QdL,
+                                                   const T* __restrict__ QuY, const T* __restrict__ QdY,
+                                                   const float4* __restrict__ surf, int ne, int npad, T kappa,
+                                                   T* __restrict__ potL_out, T* __restrict__ potY_out,
+                                                   T* __restrict__ dnL_out, T* __restrict__ dnY_out) {
+    using V = typename V4<T>::type;
+    constexpr int CH = 128;
+    constexpr int NR = DN ? 4 : 2;
+    __shared__ V s_q[CH];
+    __shared__ V s_m[CH];
+    __shared__ T s_red[NR][NT * CH];
+    int li = blockIdx.x;
+    if (li >= nleaf) return;
+    const int b = leaves[li];
+    const int t0 = tb[b], t1 = te[b];
+    int slots = CH;
+    while (slots > 8 && NT * (slots / 2) >= t1 - t0) slots /= 2;
+    const int G = CH / slots;
+    const int tloc = threadIdx.x % slots, g = threadIdx.x / slots;
+    const int nw = W_off[b + 1] - W_off[b];
+    const int nsrcbox = nw + (level[b] >= 2 ? 1 : 0);
+    for (int tc = t0; tc < t1; tc += NT * slots) {
+        int ti[NT];
+        bool vt[NT];
+        float4 xt[NT];
+        T nx[NT], ny[NT], nz[NT], pL[NT], pY[NT], dL[NT], dY[NT];
+#pragma unroll
+        for (int u = 0; u < NT; ++u) {
+            ti[u] = tc + tloc + u * slots;
+            vt[u] = ti[u] < t1;
+            xt[u] = vt[u] ? tpos[ti[u]] : make_float4(0, 0, 0, 0);
+            nx[u] = ny[u] = nz[u] = T(0);
+            if (DN && vt[u]) { V nn = tn[ti[u]]; nx[u] = nn.x; ny[u] = nn.y; nz[u] = nn.z; }
+            pL[u] = pY[u] = dL[u] = dY[u] = T(0);
+        }
+        // P2P
+        for (int ui = U_off[b]; ui < U_off[b + 1]; ++ui) {
+            const int a = U_ids[ui];
+            const int j0 = sb[a], j1 = se[a];
+            for (int jc = j0; jc < j1; jc += CH) {
+                int j = jc + threadIdx.x;
+                __syncthreads();
+                if (j < j1) {
+                    s_q[threadIdx.x] = sq[j];
+                    s_m[threadIdx.x] = sm[j];
+                }
+                __syncthreads();
+                const int cnt = min(CH, j1 - jc);
+                if (a == b) {
+                    for (int k = g; k < cnt; k += G) {
+                        V s = s_q[k], mm = s_m[k];
+#pragma unroll
+                        for (int u = 0; u < NT; ++u)
+                            interact_pair<T, DL, DN, true>((T)xt[u].x - s.x, (T)xt[u].y - s.y, (T)xt[u].z - s.z, s.w,
+                                                           mm.w, mm.x, mm.y, mm.z, nx[u], ny[u], nz[u], kappa, pL[u],
+                                                           pY[u], dL[u], dY[u]);
+                    }
+                } else {
+                    for (int k = g; k < cnt; k += G) {
+                        V s = s_q[k], mm = s_m[k];
+#pragma unroll
+                        for (int u = 0; u < NT; ++u)
+                            interact_pair<T, DL, DN, false>((T)xt[u].x - s.x, (T)xt[u].y - s.y, (T)xt[u].z - s.z,
+                                                            s.w, mm.w, mm.x, mm.y, mm.z, nx[u], ny[u], nz[u], kappa,
+                                                            pL[u], pY[u], dL[u], dY[u]);
+                    }
+                }
+            }
+        }
+        // M2P (W list) and L2P (own downward equivalent)
+        for (int wi = 0; wi < nsrcbox; ++wi) {
+            const int a = (wi < nw) ? W_ids[W_off[b] + wi] : b;
+            const T* QL = (wi < nw) ? QuL : QdL;
+            const T* QY = (wi < nw) ? QuY : QdY;
+            const double4 ca = center[a];
+            const T alpha = T(wi < nw ? kAlphaInner : kAlphaOuter) * (T)ca.w;
+            T rx[NT], ry[NT], rz[NT];
+#pragma unroll
+            for (int u = 0; u < NT; ++u) {
+                rx[u] = (T)((double)xt[u].x - ca.x);
+                ry[u] = (T)((double)xt[u].y - ca.y);
+                rz[u] = (T)((double)xt[u].z - ca.z);
+            }
+            for (int jc = 0; jc < ne; jc += CH) {
+                int j = jc + threadIdx.x;
+                __syncthreads();
+                if (j < ne) {
+                    float4 s = surf[j];
+                    s_q[threadIdx.x] = {alpha * (T)s.x, alpha * (T)s.y, alpha * (T)s.z, QL[(size_t)a * npad + j]};
+                    s_m[threadIdx.x].w = QY[(size_t)a * npad + j];
+                }
+                __syncthreads();
+                const int cnt = min(CH, ne - jc);
+                for (int k = g; k < cnt; k += G) {
+                    V s = s_q[k];
+                    T qy = s_m[k].w;
+#pragma unroll
+                    for (int u = 0; u < NT; ++u)
+                        interact_pair<T, false, DN, false>(rx[u] - s.x, ry[u] - s.y, rz[u] - s.z, s.w, qy, 0, 0, 0,
+                                                           nx[u], ny[u], nz[u], kappa, pL[u], pY[u], dL[u], dY[u]);
+                }
+            }
+        }
+        // combine the G partial sums of each target
+        __syncthreads();
+#pragma unroll
+        for (int u = 0; u < NT; ++u) {
+            s_red[0][u * CH + threadIdx.x] = pL[u];
+            s_red[1][u * CH + threadIdx.x] = pY[u];
+            if (DN) {
+                s_red[NR - 2][u * CH + threadIdx.x] = dL[u];
+                s_red[NR - 1][u * CH + threadIdx.x] = dY[u];
+            }
+        }
+        __syncthreads();
+        if (g == 0) {
+#pragma unroll
+            for (int u = 0; u < NT; ++u) {
+                T a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+                for (int q = 0; q < G; ++q) {
+                    const int o = u * CH + tloc + q * slots;
+                    a0 += s_red[0][o];
+                    a1 += s_red[1][o];
+                    if (DN) { a2 += s_red[NR - 2][o]; a3 += s_red[NR - 1][o]; }
+                }
+                if (vt[u]) {
+                    potL_out[ti[u]] = a0 * T(kInv4PiD);
+                    potY_out[ti[u]] = a1 * T(kInv4PiD);
+                    if (DN) {
+                        dnL_out[ti[u]] = a2 * T(kInv4PiD);
+                        dnY_out[ti[u]] = a3 * T(kInv4PiD);
+                    }
+                }
+            }
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------
 // host driver
 // ---------------------------------------------------------------------------
@@ -643,25 +918,122 @@ const float* opsel<float>(const Operators&, const DBuf<float>& f, const DBuf<dou
 template <>
 const double* opsel<double>(const Operators&, const DBuf<float>&, const DBuf<double>& d) { return d.p; }
 
+// ---- far-field steps of one kernel (operators O, work W), shared by the
+// single and the paired apply
+template <typename T>
+static GemmArgs tree_gemm_args(const fmm_tree* Tr) {
+    GemmArgs ga{};
+    ga.first_child = Tr->first_child.p;
+    ga.nchild = Tr->nchild.p;
+    ga.anchor = Tr->anchor.p;
+    ga.parent = Tr->parent.p;
+    return ga;
+}
+
+// UC2UE at every leaf with sources (upward check potentials in W.chk)
+template <typename T>
+static void far_uc2ue(fmm_tree* Tr, const Operators& O, Work<T>& W) {
+    GemmArgs ga = tree_gemm_args<T>(Tr);
+    for (int l = 0; l < Tr->nlev; ++l) {
+        int a0 = Tr->sleaf_lvl_off[l], a1 = Tr->sleaf_lvl_off[l + 1];
+        if (a1 <= a0) continue;
+        check2equiv<T>(O, l, true, Tr->ctx->stream, ga, a1 - a0, Tr->sleaf_ids.p + a0, W.chk.p, W.Qu.p);
+    }
+}
+
+// M2M, post-order: parents at level l from children at level l + 1 (leaves
+// of level l keep their P2M result: the kernels skip them)
+template <typename T>
+static void far_m2m(fmm_tree* Tr, const Operators& O, Work<T>& W) {
+    pb_ctx* ctx = Tr->ctx;
+    cudaStream_t st = ctx->stream;
+    GemmArgs ga = tree_gemm_args<T>(Tr);
+    const T* m2m = opsel<T>(O, O.m2m, O.m2m_d);
+    for (int l = Tr->nlev - 2; l >= 2; --l) {
+        if constexpr (std::is_same<T, float>::value) {
+            if (!ctx->deterministic && pc_tc_launch(Tr, O, l + 1, true, W.Qu.p, ctx->dev_err, st)) continue;
+        }
+        int a0 = Tr->lvl_off[l], a1 = Tr->lvl_off[l + 1];
+        ga.mode = G_M2M; ga.ncols = a1 - a0; ga.cols = nullptr; ga.col_base = a0; ga.level = l + 1;
+        gemm_dispatch<T, T>(O.npad, st, div_up(a1 - a0, kTC), ga, m2m, W.Qu.p, W.Qu.p);
+    }
+}
+
+// DC2DE at every X-list box (downward check potentials of P2L in W.chk);
+// writes Qd of those boxes before the M2L accumulates
+template <typename T>
+static void far_dc2de_x(fmm_tree* Tr, const Operators& O, Work<T>& W) {
+    GemmArgs ga = tree_gemm_args<T>(Tr);
+    for (int l = 0; l < Tr->nlev; ++l) {
+        int a0 = Tr->xbox_lvl_off[l], a1 = Tr->xbox_lvl_off[l + 1];
+        if (a1 <= a0) continue;
+        check2equiv<T>(O, l, false, Tr->ctx->stream, ga, a1 - a0, Tr->xbox_ids.p + a0, W.chk.p, W.Qd.p);
+    }
+}
+
+// M2L over the V lists with DC2DE folded into the operators: accumulate into Qd
+template <typename T>
+static void far_m2l(fmm_tree* Tr, const Operators& O, Work<T>& W) {
+    pb_ctx* ctx = Tr->ctx;
+    bool tc_done = false;
+    if constexpr (std::is_same<T, float>::value) {
+        if (Tr->m2l_pairs.nitems > 0 && !ctx->deterministic)
+            tc_done = m2l_tc_launch(Tr, O, W.Qu.p, W.Qd.p, ctx->dev_err, ctx->stream);
+    }
+    if (!tc_done && Tr->m2l.ntile > 0) {
+        GemmArgs ga = tree_gemm_args<T>(Tr);
+        ga.mode = G_M2L;
+        ga.tile_box = Tr->m2l.tile_box.p;
+        ga.tile_level = Tr->m2l.tile_level.p;
+        ga.entry_off = Tr->m2l.entry_off.p;
+        ga.entry_oidx = Tr->m2l.entry_offset_idx.p;
+        ga.entry_src = Tr->m2l.entry_src.p;
+        gemm_dispatch<T, T>(O.npad, ctx->stream, Tr->m2l.ntile, ga, opsel<T>(O, O.m2l, O.m2l_d), W.Qu.p, W.Qd.p);
+    }
+}
+
+// L2L, pre-order (DC2DE folded), from parents at level l - 1
+template <typename T>
+static void far_l2l(fmm_tree* Tr, const Operators& O, Work<T>& W) {
+    pb_ctx* ctx = Tr->ctx;
+    cudaStream_t st = ctx->stream;
+    GemmArgs ga = tree_gemm_args<T>(Tr);
+    const T* l2l = opsel<T>(O, O.l2l, O.l2l_d);
+    for (int l = 3; l < Tr->nlev; ++l) {
+        if constexpr (std::is_same<T, float>::value) {
+            if (!ctx->deterministic && pc_tc_launch(Tr, O, l, false, W.Qd.p, ctx->dev_err, st)) continue;
+        }
+        int p0 = Tr->lvl_off[l - 1], p1 = Tr->lvl_off[l];
+        ga.mode = G_L2L; ga.ncols = p1 - p0; ga.cols = nullptr; ga.col_base = p0; ga.level = l;
+        gemm_dispatch<T, T>(O.npad, st, div_up(p1 - p0, kTC), ga, l2l, W.Qd.p, W.Qd.p);
+    }
+}
+
+// equivalent densities and check potentials of one kernel
+template <typename T>
+static void alloc_far(Work<T>& W, size_t nbox_npad, cudaStream_t st) {
+    W.Qu.alloc(nbox_npad, st);
+    W.Qd.alloc(nbox_npad, st);
+    W.chk.alloc(nbox_npad, st);
+    W.Qu.zero(st);
+    W.Qd.zero(st);
+    W.chk.zero(st);
+}
+
 template <typename T, typename In, bool YUK>
 static void apply_t(fmm_tree* Tr, const Operators& O, double kappa_d, const In* q, const In* dip, const In* src_n,
                     const In* tgt_n, In* out, In* out_dn) {
     cudaStream_t st = Tr->ctx->stream;
     const long long ns = Tr->ns, nt = Tr->same ? Tr->ns : Tr->nt;
-    const int npad = O.npad, nb = Tr->nbox;
     const T kappa = (T)kappa_d;
     const bool DL = dip != nullptr, DN = out_dn != nullptr;
+    if (DL && DN) throw Error(PB_EINVAL, "double layer with target-normal derivative is not provided");
     Work<T> W;
     W.sq.alloc(ns, st);
     if (DL) W.sm.alloc(ns, st);
-    W.Qu.alloc((size_t)nb * npad, st);
-    W.Qd.alloc((size_t)nb * npad, st);
-    W.chk.alloc((size_t)nb * npad, st);
+    alloc_far(W, (size_t)Tr->nbox * O.npad, st);
     W.pot.alloc(nt, st);
     if (DN) { W.dn.alloc(nt, st); W.tn.alloc(nt, st); }
-    W.Qu.zero(st);
-    W.Qd.zero(st);
-    W.chk.zero(st);
     pb_ctx* ctx = Tr->ctx;
     auto ph = std::make_unique<PhaseTimer>(ctx, PB_PH_GATHER);
     k_gather_src<T, In><<<div_up(ns, 256), 256, 0, st>>>(ns, Tr->perm_s.p, Tr->pos_s.p, q, dip, src_n, W.sq.p,
@@ -672,88 +1044,138 @@ static void apply_t(fmm_tree* Tr, const Operators& O, double kappa_d, const In* 
         k_gather_tn<T, In><<<div_up(nt, 256), 256, 0, st>>>(nt, pt, tgt_n, W.tn.p);
         PB_CHECK_LAUNCH();
     }
-    const T* m2m = opsel<T>(O, O.m2m, O.m2m_d);
-    const T* l2l = opsel<T>(O, O.l2l, O.l2l_d);
-    const T* m2l = opsel<T>(O, O.m2l, O.m2l_d);
-    GemmArgs ga{};
-    ga.first_child = Tr->first_child.p;
-    ga.nchild = Tr->nchild.p;
-    ga.anchor = Tr->anchor.p;
-    ga.parent = Tr->parent.p;
     const int nsl = Tr->sleaf_lvl_off[Tr->nlev];
     ph.reset(); ph = std::make_unique<PhaseTimer>(ctx, PB_PH_P2M);
     // ---- upward pass: P2M at leaves with sources, then UC2UE per level
     if (DL) launch_p2check<T, YUK, true>(st, nsl, Tr->sleaf_ids.p, 0, Tr, W, O, kappa);
     else launch_p2check<T, YUK, false>(st, nsl, Tr->sleaf_ids.p, 0, Tr, W, O, kappa);
-    for (int l = 0; l < Tr->nlev; ++l) {
-        int a0 = Tr->sleaf_lvl_off[l], a1 = Tr->sleaf_lvl_off[l + 1];
-        if (a1 <= a0) continue;
-        check2equiv<T>(O, l, true, st, ga, a1 - a0, Tr->sleaf_ids.p + a0, W.chk.p, W.Qu.p);
-    }
+    far_uc2ue(Tr, O, W);
     ph.reset(); ph = std::make_unique<PhaseTimer>(ctx, PB_PH_M2M);
-    // M2M, post-order: parents at level l from children at level l + 1
-    // (leaves of level l keep their P2M result: the kernel skips them)
-    for (int l = Tr->nlev - 2; l >= 2; --l) {
-        if constexpr (std::is_same<T, float>::value) {
-            if (!ctx->deterministic && pc_tc_launch(Tr, O, l + 1, true, W.Qu.p, ctx->dev_err, st)) continue;
-        }
-        int a0 = Tr->lvl_off[l], a1 = Tr->lvl_off[l + 1];
-        ga.mode = G_M2M; ga.ncols = a1 - a0; ga.cols = nullptr; ga.col_base = a0; ga.level = l + 1;
-        gemm_dispatch<T, T>(npad, st, div_up(a1 - a0, kTC), ga, m2m, W.Qu.p, W.Qu.p);
-    }
+    far_m2m(Tr, O, W);
     ph.reset(); ph = std::make_unique<PhaseTimer>(ctx, PB_PH_P2L);
     // ---- far field into downward equivalent densities.
-    // P2L: X-list sources -> downward check -> DC2DE (FP64), per level
+    // P2L: X-list sources -> downward check -> DC2DE, per level
     if (Tr->n_xbox > 0) {
         if (DL) launch_p2check<T, YUK, true>(st, Tr->n_xbox, Tr->xbox_ids.p, 1, Tr, W, O, kappa);
         else launch_p2check<T, YUK, false>(st, Tr->n_xbox, Tr->xbox_ids.p, 1, Tr, W, O, kappa);
-        for (int l = 0; l < Tr->nlev; ++l) {
-            int a0 = Tr->xbox_lvl_off[l], a1 = Tr->xbox_lvl_off[l + 1];
-            if (a1 <= a0) continue;
-            check2equiv<T>(O, l, false, st, ga, a1 - a0, Tr->xbox_ids.p + a0, W.chk.p, W.Qd.p);
-        }
+        far_dc2de_x(Tr, O, W);
     }
-    // M2L (V list) with DC2DE folded into the operators: accumulate into Qd
     ph.reset(); ph = std::make_unique<PhaseTimer>(ctx, PB_PH_M2L);
-    bool tc_done = false;
-    if constexpr (std::is_same<T, float>::value) {
-        if (Tr->m2l_pairs.nitems > 0 && !ctx->deterministic)
-            tc_done = m2l_tc_launch(Tr, O, W.Qu.p, W.Qd.p, ctx->dev_err, st);
-    }
-    if (!tc_done && Tr->m2l.ntile > 0) {
-        ga.mode = G_M2L;
-        ga.tile_box = Tr->m2l.tile_box.p;
-        ga.tile_level = Tr->m2l.tile_level.p;
-        ga.entry_off = Tr->m2l.entry_off.p;
-        ga.entry_oidx = Tr->m2l.entry_offset_idx.p;
-        ga.entry_src = Tr->m2l.entry_src.p;
-        gemm_dispatch<T, T>(npad, st, Tr->m2l.ntile, ga, m2l, W.Qu.p, W.Qd.p);
-    }
-    // ---- downward pass, pre-order: L2L (DC2DE folded) from parents at level l - 1
+    far_m2l(Tr, O, W);
+    // ---- downward pass
     ph.reset(); ph = std::make_unique<PhaseTimer>(ctx, PB_PH_DOWN);
-    for (int l = 3; l < Tr->nlev; ++l) {
-        if constexpr (std::is_same<T, float>::value) {
-            if (!ctx->deterministic && pc_tc_launch(Tr, O, l, false, W.Qd.p, ctx->dev_err, st)) continue;
-        }
-        int p0 = Tr->lvl_off[l - 1], p1 = Tr->lvl_off[l];
-        ga.mode = G_L2L; ga.ncols = p1 - p0; ga.cols = nullptr; ga.col_base = p0; ga.level = l;
-        gemm_dispatch<T, T>(npad, st, div_up(p1 - p0, kTC), ga, l2l, W.Qd.p, W.Qd.p);
-    }
+    far_l2l(Tr, O, W);
     ph.reset(); ph = std::make_unique<PhaseTimer>(ctx, PB_PH_LEAF);
     // ---- leaves: P2P + M2P + L2P
-    if (DL) {
-        if (DN) throw Error(PB_EINVAL, "double layer with target-normal derivative is not provided");
-        launch_leaf<T, YUK, true, false>(st, Tr, W, O, kappa);
-    } else {
-        if (DN) launch_leaf<T, YUK, false, true>(st, Tr, W, O, kappa);
-        else launch_leaf<T, YUK, false, false>(st, Tr, W, O, kappa);
-    }
+    if (DL) launch_leaf<T, YUK, true, false>(st, Tr, W, O, kappa);
+    else if (DN) launch_leaf<T, YUK, false, true>(st, Tr, W, O, kappa);
+    else launch_leaf<T, YUK, false, false>(st, Tr, W, O, kappa);
     ph.reset(); ph = std::make_unique<PhaseTimer>(ctx, PB_PH_SCATTER);
     const int* pt = Tr->same ? Tr->perm_s.p : Tr->perm_t.p;
     k_scatter<T, In><<<div_up(nt, 256), 256, 0, st>>>(nt, pt, W.pot.p, out);
     PB_CHECK_LAUNCH();
     if (DN) k_scatter<T, In><<<div_up(nt, 256), 256, 0, st>>>(nt, pt, W.dn.p, out_dn);
     if (DN) PB_CHECK_LAUNCH();
+    ph.reset();
+}
+
+// ---- paired apply: Laplace (operators OL) and Yukawa (OY) in one traversal
+template <typename T, bool DL>
+static void launch_p2check_pair(cudaStream_t st, int nbox, const int* boxes, int mode, fmm_tree* Tr, Work<T>& WL,
+                                Work<T>& WY, const Operators& O, T kappa) {
+    if (nbox <= 0) return;
+    if (O.npad <= 256)
+        k_p2check_pair<T, DL, 1><<<nbox, O.npad, 0, st>>>(nbox, boxes, mode, Tr->center.p, Tr->sb.p, Tr->se.p,
+                                                          Tr->X.p, Tr->X_n.p, WL.sq.p, WL.sm.p,
+                                                          (const float4*)O.surf_f.p, O.ne, O.npad, kappa, WL.chk.p,
+                                                          WY.chk.p);
+    else
+        k_p2check_pair<T, DL, 2><<<nbox, 256, 0, st>>>(nbox, boxes, mode, Tr->center.p, Tr->sb.p, Tr->se.p,
+                                                       Tr->X.p, Tr->X_n.p, WL.sq.p, WL.sm.p,
+                                                       (const float4*)O.surf_f.p, O.ne, O.npad, kappa, WL.chk.p,
+                                                       WY.chk.p);
+    PB_CHECK_LAUNCH();
+}
+
+template <typename T, bool DL, bool DN>
+static void launch_leaf_pair(cudaStream_t st, fmm_tree* Tr, Work<T>& WL, Work<T>& WY, const Operators& O, T kappa) {
+    if (Tr->n_tleaf <= 0) return;
+    const float4* tpos = Tr->same ? Tr->pos_s.p : Tr->pos_t.p;
+    const int* tb = Tr->same ? Tr->sb.p : Tr->tb.p;
+    const int* te = Tr->same ? Tr->se.p : Tr->te.p;
+    constexpr int NT = 2;
+    k_leaf_pair<T, DL, DN, NT><<<Tr->n_tleaf, 128, 0, st>>>(
+        Tr->leaf_ids.p, Tr->n_tleaf, tb, te, Tr->sb.p, Tr->se.p, Tr->U_off.p, Tr->U_ids.p, Tr->W_off.p, Tr->W_ids.p,
+        Tr->level.p, Tr->center.p, tpos, WL.tn.p, WL.sq.p, WL.sm.p, WL.Qu.p, WL.Qd.p, WY.Qu.p, WY.Qd.p,
+        (const float4*)O.surf_f.p, O.ne, O.npad, kappa, WL.pot.p, WY.pot.p, WL.dn.p, WY.dn.p);
+    PB_CHECK_LAUNCH();
+}
+
+template <typename T, typename In>
+static void apply_pair_t(fmm_tree* Tr, const Operators& OL, const Operators& OY, double kappa_d, const In* qL,
+                         const In* qY, const In* dip, const In* src_n, const In* tgt_n, In* outL, In* outY,
+                         In* dnL, In* dnY) {
+    cudaStream_t st = Tr->ctx->stream;
+    const long long ns = Tr->ns, nt = Tr->same ? Tr->ns : Tr->nt;
+    const T kappa = (T)kappa_d;
+    const bool DL = dip != nullptr, DN = dnL != nullptr;
+    if (DL && DN) throw Error(PB_EINVAL, "double layer with target-normal derivative is not provided");
+    Work<T> WL, WY;
+    WL.sq.alloc(ns, st);
+    WL.sm.alloc(ns, st);
+    alloc_far(WL, (size_t)Tr->nbox * OL.npad, st);
+    alloc_far(WY, (size_t)Tr->nbox * OY.npad, st);
+    WL.pot.alloc(nt, st);
+    WY.pot.alloc(nt, st);
+    if (DN) { WL.dn.alloc(nt, st); WY.dn.alloc(nt, st); WL.tn.alloc(nt, st); }
+    pb_ctx* ctx = Tr->ctx;
+    auto ph = std::make_unique<PhaseTimer>(ctx, PB_PH_GATHER);
+    k_gather_pair<T, In><<<div_up(ns, 256), 256, 0, st>>>(ns, Tr->perm_s.p, Tr->pos_s.p, qL, qY, dip, src_n, WL.sq.p,
+                                                           WL.sm.p);
+    PB_CHECK_LAUNCH();
+    if (DN) {
+        const int* pt = Tr->same ? Tr->perm_s.p : Tr->perm_t.p;
+        k_gather_tn<T, In><<<div_up(nt, 256), 256, 0, st>>>(nt, pt, tgt_n, WL.tn.p);
+        PB_CHECK_LAUNCH();
+    }
+    const int nsl = Tr->sleaf_lvl_off[Tr->nlev];
+    ph.reset(); ph = std::make_unique<PhaseTimer>(ctx, PB_PH_P2M);
+    if (DL) launch_p2check_pair<T, true>(st, nsl, Tr->sleaf_ids.p, 0, Tr, WL, WY, OL, kappa);
+    else launch_p2check_pair<T, false>(st, nsl, Tr->sleaf_ids.p, 0, Tr, WL, WY, OL, kappa);
+    far_uc2ue(Tr, OL, WL);
+    far_uc2ue(Tr, OY, WY);
+    ph.reset(); ph = std::make_unique<PhaseTimer>(ctx, PB_PH_M2M);
+    far_m2m(Tr, OL, WL);
+    far_m2m(Tr, OY, WY);
+    ph.reset(); ph = std::make_unique<PhaseTimer>(ctx, PB_PH_P2L);
+    if (Tr->n_xbox > 0) {
+        if (DL) launch_p2check_pair<T, true>(st, Tr->n_xbox, Tr->xbox_ids.p, 1, Tr, WL, WY, OL, kappa);
+        else launch_p2check_pair<T, false>(st, Tr->n_xbox, Tr->xbox_ids.p, 1, Tr, WL, WY, OL, kappa);
+        far_dc2de_x(Tr, OL, WL);
+        far_dc2de_x(Tr, OY, WY);
+    }
+    ph.reset(); ph = std::make_unique<PhaseTimer>(ctx, PB_PH_M2L);
+    far_m2l(Tr, OL, WL);
+    far_m2l(Tr, OY, WY);
+    ph.reset(); ph = std::make_unique<PhaseTimer>(ctx, PB_PH_DOWN);
+    far_l2l(Tr, OL, WL);
+    far_l2l(Tr, OY, WY);
+    ph.reset(); ph = std::make_unique<PhaseTimer>(ctx, PB_PH_LEAF);
+    if (DL) launch_leaf_pair<T, true, false>(st, Tr, WL, WY, OL, kappa);
+    else if (DN) launch_leaf_pair<T, false, true>(st, Tr, WL, WY, OL, kappa);
+    else launch_leaf_pair<T, false, false>(st, Tr, WL, WY, OL, kappa);
+    ph.reset(); ph = std::make_unique<PhaseTimer>(ctx, PB_PH_SCATTER);
+    const int* pt = Tr->same ? Tr->perm_s.p : Tr->perm_t.p;
+    k_scatter<T, In><<<div_up(nt, 256), 256, 0, st>>>(nt, pt, WL.pot.p, outL);
+    PB_CHECK_LAUNCH();
+    k_scatter<T, In><<<div_up(nt, 256), 256, 0, st>>>(nt, pt, WY.pot.p, outY);
+    PB_CHECK_LAUNCH();
+    if (DN) {
+        k_scatter<T, In><<<div_up(nt, 256), 256, 0, st>>>(nt, pt, WL.dn.p, dnL);
+        PB_CHECK_LAUNCH();
+        k_scatter<T, In><<<div_up(nt, 256), 256, 0, st>>>(nt, pt, WY.dn.p, dnY);
+        PB_CHECK_LAUNCH();
+    }
     ph.reset();
 }
 
@@ -770,6 +1192,23 @@ void fmm_apply_impl(fmm_tree* Tr, int kernel, double kappa, int p, int precision
         f(Tr, *O, kappa, (const float*)q, (const float*)dip, (const float*)src_n, (const float*)tgt_n, (float*)out,
           (float*)out_dn);
     }
+}
+
+
+void fmm_apply_pair_impl(fmm_tree* Tr, double kappa, int p, int precision, const void* qL, const void* qY,
+                         const void* dip, const void* src_n, const void* tgt_n, void* outL, void* outY, void* dnL,
+                         void* dnY) {
+    const bool fp64 = precision == PB_FP64;
+    auto OL = get_operators(Tr, FMM_LAPLACE, 0.0, p, fp64);
+    auto OY = get_operators(Tr, FMM_YUKAWA, kappa, p, fp64);
+    if (fp64)
+        apply_pair_t<double, double>(Tr, *OL, *OY, kappa, (const double*)qL, (const double*)qY, (const double*)dip,
+                                     (const double*)src_n, (const double*)tgt_n, (double*)outL, (double*)outY,
+                                     (double*)dnL, (double*)dnY);
+    else
+        apply_pair_t<float, float>(Tr, *OL, *OY, kappa, (const float*)qL, (const float*)qY, (const float*)dip,
+                                   (const float*)src_n, (const float*)tgt_n, (float*)outL, (float*)outY,
+                                   (float*)dnL, (float*)dnY);
 }
 
 }  // namespace pbfmm
