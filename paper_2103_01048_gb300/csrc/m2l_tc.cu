@@ -302,17 +302,43 @@ void build_pc_pairs(fmm_tree* T) {
 }
 
 // ---------------------------------------------------------------------------
-// the kernel
+// the kernel: warp-specialised pipeline
+//   warps 0-7   producers: two threads per pair row gather the source box's
+//               Qu row, split it into TF32 hi + lo and write it swizzled
+//               into a ring of kTcStages A stages (one K block each);
+//   warps 8-11  epilogue: one TMEM lane quarter each; read the finished
+//               accumulator and add every row into its target's Qd row;
+//   warp 12     one thread issues the MMAs and the commits.
+// Two TMEM accumulators alternate between tiles, so the epilogue of a tile
+// overlaps the MMAs of the next and the gathers of the one after.
 // ---------------------------------------------------------------------------
-constexpr int kTcStages = 3;            // A-tile ring depth
-constexpr int kTcThreads = 256;         // 8 warps: two threads per gathered row
+constexpr int kTcStages = 3;                    // A-stage ring depth
+constexpr int kTcProdWarps = 8;
+constexpr int kTcEpiWarps = 4;
+constexpr int kTcThreads = 32 * (kTcProdWarps + kTcEpiWarps + 1);
 
 struct TcSmem {
-    uint64_t barB, barMMA[kTcStages];
+    uint64_t barB, full[kTcStages], empty[kTcStages], accf[2], acce[2];
     uint32_t tmem_slot;
     int failed;
-    int src[kTcRows], tgt[kTcRows];
 };
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+// bounded wait that gives up as soon as another role of the CTA has failed;
+// a timeout marks the CTA failed
+__device__ __forceinline__ bool mbar_wait_cta(uint64_t* bar, uint32_t parity, volatile int* failed) {
+    long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity)) {
+        if (*failed) return false;
+        if (clock64() - t0 > 2000000000LL) {
+            *failed = 1;
+            return false;
+        }
+    }
+    return true;
+}
 
 template <int NPAD>
 __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(const int4* __restrict__ items, const int* __restrict__ ptgt,
@@ -327,22 +353,31 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(const int4* __restrict
     constexpr int KB = NPAD / 32;                    // K blocks of 32 tf32 (128 B)
     constexpr uint32_t B_SPLIT = KB * NH * 128;      // bytes of one of hi / lo
     constexpr uint32_t A_SPLIT = kTcRows * 128;      // 16 KB
-    constexpr uint32_t TCOLS = NH <= 32 ? 32 : (NH <= 64 ? 64 : (NH <= 128 ? 128 : 256));
+    constexpr uint32_t ACOLS = NH <= 32 ? 32 : (NH <= 64 ? 64 : 128);   // columns of one accumulator
+    constexpr uint32_t TCOLS = 2 * ACOLS;
     constexpr uint32_t IDESC = idesc_tf32(NH);
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint8_t* sB = smem;                               // [hi|lo][KB][NH][128]
     uint8_t* sA = smem + 2 * B_SPLIT;                 // [stage][hi|lo][128][128]
     TcSmem* S = (TcSmem*)(sA + kTcStages * 2 * A_SPLIT);
+    volatile int* failed = &S->failed;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int row = tid & (kTcRows - 1), part = tid >> 7;     // row of the A tile, chunk half
     const int4 it = items[blockIdx.x];
     const int half = blockIdx.y;
     const int first = it.x, npairs = it.y, opi = it.z;
+    const int ntile = (npairs + kTcRows - 1) / kTcRows;
 
     if (tid == 0) {
         mbar_init(&S->barB, 1);
-        for (int q = 0; q < kTcStages; ++q) mbar_init(&S->barMMA[q], 1);
+        for (int q = 0; q < kTcStages; ++q) {
+            mbar_init(&S->full[q], kTcProdWarps * 32);
+            mbar_init(&S->empty[q], 1);
+        }
+        for (int q = 0; q < 2; ++q) {
+            mbar_init(&S->accf[q], 1);
+            mbar_init(&S->acce[q], kTcEpiWarps * 32);
+        }
         S->failed = 0;
         fence_mbar_init();
     }
@@ -356,107 +391,123 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(const int4* __restrict
     const uint32_t taddr = S->tmem_slot;
 
     // resident operator half: hi and lo, one bulk copy each
-    const uint8_t* gB = (const uint8_t*)ops + ((long long)opi * 2 + half) * (2LL * B_SPLIT);
     if (tid == 0) {
+        const uint8_t* gB = (const uint8_t*)ops + ((long long)opi * 2 + half) * (2LL * B_SPLIT);
         mbar_arrive_expect_tx(&S->barB, 2 * B_SPLIT);
         bulk_g2s(sB, gB, B_SPLIT, &S->barB);
         bulk_g2s(sB + B_SPLIT, gB + B_SPLIT, B_SPLIT, &S->barB);
     }
-    bool ok = mbar_wait(&S->barB, 0);
-    uint32_t commits[kTcStages] = {0, 0, 0};
-    int last_stage = -1;
-    int step = 0;
-    const int ntile = (npairs + kTcRows - 1) / kTcRows;
-    if (__syncthreads_or(!ok)) goto fail;
 
-    for (int tile = 0; tile < ntile; ++tile) {
-        const int row0 = first + tile * kTcRows;
-        const int nrow = min(kTcRows, npairs - tile * kTcRows);
-        if (part == 0) {
-            S->src[row] = row < nrow ? psrc[row0 + row] : -1;
-            S->tgt[row] = row < nrow ? ptgt[row0 + row] : -1;
-        }
-        __syncthreads();
-        // all loads of this thread's half row for every K block at once: one
-        // memory latency per tile instead of one per K block
-        float4 v[KB][4];
-        {
-            const int sbox = S->src[row];
-            const float4* q4 = sbox >= 0 ? (const float4*)(Qu + (size_t)sbox * NPAD) : nullptr;
+    if (warp < kTcProdWarps) {
+        // ---- producers
+        const int row = tid & (kTcRows - 1), part = tid >> 7;
+        int g = 0;
+        int sbox = (row < npairs) ? psrc[first + row] : -1;
+        for (int tile = 0; tile < ntile; ++tile) {
+            // all loads of this thread's half row at once: one latency per tile
+            float4 v[KB][4];
+            {
+                const float4* q4 = sbox >= 0 ? (const float4*)(Qu + (size_t)sbox * NPAD) : nullptr;
 #pragma unroll
-            for (int kb = 0; kb < KB; ++kb)
+                for (int kb = 0; kb < KB; ++kb)
 #pragma unroll
-                for (int c = 0; c < 4; ++c) v[kb][c] = q4 ? q4[kb * 8 + part * 4 + c] : make_float4(0.f, 0.f, 0.f, 0.f);
-        }
-#pragma unroll
-        for (int kb = 0; kb < KB; ++kb, ++step) {
-            const int s = step % kTcStages;
-            if (commits[s] > 0) ok = mbar_wait(&S->barMMA[s], (commits[s] - 1) & 1);
-            if (__syncthreads_or(!ok)) goto fail;
-            // split into hi / lo and write swizzled into the stage
-            uint8_t* aHi = sA + (size_t)s * 2 * A_SPLIT;
-            uint8_t* aLo = aHi + A_SPLIT;
-#pragma unroll
-            for (int c = 0; c < 4; ++c) {
-                const float4 x = v[kb][c];
-                float4 h = make_float4(tf32_hi(x.x), tf32_hi(x.y), tf32_hi(x.z), tf32_hi(x.w));
-                float4 l = make_float4(x.x - h.x, x.y - h.y, x.z - h.z, x.w - h.w);
-                uint32_t off = sw128_off(row, (part * 4 + c) * 4);
-                *(float4*)(aHi + off) = h;
-                *(float4*)(aLo + off) = l;
+                    for (int c = 0; c < 4; ++c)
+                        v[kb][c] = q4 ? q4[kb * 8 + part * 4 + c] : make_float4(0.f, 0.f, 0.f, 0.f);
             }
-            fence_proxy_async();
-            __syncthreads();
-            if (tid == 0) {
-                tc_fence_after();
-                const uint32_t aH = smem_u32(aHi), aL = smem_u32(aLo);
-                const uint32_t bH = smem_u32(sB) + kb * NH * 128, bL = bH + B_SPLIT;
+            const int nr = (tile + 1) * kTcRows + row;
+            sbox = (tile + 1 < ntile && nr < npairs) ? psrc[first + nr] : -1;   // next tile's source
 #pragma unroll
-                for (int ks = 0; ks < 4; ++ks) {
-                    const uint32_t acc0 = (kb > 0 || ks > 0) ? 1u : 0u;
-                    mma_tf32(taddr, sw128_desc(aH + ks * 32), sw128_desc(bH + ks * 32), IDESC, acc0);
-                    mma_tf32(taddr, sw128_desc(aH + ks * 32), sw128_desc(bL + ks * 32), IDESC, 1u);
-                    mma_tf32(taddr, sw128_desc(aL + ks * 32), sw128_desc(bH + ks * 32), IDESC, 1u);
+            for (int kb = 0; kb < KB; ++kb, ++g) {
+                const int s = g % kTcStages, n = g / kTcStages;
+                if (n > 0 && !mbar_wait_cta(&S->empty[s], (n - 1) & 1, failed)) goto prod_done;
+                uint8_t* aHi = sA + (size_t)s * 2 * A_SPLIT;
+                uint8_t* aLo = aHi + A_SPLIT;
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                    const float4 x = v[kb][c];
+                    float4 h = make_float4(tf32_hi(x.x), tf32_hi(x.y), tf32_hi(x.z), tf32_hi(x.w));
+                    float4 l = make_float4(x.x - h.x, x.y - h.y, x.z - h.z, x.w - h.w);
+                    uint32_t off = sw128_off(row, (part * 4 + c) * 4);
+                    *(float4*)(aHi + off) = h;
+                    *(float4*)(aLo + off) = l;
                 }
-                mma_commit(&S->barMMA[s]);
+                fence_proxy_async();
+                mbar_arrive(&S->full[s]);
             }
-            commits[s]++;
-            last_stage = s;
         }
-        // accumulator complete once the last commit of the tile has arrived
-        ok = mbar_wait(&S->barMMA[last_stage], (commits[last_stage] - 1) & 1);
-        if (__syncthreads_or(!ok)) goto fail;
-        tc_fence_after();
-        {
-            // warps w and w + 4 read the same TMEM lane quarter, one column half each
-            const int erow = (warp & 3) * 32 + lane;
-            const int t = S->tgt[erow];
-            const int c_lo = part * (NH / 2);
+    prod_done:
+        __syncwarp();
+    } else if (warp < kTcProdWarps + kTcEpiWarps) {
+        // ---- epilogue: warp w reads TMEM lanes 32 (w % 4) ... + 31
+        const int q = warp & 3;
+        const int erow = q * 32 + lane;
+        for (int tile = 0; tile < ntile; ++tile) {
+            const int a = tile & 1, u = tile >> 1;
+            const int r = tile * kTcRows + erow;
+            const int t = r < npairs ? ptgt[first + r] : -1;
+            bool ok = mbar_wait_cta(&S->accf[a], u & 1, failed);
+            if (!__all_sync(0xffffffffu, ok)) break;
+            tc_fence_after();
             float* dst = t >= 0 ? Qd + (size_t)t * NPAD + half * NH : nullptr;
 #pragma unroll 1
-            for (int c0 = c_lo; c0 < c_lo + NH / 2; c0 += 8) {
+            for (int c0 = 0; c0 < NH; c0 += 8) {
                 float v[8];
-                tmem_ld8(taddr + ((uint32_t)((warp & 3) * 32) << 16) + c0, v);
+                tmem_ld8(taddr + ((uint32_t)(q * 32) << 16) + a * ACOLS + c0, v);
                 if (dst) {
                     red_add_v4(dst + c0, v[0], v[1], v[2], v[3]);
                     red_add_v4(dst + c0 + 4, v[4], v[5], v[6], v[7]);
                 }
             }
+            tc_fence_before();
+            mbar_arrive(&S->acce[a]);
         }
-        tc_fence_before();
-        __syncthreads();
+        __syncwarp();
+    } else {
+        // ---- MMA issuer
+        if (lane == 0) {
+            uint64_t* last = nullptr;      // barrier of the last commit, and its phase parity
+            uint32_t last_par = 0;
+            int g = 0;
+            bool ok = mbar_wait_cta(&S->barB, 0, failed);
+            for (int tile = 0; ok && tile < ntile; ++tile) {
+                const int a = tile & 1, u = tile >> 1;
+                if (u > 0 && !(ok = mbar_wait_cta(&S->acce[a], (u - 1) & 1, failed))) break;
+                const uint32_t dacc = taddr + a * ACOLS;
+                for (int kb = 0; kb < KB; ++kb, ++g) {
+                    const int s = g % kTcStages, n = g / kTcStages;
+                    if (!(ok = mbar_wait_cta(&S->full[s], n & 1, failed))) break;
+                    tc_fence_after();
+                    const uint32_t aH = smem_u32(sA + (size_t)s * 2 * A_SPLIT), aL = aH + A_SPLIT;
+                    const uint32_t bH = smem_u32(sB) + kb * NH * 128, bL = bH + B_SPLIT;
+#pragma unroll
+                    for (int ks = 0; ks < 4; ++ks) {
+                        const uint32_t acc0 = (kb > 0 || ks > 0) ? 1u : 0u;
+                        mma_tf32(dacc, sw128_desc(aH + ks * 32), sw128_desc(bH + ks * 32), IDESC, acc0);
+                        mma_tf32(dacc, sw128_desc(aH + ks * 32), sw128_desc(bL + ks * 32), IDESC, 1u);
+                        mma_tf32(dacc, sw128_desc(aL + ks * 32), sw128_desc(bH + ks * 32), IDESC, 1u);
+                    }
+                    mma_commit(&S->empty[s]);
+                    last = &S->empty[s];
+                    last_par = n & 1;
+                }
+                if (!ok) break;
+                mma_commit(&S->accf[a]);
+                last = &S->accf[a];
+                last_par = u & 1;
+            }
+            // after a failure: every MMA issued here has completed before TMEM is freed
+            if (!ok && last) mbar_wait(last, last_par);
+        }
+        __syncwarp();
     }
-    goto done;
 
-fail:
-    if (tid == 0) atomicExch(err, 1);
-    // drain: every MMA this CTA issued has been committed; wait (bounded) for the last
-    if (last_stage >= 0) mbar_wait(&S->barMMA[last_stage], (commits[last_stage] - 1) & 1);
-    mbar_wait(&S->barB, 0);
-done:
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
+    if (tid == 0 && S->failed) {
+        atomicExch(err, 1);
+        mbar_wait(&S->barB, 0);         // the operator copy has landed before shared memory is released
+    }
     if (warp == 0) tmem_dealloc(taddr, TCOLS);
 }
 
