@@ -401,21 +401,27 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(const int4* __restrict
     if (warp < kTcProdWarps) {
         // ---- producers
         const int row = tid & (kTcRows - 1), part = tid >> 7;
+        auto src_of = [&](int tile) -> int {
+            const int r = tile * kTcRows + row;
+            return (tile < ntile && r < npairs) ? psrc[first + r] : -1;
+        };
+        // Register rotation: once K block kb of a tile is in its stage, the
+        // same registers load block kb of the next tile, so each gather has a
+        // whole tile of MMA time to arrive.
+        float4 v[KB][4];
+        {
+            const int s0 = src_of(0);
+            const float4* q4 = s0 >= 0 ? (const float4*)(Qu + (size_t)s0 * NPAD) : nullptr;
+#pragma unroll
+            for (int kb = 0; kb < KB; ++kb)
+#pragma unroll
+                for (int c = 0; c < 4; ++c)
+                    v[kb][c] = q4 ? q4[kb * 8 + part * 4 + c] : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
         int g = 0;
-        int sbox = (row < npairs) ? psrc[first + row] : -1;
+        int snext = src_of(1);
         for (int tile = 0; tile < ntile; ++tile) {
-            // all loads of this thread's half row at once: one latency per tile
-            float4 v[KB][4];
-            {
-                const float4* q4 = sbox >= 0 ? (const float4*)(Qu + (size_t)sbox * NPAD) : nullptr;
-#pragma unroll
-                for (int kb = 0; kb < KB; ++kb)
-#pragma unroll
-                    for (int c = 0; c < 4; ++c)
-                        v[kb][c] = q4 ? q4[kb * 8 + part * 4 + c] : make_float4(0.f, 0.f, 0.f, 0.f);
-            }
-            const int nr = (tile + 1) * kTcRows + row;
-            sbox = (tile + 1 < ntile && nr < npairs) ? psrc[first + nr] : -1;   // next tile's source
+            const float4* qn = snext >= 0 ? (const float4*)(Qu + (size_t)snext * NPAD) : nullptr;
 #pragma unroll
             for (int kb = 0; kb < KB; ++kb, ++g) {
                 const int s = g % kTcStages, n = g / kTcStages;
@@ -433,7 +439,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(const int4* __restrict
                 }
                 fence_proxy_async();
                 mbar_arrive(&S->full[s]);
+#pragma unroll
+                for (int c = 0; c < 4; ++c)
+                    v[kb][c] = qn ? qn[kb * 8 + part * 4 + c] : make_float4(0.f, 0.f, 0.f, 0.f);
             }
+            snext = src_of(tile + 2);
         }
     prod_done:
         __syncwarp();
