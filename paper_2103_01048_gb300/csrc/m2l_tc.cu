@@ -317,7 +317,13 @@ constexpr int kTcProdWarps = 8;
 constexpr int kTcEpiWarps = 4;
 constexpr int kTcThreads = 32 * (kTcProdWarps + kTcEpiWarps + 1);
 
+constexpr int kTcEpiLd = 16;                    // accumulator columns per epilogue TMEM load
+constexpr int kTcEpiStride = 20;                // padded row of the epilogue transpose buffer (floats)
+
 struct TcSmem {
+    // per epilogue warp: 32 rows x kTcEpiLd columns, transposed through shared
+    // memory so that each reduction instruction covers 8 rows x 64 B
+    alignas(16) float epi[kTcEpiWarps][32][kTcEpiStride];
     uint64_t barB, full[kTcStages], empty[kTcStages], accf[2], acce[2];
     uint32_t tmem_slot;
     int failed;
@@ -399,29 +405,30 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(const int4* __restrict
     }
 
     if (warp < kTcProdWarps) {
-        // ---- producers
-        const int row = tid & (kTcRows - 1), part = tid >> 7;
-        auto src_of = [&](int tile) -> int {
-            const int r = tile * kTcRows + row;
+        // ---- producers: lane l8 = lane % 8 carries 16 B of a 128-B K-block row;
+        // a warp instruction covers 4 whole rows (coalesced). Thread rows:
+        // i * 32 + warp * 4 + lane / 8, i = 0..3.
+        const int l8 = lane & 7, rbase = warp * 4 + (lane >> 3);
+        auto src_of = [&](int tile, int i) -> int {
+            const int r = tile * kTcRows + i * 32 + rbase;
             return (tile < ntile && r < npairs) ? psrc[first + r] : -1;
         };
         // Register rotation: once K block kb of a tile is in its stage, the
         // same registers load block kb of the next tile, so each gather has a
         // whole tile of MMA time to arrive.
         float4 v[KB][4];
-        {
-            const int s0 = src_of(0);
+        int sn[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int s0 = src_of(0, i);
             const float4* q4 = s0 >= 0 ? (const float4*)(Qu + (size_t)s0 * NPAD) : nullptr;
 #pragma unroll
-            for (int kb = 0; kb < KB; ++kb)
-#pragma unroll
-                for (int c = 0; c < 4; ++c)
-                    v[kb][c] = q4 ? q4[kb * 8 + part * 4 + c] : make_float4(0.f, 0.f, 0.f, 0.f);
+            for (int kb = 0; kb < KB; ++kb) v[kb][i] = q4 ? q4[kb * 8 + l8] : make_float4(0.f, 0.f, 0.f, 0.f);
         }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) sn[i] = src_of(1, i);
         int g = 0;
-        int snext = src_of(1);
         for (int tile = 0; tile < ntile; ++tile) {
-            const float4* qn = snext >= 0 ? (const float4*)(Qu + (size_t)snext * NPAD) : nullptr;
 #pragma unroll
             for (int kb = 0; kb < KB; ++kb, ++g) {
                 const int s = g % kTcStages, n = g / kTcStages;
@@ -429,21 +436,24 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(const int4* __restrict
                 uint8_t* aHi = sA + (size_t)s * 2 * A_SPLIT;
                 uint8_t* aLo = aHi + A_SPLIT;
 #pragma unroll
-                for (int c = 0; c < 4; ++c) {
-                    const float4 x = v[kb][c];
+                for (int i = 0; i < 4; ++i) {
+                    const float4 x = v[kb][i];
                     float4 h = make_float4(tf32_hi(x.x), tf32_hi(x.y), tf32_hi(x.z), tf32_hi(x.w));
                     float4 l = make_float4(x.x - h.x, x.y - h.y, x.z - h.z, x.w - h.w);
-                    uint32_t off = sw128_off(row, (part * 4 + c) * 4);
+                    uint32_t off = sw128_off(i * 32 + rbase, l8 * 4);
                     *(float4*)(aHi + off) = h;
                     *(float4*)(aLo + off) = l;
                 }
                 fence_proxy_async();
                 mbar_arrive(&S->full[s]);
 #pragma unroll
-                for (int c = 0; c < 4; ++c)
-                    v[kb][c] = qn ? qn[kb * 8 + part * 4 + c] : make_float4(0.f, 0.f, 0.f, 0.f);
+                for (int i = 0; i < 4; ++i) {
+                    const float4* qn = sn[i] >= 0 ? (const float4*)(Qu + (size_t)sn[i] * NPAD) : nullptr;
+                    v[kb][i] = qn ? qn[kb * 8 + l8] : make_float4(0.f, 0.f, 0.f, 0.f);
+                }
             }
-            snext = src_of(tile + 2);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) sn[i] = src_of(tile + 2, i);
         }
     prod_done:
         __syncwarp();
@@ -458,15 +468,24 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(const int4* __restrict
             bool ok = mbar_wait_cta(&S->accf[a], u & 1, failed);
             if (!__all_sync(0xffffffffu, ok)) break;
             tc_fence_after();
-            float* dst = t >= 0 ? Qd + (size_t)t * NPAD + half * NH : nullptr;
+            float (*buf)[kTcEpiStride] = S->epi[q];
 #pragma unroll 1
-            for (int c0 = 0; c0 < NH; c0 += 8) {
-                float v[8];
-                tmem_ld8(taddr + ((uint32_t)(q * 32) << 16) + a * ACOLS + c0, v);
-                if (dst) {
-                    red_add_v4(dst + c0, v[0], v[1], v[2], v[3]);
-                    red_add_v4(dst + c0 + 4, v[4], v[5], v[6], v[7]);
+            for (int c0 = 0; c0 < NH; c0 += kTcEpiLd) {
+                float v[kTcEpiLd];
+                tmem_ld16(taddr + ((uint32_t)(q * 32) << 16) + a * ACOLS + c0, v);
+#pragma unroll
+                for (int c = 0; c < kTcEpiLd; c += 4)
+                    *(float4*)&buf[lane][c] = make_float4(v[c], v[c + 1], v[c + 2], v[c + 3]);
+                __syncwarp();
+                // lane: row j * 8 + lane / 4 of the warp's 32, columns 4 (lane % 4) .. + 3
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int rr = j * 8 + (lane >> 2), cc = (lane & 3) * 4;
+                    const float4 x = *(const float4*)&buf[rr][cc];
+                    const int tr = __shfl_sync(0xffffffffu, t, rr);
+                    if (tr >= 0) red_add_v4(Qd + (size_t)tr * NPAD + half * NH + c0 + cc, x.x, x.y, x.z, x.w);
                 }
+                __syncwarp();
             }
             tc_fence_before();
             mbar_arrive(&S->acce[a]);
