@@ -281,73 +281,6 @@ __global__ void __launch_bounds__(256) k_p2check_pair(int nbox, const int* __res
     }
 }
 
-// Check potential -> equivalent density, X (float) -> Y (float), with the
-// ill-conditioned operator (UC2UE or DC2DE, norm ~1e6) held as an FP32 pair
-// op = hi + lo and every product and sum carried in double-float
-// (error-free product by FMA, TwoSum accumulation): ~48-bit arithmetic on
-// the FP32 pipes instead of the FP64 units.
-template <int NPAD>
-__global__ void __launch_bounds__(256) k_check2equiv_df(int ncols, const int* __restrict__ cols, int col_base,
-                                                        const float* __restrict__ op_hi,
-                                                        const float* __restrict__ op_lo, const float* __restrict__ Xv,
-                                                        float* __restrict__ Yv) {
-    constexpr int KC = NPAD > 256 ? 8 : 16;
-    constexpr int RPT = NPAD / 16;
-    __shared__ float s_h[KC][NPAD + 1];
-    __shared__ float s_l[KC][NPAD + 1];
-    __shared__ float s_x[KC][kTC + 1];
-    __shared__ int s_box[kTC];
-    const int tid = threadIdx.x, ty = tid / 16, tx = tid % 16;
-    if (tid < kTC) {
-        int ci = blockIdx.x * kTC + tid;
-        s_box[tid] = ci < ncols ? (cols ? cols[ci] : col_base + ci) : -1;
-    }
-    float sum[RPT][2], cmp[RPT][2];
-#pragma unroll
-    for (int r = 0; r < RPT; ++r) sum[r][0] = sum[r][1] = cmp[r][0] = cmp[r][1] = 0.f;
-    for (int k0 = 0; k0 < NPAD; k0 += KC) {
-        __syncthreads();
-        for (int i = tid; i < NPAD * KC; i += 256) {
-            int row = i / KC, kk = i % KC;
-            s_h[kk][row] = op_hi[(size_t)row * NPAD + k0 + kk];
-            s_l[kk][row] = op_lo[(size_t)row * NPAD + k0 + kk];
-        }
-        for (int i = tid; i < kTC * KC; i += 256) {
-            int c = i / KC, kk = i % KC;
-            int s = s_box[c];
-            s_x[kk][c] = (s >= 0) ? Xv[(size_t)s * NPAD + k0 + kk] : 0.f;
-        }
-        __syncthreads();
-#pragma unroll
-        for (int kk = 0; kk < KC; ++kk) {
-            float x[2] = {s_x[kk][2 * tx], s_x[kk][2 * tx + 1]};
-#pragma unroll
-            for (int r = 0; r < RPT; ++r) {
-                float oh = s_h[kk][ty + 16 * r], ol = s_l[kk][ty + 16 * r];
-#pragma unroll
-                for (int cc = 0; cc < 2; ++cc) {
-                    float p = __fmul_rn(oh, x[cc]);
-                    float e = fmaf(oh, x[cc], -p);          // exact error of oh * x
-                    e = fmaf(ol, x[cc], e);
-                    float s = sum[r][cc];
-                    float t = __fadd_rn(s, p);               // TwoSum(s, p)
-                    float bp = __fsub_rn(t, s);
-                    float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(p, bp));
-                    sum[r][cc] = t;
-                    cmp[r][cc] += err + e;
-                }
-            }
-        }
-    }
-#pragma unroll
-    for (int cc = 0; cc < 2; ++cc) {
-        int d = s_box[2 * tx + cc];
-        if (d < 0) continue;
-#pragma unroll
-        for (int r = 0; r < RPT; ++r) Yv[(size_t)d * NPAD + ty + 16 * r] = sum[r][cc] + cmp[r][cc];
-    }
-}
-
 // ---------------------------------------------------------------------------
 // Dense operator x box-vector products (UC2UE, DC2DE, M2M, L2L, M2L), SIMT.
 // A CTA computes C[npad x 32 boxes] = sum over terms of Op_term x X_gathered,
@@ -809,6 +742,7 @@ template <typename T>
 struct Work {
     DBuf<typename V4<T>::type> sq, sm, tn;
     DBuf<T> Qu, Qd, chk, pot, dn;
+    DBuf<T> tmp;          // FP32 path: intermediate of the factored check -> equivalent solves
 };
 
 template <typename T, typename TO, int NPAD>
@@ -853,46 +787,22 @@ static void launch_p2check(cudaStream_t st, int nbox, const int* boxes, int mode
     PB_CHECK_LAUNCH();
 }
 
-template <int NPAD>
-static void launch_df(cudaStream_t st, int ncols, const int* cols, int base, const float* hi, const float* lo,
-                      const float* X, float* Y) {
-    k_check2equiv_df<NPAD><<<div_up(ncols, kTC), 256, 0, st>>>(ncols, cols, base, hi, lo, X, Y);
-    PB_CHECK_LAUNCH();
-}
-
-// Y[col] = (hi + lo) X[col] for ncols boxes (double-float accumulation)
-static void check2equiv_df(int npad, cudaStream_t st, int ncols, const int* cols, int base, const float* hi,
-                           const float* lo, const float* X, float* Y) {
-    if (ncols <= 0) return;
-    switch (npad) {
-        case 32: launch_df<32>(st, ncols, cols, base, hi, lo, X, Y); break;
-        case 64: launch_df<64>(st, ncols, cols, base, hi, lo, X, Y); break;
-        case 128: launch_df<128>(st, ncols, cols, base, hi, lo, X, Y); break;
-        case 160: launch_df<160>(st, ncols, cols, base, hi, lo, X, Y); break;
-        case 224: launch_df<224>(st, ncols, cols, base, hi, lo, X, Y); break;
-        case 320: launch_df<320>(st, ncols, cols, base, hi, lo, X, Y); break;
-        case 416: launch_df<416>(st, ncols, cols, base, hi, lo, X, Y); break;
-        case 512: launch_df<512>(st, ncols, cols, base, hi, lo, X, Y); break;
-        default: throw Error(PB_EINVAL, "unsupported expansion order");
-    }
-}
-
-// the two check -> equivalent conversions: FP64 for the FP64 path,
-// double-float for the FP32 path
+// the two check -> equivalent conversions: the FP64 solve for the FP64
+// path; for the FP32 path the factored solve Y = W2 (W1 X), two FP32
+// passes through `tmp` (box-major like X and Y)
 template <typename T>
 static void check2equiv(const Operators& O, int level, bool up, cudaStream_t st, GemmArgs ga, int ncols,
-                        const int* cols, const T* X, T* Y);
+                        const int* cols, const T* X, T* Y, T* tmp);
 template <>
-void check2equiv<float>(const Operators& O, int level, bool up, cudaStream_t st, GemmArgs, int ncols,
-                        const int* cols, const float* X, float* Y) {
-    const size_t m2 = (size_t)O.npad * O.npad;
-    const float* hi = (up ? O.uc2ue_hi.p : O.dc2de_hi.p) + level * m2;
-    const float* lo = (up ? O.uc2ue_lo.p : O.dc2de_lo.p) + level * m2;
-    check2equiv_df(O.npad, st, ncols, cols, 0, hi, lo, X, Y);
+void check2equiv<float>(const Operators& O, int level, bool up, cudaStream_t st, GemmArgs ga, int ncols,
+                        const int* cols, const float* X, float* Y, float* tmp) {
+    ga.mode = G_DENSE; ga.ncols = ncols; ga.cols = cols; ga.col_base = 0; ga.level = level; ga.accumulate = 0;
+    gemm_dispatch<float, float>(O.npad, st, div_up(ncols, kTC), ga, up ? O.uc2ue_w1.p : O.dc2de_w1.p, X, tmp);
+    gemm_dispatch<float, float>(O.npad, st, div_up(ncols, kTC), ga, up ? O.uc2ue_w2.p : O.dc2de_w2.p, tmp, Y);
 }
 template <>
 void check2equiv<double>(const Operators& O, int level, bool up, cudaStream_t st, GemmArgs ga, int ncols,
-                         const int* cols, const double* X, double* Y) {
+                         const int* cols, const double* X, double* Y, double*) {
     ga.mode = G_DENSE; ga.ncols = ncols; ga.cols = cols; ga.col_base = 0; ga.level = level; ga.accumulate = 0;
     gemm_dispatch<double, double>(O.npad, st, div_up(ncols, kTC), ga, up ? O.uc2ue_d.p : O.dc2de_d.p, X, Y);
 }
@@ -937,7 +847,7 @@ static void far_uc2ue(fmm_tree* Tr, const Operators& O, Work<T>& W) {
     for (int l = 0; l < Tr->nlev; ++l) {
         int a0 = Tr->sleaf_lvl_off[l], a1 = Tr->sleaf_lvl_off[l + 1];
         if (a1 <= a0) continue;
-        check2equiv<T>(O, l, true, Tr->ctx->stream, ga, a1 - a0, Tr->sleaf_ids.p + a0, W.chk.p, W.Qu.p);
+        check2equiv<T>(O, l, true, Tr->ctx->stream, ga, a1 - a0, Tr->sleaf_ids.p + a0, W.chk.p, W.Qu.p, W.tmp.p);
     }
 }
 
@@ -967,7 +877,7 @@ static void far_dc2de_x(fmm_tree* Tr, const Operators& O, Work<T>& W) {
     for (int l = 0; l < Tr->nlev; ++l) {
         int a0 = Tr->xbox_lvl_off[l], a1 = Tr->xbox_lvl_off[l + 1];
         if (a1 <= a0) continue;
-        check2equiv<T>(O, l, false, Tr->ctx->stream, ga, a1 - a0, Tr->xbox_ids.p + a0, W.chk.p, W.Qd.p);
+        check2equiv<T>(O, l, false, Tr->ctx->stream, ga, a1 - a0, Tr->xbox_ids.p + a0, W.chk.p, W.Qd.p, W.tmp.p);
     }
 }
 
@@ -1018,6 +928,7 @@ static void alloc_far(Work<T>& W, size_t nbox_npad, cudaStream_t st) {
     W.Qu.zero(st);
     W.Qd.zero(st);
     W.chk.zero(st);
+    if (std::is_same<T, float>::value) W.tmp.alloc(nbox_npad, st);
 }
 
 template <typename T, typename In, bool YUK>

@@ -24,7 +24,8 @@ struct Operators {
     DBuf<float> surf_f;           // [ne][4] float copy (x, y, z, 0)
     // FP32 copies
     DBuf<float> uc2ue, dc2de;     // [nlev][npad^2]
-    DBuf<float> uc2ue_hi, uc2ue_lo, dc2de_hi, dc2de_lo;   // FP32 pairs of the FP64 solves
+    // factored solves of the FP32 path: pinv = W2 W1 (W1 = D V^T K^T, W2 = V)
+    DBuf<float> uc2ue_w1, uc2ue_w2, dc2de_w1, dc2de_w2;   // [nlev][npad^2]
     DBuf<float> m2m, l2l;         // [nlev][8][npad^2]  (child level index)
     DBuf<float> m2l;              // [nlev][343][npad^2]
     // tensor-core M2L (p <= 6): per level and offset, the operator split into

@@ -11,13 +11,23 @@
 // The pseudo-inverses have norms ~1e6-1e7, so a product with one of them
 // computed in FP32 loses every digit; folded into the translations above
 // (in FP64) the operators have norms of order 1-100 and are stored in FP32.
-// UC2UE / DC2DE themselves are kept in FP64 for the two places where raw
-// check potentials are converted (P2M at leaves, P2L of X lists).
+// UC2UE / DC2DE themselves are needed where raw check potentials are
+// converted (P2M at leaves, P2L of X lists): in FP64 for the all-FP64 path,
+// and for the FP32 path in factored form, pinv = V D V^T K^T with
+// K^T K = V diag(mu) V^T (cyclic Jacobi, FP64, on the host) and
+// D = diag(1 / (mu + lam)): W1 = D V^T K^T and W2 = V are well scaled, and the
+// FP32 rounding of W1 x is amplified only along eigenvectors of small mu,
+// whose equivalent densities produce correspondingly small fields away from
+// the surfaces (the part of the potential the FMM uses).
 // The paper says only "solve the linear systems"; the regularised solve used
 // here is Tikhonov: pinv(K) = (K^T K + lam I)^{-1} K^T with
-// lam = (1e-7 ||K||_F)^2, by a Cholesky factorisation.
+// lam = (1e-7 ||K||_F)^2, by a Cholesky factorisation (FP64 path) or the
+// eigendecomposition above (FP32 path).
 #include "fmm.cuh"
+#include <algorithm>
+#include <atomic>
 #include <cmath>
+#include <thread>
 
 namespace pbfmm {
 
@@ -108,14 +118,90 @@ __global__ void k_matmul(int n, const double* __restrict__ A, const double* __re
     C[idx] = s;
 }
 
-__global__ void k_split_pair(long long n, const double* __restrict__ src, float* __restrict__ hi,
-                             float* __restrict__ lo) {
-    long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    double v = src[i];
-    float h = (float)v;
-    hi[i] = h;
-    lo[i] = (float)(v - (double)h);
+// Symmetric eigendecomposition A = V diag(w) V^T by the cyclic Jacobi method
+// (plane rotations that annihilate one off-diagonal entry each, with the
+// rotation angle from theta = (a_qq - a_pp) / (2 a_pq), t = sgn(theta) /
+// (|theta| + sqrt(theta^2 + 1))). A (n x n, row-major) is overwritten.
+static void jacobi_eig(int n, std::vector<double>& A, std::vector<double>& V, std::vector<double>& w) {
+    V.assign((size_t)n * n, 0.0);
+    for (int i = 0; i < n; ++i) V[(size_t)i * n + i] = 1.0;
+    for (int sweep = 0; sweep < 60; ++sweep) {
+        double off = 0.0, dg = 0.0;
+        for (int i = 0; i < n; ++i) {
+            dg += A[(size_t)i * n + i] * A[(size_t)i * n + i];
+            for (int j = i + 1; j < n; ++j) off += A[(size_t)i * n + j] * A[(size_t)i * n + j];
+        }
+        if (off <= 1e-32 * dg) break;
+        for (int p = 0; p < n - 1; ++p)
+            for (int q = p + 1; q < n; ++q) {
+                const double apq = A[(size_t)p * n + q];
+                const double app = A[(size_t)p * n + p], aqq = A[(size_t)q * n + q];
+                if (std::fabs(apq) <= 1e-18 * std::sqrt(std::fabs(app * aqq))) {
+                    A[(size_t)p * n + q] = A[(size_t)q * n + p] = 0.0;
+                    continue;
+                }
+                const double th = (aqq - app) / (2.0 * apq);
+                const double t = (th >= 0 ? 1.0 : -1.0) / (std::fabs(th) + std::sqrt(th * th + 1.0));
+                const double c = 1.0 / std::sqrt(t * t + 1.0), sn = t * c;
+                for (int k = 0; k < n; ++k) {
+                    const double akp = A[(size_t)k * n + p], akq = A[(size_t)k * n + q];
+                    A[(size_t)k * n + p] = c * akp - sn * akq;
+                    A[(size_t)k * n + q] = sn * akp + c * akq;
+                }
+                for (int k = 0; k < n; ++k) {
+                    const double apk = A[(size_t)p * n + k], aqk = A[(size_t)q * n + k];
+                    A[(size_t)p * n + k] = c * apk - sn * aqk;
+                    A[(size_t)q * n + k] = sn * apk + c * aqk;
+                }
+                for (int k = 0; k < n; ++k) {
+                    const double vkp = V[(size_t)k * n + p], vkq = V[(size_t)k * n + q];
+                    V[(size_t)k * n + p] = c * vkp - sn * vkq;
+                    V[(size_t)k * n + q] = sn * vkp + c * vkq;
+                }
+            }
+    }
+    w.resize(n);
+    for (int i = 0; i < n; ++i) w[i] = A[(size_t)i * n + i];
+}
+
+// Factored Tikhonov pseudo-inverse of K(check surface at scale tscale,
+// equivalent surface at scale sscale), both centred at the origin:
+// W1 = D V^T K^T and W2 = V, written padded to npad x npad in FP32.
+static void factored_pinv(int n, int npad, int kernel, double kappa, const std::vector<double>& surf, double tscale,
+                          double sscale, float* W1, float* W2) {
+    std::vector<double> K((size_t)n * n), G((size_t)n * n), V, mu;
+    double fro = 0.0;
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) {
+            const double dx = tscale * surf[3 * i] - sscale * surf[3 * j];
+            const double dy = tscale * surf[3 * i + 1] - sscale * surf[3 * j + 1];
+            const double dz = tscale * surf[3 * i + 2] - sscale * surf[3 * j + 2];
+            const double r = std::sqrt(dx * dx + dy * dy + dz * dz);
+            double g = kInv4Pi / r;
+            if (kernel == FMM_YUKAWA) g *= std::exp(-kappa * r);
+            K[(size_t)i * n + j] = g;
+            fro += g * g;
+        }
+    for (int i = 0; i < n; ++i)
+        for (int j = i; j < n; ++j) {
+            double a = 0.0;
+            for (int k = 0; k < n; ++k) a += K[(size_t)k * n + i] * K[(size_t)k * n + j];
+            G[(size_t)i * n + j] = G[(size_t)j * n + i] = a;
+        }
+    jacobi_eig(n, G, V, mu);
+    const double lam = 1e-14 * fro;
+    std::fill(W1, W1 + (size_t)npad * npad, 0.f);
+    std::fill(W2, W2 + (size_t)npad * npad, 0.f);
+    for (int j = 0; j < n; ++j) {
+        const double d = 1.0 / (std::max(mu[j], 0.0) + lam);
+        for (int i = 0; i < n; ++i) {
+            double a = 0.0;
+            for (int k = 0; k < n; ++k) a += K[(size_t)i * n + k] * V[(size_t)k * n + j];
+            W1[(size_t)j * npad + i] = (float)(d * a);
+        }
+    }
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) W2[(size_t)i * npad + j] = (float)V[(size_t)i * n + j];
 }
 
 __global__ void k_store_padded(int n, int npad, const double* __restrict__ src, float* __restrict__ dst_f,
@@ -249,11 +335,42 @@ std::shared_ptr<Operators> get_operators(fmm_tree* T, int kernel, double kappa, 
         }
         PB_CHECK_LAUNCH();
     }
-    O->uc2ue_hi.alloc(L * m2, st); O->uc2ue_lo.alloc(L * m2, st);
-    O->dc2de_hi.alloc(L * m2, st); O->dc2de_lo.alloc(L * m2, st);
-    k_split_pair<<<div_up(L * m2, 256), 256, 0, st>>>(L * m2, O->uc2ue_d.p, O->uc2ue_hi.p, O->uc2ue_lo.p);
-    k_split_pair<<<div_up(L * m2, 256), 256, 0, st>>>(L * m2, O->dc2de_d.p, O->dc2de_hi.p, O->dc2de_lo.p);
-    PB_CHECK_LAUNCH();
+    // factored UC2UE / DC2DE for the FP32 path: one host job per level and
+    // direction, spread over the host cores
+    {
+        std::vector<float> w1((size_t)2 * L * m2), w2((size_t)2 * L * m2);
+        std::atomic<int> next(0);
+        auto work = [&]() {
+            for (int job; (job = next.fetch_add(1)) < 2 * L;) {
+                const int l = job / 2;
+                const bool up = (job % 2) == 0;
+                const double r = std::ldexp(T->R, -l);
+                factored_pinv(n, np, kernel, kappa, s, (up ? kAlphaOuter : kAlphaInner) * r,
+                              (up ? kAlphaInner : kAlphaOuter) * r, w1.data() + (size_t)job * m2,
+                              w2.data() + (size_t)job * m2);
+            }
+        };
+        const int nth = std::max(1, std::min<int>(2 * L, (int)std::thread::hardware_concurrency()));
+        std::vector<std::thread> pool;
+        for (int t = 1; t < nth; ++t) pool.emplace_back(work);
+        work();
+        for (auto& th : pool) th.join();
+        // [job = 2 l + (0 up, 1 down)] -> [level] per direction
+        std::vector<float> u1((size_t)L * m2), u2((size_t)L * m2), d1((size_t)L * m2), d2((size_t)L * m2);
+        for (int l = 0; l < L; ++l) {
+            std::copy_n(w1.data() + (size_t)(2 * l) * m2, m2, u1.data() + (size_t)l * m2);
+            std::copy_n(w2.data() + (size_t)(2 * l) * m2, m2, u2.data() + (size_t)l * m2);
+            std::copy_n(w1.data() + (size_t)(2 * l + 1) * m2, m2, d1.data() + (size_t)l * m2);
+            std::copy_n(w2.data() + (size_t)(2 * l + 1) * m2, m2, d2.data() + (size_t)l * m2);
+        }
+        O->uc2ue_w1.alloc(L * m2, st); O->uc2ue_w2.alloc(L * m2, st);
+        O->dc2de_w1.alloc(L * m2, st); O->dc2de_w2.alloc(L * m2, st);
+        PB_CUDA(cudaMemcpyAsync(O->uc2ue_w1.p, u1.data(), L * m2 * sizeof(float), cudaMemcpyHostToDevice, st));
+        PB_CUDA(cudaMemcpyAsync(O->uc2ue_w2.p, u2.data(), L * m2 * sizeof(float), cudaMemcpyHostToDevice, st));
+        PB_CUDA(cudaMemcpyAsync(O->dc2de_w1.p, d1.data(), L * m2 * sizeof(float), cudaMemcpyHostToDevice, st));
+        PB_CUDA(cudaMemcpyAsync(O->dc2de_w2.p, d2.data(), L * m2 * sizeof(float), cudaMemcpyHostToDevice, st));
+        PB_CUDA(cudaStreamSynchronize(st));    // the host vectors go out of scope
+    }
     pack_m2l_tc(*O, st);
     PB_CUDA(cudaStreamSynchronize(st));
     T->ops[key] = O;
