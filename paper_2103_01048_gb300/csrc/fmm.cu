@@ -77,27 +77,34 @@ __device__ __forceinline__ void interact(T dx, T dy, T dz, T q, T mx, T my, T mz
 //   potL += g qL + (d.m) f,               dnL -= (d.n) f qL,
 //   potY += e (g qY + (d.m) f (1 + kr)),  dnY -= e (1 + kr) (d.n) f qY,
 //   g = 1/r, f = 1/r^3, e = exp(-kappa r) (Sec. "Fast multipole method").
+// kl2 = -kappa log2(e), so that e = 2^(kl2 r).  Grouped as
+//   potL += (qL + (d.m) / r^2) / r,   potY += (e / r) (qY + (d.m)(1 + kr) / r^2).
 template <typename T, bool DL, bool DN, bool GUARD>
 __device__ __forceinline__ void interact_pair(T dx, T dy, T dz, T qL, T qY, T mx, T my, T mz, T nx, T ny, T nz,
-                                              T kappa, T& potL, T& potY, T& dnL, T& dnY) {
+                                              T kappa, T kl2, T& potL, T& potY, T& dnL, T& dnY) {
     T r2 = dx * dx + dy * dy + dz * dz;
     T rinv = GUARD ? (r2 > T(0) ? rsqrt_t<T>(r2) : T(0)) : rsqrt_t<T>(r2);
-    T f = rinv * rinv * rinv;
     T r = r2 * rinv;
-    T e = exp_t<T>(-kappa * r);
-    T fy = f * (T(1) + kappa * r);
-    potL += rinv * qL;
-    T sy = rinv * qY;
-    if (DL) {
-        T dm = dx * mx + dy * my + dz * mz;
-        potL += dm * f;
-        sy += dm * fy;
-    }
-    potY += e * sy;
-    if (DN) {
-        T dn = dx * nx + dy * ny + dz * nz;
-        dnL -= dn * f * qL;
-        dnY -= e * fy * dn * qY;
+    T er = exp2_t<T>(kl2 * r) * rinv;              // e^{-kr} / r
+    if (DL || DN) {
+        T rinv2 = rinv * rinv;
+        T u = kappa * r + T(1);
+        if (DL) {
+            T w = (dx * mx + dy * my + dz * mz) * rinv2;
+            potL += rinv * (w + qL);
+            potY += er * (w * u + qY);
+        } else {
+            potL += rinv * qL;
+            potY += er * qY;
+        }
+        if (DN) {
+            T dn = (dx * nx + dy * ny + dz * nz) * rinv2;
+            dnL -= rinv * dn * qL;
+            dnY -= er * u * dn * qY;
+        }
+    } else {
+        potL += rinv * qL;
+        potY += er * qY;
     }
 }
 
@@ -249,6 +256,7 @@ __global__ void __launch_bounds__(256) k_p2check_pair(int nbox, const int* __res
     }
     int nlist = (mode == 0) ? 1 : X_n[b];
     T d0 = T(0), d1 = T(0);
+    const T kl2 = -kappa * T(kLog2E);
     for (int li = 0; li < nlist; ++li) {
         int a = (mode == 0) ? b : X[(long long)b * kXCap + li];
         int j0 = sb[a], j1 = se[a];
@@ -262,12 +270,13 @@ __global__ void __launch_bounds__(256) k_p2check_pair(int nbox, const int* __res
             }
             __syncthreads();
             int cnt = min(CH, j1 - jc);
+#pragma unroll 4
             for (int t = 0; t < cnt; ++t) {
                 V s = s_q[t], mm = s_m[t];
 #pragma unroll
                 for (int m = 0; m < MAXP; ++m)
                     interact_pair<T, DL, false, false>(px[m] - s.x, py[m] - s.y, pz[m] - s.z, s.w, mm.w, mm.x, mm.y,
-                                                       mm.z, 0, 0, 0, kappa, aL[m], aY[m], d0, d1);
+                                                       mm.z, 0, 0, 0, kappa, kl2, aL[m], aY[m], d0, d1);
             }
         }
     }
@@ -618,6 +627,7 @@ __global__ void __launch_bounds__(128) k_leaf_pair(const int* __restrict__ leave
     const int tloc = threadIdx.x % slots, g = threadIdx.x / slots;
     const int nw = W_off[b + 1] - W_off[b];
     const int nsrcbox = nw + (level[b] >= 2 ? 1 : 0);
+    const T kl2 = -kappa * T(kLog2E);
     for (int tc = t0; tc < t1; tc += NT * slots) {
         int ti[NT];
         bool vt[NT];
@@ -645,23 +655,28 @@ __global__ void __launch_bounds__(128) k_leaf_pair(const int* __restrict__ leave
                 }
                 __syncthreads();
                 const int cnt = min(CH, j1 - jc);
+                // group g takes a contiguous share of the chunk
+                const int per = (cnt + G - 1) / G;
+                const int k0 = g * per, k1 = min(cnt, k0 + per);
                 if (a == b) {
-                    for (int k = g; k < cnt; k += G) {
+#pragma unroll 2
+                    for (int k = k0; k < k1; ++k) {
                         V s = s_q[k], mm = s_m[k];
 #pragma unroll
                         for (int u = 0; u < NT; ++u)
                             interact_pair<T, DL, DN, true>((T)xt[u].x - s.x, (T)xt[u].y - s.y, (T)xt[u].z - s.z, s.w,
-                                                           mm.w, mm.x, mm.y, mm.z, nx[u], ny[u], nz[u], kappa, pL[u],
-                                                           pY[u], dL[u], dY[u]);
+                                                           mm.w, mm.x, mm.y, mm.z, nx[u], ny[u], nz[u], kappa, kl2,
+                                                           pL[u], pY[u], dL[u], dY[u]);
                     }
                 } else {
-                    for (int k = g; k < cnt; k += G) {
+#pragma unroll 4
+                    for (int k = k0; k < k1; ++k) {
                         V s = s_q[k], mm = s_m[k];
 #pragma unroll
                         for (int u = 0; u < NT; ++u)
                             interact_pair<T, DL, DN, false>((T)xt[u].x - s.x, (T)xt[u].y - s.y, (T)xt[u].z - s.z,
                                                             s.w, mm.w, mm.x, mm.y, mm.z, nx[u], ny[u], nz[u], kappa,
-                                                            pL[u], pY[u], dL[u], dY[u]);
+                                                            kl2, pL[u], pY[u], dL[u], dY[u]);
                     }
                 }
             }
@@ -690,13 +705,17 @@ __global__ void __launch_bounds__(128) k_leaf_pair(const int* __restrict__ leave
                 }
                 __syncthreads();
                 const int cnt = min(CH, ne - jc);
-                for (int k = g; k < cnt; k += G) {
+                const int per = (cnt + G - 1) / G;
+                const int k0 = g * per, k1 = min(cnt, k0 + per);
+#pragma unroll 4
+                for (int k = k0; k < k1; ++k) {
                     V s = s_q[k];
                     T qy = s_m[k].w;
 #pragma unroll
                     for (int u = 0; u < NT; ++u)
                         interact_pair<T, false, DN, false>(rx[u] - s.x, ry[u] - s.y, rz[u] - s.z, s.w, qy, 0, 0, 0,
-                                                           nx[u], ny[u], nz[u], kappa, pL[u], pY[u], dL[u], dY[u]);
+                                                           nx[u], ny[u], nz[u], kappa, kl2, pL[u], pY[u], dL[u],
+                                                           dY[u]);
                 }
             }
         }
