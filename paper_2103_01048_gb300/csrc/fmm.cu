@@ -17,6 +17,8 @@ namespace pbfmm {
 bool m2l_tc_launch(const fmm_tree* T, const Operators& O, const float* Qu, float* Qd, int* err, cudaStream_t st);
 bool pc_tc_launch(const fmm_tree* T, const Operators& O, int child_level, bool up, float* Q, int* err,
                   cudaStream_t st);
+bool c2e_tc_launch(const fmm_tree* T, const Operators& O, bool up, const float* X, float* Y, float* tmp, int* err,
+                   cudaStream_t st);
 
 constexpr double kInv4PiD = 0.07957747154594767;
 constexpr double kLog2E = 1.4426950408889634;     // log2(e)
@@ -862,6 +864,9 @@ static GemmArgs tree_gemm_args(const fmm_tree* Tr) {
 // UC2UE at every leaf with sources (upward check potentials in W.chk)
 template <typename T>
 static void far_uc2ue(fmm_tree* Tr, const Operators& O, Work<T>& W) {
+    if constexpr (std::is_same<T, float>::value) {
+        if (c2e_tc_launch(Tr, O, true, W.chk.p, W.Qu.p, W.tmp.p, Tr->ctx->dev_err, Tr->ctx->stream)) return;
+    }
     GemmArgs ga = tree_gemm_args<T>(Tr);
     for (int l = 0; l < Tr->nlev; ++l) {
         int a0 = Tr->sleaf_lvl_off[l], a1 = Tr->sleaf_lvl_off[l + 1];
@@ -892,6 +897,9 @@ static void far_m2m(fmm_tree* Tr, const Operators& O, Work<T>& W) {
 // writes Qd of those boxes before the M2L accumulates
 template <typename T>
 static void far_dc2de_x(fmm_tree* Tr, const Operators& O, Work<T>& W) {
+    if constexpr (std::is_same<T, float>::value) {
+        if (c2e_tc_launch(Tr, O, false, W.chk.p, W.Qd.p, W.tmp.p, Tr->ctx->dev_err, Tr->ctx->stream)) return;
+    }
     GemmArgs ga = tree_gemm_args<T>(Tr);
     for (int l = 0; l < Tr->nlev; ++l) {
         int a0 = Tr->xbox_lvl_off[l], a1 = Tr->xbox_lvl_off[l + 1];

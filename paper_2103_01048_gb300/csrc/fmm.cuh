@@ -33,6 +33,7 @@ struct Operators {
     // [level][343][half][hi|lo][K/32][npad/2 rows][128 B]
     DBuf<float> m2l_tc;
     DBuf<float> m2m_tc, l2l_tc;   // same packing, [level][8 octants]
+    DBuf<float> uc2ue_w1_tc, uc2ue_w2_tc, dc2de_w1_tc, dc2de_w2_tc;   // same packing, [level]
     bool have_tc = false;
     // FP64 copies (all-FP64 path)
     DBuf<double> uc2ue_d, dc2de_d, m2m_d, l2l_d, m2l_d;

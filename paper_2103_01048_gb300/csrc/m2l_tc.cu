@@ -176,6 +176,12 @@ void pack_m2l_tc(Operators& O, cudaStream_t st) {
     pack_tc(O.npad, (long long)O.nlev * kNumOffsets, O.m2l.p, O.m2l_tc, st);
     if (O.m2m.p) pack_tc(O.npad, (long long)O.nlev * 8, O.m2m.p, O.m2m_tc, st);
     if (O.l2l.p) pack_tc(O.npad, (long long)O.nlev * 8, O.l2l.p, O.l2l_tc, st);
+    if (O.uc2ue_w1.p) {
+        pack_tc(O.npad, O.nlev, O.uc2ue_w1.p, O.uc2ue_w1_tc, st);
+        pack_tc(O.npad, O.nlev, O.uc2ue_w2.p, O.uc2ue_w2_tc, st);
+        pack_tc(O.npad, O.nlev, O.dc2de_w1.p, O.dc2de_w1_tc, st);
+        pack_tc(O.npad, O.nlev, O.dc2de_w2.p, O.dc2de_w2_tc, st);
+    }
     O.have_tc = true;
 }
 
@@ -256,6 +262,28 @@ void build_m2l_pairs(fmm_tree* T) {
     P.items.alloc(items.size(), st);
     PB_CUDA(cudaMemcpyAsync(P.items.p, items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice, st));
     PB_CUDA(cudaStreamSynchronize(st));
+}
+
+// Items of the check -> equivalent solves on the tensor cores: the boxes of
+// each level (one row each) in chunks of at most kTcItemPairs.
+static void level_items(const std::vector<int>& lvl_off, int nlev, DBuf<int4>& items, int& n, cudaStream_t st) {
+    std::vector<int4> h;
+    for (int l = 0; l < nlev; ++l)
+        for (int a = lvl_off[l]; a < lvl_off[l + 1]; a += kTcItemPairs)
+            h.push_back(make_int4(a, std::min(kTcItemPairs, lvl_off[l + 1] - a), l, 0));
+    n = (int)h.size();
+    if (h.empty()) return;
+    items.alloc(h.size(), st);
+    PB_CUDA(cudaMemcpyAsync(items.p, h.data(), h.size() * sizeof(int4), cudaMemcpyHostToDevice, st));
+    PB_CUDA(cudaStreamSynchronize(st));
+}
+
+void build_c2e_items(fmm_tree* T) {
+    cudaStream_t st = T->ctx->stream;
+    if ((int)T->sleaf_lvl_off.size() == T->nlev + 1)
+        level_items(T->sleaf_lvl_off, T->nlev, T->c2e_items_up, T->n_c2e_up, st);
+    if ((int)T->xbox_lvl_off.size() == T->nlev + 1)
+        level_items(T->xbox_lvl_off, T->nlev, T->c2e_items_dn, T->n_c2e_dn, st);
 }
 
 // Parent-child pairs for M2M / L2L on the tensor cores: children of level
@@ -594,6 +622,34 @@ bool pc_tc_launch(const fmm_tree* T, const Operators& O, int child_level, bool u
         case 64: launch_tc_items<64>(items, i1 - i0, tgt, src, ops, Q, Q, err, st); return true;
         case 128: launch_tc_items<128>(items, i1 - i0, tgt, src, ops, Q, Q, err, st); return true;
         case 160: launch_tc_items<160>(items, i1 - i0, tgt, src, ops, Q, Q, err, st); return true;
+        default: return false;
+    }
+}
+
+// Check -> equivalent solve Y = W2 (W1 X) at the upward (sleaf) or downward
+// (X-list) boxes on the tensor cores: two passes through `tmp`, which is
+// zeroed first (every row of a pass receives exactly one product, so the
+// result does not depend on the order of the reductions). Y rows of those
+// boxes must be zero on entry. False when the tensor-core path does not apply.
+bool c2e_tc_launch(const fmm_tree* T, const Operators& O, bool up, const float* X, float* Y, float* tmp, int* err,
+                   cudaStream_t st) {
+    if (!O.have_tc || !O.uc2ue_w1_tc.p) return false;
+    const int nitems = up ? T->n_c2e_up : T->n_c2e_dn;
+    if (nitems == 0) return true;
+    const int4* items = up ? T->c2e_items_up.p : T->c2e_items_dn.p;
+    const int* ids = up ? T->sleaf_ids.p : T->xbox_ids.p;
+    const float* w1 = up ? O.uc2ue_w1_tc.p : O.dc2de_w1_tc.p;
+    const float* w2 = up ? O.uc2ue_w2_tc.p : O.dc2de_w2_tc.p;
+    PB_CUDA(cudaMemsetAsync(tmp, 0, (size_t)T->nbox * O.npad * sizeof(float), st));
+    switch (O.npad) {
+        case 32: launch_tc_items<32>(items, nitems, ids, ids, w1, X, tmp, err, st);
+                 launch_tc_items<32>(items, nitems, ids, ids, w2, tmp, Y, err, st); return true;
+        case 64: launch_tc_items<64>(items, nitems, ids, ids, w1, X, tmp, err, st);
+                 launch_tc_items<64>(items, nitems, ids, ids, w2, tmp, Y, err, st); return true;
+        case 128: launch_tc_items<128>(items, nitems, ids, ids, w1, X, tmp, err, st);
+                  launch_tc_items<128>(items, nitems, ids, ids, w2, tmp, Y, err, st); return true;
+        case 160: launch_tc_items<160>(items, nitems, ids, ids, w1, X, tmp, err, st);
+                  launch_tc_items<160>(items, nitems, ids, ids, w2, tmp, Y, err, st); return true;
         default: return false;
     }
 }

@@ -406,6 +406,7 @@ static T read1(const T* d, cudaStream_t st) {
 
 void build_m2l_pairs(fmm_tree* T);
 void build_pc_pairs(fmm_tree* T);
+void build_c2e_items(fmm_tree* T);
 
 void build_tree(fmm_tree* T, const float* src, const float* tgt) {
     cudaStream_t st = T->ctx->stream;
@@ -663,6 +664,7 @@ void build_tree(fmm_tree* T, const float* src, const float* tgt) {
     // 9. V-list pairs grouped by (level, offset) for the tensor-core M2L
     build_m2l_pairs(T);
     build_pc_pairs(T);
+    build_c2e_items(T);
     PB_CUDA(cudaStreamSynchronize(st));
 }
 

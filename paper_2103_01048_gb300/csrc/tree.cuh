@@ -84,6 +84,10 @@ struct fmm_tree {
     pbfmm::M2LSchedule m2l;
     pbfmm::M2LPairs m2l_pairs;
     pbfmm::PCPairs pc_pairs;
+    // tensor-core items of the check -> equivalent solves: (first, count,
+    // level) over sleaf_ids (upward) and xbox_ids (downward), one box per row
+    pbfmm::DBuf<int4> c2e_items_up, c2e_items_dn;
+    int n_c2e_up = 0, n_c2e_dn = 0;
 
     std::map<std::tuple<int, double, int, int>, std::shared_ptr<pbfmm::Operators>> ops;
 };
