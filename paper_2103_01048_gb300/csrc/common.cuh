@@ -9,6 +9,7 @@
 #include <stdexcept>
 
 #include "../../include/pbfmm.h"
+#include <nvtx3/nvToolsExt.h>
 
 namespace pbfmm {
 
@@ -120,11 +121,17 @@ struct pb_ctx {
 
 namespace pbfmm {
 // Scoped phase timer: records an event pair around a phase when profiling.
+// A phase of the library's work: an NVTX range named after the phase (for
+// profilers and tracers; without a tool attached the calls do nothing) and,
+// with pb_profile on, a pair of CUDA events on the context stream.
+constexpr const char* kPhaseNames[PB_PH_COUNT] = {"gather", "p2m", "m2m", "p2l", "m2l",
+                                                  "down", "leaf", "scatter", "bem", "gmres"};
 struct PhaseTimer {
     pb_ctx* ctx;
     int phase;
     cudaEvent_t a = nullptr, b = nullptr;
     PhaseTimer(pb_ctx* c, int ph) : ctx(c), phase(ph) {
+        nvtxRangePushA(kPhaseNames[ph]);
         if (ctx->profile) {
             cudaEventCreate(&a);
             cudaEventCreate(&b);
@@ -136,6 +143,7 @@ struct PhaseTimer {
             cudaEventRecord(b, ctx->stream);
             ctx->pending.push_back({phase, {a, b}});
         }
+        nvtxRangePop();
     }
 };
 void profile_collect(pb_ctx* ctx);
