@@ -140,6 +140,9 @@ void solve_batch(pb_ctx* ctx, pb_mesh* const* meshes, int nsys, pb_result** resu
         S.sub.sm_count = ctx->sm_count;
         S.sub.dev_err = ctx->dev_err;
         S.sub.profile = false;
+        S.sub.coupling = ctx->coupling;
+        S.sub.deterministic = ctx->deterministic;
+        S.sub.singular = ctx->singular;
         PB_CUDA(cudaStreamCreateWithFlags(&S.sub.stream, cudaStreamNonBlocking));
         S.saved_mesh_ctx = S.M->ctx;
         S.saved_tree_ctx = S.M->tree->ctx;

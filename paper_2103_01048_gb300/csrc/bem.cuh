@@ -26,6 +26,17 @@ struct pb_mesh {
     int sing_mode = 0;                // 1: FP64 rule, 2: FP32 rule
     pbfmm::DBuf<int> adj_tr;          // for CSR entry (i, j): the index of entry (j, i)
     fmm_tree* tree = nullptr;
+    // preconditioned mat-vec of pb_solve captured as a CUDA graph (fixed
+    // input/output vectors), valid for the parameters in mv_key
+    cudaGraph_t mv_graph = nullptr;
+    cudaGraphExec_t mv_exec = nullptr;
+    pbfmm::DBuf<double> mv_in, mv_out;
+    double mv_key[8] = {};
+    bool mv_warm = false;             // one uncaptured mat-vec ran with mv_key (caches filled)
+    ~pb_mesh() {
+        if (mv_exec) cudaGraphExecDestroy(mv_exec);
+        if (mv_graph) cudaGraphDestroy(mv_graph);
+    }
 };
 
 namespace pbfmm {

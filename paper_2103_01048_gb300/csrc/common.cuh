@@ -120,7 +120,6 @@ struct pb_ctx {
 };
 
 namespace pbfmm {
-// Scoped phase timer: records an event pair around a phase when profiling.
 // A phase of the library's work: an NVTX range named after the phase (for
 // profilers and tracers; without a tool attached the calls do nothing) and,
 // with pb_profile on, a pair of CUDA events on the context stream.

@@ -128,6 +128,35 @@ def test_solve_energy_vs_oracle(pb, ctx, sphere3, precision):
     assert np.allclose(phir, pr_ref, rtol=2e-4, atol=1e-8)
 
 
+@pytest.mark.parametrize("precision", ["mixed", "fp64"])
+def test_repeated_solve_graph_replay(pb, ctx, sphere3, precision):
+    """The second solve with the same parameters replays the mat-vec as a
+    captured CUDA graph: same iterations and energy as the first (launched)
+    solve, and a changed kappa falls back to launching and recaptures."""
+    V, F, mats = sphere3
+    atoms = np.array([[0.3, -0.2, 0.5], [-0.6, 0.1, -0.2]])
+    q = np.array([0.7, -0.4])
+    prec = pb.PB_MIXED if precision == "mixed" else pb.PB_FP64
+    m = pb.pb_mesh_setup(ctx, V, F.astype(np.int32), 3, 6 if precision == "mixed" else 8, 64)
+    try:
+        out = []
+        for kappa in (KAPPA, KAPPA, KAPPA, 0.3, 0.3):
+            res, st = pb.pb_solve(ctx, m, atoms, q, EPS_IN, EPS_OUT, kappa, 1e-7, 300, precision=prec)
+            assert st == pb.PB_OK
+            it, rr, _ = pb.pb_result_get(res)
+            out.append((it, pb.pb_solvation_energy(ctx, res)))
+            pb.pb_result_destroy(res)
+    finally:
+        pb.pb_mesh_destroy(m)
+    tol = 1e-6 if precision == "mixed" else 1e-12      # FP32 M2L reductions are order-dependent
+    for a, b in ((0, 1), (0, 2), (3, 4)):
+        assert abs(out[a][0] - out[b][0]) <= 1
+        assert abs(out[a][1] - out[b][1]) <= tol * abs(out[a][1])
+    E_ref, *_ = bem.solve_energy(V, F, 3, atoms, q, EPS_IN, EPS_OUT, KAPPA, mats=mats)
+    assert abs(out[2][1] - E_ref) / abs(E_ref) < 1e-4
+    assert abs(out[4][1] - out[0][1]) > 1e-3 * abs(out[0][1])   # kappa changed the answer
+
+
 def test_born_ion_full(pb, ctx):
     """Born ion, radius 2 A, 5,120-triangle icosphere, 3-point rule, P0,
     GMRES tol 1e-6 (the Born-ion configuration), mixed and FP64 paths."""
