@@ -36,6 +36,10 @@ SM_COUNT = 152
 FP32_LANES = 128
 SM_MAX_MHZ = 2070.0
 MUFU_PER_SM_CLK = 16
+# dram__bytes_read.sum + dram__bytes_write.sum of one k_leaf_pair launch on
+# this workload (4M points, p = 6, ncrit = 128), from one ncu capture of the
+# current kernel (535.8 + 28.2 MB); None once the kernel changes
+LEAF_TRAFFIC_BYTES = 564.0e6
 # Arithmetic of one source-target pair in the paired (Laplace + Yukawa)
 # evaluation, FMA = 2 FLOPs, MUFU counted apart: SL+DL of both kernels
 # 30 FLOPs + 2 MUFU (rsqrt, ex2); monopole-only pairs of equivalent
@@ -352,7 +356,10 @@ def main():
     achieved = leaf_flops / (leaf_ms * 1e-3) / 1e12
     peak = leaf_flops / t_roof / 1e12
     roof = {"kernel": "k_leaf_pair (P2P+M2P+L2P, Laplace+Yukawa)", "bound": "alu", "achieved": achieved,
-            "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+            "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "traffic": LEAF_TRAFFIC_BYTES if (args.n == N_POINTS and args.p == P_ORDER and args.ncrit == NCRIT) else None,
+            "traffic_note": "DRAM bytes per launch (ncu dram__bytes_read.sum + dram__bytes_write.sum); "
+                            "the launch streams each target leaf's U-list sources (~0.56 GB, L2-filtered)",
             "peak_note": "derived ALU roof of this launch's instruction mix: max(FLOPs / FP32 FMA peak "
                          "(152 SMs x 128 lanes x 2 x 2070 MHz = 80.5 TFLOP/s), MUFU ops / MUFU peak "
                          "(152 x 16 x 2070 MHz)); not measured",
