@@ -256,30 +256,43 @@ __global__ void __launch_bounds__(256) k_p2check_pair(int nbox, const int* __res
         px[m] = alpha * (T)s.x; py[m] = alpha * (T)s.y; pz[m] = alpha * (T)s.z;
         aL[m] = aY[m] = T(0);
     }
-    int nlist = (mode == 0) ? 1 : X_n[b];
+    // sources: B's own (P2M) or those of the X-list boxes (P2L), the boxes
+    // concatenated into full chunks by a uniform cursor over their ranges
+    __shared__ int s_xb[kXCap], s_xn[kXCap];
+    const int nlist = (mode == 0) ? 1 : X_n[b];
+    if (threadIdx.x < nlist) {
+        const int a = (mode == 0) ? b : X[(long long)b * kXCap + threadIdx.x];
+        s_xb[threadIdx.x] = sb[a];
+        s_xn[threadIdx.x] = se[a] - sb[a];
+    }
     T d0 = T(0), d1 = T(0);
     const T kl2 = -kappa * T(kLog2E);
-    for (int li = 0; li < nlist; ++li) {
-        int a = (mode == 0) ? b : X[(long long)b * kXCap + li];
-        int j0 = sb[a], j1 = se[a];
-        for (int jc = j0; jc < j1; jc += CH) {
-            int j = jc + threadIdx.x;
-            __syncthreads();
-            if (j < j1) {
+    int ui = 0, off = 0;
+    while (ui < nlist) {
+        __syncthreads();
+        int filled = 0;
+        while (filled < CH && ui < nlist) {
+            const int n = s_xn[ui];
+            const int m = min(CH - filled, n - off);
+            const int t = threadIdx.x - filled;
+            if (t >= 0 && t < m) {
+                const int j = s_xb[ui] + off + t;
                 V v = sq[j];
                 s_q[threadIdx.x] = {(T)((double)v.x - c.x), (T)((double)v.y - c.y), (T)((double)v.z - c.z), v.w};
                 s_m[threadIdx.x] = sm[j];
             }
-            __syncthreads();
-            int cnt = min(CH, j1 - jc);
+            filled += m;
+            off += m;
+            if (off >= n) { ++ui; off = 0; }
+        }
+        __syncthreads();
 #pragma unroll 4
-            for (int t = 0; t < cnt; ++t) {
-                V s = s_q[t], mm = s_m[t];
+        for (int t = 0; t < filled; ++t) {
+            V s = s_q[t], mm = s_m[t];
 #pragma unroll
-                for (int m = 0; m < MAXP; ++m)
-                    interact_pair<T, DL, false, false>(px[m] - s.x, py[m] - s.y, pz[m] - s.z, s.w, mm.w, mm.x, mm.y,
-                                                       mm.z, 0, 0, 0, kappa, kl2, aL[m], aY[m], d0, d1);
-            }
+            for (int m = 0; m < MAXP; ++m)
+                interact_pair<T, DL, false, false>(px[m] - s.x, py[m] - s.y, pz[m] - s.z, s.w, mm.w, mm.x, mm.y,
+                                                   mm.z, 0, 0, 0, kappa, kl2, aL[m], aY[m], d0, d1);
         }
     }
 #pragma unroll
