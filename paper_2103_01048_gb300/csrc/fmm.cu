@@ -311,7 +311,7 @@ __global__ void __launch_bounds__(256) k_p2check_pair(int nbox, const int* __res
 // 256 threads as 16 row groups x 16 column pairs, K chunks of 16 in smem.
 // ---------------------------------------------------------------------------
 
-enum GemmMode { G_DENSE = 0, G_M2M = 1, G_L2L = 2, G_M2L = 3 };
+enum GemmMode { G_DENSE = 0, G_M2M = 1, G_L2L = 2, G_M2L = 3, G_PAIRS = 4 };
 
 struct GemmArgs {
     int mode;
@@ -330,6 +330,11 @@ struct GemmArgs {
     const int* entry_src;
     int level;                 // operator level (modes 0-2)
     int accumulate;            // mode 0: Y += (else Y =)
+    // G_PAIRS: items (first pair, count <= 32, operator index) over (tgt, src)
+    // pairs that share one operator; results added into Y with reductions
+    const int4* pitems;
+    const int* ptgt;
+    const int* psrc;
 };
 
 // T: type of the box vectors; TO: type of the operator and the accumulation
@@ -351,6 +356,9 @@ __device__ __forceinline__ void box_gemm_body(const GemmArgs& a, const TO* __res
     if (a.mode == G_M2L) {
         nterm = a.entry_off[tile + 1] - a.entry_off[tile];
         level = a.tile_level[tile];
+    } else if (a.mode == G_PAIRS) {
+        nterm = 1;
+        level = a.pitems[tile].z;          // operator index
     } else {
         nterm = (a.mode == G_DENSE) ? 1 : 8;
         level = a.level;
@@ -367,6 +375,12 @@ __device__ __forceinline__ void box_gemm_body(const GemmArgs& a, const TO* __res
                 int e = a.entry_off[tile] + term;
                 src = a.entry_src[(long long)e * kTC + tid];
                 dst = a.tile_box[(long long)tile * kTC + tid];
+            } else if (a.mode == G_PAIRS) {
+                const int4 it = a.pitems[tile];
+                if (tid < it.y) {
+                    src = a.psrc[it.x + tid];
+                    dst = a.ptgt[it.x + tid];
+                }
             } else {
                 int ci = tile * kTC + tid;
                 int b = ci < a.ncols ? (a.cols ? a.cols[ci] : a.col_base + ci) : -1;
@@ -395,6 +409,7 @@ __device__ __forceinline__ void box_gemm_body(const GemmArgs& a, const TO* __res
         if (!any) continue;
         const TO* op;
         if (a.mode == G_M2L) op = ops + ((size_t)level * kNumOffsets + a.entry_oidx[a.entry_off[tile] + term]) * m2;
+        else if (a.mode == G_PAIRS) op = ops + (size_t)level * m2;
         else if (a.mode == G_DENSE) op = ops + (size_t)level * m2;
         else op = ops + ((size_t)level * 8 + term) * m2;
         for (int k0 = 0; k0 < NPAD; k0 += KC) {
@@ -434,6 +449,16 @@ __device__ __forceinline__ void box_gemm_body(const GemmArgs& a, const TO* __res
         }
     }
     if (a.mode == G_L2L) return;
+    if (a.mode == G_PAIRS) {
+#pragma unroll
+        for (int cc = 0; cc < 2; ++cc) {
+            int d = s_dst[2 * tx + cc];
+            if (d < 0) continue;
+#pragma unroll
+            for (int r = 0; r < RPT; ++r) atomicAdd(&Yv[(size_t)d * NPAD + ty + 16 * r], (T)acc[r][cc]);
+        }
+        return;
+    }
 #pragma unroll
     for (int cc = 0; cc < 2; ++cc) {
         int d = s_dst[2 * tx + cc];
@@ -783,7 +808,8 @@ template <typename T, typename TO, int NPAD>
 static void gemm_launch(cudaStream_t st, int nblocks, const GemmArgs& a, const TO* ops, const T* X, T* Y) {
     if (nblocks <= 0) return;
     switch (a.mode) {
-        case G_M2L: k_m2l_simt<T, TO, NPAD><<<nblocks, 256, 0, st>>>(a, ops, X, Y); break;
+        case G_M2L:
+        case G_PAIRS: k_m2l_simt<T, TO, NPAD><<<nblocks, 256, 0, st>>>(a, ops, X, Y); break;
         case G_M2M: k_m2m<T, TO, NPAD><<<nblocks, 256, 0, st>>>(a, ops, X, Y); break;
         case G_L2L: k_l2l<T, TO, NPAD><<<nblocks, 256, 0, st>>>(a, ops, X, Y); break;
         default: k_check2equiv<T, TO, NPAD><<<nblocks, 256, 0, st>>>(a, ops, X, Y); break;
@@ -929,6 +955,18 @@ static void far_m2l(fmm_tree* Tr, const Operators& O, Work<T>& W) {
     if constexpr (std::is_same<T, float>::value) {
         if (Tr->m2l_pairs.nitems > 0 && !ctx->deterministic)
             tc_done = m2l_tc_launch(Tr, O, W.Qu.p, W.Qd.p, ctx->dev_err, ctx->stream);
+    }
+    if (!tc_done && !ctx->deterministic && Tr->m2l_pairs.nitems32 > 0) {
+        // one CTA per at most 32 V-list pairs of one (level, offset) group:
+        // parallel over pairs, so small trees fill the GPU too
+        GemmArgs ga = tree_gemm_args<T>(Tr);
+        ga.mode = G_PAIRS;
+        ga.pitems = Tr->m2l_pairs.items32.p;
+        ga.ptgt = Tr->m2l_pairs.tgt.p;
+        ga.psrc = Tr->m2l_pairs.src.p;
+        gemm_dispatch<T, T>(O.npad, ctx->stream, Tr->m2l_pairs.nitems32, ga, opsel<T>(O, O.m2l, O.m2l_d), W.Qu.p,
+                            W.Qd.p);
+        tc_done = true;
     }
     if (!tc_done && Tr->m2l.ntile > 0) {
         GemmArgs ga = tree_gemm_args<T>(Tr);

@@ -261,6 +261,12 @@ void build_m2l_pairs(fmm_tree* T) {
     P.nitems = (int)items.size();
     P.items.alloc(items.size(), st);
     PB_CUDA(cudaMemcpyAsync(P.items.p, items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice, st));
+    std::vector<int4> items32;
+    for (const int4& it : items)
+        for (int a = 0; a < it.y; a += 32) items32.push_back(make_int4(it.x + a, std::min(32, it.y - a), it.z, 0));
+    P.nitems32 = (int)items32.size();
+    P.items32.alloc(items32.size(), st);
+    PB_CUDA(cudaMemcpyAsync(P.items32.p, items32.data(), items32.size() * sizeof(int4), cudaMemcpyHostToDevice, st));
     PB_CUDA(cudaStreamSynchronize(st));
 }
 

@@ -33,6 +33,8 @@ struct M2LPairs {
     DBuf<int4> items;
     int nitems = 0;
     long long npairs = 0;
+    DBuf<int4> items32;        // the same groups in chunks of at most 32 pairs (CUDA-core M2L)
+    int nitems32 = 0;
 };
 
 // Parent-child pairs (children of level >= 3) grouped by (level, octant) for

@@ -66,6 +66,41 @@ def random_subsample(n: int, k: int, seed: int = 2):
     return np.sort(rng.choice(n, size=k, replace=False)).astype(np.int64)
 
 
+def octasphere(level: int, radius: float = 1.0):
+    """Octahedron subdivided `level` times (each triangle into four at its
+    edge midpoints), vertices projected to the sphere: nt = 8 * 4**level
+    (512, 2,048, 8,192, 32,768, 131,072 for levels 3-7, the element counts of
+    the off-centre-charge sphere refinement study).  Returns (verts float64
+    [nv,3], tris int32 [nt,3]), counter-clockwise seen from outside."""
+    v = [(1, 0, 0), (-1, 0, 0), (0, 1, 0), (0, -1, 0), (0, 0, 1), (0, 0, -1)]
+    f = [(0, 2, 4), (2, 1, 4), (1, 3, 4), (3, 0, 4), (2, 0, 5), (1, 2, 5), (3, 1, 5), (0, 3, 5)]
+    verts = [np.array(q, dtype=np.float64) for q in v]
+    faces = list(f)
+    for _ in range(level):
+        cache = {}
+
+        def mid(a, b):
+            key = (a, b) if a < b else (b, a)
+            if key not in cache:
+                m = verts[a] + verts[b]
+                verts.append(m / np.linalg.norm(m))
+                cache[key] = len(verts) - 1
+            return cache[key]
+
+        nf = []
+        for (a, b, c) in faces:
+            ab, bc, ca = mid(a, b), mid(b, c), mid(c, a)
+            nf += [(a, ab, ca), (b, bc, ab), (c, ca, bc), (ab, bc, ca)]
+        faces = nf
+    V = np.array(verts) * radius
+    F = np.array(faces, dtype=np.int32)
+    p0, p1, p2 = V[F[:, 0]], V[F[:, 1]], V[F[:, 2]]
+    nrm = np.cross(p1 - p0, p2 - p0)
+    flip = (nrm * (p0 + p1 + p2)).sum(axis=1) < 0
+    F[flip] = F[flip][:, [0, 2, 1]]
+    return np.ascontiguousarray(V), np.ascontiguousarray(F)
+
+
 def icosphere(level: int, radius: float = 1.0):
     """Icosahedron subdivided `level` times, vertices projected to the sphere.
 
