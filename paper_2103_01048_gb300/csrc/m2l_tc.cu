@@ -26,7 +26,8 @@
 namespace pbfmm {
 
 constexpr int kTcRows = 128;           // pairs per row tile (MMA M)
-constexpr int kTcItemPairs = 1024;     // pairs per work item
+constexpr int kTcItemPairs = 2048;     // pairs per M2L work item (one operator load each)
+constexpr int kTcSmallItemPairs = 512; // M2M / L2L / check->equivalent items: fewer pairs per operator, more CTAs
 constexpr int kTcMaxNpad = 160;        // resident operator half must fit in shared memory
 
 // ---------------------------------------------------------------------------
@@ -275,8 +276,8 @@ void build_m2l_pairs(fmm_tree* T) {
 static void level_items(const std::vector<int>& lvl_off, int nlev, DBuf<int4>& items, int& n, cudaStream_t st) {
     std::vector<int4> h;
     for (int l = 0; l < nlev; ++l)
-        for (int a = lvl_off[l]; a < lvl_off[l + 1]; a += kTcItemPairs)
-            h.push_back(make_int4(a, std::min(kTcItemPairs, lvl_off[l + 1] - a), l, 0));
+        for (int a = lvl_off[l]; a < lvl_off[l + 1]; a += kTcSmallItemPairs)
+            h.push_back(make_int4(a, std::min(kTcSmallItemPairs, lvl_off[l + 1] - a), l, 0));
     n = (int)h.size();
     if (h.empty()) return;
     items.alloc(h.size(), st);
@@ -316,8 +317,8 @@ void build_pc_pairs(fmm_tree* T) {
         P.level_item_off[l] = (int)items.size();
         for (int o = 0; o < 8; ++o) {
             auto& v = bucket[(size_t)l * 8 + o];
-            for (size_t a = 0; a < v.size(); a += kTcItemPairs) {
-                int cnt = (int)std::min<size_t>(kTcItemPairs, v.size() - a);
+            for (size_t a = 0; a < v.size(); a += kTcSmallItemPairs) {
+                int cnt = (int)std::min<size_t>(kTcSmallItemPairs, v.size() - a);
                 items.push_back(make_int4((int)hc.size(), cnt, l * 8 + o, 0));
                 for (int k = 0; k < cnt; ++k) { hc.push_back(v[a + k]); hp.push_back(par[v[a + k]]); }
             }
