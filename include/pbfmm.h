@@ -278,7 +278,11 @@ int pb_mesh_matvec(pb_ctx* ctx, pb_mesh* mesh, double eps_in, double eps_out, do
  * kappa the inverse Debye length (1/A).  Full GMRES (no restart, x0 = 0,
  * left block-diagonal preconditioning) in FP64 until the preconditioned
  * relative residual is <= tol or max_iter (1..2000) iterations.  Returns PB_OK, or
- * PB_ENOCONV with *out still holding the last iterate.  Synchronous. */
+ * PB_ENOCONV with *out still holding the last iterate.  Synchronous.
+ * From the second solve on a mesh with unchanged eps, kappa, precision and
+ * options, the mat-vec is replayed from a CUDA graph the mesh keeps (the
+ * first solve launches it directly and fills the caches); pb_profile's
+ * phase timers and launch count then cover only directly launched work. */
 int pb_solve(pb_ctx* ctx, pb_mesh* mesh, const double* atoms, const double* q, int64_t na, double eps_in,
              double eps_out, double kappa, double tol, int max_iter, int precision, pb_result** out);
 int pb_result_destroy(pb_result* res);
