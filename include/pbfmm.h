@@ -119,8 +119,15 @@ int pb_profile(pb_ctx* ctx, int enable);
  *                         0 (default): FP64 with a 5-level graded rule up to
  *                         262,144 triangles, else FP32 with a 4-level rule;
  *                         1: always FP64; 2: always FP32.
+ *   PB_OPT_OVERLAP        0 (default): one stream; 1: the near field (P2P) of
+ *                         fmm_apply_pair runs on a second stream of the
+ *                         context, beside the far-field passes (fork and join
+ *                         by events, also inside captured graphs).  On the
+ *                         4M-point p = 6 workload it does not pay: the
+ *                         tensor-core kernels cannot share an SM with the
+ *                         near-field CTAs (shared memory).
  * Errors: PB_EINVAL for an unknown option or value. */
-enum { PB_OPT_COUPLING = 1, PB_OPT_DETERMINISTIC = 2, PB_OPT_SINGULAR = 3 };
+enum { PB_OPT_COUPLING = 1, PB_OPT_DETERMINISTIC = 2, PB_OPT_SINGULAR = 3, PB_OPT_OVERLAP = 4 };
 int pb_set_option(pb_ctx* ctx, int option, int value);
 int pb_profile_read(pb_ctx* ctx, int phase, double* ms, int64_t* calls);
 

@@ -143,6 +143,7 @@ void solve_batch(pb_ctx* ctx, pb_mesh* const* meshes, int nsys, pb_result** resu
         S.sub.coupling = ctx->coupling;
         S.sub.deterministic = ctx->deterministic;
         S.sub.singular = ctx->singular;
+        S.sub.overlap = 0;              // systems already run side by side on their own streams
         PB_CUDA(cudaStreamCreateWithFlags(&S.sub.stream, cudaStreamNonBlocking));
         S.saved_mesh_ctx = S.M->ctx;
         S.saved_tree_ctx = S.M->tree->ctx;

@@ -1098,8 +1098,9 @@ static void reaction_potential(pb_mesh* M, pb_result* R, double* phir) {
 // caller launches the kernels itself.
 static bool matvec_graph(pb_mesh* M, pb_result* R) {
     pb_ctx* ctx = M->ctx;
-    const double key[8] = {R->eps_in, R->eps_out, R->kappa, (double)R->precision, (double)ctx->deterministic,
-                           (double)ctx->singular, (double)(uintptr_t)M->S_d.p, (double)(uintptr_t)M->S_f.p};
+    const double key[8] = {R->eps_in, R->eps_out, R->kappa, (double)R->precision,
+                           (double)(ctx->deterministic + 2 * ctx->overlap), (double)ctx->singular,
+                           (double)(uintptr_t)M->S_d.p, (double)(uintptr_t)M->S_f.p};
     const bool same = std::equal(key, key + 8, M->mv_key);
     if (same && M->mv_exec) return true;
     if (!same || !M->mv_warm) {
@@ -1123,6 +1124,10 @@ static bool matvec_graph(pb_mesh* M, pb_result* R) {
     sub.coupling = ctx->coupling;
     sub.deterministic = ctx->deterministic;
     sub.singular = ctx->singular;
+    sub.overlap = ctx->overlap;
+    sub.aux = ctx->aux;                 // joins the capture through the fork event
+    sub.ev_fork = ctx->ev_fork;
+    sub.ev_join = ctx->ev_join;
     PB_CUDA(cudaStreamCreateWithFlags(&sub.stream, cudaStreamNonBlocking));
     pb_ctx* saved_tree = M->tree->ctx;
     M->ctx = &sub;

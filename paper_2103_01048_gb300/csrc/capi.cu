@@ -125,6 +125,9 @@ int pb_create(pb_ctx** out, int device, void* cuda_stream) {
     PB_CUDA(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr));
     PB_CUDA(cudaMalloc((void**)&ctx->dev_err, sizeof(int)));
     PB_CUDA(cudaMemset(ctx->dev_err, 0, sizeof(int)));
+    PB_CUDA(cudaStreamCreateWithFlags(&ctx->aux, cudaStreamNonBlocking));
+    PB_CUDA(cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming));
+    PB_CUDA(cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming));
     *out = ctx;
     PB_API_END(ctx)
 }
@@ -132,6 +135,12 @@ int pb_create(pb_ctx** out, int device, void* cuda_stream) {
 int pb_destroy(pb_ctx* ctx) {
     if (!ctx) return PB_EINVAL;
     cudaStreamSynchronize(ctx->stream);
+    if (ctx->aux) {
+        cudaStreamSynchronize(ctx->aux);
+        cudaStreamDestroy(ctx->aux);
+    }
+    if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+    if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
     if (ctx->dev_err) cudaFree(ctx->dev_err);
     delete ctx;
     return PB_OK;
@@ -177,6 +186,7 @@ int pb_set_option(pb_ctx* ctx, int option, int value) {
     if (option == PB_OPT_COUPLING && value >= 0 && value <= 2) { ctx->coupling = value; return PB_OK; }
     if (option == PB_OPT_DETERMINISTIC && (value == 0 || value == 1)) { ctx->deterministic = value; return PB_OK; }
     if (option == PB_OPT_SINGULAR && value >= 0 && value <= 2) { ctx->singular = value; return PB_OK; }
+    if (option == PB_OPT_OVERLAP && (value == 0 || value == 1)) { ctx->overlap = value; return PB_OK; }
     ctx->last_error = "pb_set_option: unknown option or value";
     return PB_EINVAL;
 }

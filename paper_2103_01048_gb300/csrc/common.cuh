@@ -117,6 +117,11 @@ struct pb_ctx {
     int coupling = 0;          // 0 auto, 1 direct sums, 2 FMM
     int deterministic = 0;     // 1: no run-dependent reductions (SIMT M2L/M2M/L2L)
     int singular = 0;          // singular entries: 0 auto, 1 FP64 (depth 5), 2 FP32 (depth 4)
+    int overlap = 0;           // 1: near field of the paired apply on `aux`, beside the far field
+    // second stream (and fork / join events) for the near field of the paired
+    // apply; null: everything on `stream`
+    cudaStream_t aux = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 };
 
 namespace pbfmm {
@@ -128,18 +133,20 @@ constexpr const char* kPhaseNames[PB_PH_COUNT] = {"gather", "p2m", "m2m", "p2l",
 struct PhaseTimer {
     pb_ctx* ctx;
     int phase;
+    cudaStream_t st;
     cudaEvent_t a = nullptr, b = nullptr;
-    PhaseTimer(pb_ctx* c, int ph) : ctx(c), phase(ph) {
+    PhaseTimer(pb_ctx* c, int ph) : PhaseTimer(c, ph, c->stream) {}
+    PhaseTimer(pb_ctx* c, int ph, cudaStream_t s) : ctx(c), phase(ph), st(s) {
         nvtxRangePushA(kPhaseNames[ph]);
         if (ctx->profile) {
             cudaEventCreate(&a);
             cudaEventCreate(&b);
-            cudaEventRecord(a, ctx->stream);
+            cudaEventRecord(a, st);
         }
     }
     ~PhaseTimer() {
         if (a) {
-            cudaEventRecord(b, ctx->stream);
+            cudaEventRecord(b, st);
             ctx->pending.push_back({phase, {a, b}});
         }
         nvtxRangePop();

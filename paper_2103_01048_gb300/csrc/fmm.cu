@@ -635,7 +635,9 @@ __global__ void __launch_bounds__(128) k_leaf_eval(const int* __restrict__ leave
 
 // Leaf evaluation of the paired apply: the same work split as k_leaf_eval,
 // with the Laplace and the Yukawa sums of every pair taken together.
-template <typename T, bool DL, bool DN, int NT>
+// PART 0: everything; 1: the near field (P2P) only, writing the outputs;
+// 2: the far field (M2P, L2P) only, adding to the outputs of a PART 1 launch.
+template <typename T, bool DL, bool DN, int NT, int PART>
 __global__ void __launch_bounds__(128) k_leaf_pair(const int* __restrict__ leaves, int nleaf,
                                                    const int* __restrict__ tb, const int* __restrict__ te,
                                                    const int* __restrict__ sb, const int* __restrict__ se,
@@ -683,7 +685,7 @@ __global__ void __launch_bounds__(128) k_leaf_pair(const int* __restrict__ leave
             pL[u] = pY[u] = dL[u] = dY[u] = T(0);
         }
         // P2P
-        for (int ui = U_off[b]; ui < U_off[b + 1]; ++ui) {
+        for (int ui = U_off[b]; PART != 2 && ui < U_off[b + 1]; ++ui) {
             const int a = U_ids[ui];
             const int j0 = sb[a], j1 = se[a];
             for (int jc = j0; jc < j1; jc += CH) {
@@ -722,7 +724,7 @@ __global__ void __launch_bounds__(128) k_leaf_pair(const int* __restrict__ leave
             }
         }
         // M2P (W list) and L2P (own downward equivalent)
-        for (int wi = 0; wi < nsrcbox; ++wi) {
+        for (int wi = 0; PART != 1 && wi < nsrcbox; ++wi) {
             const int a = (wi < nw) ? W_ids[W_off[b] + wi] : b;
             const T* QL = (wi < nw) ? QuL : QdL;
             const T* QY = (wi < nw) ? QuY : QdY;
@@ -782,11 +784,20 @@ __global__ void __launch_bounds__(128) k_leaf_pair(const int* __restrict__ leave
                     if (DN) { a2 += s_red[NR - 2][o]; a3 += s_red[NR - 1][o]; }
                 }
                 if (vt[u]) {
-                    potL_out[ti[u]] = a0 * T(kInv4PiD);
-                    potY_out[ti[u]] = a1 * T(kInv4PiD);
-                    if (DN) {
-                        dnL_out[ti[u]] = a2 * T(kInv4PiD);
-                        dnY_out[ti[u]] = a3 * T(kInv4PiD);
+                    if (PART == 2) {          // after the near-field launch (each target has one thread)
+                        potL_out[ti[u]] += a0 * T(kInv4PiD);
+                        potY_out[ti[u]] += a1 * T(kInv4PiD);
+                        if (DN) {
+                            dnL_out[ti[u]] += a2 * T(kInv4PiD);
+                            dnY_out[ti[u]] += a3 * T(kInv4PiD);
+                        }
+                    } else {
+                        potL_out[ti[u]] = a0 * T(kInv4PiD);
+                        potY_out[ti[u]] = a1 * T(kInv4PiD);
+                        if (DN) {
+                            dnL_out[ti[u]] = a2 * T(kInv4PiD);
+                            dnY_out[ti[u]] = a3 * T(kInv4PiD);
+                        }
                     }
                 }
             }
@@ -1086,14 +1097,14 @@ static void launch_p2check_pair(cudaStream_t st, int nbox, const int* boxes, int
     PB_CHECK_LAUNCH();
 }
 
-template <typename T, bool DL, bool DN>
+template <typename T, bool DL, bool DN, int PART>
 static void launch_leaf_pair(cudaStream_t st, fmm_tree* Tr, Work<T>& WL, Work<T>& WY, const Operators& O, T kappa) {
     if (Tr->n_tleaf <= 0) return;
     const float4* tpos = Tr->same ? Tr->pos_s.p : Tr->pos_t.p;
     const int* tb = Tr->same ? Tr->sb.p : Tr->tb.p;
     const int* te = Tr->same ? Tr->se.p : Tr->te.p;
     constexpr int NT = 2;
-    k_leaf_pair<T, DL, DN, NT><<<Tr->n_tleaf, 128, 0, st>>>(
+    k_leaf_pair<T, DL, DN, NT, PART><<<Tr->n_tleaf, 128, 0, st>>>(
         Tr->leaf_ids.p, Tr->n_tleaf, tb, te, Tr->sb.p, Tr->se.p, Tr->U_off.p, Tr->U_ids.p, Tr->W_off.p, Tr->W_ids.p,
         Tr->level.p, Tr->center.p, tpos, WL.tn.p, WL.sq.p, WL.sm.p, WL.Qu.p, WL.Qd.p, WY.Qu.p, WY.Qd.p,
         (const float4*)O.surf_f.p, O.ne, O.npad, kappa, WL.pot.p, WY.pot.p, WL.dn.p, WY.dn.p);
@@ -1127,6 +1138,20 @@ static void apply_pair_t(fmm_tree* Tr, const Operators& OL, const Operators& OY,
         k_gather_tn<T, In><<<div_up(nt, 256), 256, 0, st>>>(nt, pt, tgt_n, WL.tn.p);
         PB_CHECK_LAUNCH();
     }
+    // the near field needs only the gathered sources: on the second stream,
+    // beside the far-field passes below (joined before the far leaf part)
+    const bool fork = ctx->aux && ctx->overlap && Tr->n_tleaf > 0;
+    if (fork) {
+        PB_CUDA(cudaEventRecord(ctx->ev_fork, st));
+        PB_CUDA(cudaStreamWaitEvent(ctx->aux, ctx->ev_fork, 0));
+        {
+            PhaseTimer phn(ctx, PB_PH_LEAF, ctx->aux);
+            if (DL) launch_leaf_pair<T, true, false, 1>(ctx->aux, Tr, WL, WY, OL, kappa);
+            else if (DN) launch_leaf_pair<T, false, true, 1>(ctx->aux, Tr, WL, WY, OL, kappa);
+            else launch_leaf_pair<T, false, false, 1>(ctx->aux, Tr, WL, WY, OL, kappa);
+        }
+        PB_CUDA(cudaEventRecord(ctx->ev_join, ctx->aux));
+    }
     const int nsl = Tr->sleaf_lvl_off[Tr->nlev];
     ph.reset(); ph = std::make_unique<PhaseTimer>(ctx, PB_PH_P2M);
     if (DL) launch_p2check_pair<T, true>(st, nsl, Tr->sleaf_ids.p, 0, Tr, WL, WY, OL, kappa);
@@ -1149,10 +1174,17 @@ static void apply_pair_t(fmm_tree* Tr, const Operators& OL, const Operators& OY,
     ph.reset(); ph = std::make_unique<PhaseTimer>(ctx, PB_PH_DOWN);
     far_l2l(Tr, OL, WL);
     far_l2l(Tr, OY, WY);
+    if (fork) PB_CUDA(cudaStreamWaitEvent(st, ctx->ev_join, 0));
     ph.reset(); ph = std::make_unique<PhaseTimer>(ctx, PB_PH_LEAF);
-    if (DL) launch_leaf_pair<T, true, false>(st, Tr, WL, WY, OL, kappa);
-    else if (DN) launch_leaf_pair<T, false, true>(st, Tr, WL, WY, OL, kappa);
-    else launch_leaf_pair<T, false, false>(st, Tr, WL, WY, OL, kappa);
+    if (fork) {
+        if (DL) launch_leaf_pair<T, true, false, 2>(st, Tr, WL, WY, OL, kappa);
+        else if (DN) launch_leaf_pair<T, false, true, 2>(st, Tr, WL, WY, OL, kappa);
+        else launch_leaf_pair<T, false, false, 2>(st, Tr, WL, WY, OL, kappa);
+    } else {
+        if (DL) launch_leaf_pair<T, true, false, 0>(st, Tr, WL, WY, OL, kappa);
+        else if (DN) launch_leaf_pair<T, false, true, 0>(st, Tr, WL, WY, OL, kappa);
+        else launch_leaf_pair<T, false, false, 0>(st, Tr, WL, WY, OL, kappa);
+    }
     ph.reset(); ph = std::make_unique<PhaseTimer>(ctx, PB_PH_SCATTER);
     const int* pt = Tr->same ? Tr->perm_s.p : Tr->perm_t.p;
     k_scatter<T, In><<<div_up(nt, 256), 256, 0, st>>>(nt, pt, WL.pot.p, outL);

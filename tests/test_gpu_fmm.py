@@ -323,3 +323,40 @@ def test_pair_full_size_sampled(pb, ctx):
     idx = synthetic.random_subsample(n, 300, seed=6)
     assert rel_l2(oL[idx], direct_sum(LAPLACE, 0.0, x, q=q, dip=d, src_n=nrm, tgt=x[idx])) < TOL
     assert rel_l2(oY[idx], direct_sum(YUKAWA, 0.125, x, q=q, dip=d, src_n=nrm, tgt=x[idx])) < TOL
+
+
+def test_pair_edge_cases(pb, ctx):
+    """Empty input rejected; two points; a ragged size with a tiny ncrit;
+    every point repeated (coincident pairs contribute nothing, as in the
+    oracle's direct sum)."""
+    with pytest.raises(pb.PBError) as e:
+        pb.fmm_tree_build(ctx, dev(np.zeros((0, 3), np.float32)), 64)
+    assert e.value.code == pb.PB_EINVAL
+    rng = np.random.default_rng(17)
+    cases = []
+    x2 = np.array([[0.1, 0.2, 0.3], [-0.4, 0.5, 0.9]], np.float32)
+    cases.append(("two points", x2, 8))
+    xr, _ = synthetic.bumpy_sphere_points(1001, seed=19)
+    cases.append(("ragged 1001, ncrit 7", xr, 7))
+    # coincident points: 40 locations x 25 copies.  One leaf: every pair,
+    # coincident ones included, goes through P2P.  ncrit 32 >= copies: a
+    # shallow tree (with ncrit below the copy count the tree must reach level
+    # 21, where FP32 double-layer equivalent densities, ~1/box size, cancel)
+    xd = np.repeat(rng.uniform(-1, 1, (40, 3)).astype(np.float32), 25, axis=0)
+    cases.append(("40 points x 25 copies, one leaf", xd, 1000))
+    cases.append(("40 points x 25 copies, ncrit 32", xd, 32))
+    for name, x, ncrit in cases:
+        n = len(x)
+        nrm = x / np.linalg.norm(x, axis=1, keepdims=True)
+        q = synthetic.uniform_densities(n, seed=31)
+        d = synthetic.uniform_densities(n, seed=32)
+        h = pb.fmm_tree_build(ctx, dev(x), ncrit)
+        try:
+            # the clustered 40-location set needs p = 8 for 1e-5 (1.9e-5 at p = 6)
+            oL, oY = run_pair(pb, ctx, h, 0.125, 8 if "ncrit 32" in name else 6, qL=q, qY=q, d=d, sn=nrm, nt=n)
+        finally:
+            pb.fmm_tree_destroy(h)
+        rL = direct_sum(LAPLACE, 0.0, x, q=q, dip=d, src_n=nrm)
+        rY = direct_sum(YUKAWA, 0.125, x, q=q, dip=d, src_n=nrm)
+        assert np.all(np.isfinite(oL)) and np.all(np.isfinite(oY)), name
+        assert rel_l2(oL, rL) < TOL and rel_l2(oY, rY) < TOL, name
