@@ -48,6 +48,24 @@ FLOPS_PAIR = {"pair_sd": 30, "pair_m": 16}
 MUFU_PAIR = 2
 
 
+def max_over_ranks(ms, dist):
+    """The slowest rank's step time (the job's time); plain value at N = 1.
+    Reduced on the GPU under NCCL, on the host under gloo."""
+    if dist is None:
+        return ms
+    import torch
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world, n_points, ms):
+    """Whole-job points/s: every rank (replica) evaluates both kernels at its
+    own n_points targets per step of ms milliseconds (weak scaling)."""
+    return world * 2 * n_points / (ms * 1e-3)
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -357,12 +375,8 @@ def main():
     pb.pb_profile(ctx, False)
     if dist:
         dist.barrier()
-    ms = sum(a.elapsed_time(b) for a, b in ev) / args.steps
-    if dist:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * 2 * args.n / (ms * 1e-3)
+    ms = max_over_ranks(sum(a.elapsed_time(b) for a, b in ev) / args.steps, dist)
+    value = job_throughput(world, args.n, ms)
 
     # the same work as two single-kernel applies (for comparison; untimed by the metric)
     for _ in range(2):
@@ -393,7 +407,7 @@ def main():
     for _ in range(args.steps):
         step_host()
     torch.cuda.synchronize()
-    e2e_ms = (time.perf_counter() - t0) * 1e3 / args.steps
+    e2e_ms = max_over_ranks((time.perf_counter() - t0) * 1e3 / args.steps, dist)
     h2d = 2 * q.nbytes + d.nbytes + nrm.nbytes          # q_lap and q_yuk are staged separately
     d2h = 2 * 4 * args.n
 
@@ -525,7 +539,7 @@ def main():
                                     "m2p_targets": info.m2p_targets, "p2l_sources": info.p2l_sources,
                                     "l2p_targets": info.l2p_targets}},
                 "roofline": roof, "cpu_baseline": cpu,
-                "e2e": {"value": world * 2 * args.n / (e2e_ms * 1e-3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "e2e": {"value": job_throughput(world, args.n, e2e_ms), "unit": UNIT, "h2d_bytes_per_step": h2d,
                         "d2h_bytes_per_step": d2h},
                 "gpu_launches": int(launches), "clocks": clocks, "pb_solve": solve, "pb_solve_batch": batch,
                 "phases_ms_per_step": {k: v[0] / args.steps for k, v in phases.items()},
