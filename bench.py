@@ -38,8 +38,8 @@ SM_MAX_MHZ = 2070.0
 MUFU_PER_SM_CLK = 16
 # dram__bytes_read.sum + dram__bytes_write.sum of one k_leaf_pair launch on
 # this workload (4M points, p = 6, ncrit = 128), from one ncu capture of the
-# current kernel (535.8 + 28.2 MB); None once the kernel changes
-LEAF_TRAFFIC_BYTES = None
+# current kernel (536.4 + 27.5 MB); None once the kernel changes
+LEAF_TRAFFIC_BYTES = 563.9e6
 # Arithmetic of one source-target pair in the paired (Laplace + Yukawa)
 # evaluation, FMA = 2 FLOPs, MUFU counted apart: SL+DL of both kernels
 # 30 FLOPs + 2 MUFU (rsqrt, ex2); monopole-only pairs of equivalent
