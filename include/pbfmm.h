@@ -237,6 +237,7 @@ int fmm_apply(pb_ctx* ctx, fmm_tree* tree, int kernel, double kappa, int p, int 
  * q_lap / q_yuk / dip may each be NULL (no such term), dip needs src_n,
  * dn_lap and dn_yuk are both NULL or both given (then tgt_n is required and
  * dip must be NULL).  Results equal two fmm_apply calls up to rounding.
+ * q_lap and q_yuk may be the same array (copied once when on the host).
  * Errors: PB_EINVAL as fmm_apply, and kappa <= 0. */
 int fmm_apply_pair(pb_ctx* ctx, fmm_tree* tree, double kappa, int p, int precision,
                    const void* q_lap, const void* q_yuk, const void* dip, const void* src_n,

@@ -367,7 +367,8 @@ int fmm_apply_pair(pb_ctx* ctx, fmm_tree* T, double kappa, int p, int precision,
     const size_t es = precision == PB_FP64 ? 8 : 4;
     Staged sqL, sqY, sd, sn, tn;
     sqL.in(q_lap, T->ns * es, st);
-    sqY.in(q_yuk, T->ns * es, st);
+    if (q_yuk != q_lap) sqY.in(q_yuk, T->ns * es, st);     // the same host array is staged once
+    else sqY.dev = sqL.dev;
     sd.in(dip, T->ns * es, st);
     sn.in(src_n, T->ns * 3 * es, st);
     tn.in(tgt_n, T->nt * 3 * es, st);
