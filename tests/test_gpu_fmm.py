@@ -360,3 +360,15 @@ def test_pair_edge_cases(pb, ctx):
         rY = direct_sum(YUKAWA, 0.125, x, q=q, dip=d, src_n=nrm)
         assert np.all(np.isfinite(oL)) and np.all(np.isfinite(oY)), name
         assert rel_l2(oL, rL) < TOL and rel_l2(oY, rY) < TOL, name
+
+
+def test_pair_same_host_array_for_both_kernels(pb, ctx, case20k):
+    """One host array given as both monopole densities (staged once) gives
+    the results of separate device copies."""
+    x, nrm, q, d, h = case20k
+    n = len(x)
+    hL = np.zeros(n, np.float32)
+    hY = np.zeros(n, np.float32)
+    pb.fmm_apply_pair(ctx, h, 0.125, 6, hL, hY, q_lap=q, q_yuk=q, dip=d, src_n=nrm)
+    oL, oY = run_pair(pb, ctx, h, 0.125, 6, qL=q, qY=q.copy(), d=d, sn=nrm, nt=n)
+    assert rel_l2(hL, oL) < 1e-6 and rel_l2(hY, oY) < 1e-6
