@@ -19,6 +19,13 @@ bool pc_tc_launch(const fmm_tree* T, const Operators& O, int child_level, bool u
                   cudaStream_t st);
 bool c2e_tc_launch(const fmm_tree* T, const Operators& O, bool up, const float* X, float* Y, float* tmp, int* err,
                    cudaStream_t st);
+// two operator sets (Laplace, Yukawa) in the same launches
+bool m2l_tc_launch2(const fmm_tree* T, const Operators& O, const Operators* O2, const float* Qu, float* Qd,
+                    const float* Qu2, float* Qd2, int* err, cudaStream_t st);
+bool pc_tc_launch2(const fmm_tree* T, const Operators& O, const Operators* O2, int child_level, bool up, float* Q,
+                   float* Q2, int* err, cudaStream_t st);
+bool c2e_tc_launch2(const fmm_tree* T, const Operators& O, const Operators* O2, bool up, const float* X, float* Y,
+                    float* tmp, const float* X2, float* Y2, float* tmp2, int* err, cudaStream_t st);
 
 constexpr double kInv4PiD = 0.07957747154594767;
 constexpr double kLog2E = 1.4426950408889634;     // log2(e)
@@ -928,19 +935,21 @@ static void far_uc2ue(fmm_tree* Tr, const Operators& O, Work<T>& W) {
 // M2M, post-order: parents at level l from children at level l + 1 (leaves
 // of level l keep their P2M result: the kernels skip them)
 template <typename T>
-static void far_m2m(fmm_tree* Tr, const Operators& O, Work<T>& W) {
+static void m2m_level(fmm_tree* Tr, const Operators& O, Work<T>& W, int l) {
     pb_ctx* ctx = Tr->ctx;
     cudaStream_t st = ctx->stream;
-    GemmArgs ga = tree_gemm_args<T>(Tr);
-    const T* m2m = opsel<T>(O, O.m2m, O.m2m_d);
-    for (int l = Tr->nlev - 2; l >= 2; --l) {
-        if constexpr (std::is_same<T, float>::value) {
-            if (!ctx->deterministic && pc_tc_launch(Tr, O, l + 1, true, W.Qu.p, ctx->dev_err, st)) continue;
-        }
-        int a0 = Tr->lvl_off[l], a1 = Tr->lvl_off[l + 1];
-        ga.mode = G_M2M; ga.ncols = a1 - a0; ga.cols = nullptr; ga.col_base = a0; ga.level = l + 1;
-        gemm_dispatch<T, T>(O.npad, st, div_up(a1 - a0, kTC), ga, m2m, W.Qu.p, W.Qu.p);
+    if constexpr (std::is_same<T, float>::value) {
+        if (!ctx->deterministic && pc_tc_launch(Tr, O, l + 1, true, W.Qu.p, ctx->dev_err, st)) return;
     }
+    GemmArgs ga = tree_gemm_args<T>(Tr);
+    int a0 = Tr->lvl_off[l], a1 = Tr->lvl_off[l + 1];
+    ga.mode = G_M2M; ga.ncols = a1 - a0; ga.cols = nullptr; ga.col_base = a0; ga.level = l + 1;
+    gemm_dispatch<T, T>(O.npad, st, div_up(a1 - a0, kTC), ga, opsel<T>(O, O.m2m, O.m2m_d), W.Qu.p, W.Qu.p);
+}
+
+template <typename T>
+static void far_m2m(fmm_tree* Tr, const Operators& O, Work<T>& W) {
+    for (int l = Tr->nlev - 2; l >= 2; --l) m2m_level(Tr, O, W, l);
 }
 
 // DC2DE at every X-list box (downward check potentials of P2L in W.chk);
@@ -993,19 +1002,74 @@ static void far_m2l(fmm_tree* Tr, const Operators& O, Work<T>& W) {
 
 // L2L, pre-order (DC2DE folded), from parents at level l - 1
 template <typename T>
-static void far_l2l(fmm_tree* Tr, const Operators& O, Work<T>& W) {
+static void l2l_level(fmm_tree* Tr, const Operators& O, Work<T>& W, int l) {
     pb_ctx* ctx = Tr->ctx;
     cudaStream_t st = ctx->stream;
+    if constexpr (std::is_same<T, float>::value) {
+        if (!ctx->deterministic && pc_tc_launch(Tr, O, l, false, W.Qd.p, ctx->dev_err, st)) return;
+    }
     GemmArgs ga = tree_gemm_args<T>(Tr);
-    const T* l2l = opsel<T>(O, O.l2l, O.l2l_d);
+    int p0 = Tr->lvl_off[l - 1], p1 = Tr->lvl_off[l];
+    ga.mode = G_L2L; ga.ncols = p1 - p0; ga.cols = nullptr; ga.col_base = p0; ga.level = l;
+    gemm_dispatch<T, T>(O.npad, st, div_up(p1 - p0, kTC), ga, opsel<T>(O, O.l2l, O.l2l_d), W.Qd.p, W.Qd.p);
+}
+
+template <typename T>
+static void far_l2l(fmm_tree* Tr, const Operators& O, Work<T>& W) {
+    for (int l = 3; l < Tr->nlev; ++l) l2l_level(Tr, O, W, l);
+}
+
+// ---- the far-field steps of the paired apply: both kernels in one
+// tensor-core launch where that path applies, else one kernel after the other
+template <typename T>
+static void far_pair_c2e(fmm_tree* Tr, const Operators& OL, const Operators& OY, Work<T>& WL, Work<T>& WY, bool up) {
+    if constexpr (std::is_same<T, float>::value) {
+        if (c2e_tc_launch2(Tr, OL, &OY, up, WL.chk.p, up ? WL.Qu.p : WL.Qd.p, WL.tmp.p, WY.chk.p,
+                           up ? WY.Qu.p : WY.Qd.p, WY.tmp.p, Tr->ctx->dev_err, Tr->ctx->stream))
+            return;
+    }
+    if (up) { far_uc2ue(Tr, OL, WL); far_uc2ue(Tr, OY, WY); }
+    else { far_dc2de_x(Tr, OL, WL); far_dc2de_x(Tr, OY, WY); }
+}
+
+template <typename T>
+static void far_pair_m2m(fmm_tree* Tr, const Operators& OL, const Operators& OY, Work<T>& WL, Work<T>& WY) {
+    pb_ctx* ctx = Tr->ctx;
+    for (int l = Tr->nlev - 2; l >= 2; --l) {
+        if constexpr (std::is_same<T, float>::value) {
+            if (!ctx->deterministic &&
+                pc_tc_launch2(Tr, OL, &OY, l + 1, true, WL.Qu.p, WY.Qu.p, ctx->dev_err, ctx->stream))
+                continue;
+        }
+        m2m_level(Tr, OL, WL, l);
+        m2m_level(Tr, OY, WY, l);
+    }
+}
+
+template <typename T>
+static void far_pair_l2l(fmm_tree* Tr, const Operators& OL, const Operators& OY, Work<T>& WL, Work<T>& WY) {
+    pb_ctx* ctx = Tr->ctx;
     for (int l = 3; l < Tr->nlev; ++l) {
         if constexpr (std::is_same<T, float>::value) {
-            if (!ctx->deterministic && pc_tc_launch(Tr, O, l, false, W.Qd.p, ctx->dev_err, st)) continue;
+            if (!ctx->deterministic &&
+                pc_tc_launch2(Tr, OL, &OY, l, false, WL.Qd.p, WY.Qd.p, ctx->dev_err, ctx->stream))
+                continue;
         }
-        int p0 = Tr->lvl_off[l - 1], p1 = Tr->lvl_off[l];
-        ga.mode = G_L2L; ga.ncols = p1 - p0; ga.cols = nullptr; ga.col_base = p0; ga.level = l;
-        gemm_dispatch<T, T>(O.npad, st, div_up(p1 - p0, kTC), ga, l2l, W.Qd.p, W.Qd.p);
+        l2l_level(Tr, OL, WL, l);
+        l2l_level(Tr, OY, WY, l);
     }
+}
+
+template <typename T>
+static void far_pair_m2l(fmm_tree* Tr, const Operators& OL, const Operators& OY, Work<T>& WL, Work<T>& WY) {
+    pb_ctx* ctx = Tr->ctx;
+    if constexpr (std::is_same<T, float>::value) {
+        if (Tr->m2l_pairs.nitems > 0 && !ctx->deterministic &&
+            m2l_tc_launch2(Tr, OL, &OY, WL.Qu.p, WL.Qd.p, WY.Qu.p, WY.Qd.p, ctx->dev_err, ctx->stream))
+            return;
+    }
+    far_m2l(Tr, OL, WL);
+    far_m2l(Tr, OY, WY);
 }
 
 // equivalent densities and check potentials of one kernel
@@ -1156,24 +1220,19 @@ static void apply_pair_t(fmm_tree* Tr, const Operators& OL, const Operators& OY,
     ph.reset(); ph = std::make_unique<PhaseTimer>(ctx, PB_PH_P2M);
     if (DL) launch_p2check_pair<T, true>(st, nsl, Tr->sleaf_ids.p, 0, Tr, WL, WY, OL, kappa);
     else launch_p2check_pair<T, false>(st, nsl, Tr->sleaf_ids.p, 0, Tr, WL, WY, OL, kappa);
-    far_uc2ue(Tr, OL, WL);
-    far_uc2ue(Tr, OY, WY);
+    far_pair_c2e(Tr, OL, OY, WL, WY, true);
     ph.reset(); ph = std::make_unique<PhaseTimer>(ctx, PB_PH_M2M);
-    far_m2m(Tr, OL, WL);
-    far_m2m(Tr, OY, WY);
+    far_pair_m2m(Tr, OL, OY, WL, WY);
     ph.reset(); ph = std::make_unique<PhaseTimer>(ctx, PB_PH_P2L);
     if (Tr->n_xbox > 0) {
         if (DL) launch_p2check_pair<T, true>(st, Tr->n_xbox, Tr->xbox_ids.p, 1, Tr, WL, WY, OL, kappa);
         else launch_p2check_pair<T, false>(st, Tr->n_xbox, Tr->xbox_ids.p, 1, Tr, WL, WY, OL, kappa);
-        far_dc2de_x(Tr, OL, WL);
-        far_dc2de_x(Tr, OY, WY);
+        far_pair_c2e(Tr, OL, OY, WL, WY, false);
     }
     ph.reset(); ph = std::make_unique<PhaseTimer>(ctx, PB_PH_M2L);
-    far_m2l(Tr, OL, WL);
-    far_m2l(Tr, OY, WY);
+    far_pair_m2l(Tr, OL, OY, WL, WY);
     ph.reset(); ph = std::make_unique<PhaseTimer>(ctx, PB_PH_DOWN);
-    far_l2l(Tr, OL, WL);
-    far_l2l(Tr, OY, WY);
+    far_pair_l2l(Tr, OL, OY, WL, WY);
     if (fork) PB_CUDA(cudaStreamWaitEvent(st, ctx->ev_join, 0));
     ph.reset(); ph = std::make_unique<PhaseTimer>(ctx, PB_PH_LEAF);
     if (fork) {

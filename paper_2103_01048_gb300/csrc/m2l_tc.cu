@@ -381,15 +381,27 @@ __device__ __forceinline__ bool mbar_wait_cta(uint64_t* bar, uint32_t parity, vo
     return true;
 }
 
+// Operator set and box vectors of one launch; blockIdx.z selects the set, so
+// one launch serves the Laplace and the Yukawa half of the paired apply
+// (their pair lists and operator indices coincide).
+struct TcSets {
+    const float* ops[2];
+    const float* X[2];
+    float* Y[2];
+};
+
 template <int NPAD>
 __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(const int4* __restrict__ items, const int* __restrict__ ptgt,
-                                                          const int* __restrict__ psrc, const float* __restrict__ ops,
-                                                          const float* __restrict__ Qu, float* __restrict__ Qd,
+                                                          const int* __restrict__ psrc, const TcSets sets,
                                                           int* __restrict__ err) {
     // Generic tensor-core box-operator product: for every pair p of the
-    // item, Qd[tgt[p]] += Op(item) Qu[src[p]] (Op resident for the CTA).
-    // Used for M2L (operator per level and offset) and for M2M / L2L
-    // (operator per child level and octant).
+    // item, Y[tgt[p]] += Op(item) X[src[p]] (Op resident for the CTA).
+    // Used for M2L (operator per level and offset), for M2M / L2L
+    // (operator per child level and octant) and for the factored
+    // check -> equivalent solves (operator per level).
+    const float* __restrict__ ops = sets.ops[blockIdx.z];
+    const float* __restrict__ Qu = sets.X[blockIdx.z];
+    float* __restrict__ Qd = sets.Y[blockIdx.z];
     constexpr int NH = NPAD / 2;                     // output rows of this CTA (MMA N)
     constexpr int KB = NPAD / 32;                    // K blocks of 32 tf32 (128 B)
     constexpr uint32_t B_SPLIT = KB * NH * 128;      // bytes of one of hi / lo
@@ -582,18 +594,8 @@ static size_t tc_smem_bytes() {
 }
 
 template <int NPAD>
-static void launch_tc_items(const int4* items, int nitems, const int* tgt, const int* src, const float* ops,
-                            const float* X, float* Y, int* err, cudaStream_t st);
-
-template <int NPAD>
-static void launch_tc(const fmm_tree* T, const Operators& O, const float* Qu, float* Qd, int* err, cudaStream_t st) {
-    launch_tc_items<NPAD>(T->m2l_pairs.items.p, T->m2l_pairs.nitems, T->m2l_pairs.tgt.p, T->m2l_pairs.src.p,
-                          O.m2l_tc.p, Qu, Qd, err, st);
-}
-
-template <int NPAD>
-static void launch_tc_items(const int4* items, int nitems, const int* tgt, const int* src, const float* ops,
-                            const float* X, float* Y, int* err, cudaStream_t st) {
+static void launch_tc_items(const int4* items, int nitems, const int* tgt, const int* src, const TcSets& sets,
+                            int nsets, int* err, cudaStream_t st) {
     if (nitems <= 0) return;
     const size_t sm = tc_smem_bytes<NPAD>();
     // opt in to the large shared-memory carve-out once per process and device
@@ -605,72 +607,92 @@ static void launch_tc_items(const int4* items, int nitems, const int* tgt, const
         PB_CUDA(cudaFuncSetAttribute(k_m2l_tc<NPAD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
         attr_set[dev] = true;
     }
-    dim3 grid(nitems, 2);
-    k_m2l_tc<NPAD><<<grid, kTcThreads, sm, st>>>(items, tgt, src, ops, X, Y, err);
+    dim3 grid(nitems, 2, nsets);
+    k_m2l_tc<NPAD><<<grid, kTcThreads, sm, st>>>(items, tgt, src, sets, err);
     PB_CHECK_LAUNCH();
 }
 
+static bool tc_dispatch(int npad, const int4* items, int nitems, const int* tgt, const int* src, const TcSets& sets,
+                        int nsets, int* err, cudaStream_t st) {
+    switch (npad) {
+        case 32: launch_tc_items<32>(items, nitems, tgt, src, sets, nsets, err, st); return true;
+        case 64: launch_tc_items<64>(items, nitems, tgt, src, sets, nsets, err, st); return true;
+        case 128: launch_tc_items<128>(items, nitems, tgt, src, sets, nsets, err, st); return true;
+        case 160: launch_tc_items<160>(items, nitems, tgt, src, sets, nsets, err, st); return true;
+        default: return false;
+    }
+}
+
+static bool tc_ok(const Operators& O) { return O.have_tc && O.npad <= kTcMaxNpad && O.npad % 32 == 0; }
+
 // M2M (up = true: parents at level l - 1 += M2M children at level l) or L2L
-// (children at level l += L2L parents at level l - 1) on the tensor cores;
-// false when the tensor-core path does not apply
-bool pc_tc_launch(const fmm_tree* T, const Operators& O, int child_level, bool up, float* Q, int* err,
-                  cudaStream_t st) {
-    if (!O.have_tc || !O.m2m_tc.p || !O.l2l_tc.p) return false;
+// (children at level l += L2L parents at level l - 1) on the tensor cores,
+// for one operator set (O2 == nullptr) or for two in one launch; false when
+// the tensor-core path does not apply
+bool pc_tc_launch2(const fmm_tree* T, const Operators& O, const Operators* O2, int child_level, bool up, float* Q,
+                   float* Q2, int* err, cudaStream_t st) {
+    if (!tc_ok(O) || !O.m2m_tc.p || !O.l2l_tc.p) return false;
+    if (O2 && (!tc_ok(*O2) || !O2->m2m_tc.p || !O2->l2l_tc.p || O2->npad != O.npad)) return false;
     const auto& P = T->pc_pairs;
     if (child_level < 3 || child_level >= T->nlev || (int)P.level_item_off.size() != T->nlev + 1) return false;
     const int i0 = P.level_item_off[child_level], i1 = P.level_item_off[child_level + 1];
     if (i1 <= i0) return true;
-    const int4* items = P.items.p + i0;
     const int* tgt = up ? P.parent.p : P.child.p;
     const int* src = up ? P.child.p : P.parent.p;
-    const float* ops = up ? O.m2m_tc.p : O.l2l_tc.p;
-    switch (O.npad) {
-        case 32: launch_tc_items<32>(items, i1 - i0, tgt, src, ops, Q, Q, err, st); return true;
-        case 64: launch_tc_items<64>(items, i1 - i0, tgt, src, ops, Q, Q, err, st); return true;
-        case 128: launch_tc_items<128>(items, i1 - i0, tgt, src, ops, Q, Q, err, st); return true;
-        case 160: launch_tc_items<160>(items, i1 - i0, tgt, src, ops, Q, Q, err, st); return true;
-        default: return false;
-    }
+    TcSets sets{{up ? O.m2m_tc.p : O.l2l_tc.p, O2 ? (up ? O2->m2m_tc.p : O2->l2l_tc.p) : nullptr},
+                {Q, Q2}, {Q, Q2}};
+    return tc_dispatch(O.npad, P.items.p + i0, i1 - i0, tgt, src, sets, O2 ? 2 : 1, err, st);
+}
+
+bool pc_tc_launch(const fmm_tree* T, const Operators& O, int child_level, bool up, float* Q, int* err,
+                  cudaStream_t st) {
+    return pc_tc_launch2(T, O, nullptr, child_level, up, Q, nullptr, err, st);
 }
 
 // Check -> equivalent solve Y = W2 (W1 X) at the upward (sleaf) or downward
 // (X-list) boxes on the tensor cores: two passes through `tmp`, which is
 // zeroed first (every row of a pass receives exactly one product, so the
 // result does not depend on the order of the reductions). Y rows of those
-// boxes must be zero on entry. False when the tensor-core path does not apply.
-bool c2e_tc_launch(const fmm_tree* T, const Operators& O, bool up, const float* X, float* Y, float* tmp, int* err,
-                   cudaStream_t st) {
-    if (!O.have_tc || !O.uc2ue_w1_tc.p) return false;
+// boxes must be zero on entry. One operator set, or two (O2, X2, Y2, tmp2)
+// in the same launches. False when the tensor-core path does not apply.
+bool c2e_tc_launch2(const fmm_tree* T, const Operators& O, const Operators* O2, bool up, const float* X, float* Y,
+                    float* tmp, const float* X2, float* Y2, float* tmp2, int* err, cudaStream_t st) {
+    if (!tc_ok(O) || !O.uc2ue_w1_tc.p) return false;
+    if (O2 && (!tc_ok(*O2) || !O2->uc2ue_w1_tc.p || O2->npad != O.npad)) return false;
     const int nitems = up ? T->n_c2e_up : T->n_c2e_dn;
     if (nitems == 0) return true;
     const int4* items = up ? T->c2e_items_up.p : T->c2e_items_dn.p;
     const int* ids = up ? T->sleaf_ids.p : T->xbox_ids.p;
-    const float* w1 = up ? O.uc2ue_w1_tc.p : O.dc2de_w1_tc.p;
-    const float* w2 = up ? O.uc2ue_w2_tc.p : O.dc2de_w2_tc.p;
-    PB_CUDA(cudaMemsetAsync(tmp, 0, (size_t)T->nbox * O.npad * sizeof(float), st));
-    switch (O.npad) {
-        case 32: launch_tc_items<32>(items, nitems, ids, ids, w1, X, tmp, err, st);
-                 launch_tc_items<32>(items, nitems, ids, ids, w2, tmp, Y, err, st); return true;
-        case 64: launch_tc_items<64>(items, nitems, ids, ids, w1, X, tmp, err, st);
-                 launch_tc_items<64>(items, nitems, ids, ids, w2, tmp, Y, err, st); return true;
-        case 128: launch_tc_items<128>(items, nitems, ids, ids, w1, X, tmp, err, st);
-                  launch_tc_items<128>(items, nitems, ids, ids, w2, tmp, Y, err, st); return true;
-        case 160: launch_tc_items<160>(items, nitems, ids, ids, w1, X, tmp, err, st);
-                  launch_tc_items<160>(items, nitems, ids, ids, w2, tmp, Y, err, st); return true;
-        default: return false;
-    }
+    auto w1 = [&](const Operators& o) { return up ? o.uc2ue_w1_tc.p : o.dc2de_w1_tc.p; };
+    auto w2 = [&](const Operators& o) { return up ? o.uc2ue_w2_tc.p : o.dc2de_w2_tc.p; };
+    const size_t bytes = (size_t)T->nbox * O.npad * sizeof(float);
+    PB_CUDA(cudaMemsetAsync(tmp, 0, bytes, st));
+    if (O2) PB_CUDA(cudaMemsetAsync(tmp2, 0, bytes, st));
+    const int ns = O2 ? 2 : 1;
+    TcSets p1{{w1(O), O2 ? w1(*O2) : nullptr}, {X, X2}, {tmp, tmp2}};
+    TcSets p2{{w2(O), O2 ? w2(*O2) : nullptr}, {tmp, tmp2}, {Y, Y2}};
+    if (!tc_dispatch(O.npad, items, nitems, ids, ids, p1, ns, err, st)) return false;
+    return tc_dispatch(O.npad, items, nitems, ids, ids, p2, ns, err, st);
 }
 
-// returns false when the tensor-core path does not apply (caller uses SIMT)
+bool c2e_tc_launch(const fmm_tree* T, const Operators& O, bool up, const float* X, float* Y, float* tmp, int* err,
+                   cudaStream_t st) {
+    return c2e_tc_launch2(T, O, nullptr, up, X, Y, tmp, nullptr, nullptr, nullptr, err, st);
+}
+
+// M2L on the tensor cores for one or two operator sets; false when the
+// tensor-core path does not apply (caller uses the CUDA-core kernel)
+bool m2l_tc_launch2(const fmm_tree* T, const Operators& O, const Operators* O2, const float* Qu, float* Qd,
+                    const float* Qu2, float* Qd2, int* err, cudaStream_t st) {
+    if (!tc_ok(O) || (O2 && (!tc_ok(*O2) || O2->npad != O.npad))) return false;
+    if (T->m2l_pairs.nitems == 0) return true;
+    TcSets sets{{O.m2l_tc.p, O2 ? O2->m2l_tc.p : nullptr}, {Qu, Qu2}, {Qd, Qd2}};
+    return tc_dispatch(O.npad, T->m2l_pairs.items.p, T->m2l_pairs.nitems, T->m2l_pairs.tgt.p, T->m2l_pairs.src.p,
+                       sets, O2 ? 2 : 1, err, st);
+}
+
 bool m2l_tc_launch(const fmm_tree* T, const Operators& O, const float* Qu, float* Qd, int* err, cudaStream_t st) {
-    if (!O.have_tc || T->m2l_pairs.nitems == 0) return T->m2l_pairs.nitems == 0 && O.have_tc;
-    switch (O.npad) {
-        case 32: launch_tc<32>(T, O, Qu, Qd, err, st); return true;
-        case 64: launch_tc<64>(T, O, Qu, Qd, err, st); return true;
-        case 128: launch_tc<128>(T, O, Qu, Qd, err, st); return true;
-        case 160: launch_tc<160>(T, O, Qu, Qd, err, st); return true;
-        default: return false;
-    }
+    return m2l_tc_launch2(T, O, nullptr, Qu, Qd, nullptr, nullptr, err, st);
 }
 
 }  // namespace pbfmm
