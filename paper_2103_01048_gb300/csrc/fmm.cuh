@@ -23,7 +23,6 @@ struct Operators {
     DBuf<double> surf;            // [ne][3] unit surface points
     DBuf<float> surf_f;           // [ne][4] float copy (x, y, z, 0)
     // FP32 copies
-    DBuf<float> uc2ue, dc2de;     // [nlev][npad^2]
     // factored solves of the FP32 path: pinv = W2 W1 (W1 = D V^T K^T, W2 = V)
     DBuf<float> uc2ue_w1, uc2ue_w2, dc2de_w1, dc2de_w2;   // [nlev][npad^2]
     DBuf<float> m2m, l2l;         // [nlev][8][npad^2]  (child level index)

@@ -210,7 +210,7 @@ __global__ void k_store_padded(int n, int npad, const double* __restrict__ src, 
     if (idx >= npad * npad) return;
     int i = idx / npad, j = idx % npad;
     double v = (i < n && j < n) ? src[i * n + j] : 0.0;
-    dst_f[idx] = (float)v;
+    if (dst_f) dst_f[idx] = (float)v;
     if (dst_d) dst_d[idx] = v;
 }
 
@@ -279,7 +279,6 @@ std::shared_ptr<Operators> get_operators(fmm_tree* T, int kernel, double kappa, 
     PB_CUDA(cudaMemcpyAsync(O->surf.p, s.data(), s.size() * sizeof(double), cudaMemcpyHostToDevice, st));
     PB_CUDA(cudaMemcpyAsync(O->surf_f.p, sf.data(), sf.size() * sizeof(float), cudaMemcpyHostToDevice, st));
     const size_t m2 = (size_t)np * np;
-    O->uc2ue.alloc(L * m2, st); O->dc2de.alloc(L * m2, st);
     O->uc2ue_d.alloc(L * m2, st); O->dc2de_d.alloc(L * m2, st);
     O->m2m.alloc(L * 8 * m2, st); O->l2l.alloc(L * 8 * m2, st);
     O->m2l.alloc(L * (size_t)kNumOffsets * m2, st);
@@ -300,11 +299,11 @@ std::shared_ptr<Operators> get_operators(fmm_tree* T, int kernel, double kappa, 
         // UC2UE_l, DC2DE_l
         Bd.kmat(Bd.A.p, zero, kAlphaOuter * r, zero, kAlphaInner * r);
         Bd.pinv(Bd.A.p, Bd.B.p);
-        Bd.store(Bd.B.p, O->uc2ue.p + l * m2, O->uc2ue_d.p + l * m2, np);
+        Bd.store(Bd.B.p, nullptr, O->uc2ue_d.p + l * m2, np);
         // DC2DE_l (kept in Bd.G's sibling buffer `dc`)
         Bd.kmat(Bd.A.p, zero, kAlphaInner * r, zero, kAlphaOuter * r);
         Bd.pinv(Bd.A.p, dc.p);
-        Bd.store(dc.p, O->dc2de.p + l * m2, O->dc2de_d.p + l * m2, np);
+        Bd.store(dc.p, nullptr, O->dc2de_d.p + l * m2, np);
         if (l > 0) {
             for (int c = 0; c < 8; ++c) {
                 const double cc[3] = {((c >> 2) & 1) ? r : -r, ((c >> 1) & 1) ? r : -r, (c & 1) ? r : -r};
