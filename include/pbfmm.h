@@ -110,10 +110,11 @@ int pb_profile(pb_ctx* ctx, int enable);
  *                         atoms x quadrature points <= 4e9, else by the FMM
  *                         (trees over atoms and quadrature points, order p
  *                         of the mesh); 1: always direct; 2: always FMM.
- *   PB_OPT_DETERMINISTIC  0 (default): tensor-core M2L/M2M/L2L with row
- *                         reductions (summation order run-dependent at
- *                         ~1e-7); 1: CUDA-core kernels with a fixed order,
- *                         bitwise reproducible results.
+ *   PB_OPT_DETERMINISTIC  0 (default): M2L/M2M/L2L with row reductions
+ *                         (tensor cores, or CUDA cores parallel over pairs;
+ *                         summation order run-dependent); 1: CUDA-core
+ *                         kernels with a fixed order, bitwise reproducible
+ *                         results.
  *   PB_OPT_SINGULAR       singular Galerkin entries of vertex-sharing pairs
  *                         (analytic inner integrals, graded outer rule):
  *                         0 (default): FP64 with a 5-level graded rule up to
@@ -213,11 +214,14 @@ int fmm_tree_export_list(const fmm_tree* tree, int which, int64_t* off, int32_t*
  * Buffers may be host or device memory (see conventions).  With device
  * buffers the call is asynchronous; with any host buffer it synchronises.
  * Operators for (kernel, kappa, p, tree size) are precomputed on first use
- * and cached in the tree.  With PB_MIXED and p <= 6 the M2L runs on the
- * tensor cores (TF32 split into hi + lo parts, three products per step);
- * its row reductions make the summation order run-dependent at the 1e-7
- * level.  Its waits are bounded: a timeout is reported as PB_ETIMEOUT by the
- * next synchronising call (pb_sync, or this call when it synchronises).
+ * and cached in the tree.  With PB_MIXED and p <= 6 the M2L, M2M, L2L and
+ * the check -> equivalent solves run on the tensor cores (TF32 split into
+ * hi + lo parts, three products per step); otherwise on the CUDA cores, the
+ * M2L parallel over interaction pairs.  The M2L / M2M / L2L reductions make
+ * the summation order run-dependent (~1e-7 in FP32, ~1e-16 in FP64);
+ * PB_OPT_DETERMINISTIC selects fixed-order CUDA-core kernels.  The tensor-core
+ * waits are bounded: a timeout is reported as PB_ETIMEOUT by the next
+ * synchronising call (pb_sync, or this call when it synchronises).
  * Errors: PB_EINVAL for missing normals, p out of range, kappa <= 0 with
  * FMM_YUKAWA, dip together with out_dn. */
 int fmm_apply(pb_ctx* ctx, fmm_tree* tree, int kernel, double kappa, int p, int precision,
