@@ -372,3 +372,15 @@ def test_pair_same_host_array_for_both_kernels(pb, ctx, case20k):
     pb.fmm_apply_pair(ctx, h, 0.125, 6, hL, hY, q_lap=q, q_yuk=q, dip=d, src_n=nrm)
     oL, oY = run_pair(pb, ctx, h, 0.125, 6, qL=q, qY=q.copy(), d=d, sn=nrm, nt=n)
     assert rel_l2(hL, oL) < 1e-6 and rel_l2(hY, oY) < 1e-6
+
+
+@pytest.mark.parametrize("p", [3, 4, 5])
+def test_pair_equals_two_applies_low_order(pb, ctx, case20k, p):
+    """The merged Laplace + Yukawa tensor-core launches at the smaller
+    operator sizes (npad 32 and 64: p = 3, 4, 5) give the single-kernel
+    results."""
+    x, nrm, q, d, h = case20k
+    oL, oY = run_pair(pb, ctx, h, 0.125, p, qL=q, qY=q, d=d, sn=nrm, nt=len(x))
+    sL, _ = run_apply(pb, ctx, h, LAPLACE, 0.0, p, q=q, d=d, sn=nrm, nt=len(x))
+    sY, _ = run_apply(pb, ctx, h, YUKAWA, 0.125, p, q=q, d=d, sn=nrm, nt=len(x))
+    assert rel_l2(oL, sL) < 1e-6 and rel_l2(oY, sY) < 1e-6
