@@ -184,9 +184,11 @@ def run_reference(args, rank, world):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"fmm_apply {args.n} bumpy-sphere points, Laplace+Yukawa SL+DL, "
-                                   f"FP64 direct sum on {ntgt} sampled targets per step",
-                       "global_batch": args.n, "seq_len": None, "parallelism": "host cores"},
+            "config": {"workload": f"fmm_apply_pair {args.n} bumpy-sphere points (amp 0.05), Laplace+Yukawa "
+                                   f"(kappa {KAPPA}) SL+DL in one traversal, p={args.p}, ncrit={args.ncrit}, "
+                                   f"tree cached",
+                       "global_batch": args.n, "seq_len": None, "parallelism": "host cores",
+                       "reference_sample": f"FP64 direct sums (the oracle) at {ntgt} sampled targets per step"},
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": f"{ntgt} targets x {args.n} sources x 2 kernels per step",
                              "cpu": cpu_model()},
