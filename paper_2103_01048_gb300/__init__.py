@@ -4,6 +4,19 @@ Argument marshalling only: every step of the computation runs in the CUDA
 library libpbfmm.so built from csrc/.  Buffers may be torch tensors (device
 or host) or numpy arrays (host); their raw pointers are passed through.
 There is no fallback: importing this package fails if the library is absent.
+
+Typical use (device tensors; host arrays work too and synchronise):
+
+    import paper_2103_01048_gb300 as pb
+    ctx = pb.pb_create(0, None)
+    tree = pb.fmm_tree_build(ctx, xyz, 128)            # float32 [n, 3]
+    pb.fmm_apply_pair(ctx, tree, 0.125, 6, out_lap, out_yuk,
+                      q_lap=q, q_yuk=q, dip=d, src_n=normals)
+    mesh = pb.pb_mesh_setup(ctx, verts, tris, 3, 6, 128)
+    res, status = pb.pb_solve(ctx, mesh, atoms, charges, 4.0, 80.0, 0.125, 1e-6)
+    dG = pb.pb_solvation_energy(ctx, res)              # kcal/mol
+    pb.pb_result_destroy(res); pb.pb_mesh_destroy(mesh)
+    pb.fmm_tree_destroy(tree); pb.pb_destroy(ctx)
 """
 from __future__ import annotations
 
