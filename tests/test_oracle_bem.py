@@ -158,3 +158,36 @@ def test_kirkwood_discrete_off_centre():
     assert errs[1] < errs[0] and errs[2] < errs[1]
     assert 3.0 < errs[1] / errs[2] < 5.0
     assert errs[-1] / abs(g["energy_kcal_mol"]) < 1e-2
+
+
+def _monomial_exact(a, b):
+    """int over the reference triangle (area 1/2) of l1^a l2^b, divided by
+    its area: 2 a! b! / (a + b + 2)!  (Dirichlet integral)."""
+    from math import factorial
+    return 2.0 * factorial(a) * factorial(b) / factorial(a + b + 2)
+
+
+@pytest.mark.parametrize("nq,degree", [(3, 2), (6, 4)])
+def test_regular_rule_exact_degree(nq, degree):
+    """The regular rules integrate every monomial l1^a l2^b with a + b <= the
+    rule's degree exactly (interior degree-2 3-point rule, Dunavant's degree-4
+    6-point rule; weights normalised to sum to 1), and are not exact one
+    degree higher.  The published constants are given to 15 digits, so
+    'exact' is 1e-13 here."""
+    L, W = bem.regular_rule(nq)
+    assert abs(W.sum() - 1.0) < 1e-14
+    assert np.allclose(L.sum(axis=1), 1.0, atol=1e-15)
+    for a in range(degree + 1):
+        for b in range(degree + 1 - a):
+            got = (W * L[:, 1] ** a * L[:, 2] ** b).sum()
+            assert abs(got - _monomial_exact(a, b)) < 1e-13, (nq, a, b)
+    # one degree higher the rule is no longer exact for some monomial
+    errs = [abs((W * L[:, 1] ** a * L[:, 2] ** (degree + 1 - a)).sum() - _monomial_exact(a, degree + 1 - a))
+            for a in range(degree + 2)]
+    assert max(errs) > 1e-6
+    # symmetric under permutations of the barycentric coordinates
+    for perm in ([1, 2, 0], [2, 0, 1], [1, 0, 2]):
+        Lp = L[:, perm]
+        for a in range(degree + 1):
+            for b in range(degree + 1 - a):
+                assert abs((W * Lp[:, 1] ** a * Lp[:, 2] ** b).sum() - _monomial_exact(a, b)) < 1e-13
