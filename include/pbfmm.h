@@ -143,10 +143,24 @@ int pb_profile_read(pb_ctx* ctx, int phase, double* ms, int64_t* calls);
  * `tgt_xyz` is non-NULL, a distinct target set (device, float [n_tgt][3]);
  * with tgt_xyz NULL the targets are the sources (n_tgt ignored).
  * ncrit >= 1 is the maximum point count of a leaf (sources plus targets when
- * the sets differ).  Cube, Morton keys (63-bit, FP64 quantisation with
- * correctly rounded operations), stable key sort, split rule and list
- * definitions are documented in the library's DESIGN notes and reproduced
- * bit for bit by the oracle.  Synchronous (returns when the tree is built).
+ * the sets differ).  Synchronous (returns when the tree is built).  The tree
+ * is defined exactly (the oracle reproduces it bit for bit):
+ *   - cube: centre = midpoint of the FP32 coordinate extremes, half-width
+ *     R = (max extent / 2)(1 + 2^-20), in FP64;
+ *   - Morton keys: per axis floor((x - lo) 2^21 / (2R)) clamped to
+ *     [0, 2^21 - 1], computed with correctly rounded FP64 operations (no
+ *     fused multiply-add), bits interleaved x, y, z from the most
+ *     significant; 63-bit keys sorted stably (ties keep the input order);
+ *   - a box splits while it holds more than ncrit points and its level is
+ *     below 21; empty children are dropped; boxes are numbered level by
+ *     level in Morton order;
+ *   - lists (adjacency = the closed cubes intersect; colleagues = the
+ *     adjacent boxes of the same level): U(B), for a leaf B, every adjacent
+ *     leaf, B included (near field, P2P); V(B) the children of the parent's
+ *     colleagues not adjacent to B (interaction list, M2L); W(B), for a leaf
+ *     B, the descendants D of B's colleagues with D not adjacent to B but
+ *     D's parent adjacent (M2P); X(B) the coarser leaves adjacent to B's
+ *     parent but not to B (P2L).
  * Errors: PB_EINVAL for n_src < 1, ncrit < 1 or NULL src_xyz. */
 int fmm_tree_build(pb_ctx* ctx, const float* src_xyz, int64_t n_src,
                    const float* tgt_xyz, int64_t n_tgt, int ncrit, fmm_tree** out);
@@ -343,19 +357,33 @@ int pb_tune_ncrit(pb_ctx* ctx, const float* xyz, int64_t n, int p, const int32_t
  * adjoint iterate).  Synchronous. */
 int pb_energy_grad(pb_ctx* ctx, pb_result* res, double tol, int max_iter, double* dEdq, double* dEdx);
 
-/* Same result as pb_solvation_energy, without allocating device memory.
- * No counterpart in the paper: it exists for callers that cannot allocate
- * at this point (for example while a CUDA graph is being captured, or with
- * an allocator that is locked after start-up).  The reaction potential at
- * the atoms is kept in a fixed scratch array compiled into the library
- * (262,144 doubles, 2 MB, held on every GPU that loads the library until
- * the process exits), so res may hold at most 262,144 atoms (else
- * PB_EINVAL).  dG_device is a caller-owned DEVICE double that receives the
- * energy in kcal/mol.  Asynchronous on the context stream.  The first call
- * on a device looks up the scratch array's device address (once per
- * device); make that first call before any stream capture.  All calls share
- * the one scratch array: calls that overlap on the GPU (other streams or
- * contexts on the same device) race and must be serialised by the caller. */
+/* The polar solvation energy of a solved system, like pb_solvation_energy,
+ * but without allocating any device memory.  The paper has no counterpart:
+ * this entry exists for callers that cannot allocate device memory at the
+ * point where they need the energy, for example an application whose
+ * device allocator is locked after start-up (a fixed memory budget reserved
+ * up front), or a real-time loop that must not enter the allocator and risk
+ * its latency or an out-of-memory failure in the middle of a step.
+ *   - All intermediate values (partial reaction potentials at the atoms)
+ *     live in one fixed scratch array compiled into the library: 524,288
+ *     doubles (4 MB), held on every GPU that loads the library until the
+ *     process exits.  res may hold at most 262,144 atoms (else PB_EINVAL).
+ *   - The reaction potential is always the direct FP64 sum over the
+ *     quadrature points (Eq. phi_reac), whatever PB_OPT_COUPLING says.
+ *     Where pb_solvation_energy uses the FMM coupling instead (option 2, or
+ *     atoms x quadrature points above 4e9 under the automatic setting) the
+ *     two energies differ by the FMM's error (about 1e-6 relative at p = 6),
+ *     otherwise by rounding only.  The direct sum costs atoms x quadrature
+ *     points pair evaluations, so it is slow for very large systems.
+ *   - dG_device must be a caller-owned DEVICE double on the context's GPU
+ *     (else PB_EINVAL); it receives the energy in kcal/mol.
+ *   - Asynchronous on the context stream.  The first call on a device looks
+ *     up the scratch array's device address (once per device, with that
+ *     device current).
+ *   - All calls share the one scratch array and its contents are whatever
+ *     the last call left: calls whose work overlaps on the GPU (other
+ *     streams or contexts on the same device) race, and the caller must
+ *     serialise them. */
 int pb_solvation_energy_noalloc(pb_ctx* ctx, const pb_result* res, double* dG_device);
 
 #ifdef __cplusplus

@@ -1,0 +1,52 @@
+/*
+ * Test hooks of the pbfmm library.  They are not part of the solver's
+ * interface (include/pbfmm.h): the library's own tests use them to reach
+ * failure paths that a healthy GPU never takes, without faulting or hanging
+ * the GPU.  All of them act process-wide (every context, every thread).
+ */
+#ifndef PBFMM_TESTING_H
+#define PBFMM_TESTING_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Number of device allocations the library has made so far (every buffer
+ * of trees, meshes, operators, results and per-call workspace; not the
+ * context's 4-byte error flag nor the scratch array of
+ * pb_solvation_energy_noalloc, which is static). */
+int64_t pbfmm_test_alloc_count(void);
+
+/* Make the nth device allocation from now (nth >= 1) fail as a failed
+ * cudaMallocAsync would: the call that needs it returns PB_ENOMEM and
+ * releases whatever it had allocated.  nth <= 0 switches the injection
+ * off.  The injection fires once. */
+void pbfmm_test_fail_alloc(int64_t nth);
+
+/* Bytes currently allocated (not cached) from the default stream-ordered
+ * memory pool of CUDA device `device`, from which the library takes all its
+ * buffers; -1 if the query fails.  Work queued on the library's streams
+ * should be synchronised first. */
+int64_t pbfmm_test_pool_used(int device);
+
+/* Cycle limit of the bounded mbarrier waits in the tensor-core box-operator
+ * kernel (M2L, M2M, L2L and the check -> equivalent solves; default 2e9
+ * cycles, about one second).  A small limit makes waits give up: the CTA
+ * then stops its roles, lets its issued MMAs and copies finish, frees its
+ * tensor memory and reports PB_ETIMEOUT through the next synchronising call
+ * (pb_sync).  cycles <= 0 restores the default.  Read at kernel launch, so
+ * a CUDA graph captured meanwhile keeps the value it was captured with. */
+void pbfmm_test_wait_limit(int64_t cycles);
+
+/* D = Q Op^T for one operator through the tensor-core box-operator kernel
+ * (host buffers: Q [nrows][npad], Op [npad][npad], D [nrows][npad]; npad in
+ * {32, 64, 128, 160}).  PB_OK, PB_EINVAL or PB_ETIMEOUT. */
+int pbfmm_selftest_m2l_tc(int nrows, int npad, const float* Q, const float* Op, float* D);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PBFMM_TESTING_H */

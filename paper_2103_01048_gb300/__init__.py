@@ -308,9 +308,19 @@ def pb_solvation_energy(ctx, res, na=None):
     return (e.value, phir) if na else e.value
 
 
-def pb_solvation_energy_noalloc(ctx, res, dG_device):
-    """Energy into a caller-owned device double (e.g. a 1-element float64
-    CUDA tensor) without device allocation; asynchronous on the context stream."""
+def pb_solvation_energy_noalloc(ctx, res, dG_device, device=None):
+    """Energy into a caller-owned device double without any device
+    allocation; asynchronous on the context stream.  dG_device must be a
+    CUDA torch tensor of dtype float64 with at least one element on the
+    context's device (`device`, default the current CUDA device)."""
+    if not (hasattr(dG_device, "is_cuda") and dG_device.is_cuda):
+        raise ValueError("dG_device must be a CUDA tensor")
+    import torch
+    if dG_device.dtype != torch.float64 or dG_device.numel() < 1:
+        raise ValueError("dG_device must be float64 with at least one element")
+    want = torch.cuda.current_device() if device is None else int(device)
+    if dG_device.device.index != want:
+        raise ValueError(f"dG_device is on cuda:{dG_device.device.index}, the context on cuda:{want}")
     _check(_lib.pb_solvation_energy_noalloc(ctx, res, ptr(dG_device)), ctx)
 
 
@@ -354,9 +364,37 @@ def pb_tune_ncrit(ctx, xyz, p, candidates):
     return best.value, ms.value
 
 
-# internal self-test hook of the tensor-core M2L kernel (not part of the ABI)
+# test hooks (include/pbfmm_testing.h; not part of the solver's interface)
 _lib.pbfmm_selftest_m2l_tc.argtypes = [ctypes.c_int, ctypes.c_int, _P, _P, _P]
 _lib.pbfmm_selftest_m2l_tc.restype = ctypes.c_int
+_lib.pbfmm_test_alloc_count.argtypes = []
+_lib.pbfmm_test_alloc_count.restype = _I64
+_lib.pbfmm_test_fail_alloc.argtypes = [_I64]
+_lib.pbfmm_test_fail_alloc.restype = None
+_lib.pbfmm_test_wait_limit.argtypes = [_I64]
+_lib.pbfmm_test_wait_limit.restype = None
+_lib.pbfmm_test_pool_used.argtypes = [ctypes.c_int]
+_lib.pbfmm_test_pool_used.restype = _I64
+
+
+def _test_pool_used(device=0):
+    """Bytes in use (not cached) in the device's default stream-ordered pool."""
+    return int(_lib.pbfmm_test_pool_used(int(device)))
+
+
+def _test_alloc_count():
+    """Device allocations the library has made so far."""
+    return int(_lib.pbfmm_test_alloc_count())
+
+
+def _test_fail_alloc(nth):
+    """Make the nth device allocation from now fail with PB_ENOMEM (0: off)."""
+    _lib.pbfmm_test_fail_alloc(int(nth))
+
+
+def _test_wait_limit(cycles):
+    """Cycle limit of the tensor-core kernel's bounded waits (<= 0: default)."""
+    _lib.pbfmm_test_wait_limit(int(cycles))
 
 
 def _selftest_m2l_tc(Q, Op):
@@ -368,3 +406,22 @@ def _selftest_m2l_tc(Q, Op):
     if rc != PB_OK:
         raise PBError(rc, "tensor-core M2L self-test failed")
     return D
+
+
+# arithmetic-pipe microbenchmarks (include/pbfmm_peaks.h)
+_lib.pbfmm_measure_peaks.argtypes = [ctypes.c_int, _P]
+_lib.pbfmm_measure_peaks.restype = ctypes.c_int
+PEAK_KEYS = ("fp32_fma_tflops", "mufu_rsqrt_tops", "mufu_ex2_tops", "fp64_fma_tflops", "tf32_tc_tflops",
+             "bf16_tc_tflops")
+
+
+def measure_peaks(device=0):
+    """Measured rates of the FP32 FMA pipe, the MUFU rsqrt and ex2 units, FP64
+    FMA and the tcgen05 TF32 / BF16 tensor cores on `device` (dict, units in
+    the key names: TFLOP/s or 10^12 results/s)."""
+    out = np.zeros(6)
+    rc = _lib.pbfmm_measure_peaks(int(device), ptr(out))
+    if rc != PB_OK:
+        raise PBError(rc, "peak microbenchmarks failed")
+    return dict(zip(PEAK_KEYS, (float(v) for v in out)))
+

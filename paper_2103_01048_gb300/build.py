@@ -36,7 +36,8 @@ def build(verbose=False, force=False):
         f.write(arch)
     nvcc = os.environ.get("NVCC", "nvcc")
     headers = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cuh", ".h"))]
-    headers.append(os.path.join(ROOT, "include", "pbfmm.h"))
+    inc = os.path.join(ROOT, "include")
+    headers += [os.path.join(inc, f) for f in os.listdir(inc) if f.endswith(".h")]
     objs, jobs = [], []
     for s in sources():
         src = os.path.join(CSRC, s)

@@ -50,6 +50,10 @@ pb_result* make_result(pb_ctx* ctx, pb_mesh* M, const double* atoms, const doubl
 }
 
 thread_local long long g_launch_count = 0;
+std::atomic<long long> g_alloc_count{0};
+std::atomic<long long> g_alloc_fail_at{0};
+constexpr long long kDefaultWaitLimit = 2000000000LL;
+std::atomic<long long> g_wait_limit{kDefaultWaitLimit};
 
 void profile_collect(pb_ctx* ctx) {
     for (auto& e : ctx->pending) {
@@ -541,8 +545,16 @@ int pb_solve(pb_ctx* ctx, pb_mesh* M, const double* atoms, const double* q, int6
     (void)st;
     pb_result* R = make_result(ctx, M, atoms, q, na, eps_in, eps_out, kappa, precision);
     *out = R;
-    status = solve(M, R, tol, max_iter);
-    check_device_error(ctx);
+    try {
+        status = solve(M, R, tol, max_iter);
+        check_device_error(ctx);
+    } catch (...) {
+        // no result object survives a failed call (PB_ENOCONV keeps its result)
+        cudaStreamSynchronize(ctx->stream);
+        delete R;
+        *out = nullptr;
+        throw;
+    }
     if (status != PB_OK) {
         ctx->last_error = "pb_solve: GMRES did not reach tol within max_iter";
         return status;
@@ -594,10 +606,19 @@ int pb_solve_batch(pb_ctx* ctx, pb_mesh* const* meshes, int nsys, const double* 
             PB_REQUIRE(meshes[t] != meshes[s], PB_EINVAL, "pb_solve_batch: meshes must be distinct");
     }
     PB_CUDA(cudaSetDevice(ctx->device));
-    for (int s = 0; s < nsys; ++s)
-        out[s] = make_result(ctx, meshes[s], atoms[s], charges[s], na[s], eps_in, eps_out, kappa, precision);
-    solve_batch(ctx, meshes, nsys, out, tol, max_iter, status);
-    check_device_error(ctx);
+    try {
+        for (int s = 0; s < nsys; ++s)
+            out[s] = make_result(ctx, meshes[s], atoms[s], charges[s], na[s], eps_in, eps_out, kappa, precision);
+        solve_batch(ctx, meshes, nsys, out, tol, max_iter, status);
+        check_device_error(ctx);
+    } catch (...) {
+        cudaStreamSynchronize(ctx->stream);
+        for (int s = 0; s < nsys; ++s) {
+            delete out[s];
+            out[s] = nullptr;
+        }
+        throw;
+    }
     for (int s = 0; s < nsys; ++s)
         if (status[s] != PB_OK) rc = PB_ENOCONV;
     if (rc != PB_OK) {
@@ -635,5 +656,24 @@ int pb_energy_grad(pb_ctx* ctx, pb_result* R, double tol, int max_iter, double* 
     }
     PB_API_END(ctx)
 }
+
+// ---------------------------------------------------------------------------
+// test hooks (include/pbfmm_testing.h)
+// ---------------------------------------------------------------------------
+int64_t pbfmm_test_alloc_count(void) { return g_alloc_count.load(); }
+
+void pbfmm_test_fail_alloc(int64_t nth) {
+    g_alloc_fail_at.store(nth > 0 ? g_alloc_count.load() + nth : 0);
+}
+
+int64_t pbfmm_test_pool_used(int device) {
+    cudaMemPool_t pool;
+    if (cudaDeviceGetDefaultMemPool(&pool, device) != cudaSuccess) return -1;
+    uint64_t used = 0;
+    if (cudaMemPoolGetAttribute(pool, cudaMemPoolAttrUsedMemCurrent, &used) != cudaSuccess) return -1;
+    return (int64_t)used;
+}
+
+void pbfmm_test_wait_limit(int64_t cycles) { g_wait_limit.store(cycles > 0 ? cycles : kDefaultWaitLimit); }
 
 }  // extern "C"

@@ -7,6 +7,7 @@
 #include <cstdio>
 #include <cstring>
 #include <stdexcept>
+#include <atomic>
 
 #include "../../include/pbfmm.h"
 #include <nvtx3/nvToolsExt.h>
@@ -49,6 +50,20 @@ extern thread_local long long g_launch_count;
         if (!(cond)) throw ::pbfmm::Error(code, msg);                              \
     } while (0)
 
+// Device allocations made through DBuf (all of the library's device memory
+// except the context's error flag), counted for tests; and an injected
+// failure: when g_alloc_fail_at > 0, the allocation with that count number
+// throws PB_ENOMEM as a failed cudaMallocAsync would (pbfmm_testing.h).
+extern std::atomic<long long> g_alloc_count;
+extern std::atomic<long long> g_alloc_fail_at;
+inline void count_alloc() {
+    const long long k = ++g_alloc_count;
+    if (k == g_alloc_fail_at.load()) throw Error(PB_ENOMEM, "device allocation failed (injected by a test)");
+}
+// Cycle limit of the tensor-core kernels' bounded waits (about 1 s at the
+// boost clock); tests shorten it to make a wait give up (pbfmm_testing.h).
+extern std::atomic<long long> g_wait_limit;
+
 // Owning device buffer (stream-ordered allocations on the context stream).
 template <typename T>
 struct DBuf {
@@ -67,19 +82,20 @@ struct DBuf {
     void alloc(size_t count, cudaStream_t stream) {
         release();
         s = stream;
-        n = count;
         if (count) {
+            count_alloc();
             cudaError_t e = cudaMallocAsync((void**)&p, count * sizeof(T), stream);
             if (e != cudaSuccess) {
                 p = nullptr;
-                n = 0;
                 throw Error(PB_ENOMEM, std::string("device allocation failed: ") + cudaGetErrorString(e));
             }
+            n = count;
         }
     }
     // grow keeping contents
     void grow(size_t count, cudaStream_t stream) {
         if (count <= n) return;
+        count_alloc();
         T* q = nullptr;
         cudaError_t e = cudaMallocAsync((void**)&q, count * sizeof(T), stream);
         if (e != cudaSuccess) throw Error(PB_ENOMEM, "device allocation failed");

@@ -20,6 +20,7 @@
 // Every wait is bounded (~1 s); on a timeout the kernel records an error
 // code, drains its own MMAs, frees TMEM and returns.
 #include "fmm.cuh"
+#include "tc_ptx.cuh"
 #include <cub/cub.cuh>
 #include <algorithm>
 
@@ -29,116 +30,6 @@ constexpr int kTcRows = 128;           // pairs per row tile (MMA M)
 constexpr int kTcItemPairs = 2048;     // pairs per M2L work item (one operator load each)
 constexpr int kTcSmallItemPairs = 512; // M2M / L2L / check->equivalent items: fewer pairs per operator, more CTAs
 constexpr int kTcMaxNpad = 160;        // resident operator half must fit in shared memory
-
-// ---------------------------------------------------------------------------
-// PTX helpers
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}\n"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-// bounded wait (about one second at the boost clock); false on timeout
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
-    long long t0 = clock64();
-    while (!mbar_try_wait(bar, parity)) {
-        if (clock64() - t0 > 2000000000LL) return false;
-    }
-    return true;
-}
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-                 : "memory");
-}
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_u32(dst)),
-        "l"(src), "r"(bytes), "r"(smem_u32(bar))
-        : "memory");
-}
-__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
-__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-
-__device__ __forceinline__ void tmem_alloc(uint32_t* slot, uint32_t ncols) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(slot)),
-                 "r"(ncols)
-                 : "memory");
-}
-__device__ __forceinline__ void tmem_relinquish() {
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
-}
-__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
-}
-__device__ __forceinline__ void mma_tf32(uint32_t dt, uint64_t ad, uint64_t bd, uint32_t idesc, uint32_t acc) {
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(dt),
-        "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
-        : "memory");
-}
-__device__ __forceinline__ void mma_commit(uint64_t* bar) {
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
-                 : "memory");
-}
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
-    uint32_t r[16];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
-}
-__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
-    uint32_t r[8];
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
-                 : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
-}
-__device__ __forceinline__ void red_add_v4(float* p, float a, float b, float c, float d) {
-    asm volatile("red.global.add.v4.f32 [%0], {%1,%2,%3,%4};" ::"l"(p), "f"(a), "f"(b), "f"(c), "f"(d) : "memory");
-}
-
-// UMMA shared-memory descriptor: K-major, 128B swizzle, 8-row atoms of 1024 B
-__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
-    uint64_t d = 0;
-    d |= (uint64_t)((saddr >> 4) & 0x3FFF);      // start address
-    d |= (uint64_t)1 << 16;                      // leading byte offset (unused with swizzle)
-    d |= (uint64_t)(1024 >> 4) << 32;            // stride byte offset: next 8-row atom
-    d |= (uint64_t)1 << 46;                      // descriptor version
-    d |= (uint64_t)2 << 61;                      // 128B swizzle
-    return d;
-}
-// instruction descriptor: D f32, A/B tf32, K-major both, M = 128, N = n
-__host__ __device__ constexpr uint32_t idesc_tf32(int n) {
-    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
-}
-
-// byte offset of element (row, k) of a [rows][32] fp32 K-block in the 128B-swizzled layout
-__host__ __device__ __forceinline__ uint32_t sw128_off(int row, int k) {
-    int c = k >> 2, w = k & 3;
-    return (uint32_t)((row >> 3) * 1024 + (row & 7) * 128 + ((c ^ (row & 7)) << 4) + (w << 2));
-}
 
 // TF32 part of x, rounded to nearest (ties away from zero); x - hi is exact in FP32
 __device__ __forceinline__ float tf32_hi(float x) {
@@ -364,16 +255,14 @@ struct TcSmem {
     int failed;
 };
 
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
 // bounded wait that gives up as soon as another role of the CTA has failed;
 // a timeout marks the CTA failed
-__device__ __forceinline__ bool mbar_wait_cta(uint64_t* bar, uint32_t parity, volatile int* failed) {
+__device__ __forceinline__ bool mbar_wait_cta(uint64_t* bar, uint32_t parity, volatile int* failed,
+                                              long long limit) {
     long long t0 = clock64();
     while (!mbar_try_wait(bar, parity)) {
         if (*failed) return false;
-        if (clock64() - t0 > 2000000000LL) {
+        if (clock64() - t0 > limit) {
             *failed = 1;
             return false;
         }
@@ -388,6 +277,7 @@ struct TcSets {
     const float* ops[2];
     const float* X[2];
     float* Y[2];
+    long long wait_limit;    // cycles a role waits on a barrier before giving up (set at launch)
 };
 
 template <int NPAD>
@@ -402,6 +292,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(const int4* __restrict
     const float* __restrict__ ops = sets.ops[blockIdx.z];
     const float* __restrict__ Qu = sets.X[blockIdx.z];
     float* __restrict__ Qd = sets.Y[blockIdx.z];
+    const long long wl = sets.wait_limit;
     constexpr int NH = NPAD / 2;                     // output rows of this CTA (MMA N)
     constexpr int KB = NPAD / 32;                    // K blocks of 32 tf32 (128 B)
     constexpr uint32_t B_SPLIT = KB * NH * 128;      // bytes of one of hi / lo
@@ -479,7 +370,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(const int4* __restrict
 #pragma unroll
             for (int kb = 0; kb < KB; ++kb, ++g) {
                 const int s = g % kTcStages, n = g / kTcStages;
-                if (n > 0 && !mbar_wait_cta(&S->empty[s], (n - 1) & 1, failed)) goto prod_done;
+                if (n > 0 && !mbar_wait_cta(&S->empty[s], (n - 1) & 1, failed, wl)) goto prod_done;
                 uint8_t* aHi = sA + (size_t)s * 2 * A_SPLIT;
                 uint8_t* aLo = aHi + A_SPLIT;
 #pragma unroll
@@ -512,7 +403,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(const int4* __restrict
             const int a = tile & 1, u = tile >> 1;
             const int r = tile * kTcRows + erow;
             const int t = r < npairs ? ptgt[first + r] : -1;
-            bool ok = mbar_wait_cta(&S->accf[a], u & 1, failed);
+            bool ok = mbar_wait_cta(&S->accf[a], u & 1, failed, wl);
             if (!__all_sync(0xffffffffu, ok)) break;
             tc_fence_after();
             float (*buf)[kTcEpiStride] = S->epi[q];
@@ -544,14 +435,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(const int4* __restrict
             uint64_t* last = nullptr;      // barrier of the last commit, and its phase parity
             uint32_t last_par = 0;
             int g = 0;
-            bool ok = mbar_wait_cta(&S->barB, 0, failed);
+            bool ok = mbar_wait_cta(&S->barB, 0, failed, wl);
             for (int tile = 0; ok && tile < ntile; ++tile) {
                 const int a = tile & 1, u = tile >> 1;
-                if (u > 0 && !(ok = mbar_wait_cta(&S->acce[a], (u - 1) & 1, failed))) break;
+                if (u > 0 && !(ok = mbar_wait_cta(&S->acce[a], (u - 1) & 1, failed, wl))) break;
                 const uint32_t dacc = taddr + a * ACOLS;
                 for (int kb = 0; kb < KB; ++kb, ++g) {
                     const int s = g % kTcStages, n = g / kTcStages;
-                    if (!(ok = mbar_wait_cta(&S->full[s], n & 1, failed))) break;
+                    if (!(ok = mbar_wait_cta(&S->full[s], n & 1, failed, wl))) break;
                     tc_fence_after();
                     const uint32_t aH = smem_u32(sA + (size_t)s * 2 * A_SPLIT), aL = aH + A_SPLIT;
                     const uint32_t bH = smem_u32(sB) + kb * NH * 128, bL = bH + B_SPLIT;
@@ -608,7 +499,9 @@ static void launch_tc_items(const int4* items, int nitems, const int* tgt, const
         attr_set[dev] = true;
     }
     dim3 grid(nitems, 2, nsets);
-    k_m2l_tc<NPAD><<<grid, kTcThreads, sm, st>>>(items, tgt, src, sets, err);
+    TcSets s2 = sets;
+    s2.wait_limit = g_wait_limit.load();
+    k_m2l_tc<NPAD><<<grid, kTcThreads, sm, st>>>(items, tgt, src, s2, err);
     PB_CHECK_LAUNCH();
 }
 

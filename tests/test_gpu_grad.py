@@ -71,7 +71,7 @@ def test_autograd_function(pb, ctx, system):
         pb.pb_result_destroy(res)
     finally:
         pb.pb_mesh_destroy(mesh)
-    assert abs(float(e) - e2) < 1e-6 * abs(e2)
+    assert abs(float(e.detach()) - e2) < 1e-6 * abs(e2)
     assert np.allclose(qt.grad.numpy(), gq, rtol=1e-5, atol=1e-9)
     assert np.allclose(xt.grad.numpy(), gx, rtol=1e-5, atol=1e-9)
     assert np.abs(qt.grad.numpy() - gq_ref).max() < 1e-4 * np.abs(gq_ref).max()

@@ -191,3 +191,15 @@ def test_regular_rule_exact_degree(nq, degree):
         for a in range(degree + 1):
             for b in range(degree + 1 - a):
                 assert abs((W * Lp[:, 1] ** a * Lp[:, 2] ** b).sum() - _monomial_exact(a, b)) < 1e-13
+
+
+def test_born_ion_golden_file():
+    """The stored dense-LU energy of the 5,120-triangle Born ion (written by
+    tests/golden/make_born_ion.py, oracle only) lies within the P0
+    discretisation error of the Born closed form: the 1/N convergence pinned
+    above gives about 7e-4 relative at this size."""
+    g = json.load(open(os.path.join(HERE, "golden", "born_ion_5120.json")))
+    born = cf.born_energy(1.0, 2.0, g["eps_in"], g["eps_out"], g["kappa"])
+    assert abs(g["born_closed_form_kcal_mol"] - born) < 1e-12
+    rel = abs(g["energy_kcal_mol"] - born) / abs(born)
+    assert 1e-4 < rel < 2e-3
