@@ -2,6 +2,7 @@
 // internal exceptions into a status code and a message on the context.
 #include "bem.cuh"
 #include <new>
+#include <memory>
 
 namespace pbfmm {
 void build_tree(fmm_tree* T, const float* src, const float* tgt);
@@ -25,7 +26,8 @@ void tune_ncrit(pb_ctx* ctx, const float* xyz_dev, long long n, int p, const int
 // A result object for the charges of one system (atoms as (x, y, z, q) on the device).
 pb_result* make_result(pb_ctx* ctx, pb_mesh* M, const double* atoms, const double* q, int64_t na, double eps_in,
                        double eps_out, double kappa, int precision) {
-    auto* R = new pb_result();
+    std::unique_ptr<pb_result> owner(new pb_result());
+    pb_result* R = owner.get();
     R->mesh = M;
     R->nt = M->nt;
     R->na = na;
@@ -36,17 +38,14 @@ pb_result* make_result(pb_ctx* ctx, pb_mesh* M, const double* atoms, const doubl
     std::vector<double> a4(4 * na), ha(3 * na), hq(na);
     cudaError_t e1 = cudaMemcpy(ha.data(), atoms, 3 * na * sizeof(double), cudaMemcpyDefault);
     cudaError_t e2 = cudaMemcpy(hq.data(), q, na * sizeof(double), cudaMemcpyDefault);
-    if (e1 != cudaSuccess || e2 != cudaSuccess) {
-        delete R;
-        throw Error(PB_ECUDA, "copying atoms/charges failed");
-    }
+    if (e1 != cudaSuccess || e2 != cudaSuccess) throw Error(PB_ECUDA, "copying atoms/charges failed");
     for (int64_t k = 0; k < na; ++k) {
         a4[4 * k] = ha[3 * k]; a4[4 * k + 1] = ha[3 * k + 1]; a4[4 * k + 2] = ha[3 * k + 2]; a4[4 * k + 3] = hq[k];
     }
     R->atoms.alloc(4 * na, ctx->stream);
     PB_CUDA(cudaMemcpyAsync(R->atoms.p, a4.data(), 4 * na * sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
     PB_CUDA(cudaStreamSynchronize(ctx->stream));
-    return R;
+    return owner.release();
 }
 
 thread_local long long g_launch_count = 0;
