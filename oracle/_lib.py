@@ -40,5 +40,10 @@ def lib():
         L.or_regular_rule.restype = ctypes.c_int
         L.or_triangle_rule.argtypes = [ctypes.c_int, P, P, P]
         L.or_triangle_rule.restype = None
+        L.or_tri_lin.argtypes = [P, P, P, P, P, P]
+        L.or_tri_lin.restype = None
+        L.or_assemble_p1.argtypes = [ctypes.c_long, P, ctypes.c_long, P, ctypes.c_int, ctypes.c_double,
+                                     ctypes.c_int, ctypes.c_int, ctypes.c_int, P, P, P, P, P, P]
+        L.or_assemble_p1.restype = ctypes.c_int
         _lib = L
     return _lib

@@ -23,6 +23,11 @@
  *                        int g phi_j), regular product rule for disjoint
  *                        triangle pairs, semi-analytic rule for identical or
  *                        vertex-sharing pairs.
+ *   or_tri_lin           linear-density versions of or_tri_sl / or_tri_dl
+ *                        (one value per barycentric coordinate).
+ *   or_assemble_p1       dense P1 Galerkin matrices of V, K and the
+ *                        hypersingular W (Eq. adj_hyp) of both kernels for
+ *                        the derivative formulations (Eq. juffer, Eq. lu).
  */
 #include <math.h>
 #include <stdlib.h>
@@ -454,3 +459,286 @@ int or_assemble_p0(long nv, const double *verts, long nt, const int *tris,
 /* Triangle rule export so the Python side can build points with the same rule. */
 int or_regular_rule(int nq, double *L, double *W) { return regular_rule(nq, L, W); }
 void or_triangle_rule(int n, double *l1, double *l2, double *w) { triangle_rule(n, l1, l2, w); }
+
+/* ------------------------------------------------------------------ */
+/* P1 (continuous piecewise-linear) Galerkin assembly                   */
+/* ------------------------------------------------------------------ */
+
+/*
+ * Linear-density inner integrals over the flat triangle T = (v0, v1, v2)
+ * at the point x, for the three barycentric coordinates lambda_b of T:
+ *   sl3[b] = int_T lambda_b(y) / |x - y| dA_y
+ *   dl3[b] = int_T lambda_b(y) (x - y).n / |x - y|^3 dA_y
+ * Written around the projection p of x on T's plane (height h = (x-v0).n):
+ * lambda_b(y) = lambda_b(p) + grad lambda_b . (y - p), so each integral is
+ * lambda_b(p) times the uniform-density one (or_tri_sl, or_tri_dl) plus
+ * grad lambda_b dotted with a vector moment, turned into edge integrals by
+ * the divergence theorem in the plane (R = |x - y|, m_e the outward in-plane
+ * normal of edge e):
+ *   int_T (y - p)/R dA     =  sum_e m_e int_e R ds
+ *   int_T (y - p) h/R^3 dA = -h sum_e m_e int_e 1/R ds
+ * with int R ds = (s R + R0^2 ln(s + R))/2 and int 1/R ds = ln(s + R)
+ * along the edge (s the coordinate along it from the foot of p, R0 the
+ * distance of x from the edge line).
+ */
+void or_tri_lin(const double *x, const double *v0, const double *v1, const double *v2, double *sl3, double *dl3)
+{
+    double e1[3], e2[3], n[3], t[3];
+    sub3(v1, v0, e1); sub3(v2, v0, e2); cross3(e1, e2, n);
+    const double twoA = norm3(n);
+    n[0] /= twoA; n[1] /= twoA; n[2] /= twoA;
+    sub3(x, v0, t);
+    const double h = dot3(t, n);
+    const double p[3] = { x[0] - h * n[0], x[1] - h * n[1], x[2] - h * n[2] };
+    const double *V[3] = { v0, v1, v2 };
+    const double scale = norm3(e1) + norm3(e2);
+    /* barycentric coordinates of p and gradients of lambda_b (in-plane) */
+    double lam[3], grad[3][3];
+    for (int b = 0; b < 3; ++b) {
+        const double *a = V[(b + 1) % 3], *c = V[(b + 2) % 3];
+        double ac[3], ap[3], cr[3];
+        sub3(c, a, ac); sub3(p, a, ap);
+        cross3(ac, ap, cr);
+        lam[b] = dot3(cr, n) / twoA;           /* signed area of (a, c, p) / area of T */
+        cross3(n, ac, grad[b]);                /* n x (v_{b+2} - v_{b+1}) / (2A) */
+        for (int k = 0; k < 3; ++k) grad[b][k] /= twoA;
+    }
+    /* vector moments I1 = int (y - p)/R dA, J1 = int (y - p)/R^3 dA */
+    double I1[3] = { 0, 0, 0 }, J1[3] = { 0, 0, 0 };
+    for (int k = 0; k < 3; ++k) {
+        const double *a = V[k], *b = V[(k + 1) % 3];
+        double L[3], l[3], m[3], ap[3], bp[3], xa[3], xb[3];
+        sub3(b, a, L);
+        const double len = norm3(L);
+        l[0] = L[0] / len; l[1] = L[1] / len; l[2] = L[2] / len;
+        cross3(l, n, m);                        /* outward in-plane edge normal */
+        sub3(a, p, ap); sub3(b, p, bp);
+        const double P0 = dot3(ap, m);
+        const double sm = dot3(ap, l), sp = dot3(bp, l);
+        sub3(x, a, xa); sub3(x, b, xb);
+        const double Rm = norm3(xa), Rp = norm3(xb);
+        const double R02 = P0 * P0 + h * h;
+        double intR = 0.5 * (sp * Rp - sm * Rm);
+        double intInvR = 0.0;
+        if (R02 > 1e-28 * scale * scale) {
+            const double lg = log(r_plus_s(Rp, sp, R02) / r_plus_s(Rm, sm, R02));
+            intR += 0.5 * R02 * lg;
+            intInvR = lg;
+        }
+        for (int c = 0; c < 3; ++c) {
+            I1[c] += m[c] * intR;
+            J1[c] += m[c] * intInvR;
+        }
+    }
+    const double sl0 = or_tri_sl(x, v0, v1, v2);
+    const double dl0 = (fabs(h) > 0.0) ? or_tri_dl(x, v0, v1, v2) : 0.0;
+    for (int b = 0; b < 3; ++b) {
+        sl3[b] = lam[b] * sl0 + dot3(grad[b], I1);
+        dl3[b] = lam[b] * dl0 - h * dot3(grad[b], J1);
+    }
+}
+
+/* surface curl of the hat function of local vertex a on triangle T:
+   n x grad lambda_a = (v_{a+1} - v_{a+2}) / (2 |T|) */
+static void hat_curl(const tri_t *T, double area, int a, double *c)
+{
+    const double *p = T->v[(a + 1) % 3], *q = T->v[(a + 2) % 3];
+    for (int k = 0; k < 3; ++k) c[k] = (p[k] - q[k]) / (2.0 * area);
+}
+
+/* inner linear-density integrals of the four kernels at x over Tj:
+   out[op][b], op = V_L, K_L, V_Y, K_Y (including 1/(4 pi)) */
+static void inner_lin(const double *x, const tri_t *Tj, const double *nj, double areaj, int identical,
+                      double kappa, int ni, const double *li1, const double *li2, const double *wi,
+                      double out[4][3])
+{
+    const double k4pi = 1.0 / (4.0 * OR_PI);
+    double sl[3], dl[3];
+    or_tri_lin(x, Tj->v[0], Tj->v[1], Tj->v[2], sl, dl);
+    if (identical) dl[0] = dl[1] = dl[2] = 0.0;
+    double rs[3] = { 0, 0, 0 }, rd[3] = { 0, 0, 0 };
+    for (int k = 0; k < ni; ++k) {
+        double y[3], rv[3];
+        tri_point(Tj, li1[k], li2[k], y);
+        sub3(x, y, rv);
+        const double r = norm3(rv);
+        const double s = kappa * r;
+        double fsl, fdl;
+        if (r < 1e-300) {
+            fsl = -kappa; fdl = 0.0;
+        } else {
+            fsl = expm1(-s) / r;
+            fdl = dot3(rv, nj) * (expm1(-s) + s * exp(-s)) / (r * r * r);
+        }
+        const double lb[3] = { 1.0 - li1[k] - li2[k], li1[k], li2[k] };
+        for (int b = 0; b < 3; ++b) {
+            rs[b] += wi[k] * lb[b] * fsl;
+            rd[b] += wi[k] * lb[b] * fdl;
+        }
+    }
+    for (int b = 0; b < 3; ++b) {
+        out[0][b] = k4pi * sl[b];
+        out[1][b] = k4pi * dl[b];
+        out[2][b] = k4pi * (sl[b] + areaj * rs[b]);
+        out[3][b] = identical ? 0.0 : k4pi * (dl[b] + areaj * rd[b]);
+    }
+}
+
+typedef struct {
+    const tri_t *Tj; const double *nj; double areaj; int identical; double kappa;
+    int no; const double *lo1, *lo2, *wo;
+    int ni; const double *li1, *li2, *wi;
+    double tol;
+} outer_lin_ctx;
+
+/* acc[op][a][b] += int_S lambda_a^{Ti}(x) inner_lin(x)[op][b]; S a piece of
+   Ti (graded toward the edges of Tj), Ti's barycentric coordinates of x
+   from (Ti, S) */
+static void outer_graded_lin(const outer_lin_ctx *C, const tri_t *Ti, const tri_t *S, int depth,
+                             double acc[4][3][3])
+{
+    if (depth > 0 && touches_edges(S, C->Tj, C->tol)) {
+        tri_t ch[4];
+        split4(S, ch);
+        for (int i = 0; i < 4; ++i) outer_graded_lin(C, Ti, &ch[i], depth - 1, acc);
+        return;
+    }
+    double ni_[3];
+    const double as = tri_area_normal(S, ni_);
+    const double ai = tri_area_normal(Ti, ni_);
+    for (int k = 0; k < C->no; ++k) {
+        double x[3], in[4][3];
+        tri_point(S, C->lo1[k], C->lo2[k], x);
+        inner_lin(x, C->Tj, C->nj, C->areaj, C->identical, C->kappa, C->ni, C->li1, C->li2, C->wi, in);
+        /* barycentric coordinates of x in Ti (areas of the sub-triangles) */
+        double la[3];
+        for (int a = 0; a < 3; ++a) {
+            double u[3], w[3], cr[3];
+            sub3(Ti->v[(a + 1) % 3], x, u); sub3(Ti->v[(a + 2) % 3], x, w);
+            cross3(u, w, cr);
+            la[a] = dot3(cr, ni_) / (2.0 * ai);
+        }
+        const double wgt = C->wo[k] * as;
+        for (int op = 0; op < 4; ++op)
+            for (int a = 0; a < 3; ++a)
+                for (int b = 0; b < 3; ++b) acc[op][a][b] += wgt * la[a] * in[op][b];
+    }
+}
+
+/*
+ * Dense P1 Galerkin matrices [nv][nv], row = test vertex, column = trial
+ * vertex (hat functions phi_i):
+ *   VL_ij = int int phi_i(x) g_L phi_j(y),  KL_ij = ... dg_L/dn_y ...,
+ *   VY, KY the Yukawa pair,
+ *   WL_ij = int int g_L curl phi_i(x) . curl phi_j(y)
+ *   WY_ij = int int g_Y [curl phi_i . curl phi_j + kappa^2 (n_x.n_y) phi_i phi_j]
+ * (the hypersingular operators of Eq. adj_hyp in the integrated-by-parts
+ * form that holds for continuous trial and test functions on a closed
+ * surface; curl phi = n x grad phi is constant on each triangle).  Triangle
+ * pairs without a shared vertex use the product of the nq-point regular rule;
+ * identical or vertex-sharing pairs the graded outer rule of the analytic
+ * linear-density inner integrals (as or_assemble_p0).  One row per thread:
+ * every (Ti, Tj) block is computed once for each vertex of Ti.
+ */
+int or_assemble_p1(long nv, const double *verts, long nt, const int *tris,
+                   int nq, double kappa, int L_outer, int n_outer, int n_inner,
+                   double *VL, double *KL, double *VY, double *KY, double *WL, double *WY)
+{
+    double RL[6 * 3], RW[6];
+    if (regular_rule(nq, RL, RW) != 0) return -1;
+    tri_t *T = malloc(sizeof(tri_t) * nt);
+    double *N = malloc(sizeof(double) * 3 * nt), *A = malloc(sizeof(double) * nt);
+    double *Q = malloc(sizeof(double) * 3 * nq * nt);
+    for (long i = 0; i < nt; ++i) {
+        for (int a = 0; a < 3; ++a)
+            for (int c = 0; c < 3; ++c) T[i].v[a][c] = verts[3 * tris[3 * i + a] + c];
+        A[i] = tri_area_normal(&T[i], N + 3 * i);
+        for (int k = 0; k < nq; ++k)
+            for (int c = 0; c < 3; ++c)
+                Q[(i * nq + k) * 3 + c] = RL[3 * k] * T[i].v[0][c] + RL[3 * k + 1] * T[i].v[1][c]
+                                          + RL[3 * k + 2] * T[i].v[2][c];
+    }
+    /* vertex -> incident triangles */
+    long *vcnt = calloc((size_t)nv + 1, sizeof(long));
+    for (long i = 0; i < nt; ++i)
+        for (int a = 0; a < 3; ++a) vcnt[tris[3 * i + a] + 1]++;
+    for (long v = 0; v < nv; ++v) vcnt[v + 1] += vcnt[v];
+    long *vtri = malloc(sizeof(long) * 3 * (size_t)nt), *vfill = calloc((size_t)nv, sizeof(long));
+    for (long i = 0; i < nt; ++i)
+        for (int a = 0; a < 3; ++a) {
+            const long v = tris[3 * i + a];
+            vtri[vcnt[v] + vfill[v]++] = i;
+        }
+    const int no = n_outer * n_outer, ni = n_inner * n_inner;
+    double *lo1 = malloc(sizeof(double) * no), *lo2 = malloc(sizeof(double) * no), *wo = malloc(sizeof(double) * no);
+    double *li1 = malloc(sizeof(double) * ni), *li2 = malloc(sizeof(double) * ni), *wi = malloc(sizeof(double) * ni);
+    triangle_rule(n_outer, lo1, lo2, wo);
+    triangle_rule(n_inner, li1, li2, wi);
+    const double k4pi = 1.0 / (4.0 * OR_PI);
+    memset(VL, 0, sizeof(double) * nv * nv); memset(KL, 0, sizeof(double) * nv * nv);
+    memset(VY, 0, sizeof(double) * nv * nv); memset(KY, 0, sizeof(double) * nv * nv);
+    memset(WL, 0, sizeof(double) * nv * nv); memset(WY, 0, sizeof(double) * nv * nv);
+
+#pragma omp parallel for schedule(dynamic, 2)
+    for (long v = 0; v < nv; ++v) {
+        for (long e = vcnt[v]; e < vcnt[v + 1]; ++e) {
+            const long i = vtri[e];
+            int a = 0;
+            while (tris[3 * i + a] != v) ++a;
+            double ca[3];
+            hat_curl(&T[i], A[i], a, ca);
+            for (long j = 0; j < nt; ++j) {
+                int shared = 0;
+                for (int s = 0; s < 3; ++s)
+                    for (int t = 0; t < 3; ++t)
+                        if (tris[3 * i + s] == tris[3 * j + t]) shared++;
+                double blk[4][3][3];
+                memset(blk, 0, sizeof(blk));
+                if (shared == 0) {
+                    for (int qa = 0; qa < nq; ++qa) {
+                        const double *x = Q + (i * nq + qa) * 3;
+                        for (int qb = 0; qb < nq; ++qb) {
+                            const double *y = Q + (j * nq + qb) * 3;
+                            double rv[3];
+                            sub3(x, y, rv);
+                            const double r = norm3(rv);
+                            const double w = RW[qa] * A[i] * RW[qb] * A[j];
+                            const double rn = dot3(rv, N + 3 * j);
+                            const double ek = exp(-kappa * r);
+                            const double kk[4] = { k4pi / r, k4pi * rn / (r * r * r), k4pi * ek / r,
+                                                   k4pi * ek * (1.0 + kappa * r) * rn / (r * r * r) };
+                            for (int op = 0; op < 4; ++op)
+                                for (int aa = 0; aa < 3; ++aa)
+                                    for (int b = 0; b < 3; ++b)
+                                        blk[op][aa][b] += w * RL[3 * qa + aa] * RL[3 * qb + b] * kk[op];
+                        }
+                    }
+                } else {
+                    outer_lin_ctx C = { &T[j], N + 3 * j, A[j], shared == 3, kappa,
+                                        no, lo1, lo2, wo, ni, li1, li2, wi, 1e-10 * sqrt(A[j]) };
+                    outer_graded_lin(&C, &T[i], &T[i], L_outer, blk);
+                }
+                /* P0 sums of the single layers: the curl-curl term */
+                double vl0 = 0.0, vy0 = 0.0;
+                for (int aa = 0; aa < 3; ++aa)
+                    for (int b = 0; b < 3; ++b) { vl0 += blk[0][aa][b]; vy0 += blk[2][aa][b]; }
+                const double nn = dot3(N + 3 * i, N + 3 * j);
+                for (int b = 0; b < 3; ++b) {
+                    const long col = tris[3 * j + b];
+                    double cb[3];
+                    hat_curl(&T[j], A[j], b, cb);
+                    const double cc = dot3(ca, cb);
+                    VL[v * nv + col] += blk[0][a][b];
+                    KL[v * nv + col] += blk[1][a][b];
+                    VY[v * nv + col] += blk[2][a][b];
+                    KY[v * nv + col] += blk[3][a][b];
+                    WL[v * nv + col] += cc * vl0;
+                    WY[v * nv + col] += cc * vy0 + kappa * kappa * nn * blk[2][a][b];
+                }
+            }
+        }
+    }
+    free(T); free(N); free(A); free(Q); free(vcnt); free(vtri); free(vfill);
+    free(lo1); free(lo2); free(wo); free(li1); free(li2); free(wi);
+    return 0;
+}
