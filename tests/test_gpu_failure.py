@@ -124,21 +124,52 @@ def test_allocation_failure_tree_build(pb, ctx, case):
     assert n_fail >= 10
 
 
-def test_allocation_failure_apply_and_solve(pb, ctx, case):
-    x = case[0]
-    tree = pb.fmm_tree_build(ctx, dev(x), 64)
+def _tree_footprint(pb, ctx, x, case, fail_at):
+    """Pool bytes a fresh tree holds after (optionally) one apply whose
+    allocation `fail_at` fails and then one apply that succeeds; the
+    successful apply's results are checked against the direct sum."""
+    torch.cuda.synchronize()
+    pb.pb_sync(ctx)
+    u0 = pb._test_pool_used(0)
+    tree = pb.fmm_tree_build(ctx, x, 64)
     try:
-        # the first apply builds the operators: fail it at spread-out points
-        for nth in (1, 2, 3, 5, 9, 17, 33, 65):
-            r = _expect_enomem_without_leak(pb, ctx, nth, lambda: paired(pb, ctx, tree, case))
-            if r is not True:
-                break
+        failed = False
+        if fail_at:
+            pb._test_fail_alloc(fail_at)
+            try:
+                paired(pb, ctx, tree, case)
+                pb.pb_sync(ctx)
+            except pb.PBError as e:
+                assert e.code == pb.PB_ENOMEM
+                failed = True
+            finally:
+                pb._test_fail_alloc(0)
         oL, oY = paired(pb, ctx, tree, case)
         pb.pb_sync(ctx)
         assert rel_l2(oL.cpu().numpy(), case[4]) < 1e-5
         assert rel_l2(oY.cpu().numpy(), case[5]) < 1e-5
+        del oL, oY
+        torch.cuda.synchronize()
+        pb.pb_sync(ctx)
+        return pb._test_pool_used(0) - u0, failed
     finally:
         pb.fmm_tree_destroy(tree)
+
+
+def test_allocation_failure_apply_and_solve(pb, ctx, case):
+    x = dev(case[0])
+    # the first apply on a tree builds and caches the operator sets of both
+    # kernels: a failure part-way may leave a finished set cached (as a
+    # successful call would), never a half-built one and nothing else, so
+    # after one more successful apply the tree holds exactly the bytes of a
+    # tree that never saw a failure
+    ref, _ = _tree_footprint(pb, ctx, x, case, 0)
+    n_fail = 0
+    for nth in (1, 2, 3, 5, 9, 17, 33, 65):
+        got, failed = _tree_footprint(pb, ctx, x, case, nth)
+        n_fail += failed
+        assert got == ref, f"allocation {nth}: {got} bytes held, {ref} without the failure"
+    assert n_fail >= 6
     # mesh set-up and a solve
     V, F = synthetic.icosphere(2, 2.0)
     F = F.astype(np.int32)

@@ -411,13 +411,14 @@ def test_pair_equals_two_applies_low_order(pb, ctx, case20k, p):
 # Accuracy the paper states per expansion order (Sec. "Fast multipole
 # method" results): about 4 digits at p = 4, 5 digits at p = 5, 9 digits at
 # p = 10 in FP64.  The FP32 path is limited near 1e-6 by its own rounding.
-# The bounds: the paper's digits where it states them (p = 4, 5), the 1e-5
-# target from p = 6 on in both precisions, and the FP64 orders tightening
-# with p (p = 8: 1e-6, p = 10: 1e-7; the pseudo-inverses' Tikhonov
-# regularisation, relative 1e-7, keeps p = 10 from the paper's 9 digits).
+# The bounds: the paper's digits where it states them (p = 4: 1e-4, p = 5:
+# 1e-5, p = 10 in FP64: 9 digits, 1e-8 allowed), the 1e-5 target from p = 6
+# on in FP32, and FP64 tightening with p in between (p = 6: 1e-6, p = 8:
+# 1e-7).  Measured on GB300 at 20k points: 1.1e-5, 1.3e-6, 2.2e-7, 2.0e-8,
+# 4.0e-9 (FP64, p = 4, 5, 6, 8, 10); FP32 levels off at 4e-7.
 ORDER_BOUND = {("mixed", 4): 1e-4, ("mixed", 5): 1e-5, ("mixed", 6): 1e-5, ("mixed", 8): 1e-5,
-               ("mixed", 10): 1e-5, ("fp64", 4): 1e-4, ("fp64", 5): 1e-5, ("fp64", 6): 1e-5,
-               ("fp64", 8): 1e-6, ("fp64", 10): 1e-7}
+               ("mixed", 10): 1e-5, ("fp64", 4): 1e-4, ("fp64", 5): 1e-5, ("fp64", 6): 1e-6,
+               ("fp64", 8): 1e-7, ("fp64", 10): 1e-8}
 _order_errs = {}
 
 
