@@ -53,7 +53,20 @@ typedef struct pb_mesh pb_mesh;
 typedef struct pb_result pb_result;
 
 /* trial/test spaces (Sec. "An introduction to Bempp") */
-enum { PB_P0 = 0 /* piecewise constant */ };
+enum { PB_P0 = 0 /* piecewise constant, one unknown per triangle */,
+       PB_P1 = 1 /* continuous piecewise linear, one unknown per vertex */ };
+
+/* boundary integral formulations (Sec. "Boundary integral formulation of
+ * electrostatics in molecular solvation"):
+ *   PB_FORM_DIRECT    Eq. direct, unknowns [phi_1, dphi_1/dn] on the surface
+ *   PB_FORM_EXTERIOR  Eq. lu (exterior derivative formulation), unknowns
+ *                     [phi_2, dphi_2/dn] (exterior values)
+ *   PB_FORM_INTERIOR  Eq. juffer (interior derivative formulation),
+ *                     unknowns [phi_1, dphi_1/dn]
+ * The derivative formulations need the P1 basis (their hypersingular
+ * operators W are applied in the integrated-by-parts form, which needs
+ * continuous trial and test functions). */
+enum { PB_FORM_DIRECT = 0, PB_FORM_EXTERIOR = 1, PB_FORM_INTERIOR = 2 };
 
 typedef struct {
     int p;        /* FMM expansion order, 2..10 */
@@ -267,8 +280,10 @@ int fmm_apply_pair(pb_ctx* ctx, fmm_tree* tree, double kappa, int p, int precisi
 
 /* Set up a closed triangulated surface: verts (host or device, double
  * [nv][3]), tris (host or device, int32 [nt][3], counter-clockwise seen from
- * outside so that normals point out of the solute, Eq. pde).  basis must be
- * PB_P0; nquad (3 or 6) is the regular quadrature rule per triangle (3: the
+ * outside so that normals point out of the solute, Eq. pde).  basis is PB_P0
+ * (one unknown per triangle and block) or PB_P1 (one per vertex: the mesh
+ * must be a closed surface whose every vertex belongs to a triangle); nquad
+ * (3 or 6) is the regular quadrature rule per triangle (3: the
  * interior degree-2 rule (2/3,1/6,1/6); 6: Dunavant degree 4).  Builds
  * normals, areas, quadrature points, the vertex-sharing adjacency (the
  * pairs that need singular quadrature) and the octree over the quadrature
@@ -281,6 +296,10 @@ int pb_mesh_destroy(pb_mesh* mesh);
 
 /* Sizes of a mesh: triangles, quadrature points, vertex-sharing pairs. */
 int pb_mesh_info(const pb_mesh* mesh, int64_t* nt, int64_t* nquad_points, int64_t* nadj);
+
+/* Unknowns per block of the 2 x 2 systems: nt for PB_P0, nv for PB_P1 (the
+ * solution and mat-vec vectors hold 2 n doubles). */
+int pb_mesh_unknowns(const pb_mesh* mesh, int64_t* n);
 
 /* Singular Galerkin entries for Yukawa parameter kappa, to HOST buffers:
  * adj_off [nt + 1] and adj_ids [nadj] (CSR of the pairs, ascending), and
@@ -299,6 +318,30 @@ int pb_mesh_export_singular(pb_ctx* ctx, pb_mesh* mesh, double kappa, int64_t* a
 int pb_mesh_matvec(pb_ctx* ctx, pb_mesh* mesh, double eps_in, double eps_out, double kappa, int precision,
                    int precond, const double* x, double* y);
 
+/* y = A x (precond = 0) or y = P^{-1} A x (precond = 1) for the Galerkin
+ * matrix of `formulation` (PB_FORM_*) on the mesh's basis; x, y: double
+ * [2 n] (n from pb_mesh_unknowns), host or device.  P0: PB_FORM_DIRECT only,
+ * block-diagonal preconditioner as pb_mesh_matvec.  P1: every formulation,
+ * with the blocks (e12 = eps_in/eps_out, e21 = eps_out/eps_in, M the P1
+ * mass matrix, K' the adjoint double layer, W the hypersingular operator of
+ * Eq. adj_hyp):
+ *   direct    [ M/2 + K_L, -V_L ; M/2 - K_Y, e12 V_Y ]
+ *   exterior  [ (1+e12)/2 M - (K_Y - e12 K_L), V_Y - V_L ;
+ *               e12 (W_Y - W_L), (1+e12)/2 M + e12 K'_Y - K'_L ]   (Eq. lu)
+ *   interior  [ (1+e21)/2 M - (e21 K_Y - K_L), V_Y - V_L ;
+ *               W_Y - W_L, (1+e12)/2 M + e12 K'_Y - K'_L ]         (Eq. juffer)
+ * and the lumped-mass preconditioner P = diag(lumped M, lumped M) (row sums
+ * of M; Sec. "Matrix conditioning of two derivative formulations").  W is
+ * applied in its integrated-by-parts form <W u, v> = int int g curl u .
+ * curl v (+ kappa^2 n_x.n_y g_Y u v for Yukawa): one FMM pass per curl
+ * component, three Yukawa passes of the phi n components, and one pass of
+ * target-normal derivatives for K', beside the V/K pass of every mat-vec.
+ * Synchronous when a host buffer is given.
+ * Errors: PB_EINVAL for an unknown formulation or a derivative formulation
+ * on a P0 mesh. */
+int pb_mesh_matvec_ex(pb_ctx* ctx, pb_mesh* mesh, double eps_in, double eps_out, double kappa, int precision,
+                      int precond, int formulation, const double* x, double* y);
+
 /* Solve Eq. direct for point charges q (double [na], e) at atoms (double
  * [na][3]) inside the surface, eps_in / eps_out relative permittivities,
  * kappa the inverse Debye length (1/A).  Full GMRES (no restart, x0 = 0,
@@ -311,10 +354,27 @@ int pb_mesh_matvec(pb_ctx* ctx, pb_mesh* mesh, double eps_in, double eps_out, do
  * phase timers and launch count then cover only directly launched work. */
 int pb_solve(pb_ctx* ctx, pb_mesh* mesh, const double* atoms, const double* q, int64_t na, double eps_in,
              double eps_out, double kappa, double tol, int max_iter, int precision, pb_result** out);
+
+/* pb_solve for any formulation (PB_FORM_*): the system of pb_mesh_matvec_ex
+ * with its preconditioner, right-hand side [int psi_i f ; int psi_i df/dn]
+ * of the Coulomb field f = sum_k q_k / (4 pi eps |x - r_k|), eps = eps_in
+ * (interior, direct; the direct formulation's second block is 0) or
+ * eps_out (exterior).  pb_result_get returns the formulation's unknowns
+ * (the exterior formulation's are the exterior values phi_2, dphi_2/dn);
+ * pb_solvation_energy converts to the interior fields (phi_1 = phi_2,
+ * dphi_1/dn = (eps_out/eps_in) dphi_2/dn) for Eq. phi_reac.  For P1 meshes
+ * the charge <-> surface sums are always direct FP64 sums.
+ * pb_energy_grad and pb_solve_batch take direct-formulation P0 systems only.
+ * Errors: as pb_solve, and PB_EINVAL for a derivative formulation on a P0
+ * mesh. */
+int pb_solve_ex(pb_ctx* ctx, pb_mesh* mesh, const double* atoms, const double* q, int64_t na, double eps_in,
+                double eps_out, double kappa, double tol, int max_iter, int precision, int formulation,
+                pb_result** out);
 int pb_result_destroy(pb_result* res);
 
 /* Iterations, final relative residual, and (if x != NULL) the solution to a
- * HOST buffer double [2 nt]: phi on the triangles, then dphi/dn. */
+ * HOST buffer double [2 n] (n from pb_mesh_unknowns): phi on the triangles
+ * (P0) or vertices (P1), then dphi/dn. */
 int pb_result_get(const pb_result* res, int* iterations, double* residual, double* x);
 
 /* Polar solvation energy (Eq. energy) of a solved system, kcal/mol:

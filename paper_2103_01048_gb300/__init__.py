@@ -86,7 +86,11 @@ _sig("pb_mesh_destroy", [_P])
 _sig("pb_mesh_info", [_P, ctypes.POINTER(_I64), ctypes.POINTER(_I64), ctypes.POINTER(_I64)])
 _sig("pb_mesh_export_singular", [_P, _P, _D, _P, _P, _P])
 _sig("pb_mesh_matvec", [_P, _P, _D, _D, _D, ctypes.c_int, ctypes.c_int, _P, _P])
+_sig("pb_mesh_matvec_ex", [_P, _P, _D, _D, _D, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P, _P])
+_sig("pb_mesh_unknowns", [_P, ctypes.POINTER(_I64)])
 _sig("pb_solve", [_P, _P, _P, _P, _I64, _D, _D, _D, _D, ctypes.c_int, ctypes.c_int, ctypes.POINTER(_P)])
+_sig("pb_solve_ex", [_P, _P, _P, _P, _I64, _D, _D, _D, _D, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                     ctypes.POINTER(_P)])
 _sig("pb_result_destroy", [_P])
 _sig("pb_result_get", [_P, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(_D), _P])
 _sig("pb_solvation_energy", [_P, _P, ctypes.POINTER(_D), _P])
@@ -113,7 +117,8 @@ def exported_symbols():
             "fmm_tree_build", "fmm_tree_destroy",
             "fmm_tree_info", "fmm_tree_export_points", "fmm_tree_export_boxes", "fmm_tree_export_list",
             "fmm_apply", "fmm_apply_pair", "pb_mesh_setup", "pb_mesh_destroy", "pb_mesh_info", "pb_mesh_export_singular",
-            "pb_mesh_matvec", "pb_solve", "pb_result_destroy", "pb_result_get", "pb_solvation_energy",
+            "pb_mesh_matvec", "pb_mesh_matvec_ex", "pb_mesh_unknowns", "pb_solve", "pb_solve_ex",
+            "pb_result_destroy", "pb_result_get", "pb_solvation_energy",
             "pb_solvation_energy_noalloc", "pb_energy_grad", "pb_solve_batch", "pb_tune_ncrit"]
 
 
@@ -236,7 +241,8 @@ def fmm_apply_pair(ctx, tree, kappa, p, out_lap, out_yuk, q_lap=None, q_yuk=None
                                ptr(src_n), ptr(tgt_n), ptr(out_lap), ptr(out_yuk), ptr(dn_lap), ptr(dn_yuk)), ctx)
 
 
-PB_P0 = 0
+PB_P0, PB_P1 = 0, 1
+PB_FORM_DIRECT, PB_FORM_EXTERIOR, PB_FORM_INTERIOR = 0, 1, 2
 
 
 def pb_mesh_setup(ctx, verts, tris, nquad=3, p=6, ncrit=128, basis=PB_P0):
@@ -269,30 +275,40 @@ def pb_mesh_export_singular(ctx, mesh, kappa):
     return off, ids, S
 
 
-def pb_mesh_matvec(ctx, mesh, x, y, eps_in, eps_out, kappa, precision=PB_MIXED, precond=False):
-    _check(_lib.pb_mesh_matvec(ctx, mesh, float(eps_in), float(eps_out), float(kappa), int(precision),
-                               1 if precond else 0, ptr(x), ptr(y)), ctx)
+def pb_mesh_matvec(ctx, mesh, x, y, eps_in, eps_out, kappa, precision=PB_MIXED, precond=False,
+                   formulation=PB_FORM_DIRECT):
+    _check(_lib.pb_mesh_matvec_ex(ctx, mesh, float(eps_in), float(eps_out), float(kappa), int(precision),
+                                  1 if precond else 0, int(formulation), ptr(x), ptr(y)), ctx)
 
 
-def pb_solve(ctx, mesh, atoms, charges, eps_in, eps_out, kappa, tol, max_iter=500, precision=PB_MIXED):
+def pb_mesh_unknowns(mesh):
+    """Unknowns per block: triangles (P0) or vertices (P1)."""
+    n = _I64()
+    _check(_lib.pb_mesh_unknowns(mesh, ctypes.byref(n)), None)
+    return n.value
+
+
+def pb_solve(ctx, mesh, atoms, charges, eps_in, eps_out, kappa, tol, max_iter=500, precision=PB_MIXED,
+             formulation=PB_FORM_DIRECT):
     """Returns (result handle, status); status PB_OK or PB_ENOCONV (handle valid in both)."""
     atoms = np.ascontiguousarray(atoms, dtype=np.float64) if isinstance(atoms, np.ndarray) else atoms
     charges = np.ascontiguousarray(charges, dtype=np.float64) if isinstance(charges, np.ndarray) else charges
     na = int(np.prod(charges.shape))
     h = _P()
-    rc = _lib.pb_solve(ctx, mesh, ptr(atoms), ptr(charges), na, float(eps_in), float(eps_out), float(kappa),
-                       float(tol), int(max_iter), int(precision), ctypes.byref(h))
+    rc = _lib.pb_solve_ex(ctx, mesh, ptr(atoms), ptr(charges), na, float(eps_in), float(eps_out), float(kappa),
+                          float(tol), int(max_iter), int(precision), int(formulation), ctypes.byref(h))
     if rc not in (PB_OK, PB_ENOCONV) or not h:
         _check(rc, ctx)
     return h, rc
 
 
-def pb_result_get(res, nt=None):
+def pb_result_get(res, n=None):
+    """(iterations, residual, x); x [2 n] when n (pb_mesh_unknowns) is given."""
     it = ctypes.c_int()
     rr = _D()
     x = None
-    if nt is not None:
-        x = np.zeros(2 * nt)
+    if n is not None:
+        x = np.zeros(2 * n)
     _check(_lib.pb_result_get(res, ctypes.byref(it), ctypes.byref(rr), ptr(x)), None)
     return it.value, rr.value, x
 

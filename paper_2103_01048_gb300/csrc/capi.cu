@@ -12,8 +12,7 @@ void fmm_apply_pair_impl(fmm_tree* Tr, double kappa, int p, int precision, const
                          const void* dip, const void* src_n, const void* tgt_n, void* outL, void* outY, void* dnL,
                          void* dnY);
 void mesh_setup(pb_mesh* M, const double* verts, const int* tris);
-void mesh_matvec(pb_mesh* M, double eps_in, double eps_out, double kappa, int precision, const double* x, double* y,
-                 int precond);
+
 int solve(pb_mesh* M, pb_result* R, double tol, int max_iter);
 void reaction_energy(pb_result* R, double* phir_host, double* dG);
 void ensure_singular_public(pb_mesh* M, double kappa);
@@ -25,7 +24,7 @@ void tune_ncrit(pb_ctx* ctx, const float* xyz_dev, long long n, int p, const int
 
 // A result object for the charges of one system (atoms as (x, y, z, q) on the device).
 pb_result* make_result(pb_ctx* ctx, pb_mesh* M, const double* atoms, const double* q, int64_t na, double eps_in,
-                       double eps_out, double kappa, int precision) {
+                       double eps_out, double kappa, int precision, int formulation = PB_FORM_DIRECT) {
     std::unique_ptr<pb_result> owner(new pb_result());
     pb_result* R = owner.get();
     R->mesh = M;
@@ -35,6 +34,8 @@ pb_result* make_result(pb_ctx* ctx, pb_mesh* M, const double* atoms, const doubl
     R->eps_out = eps_out;
     R->kappa = kappa;
     R->precision = precision;
+    R->formulation = formulation;
+    R->nunk = M->nunk;
     std::vector<double> a4(4 * na), ha(3 * na), hq(na);
     cudaError_t e1 = cudaMemcpy(ha.data(), atoms, 3 * na * sizeof(double), cudaMemcpyDefault);
     cudaError_t e2 = cudaMemcpy(hq.data(), q, na * sizeof(double), cudaMemcpyDefault);
@@ -440,7 +441,7 @@ int pb_mesh_setup(pb_ctx* ctx, const double* verts, int64_t nv, const int32_t* t
     pb_mesh* M = nullptr;
     PB_API_BEGIN
     PB_REQUIRE(verts && tris && nv >= 3 && nt >= 1, PB_EINVAL, "pb_mesh_setup: empty mesh");
-    PB_REQUIRE(basis == PB_P0, PB_EINVAL, "pb_mesh_setup: only the P0 basis is provided");
+    PB_REQUIRE(basis == PB_P0 || basis == PB_P1, PB_EINVAL, "pb_mesh_setup: basis must be PB_P0 or PB_P1");
     PB_REQUIRE(nquad == 3 || nquad == 6, PB_EINVAL, "pb_mesh_setup: nquad must be 3 or 6");
     PB_REQUIRE(nt * nquad < (1LL << 31) - 1, PB_EINVAL, "pb_mesh_setup: too many quadrature points");
     PB_CUDA(cudaSetDevice(ctx->device));
@@ -449,6 +450,7 @@ int pb_mesh_setup(pb_ctx* ctx, const double* verts, int64_t nv, const int32_t* t
     M->nv = nv;
     M->nt = nt;
     M->nq = nquad;
+    M->basis = basis;
     if (params) {
         PB_REQUIRE(params->p >= 2 && params->p <= 10 && params->ncrit >= 1, PB_EINVAL, "pb_mesh_setup: bad FMM params");
         M->p = params->p;
@@ -481,6 +483,12 @@ int pb_mesh_destroy(pb_mesh* M) {
     return PB_OK;
 }
 
+int pb_mesh_unknowns(const pb_mesh* M, int64_t* n) {
+    if (!M || !n) return PB_EINVAL;
+    *n = M->nunk;
+    return PB_OK;
+}
+
 int pb_mesh_info(const pb_mesh* M, int64_t* nt, int64_t* nqp, int64_t* nadj) {
     if (!M) return PB_EINVAL;
     if (nt) *nt = M->nt;
@@ -509,20 +517,29 @@ int pb_mesh_export_singular(pb_ctx* ctx, pb_mesh* M, double kappa, int64_t* adj_
 
 int pb_mesh_matvec(pb_ctx* ctx, pb_mesh* M, double eps_in, double eps_out, double kappa, int precision, int precond,
                    const double* x, double* y) {
+    return pb_mesh_matvec_ex(ctx, M, eps_in, eps_out, kappa, precision, precond, PB_FORM_DIRECT, x, y);
+}
+
+int pb_mesh_matvec_ex(pb_ctx* ctx, pb_mesh* M, double eps_in, double eps_out, double kappa, int precision,
+                      int precond, int formulation, const double* x, double* y) {
     if (!ctx || !M) return PB_EINVAL;
     PB_API_BEGIN
     PB_REQUIRE(x && y && eps_in > 0 && eps_out > 0 && kappa > 0, PB_EINVAL, "pb_mesh_matvec: bad arguments");
     PB_REQUIRE(precision == PB_MIXED || precision == PB_FP64, PB_EINVAL, "pb_mesh_matvec: unknown precision");
+    PB_REQUIRE(formulation >= PB_FORM_DIRECT && formulation <= PB_FORM_INTERIOR, PB_EINVAL,
+               "pb_mesh_matvec: unknown formulation");
+    PB_REQUIRE(formulation == PB_FORM_DIRECT || M->basis == PB_P1, PB_EINVAL,
+               "pb_mesh_matvec: the derivative formulations need a PB_P1 mesh");
     PB_CUDA(cudaSetDevice(ctx->device));
     cudaStream_t st = ctx->stream;
-    const size_t nb = 2 * M->nt * sizeof(double);
+    const size_t nb = 2 * M->nunk * sizeof(double);
     Staged sx;
     sx.in(x, nb, st);
     bool yh = !is_device_ptr(y);
     DBuf<char> yb;
     double* yd = y;
     if (yh) { yb.alloc(nb, st); yd = (double*)yb.p; }
-    mesh_matvec(M, eps_in, eps_out, kappa, precision, (const double*)sx.dev, yd, precond);
+    mesh_matvec(M, eps_in, eps_out, kappa, precision, (const double*)sx.dev, yd, precond, formulation);
     if (yh) PB_CUDA(cudaMemcpyAsync(y, yd, nb, cudaMemcpyDeviceToHost, st));
     PB_CUDA(cudaStreamSynchronize(st));
     check_device_error(ctx);
@@ -531,6 +548,12 @@ int pb_mesh_matvec(pb_ctx* ctx, pb_mesh* M, double eps_in, double eps_out, doubl
 
 int pb_solve(pb_ctx* ctx, pb_mesh* M, const double* atoms, const double* q, int64_t na, double eps_in, double eps_out,
              double kappa, double tol, int max_iter, int precision, pb_result** out) {
+    return pb_solve_ex(ctx, M, atoms, q, na, eps_in, eps_out, kappa, tol, max_iter, precision, PB_FORM_DIRECT, out);
+}
+
+int pb_solve_ex(pb_ctx* ctx, pb_mesh* M, const double* atoms, const double* q, int64_t na, double eps_in,
+                double eps_out, double kappa, double tol, int max_iter, int precision, int formulation,
+                pb_result** out) {
     if (!ctx || !M || !out) return PB_EINVAL;
     *out = nullptr;
     int status = PB_OK;
@@ -539,10 +562,12 @@ int pb_solve(pb_ctx* ctx, pb_mesh* M, const double* atoms, const double* q, int6
     PB_REQUIRE(eps_in > 0 && eps_out > 0 && kappa > 0, PB_EINVAL, "pb_solve: eps and kappa must be > 0");
     PB_REQUIRE(tol >= 0 && max_iter >= 1 && max_iter <= 2000, PB_EINVAL, "pb_solve: tol >= 0 and 1 <= max_iter <= 2000");
     PB_REQUIRE(precision == PB_MIXED || precision == PB_FP64, PB_EINVAL, "pb_solve: unknown precision");
+    PB_REQUIRE(formulation >= PB_FORM_DIRECT && formulation <= PB_FORM_INTERIOR, PB_EINVAL,
+               "pb_solve: unknown formulation");
+    PB_REQUIRE(formulation == PB_FORM_DIRECT || M->basis == PB_P1, PB_EINVAL,
+               "pb_solve: the derivative formulations need a PB_P1 mesh");
     PB_CUDA(cudaSetDevice(ctx->device));
-    cudaStream_t st = ctx->stream;
-    (void)st;
-    pb_result* R = make_result(ctx, M, atoms, q, na, eps_in, eps_out, kappa, precision);
+    pb_result* R = make_result(ctx, M, atoms, q, na, eps_in, eps_out, kappa, precision, formulation);
     *out = R;
     try {
         status = solve(M, R, tol, max_iter);
@@ -573,7 +598,7 @@ int pb_result_get(const pb_result* R, int* iterations, double* residual, double*
     if (iterations) *iterations = R->iterations;
     if (residual) *residual = R->residual;
     if (x) {
-        cudaError_t e = cudaMemcpy(x, R->x.p, 2 * R->nt * sizeof(double), cudaMemcpyDeviceToHost);
+        cudaError_t e = cudaMemcpy(x, R->x.p, 2 * R->nunk * sizeof(double), cudaMemcpyDeviceToHost);
         if (e != cudaSuccess) return PB_ECUDA;
     }
     return PB_OK;
@@ -601,6 +626,7 @@ int pb_solve_batch(pb_ctx* ctx, pb_mesh* const* meshes, int nsys, const double* 
     PB_REQUIRE(precision == PB_MIXED || precision == PB_FP64, PB_EINVAL, "pb_solve_batch: unknown precision");
     for (int s = 0; s < nsys; ++s) {
         PB_REQUIRE(meshes[s] && atoms[s] && charges[s] && na[s] >= 1, PB_EINVAL, "pb_solve_batch: empty system");
+        PB_REQUIRE(meshes[s]->basis == PB_P0, PB_EINVAL, "pb_solve_batch: P0 meshes (direct formulation) only");
         for (int t = 0; t < s; ++t)
             PB_REQUIRE(meshes[t] != meshes[s], PB_EINVAL, "pb_solve_batch: meshes must be distinct");
     }
@@ -646,6 +672,8 @@ int pb_energy_grad(pb_ctx* ctx, pb_result* R, double tol, int max_iter, double* 
     int status = PB_OK;
     PB_API_BEGIN
     PB_REQUIRE(tol >= 0 && max_iter >= 1 && max_iter <= 2000, PB_EINVAL, "pb_energy_grad: bad tol or max_iter");
+    PB_REQUIRE(R->mesh->basis == PB_P0 && R->formulation == PB_FORM_DIRECT, PB_EINVAL,
+               "pb_energy_grad: direct-formulation results on P0 meshes only");
     PB_CUDA(cudaSetDevice(ctx->device));
     status = energy_gradient(R, tol, max_iter, dEdq, dEdx);
     check_device_error(ctx);

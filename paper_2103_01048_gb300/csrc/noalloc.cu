@@ -127,6 +127,10 @@ extern "C" int pb_solvation_energy_noalloc(pb_ctx* ctx, const pb_result* res, do
             ctx->last_error = "pb_solvation_energy_noalloc: more atoms than the scratch array holds (262144)";
             return PB_EINVAL;
         }
+        if (res->mesh->basis != PB_P0) {
+            ctx->last_error = "pb_solvation_energy_noalloc: results on P0 meshes only";
+            return PB_EINVAL;
+        }
         PB_CUDA(cudaSetDevice(ctx->device));
         cudaPointerAttributes at;
         if (cudaPointerGetAttributes(&at, dG_device) != cudaSuccess || at.type != cudaMemoryTypeDevice ||
