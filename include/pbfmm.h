@@ -241,9 +241,11 @@ int fmm_tree_export_list(const fmm_tree* tree, int which, int64_t* off, int32_t*
  * Buffers may be host or device memory (see conventions).  With device
  * buffers the call is asynchronous; with any host buffer it synchronises.
  * Operators for (kernel, kappa, p, tree size) are precomputed on first use
- * and cached in the tree.  With PB_MIXED and p <= 6 the M2L, M2M, L2L and
- * the check -> equivalent solves run on the tensor cores (TF32 split into
- * hi + lo parts, three products per step); otherwise on the CUDA cores, the
+ * and cached in the tree.  With PB_MIXED and p in 2..6, 8 or 10 the M2L,
+ * M2M, L2L and the check -> equivalent solves run on the tensor cores (TF32
+ * split into hi + lo parts, three products per step; at p = 8 and 10 each
+ * operator is split into parts that fit in shared memory); with p = 7 or 9
+ * or PB_FP64 on the CUDA cores, the
  * M2L parallel over interaction pairs.  The M2L / M2M / L2L reductions make
  * the summation order run-dependent (~1e-7 in FP32, ~1e-16 in FP64);
  * PB_OPT_DETERMINISTIC selects fixed-order CUDA-core kernels.  The tensor-core
@@ -303,8 +305,14 @@ int pb_mesh_unknowns(const pb_mesh* mesh, int64_t* n);
 
 /* Singular Galerkin entries for Yukawa parameter kappa, to HOST buffers:
  * adj_off [nt + 1] and adj_ids [nadj] (CSR of the pairs, ascending), and
- * S [nadj][4] = (V_L, K_L, V_Y, K_Y) entries int_Ti int_Tj of the kernels of
- * Eq. single_double (identical or vertex-sharing triangle pairs).
+ *   P0 mesh: S [nadj][4] = (V_L, K_L, V_Y, K_Y) entries int_Ti int_Tj of the
+ *            kernels of Eq. single_double (identical or vertex-sharing
+ *            triangle pairs);
+ *   P1 mesh: S [nadj][4][3][3] = for the same four kernels, the blocks
+ *            int_Ti lambda_a int_Tj lambda_b k (a the test vertex of T_i, b the
+ *            trial vertex of T_j, in the triangles' vertex order) minus the
+ *            same blocks under the regular product rule: what the mat-vec
+ *            adds to its point sums for these pairs.
  * Synchronous; assembles S on first use for this kappa. */
 int pb_mesh_export_singular(pb_ctx* ctx, pb_mesh* mesh, double kappa, int64_t* adj_off, int32_t* adj_ids,
                             double* S);

@@ -71,6 +71,24 @@ def assemble_p1(verts, tris, nq, kappa, L_outer=6, n_outer=4, n_inner=4):
     return mats
 
 
+def pair_blocks(verts, tris, pairs, nq, kappa, minus_regular=True, L_outer=6):
+    """P1 blocks [npairs][4][3][3] (V_L, K_L, V_Y, K_Y; test vertex, trial
+    vertex) of the triangle pairs (i, j), optionally minus their regular
+    product-rule part (oracle.c or_pair_p1)."""
+    V = np.ascontiguousarray(verts, dtype=np.float64)
+    F = np.ascontiguousarray(tris, dtype=np.int32)
+    out = np.zeros((len(pairs), 4, 3, 3))
+    buf = np.zeros(36)
+    for k, (i, j) in enumerate(pairs):
+        ti = np.ascontiguousarray(F[i])
+        tj = np.ascontiguousarray(F[j])
+        if lib().or_pair_p1(_p(V), _p(ti), _p(tj), int(nq), float(kappa), int(L_outer), 4, 4,
+                            1 if minus_regular else 0, _p(buf)) != 0:
+            raise ValueError("pair block failed")
+        out[k] = buf.reshape(4, 3, 3)
+    return out
+
+
 def mass_p1(verts, tris):
     """P1 mass matrix: sum over triangles of |T| (1 + delta_ab) / 12."""
     _, area = geometry(verts, tris)

@@ -742,3 +742,64 @@ int or_assemble_p1(long nv, const double *verts, long nt, const int *tris,
     free(lo1); free(lo2); free(wo); free(li1); free(li2); free(wi);
     return 0;
 }
+
+/*
+ * P1 block of one triangle pair (test triangle Ti = vertices ti[0..2],
+ * trial Tj), for op = V_L, K_L, V_Y, K_Y and local test / trial vertices a,
+ * b: out[op*9 + 3a + b] = int_Ti lambda_a int_Tj lambda_b k.  With
+ * `minus_regular`, the same block under the nq x nq regular product rule
+ * (pairs at distance 0 excluded) is subtracted: what the singular quadrature
+ * adds to a point-sum (FMM) evaluation of the pair.  Identical or
+ * vertex-sharing pairs use the graded outer rule of or_assemble_p1.
+ */
+int or_pair_p1(const double *verts, const int *ti, const int *tj, int nq, double kappa,
+               int L_outer, int n_outer, int n_inner, int minus_regular, double *out)
+{
+    double RL[6 * 3], RW[6];
+    if (regular_rule(nq, RL, RW) != 0) return -1;
+    tri_t Ti, Tj;
+    for (int a = 0; a < 3; ++a)
+        for (int c = 0; c < 3; ++c) { Ti.v[a][c] = verts[3 * ti[a] + c]; Tj.v[a][c] = verts[3 * tj[a] + c]; }
+    double ni[3], nj[3];
+    const double ai = tri_area_normal(&Ti, ni), aj = tri_area_normal(&Tj, nj);
+    int shared = 0;
+    for (int s = 0; s < 3; ++s)
+        for (int t = 0; t < 3; ++t)
+            if (ti[s] == tj[t]) shared++;
+    const int no = n_outer * n_outer, ni_ = n_inner * n_inner;
+    double lo1[64], lo2[64], wo[64], li1[64], li2[64], wi[64];
+    if (no > 64 || ni_ > 64) return -1;
+    triangle_rule(n_outer, lo1, lo2, wo);
+    triangle_rule(n_inner, li1, li2, wi);
+    double blk[4][3][3];
+    memset(blk, 0, sizeof(blk));
+    outer_lin_ctx C = { &Tj, nj, aj, shared == 3, kappa, no, lo1, lo2, wo, ni_, li1, li2, wi, 1e-10 * sqrt(aj) };
+    outer_graded_lin(&C, &Ti, &Ti, shared ? L_outer : 0, blk);
+    if (minus_regular) {
+        const double k4pi = 1.0 / (4.0 * OR_PI);
+        for (int qa = 0; qa < nq; ++qa) {
+            double x[3], y[3], rv[3];
+            for (int c = 0; c < 3; ++c)
+                x[c] = RL[3 * qa] * Ti.v[0][c] + RL[3 * qa + 1] * Ti.v[1][c] + RL[3 * qa + 2] * Ti.v[2][c];
+            for (int qb = 0; qb < nq; ++qb) {
+                for (int c = 0; c < 3; ++c)
+                    y[c] = RL[3 * qb] * Tj.v[0][c] + RL[3 * qb + 1] * Tj.v[1][c] + RL[3 * qb + 2] * Tj.v[2][c];
+                sub3(x, y, rv);
+                const double r = norm3(rv);
+                if (r == 0.0) continue;
+                const double w = RW[qa] * ai * RW[qb] * aj;
+                const double rn = dot3(rv, nj);
+                const double ek = exp(-kappa * r);
+                const double kk[4] = { k4pi / r, k4pi * rn / (r * r * r), k4pi * ek / r,
+                                       k4pi * ek * (1.0 + kappa * r) * rn / (r * r * r) };
+                for (int op = 0; op < 4; ++op)
+                    for (int a = 0; a < 3; ++a)
+                        for (int b = 0; b < 3; ++b) blk[op][a][b] -= w * RL[3 * qa + a] * RL[3 * qb + b] * kk[op];
+            }
+        }
+    }
+    for (int op = 0; op < 4; ++op)
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) out[op * 9 + 3 * a + b] = blk[op][a][b];
+    return 0;
+}

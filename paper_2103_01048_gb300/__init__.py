@@ -266,11 +266,12 @@ def pb_mesh_info(mesh):
     return a.value, b.value, c.value
 
 
-def pb_mesh_export_singular(ctx, mesh, kappa):
+def pb_mesh_export_singular(ctx, mesh, kappa, p1=False):
+    """(adj_off, adj_ids, S): S [nadj, 4] for a P0 mesh, [nadj, 4, 3, 3] for a P1 mesh (p1=True)."""
     nt, _, nadj = pb_mesh_info(mesh)
     off = np.zeros(nt + 1, np.int64)
     ids = np.zeros(nadj, np.int32)
-    S = np.zeros((nadj, 4))
+    S = np.zeros((nadj, 4, 3, 3) if p1 else (nadj, 4))
     _check(_lib.pb_mesh_export_singular(ctx, mesh, float(kappa), ptr(off), ptr(ids), ptr(S)), ctx)
     return off, ids, S
 

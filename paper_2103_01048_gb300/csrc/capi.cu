@@ -16,6 +16,7 @@ void mesh_setup(pb_mesh* M, const double* verts, const int* tris);
 int solve(pb_mesh* M, pb_result* R, double tol, int max_iter);
 void reaction_energy(pb_result* R, double* phir_host, double* dG);
 void ensure_singular_public(pb_mesh* M, double kappa);
+void ensure_singular_p1_public(pb_mesh* M, double kappa);
 int energy_gradient(pb_result* R, double tol, int max_iter, double* dEdq_host, double* dEdx_host);
 void solve_batch(pb_ctx* ctx, pb_mesh* const* meshes, int nsys, pb_result** results, double tol, int max_iter,
                  int* status);
@@ -502,7 +503,8 @@ int pb_mesh_export_singular(pb_ctx* ctx, pb_mesh* M, double kappa, int64_t* adj_
     PB_API_BEGIN
     PB_REQUIRE(kappa > 0, PB_EINVAL, "pb_mesh_export_singular: kappa must be > 0");
     cudaStream_t st = ctx->stream;
-    ensure_singular_public(M, kappa);
+    if (M->basis == PB_P1) ensure_singular_p1_public(M, kappa);
+    else ensure_singular_public(M, kappa);
     if (adj_off) {
         std::vector<int> o(M->nt + 1);
         PB_CUDA(cudaMemcpyAsync(o.data(), M->adj_off.p, (M->nt + 1) * 4, cudaMemcpyDeviceToHost, st));
@@ -510,7 +512,10 @@ int pb_mesh_export_singular(pb_ctx* ctx, pb_mesh* M, double kappa, int64_t* adj_
         for (int64_t i = 0; i <= M->nt; ++i) adj_off[i] = o[i];
     }
     if (adj_ids) PB_CUDA(cudaMemcpyAsync(adj_ids, M->adj_ids.p, M->nadj * 4, cudaMemcpyDeviceToHost, st));
-    if (S) PB_CUDA(cudaMemcpyAsync(S, M->S_d.p, M->nadj * 4 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    if (S && M->basis == PB_P1)
+        PB_CUDA(cudaMemcpyAsync(S, M->D1.p, M->nadj * 36 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    else if (S)
+        PB_CUDA(cudaMemcpyAsync(S, M->S_d.p, M->nadj * 4 * sizeof(double), cudaMemcpyDeviceToHost, st));
     PB_CUDA(cudaStreamSynchronize(st));
     PB_API_END(ctx)
 }

@@ -27,13 +27,15 @@ struct Operators {
     DBuf<float> uc2ue_w1, uc2ue_w2, dc2de_w1, dc2de_w2;   // [nlev][npad^2]
     DBuf<float> m2m, l2l;         // [nlev][8][npad^2]  (child level index)
     DBuf<float> m2l;              // [nlev][343][npad^2]
-    // tensor-core M2L (p <= 6): per level and offset, the operator split into
-    // TF32 hi + lo parts, pre-swizzled (128B swizzle, K-major) per N half:
-    // [level][343][half][hi|lo][K/32][npad/2 rows][128 B]
+    // tensor-core M2L: per level and offset (Laplace: one level), the
+    // operator split into TF32 hi + lo parts, pre-swizzled (128B swizzle,
+    // K-major) per part of its rows and inner columns:
+    // [level][343][part][hi|lo][K blocks][rows of the part][128 B]
     DBuf<float> m2l_tc;
     DBuf<float> m2m_tc, l2l_tc;   // same packing, [level][8 octants]
     DBuf<float> uc2ue_w1_tc, uc2ue_w2_tc, dc2de_w1_tc, dc2de_w2_tc;   // same packing, [level]
     bool have_tc = false;
+    bool m2l_tc_single = false;   // Laplace: m2l_tc holds one level (the operators are level-invariant)
     // FP64 copies (all-FP64 path)
     DBuf<double> uc2ue_d, dc2de_d, m2m_d, l2l_d, m2l_d;
     bool have_d = false;

@@ -3,20 +3,24 @@
 // The V-list pairs (Sec. "Fast multipole method": interaction list I(B)) are
 // grouped by (level, relative offset): all pairs of a group share one M2L
 // operator (with the DC2DE solve folded in, FP64-built, FP32-stored).  A CTA
-// owns one group chunk and one half of the operator's output rows:
-//   * the operator half, split into TF32 hi + lo parts and pre-swizzled in
+// owns one group chunk and one part of the operator: a block of its output
+// rows times a block of its inner columns (two row halves up to p = 6;
+// 4 x 2 parts at p = 8, 4 x 4 at p = 10), so that the part fits in shared
+// memory:
+//   * the operator part, split into TF32 hi + lo parts and pre-swizzled in
 //     global memory (128B swizzle, K-major), is copied into shared memory
 //     once with cp.async.bulk and stays resident;
 //   * 128-pair row tiles stream through: the producer threads gather the
-//     source boxes' upward densities (Qu rows), split them into TF32 hi + lo
-//     and write them swizzled into a double-buffered A stage;
-//   * one thread issues tcgen05.mma kind::tf32 (M = 128 pairs, N = npad/2,
-//     K = 8 per instruction), three products per k-step (hi*hi + hi*lo +
-//     lo*hi: FP32-level accuracy), accumulating in TMEM;
+//     source boxes' upward densities (the part's columns of the Qu rows),
+//     split them into TF32 hi + lo and write them swizzled into a ring of
+//     A stages;
+//   * one thread issues tcgen05.mma kind::tf32 (M = 128 pairs, N = the
+//     part's rows, K = 8 per instruction), three products per k-step
+//     (hi*hi + hi*lo + lo*hi: FP32-level accuracy), accumulating in TMEM;
 //   * the epilogue reads the accumulator with tcgen05.ld and adds each row
 //     into the target box's downward density with red.global.add.v4.f32
-//     (targets of one group are distinct; groups overlap, hence the
-//     reduction).  Summation order across groups is not fixed.
+//     (targets of one group are distinct; groups and inner parts overlap,
+//     hence the reduction).  Summation order across groups is not fixed.
 // Every wait is bounded (~1 s); on a timeout the kernel records an error
 // code, drains its own MMAs, frees TMEM and returns.
 #include "fmm.cuh"
@@ -29,7 +33,23 @@ namespace pbfmm {
 constexpr int kTcRows = 128;           // pairs per row tile (MMA M)
 constexpr int kTcItemPairs = 2048;     // pairs per M2L work item (one operator load each)
 constexpr int kTcSmallItemPairs = 512; // M2M / L2L / check->equivalent items: fewer pairs per operator, more CTAs
-constexpr int kTcMaxNpad = 160;        // resident operator half must fit in shared memory
+
+// Operator split per padded size: NS parts of the output rows (MMA N =
+// npad / NS) times KS parts of the inner dimension (npad / KS columns,
+// whole 32-column blocks), so that one part (TF32 hi + lo) stays resident
+// in shared memory beside a ring of STAGES A stages.  Each CTA owns one
+// part; the KS parts of a row add into the target with the reduction.
+template <int NPAD> struct TcCfg { static constexpr int NS = 2, KS = 1, STAGES = 3; };
+template <> struct TcCfg<320> { static constexpr int NS = 4, KS = 2, STAGES = 3; };   // p = 8
+template <> struct TcCfg<512> { static constexpr int NS = 4, KS = 4, STAGES = 2; };   // p = 10
+static bool tc_split(int npad, int& ns, int& ks) {
+    switch (npad) {
+        case 32: case 64: case 128: case 160: ns = 2; ks = 1; return true;
+        case 320: ns = TcCfg<320>::NS; ks = TcCfg<320>::KS; return true;
+        case 512: ns = TcCfg<512>::NS; ks = TcCfg<512>::KS; return true;
+        default: return false;
+    }
+}
 
 // TF32 part of x, rounded to nearest (ties away from zero); x - hi is exact in FP32
 __device__ __forceinline__ float tf32_hi(float x) {
@@ -37,35 +57,47 @@ __device__ __forceinline__ float tf32_hi(float x) {
 }
 
 // ---------------------------------------------------------------------------
-// operator packing: [level][343][half][hi|lo][kb][nh rows][32] swizzled
+// operator packing: [matrix][part = ns * KS + ks][hi|lo][kb][nh rows][32]
+// swizzled (nh = npad / NS output rows, KB = npad / KS / 32 blocks of 32
+// inner columns); the part a CTA owns is one contiguous block
 // ---------------------------------------------------------------------------
-__global__ void k_pack_m2l_tc(int npad, long long nmat, const float* __restrict__ m2l, float* __restrict__ out) {
+__global__ void k_pack_m2l_tc(int npad, int NS, int KS, long long nmat, const float* __restrict__ m2l,
+                              float* __restrict__ out) {
     long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     const long long m2 = (long long)npad * npad;
     if (idx >= nmat * m2) return;
     long long mat = idx / m2;
     int n = (int)((idx % m2) / npad), k = (int)(idx % npad);
-    const int nh = npad / 2, kb_n = npad / 32;
-    int half = n / nh, nr = n % nh, kb = k / 32, kk = k % 32;
+    const int nh = npad / NS, kc = npad / KS, kb_n = kc / 32;
+    int ns = n / nh, nr = n % nh, ks = k / kc, kk = k % kc, kb = kk / 32, kq = kk % 32;
     float x = m2l[idx];
     float hi = tf32_hi(x), lo = x - hi;
-    const long long half_bytes = 2LL * kb_n * nh * 128;
-    char* base = (char*)out + mat * 2 * half_bytes + half * half_bytes;
-    uint32_t off = (uint32_t)kb * nh * 128 + sw128_off(nr, kk);
+    const long long part_bytes = 2LL * kb_n * nh * 128;
+    char* base = (char*)out + (mat * NS * KS + ns * KS + ks) * part_bytes;
+    uint32_t off = (uint32_t)kb * nh * 128 + sw128_off(nr, kq);
     *(float*)(base + off) = hi;
     *(float*)(base + (long long)kb_n * nh * 128 + off) = lo;
 }
 
 static void pack_tc(int npad, long long nmat, const float* src, DBuf<float>& dst, cudaStream_t st) {
+    int ns = 0, ks = 0;
+    if (!tc_split(npad, ns, ks)) throw Error(PB_EINVAL, "no tensor-core split for this operator size");
     const long long m2 = (long long)npad * npad;
     dst.alloc(nmat * m2 * 2, st);
-    k_pack_m2l_tc<<<div_up(nmat * m2, 256), 256, 0, st>>>(npad, nmat, src, dst.p);
+    k_pack_m2l_tc<<<div_up(nmat * m2, 256), 256, 0, st>>>(npad, ns, ks, nmat, src, dst.p);
     PB_CHECK_LAUNCH();
 }
 
+// Laplace M2L operators (the down-check -> down-equivalent solve folded in)
+// do not depend on the level: the 1/r kernel scales as 2^l with the box
+// size and the regularised pseudo-inverse as 2^-l.  Their tensor-core copy
+// keeps one level (the first with interaction lists), indexed by offset.
 void pack_m2l_tc(Operators& O, cudaStream_t st) {
-    if (O.npad > kTcMaxNpad || O.npad % 32 != 0) { O.have_tc = false; return; }
-    pack_tc(O.npad, (long long)O.nlev * kNumOffsets, O.m2l.p, O.m2l_tc, st);
+    int ns = 0, ks = 0;
+    if (!tc_split(O.npad, ns, ks)) { O.have_tc = false; return; }
+    O.m2l_tc_single = O.kernel == FMM_LAPLACE && O.nlev > 2;
+    if (O.m2l_tc_single) pack_tc(O.npad, kNumOffsets, O.m2l.p + 2LL * kNumOffsets * O.npad * O.npad, O.m2l_tc, st);
+    else pack_tc(O.npad, (long long)O.nlev * kNumOffsets, O.m2l.p, O.m2l_tc, st);
     if (O.m2m.p) pack_tc(O.npad, (long long)O.nlev * 8, O.m2m.p, O.m2m_tc, st);
     if (O.l2l.p) pack_tc(O.npad, (long long)O.nlev * 8, O.l2l.p, O.l2l_tc, st);
     if (O.uc2ue_w1.p) {
@@ -231,14 +263,13 @@ void build_pc_pairs(fmm_tree* T) {
 // the kernel: warp-specialised pipeline
 //   warps 0-7   producers: two threads per pair row gather the source box's
 //               Qu row, split it into TF32 hi + lo and write it swizzled
-//               into a ring of kTcStages A stages (one K block each);
+//               into a ring of A stages (one K block each);
 //   warps 8-11  epilogue: one TMEM lane quarter each; read the finished
 //               accumulator and add every row into its target's Qd row;
 //   warp 12     one thread issues the MMAs and the commits.
 // Two TMEM accumulators alternate between tiles, so the epilogue of a tile
 // overlaps the MMAs of the next and the gathers of the one after.
 // ---------------------------------------------------------------------------
-constexpr int kTcStages = 3;                    // A-stage ring depth
 constexpr int kTcProdWarps = 8;
 constexpr int kTcEpiWarps = 4;
 constexpr int kTcThreads = 32 * (kTcProdWarps + kTcEpiWarps + 1);
@@ -246,11 +277,12 @@ constexpr int kTcThreads = 32 * (kTcProdWarps + kTcEpiWarps + 1);
 constexpr int kTcEpiLd = 16;                    // accumulator columns per epilogue TMEM load
 constexpr int kTcEpiStride = 20;                // padded row of the epilogue transpose buffer (floats)
 
+template <int STAGES>
 struct TcSmem {
     // per epilogue warp: 32 rows x kTcEpiLd columns, transposed through shared
     // memory so that each reduction instruction covers 8 rows x 64 B
     alignas(16) float epi[kTcEpiWarps][32][kTcEpiStride];
-    uint64_t barB, full[kTcStages], empty[kTcStages], accf[2], acce[2];
+    uint64_t barB, full[STAGES], empty[STAGES], accf[2], acce[2];
     uint32_t tmem_slot;
     int failed;
 };
@@ -277,6 +309,7 @@ struct TcSets {
     const float* ops[2];
     const float* X[2];
     float* Y[2];
+    int single[2];           // 1: the set holds one level of M2L operators, indexed by offset alone
     long long wait_limit;    // cycles a role waits on a barrier before giving up (set at launch)
 };
 
@@ -293,23 +326,28 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(const int4* __restrict
     const float* __restrict__ Qu = sets.X[blockIdx.z];
     float* __restrict__ Qd = sets.Y[blockIdx.z];
     const long long wl = sets.wait_limit;
-    constexpr int NH = NPAD / 2;                     // output rows of this CTA (MMA N)
-    constexpr int KB = NPAD / 32;                    // K blocks of 32 tf32 (128 B)
+    constexpr int NS = TcCfg<NPAD>::NS, KS = TcCfg<NPAD>::KS, kTcStages = TcCfg<NPAD>::STAGES;
+    constexpr int NH = NPAD / NS;                    // output rows of this CTA (MMA N)
+    constexpr int KC = NPAD / KS;                    // inner columns of this CTA
+    constexpr int KB = KC / 32;                      // K blocks of 32 tf32 (128 B)
+    static_assert(NH % 16 == 0 && NH <= 256 && KC % 32 == 0, "tensor-core split");
     constexpr uint32_t B_SPLIT = KB * NH * 128;      // bytes of one of hi / lo
     constexpr uint32_t A_SPLIT = kTcRows * 128;      // 16 KB
-    constexpr uint32_t ACOLS = NH <= 32 ? 32 : (NH <= 64 ? 64 : 128);   // columns of one accumulator
+    constexpr uint32_t ACOLS = NH <= 32 ? 32 : (NH <= 64 ? 64 : (NH <= 128 ? 128 : 256));   // one accumulator
     constexpr uint32_t TCOLS = 2 * ACOLS;
     constexpr uint32_t IDESC = idesc_tf32(NH);
     extern __shared__ uint8_t smem_raw[];
     uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
     uint8_t* sB = smem;                               // [hi|lo][KB][NH][128]
     uint8_t* sA = smem + 2 * B_SPLIT;                 // [stage][hi|lo][128][128]
-    TcSmem* S = (TcSmem*)(sA + kTcStages * 2 * A_SPLIT);
+    TcSmem<kTcStages>* S = (TcSmem<kTcStages>*)(sA + kTcStages * 2 * A_SPLIT);
     volatile int* failed = &S->failed;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int4 it = items[blockIdx.x];
-    const int half = blockIdx.y;
-    const int first = it.x, npairs = it.y, opi = it.z;
+    const int part = blockIdx.y;                     // operator part: rows half, inner columns kpart
+    const int half = part / KS, kpart = part % KS;
+    const int first = it.x, npairs = it.y;
+    const int opi = sets.single[blockIdx.z] ? it.z % kNumOffsets : it.z;
     const int ntile = (npairs + kTcRows - 1) / kTcRows;
 
     if (tid == 0) {
@@ -334,9 +372,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(const int4* __restrict
     tc_fence_after();
     const uint32_t taddr = S->tmem_slot;
 
-    // resident operator half: hi and lo, one bulk copy each
+    // resident operator part: hi and lo, one bulk copy each
     if (tid == 0) {
-        const uint8_t* gB = (const uint8_t*)ops + ((long long)opi * 2 + half) * (2LL * B_SPLIT);
+        const uint8_t* gB = (const uint8_t*)ops + ((long long)opi * (NS * KS) + part) * (2LL * B_SPLIT);
         mbar_arrive_expect_tx(&S->barB, 2 * B_SPLIT);
         bulk_g2s(sB, gB, B_SPLIT, &S->barB);
         bulk_g2s(sB + B_SPLIT, gB + B_SPLIT, B_SPLIT, &S->barB);
@@ -359,7 +397,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(const int4* __restrict
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             const int s0 = src_of(0, i);
-            const float4* q4 = s0 >= 0 ? (const float4*)(Qu + (size_t)s0 * NPAD) : nullptr;
+            const float4* q4 = s0 >= 0 ? (const float4*)(Qu + (size_t)s0 * NPAD + kpart * KC) : nullptr;
 #pragma unroll
             for (int kb = 0; kb < KB; ++kb) v[kb][i] = q4 ? q4[kb * 8 + l8] : make_float4(0.f, 0.f, 0.f, 0.f);
         }
@@ -386,7 +424,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(const int4* __restrict
                 mbar_arrive(&S->full[s]);
 #pragma unroll
                 for (int i = 0; i < 4; ++i) {
-                    const float4* qn = sn[i] >= 0 ? (const float4*)(Qu + (size_t)sn[i] * NPAD) : nullptr;
+                    const float4* qn = sn[i] >= 0 ? (const float4*)(Qu + (size_t)sn[i] * NPAD + kpart * KC) : nullptr;
                     v[kb][i] = qn ? qn[kb * 8 + l8] : make_float4(0.f, 0.f, 0.f, 0.f);
                 }
             }
@@ -479,10 +517,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(const int4* __restrict
 }
 
 template <int NPAD>
-static size_t tc_smem_bytes() {
-    return 1024 + 2 * (size_t)(NPAD / 32) * (NPAD / 2) * 128 + kTcStages * 2 * (size_t)kTcRows * 128 +
-           sizeof(TcSmem);
+static constexpr size_t tc_smem_bytes() {
+    using C = TcCfg<NPAD>;
+    return 1024 + 2 * (size_t)(NPAD / C::KS / 32) * (NPAD / C::NS) * 128 + C::STAGES * 2 * (size_t)kTcRows * 128 +
+           sizeof(TcSmem<C::STAGES>);
 }
+static_assert(tc_smem_bytes<160>() <= 232448 && tc_smem_bytes<320>() <= 232448 && tc_smem_bytes<512>() <= 232448,
+              "shared memory per CTA");
 
 template <int NPAD>
 static void launch_tc_items(const int4* items, int nitems, const int* tgt, const int* src, const TcSets& sets,
@@ -498,7 +539,7 @@ static void launch_tc_items(const int4* items, int nitems, const int* tgt, const
         PB_CUDA(cudaFuncSetAttribute(k_m2l_tc<NPAD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
         attr_set[dev] = true;
     }
-    dim3 grid(nitems, 2, nsets);
+    dim3 grid(nitems, TcCfg<NPAD>::NS * TcCfg<NPAD>::KS, nsets);
     TcSets s2 = sets;
     s2.wait_limit = g_wait_limit.load();
     k_m2l_tc<NPAD><<<grid, kTcThreads, sm, st>>>(items, tgt, src, s2, err);
@@ -512,11 +553,16 @@ static bool tc_dispatch(int npad, const int4* items, int nitems, const int* tgt,
         case 64: launch_tc_items<64>(items, nitems, tgt, src, sets, nsets, err, st); return true;
         case 128: launch_tc_items<128>(items, nitems, tgt, src, sets, nsets, err, st); return true;
         case 160: launch_tc_items<160>(items, nitems, tgt, src, sets, nsets, err, st); return true;
+        case 320: launch_tc_items<320>(items, nitems, tgt, src, sets, nsets, err, st); return true;
+        case 512: launch_tc_items<512>(items, nitems, tgt, src, sets, nsets, err, st); return true;
         default: return false;
     }
 }
 
-static bool tc_ok(const Operators& O) { return O.have_tc && O.npad <= kTcMaxNpad && O.npad % 32 == 0; }
+static bool tc_ok(const Operators& O) {
+    int ns, ks;
+    return O.have_tc && tc_split(O.npad, ns, ks);
+}
 
 // M2M (up = true: parents at level l - 1 += M2M children at level l) or L2L
 // (children at level l += L2L parents at level l - 1) on the tensor cores,
@@ -579,7 +625,8 @@ bool m2l_tc_launch2(const fmm_tree* T, const Operators& O, const Operators* O2, 
                     const float* Qu2, float* Qd2, int* err, cudaStream_t st) {
     if (!tc_ok(O) || (O2 && (!tc_ok(*O2) || O2->npad != O.npad))) return false;
     if (T->m2l_pairs.nitems == 0) return true;
-    TcSets sets{{O.m2l_tc.p, O2 ? O2->m2l_tc.p : nullptr}, {Qu, Qu2}, {Qd, Qd2}};
+    TcSets sets{{O.m2l_tc.p, O2 ? O2->m2l_tc.p : nullptr}, {Qu, Qu2}, {Qd, Qd2},
+                {O.m2l_tc_single ? 1 : 0, (O2 && O2->m2l_tc_single) ? 1 : 0}, 0};
     return tc_dispatch(O.npad, T->m2l_pairs.items.p, T->m2l_pairs.nitems, T->m2l_pairs.tgt.p, T->m2l_pairs.src.p,
                        sets, O2 ? 2 : 1, err, st);
 }
@@ -597,7 +644,8 @@ bool m2l_tc_launch(const fmm_tree* T, const Operators& O, const float* Qu, float
 using namespace pbfmm;
 extern "C" int pbfmm_selftest_m2l_tc(int nrows, int npad, const float* Q, const float* Op, float* D) {
     try {
-        if (nrows < 1 || (npad != 32 && npad != 64 && npad != 128 && npad != 160)) return PB_EINVAL;
+        int ns_, ks_;
+        if (nrows < 1 || !tc_split(npad, ns_, ks_)) return PB_EINVAL;
         cudaStream_t st = nullptr;
         fmm_tree T;
         Operators O;

@@ -320,8 +320,17 @@ std::shared_ptr<Operators> get_operators(fmm_tree* T, int kernel, double kappa, 
             }
         }
         PB_CUDA(cudaMemcpyAsync(uc2ue_prev.p, Bd.B.p, (size_t)n * n * sizeof(double), cudaMemcpyDeviceToDevice, st));
-        // M2L_l[o] = DC2DE_l K(dc of B, ue of the box at offset o)
-        if (l >= 2) {
+        // M2L_l[o] = DC2DE_l K(dc of B, ue of the box at offset o); the
+        // Laplace operators do not depend on the level (1/r scales as 2^l,
+        // the regularised pseudo-inverse as 2^-l): levels below take level 2's
+        if (l > 2 && kernel == FMM_LAPLACE) {
+            const size_t blk = (size_t)kNumOffsets * m2;
+            PB_CUDA(cudaMemcpyAsync(O->m2l.p + l * blk, O->m2l.p + 2 * blk, blk * sizeof(float),
+                                    cudaMemcpyDeviceToDevice, st));
+            if (need_fp64)
+                PB_CUDA(cudaMemcpyAsync(O->m2l_d.p + l * blk, O->m2l_d.p + 2 * blk, blk * sizeof(double),
+                                        cudaMemcpyDeviceToDevice, st));
+        } else if (l >= 2) {
             for (int o = 0; o < kNumOffsets; ++o) {
                 int ox = o / 49 - 3, oy = (o / 7) % 7 - 3, oz = o % 7 - 3;
                 if (std::abs(ox) <= 1 && std::abs(oy) <= 1 && std::abs(oz) <= 1) continue;

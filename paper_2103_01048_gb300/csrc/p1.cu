@@ -643,6 +643,8 @@ static void ensure_singular_p1(pb_mesh* M, double kappa) {
     M->sing_mode1 = mode;
 }
 
+void ensure_singular_p1_public(pb_mesh* M, double kappa) { ensure_singular_p1(M, kappa); }
+
 template <typename T>
 static void matvec_p1_t(pb_mesh* M, const Form& fm, const double* x, double* y, int precond) {
     cudaStream_t st = M->ctx->stream;

@@ -97,11 +97,12 @@ def split3_bound(npad):
     return 5 * 2.0 ** -22 + 3 * npad * 2.0 ** -23
 
 
-@pytest.mark.parametrize("npad,nrows", [(32, 130), (64, 1), (128, 257), (160, 2500)])
+@pytest.mark.parametrize("npad,nrows", [(32, 130), (64, 1), (128, 257), (160, 2500), (320, 700), (512, 300)])
 def test_tcgen05_m2l_kernel(pb, npad, nrows):
     """The tensor-core M2L kernel alone: D = Q Op^T with TF32 hi/lo splitting
     matches the FP64 product within the 3xTF32 bound, element by element
-    (ragged row tiles, several work items)."""
+    (ragged row tiles, several work items; at npad 320 and 512 the operator
+    is split into 4 x 2 and 4 x 4 parts whose inner parts add up)."""
     rng = np.random.default_rng(npad + nrows)
     Q = rng.uniform(-1, 1, (nrows, npad)).astype(np.float32)
     Op = rng.uniform(-1, 1, (npad, npad)).astype(np.float32)

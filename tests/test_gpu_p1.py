@@ -54,6 +54,25 @@ def oracle_mats():
 
 
 @pytest.mark.parametrize("name", ["sphere320", "gaussian648"])
+def test_p1_singular_blocks(pb, ctx, oracle_mats, name):
+    """The P1 singular blocks (minus their regular-rule part) of every
+    vertex-sharing pair against the oracle's (graded outer rule 5 levels
+    deep on the GPU, 6 in the oracle)."""
+    V, F, _ = oracle_mats[name]
+    mesh = pb.pb_mesh_setup(ctx, V, F, 3, 6, 32, basis=pb.PB_P1)
+    try:
+        off, ids, S = pb.pb_mesh_export_singular(ctx, mesh, EPS[2], p1=True)
+    finally:
+        pb.pb_mesh_destroy(mesh)
+    pairs = [(i, int(ids[e])) for i in range(len(F)) for e in range(off[i], off[i + 1])]
+    ref = bem_p1.pair_blocks(V, F, pairs, 3, EPS[2], minus_regular=True)
+    for op in range(4):
+        err = np.abs(S[:, op] - ref[:, op]).max() / np.abs(ref[:, op]).max()
+        print(f"P1 singular blocks {name} op {op}: max rel {err:.2e}")
+        assert err < 2e-5, op
+
+
+@pytest.mark.parametrize("name", ["sphere320", "gaussian648"])
 @pytest.mark.parametrize("form", ["direct", "exterior", "interior"])
 @pytest.mark.parametrize("prec", ["mixed", "fp64"])
 def test_p1_matvec_vs_dense(pb, ctx, oracle_mats, name, form, prec):
