@@ -206,6 +206,10 @@ __global__ void __launch_bounds__(256) k_singular_p1(long long nadj, int nt, con
         // the point sums include for it), in the same scaling
         for (int q = lane; q < rr.nq * rr.nq; q += 32) {
             const int qa = q / rr.nq, qb = q % rr.nq;
+            // a point paired with itself (identical triangles) is excluded by
+            // the point sums; here x and y are built in different frames, so
+            // their rounded difference is not exactly zero: skip by index
+            if (same && qa == qb) continue;
             const V3<T> x = (T)rr.l[qa][1] * E1 + (T)rr.l[qa][2] * E2;
             const V3<T> y = ((T)rr.l[qb][0] * Tj[0]) + ((T)rr.l[qb][1] * Tj[1]) + ((T)rr.l[qb][2] * Tj[2]);
             const V3<T> dv = x - y;
