@@ -76,6 +76,7 @@ def parse():
     ap.add_argument("--virus", action="store_true", help="virus-scale shell solve only (10M triangles, 1.6M atoms)")
     ap.add_argument("--virus-face", type=int, default=645, help="cube-sphere subdivision (12 n^2 triangles per wall)")
     ap.add_argument("--virus-atoms", type=int, default=1_600_000)
+    ap.add_argument("--sweep", action="store_true", help="p x ncrit grid of the 4M-point apply")
     ap.add_argument("--kirkwood", action="store_true",
                     help="off-centre-charge sphere refinement study (512 ... 131,072 elements)")
     return ap.parse_args()
@@ -305,8 +306,63 @@ def run_kirkwood(args):
     pb.pb_destroy(ctx)
 
 
+def run_sweep(args):
+    """The expansion orders and leaf sizes of the 4M-point FMM workload:
+    paired apply (Laplace + Yukawa SL+DL) at p = 4, 6, 8, 10 and ncrit =
+    64, 128, 256, ms per apply (median of 5 after 2 warm-ups, L2 flushed),
+    tree build and operator set-up time; one JSON line."""
+    import torch
+    import paper_2103_01048_gb300 as pb
+    x, nrm, q, d = inputs(args.n)
+    stream = torch.cuda.Stream()
+    ctx = pb.pb_create(0, stream)
+    X, Nr, Q, D = (torch.from_numpy(a).cuda() for a in (x, nrm, q, d))
+    out_l = torch.empty(args.n, device="cuda")
+    out_y = torch.empty(args.n, device="cuda")
+    flush = torch.empty(256 * 1024 * 1024 // 4, device="cuda")
+    rows = []
+    for ncrit in (64, 128, 256):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        tree = pb.fmm_tree_build(ctx, X, ncrit)
+        t_tree = (time.perf_counter() - t0) * 1e3
+        info = pb.fmm_tree_info(tree)
+        for p in (4, 6, 8, 10):
+            t0 = time.perf_counter()
+            pb.fmm_apply_pair(ctx, tree, KAPPA, p, out_l, out_y, q_lap=Q, q_yuk=Q, dip=D, src_n=Nr)
+            pb.pb_sync(ctx)
+            t_first = time.perf_counter() - t0
+            pb.fmm_apply_pair(ctx, tree, KAPPA, p, out_l, out_y, q_lap=Q, q_yuk=Q, dip=D, src_n=Nr)
+            ts = []
+            for k in range(5):
+                with torch.cuda.stream(stream):
+                    flush.fill_(float(k))
+                    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    a.record(stream)
+                    pb.fmm_apply_pair(ctx, tree, KAPPA, p, out_l, out_y, q_lap=Q, q_yuk=Q, dip=D, src_n=Nr)
+                    b.record(stream)
+                torch.cuda.synchronize()
+                ts.append(a.elapsed_time(b))
+            pb.pb_sync(ctx)
+            ms = float(np.median(ts))
+            rows.append({"p": p, "ncrit": ncrit, "ms_per_paired_apply": ms, "points_per_s": 2 * args.n / (ms * 1e-3),
+                         "first_apply_s_incl_operators": t_first, "tree_build_ms": t_tree,
+                         "boxes": info.n_box, "levels": info.n_levels, "v_pairs": info.n_v})
+            print(f"[sweep] ncrit {ncrit} p {p}: {ms:.2f} ms, first apply {t_first:.1f} s", file=sys.stderr,
+                  flush=True)
+        pb.fmm_tree_destroy(tree)
+    print(json.dumps({"metric": "FMM apply points/s over the expansion orders and leaf sizes",
+                      "unit": "points/s", "n_gpus": 1, "dtype": "f32", "data": "synthetic",
+                      "config": {"workload": f"fmm_apply_pair {args.n} bumpy-sphere points, Laplace+Yukawa "
+                                             f"(kappa {KAPPA}) SL+DL", "l2": "flushed between applies"},
+                      "rows": rows}), flush=True)
+    pb.pb_destroy(ctx)
+
+
 def main():
     args = parse()
+    if args.sweep:
+        return run_sweep(args)
     if args.virus:
         return run_virus(args)
     if args.kirkwood:
@@ -493,14 +549,16 @@ def main():
         solve = {"workload": "Born ion r=2 A, 5120 triangles, 3-pt rule, P0, tol 1e-6, eps 4/80, kappa 0.125",
                  "oracle_dG_kcal_mol": e_or, "by_p": {}}
 
-        def timed_solve(mesh, a_, q_, prec, tol, reps):
-            res, st = pb.pb_solve(ctx, mesh, a_, q_, 4.0, 80.0, 0.125, tol, 500, precision=prec)
+        def timed_solve(mesh, a_, q_, prec, tol, reps, formulation=pb.PB_FORM_DIRECT):
+            res, st = pb.pb_solve(ctx, mesh, a_, q_, 4.0, 80.0, 0.125, tol, 500, precision=prec,
+                                  formulation=formulation)
             pb.pb_result_destroy(res)                     # warm: operators, singular entries, graph
             ts = []
             for _ in range(reps):
                 torch.cuda.synchronize()
                 t0 = time.perf_counter()
-                res, st = pb.pb_solve(ctx, mesh, a_, q_, 4.0, 80.0, 0.125, tol, 500, precision=prec)
+                res, st = pb.pb_solve(ctx, mesh, a_, q_, 4.0, 80.0, 0.125, tol, 500, precision=prec,
+                                      formulation=formulation)
                 e = pb.pb_solvation_energy(ctx, res)
                 ts.append((time.perf_counter() - t0) * 1e3)
                 it, rr, _ = pb.pb_result_get(res)
@@ -537,6 +595,28 @@ def main():
             prot["fp64"]["dG_kcal_mol"])
         prot["speedup_mixed_over_fp64"] = prot["fp64"]["ms_per_mesh"] / prot["mixed"]["ms_per_mesh"]
         solve["protein"] = prot
+        # the exterior derivative formulation (Eq. lu, P1, lumped-mass
+        # preconditioner) on the same two surfaces: iterations and ms per
+        # mesh beside the direct formulation's
+        # Born's closed form for a unit charge at the centre of a sphere of
+        # radius a = 2 A: (q^2 / 2a) (1 / (eps_out (1 + kappa a)) - 1 / eps_in) C
+        born = 0.5 * (1.0 / (80.0 * (1 + 0.125 * 2.0)) - 1.0 / 4.0) / 2.0 * 332.0637
+        deriv = {"workload": "exterior derivative formulation (Eq. lu), P1, lumped-mass preconditioner, "
+                             "same meshes, p and tolerances as the direct rows",
+                 "born_closed_form_kcal_mol": born}
+        mesh = pb.pb_mesh_setup(ctx, V, F.astype(np.int32), 3, int(hp), 128, basis=pb.PB_P1)
+        for name, prec in (("mixed", pb.PB_MIXED), ("fp64", pb.PB_FP64)):
+            r = timed_solve(mesh, atoms, qa, prec, 1e-6, 3, formulation=pb.PB_FORM_EXTERIOR)
+            r["rel_dG_vs_born"] = abs(r["dG_kcal_mol"] - born) / abs(born)
+            deriv["born_" + name] = r
+        pb.pb_mesh_destroy(mesh)
+        deriv["born_direct_rel_dG_vs_born"] = abs(solve["mixed"]["dG_kcal_mol"] - born) / abs(born)
+        mesh = pb.pb_mesh_setup(ctx, Vp, Tp.astype(np.int32), 3, 6, 128, basis=pb.PB_P1)
+        deriv["protein_mixed"] = timed_solve(mesh, xyz_p, q_p, pb.PB_MIXED, 1e-5, 1, formulation=pb.PB_FORM_EXTERIOR)
+        pb.pb_mesh_destroy(mesh)
+        deriv["protein_rel_dG_exterior_P1_vs_direct_P0"] = abs(
+            deriv["protein_mixed"]["dG_kcal_mol"] - prot["mixed"]["dG_kcal_mol"]) / abs(prot["mixed"]["dG_kcal_mol"])
+        solve["derivative"] = deriv
 
     # batched binding energies: complexes -> (complex, receptor, ligand)
     # meshes solved together by pb_solve_batch vs one at a time

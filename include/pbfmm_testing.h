@@ -40,6 +40,12 @@ int64_t pbfmm_test_pool_used(int device);
  * a CUDA graph captured meanwhile keeps the value it was captured with. */
 void pbfmm_test_wait_limit(int64_t cycles);
 
+/* Stable sort of n (key, value) pairs by the low `bits` bits of the keys
+ * (1 <= bits <= 64) with the library's radix sort (the Morton-key sort of
+ * the octree build); host buffers in and out.  PB_OK or PB_EINVAL. */
+int pbfmm_test_radix_sort(const uint64_t* keys, const int32_t* vals, int64_t n, int bits, uint64_t* keys_out,
+                          int32_t* vals_out);
+
 /* D = Q Op^T for one operator through the tensor-core box-operator kernel
  * (host buffers: Q [nrows][npad], Op [npad][npad], D [nrows][npad]; npad in
  * {32, 64, 128, 160}).  PB_OK, PB_EINVAL or PB_ETIMEOUT. */

@@ -390,8 +390,22 @@ _lib.pbfmm_test_fail_alloc.argtypes = [_I64]
 _lib.pbfmm_test_fail_alloc.restype = None
 _lib.pbfmm_test_wait_limit.argtypes = [_I64]
 _lib.pbfmm_test_wait_limit.restype = None
+_lib.pbfmm_test_radix_sort.argtypes = [_P, _P, _I64, ctypes.c_int, _P, _P]
+_lib.pbfmm_test_radix_sort.restype = ctypes.c_int
 _lib.pbfmm_test_pool_used.argtypes = [ctypes.c_int]
 _lib.pbfmm_test_pool_used.restype = _I64
+
+
+def _test_radix_sort(keys, vals, bits):
+    """(sorted keys, values) by the library's stable radix sort (uint64 keys, int32 values)."""
+    k = np.ascontiguousarray(keys, np.uint64)
+    v = np.ascontiguousarray(vals, np.int32)
+    ko = np.zeros_like(k)
+    vo = np.zeros_like(v)
+    rc = _lib.pbfmm_test_radix_sort(ptr(k), ptr(v), len(k), int(bits), ptr(ko), ptr(vo))
+    if rc != PB_OK:
+        raise PBError(rc, "radix sort failed")
+    return ko, vo
 
 
 def _test_pool_used(device=0):

@@ -30,6 +30,9 @@
 
 namespace pbfmm {
 
+void radix_sort_pairs(const unsigned* keys_in, const int* vals_in, unsigned* keys_out, int* vals_out, long long n,
+                      int bits, cudaStream_t st);
+
 constexpr int kTcRows = 128;           // pairs per row tile (MMA M)
 constexpr int kTcItemPairs = 2048;     // pairs per M2L work item (one operator load each)
 constexpr int kTcSmallItemPairs = 512; // M2M / L2L / check->equivalent items: fewer pairs per operator, more CTAs
@@ -157,13 +160,9 @@ void build_m2l_pairs(fmm_tree* T) {
     std::vector<int> hidx(np);
     for (long long i = 0; i < np; ++i) hidx[i] = (int)i;
     PB_CUDA(cudaMemcpyAsync(idx.p, hidx.data(), np * sizeof(int), cudaMemcpyHostToDevice, st));
-    {
-        size_t tmp = 0;
-        cub::DeviceRadixSort::SortPairs(nullptr, tmp, key.p, key_s.p, idx.p, idx_s.p, (int)np, 0, 32, st);
-        DBuf<char> t;
-        t.alloc(std::max<size_t>(tmp, 1), st);
-        cub::DeviceRadixSort::SortPairs(t.p, tmp, key.p, key_s.p, idx.p, idx_s.p, (int)np, 0, 32, st);
-    }
+    // group by (level, offset) keeping each group in box order (stable sort;
+    // level * 343 + offset < 2^13)
+    radix_sort_pairs((const unsigned*)key.p, idx.p, (unsigned*)key_s.p, idx_s.p, np, 13, st);
     P.tgt.alloc(np, st);
     P.src.alloc(np, st);
     k_gather_int<<<div_up(np, 256), 256, 0, st>>>((int)np, idx_s.p, tgt.p, P.tgt.p);

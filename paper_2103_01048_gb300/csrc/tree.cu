@@ -14,6 +14,9 @@
 
 namespace pbfmm {
 
+void radix_sort_pairs(const uint64_t* keys_in, const int* vals_in, uint64_t* keys_out, int* vals_out, long long n,
+                      int bits, cudaStream_t st);
+
 // ---------------------------------------------------------------------------
 // bounding box
 // ---------------------------------------------------------------------------
@@ -445,12 +448,7 @@ void build_tree(fmm_tree* T, const float* src, const float* tgt) {
         keys.alloc(n, st); perm.alloc(n, st);
         k_keys<<<div_up(n, 256), 256, 0, st>>>(xyz, n, lo3[0], lo3[1], lo3[2], scale, k0.p, i0.p);
         PB_CHECK_LAUNCH();
-        size_t tmp = 0;
-        cub::DeviceRadixSort::SortPairs(nullptr, tmp, k0.p, keys.p, i0.p, perm.p, (int)n, 0, 63, st);
-        DBuf<char> t;
-        t.alloc(tmp, st);
-        cub::DeviceRadixSort::SortPairs(t.p, tmp, k0.p, keys.p, i0.p, perm.p, (int)n, 0, 63, st);
-        PB_CHECK_LAUNCH();
+        radix_sort_pairs(k0.p, i0.p, keys.p, perm.p, n, 63, st);      // stable: ties keep the input order
         pos.alloc(n, st);
         k_gather_pos<<<div_up(n, 256), 256, 0, st>>>(xyz, perm.p, n, pos.p);
         PB_CHECK_LAUNCH();

@@ -478,3 +478,21 @@ def test_deterministic_mode_vs_direct(pb, ctx, case20k, ref20k, prec, p):
         pb.pb_set_option(ctx, pb.PB_OPT_DETERMINISTIC, 0)
     assert np.array_equal(oL, oL2) and np.array_equal(oY, oY2)
     assert rel_l2(oL, ref20k[0]) < TOL and rel_l2(oY, ref20k[1]) < TOL
+
+
+@pytest.mark.parametrize("n", [1, 2, 2047, 2048, 2049, 100_003])
+def test_radix_sort_stable(pb, n):
+    """The library's radix sort (the octree's Morton-key sort) against
+    numpy's stable sort: 63-bit keys with many ties, ragged tile sizes;
+    13-bit keys (the M2L grouping)."""
+    rng = np.random.default_rng(n)
+    keys = rng.integers(0, 2 ** 63 - 1, n, dtype=np.int64).astype(np.uint64)
+    keys[rng.integers(0, n, n // 2)] = keys[0]                  # ties
+    vals = np.arange(n, dtype=np.int32)
+    ko, vo = pb._test_radix_sort(keys, vals, 63)
+    order = np.argsort(keys, kind="stable")
+    assert np.array_equal(ko, keys[order]) and np.array_equal(vo, vals[order])
+    small = rng.integers(0, 7203, n).astype(np.uint64)
+    ko, vo = pb._test_radix_sort(small, vals, 13)
+    order = np.argsort(small, kind="stable")
+    assert np.array_equal(ko, small[order]) and np.array_equal(vo, vals[order])

@@ -56,8 +56,11 @@ def oracle_mats():
 @pytest.mark.parametrize("name", ["sphere320", "gaussian648"])
 def test_p1_singular_blocks(pb, ctx, oracle_mats, name):
     """The P1 singular blocks (minus their regular-rule part) of every
-    vertex-sharing pair against the oracle's (graded outer rule 5 levels
-    deep on the GPU, 6 in the oracle)."""
+    vertex-sharing pair against the oracle's with the same graded outer rule
+    (5 levels, the GPU's FP64 rule): equal to rounding.  Against the
+    oracle's default 6 levels they differ by the rule's own convergence
+    (measured: 3.7e-6 of the largest V block, 4.4e-5 of the largest K
+    block, exactly the oracle's own 5-versus-6-level difference)."""
     V, F, _ = oracle_mats[name]
     mesh = pb.pb_mesh_setup(ctx, V, F, 3, 6, 32, basis=pb.PB_P1)
     try:
@@ -65,11 +68,14 @@ def test_p1_singular_blocks(pb, ctx, oracle_mats, name):
     finally:
         pb.pb_mesh_destroy(mesh)
     pairs = [(i, int(ids[e])) for i in range(len(F)) for e in range(off[i], off[i + 1])]
-    ref = bem_p1.pair_blocks(V, F, pairs, 3, EPS[2], minus_regular=True)
+    ref5 = bem_p1.pair_blocks(V, F, pairs, 3, EPS[2], minus_regular=True, L_outer=5)
+    ref6 = bem_p1.pair_blocks(V, F, pairs, 3, EPS[2], minus_regular=True, L_outer=6)
     for op in range(4):
-        err = np.abs(S[:, op] - ref[:, op]).max() / np.abs(ref[:, op]).max()
-        print(f"P1 singular blocks {name} op {op}: max rel {err:.2e}")
-        assert err < 2e-5, op
+        err5 = np.abs(S[:, op] - ref5[:, op]).max() / np.abs(ref5[:, op]).max()
+        err6 = np.abs(S[:, op] - ref6[:, op]).max() / np.abs(ref6[:, op]).max()
+        print(f"P1 singular blocks {name} op {op}: max rel {err5:.2e} (same rule), {err6:.2e} (6 levels)")
+        assert err5 < 1e-10, op
+        assert err6 < (1e-5 if op in (0, 2) else 1e-4), op
 
 
 @pytest.mark.parametrize("name", ["sphere320", "gaussian648"])
@@ -94,7 +100,10 @@ def test_p1_matvec_vs_dense(pb, ctx, oracle_mats, name, form, prec):
                 ref = ref / np.concatenate([lm, lm])
             err = np.linalg.norm(y - ref) / np.linalg.norm(ref)
             print(f"P1 mat-vec {name} {form} {prec} precond={precond}: rel L2 {err:.2e}")
-            assert err < (2e-5 if prec == "mixed" else 2e-6)
+            # the GPU's singular rule is 5 graded levels deep, the oracle's 6:
+            # 3.7e-6 of the V blocks, 4.4e-5 of the (smaller) K blocks, so
+            # the FP64 mat-vec agrees to a few 1e-6
+            assert err < (2e-5 if prec == "mixed" else 1e-5)
     finally:
         pb.pb_mesh_destroy(mesh)
 
