@@ -77,6 +77,8 @@ def parse():
     ap.add_argument("--virus-face", type=int, default=645, help="cube-sphere subdivision (12 n^2 triangles per wall)")
     ap.add_argument("--virus-atoms", type=int, default=1_600_000)
     ap.add_argument("--sweep", action="store_true", help="p x ncrit grid of the 4M-point apply")
+    ap.add_argument("--profile", action="store_true",
+                    help="bracket the timed steps with cudaProfilerStart/Stop (for ncu --profile-from-start off)")
     ap.add_argument("--kirkwood", action="store_true",
                     help="off-centre-charge sphere refinement study (512 ... 131,072 elements)")
     return ap.parse_args()
@@ -432,6 +434,8 @@ def main():
     torch.cuda.synchronize()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     pb.pb_profile(ctx, True)
+    if args.profile:
+        torch.cuda.cudart().cudaProfilerStart()
     with Clocks(local) as clk:
         for k in range(args.steps):
             with torch.cuda.stream(stream):
@@ -440,6 +444,8 @@ def main():
                 step()
                 ev[k][1].record(stream)
         torch.cuda.synchronize()
+    if args.profile:
+        torch.cuda.cudart().cudaProfilerStop()
     prof = pb.pb_profile_read(ctx)
     pb.pb_profile(ctx, False)
     if dist:

@@ -14,7 +14,7 @@ extern "C" {
 
 /* Runs one short microbenchmark per pipe on CUDA device `device` (about
  * 0.2 s in all; CUDA events on a private stream, one warm-up launch each)
- * and writes out[6]:
+ * and writes out[7]:
  *   out[0]  FP32 fused multiply-add, TFLOP/s (2 FLOP per FMA)
  *   out[1]  MUFU rsqrt.approx.ftz.f32, 10^12 results/s
  *   out[2]  MUFU ex2.approx.ftz.f32, 10^12 results/s
@@ -22,6 +22,8 @@ extern "C" {
  *   out[4]  tcgen05.mma kind::tf32 (M 128, N 256, operands in shared
  *           memory, FP32 accumulator in TMEM), dense TFLOP/s
  *   out[5]  the same loop with kind::f16, BF16 operands, TFLOP/s
+ *   out[6]  packed FP32 fused multiply-add (fma.rn.f32x2, two FMAs per
+ *           instruction), TFLOP/s
  * The rates hold at whatever SM clock the GPU ran (sample it alongside).
  * Returns PB_OK, PB_ECUDA, or PB_ETIMEOUT if a tensor-core wait gave up. */
 int pbfmm_measure_peaks(int device, double* out);

@@ -184,3 +184,142 @@ def energy_grad_x_fd(verts, tris, nq, atoms, charges, eps_in, eps_out, kappa, ma
         em, *_ = solve_energy(verts, tris, nq, am, charges, eps_in, eps_out, kappa, mats=mats)
         out[(k, c)] = (ep - em) / (2 * h)
     return out
+
+
+# ---------------------------------------------------------------------------
+# Matrix-free solve (sizes beyond the dense LU)
+# ---------------------------------------------------------------------------
+
+def vertex_sharing_pairs(tris):
+    """All ordered pairs (i, j) of triangles sharing at least one vertex
+    (i == j included), as two index arrays."""
+    F = np.asarray(tris)
+    from collections import defaultdict
+    inc = defaultdict(list)
+    for t, f in enumerate(F):
+        for v in f:
+            inc[int(v)].append(t)
+    I, J = [], []
+    for i, f in enumerate(F):
+        js = sorted(set(t for v in f for t in inc[int(v)]))
+        I += [i] * len(js)
+        J += js
+    return np.array(I), np.array(J)
+
+
+def singular_corrections(verts, tris, nq, kappa, L_outer=6):
+    """Sparse P0 corrections of the vertex-sharing pairs, one scipy CSR
+    matrix per kernel (V_L, K_L, V_Y, K_Y): the semi-analytic entry minus the
+    same entry under the nq x nq regular product rule (what the point sums
+    already hold).  A P0 entry is the sum of the pair's P1 blocks over the
+    local vertices (the barycentric coordinates add up to one), so the
+    per-pair routine of the P1 oracle provides both."""
+    import scipy.sparse as sp
+    from .bem_p1 import pair_blocks
+    I, J = vertex_sharing_pairs(tris)
+    B = pair_blocks(verts, tris, list(zip(I, J)), nq, kappa, minus_regular=True, L_outer=L_outer)
+    nt = len(tris)
+    return [sp.csr_matrix((B[:, op].sum(axis=(1, 2)), (I, J)), shape=(nt, nt)) for op in range(4)]
+
+
+def matvec_free(verts, tris, nq, kappa, eps_in, eps_out, corr=None):
+    """The direct-formulation matrix of Eq. direct as a function x -> A x:
+    point sums of the kernels over all quadrature-point pairs (FP64 direct
+    sums, r = 0 excluded) tested with the P0 functions, plus the sparse
+    singular corrections, plus the mass terms."""
+    from .kernels import YUKAWA
+    P, w, nrm, tri = quad_points(verts, tris, nq)
+    _, area = geometry(verts, tris)
+    nt = len(tris)
+    if corr is None:
+        corr = singular_corrections(verts, tris, nq, kappa)
+    cVL, cKL, cVY, cKY = corr
+    e12 = eps_in / eps_out
+
+    def test(f):
+        out = np.zeros(nt)
+        np.add.at(out, tri, w * f)
+        return out
+
+    def A(x):
+        phi, dphi = x[:nt], x[nt:]
+        # V_L dphi and K_L phi from one Laplace sum, V_Y and K_Y from one Yukawa sum
+        pL = direct_sum(LAPLACE, 0.0, P, q=-w * dphi[tri], dip=w * phi[tri], src_n=nrm)
+        pY = direct_sum(YUKAWA, kappa, P, q=e12 * w * dphi[tri], dip=-w * phi[tri], src_n=nrm)
+        r1 = test(pL) + cKL @ phi - cVL @ dphi + 0.5 * area * phi
+        r2 = test(pY) - cKY @ phi + e12 * (cVY @ dphi) + 0.5 * area * phi
+        return np.concatenate([r1, r2])
+    return A
+
+
+def gmres(A, b, tol=1e-10, max_iter=500, M=None):
+    """Unrestarted GMRES from x0 = 0 (Arnoldi with modified Gram-Schmidt,
+    Givens rotations), left preconditioner M (a function) if given; stops at
+    ||M(b - A x)|| <= tol ||M b||.  Returns (x, iterations, relative residual)."""
+    Mf = M if M is not None else (lambda v: v)
+    r0 = Mf(b)
+    beta = np.linalg.norm(r0)
+    n = len(b)
+    if beta == 0.0:
+        return np.zeros(n), 0, 0.0
+    Vb = [r0 / beta]
+    H = np.zeros((max_iter + 1, max_iter))
+    cs, sn = np.zeros(max_iter), np.zeros(max_iter)
+    g = np.zeros(max_iter + 1)
+    g[0] = beta
+    k = 0
+    for k in range(max_iter):
+        w_ = Mf(A(Vb[k]))
+        for i in range(k + 1):
+            H[i, k] = np.dot(Vb[i], w_)
+            w_ = w_ - H[i, k] * Vb[i]
+        H[k + 1, k] = np.linalg.norm(w_)
+        for i in range(k):
+            a_, b_ = H[i, k], H[i + 1, k]
+            H[i, k], H[i + 1, k] = cs[i] * a_ + sn[i] * b_, -sn[i] * a_ + cs[i] * b_
+        rr = np.hypot(H[k, k], H[k + 1, k])
+        cs[k], sn[k] = H[k, k] / rr, H[k + 1, k] / rr
+        H[k, k], H[k + 1, k] = rr, 0.0
+        g[k + 1] = -sn[k] * g[k]
+        g[k] = cs[k] * g[k]
+        if H[k + 1, k] == 0.0 and rr == 0.0:
+            break
+        Vb.append(w_ / np.linalg.norm(w_) if np.linalg.norm(w_) > 0 else w_)
+        if abs(g[k + 1]) <= tol * beta:
+            k += 1
+            break
+    else:
+        k = max_iter
+    y = np.linalg.solve(np.triu(H[:k, :k]), g[:k])
+    x = np.zeros(n)
+    for i in range(k):
+        x += y[i] * Vb[i]
+    return x, k, abs(g[k]) / beta
+
+
+def solve_energy_free(verts, tris, nq, atoms, charges, eps_in, eps_out, kappa, tol=1e-10, max_iter=500):
+    """Eq. direct by matrix-free GMRES (direct sums, exact singular
+    corrections), preconditioned by the per-triangle 2x2 blocks of the
+    diagonal entries; then Eq. phi_reac and Eq. energy.  Returns
+    (energy, phi, dphi, iterations, residual)."""
+    nt = len(tris)
+    corr = singular_corrections(verts, tris, nq, kappa)
+    A = matvec_free(verts, tris, nq, kappa, eps_in, eps_out, corr)
+    _, area = geometry(verts, tris)
+    e12 = eps_in / eps_out
+    d11 = corr[1].diagonal() + 0.5 * area
+    d12 = -corr[0].diagonal()
+    d21 = -corr[3].diagonal() + 0.5 * area
+    d22 = e12 * corr[2].diagonal()
+    # (the self corrections stand in for the diagonal entries: only a
+    # preconditioner, it does not change the solution)
+    det = d11 * d22 - d12 * d21
+
+    def M(v):
+        a, c = v[:nt], v[nt:]
+        return np.concatenate([(d22 * a - d12 * c) / det, (-d21 * a + d11 * c) / det])
+    b = np.concatenate([rhs(verts, tris, nq, atoms, charges, eps_in), np.zeros(nt)])
+    x, it, res = gmres(A, b, tol=tol, max_iter=max_iter, M=M)
+    phi, dphi = x[:nt], x[nt:]
+    pr = phi_reac(verts, tris, nq, phi, dphi, atoms)
+    return solvation_energy(charges, pr), phi, dphi, it, res

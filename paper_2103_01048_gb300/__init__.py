@@ -443,14 +443,14 @@ def _selftest_m2l_tc(Q, Op):
 _lib.pbfmm_measure_peaks.argtypes = [ctypes.c_int, _P]
 _lib.pbfmm_measure_peaks.restype = ctypes.c_int
 PEAK_KEYS = ("fp32_fma_tflops", "mufu_rsqrt_tops", "mufu_ex2_tops", "fp64_fma_tflops", "tf32_tc_tflops",
-             "bf16_tc_tflops")
+             "bf16_tc_tflops", "fp32x2_fma_tflops")
 
 
 def measure_peaks(device=0):
-    """Measured rates of the FP32 FMA pipe, the MUFU rsqrt and ex2 units, FP64
-    FMA and the tcgen05 TF32 / BF16 tensor cores on `device` (dict, units in
-    the key names: TFLOP/s or 10^12 results/s)."""
-    out = np.zeros(6)
+    """Measured rates of the FP32 FMA pipe (scalar and packed f32x2), the MUFU
+    rsqrt and ex2 units, FP64 FMA and the tcgen05 TF32 / BF16 tensor cores on
+    `device` (dict, units in the key names: TFLOP/s or 10^12 results/s)."""
+    out = np.zeros(7)
     rc = _lib.pbfmm_measure_peaks(int(device), ptr(out))
     if rc != PB_OK:
         raise PBError(rc, "peak microbenchmarks failed")

@@ -37,6 +37,34 @@ __global__ void __launch_bounds__(512) k_peak_ffma(long long iters, float b, flo
     if (s == -1.0f) out[0] = s;      // never true: keeps the chains live
 }
 
+// packed FP32 (two lanes per register pair): fma.rn.f32x2
+__device__ __forceinline__ unsigned long long ffma2_u(unsigned long long a, unsigned long long b,
+                                                      unsigned long long c) {
+    unsigned long long d;
+    asm volatile("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ unsigned long long pack2(float x, float y) {
+    return (unsigned long long)__float_as_uint(x) | ((unsigned long long)__float_as_uint(y) << 32);
+}
+
+__global__ void __launch_bounds__(512) k_peak_ffma2(long long iters, float b, float c, float* out) {
+    unsigned long long a[kChains / 2];
+    const unsigned long long bb = pack2(b, b), cc = pack2(c, c);
+#pragma unroll
+    for (int j = 0; j < kChains / 2; ++j) a[j] = pack2(1.0f + 1e-3f * (threadIdx.x + j), 1.0f + 2e-3f * j);
+    for (long long it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int u = 0; u < 16; ++u)
+#pragma unroll
+            for (int j = 0; j < kChains / 2; ++j) a[j] = ffma2_u(a[j], bb, cc);
+    }
+    float s = 0.f;
+#pragma unroll
+    for (int j = 0; j < kChains / 2; ++j) s += __uint_as_float((unsigned)a[j]) + __uint_as_float((unsigned)(a[j] >> 32));
+    if (s == -1.0f) out[0] = s;
+}
+
 __global__ void __launch_bounds__(512) k_peak_dfma(long long iters, double b, double c, double* out) {
     double a[kChains];
 #pragma unroll
@@ -246,6 +274,10 @@ extern "C" int pbfmm_measure_peaks(int device, double* out) {
             out[4 + bf] = 2.0 * 128 * kPkN * k * kPkBatch * nb * sms / t * 1e-12;   // TFLOP/s
         }
         int herr = 0;
+        // packed FP32: the same FLOPs per thread in half the instructions
+        t = timed([&](bool w) { k_peak_ffma2<<<blocks, threads, 0, st>>>(w ? it_f / 10 : it_f, 0.999f, 1e-3f, fo); });
+        PB_CHECK_LAUNCH();
+        out[6] = 2.0 * nthreads * per_iter * it_f / t * 1e-12;            // FP32 TFLOP/s, f32x2 FMA
         PB_CUDA(cudaMemcpy(&herr, err, sizeof(int), cudaMemcpyDeviceToHost));
         cudaFree(fo);
         cudaFree(dof);

@@ -57,7 +57,9 @@ def oracle_mats():
 def test_p1_singular_blocks(pb, ctx, oracle_mats, name):
     """The P1 singular blocks (minus their regular-rule part) of every
     vertex-sharing pair against the oracle's with the same graded outer rule
-    (5 levels, the GPU's FP64 rule): equal to rounding.  Against the
+    (5 levels, the GPU's FP64 rule): the Laplace blocks equal to rounding;
+    the Yukawa blocks add the smooth remainder, which the GPU integrates with
+    a 2-level rule (measured 5e-7 of the largest block).  Against the
     oracle's default 6 levels they differ by the rule's own convergence
     (measured: 3.7e-6 of the largest V block, 4.4e-5 of the largest K
     block, exactly the oracle's own 5-versus-6-level difference)."""
@@ -74,7 +76,7 @@ def test_p1_singular_blocks(pb, ctx, oracle_mats, name):
         err5 = np.abs(S[:, op] - ref5[:, op]).max() / np.abs(ref5[:, op]).max()
         err6 = np.abs(S[:, op] - ref6[:, op]).max() / np.abs(ref6[:, op]).max()
         print(f"P1 singular blocks {name} op {op}: max rel {err5:.2e} (same rule), {err6:.2e} (6 levels)")
-        assert err5 < 1e-10, op
+        assert err5 < (1e-10 if op in (0, 1) else 2e-6), op
         assert err6 < (1e-5 if op in (0, 2) else 1e-4), op
 
 

@@ -203,3 +203,16 @@ def test_born_ion_golden_file():
     assert abs(g["born_closed_form_kcal_mol"] - born) < 1e-12
     rel = abs(g["energy_kcal_mol"] - born) / abs(born)
     assert 1e-4 < rel < 2e-3
+
+
+@pytest.mark.slow
+def test_matrix_free_gmres_matches_dense_lu():
+    """The matrix-free FP64 GMRES of the oracle (direct point sums, exact
+    singular corrections; for sizes beyond the dense LU) gives the dense LU's
+    energy on an off-centre charge in a 320-triangle sphere."""
+    V, F = synthetic.icosphere(2, 2.0)
+    atoms, q = np.array([[0.3, 0.2, -0.1]]), np.array([1.0])
+    e_lu, *_ = bem.solve_energy(V, F, 3, atoms, q, 4.0, 80.0, 0.125)
+    e_f, _, _, it, res = bem.solve_energy_free(V, F, 3, atoms, q, 4.0, 80.0, 0.125)
+    assert res <= 1e-10 and it < 100
+    assert abs(e_f - e_lu) < 1e-9 * abs(e_lu)
