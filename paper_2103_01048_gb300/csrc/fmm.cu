@@ -1143,326 +1143,11 @@ static void apply_t(fmm_tree* Tr, const Operators& O, double kappa_d, const In* 
     ph.reset();
 }
 
-// ---------------------------------------------------------------------------
-// packed FP32: two targets per thread in the two halves of 64-bit registers,
-// add / sub / mul / fma .rn.f32x2 (one instruction for both targets); the
-// MUFU reciprocal square root and exponential stay per target
-// ---------------------------------------------------------------------------
-typedef unsigned long long f32x2;
-__device__ __forceinline__ f32x2 x2_add(f32x2 a, f32x2 b) {
-    f32x2 d;
-    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-    return d;
-}
-__device__ __forceinline__ f32x2 x2_sub(f32x2 a, f32x2 b) {
-    f32x2 d;
-    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-    return d;
-}
-__device__ __forceinline__ f32x2 x2_mul(f32x2 a, f32x2 b) {
-    f32x2 d;
-    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-    return d;
-}
-__device__ __forceinline__ f32x2 x2_fma(f32x2 a, f32x2 b, f32x2 c) {
-    f32x2 d;
-    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-    return d;
-}
-__device__ __forceinline__ f32x2 x2_pack(float lo, float hi) {
-    f32x2 d;
-    asm("mov.b64 %0, {%1, %2};" : "=l"(d) : "f"(lo), "f"(hi));
-    return d;
-}
-__device__ __forceinline__ float x2_lo(f32x2 a) { return __uint_as_float((unsigned)a); }
-__device__ __forceinline__ float x2_hi(f32x2 a) { return __uint_as_float((unsigned)(a >> 32)); }
-template <bool GUARD>
-__device__ __forceinline__ f32x2 x2_rsqrt(f32x2 a) {
-    const float l = x2_lo(a), h = x2_hi(a);
-    if (GUARD) return x2_pack(l > 0.f ? rsqrt_t<float>(l) : 0.f, h > 0.f ? rsqrt_t<float>(h) : 0.f);
-    return x2_pack(rsqrt_t<float>(l), rsqrt_t<float>(h));
-}
-__device__ __forceinline__ f32x2 x2_exp2(f32x2 a) {
-    return x2_pack(exp2_t<float>(x2_lo(a)), exp2_t<float>(x2_hi(a)));
-}
-
-// interact_pair for two targets at once (the source's values duplicated in
-// both halves): the same grouping of the arithmetic
-template <bool DL, bool GUARD>
-__device__ __forceinline__ void interact_pair_x2(f32x2 dx, f32x2 dy, f32x2 dz, f32x2 qL, f32x2 qY, f32x2 mx,
-                                                 f32x2 my, f32x2 mz, f32x2 kap, f32x2 kl2, f32x2 one, f32x2& potL,
-                                                 f32x2& potY) {
-    const f32x2 r2 = x2_fma(dx, dx, x2_fma(dy, dy, x2_mul(dz, dz)));
-    const f32x2 rinv = x2_rsqrt<GUARD>(r2);
-    const f32x2 r = x2_mul(r2, rinv);
-    const f32x2 er = x2_mul(x2_exp2(x2_mul(kl2, r)), rinv);        // e^{-kr} / r
-    if (DL) {
-        const f32x2 rinv2 = x2_mul(rinv, rinv);
-        const f32x2 u = x2_fma(kap, r, one);
-        const f32x2 w = x2_mul(x2_fma(dx, mx, x2_fma(dy, my, x2_mul(dz, mz))), rinv2);
-        potL = x2_fma(rinv, x2_add(w, qL), potL);
-        potY = x2_fma(er, x2_fma(w, u, qY), potY);
-    } else {
-        potL = x2_fma(rinv, qL, potL);
-        potY = x2_fma(er, qY, potY);
-    }
-}
-
-// The paired leaf kernel (P2P + M2P + L2P, Laplace and Yukawa) in FP32
-// without target-normal derivatives, with the arithmetic of each thread's
-// 2 NP targets in packed pairs.  Sources are staged in shared memory with
-// every value duplicated, so that each packed operand is one 64-bit load.
-template <bool DL, int NP, int PART>
-__global__ void __launch_bounds__(128) k_leaf_pair_x2(const int* __restrict__ leaves, int nleaf,
-                                                      const int* __restrict__ tb, const int* __restrict__ te,
-                                                      const int* __restrict__ sb, const int* __restrict__ se,
-                                                      const int* __restrict__ U_off, const int* __restrict__ U_ids,
-                                                      const int* __restrict__ W_off, const int* __restrict__ W_ids,
-                                                      const int* __restrict__ level,
-                                                      const double4* __restrict__ center,
-                                                      const float4* __restrict__ tpos, const float4* __restrict__ sq,
-                                                      const float4* __restrict__ sm, const float* __restrict__ QuL,
-                                                      const float* __restrict__ QdL, const float* __restrict__ QuY,
-                                                      const float* __restrict__ QdY, const float4* __restrict__ surf,
-                                                      int ne, int npad, float kappa, float* __restrict__ potL_out,
-                                                      float* __restrict__ potY_out) {
-    constexpr int CH = 128;
-    constexpr int NT = 2 * NP;
-    // per source: {x, y}, {z, qL}, {mx, my}, {mz, qY}, each value in both halves
-    __shared__ ulonglong2 s_src[CH][4];
-    __shared__ float s_red[2][NT * CH];
-    const int li = blockIdx.x;
-    if (li >= nleaf) return;
-    const int b = leaves[li];
-    const int t0 = tb[b], t1 = te[b];
-    int slots = CH;
-    while (slots > 8 && NT * (slots / 2) >= t1 - t0) slots /= 2;
-    const int G = CH / slots;
-    const int tloc = threadIdx.x % slots, g = threadIdx.x / slots;
-    const int nw = W_off[b + 1] - W_off[b];
-    const int nsrcbox = nw + (level[b] >= 2 ? 1 : 0);
-    const f32x2 kap = x2_pack(kappa, kappa), kl2 = x2_pack(-kappa * float(kLog2E), -kappa * float(kLog2E));
-    const f32x2 one = x2_pack(1.f, 1.f);
-    for (int tc = t0; tc < t1; tc += NT * slots) {
-        int ti[NT];
-        float4 xt[NT];
-#pragma unroll
-        for (int u = 0; u < NT; ++u) {
-            ti[u] = tc + tloc + u * slots;
-            xt[u] = ti[u] < t1 ? tpos[ti[u]] : make_float4(0, 0, 0, 0);
-        }
-        f32x2 X[NP], Y[NP], Z[NP], pL[NP], pY[NP];
-#pragma unroll
-        for (int v = 0; v < NP; ++v) {
-            X[v] = x2_pack(xt[2 * v].x, xt[2 * v + 1].x);
-            Y[v] = x2_pack(xt[2 * v].y, xt[2 * v + 1].y);
-            Z[v] = x2_pack(xt[2 * v].z, xt[2 * v + 1].z);
-            pL[v] = pY[v] = 0ull;
-        }
-        // P2P
-        for (int ui = U_off[b]; PART != 2 && ui < U_off[b + 1]; ++ui) {
-            const int a = U_ids[ui];
-            const int j0 = sb[a], j1 = se[a];
-            for (int jc = j0; jc < j1; jc += CH) {
-                const int j = jc + threadIdx.x;
-                __syncthreads();
-                if (j < j1) {
-                    const float4 q = sq[j], m = sm[j];
-                    s_src[threadIdx.x][0] = make_ulonglong2(x2_pack(q.x, q.x), x2_pack(q.y, q.y));
-                    s_src[threadIdx.x][1] = make_ulonglong2(x2_pack(q.z, q.z), x2_pack(q.w, q.w));
-                    s_src[threadIdx.x][2] = make_ulonglong2(x2_pack(m.x, m.x), x2_pack(m.y, m.y));
-                    s_src[threadIdx.x][3] = make_ulonglong2(x2_pack(m.z, m.z), x2_pack(m.w, m.w));
-                }
-                __syncthreads();
-                const int cnt = min(CH, j1 - jc);
-                const int per = (cnt + G - 1) / G;
-                const int k0 = g * per, k1 = min(cnt, k0 + per);
-                if (a == b) {
-#pragma unroll 2
-                    for (int k = k0; k < k1; ++k) {
-                        const ulonglong2 A = s_src[k][0], B = s_src[k][1];
-                        const ulonglong2 C = DL ? s_src[k][2] : make_ulonglong2(0, 0), D = s_src[k][3];
-#pragma unroll
-                        for (int v = 0; v < NP; ++v)
-                            interact_pair_x2<DL, true>(x2_sub(X[v], A.x), x2_sub(Y[v], A.y), x2_sub(Z[v], B.x), B.y,
-                                                       D.y, C.x, C.y, D.x, kap, kl2, one, pL[v], pY[v]);
-                    }
-                } else {
-#pragma unroll 4
-                    for (int k = k0; k < k1; ++k) {
-                        const ulonglong2 A = s_src[k][0], B = s_src[k][1];
-                        const ulonglong2 C = DL ? s_src[k][2] : make_ulonglong2(0, 0), D = s_src[k][3];
-#pragma unroll
-                        for (int v = 0; v < NP; ++v)
-                            interact_pair_x2<DL, false>(x2_sub(X[v], A.x), x2_sub(Y[v], A.y), x2_sub(Z[v], B.x), B.y,
-                                                        D.y, C.x, C.y, D.x, kap, kl2, one, pL[v], pY[v]);
-                    }
-                }
-            }
-        }
-        // M2P (W list) and L2P (own downward equivalent): monopole equivalent densities
-        for (int wi = 0; PART != 1 && wi < nsrcbox; ++wi) {
-            const int a = (wi < nw) ? W_ids[W_off[b] + wi] : b;
-            const float* QL = (wi < nw) ? QuL : QdL;
-            const float* QY = (wi < nw) ? QuY : QdY;
-            const double4 ca = center[a];
-            const float alpha = float(wi < nw ? kAlphaInner : kAlphaOuter) * (float)ca.w;
-            f32x2 RX[NP], RY[NP], RZ[NP];
-#pragma unroll
-            for (int v = 0; v < NP; ++v) {
-                RX[v] = x2_pack((float)((double)xt[2 * v].x - ca.x), (float)((double)xt[2 * v + 1].x - ca.x));
-                RY[v] = x2_pack((float)((double)xt[2 * v].y - ca.y), (float)((double)xt[2 * v + 1].y - ca.y));
-                RZ[v] = x2_pack((float)((double)xt[2 * v].z - ca.z), (float)((double)xt[2 * v + 1].z - ca.z));
-            }
-            for (int jc = 0; jc < ne; jc += CH) {
-                const int j = jc + threadIdx.x;
-                __syncthreads();
-                if (j < ne) {
-                    const float4 sf = surf[j];
-                    const float sx = alpha * sf.x, sy = alpha * sf.y, sz = alpha * sf.z;
-                    const float ql = QL[(size_t)a * npad + j], qy = QY[(size_t)a * npad + j];
-                    s_src[threadIdx.x][0] = make_ulonglong2(x2_pack(sx, sx), x2_pack(sy, sy));
-                    s_src[threadIdx.x][1] = make_ulonglong2(x2_pack(sz, sz), x2_pack(ql, ql));
-                    s_src[threadIdx.x][3] = make_ulonglong2(0ull, x2_pack(qy, qy));
-                }
-                __syncthreads();
-                const int cnt = min(CH, ne - jc);
-                const int per = (cnt + G - 1) / G;
-                const int k0 = g * per, k1 = min(cnt, k0 + per);
-#pragma unroll 4
-                for (int k = k0; k < k1; ++k) {
-                    const ulonglong2 A = s_src[k][0], B = s_src[k][1];
-                    const f32x2 qy = s_src[k][3].y;
-#pragma unroll
-                    for (int v = 0; v < NP; ++v)
-                        interact_pair_x2<false, false>(x2_sub(RX[v], A.x), x2_sub(RY[v], A.y), x2_sub(RZ[v], B.x),
-                                                       B.y, qy, 0ull, 0ull, 0ull, kap, kl2, one, pL[v], pY[v]);
-                }
-            }
-        }
-        // combine the G partial sums of each target
-        __syncthreads();
-#pragma unroll
-        for (int v = 0; v < NP; ++v) {
-            s_red[0][(2 * v) * CH + threadIdx.x] = x2_lo(pL[v]);
-            s_red[0][(2 * v + 1) * CH + threadIdx.x] = x2_hi(pL[v]);
-            s_red[1][(2 * v) * CH + threadIdx.x] = x2_lo(pY[v]);
-            s_red[1][(2 * v + 1) * CH + threadIdx.x] = x2_hi(pY[v]);
-        }
-        __syncthreads();
-        if (g == 0) {
-#pragma unroll
-            for (int u = 0; u < NT; ++u) {
-                float a0 = 0, a1 = 0;
-                for (int q = 0; q < G; ++q) {
-                    const int o = u * CH + tloc + q * slots;
-                    a0 += s_red[0][o];
-                    a1 += s_red[1][o];
-                }
-                if (ti[u] < t1) {
-                    if (PART == 2) {
-                        potL_out[ti[u]] += a0 * float(kInv4PiD);
-                        potY_out[ti[u]] += a1 * float(kInv4PiD);
-                    } else {
-                        potL_out[ti[u]] = a0 * float(kInv4PiD);
-                        potY_out[ti[u]] = a1 * float(kInv4PiD);
-                    }
-                }
-            }
-        }
-    }
-}
-
-constexpr int kLeafPackedPairs = 1;   // packed target pairs per thread of k_leaf_pair_x2
-
-// P2M / P2L check potentials of the paired apply in FP32 with packed pairs:
-// each of the npad / 2 threads evaluates check points i and i + npad / 2.
-template <bool DL>
-__global__ void __launch_bounds__(256) k_p2check_pair_x2(int nbox, const int* __restrict__ boxes, int mode,
-                                                         const double4* __restrict__ center,
-                                                         const int* __restrict__ sb, const int* __restrict__ se,
-                                                         const int* __restrict__ X, const int* __restrict__ X_n,
-                                                         const float4* __restrict__ sq, const float4* __restrict__ sm,
-                                                         const float4* __restrict__ surf, int ne, int npad,
-                                                         float kappa, float* __restrict__ chkL,
-                                                         float* __restrict__ chkY) {
-    __shared__ ulonglong2 s_src[256][4];
-    const int CH = blockDim.x;                       // npad / 2
-    const int bi = blockIdx.x;
-    if (bi >= nbox) return;
-    const int b = boxes[bi];
-    const double4 c = center[b];
-    const float alpha = float(mode == 0 ? kAlphaOuter : kAlphaInner) * (float)c.w;
-    const int i0 = threadIdx.x, i1 = threadIdx.x + CH;
-    const float4 s0 = i0 < ne ? surf[i0] : make_float4(0, 0, 0, 0);
-    const float4 s1 = i1 < ne ? surf[i1] : make_float4(0, 0, 0, 0);
-    const f32x2 PX = x2_pack(alpha * s0.x, alpha * s1.x), PY = x2_pack(alpha * s0.y, alpha * s1.y);
-    const f32x2 PZ = x2_pack(alpha * s0.z, alpha * s1.z);
-    f32x2 aL = 0ull, aY = 0ull;
-    const f32x2 kap = x2_pack(kappa, kappa), kl2 = x2_pack(-kappa * float(kLog2E), -kappa * float(kLog2E));
-    const f32x2 one = x2_pack(1.f, 1.f);
-    // sources: B's own (P2M) or those of the X-list boxes (P2L), the boxes
-    // concatenated into full chunks by a uniform cursor over their ranges
-    __shared__ int s_xb[kXCap], s_xn[kXCap];
-    const int nlist = (mode == 0) ? 1 : X_n[b];
-    for (int k = threadIdx.x; k < nlist; k += CH) {       // CH may be below the X-list capacity
-        const int a = (mode == 0) ? b : X[(long long)b * kXCap + k];
-        s_xb[k] = sb[a];
-        s_xn[k] = se[a] - sb[a];
-    }
-    int ui = 0, off = 0;
-    while (ui < nlist) {
-        __syncthreads();
-        int filled = 0;
-        while (filled < CH && ui < nlist) {
-            const int n = s_xn[ui];
-            const int m = min(CH - filled, n - off);
-            const int t = threadIdx.x - filled;
-            if (t >= 0 && t < m) {
-                const int j = s_xb[ui] + off + t;
-                const float4 v = sq[j], mm = sm[j];
-                const float x = (float)((double)v.x - c.x), y = (float)((double)v.y - c.y);
-                const float z = (float)((double)v.z - c.z);
-                s_src[threadIdx.x][0] = make_ulonglong2(x2_pack(x, x), x2_pack(y, y));
-                s_src[threadIdx.x][1] = make_ulonglong2(x2_pack(z, z), x2_pack(v.w, v.w));
-                s_src[threadIdx.x][2] = make_ulonglong2(x2_pack(mm.x, mm.x), x2_pack(mm.y, mm.y));
-                s_src[threadIdx.x][3] = make_ulonglong2(x2_pack(mm.z, mm.z), x2_pack(mm.w, mm.w));
-            }
-            filled += m;
-            off += m;
-            if (off >= n) { ++ui; off = 0; }
-        }
-        __syncthreads();
-#pragma unroll 4
-        for (int t = 0; t < filled; ++t) {
-            const ulonglong2 A = s_src[t][0], B = s_src[t][1];
-            const ulonglong2 C = DL ? s_src[t][2] : make_ulonglong2(0, 0), D = s_src[t][3];
-            interact_pair_x2<DL, false>(x2_sub(PX, A.x), x2_sub(PY, A.y), x2_sub(PZ, B.x), B.y, D.y, C.x, C.y, D.x,
-                                        kap, kl2, one, aL, aY);
-        }
-    }
-    const float f = float(kInv4PiD);
-    chkL[(long long)b * npad + i0] = i0 < ne ? x2_lo(aL) * f : 0.f;
-    chkY[(long long)b * npad + i0] = i0 < ne ? x2_lo(aY) * f : 0.f;
-    chkL[(long long)b * npad + i1] = i1 < ne ? x2_hi(aL) * f : 0.f;
-    chkY[(long long)b * npad + i1] = i1 < ne ? x2_hi(aY) * f : 0.f;
-}
-
 // ---- paired apply: Laplace (operators OL) and Yukawa (OY) in one traversal
 template <typename T, bool DL>
 static void launch_p2check_pair(cudaStream_t st, int nbox, const int* boxes, int mode, fmm_tree* Tr, Work<T>& WL,
                                 Work<T>& WY, const Operators& O, T kappa) {
     if (nbox <= 0) return;
-    if constexpr (std::is_same<T, float>::value) {
-        if (O.npad % 2 == 0 && O.npad / 2 <= 256) {
-            k_p2check_pair_x2<DL><<<nbox, O.npad / 2, 0, st>>>(nbox, boxes, mode, Tr->center.p, Tr->sb.p, Tr->se.p,
-                                                               Tr->X.p, Tr->X_n.p, WL.sq.p, WL.sm.p,
-                                                               (const float4*)O.surf_f.p, O.ne, O.npad, kappa,
-                                                               WL.chk.p, WY.chk.p);
-            PB_CHECK_LAUNCH();
-            return;
-        }
-    }
     if (O.npad <= 256)
         k_p2check_pair<T, DL, 1><<<nbox, O.npad, 0, st>>>(nbox, boxes, mode, Tr->center.p, Tr->sb.p, Tr->se.p,
                                                           Tr->X.p, Tr->X_n.p, WL.sq.p, WL.sm.p,
@@ -1482,14 +1167,6 @@ static void launch_leaf_pair(cudaStream_t st, fmm_tree* Tr, Work<T>& WL, Work<T>
     const float4* tpos = Tr->same ? Tr->pos_s.p : Tr->pos_t.p;
     const int* tb = Tr->same ? Tr->sb.p : Tr->tb.p;
     const int* te = Tr->same ? Tr->se.p : Tr->te.p;
-    if constexpr (std::is_same<T, float>::value && !DN) {
-        k_leaf_pair_x2<DL, kLeafPackedPairs, PART><<<Tr->n_tleaf, 128, 0, st>>>(
-            Tr->leaf_ids.p, Tr->n_tleaf, tb, te, Tr->sb.p, Tr->se.p, Tr->U_off.p, Tr->U_ids.p, Tr->W_off.p,
-            Tr->W_ids.p, Tr->level.p, Tr->center.p, tpos, WL.sq.p, WL.sm.p, WL.Qu.p, WL.Qd.p, WY.Qu.p, WY.Qd.p,
-            (const float4*)O.surf_f.p, O.ne, O.npad, kappa, WL.pot.p, WY.pot.p);
-        PB_CHECK_LAUNCH();
-        return;
-    }
     constexpr int NT = 2;
     k_leaf_pair<T, DL, DN, NT, PART><<<Tr->n_tleaf, 128, 0, st>>>(
         Tr->leaf_ids.p, Tr->n_tleaf, tb, te, Tr->sb.p, Tr->se.p, Tr->U_off.p, Tr->U_ids.p, Tr->W_off.p, Tr->W_ids.p,

@@ -4,7 +4,9 @@
 // root and base-2 exponential), by FP64 arithmetic (the all-FP64 path), or
 // by the tensor cores (box operators: tcgen05 kind::tf32).  The BF16
 // tensor-core rate is measured with the same loop to compare this method
-// with a library GEMM's measured rate.
+// with a library GEMM's measured rate, and the packed FP32 FMA
+// (fma.rn.f32x2, two FMAs per instruction) to see whether packing raises
+// the FP32 rate or only halves the instructions.
 //
 // Each ALU kernel runs independent dependency chains in every thread (enough
 // of them to hide the pipe's latency), unrolled so that loop overhead takes
