@@ -48,5 +48,8 @@ def lib():
         L.or_pair_p1.argtypes = [P, P, P, ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                  ctypes.c_int, P]
         L.or_pair_p1.restype = ctypes.c_int
+        L.or_corrections_p0.argtypes = [ctypes.c_long, P, ctypes.c_long, P, ctypes.c_long, P, P, ctypes.c_int,
+                                        ctypes.c_double, ctypes.c_int, ctypes.c_int, ctypes.c_int, P]
+        L.or_corrections_p0.restype = ctypes.c_int
         _lib = L
     return _lib

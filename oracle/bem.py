@@ -209,17 +209,21 @@ def vertex_sharing_pairs(tris):
 
 def singular_corrections(verts, tris, nq, kappa, L_outer=6):
     """Sparse P0 corrections of the vertex-sharing pairs, one scipy CSR
-    matrix per kernel (V_L, K_L, V_Y, K_Y): the semi-analytic entry minus the
-    same entry under the nq x nq regular product rule (what the point sums
-    already hold).  A P0 entry is the sum of the pair's P1 blocks over the
-    local vertices (the barycentric coordinates add up to one), so the
-    per-pair routine of the P1 oracle provides both."""
+    matrix per kernel (V_L, K_L, V_Y, K_Y): the semi-analytic entry (as in
+    assemble_p0) minus the same entry under the nq x nq regular product rule
+    (what the point sums already hold); oracle.c or_corrections_p0."""
     import scipy.sparse as sp
-    from .bem_p1 import pair_blocks
-    I, J = vertex_sharing_pairs(tris)
-    B = pair_blocks(verts, tris, list(zip(I, J)), nq, kappa, minus_regular=True, L_outer=L_outer)
-    nt = len(tris)
-    return [sp.csr_matrix((B[:, op].sum(axis=(1, 2)), (I, J)), shape=(nt, nt)) for op in range(4)]
+    V = np.ascontiguousarray(verts, dtype=np.float64)
+    F = np.ascontiguousarray(tris, dtype=np.int32)
+    I, J = vertex_sharing_pairs(F)
+    I = np.ascontiguousarray(I, dtype=np.int64)
+    J = np.ascontiguousarray(J, dtype=np.int64)
+    out = np.zeros((len(I), 4))
+    if lib().or_corrections_p0(len(V), _p(V), len(F), _p(F), len(I), _p(I), _p(J), int(nq), float(kappa),
+                               int(L_outer), 4, 4, _p(out)) != 0:
+        raise ValueError("corrections failed")
+    nt = len(F)
+    return [sp.csr_matrix((out[:, op], (I, J)), shape=(nt, nt)) for op in range(4)]
 
 
 def matvec_free(verts, tris, nq, kappa, eps_in, eps_out, corr=None):

@@ -803,3 +803,67 @@ int or_pair_p1(const double *verts, const int *ti, const int *tj, int nq, double
             for (int b = 0; b < 3; ++b) out[op * 9 + 3 * a + b] = blk[op][a][b];
     return 0;
 }
+
+/*
+ * P0 corrections of the given triangle pairs (i[k], j[k]), k < npairs:
+ * out[4k + op] = (semi-analytic Galerkin entry of Ti x Tj) - (the same entry
+ * under the nq x nq regular product rule, pairs at distance 0 excluded),
+ * op = V_L, K_L, V_Y, K_Y.  The entries are those of or_assemble_p0 (graded
+ * outer rule L_outer levels deep for vertex-sharing pairs).  For a
+ * matrix-free mat-vec: the point sums hold the regular-rule part of every
+ * pair, the corrections swap it for the singular value.  OpenMP over pairs.
+ */
+int or_corrections_p0(long nv, const double *verts, long nt, const int *tris, long npairs, const long *pi,
+                      const long *pj, int nq, double kappa, int L_outer, int n_outer, int n_inner, double *out)
+{
+    double RL[6 * 3], RW[6];
+    if (regular_rule(nq, RL, RW) != 0) return -1;
+    (void)nv; (void)nt;
+    const int no = n_outer * n_outer, ni = n_inner * n_inner;
+    double lo1[64], lo2[64], wo[64], li1[64], li2[64], wi[64];
+    if (no > 64 || ni > 64) return -1;
+    triangle_rule(n_outer, lo1, lo2, wo);
+    triangle_rule(n_inner, li1, li2, wi);
+    const double k4pi = 1.0 / (4.0 * OR_PI);
+#pragma omp parallel for schedule(dynamic, 16)
+    for (long k = 0; k < npairs; ++k) {
+        const long i = pi[k], j = pj[k];
+        tri_t Ti, Tj;
+        for (int a = 0; a < 3; ++a)
+            for (int c = 0; c < 3; ++c) {
+                Ti.v[a][c] = verts[3 * tris[3 * i + a] + c];
+                Tj.v[a][c] = verts[3 * tris[3 * j + a] + c];
+            }
+        double ni_[3], nj[3];
+        const double ai = tri_area_normal(&Ti, ni_), aj = tri_area_normal(&Tj, nj);
+        int shared = 0;
+        for (int s = 0; s < 3; ++s)
+            for (int t = 0; t < 3; ++t)
+                if (tris[3 * i + s] == tris[3 * j + t]) shared++;
+        double acc[4] = { 0, 0, 0, 0 };
+        outer_ctx C = { &Tj, nj, aj, shared == 3, kappa, no, lo1, lo2, wo, ni, li1, li2, wi,
+                        1e-10 * sqrt(aj) };
+        outer_graded(&C, &Ti, shared ? L_outer : 0, acc);
+        for (int qa = 0; qa < nq; ++qa) {
+            double x[3], y[3], rv[3];
+            for (int c = 0; c < 3; ++c)
+                x[c] = RL[3 * qa] * Ti.v[0][c] + RL[3 * qa + 1] * Ti.v[1][c] + RL[3 * qa + 2] * Ti.v[2][c];
+            for (int qb = 0; qb < nq; ++qb) {
+                for (int c = 0; c < 3; ++c)
+                    y[c] = RL[3 * qb] * Tj.v[0][c] + RL[3 * qb + 1] * Tj.v[1][c] + RL[3 * qb + 2] * Tj.v[2][c];
+                sub3(x, y, rv);
+                const double r = norm3(rv);
+                if (r == 0.0) continue;
+                const double w = RW[qa] * ai * RW[qb] * aj;
+                const double rn = dot3(rv, nj);
+                const double ek = exp(-kappa * r);
+                acc[0] -= w * k4pi / r;
+                acc[1] -= w * k4pi * rn / (r * r * r);
+                acc[2] -= w * k4pi * ek / r;
+                acc[3] -= w * k4pi * ek * (1.0 + kappa * r) * rn / (r * r * r);
+            }
+        }
+        for (int op = 0; op < 4; ++op) out[4 * k + op] = acc[op];
+    }
+    return 0;
+}
