@@ -109,15 +109,6 @@ __global__ void k_chol_solve(int n, const double* __restrict__ L, const double* 
     }
 }
 
-__global__ void k_matmul(int n, const double* __restrict__ A, const double* __restrict__ B, double* __restrict__ C) {
-    int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= n * n) return;
-    int i = idx / n, j = idx % n;
-    double s = 0.0;
-    for (int k = 0; k < n; ++k) s += A[i * n + k] * B[k * n + j];
-    C[idx] = s;
-}
-
 // Symmetric eigendecomposition A = V diag(w) V^T by the cyclic Jacobi method
 // (plane rotations that annihilate one off-diagonal entry each, with the
 // rotation angle from theta = (a_qq - a_pp) / (2 a_pq), t = sgn(theta) /
@@ -214,6 +205,92 @@ __global__ void k_store_padded(int n, int npad, const double* __restrict__ src, 
     if (dst_d) dst_d[idx] = v;
 }
 
+// Translation operators of one level in one launch: for every z (M2L: the
+// 343 relative offsets, the 27 near ones skipped; M2M / L2L: the 8 child
+// octants) C_z = P K_z with P the level's pseudo-inverse (n x n, FP64) and
+// K_z[k][j] = g(t_z + ts u_k, s_z + ss u_j) generated on the fly from the
+// unit surface u.  Tiled FP64 GEMM: 64 x 64 outputs per CTA, 4 x 4 per thread,
+// 16-wide K steps through shared memory; written padded to npad x npad (FP32
+// and, if dst_d, FP64) at dst + z * npad^2.
+enum { OPB_M2L = 0, OPB_M2M = 1, OPB_L2L = 2 };
+constexpr int kOpTile = 64, kOpK = 16;
+
+__global__ void __launch_bounds__(256) k_build_ops(int n, int npad, int mode, int kernel, double kappa,
+                                                   const double* __restrict__ surf, const double* __restrict__ P,
+                                                   double r, double ts, double ss, float* __restrict__ dst_f,
+                                                   double* __restrict__ dst_d) {
+    const int z = blockIdx.z;
+    double tc[3] = {0, 0, 0}, sc[3] = {0, 0, 0};
+    if (mode == OPB_M2L) {
+        const int ox = z / 49 - 3, oy = (z / 7) % 7 - 3, oz = z % 7 - 3;
+        if (abs(ox) <= 1 && abs(oy) <= 1 && abs(oz) <= 1) return;   // near offsets: no operator
+        sc[0] = 2 * r * ox; sc[1] = 2 * r * oy; sc[2] = 2 * r * oz;
+    } else {
+        const double cc[3] = {((z >> 2) & 1) ? r : -r, ((z >> 1) & 1) ? r : -r, (z & 1) ? r : -r};
+        for (int a = 0; a < 3; ++a) (mode == OPB_M2M ? sc : tc)[a] = cc[a];
+    }
+    __shared__ double sA[kOpTile][kOpK + 1];
+    __shared__ double sB[kOpK][kOpTile + 1];
+    const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+    const int i0 = blockIdx.y * kOpTile, j0 = blockIdx.x * kOpTile;
+    double acc[4][4] = {};
+    for (int k0 = 0; k0 < n; k0 += kOpK) {
+        for (int e = threadIdx.x; e < kOpTile * kOpK; e += 256) {
+            const int ii = e / kOpK, kk = e % kOpK;
+            const int i = i0 + ii, k = k0 + kk;
+            sA[ii][kk] = (i < n && k < n) ? P[(size_t)i * n + k] : 0.0;
+        }
+        for (int e = threadIdx.x; e < kOpK * kOpTile; e += 256) {
+            const int kk = e / kOpTile, jj = e % kOpTile;
+            const int k = k0 + kk, j = j0 + jj;
+            double g = 0.0;
+            if (k < n && j < n) {
+                const double dx = (tc[0] + ts * surf[3 * k]) - (sc[0] + ss * surf[3 * j]);
+                const double dy = (tc[1] + ts * surf[3 * k + 1]) - (sc[1] + ss * surf[3 * j + 1]);
+                const double dz = (tc[2] + ts * surf[3 * k + 2]) - (sc[2] + ss * surf[3 * j + 2]);
+                const double rr = sqrt(dx * dx + dy * dy + dz * dz);
+                g = kInv4Pi / rr;
+                if (kernel == FMM_YUKAWA) g *= exp(-kappa * rr);
+            }
+            sB[kk][jj] = g;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < kOpK; ++kk) {
+            double a[4], b[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                a[u] = sA[ty + 16 * u][kk];
+                b[u] = sB[kk][tx + 16 * u];
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) acc[u][v] += a[u] * b[v];
+        }
+        __syncthreads();
+    }
+    const size_t m2 = (size_t)npad * npad;
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+            const int i = i0 + ty + 16 * u, j = j0 + tx + 16 * v;
+            if (i < n && j < n) {
+                dst_f[(size_t)z * m2 + (size_t)i * npad + j] = (float)acc[u][v];
+                if (dst_d) dst_d[(size_t)z * m2 + (size_t)i * npad + j] = acc[u][v];
+            }
+        }
+}
+
+static void build_ops(cudaStream_t st, int n, int npad, int mode, int kernel, double kappa, const double* surf,
+                      const double* P, double r, double ts, double ss, float* dst_f, double* dst_d) {
+    const int nz = mode == OPB_M2L ? kNumOffsets : 8;
+    dim3 grid(div_up(n, kOpTile), div_up(n, kOpTile), nz);
+    k_build_ops<<<grid, 256, 0, st>>>(n, npad, mode, kernel, kappa, surf, P, r, ts, ss, dst_f, dst_d);
+    PB_CHECK_LAUNCH();
+}
+
 namespace {
 
 struct Builder {
@@ -305,19 +382,12 @@ std::shared_ptr<Operators> get_operators(fmm_tree* T, int kernel, double kappa, 
         Bd.pinv(Bd.A.p, dc.p);
         Bd.store(dc.p, nullptr, O->dc2de_d.p + l * m2, np);
         if (l > 0) {
-            for (int c = 0; c < 8; ++c) {
-                const double cc[3] = {((c >> 2) & 1) ? r : -r, ((c >> 1) & 1) ? r : -r, (c & 1) ? r : -r};
-                // M2M_l[c] = UC2UE_{l-1} K(parent uc, child ue); parent half-width 2r
-                Bd.kmat(Bd.C.p, zero, kAlphaOuter * 2 * r, cc, kAlphaInner * r);
-                k_matmul<<<div_up((long long)n * n, 256), 256, 0, st>>>(n, uc2ue_prev.p, Bd.C.p, Bd.A.p);
-                Bd.store(Bd.A.p, O->m2m.p + ((size_t)l * 8 + c) * m2,
-                         need_fp64 ? O->m2m_d.p + ((size_t)l * 8 + c) * m2 : nullptr, np);
-                // L2L_l[c] = DC2DE_l K(child dc, parent de)
-                Bd.kmat(Bd.C.p, cc, kAlphaInner * r, zero, kAlphaOuter * 2 * r);
-                k_matmul<<<div_up((long long)n * n, 256), 256, 0, st>>>(n, dc.p, Bd.C.p, Bd.A.p);
-                Bd.store(Bd.A.p, O->l2l.p + ((size_t)l * 8 + c) * m2,
-                         need_fp64 ? O->l2l_d.p + ((size_t)l * 8 + c) * m2 : nullptr, np);
-            }
+            // M2M_l[c] = UC2UE_{l-1} K(parent uc, child-c ue); parent half-width 2r
+            build_ops(st, n, np, OPB_M2M, kernel, kappa, O->surf.p, uc2ue_prev.p, r, kAlphaOuter * 2 * r,
+                      kAlphaInner * r, O->m2m.p + (size_t)l * 8 * m2, need_fp64 ? O->m2m_d.p + (size_t)l * 8 * m2 : nullptr);
+            // L2L_l[c] = DC2DE_l K(child-c dc, parent de)
+            build_ops(st, n, np, OPB_L2L, kernel, kappa, O->surf.p, dc.p, r, kAlphaInner * r, kAlphaOuter * 2 * r,
+                      O->l2l.p + (size_t)l * 8 * m2, need_fp64 ? O->l2l_d.p + (size_t)l * 8 * m2 : nullptr);
         }
         PB_CUDA(cudaMemcpyAsync(uc2ue_prev.p, Bd.B.p, (size_t)n * n * sizeof(double), cudaMemcpyDeviceToDevice, st));
         // M2L_l[o] = DC2DE_l K(dc of B, ue of the box at offset o); the
@@ -331,15 +401,9 @@ std::shared_ptr<Operators> get_operators(fmm_tree* T, int kernel, double kappa, 
                 PB_CUDA(cudaMemcpyAsync(O->m2l_d.p + l * blk, O->m2l_d.p + 2 * blk, blk * sizeof(double),
                                         cudaMemcpyDeviceToDevice, st));
         } else if (l >= 2) {
-            for (int o = 0; o < kNumOffsets; ++o) {
-                int ox = o / 49 - 3, oy = (o / 7) % 7 - 3, oz = o % 7 - 3;
-                if (std::abs(ox) <= 1 && std::abs(oy) <= 1 && std::abs(oz) <= 1) continue;
-                const double sc[3] = {2 * r * ox, 2 * r * oy, 2 * r * oz};
-                Bd.kmat(Bd.C.p, zero, kAlphaInner * r, sc, kAlphaInner * r);
-                k_matmul<<<div_up((long long)n * n, 256), 256, 0, st>>>(n, dc.p, Bd.C.p, Bd.A.p);
-                Bd.store(Bd.A.p, O->m2l.p + ((size_t)l * kNumOffsets + o) * m2,
-                         need_fp64 ? O->m2l_d.p + ((size_t)l * kNumOffsets + o) * m2 : nullptr, np);
-            }
+            build_ops(st, n, np, OPB_M2L, kernel, kappa, O->surf.p, dc.p, r, kAlphaInner * r, kAlphaInner * r,
+                      O->m2l.p + (size_t)l * kNumOffsets * m2,
+                      need_fp64 ? O->m2l_d.p + (size_t)l * kNumOffsets * m2 : nullptr);
         }
         PB_CHECK_LAUNCH();
     }
@@ -348,8 +412,11 @@ std::shared_ptr<Operators> get_operators(fmm_tree* T, int kernel, double kappa, 
     {
         std::vector<float> w1((size_t)2 * L * m2), w2((size_t)2 * L * m2);
         std::atomic<int> next(0);
+        // Laplace: K scales as 2^l with the level, so the eigenvectors are the
+        // same and W1 scales as 2^-l (exact in FP32): decompose level 0 only
+        const int njobs = kernel == FMM_LAPLACE ? 2 : 2 * L;
         auto work = [&]() {
-            for (int job; (job = next.fetch_add(1)) < 2 * L;) {
+            for (int job; (job = next.fetch_add(1)) < njobs;) {
                 const int l = job / 2;
                 const bool up = (job % 2) == 0;
                 const double r = std::ldexp(T->R, -l);
@@ -358,11 +425,19 @@ std::shared_ptr<Operators> get_operators(fmm_tree* T, int kernel, double kappa, 
                               w2.data() + (size_t)job * m2);
             }
         };
-        const int nth = std::max(1, std::min<int>(2 * L, (int)std::thread::hardware_concurrency()));
+        const int nth = std::max(1, std::min<int>(njobs, (int)std::thread::hardware_concurrency()));
         std::vector<std::thread> pool;
         for (int t = 1; t < nth; ++t) pool.emplace_back(work);
         work();
         for (auto& th : pool) th.join();
+        for (int job = njobs; job < 2 * L; ++job) {
+            const int l = job / 2;
+            const float sc = std::ldexp(1.0f, -l);
+            for (size_t e = 0; e < m2; ++e) {
+                w1[(size_t)job * m2 + e] = sc * w1[(size_t)(job % 2) * m2 + e];
+                w2[(size_t)job * m2 + e] = w2[(size_t)(job % 2) * m2 + e];
+            }
+        }
         // [job = 2 l + (0 up, 1 down)] -> [level] per direction
         std::vector<float> u1((size_t)L * m2), u2((size_t)L * m2), d1((size_t)L * m2), d2((size_t)L * m2);
         for (int l = 0; l < L; ++l) {
