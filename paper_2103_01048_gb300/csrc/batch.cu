@@ -1,12 +1,17 @@
 // Batched solves of many systems and an ncrit autotuner.
 //
-// pb_solve_batch runs the GMRES iterations of several meshes in lockstep:
-// each system gets its own CUDA stream, its preconditioned mat-vec (P1, the
-// Laplace and Yukawa FMM passes, the fused Galerkin glue) is captured once
-// as a CUDA graph and replayed every iteration, and one host synchronisation
-// per iteration reads all the residuals.  Small systems therefore overlap
-// on the GPU instead of running one after another, and the ~60 launches of
-// a mat-vec cost one graph launch.
+// pb_solve_batch runs the GMRES iterations of several meshes in lockstep,
+// and one lockstep iteration of ALL active systems is one CUDA graph: for
+// every system, on its own stream (branches of the graph), the copy of the
+// current Krylov vector, the preconditioned mat-vec (P1, the Laplace and
+// Yukawa FMM passes, the fused Galerkin glue), the two classical
+// Gram-Schmidt passes, the Givens update with the device-side convergence
+// test, and the next basis vector.  The Arnoldi kernels read the iteration
+// index from device memory, so the same graph is replayed every iteration;
+// a system that converges marks itself done on the device and its Arnoldi
+// kernels return at once.  The host launches the graph, reads the systems'
+// done flags (one synchronisation per iteration) and re-captures the graph
+// without the converged systems, so their mat-vecs stop too.
 #include "bem.cuh"
 #include <algorithm>
 #include <cmath>
@@ -42,6 +47,121 @@ __global__ void k_set_g0(const double* nrm2, double* g);
 __global__ void k_vadd(int n, const double* a, double* b);
 
 constexpr int kDotBlocksB = 304;
+
+// Arnoldi step kernels with the iteration index j in device memory (the
+// graph of one lockstep iteration is replayed for every j); each returns at
+// once when its system is done.
+struct BatchDev {
+    int j;          // current iteration
+    int done;       // 1: converged or out of iterations
+    int m;          // iterations taken (valid once done)
+    int pad;
+    double resid;   // |g[j+1]| of the last completed iteration
+};
+
+__global__ void k_b_copy_in(long long n, const double* __restrict__ V, const BatchDev* __restrict__ d,
+                            double* __restrict__ x) {
+    if (d->done) return;
+    const double* v = V + (long long)d->j * n;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        x[i] = v[i];
+}
+
+// partial[blk][k] = sum over the block's rows of V[k][i] w[i], k <= j (all:
+// the j + 1 basis vectors; else only w with itself)
+__global__ void k_b_dots(long long n, const double* __restrict__ V, long long ld, const double* __restrict__ w,
+                         double* __restrict__ partial, int kmax, const BatchDev* __restrict__ d, int all) {
+    if (d->done) return;
+    __shared__ double red[256];
+    const int nk = all ? d->j + 1 : 1;
+    const double* base = all ? V : w;
+    long long chunk = (n + gridDim.x - 1) / gridDim.x;
+    long long i0 = blockIdx.x * chunk, i1 = min(n, i0 + chunk);
+    for (int k = 0; k < nk; ++k) {
+        double s = 0.0;
+        const double* v = base + (long long)k * ld;
+        for (long long i = i0 + threadIdx.x; i < i1; i += blockDim.x) s += v[i] * w[i];
+        red[threadIdx.x] = s;
+        __syncthreads();
+        for (int o = 128; o > 0; o >>= 1) {
+            if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) partial[(long long)blockIdx.x * kmax + k] = red[0];
+        __syncthreads();
+    }
+}
+
+__global__ void k_b_dots_reduce(int nblk, const double* __restrict__ partial, int kmax, double* __restrict__ h,
+                                const BatchDev* __restrict__ d, int all) {
+    if (d->done) return;
+    const int nk = all ? d->j + 1 : 1;
+    const int k = threadIdx.x + blockIdx.x * blockDim.x;
+    if (k >= nk) return;
+    double s = 0.0;
+    for (int b = 0; b < nblk; ++b) s += partial[(long long)b * kmax + k];
+    h[k] = s;
+}
+
+// w -= sum_k h[k] V[k], k <= j (h staged in shared memory, kmax + 1 doubles)
+__global__ void k_b_update(long long n, const double* __restrict__ V, long long ld, const double* __restrict__ h,
+                           double* __restrict__ w, const BatchDev* __restrict__ d) {
+    if (d->done) return;
+    extern __shared__ double sh[];
+    const int nk = d->j + 1;
+    for (int k = threadIdx.x; k < nk; k += blockDim.x) sh[k] = h[k];
+    __syncthreads();
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        double s = w[i];
+        for (int k = 0; k < nk; ++k) s -= sh[k] * V[(long long)k * ld + i];
+        w[i] = s;
+    }
+}
+
+__global__ void k_b_vadd(const double* __restrict__ a, double* __restrict__ b, const BatchDev* __restrict__ d) {
+    if (d->done) return;
+    for (int k = threadIdx.x; k <= d->j; k += blockDim.x) b[k] += a[k];
+}
+
+// Hessenberg column j -> Givens update, the convergence test, and j + 1
+__global__ void k_b_givens(int kmax, const double* __restrict__ h, const double* __restrict__ nrm2, double* H,
+                           double* cs, double* sn, double* g, double beta, double tol, BatchDev* d) {
+    if (threadIdx.x != 0 || blockIdx.x != 0 || d->done) return;
+    const int j = d->j;
+    double* col = H + (long long)j * (kmax + 1);
+    for (int k = 0; k <= j; ++k) col[k] = h[k];
+    col[j + 1] = sqrt(*nrm2);
+    for (int k = 0; k < j; ++k) {
+        double a = col[k], b = col[k + 1];
+        col[k] = cs[k] * a + sn[k] * b;
+        col[k + 1] = -sn[k] * a + cs[k] * b;
+    }
+    double a = col[j], b = col[j + 1];
+    double r = hypot(a, b);
+    double c = r > 0 ? a / r : 1.0, s = r > 0 ? b / r : 0.0;
+    cs[j] = c;
+    sn[j] = s;
+    col[j] = r;
+    col[j + 1] = 0.0;
+    g[j + 1] = -s * g[j];
+    g[j] = c * g[j];
+    d->resid = fabs(g[j + 1]);
+    d->j = j + 1;
+    if (d->resid <= tol * beta || j + 1 >= kmax) {
+        d->done = 1;
+        d->m = j + 1;
+    }
+}
+
+// V[j] = w / ||w|| (j already advanced by k_b_givens); skipped once done
+__global__ void k_b_scale(long long n, const double* __restrict__ w, const double* __restrict__ nrm2,
+                          double* __restrict__ V, const BatchDev* __restrict__ d) {
+    if (d->done) return;
+    const double inv = 1.0 / sqrt(*nrm2);
+    double* out = V + (long long)d->j * n;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        out[i] = w[i] * inv;
+}
 void coulomb_at_points(pb_mesh* M, pb_result* R, double* f);
 
 struct BatchSystem {
@@ -54,15 +174,12 @@ struct BatchSystem {
     int kmax = 0, nb = 0, ub = 0;
     DBuf<double> V, w, partial, h, h2, H, cs, sn, g, nrm2, resid, yv, xin, xout, b, f;
     double* host = nullptr;           // pinned: [0] residual, [1] ||b||^2
-    cudaGraph_t graph = nullptr;
-    cudaGraphExec_t exec = nullptr;
+    DBuf<BatchDev> dev;               // iteration state on the device
     double beta = 0.0;
     int j = 0;
     bool active = true;
     int status = PB_ENOCONV;
     ~BatchSystem() {
-        if (exec) cudaGraphExecDestroy(exec);
-        if (graph) cudaGraphDestroy(graph);
         if (host) cudaFreeHost(host);
     }
 };
@@ -133,7 +250,7 @@ void solve_batch(pb_ctx* ctx, pb_mesh* const* meshes, int nsys, pb_result** resu
         sys[s] = std::move(S);
     }
     PB_CUDA(cudaStreamSynchronize(main));
-    // phase 1: one stream per system, mat-vec captured as a graph
+    // phase 1: one stream per system; r0 = P^{-1} b, beta = ||r0||
     for (auto& Sp : sys) {
         BatchSystem& S = *Sp;
         S.sub.device = ctx->device;
@@ -150,12 +267,9 @@ void solve_batch(pb_ctx* ctx, pb_mesh* const* meshes, int nsys, pb_result** resu
         S.M->ctx = &S.sub;
         S.M->tree->ctx = &S.sub;
         cudaStream_t st = S.sub.stream;
-        pb_result* R = S.R;
-        PB_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-        mesh_matvec(S.M, R->eps_in, R->eps_out, R->kappa, R->precision, S.xin.p, S.xout.p, 1);
-        PB_CUDA(cudaStreamEndCapture(st, &S.graph));
-        PB_CUDA(cudaGraphInstantiate(&S.exec, S.graph, 0));
-        // r0 = P^{-1} b, beta = ||r0||
+        S.dev.alloc(1, main);
+        PB_CUDA(cudaMemsetAsync(S.dev.p, 0, sizeof(BatchDev), main));
+        PB_CUDA(cudaStreamSynchronize(main));
         batch_dots(S, S.b.p, 1, S.b.p, S.nrm2.p, 0);
         PB_CUDA(cudaMemcpyAsync(S.host + 1, S.nrm2.p, sizeof(double), cudaMemcpyDeviceToHost, st));
         k_scale<<<S.ub, 256, 0, st>>>(S.n, S.b.p, S.nrm2.p, S.V.p);
@@ -167,41 +281,104 @@ void solve_batch(pb_ctx* ctx, pb_mesh* const* meshes, int nsys, pb_result** resu
         Sp->beta = std::sqrt(Sp->host[1]);
         if (Sp->beta == 0.0) { Sp->active = false; Sp->status = PB_OK; Sp->j = 0; }
     }
-    // lockstep GMRES iterations (CGS2), one host synchronisation per iteration
-    for (int j = 0; j < max_iter; ++j) {
-        bool any = false;
-        for (auto& Sp : sys) {
-            BatchSystem& S = *Sp;
-            if (!S.active) continue;
-            any = true;
-            cudaStream_t st = S.sub.stream;
-            PB_CUDA(cudaMemcpyAsync(S.xin.p, S.V.p + (long long)j * S.n, S.n * sizeof(double),
-                                    cudaMemcpyDeviceToDevice, st));
-            PB_CUDA(cudaGraphLaunch(S.exec, st));
-            batch_dots(S, S.V.p, j + 1, S.xout.p, S.h.p, 0);
-            k_update<<<S.ub, 256, (j + 1) * sizeof(double), st>>>(S.n, S.V.p, S.n, j + 1, S.h.p, S.xout.p);
-            PB_CHECK_LAUNCH();
-            batch_dots(S, S.V.p, j + 1, S.xout.p, S.h2.p, 0);
-            k_update<<<S.ub, 256, (j + 1) * sizeof(double), st>>>(S.n, S.V.p, S.n, j + 1, S.h2.p, S.xout.p);
-            PB_CHECK_LAUNCH();
-            k_vadd<<<div_up(j + 1, 128), 128, 0, st>>>(j + 1, S.h2.p, S.h.p);
-            PB_CHECK_LAUNCH();
-            batch_dots(S, S.xout.p, 1, S.xout.p, S.nrm2.p, 0);
-            k_givens<<<1, 1, 0, st>>>(j, S.kmax, S.h.p, S.nrm2.p, S.H.p, S.cs.p, S.sn.p, S.g.p, S.resid.p);
-            PB_CHECK_LAUNCH();
-            k_scale<<<S.ub, 256, 0, st>>>(S.n, S.xout.p, S.nrm2.p, S.V.p + (long long)(j + 1) * S.n);
-            PB_CHECK_LAUNCH();
-            PB_CUDA(cudaMemcpyAsync(S.host, S.resid.p, sizeof(double), cudaMemcpyDeviceToHost, st));
+    // One lockstep iteration of every active system as one graph, captured
+    // on `origin` with a fork to each system's stream and a join back.
+    cudaStream_t origin = nullptr;
+    PB_CUDA(cudaStreamCreateWithFlags(&origin, cudaStreamNonBlocking));
+    std::vector<cudaEvent_t> evs;
+    auto new_event = [&]() {
+        cudaEvent_t e;
+        PB_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        evs.push_back(e);
+        return e;
+    };
+    cudaEvent_t fork = new_event();
+    std::vector<cudaEvent_t> joins;
+    for (int s = 0; s < nsys; ++s) joins.push_back(new_event());
+    DBuf<BatchDev> flags;              // device state of all systems, gathered for one copy
+    flags.alloc(nsys, main);
+    BatchDev* hflags = nullptr;
+    PB_CUDA(cudaMallocHost((void**)&hflags, nsys * sizeof(BatchDev)));
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    struct GraphGuard {
+        cudaGraph_t* g;
+        cudaGraphExec_t* e;
+        cudaStream_t* o;
+        std::vector<cudaEvent_t>* evs;
+        BatchDev** hf;
+        ~GraphGuard() {
+            if (*e) cudaGraphExecDestroy(*e);
+            if (*g) cudaGraphDestroy(*g);
+            if (*o) { cudaStreamSynchronize(*o); cudaStreamDestroy(*o); }
+            for (auto ev : *evs) cudaEventDestroy(ev);
+            if (*hf) cudaFreeHost(*hf);
         }
-        if (!any) break;
-        for (auto& Sp : sys) {
-            BatchSystem& S = *Sp;
+    } guard{&graph, &exec, &origin, &evs, &hflags};
+    auto capture = [&]() {
+        if (exec) { PB_CUDA(cudaGraphExecDestroy(exec)); exec = nullptr; }
+        if (graph) { PB_CUDA(cudaGraphDestroy(graph)); graph = nullptr; }
+        PB_CUDA(cudaStreamBeginCapture(origin, cudaStreamCaptureModeThreadLocal));
+        PB_CUDA(cudaEventRecord(fork, origin));
+        for (int s = 0; s < nsys; ++s) {
+            BatchSystem& S = *sys[s];
+            cudaStream_t st = S.sub.stream;
+            PB_CUDA(cudaStreamWaitEvent(st, fork, 0));
+            if (S.active) {
+                pb_result* R = S.R;
+                k_b_copy_in<<<S.ub, 256, 0, st>>>(S.n, S.V.p, S.dev.p, S.xin.p);
+                PB_CHECK_LAUNCH();
+                mesh_matvec(S.M, R->eps_in, R->eps_out, R->kappa, R->precision, S.xin.p, S.xout.p, 1);
+                for (int pass = 0; pass < 2; ++pass) {       // CGS2
+                    double* hp = pass == 0 ? S.h.p : S.h2.p;
+                    k_b_dots<<<S.nb, 256, 0, st>>>(S.n, S.V.p, S.n, S.xout.p, S.partial.p, S.kmax + 1, S.dev.p, 1);
+                    k_b_dots_reduce<<<div_up(S.kmax + 1, 128), 128, 0, st>>>(S.nb, S.partial.p, S.kmax + 1, hp,
+                                                                            S.dev.p, 1);
+                    k_b_update<<<S.ub, 256, (S.kmax + 1) * sizeof(double), st>>>(S.n, S.V.p, S.n, hp, S.xout.p,
+                                                                                S.dev.p);
+                    PB_CHECK_LAUNCH();
+                }
+                k_b_vadd<<<1, 256, 0, st>>>(S.h2.p, S.h.p, S.dev.p);
+                k_b_dots<<<S.nb, 256, 0, st>>>(S.n, S.xout.p, S.n, S.xout.p, S.partial.p, S.kmax + 1, S.dev.p, 0);
+                k_b_dots_reduce<<<1, 128, 0, st>>>(S.nb, S.partial.p, S.kmax + 1, S.nrm2.p, S.dev.p, 0);
+                k_b_givens<<<1, 1, 0, st>>>(S.kmax, S.h.p, S.nrm2.p, S.H.p, S.cs.p, S.sn.p, S.g.p, S.beta, tol,
+                                            S.dev.p);
+                k_b_scale<<<S.ub, 256, 0, st>>>(S.n, S.xout.p, S.nrm2.p, S.V.p, S.dev.p);
+                PB_CHECK_LAUNCH();
+            }
+            PB_CUDA(cudaMemcpyAsync(flags.p + s, S.dev.p, sizeof(BatchDev), cudaMemcpyDeviceToDevice, st));
+            PB_CUDA(cudaEventRecord(joins[s], st));
+            PB_CUDA(cudaStreamWaitEvent(origin, joins[s], 0));
+        }
+        PB_CUDA(cudaMemcpyAsync(hflags, flags.p, nsys * sizeof(BatchDev), cudaMemcpyDeviceToHost, origin));
+        PB_CUDA(cudaStreamEndCapture(origin, &graph));
+        PB_CUDA(cudaGraphInstantiate(&exec, graph, 0));
+    };
+    // k_b_update stages up to kmax + 1 coefficients in shared memory
+    PB_CUDA(cudaFuncSetAttribute(k_b_update, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)std::max<size_t>(48 * 1024, (max_iter + 1) * sizeof(double))));
+    int nactive = 0;
+    for (auto& Sp : sys) nactive += Sp->active ? 1 : 0;
+    bool rebuild = true;
+    for (int it = 0; it < max_iter && nactive > 0; ++it) {
+        if (rebuild) {
+            capture();
+            rebuild = false;
+        }
+        PB_CUDA(cudaGraphLaunch(exec, origin));
+        PB_CUDA(cudaStreamSynchronize(origin));
+        for (int s = 0; s < nsys; ++s) {
+            BatchSystem& S = *sys[s];
             if (!S.active) continue;
-            PB_CUDA(cudaStreamSynchronize(S.sub.stream));
-            S.j = j + 1;
-            double rel = S.host[0] / S.beta;
-            S.R->residual = rel;
-            if (rel <= tol) { S.active = false; S.status = PB_OK; }
+            S.j = hflags[s].j;
+            S.R->residual = hflags[s].resid / S.beta;
+            if (hflags[s].done) {
+                S.active = false;
+                S.j = hflags[s].m;
+                S.status = S.R->residual <= tol ? PB_OK : PB_ENOCONV;
+                --nactive;
+                rebuild = true;
+            }
         }
     }
     for (int s = 0; s < nsys; ++s) {
