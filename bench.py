@@ -79,6 +79,9 @@ def parse():
     ap.add_argument("--sweep", action="store_true", help="p x ncrit grid of the 4M-point apply")
     ap.add_argument("--profile", action="store_true",
                     help="bracket the timed steps with cudaProfilerStart/Stop (for ncu --profile-from-start off)")
+    ap.add_argument("--tc-kernel", choices=["pair", "single"], default=None,
+                    help="tensor-core box-operator kernel: CTA pairs (cta_group::2) or one CTA per operator part "
+                         "(default: the library's choice)")
     ap.add_argument("--kirkwood", action="store_true",
                     help="off-centre-charge sphere refinement study (512 ... 131,072 elements)")
     return ap.parse_args()
@@ -90,6 +93,16 @@ def inputs(n):
     q = synthetic.uniform_densities(n, seed=1)
     d = synthetic.uniform_densities(n, seed=2)
     return x, nrm, q, d
+
+
+def select_tc_kernel(pb, choice):
+    """Apply --tc-kernel and return the kernel in use ("pair" or "single")."""
+    if choice is not None:
+        pb._test_tc_pair(1 if choice == "pair" else 0)
+        return choice
+    mode = pb._test_tc_pair(0)
+    pb._test_tc_pair(mode)
+    return "pair" if mode else "single"
 
 
 def host_cores():
@@ -315,6 +328,7 @@ def run_sweep(args):
     tree build and operator set-up time; one JSON line."""
     import torch
     import paper_2103_01048_gb300 as pb
+    tc_kernel = select_tc_kernel(pb, args.tc_kernel)
     x, nrm, q, d = inputs(args.n)
     stream = torch.cuda.Stream()
     ctx = pb.pb_create(0, stream)
@@ -356,7 +370,8 @@ def run_sweep(args):
     print(json.dumps({"metric": "FMM apply points/s over the expansion orders and leaf sizes",
                       "unit": "points/s", "n_gpus": 1, "dtype": "f32", "data": "synthetic",
                       "config": {"workload": f"fmm_apply_pair {args.n} bumpy-sphere points, Laplace+Yukawa "
-                                             f"(kappa {KAPPA}) SL+DL", "l2": "flushed between applies"},
+                                             f"(kappa {KAPPA}) SL+DL", "l2": "flushed between applies",
+                                 "tc_kernel": tc_kernel},
                       "rows": rows}), flush=True)
     pb.pb_destroy(ctx)
 
@@ -380,6 +395,7 @@ def main():
     if not torch.cuda.is_available():
         raise SystemExit("bench.py needs a CUDA GPU")
     torch.cuda.set_device(local)
+    tc_kernel = select_tc_kernel(pb, args.tc_kernel)
     dist = None
     if world > 1:
         import torch.distributed as dist
@@ -676,7 +692,7 @@ def main():
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": workload_config(args, world),
+                "config": dict(workload_config(args, world), tc_kernel=tc_kernel),
                 "tree": {"boxes": info.n_box, "leaves": info.n_leaf, "levels": info.n_levels,
                          "v_pairs": info.n_v, "p2p_pairs": info.p2p_pairs, "m2p_targets": info.m2p_targets,
                          "p2l_sources": info.p2l_sources, "l2p_targets": info.l2p_targets},

@@ -46,9 +46,29 @@ void pbfmm_test_wait_limit(int64_t cycles);
 int pbfmm_test_radix_sort(const uint64_t* keys, const int32_t* vals, int64_t n, int bits, uint64_t* keys_out,
                           int32_t* vals_out);
 
+/* Kernel of the tensor-core M2L: mode 1 (the default) runs pairs of CTAs
+ * (a cluster of two, whose MMAs of M = 256 take A rows and B columns from
+ * both CTAs' shared memory) at n_pad >= 128, mode 0 one CTA per operator
+ * part.  M2M, L2L and the check -> equivalent solves always use one CTA per
+ * part.  Returns the previous mode.  Read at kernel launch. */
+int pbfmm_test_tc_pair(int mode);
+
+/* Launch properties of the CTA-pair kernel at npad 128, without launching
+ * it: out[0] registers per thread, out[1] max threads per block, out[2]
+ * static shared bytes, out[3] dynamic shared bytes of a launch, out[4] the
+ * number of clusters of two such CTAs that can be resident at once (0: the
+ * launch cannot run on this device).  PB_OK or PB_ECUDA. */
+int pbfmm_test_tc_pair_info(int* out);
+
+/* Eigendecomposition of a symmetric n x n matrix A (row-major, FP64) with
+ * the host eigensolver of the operator precomputation: w[j] eigenvalue j,
+ * V[k * n + j] component k of its unit eigenvector (A = V diag(w) V^T).
+ * Runs on the host only.  PB_OK or PB_EINVAL. */
+int pbfmm_test_sym_eig(int n, const double* A, double* w, double* V);
+
 /* D = Q Op^T for one operator through the tensor-core box-operator kernel
  * (host buffers: Q [nrows][npad], Op [npad][npad], D [nrows][npad]; npad in
- * {32, 64, 128, 160}).  PB_OK, PB_EINVAL or PB_ETIMEOUT. */
+ * {32, 64, 128, 160, 320, 512}).  PB_OK, PB_EINVAL or PB_ETIMEOUT. */
 int pbfmm_selftest_m2l_tc(int nrows, int npad, const float* Q, const float* Op, float* D);
 
 #ifdef __cplusplus

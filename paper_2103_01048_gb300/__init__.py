@@ -392,6 +392,12 @@ _lib.pbfmm_test_wait_limit.argtypes = [_I64]
 _lib.pbfmm_test_wait_limit.restype = None
 _lib.pbfmm_test_radix_sort.argtypes = [_P, _P, _I64, ctypes.c_int, _P, _P]
 _lib.pbfmm_test_radix_sort.restype = ctypes.c_int
+_lib.pbfmm_test_sym_eig.argtypes = [ctypes.c_int, _P, _P, _P]
+_lib.pbfmm_test_sym_eig.restype = ctypes.c_int
+_lib.pbfmm_test_tc_pair_info.argtypes = [_P]
+_lib.pbfmm_test_tc_pair_info.restype = ctypes.c_int
+_lib.pbfmm_test_tc_pair.argtypes = [ctypes.c_int]
+_lib.pbfmm_test_tc_pair.restype = ctypes.c_int
 _lib.pbfmm_test_pool_used.argtypes = [ctypes.c_int]
 _lib.pbfmm_test_pool_used.restype = _I64
 
@@ -411,6 +417,34 @@ def _test_radix_sort(keys, vals, bits):
 def _test_pool_used(device=0):
     """Bytes in use (not cached) in the device's default stream-ordered pool."""
     return int(_lib.pbfmm_test_pool_used(int(device)))
+
+
+def _test_sym_eig(A):
+    """(w, V) of a symmetric matrix from the library's host eigensolver."""
+    A = np.ascontiguousarray(A, dtype=np.float64)
+    n = A.shape[0]
+    w = np.zeros(n)
+    V = np.zeros((n, n))
+    rc = _lib.pbfmm_test_sym_eig(n, ptr(A), ptr(w), ptr(V))
+    if rc != PB_OK:
+        raise PBError(rc, "sym_eig")
+    return w, V
+
+
+def _test_tc_pair_info():
+    """Launch properties of the CTA-pair kernel (npad 128): registers, max
+    threads per block, static and dynamic shared bytes, resident clusters."""
+    out = np.zeros(5, dtype=np.int32)
+    rc = _lib.pbfmm_test_tc_pair_info(ptr(out))
+    if rc != PB_OK:
+        raise PBError(rc, "tc pair info")
+    return dict(zip(("regs", "max_threads", "static_smem", "dyn_smem", "max_active_clusters"), out.tolist()))
+
+
+def _test_tc_pair(mode):
+    """Select the tensor-core box-operator kernel (1: CTA pairs where
+    available, 0: one CTA per operator part); returns the previous mode."""
+    return int(_lib.pbfmm_test_tc_pair(int(mode)))
 
 
 def _test_alloc_count():

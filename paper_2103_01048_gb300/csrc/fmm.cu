@@ -501,9 +501,12 @@ __global__ void __launch_bounds__(256) k_check2equiv(GemmArgs a, const TO* __res
 // target leaf; each thread carries NT targets (t, t + slots, ...) so every
 // staged source is loaded once for NT pairs.  A leaf holds at most ncrit
 // targets, usually fewer than 128 * NT: the CTA is split into
-// G = 128 / slots groups (slots = the smallest power of two >= the target
-// count / NT, at least 8); group g takes every G-th source of each staged
-// chunk and the G partial sums are added at the end, so no thread idles.
+// G = floor(128 / slots) groups of slots = ceil(target count / NT) threads
+// (at least 4); group g takes its share of each staged chunk and the G
+// partial sums are added at the end.  The threads past G * slots idle (a
+// warp of them issues nothing); the lanes that compute padding targets are
+// at most NT - 1 per group, against up to half the CTA with power-of-two
+// group sizes.
 // ---------------------------------------------------------------------------
 template <typename T, bool YUK, bool DL, bool DN, int NT>
 __global__ void __launch_bounds__(128) k_leaf_eval(const int* __restrict__ leaves, int nleaf,
@@ -528,8 +531,7 @@ __global__ void __launch_bounds__(128) k_leaf_eval(const int* __restrict__ leave
     if (li >= nleaf) return;
     const int b = leaves[li];
     const int t0 = tb[b], t1 = te[b];
-    int slots = CH;
-    while (slots > 8 && NT * (slots / 2) >= t1 - t0) slots /= 2;
+    const int slots = min(CH, max(4, (t1 - t0 + NT - 1) / NT));
     const int G = CH / slots;
     const int tloc = threadIdx.x % slots, g = threadIdx.x / slots;
     const int nw = W_off[b + 1] - W_off[b];
@@ -562,7 +564,7 @@ __global__ void __launch_bounds__(128) k_leaf_eval(const int* __restrict__ leave
                 __syncthreads();
                 const int cnt = min(CH, j1 - jc);
                 if (a == b) {
-                    for (int k = g; k < cnt; k += G) {
+                    for (int k = g; g < G && k < cnt; k += G) {
                         V s = s_q[k];
                         T mx = 0, my = 0, mz = 0;
                         if (DL) { V mm = s_m[k]; mx = mm.x; my = mm.y; mz = mm.z; }
@@ -572,7 +574,7 @@ __global__ void __launch_bounds__(128) k_leaf_eval(const int* __restrict__ leave
                                                            mx, my, mz, nx[u], ny[u], nz[u], kappa, pot[u], dn[u]);
                     }
                 } else {
-                    for (int k = g; k < cnt; k += G) {
+                    for (int k = g; g < G && k < cnt; k += G) {
                         V s = s_q[k];
                         T mx = 0, my = 0, mz = 0;
                         if (DL) { V mm = s_m[k]; mx = mm.x; my = mm.y; mz = mm.z; }
@@ -606,7 +608,7 @@ __global__ void __launch_bounds__(128) k_leaf_eval(const int* __restrict__ leave
                 }
                 __syncthreads();
                 const int cnt = min(CH, ne - jc);
-                for (int k = g; k < cnt; k += G) {
+                for (int k = g; g < G && k < cnt; k += G) {
                     V s = s_q[k];
 #pragma unroll
                     for (int u = 0; u < NT; ++u)
@@ -670,8 +672,7 @@ __global__ void __launch_bounds__(128) k_leaf_pair(const int* __restrict__ leave
     if (li >= nleaf) return;
     const int b = leaves[li];
     const int t0 = tb[b], t1 = te[b];
-    int slots = CH;
-    while (slots > 8 && NT * (slots / 2) >= t1 - t0) slots /= 2;
+    const int slots = min(CH, max(4, (t1 - t0 + NT - 1) / NT));
     const int G = CH / slots;
     const int tloc = threadIdx.x % slots, g = threadIdx.x / slots;
     const int nw = W_off[b + 1] - W_off[b];

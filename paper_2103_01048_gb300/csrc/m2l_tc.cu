@@ -27,6 +27,9 @@
 #include "tc_ptx.cuh"
 #include <cub/cub.cuh>
 #include <algorithm>
+#include <atomic>
+#include <cstdio>
+#include <memory>
 
 namespace pbfmm {
 
@@ -310,7 +313,18 @@ struct TcSets {
     float* Y[2];
     int single[2];           // 1: the set holds one level of M2L operators, indexed by offset alone
     long long wait_limit;    // cycles a role waits on a barrier before giving up (set at launch)
+    int* trace;              // optional progress markers of the CTA-pair kernel (host-mapped), or null
 };
+
+// progress marker of the CTA-pair kernel (self-test diagnostics): slot k of
+// cluster rank r of the first cluster, written to host-mapped memory so it
+// stays readable after a failed launch
+__device__ __forceinline__ void tc_mark(int* trace, uint32_t rank, int k, int v) {
+    if (trace && blockIdx.y == 0 && blockIdx.x < 2 && blockIdx.z == 0) {
+        *(volatile int*)&trace[rank * 8 + k] = v;
+        __threadfence_system();
+    }
+}
 
 template <int NPAD>
 __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(const int4* __restrict__ items, const int* __restrict__ ptgt,
@@ -515,6 +529,277 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(const int4* __restrict
     if (warp == 0) tmem_dealloc(taddr, TCOLS);
 }
 
+// ---------------------------------------------------------------------------
+// CTA-pair variant (cluster of two CTAs, tcgen05 cta_group::2).  The two CTAs
+// of a cluster (consecutive along grid x: the pairs of tcgen05 cta_group::2
+// are formed along the cluster's x dimension) hold the two row parts
+// ns = 2 c and 2 c + 1 of the same inner
+// part and split every 256-pair row tile: CTA r gathers the tile's rows
+// r * 128 ... r * 128 + 127 into its own A stages.  The even CTA issues
+// MMAs of M = 256, N = 2 NH: A rows come from both CTAs' stages, B columns
+// from both CTAs' operator parts (the same shared-memory offsets in both),
+// and each CTA's tensor memory receives its own 128 rows x 2 NH columns.
+// Against the single-CTA kernel every source row is gathered once instead
+// of once per row part, and each A tile feeds twice the columns.
+//   producers: arrive (one per warp) on the even CTA's `full` barrier;
+//   MMA issuer (even CTA): commits to `empty` / `accf` of both CTAs;
+//   epilogues: arrive (one per warp) on the even CTA's `acce` barrier;
+//   the odd CTA relays the arrival of its operator part (`barBp`).
+// Cluster barriers after the set-up and before the teardown keep every
+// remote arrival and MMA inside the lifetime of both CTAs.
+// ---------------------------------------------------------------------------
+template <int STAGES>
+struct TcPairSmem {
+    alignas(16) float epi[kTcEpiWarps][32][kTcEpiStride];
+    uint64_t barB, barBp, full[STAGES], empty[STAGES], accf[2], acce[2];
+    uint32_t tmem_slot;
+    int failed;
+};
+
+// bounded wait on a barrier that threads of the other CTA arrive on
+__device__ __forceinline__ bool mbar_wait_cta_cl(uint64_t* bar, uint32_t parity, volatile int* failed,
+                                                 long long limit) {
+    long long t0 = clock64();
+    while (!mbar_try_wait_cluster(bar, parity)) {
+        if (*failed) return false;
+        if (clock64() - t0 > limit) {
+            *failed = 1;
+            return false;
+        }
+    }
+    return true;
+}
+
+template <int NPAD>
+__global__ void __launch_bounds__(kTcThreads, 1)
+    k_m2l_tc2(const int4* __restrict__ items, const int* __restrict__ ptgt, const int* __restrict__ psrc,
+              const TcSets sets, int* __restrict__ err) {
+    const float* __restrict__ ops = sets.ops[blockIdx.z];
+    const float* __restrict__ Qu = sets.X[blockIdx.z];
+    float* __restrict__ Qd = sets.Y[blockIdx.z];
+    const long long wl = sets.wait_limit;
+    constexpr int NS = TcCfg<NPAD>::NS, KS = TcCfg<NPAD>::KS, kTcStages = TcCfg<NPAD>::STAGES;
+    constexpr int NH = NPAD / NS;                    // operator rows held by this CTA
+    constexpr int NP = 2 * NH;                       // MMA N: the rows of the pair
+    constexpr int KC = NPAD / KS;                    // inner columns of this part
+    constexpr int KB = KC / 32;                      // K blocks of 32 tf32 (128 B)
+    constexpr int TILE = 2 * kTcRows;                // pairs per MMA row tile (M = 256)
+    static_assert(NS % 2 == 0 && NP % 16 == 0 && NP >= 32 && NP <= 256 && KC % 32 == 0, "CTA-pair split");
+    constexpr uint32_t B_SPLIT = KB * NH * 128;      // bytes of one of hi / lo
+    constexpr uint32_t A_SPLIT = kTcRows * 128;      // 16 KB
+    constexpr uint32_t ACOLS = NP <= 32 ? 32 : (NP <= 64 ? 64 : (NP <= 128 ? 128 : 256));
+    constexpr uint32_t TCOLS = 2 * ACOLS;
+    constexpr uint32_t IDESC = idesc_tf32_mn(256, NP);
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t* smem = (uint8_t*)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    uint8_t* sB = smem;                               // [hi|lo][KB][NH][128]
+    uint8_t* sA = smem + 2 * B_SPLIT;                 // [stage][hi|lo][128][128]
+    TcPairSmem<kTcStages>* S = (TcPairSmem<kTcStages>*)(sA + kTcStages * 2 * A_SPLIT);
+    volatile int* failed = &S->failed;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    // grid (x: 2 x part pairs, y: items, z: operator sets), clusters of two along x
+    const uint32_t rank = cluster_ctarank();         // 0: issues the pair's MMAs
+    const int4 it = items[blockIdx.y];
+    const int c = blockIdx.x >> 1;                   // part pair: row-part pair nsp, inner part kpart
+    const int nsp = c / KS, kpart = c % KS;
+    const int part = (2 * nsp + (int)rank) * KS + kpart;
+    const int first = it.x, npairs = it.y;
+    const int opi = sets.single[blockIdx.z] ? it.z % kNumOffsets : it.z;
+    const int ntile = (npairs + TILE - 1) / TILE;
+    const int rofs = (int)rank * kTcRows;            // this CTA's rows of a tile
+
+    if (tid == 0) {
+        mbar_init(&S->barB, 1);
+        mbar_init(&S->barBp, 1);
+        for (int q = 0; q < kTcStages; ++q) {
+            mbar_init(&S->full[q], 2 * kTcProdWarps);
+            mbar_init(&S->empty[q], 1);
+        }
+        for (int q = 0; q < 2; ++q) {
+            mbar_init(&S->accf[q], 1);
+            mbar_init(&S->acce[q], 2 * kTcEpiWarps);
+        }
+        S->failed = 0;
+        fence_mbar_init();
+    }
+    if (warp == 0) {
+        tmem_alloc_pair(&S->tmem_slot, TCOLS);
+        tmem_relinquish_pair();
+    }
+    tc_fence_before();
+    __syncthreads();
+    cluster_sync_all();                              // both CTAs' barriers exist before any remote arrival
+    tc_fence_after();
+    const uint32_t taddr = S->tmem_slot;
+    if (tid == 0) {
+        tc_mark(sets.trace, rank, 0, 1);
+        tc_mark(sets.trace, rank, 1, (int)taddr);
+    }
+
+    // resident operator part: hi and lo, one bulk copy each
+    if (tid == 0) {
+        const uint8_t* gB = (const uint8_t*)ops + ((long long)opi * (NS * KS) + part) * (2LL * B_SPLIT);
+        mbar_arrive_expect_tx(&S->barB, 2 * B_SPLIT);
+        bulk_g2s(sB, gB, B_SPLIT, &S->barB);
+        bulk_g2s(sB + B_SPLIT, gB + B_SPLIT, B_SPLIT, &S->barB);
+    }
+
+    if (warp < kTcProdWarps) {
+        // ---- producers (as in the single-CTA kernel, on this CTA's rows)
+        const int l8 = lane & 7, rbase = warp * 4 + (lane >> 3);
+        auto src_of = [&](int tile, int i) -> int {
+            const int r = tile * TILE + rofs + i * 32 + rbase;
+            return (tile < ntile && r < npairs) ? psrc[first + r] : -1;
+        };
+        float4 v[KB][4];
+        int sn[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int s0 = src_of(0, i);
+            const float4* q4 = s0 >= 0 ? (const float4*)(Qu + (size_t)s0 * NPAD + kpart * KC) : nullptr;
+#pragma unroll
+            for (int kb = 0; kb < KB; ++kb) v[kb][i] = q4 ? q4[kb * 8 + l8] : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) sn[i] = src_of(1, i);
+        int g = 0;
+        for (int tile = 0; tile < ntile; ++tile) {
+#pragma unroll
+            for (int kb = 0; kb < KB; ++kb, ++g) {
+                const int s = g % kTcStages, n = g / kTcStages;
+                if (n > 0 && !mbar_wait_cta(&S->empty[s], (n - 1) & 1, failed, wl)) goto prod_done;
+                uint8_t* aHi = sA + (size_t)s * 2 * A_SPLIT;
+                uint8_t* aLo = aHi + A_SPLIT;
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const float4 x = v[kb][i];
+                    float4 h = make_float4(tf32_hi(x.x), tf32_hi(x.y), tf32_hi(x.z), tf32_hi(x.w));
+                    float4 l = make_float4(x.x - h.x, x.y - h.y, x.z - h.z, x.w - h.w);
+                    uint32_t off = sw128_off(i * 32 + rbase, l8 * 4);
+                    *(float4*)(aHi + off) = h;
+                    *(float4*)(aLo + off) = l;
+                }
+                fence_proxy_async();
+                __syncwarp();
+                if (lane == 0) mbar_arrive_cluster(mapa_shared(smem_u32(&S->full[s]), 0));
+                if (tid == 0) tc_mark(sets.trace, rank, 5, g + 1);
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const float4* qn = sn[i] >= 0 ? (const float4*)(Qu + (size_t)sn[i] * NPAD + kpart * KC) : nullptr;
+                    v[kb][i] = qn ? qn[kb * 8 + l8] : make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+            }
+#pragma unroll
+            for (int i = 0; i < 4; ++i) sn[i] = src_of(tile + 2, i);
+        }
+    prod_done:
+        __syncwarp();
+    } else if (warp < kTcProdWarps + kTcEpiWarps) {
+        // ---- epilogue: warp w reads TMEM lanes 32 (w % 4) ... + 31 of this CTA
+        const int q = warp & 3;
+        const int erow = q * 32 + lane;
+        for (int tile = 0; tile < ntile; ++tile) {
+            const int a = tile & 1, u = tile >> 1;
+            const int r = tile * TILE + rofs + erow;
+            const int t = r < npairs ? ptgt[first + r] : -1;
+            bool ok = mbar_wait_cta(&S->accf[a], u & 1, failed, wl);
+            if (!__all_sync(0xffffffffu, ok)) break;
+            tc_fence_after();
+            float (*buf)[kTcEpiStride] = S->epi[q];
+#pragma unroll 1
+            for (int c0 = 0; c0 < NP; c0 += kTcEpiLd) {
+                float v[kTcEpiLd];
+                tmem_ld16(taddr + ((uint32_t)(q * 32) << 16) + a * ACOLS + c0, v);
+#pragma unroll
+                for (int cc = 0; cc < kTcEpiLd; cc += 4)
+                    *(float4*)&buf[lane][cc] = make_float4(v[cc], v[cc + 1], v[cc + 2], v[cc + 3]);
+                __syncwarp();
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    const int rr = j * 8 + (lane >> 2), cc = (lane & 3) * 4;
+                    const float4 x = *(const float4*)&buf[rr][cc];
+                    const int tr = __shfl_sync(0xffffffffu, t, rr);
+                    if (tr >= 0) red_add_v4(Qd + (size_t)tr * NPAD + nsp * NP + c0 + cc, x.x, x.y, x.z, x.w);
+                }
+                __syncwarp();
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive_cluster(mapa_shared(smem_u32(&S->acce[a]), 0));
+            if (warp == kTcProdWarps && lane == 0) tc_mark(sets.trace, rank, 4, tile + 1);
+        }
+        __syncwarp();
+    } else if (rank == 0) {
+        // ---- MMA issuer of the pair
+        if (lane == 0) {
+            uint64_t* last = nullptr;
+            uint32_t last_par = 0;
+            int g = 0;
+            bool ok = mbar_wait_cta(&S->barB, 0, failed, wl) && mbar_wait_cta_cl(&S->barBp, 0, failed, wl);
+            tc_mark(sets.trace, rank, 2, ok ? 1 : -1);
+            for (int tile = 0; ok && tile < ntile; ++tile) {
+                const int a = tile & 1, u = tile >> 1;
+                if (u > 0 && !(ok = mbar_wait_cta_cl(&S->acce[a], (u - 1) & 1, failed, wl))) break;
+                const uint32_t dacc = taddr + a * ACOLS;
+                for (int kb = 0; kb < KB; ++kb, ++g) {
+                    const int s = g % kTcStages, n = g / kTcStages;
+                    if (!(ok = mbar_wait_cta_cl(&S->full[s], n & 1, failed, wl))) break;
+                    tc_fence_after();
+                    const uint32_t aH = smem_u32(sA + (size_t)s * 2 * A_SPLIT), aL = aH + A_SPLIT;
+                    const uint32_t bH = smem_u32(sB) + kb * NH * 128, bL = bH + B_SPLIT;
+#pragma unroll
+                    for (int ks = 0; ks < 4; ++ks) {
+                        const uint32_t acc0 = (kb > 0 || ks > 0) ? 1u : 0u;
+                        mma_tf32_pair(dacc, sw128_desc(aH + ks * 32), sw128_desc(bH + ks * 32), IDESC, acc0);
+                        mma_tf32_pair(dacc, sw128_desc(aH + ks * 32), sw128_desc(bL + ks * 32), IDESC, 1u);
+                        mma_tf32_pair(dacc, sw128_desc(aL + ks * 32), sw128_desc(bH + ks * 32), IDESC, 1u);
+                    }
+                    mma_commit_pair(&S->empty[s], 0x3);
+                    tc_mark(sets.trace, rank, 3, g + 1);
+                    last = &S->empty[s];
+                    last_par = n & 1;
+                }
+                if (!ok) break;
+                mma_commit_pair(&S->accf[a], 0x3);
+                last = &S->accf[a];
+                last_par = u & 1;
+            }
+            // after a failure: every MMA issued here has completed before TMEM is freed
+            if (!ok && last) mbar_wait(last, last_par);
+        }
+        __syncwarp();
+    } else {
+        // ---- odd CTA: tell the issuer that this CTA's operator part has landed
+        if (lane == 0) {
+            const bool ok = mbar_wait_cta(&S->barB, 0, failed, wl);
+            if (ok) mbar_arrive_cluster(mapa_shared(smem_u32(&S->barBp), 0));
+            tc_mark(sets.trace, rank, 2, ok ? 1 : -1);
+        }
+        __syncwarp();
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    cluster_sync_all();                              // no remote arrival or MMA of the pair is pending
+    tc_fence_after();
+    if (tid == 0) {
+        tc_mark(sets.trace, rank, 7, S->failed);
+        tc_mark(sets.trace, rank, 6, 1);
+    }
+    if (tid == 0 && S->failed) {
+        atomicExch(err, 1);
+        mbar_wait(&S->barB, 0);         // the operator copy has landed before shared memory is released
+    }
+    if (warp == 0) tmem_dealloc_pair(taddr, TCOLS);
+}
+
+template <int NPAD>
+static constexpr size_t tc_pair_smem_bytes() {
+    using C = TcCfg<NPAD>;
+    return 1024 + 2 * (size_t)(NPAD / C::KS / 32) * (NPAD / C::NS) * 128 + C::STAGES * 2 * (size_t)kTcRows * 128 +
+           sizeof(TcPairSmem<C::STAGES>);
+}
+
 template <int NPAD>
 static constexpr size_t tc_smem_bytes() {
     using C = TcCfg<NPAD>;
@@ -523,37 +808,77 @@ static constexpr size_t tc_smem_bytes() {
 }
 static_assert(tc_smem_bytes<160>() <= 232448 && tc_smem_bytes<320>() <= 232448 && tc_smem_bytes<512>() <= 232448,
               "shared memory per CTA");
+static_assert(tc_pair_smem_bytes<160>() <= 232448 && tc_pair_smem_bytes<320>() <= 232448 &&
+                  tc_pair_smem_bytes<512>() <= 232448,
+              "shared memory per CTA");
+
+// Kernel choice: CTA pairs (k_m2l_tc2) where the operator size allows,
+// else one CTA per operator part (k_m2l_tc).
+static std::atomic<int> g_tc_pair{1};
+static bool tc_pair_for(int npad) { return g_tc_pair.load() != 0 && npad >= 128; }
+
+// opt in to the large shared-memory carve-out once per process, kernel and
+// device (not a stream operation, so it stays out of captured graphs)
+template <typename F>
+static void smem_optin(F* kernel, size_t bytes, bool* done) {
+    int dev = 0;
+    PB_CUDA(cudaGetDevice(&dev));
+    if (dev >= 0 && dev < 64 && !done[dev]) {
+        PB_CUDA(cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+        done[dev] = true;
+    }
+}
 
 template <int NPAD>
 static void launch_tc_items(const int4* items, int nitems, const int* tgt, const int* src, const TcSets& sets,
-                            int nsets, int* err, cudaStream_t st) {
+                            int nsets, int* err, cudaStream_t st, bool allow_pair) {
     if (nitems <= 0) return;
-    const size_t sm = tc_smem_bytes<NPAD>();
-    // opt in to the large shared-memory carve-out once per process and device
-    // (not a stream operation, so it stays out of captured graphs)
-    static bool attr_set[64] = {false};
-    int dev = 0;
-    PB_CUDA(cudaGetDevice(&dev));
-    if (dev >= 0 && dev < 64 && !attr_set[dev]) {
-        PB_CUDA(cudaFuncSetAttribute(k_m2l_tc<NPAD>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-        attr_set[dev] = true;
-    }
     dim3 grid(nitems, TcCfg<NPAD>::NS * TcCfg<NPAD>::KS, nsets);
     TcSets s2 = sets;
     s2.wait_limit = g_wait_limit.load();
+    if constexpr (NPAD >= 128) {
+        if (allow_pair && tc_pair_for(NPAD)) {
+            static bool done[64] = {false};
+            const size_t sm = tc_pair_smem_bytes<NPAD>();
+            smem_optin(k_m2l_tc2<NPAD>, sm, done);
+            cudaLaunchAttribute attr[1];
+            attr[0].id = cudaLaunchAttributeClusterDimension;
+            attr[0].val.clusterDim.x = 2;                // the two row parts of a part pair
+            attr[0].val.clusterDim.y = 1;
+            attr[0].val.clusterDim.z = 1;
+            for (int i0 = 0; i0 < nitems; i0 += 65535) {  // items along grid y
+                cudaLaunchConfig_t cfg = {};
+                cfg.gridDim = dim3(TcCfg<NPAD>::NS * TcCfg<NPAD>::KS, std::min(65535, nitems - i0), nsets);
+                cfg.blockDim = dim3(kTcThreads);
+                cfg.dynamicSmemBytes = sm;
+                cfg.stream = st;
+                cfg.attrs = attr;
+                cfg.numAttrs = 1;
+                PB_CUDA(cudaLaunchKernelEx(&cfg, k_m2l_tc2<NPAD>, items + i0, tgt, src, s2, err));
+                PB_CHECK_LAUNCH();
+            }
+            return;
+        }
+    }
+    static bool done[64] = {false};
+    const size_t sm = tc_smem_bytes<NPAD>();
+    smem_optin(k_m2l_tc<NPAD>, sm, done);
     k_m2l_tc<NPAD><<<grid, kTcThreads, sm, st>>>(items, tgt, src, s2, err);
     PB_CHECK_LAUNCH();
 }
 
+// allow_pair: the launch may use the CTA-pair kernel (the M2L, whose work
+// items hold up to 2,048 pairs; the M2M / L2L / solve items are smaller and
+// keep one CTA per operator part)
 static bool tc_dispatch(int npad, const int4* items, int nitems, const int* tgt, const int* src, const TcSets& sets,
-                        int nsets, int* err, cudaStream_t st) {
+                        int nsets, int* err, cudaStream_t st, bool allow_pair = false) {
     switch (npad) {
-        case 32: launch_tc_items<32>(items, nitems, tgt, src, sets, nsets, err, st); return true;
-        case 64: launch_tc_items<64>(items, nitems, tgt, src, sets, nsets, err, st); return true;
-        case 128: launch_tc_items<128>(items, nitems, tgt, src, sets, nsets, err, st); return true;
-        case 160: launch_tc_items<160>(items, nitems, tgt, src, sets, nsets, err, st); return true;
-        case 320: launch_tc_items<320>(items, nitems, tgt, src, sets, nsets, err, st); return true;
-        case 512: launch_tc_items<512>(items, nitems, tgt, src, sets, nsets, err, st); return true;
+        case 32: launch_tc_items<32>(items, nitems, tgt, src, sets, nsets, err, st, allow_pair); return true;
+        case 64: launch_tc_items<64>(items, nitems, tgt, src, sets, nsets, err, st, allow_pair); return true;
+        case 128: launch_tc_items<128>(items, nitems, tgt, src, sets, nsets, err, st, allow_pair); return true;
+        case 160: launch_tc_items<160>(items, nitems, tgt, src, sets, nsets, err, st, allow_pair); return true;
+        case 320: launch_tc_items<320>(items, nitems, tgt, src, sets, nsets, err, st, allow_pair); return true;
+        case 512: launch_tc_items<512>(items, nitems, tgt, src, sets, nsets, err, st, allow_pair); return true;
         default: return false;
     }
 }
@@ -627,7 +952,7 @@ bool m2l_tc_launch2(const fmm_tree* T, const Operators& O, const Operators* O2, 
     TcSets sets{{O.m2l_tc.p, O2 ? O2->m2l_tc.p : nullptr}, {Qu, Qu2}, {Qd, Qd2},
                 {O.m2l_tc_single ? 1 : 0, (O2 && O2->m2l_tc_single) ? 1 : 0}, 0};
     return tc_dispatch(O.npad, T->m2l_pairs.items.p, T->m2l_pairs.nitems, T->m2l_pairs.tgt.p, T->m2l_pairs.src.p,
-                       sets, O2 ? 2 : 1, err, st);
+                       sets, O2 ? 2 : 1, err, st, true);
 }
 
 bool m2l_tc_launch(const fmm_tree* T, const Operators& O, const float* Qu, float* Qd, int* err, cudaStream_t st) {
@@ -641,6 +966,43 @@ bool m2l_tc_launch(const fmm_tree* T, const Operators& O, const float* Qu, float
 // operator through the tensor-core M2L kernel, host buffers.
 // ---------------------------------------------------------------------------
 using namespace pbfmm;
+extern "C" int pbfmm_test_tc_pair(int mode) { return g_tc_pair.exchange(mode ? 1 : 0); }
+
+// launch properties of the CTA-pair kernel at npad 128 (no launch):
+// out = {registers, max threads per block, static shared bytes, dynamic
+// shared bytes requested, max co-resident clusters of two for that launch}
+extern "C" int pbfmm_test_tc_pair_info(int* out) {
+    try {
+        static bool done[64] = {false};
+        const size_t sm = tc_pair_smem_bytes<128>();
+        smem_optin(k_m2l_tc2<128>, sm, done);
+        cudaFuncAttributes fa;
+        PB_CUDA(cudaFuncGetAttributes(&fa, k_m2l_tc2<128>));
+        cudaLaunchConfig_t cfg = {};
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = 2;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.gridDim = dim3(2, 1, 1);
+        cfg.blockDim = dim3(kTcThreads);
+        cfg.dynamicSmemBytes = sm;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        int nclusters = -1;
+        PB_CUDA(cudaOccupancyMaxActiveClusters(&nclusters, k_m2l_tc2<128>, &cfg));
+        out[0] = fa.numRegs;
+        out[1] = fa.maxThreadsPerBlock;
+        out[2] = (int)fa.sharedSizeBytes;
+        out[3] = (int)sm;
+        out[4] = nclusters;
+        return PB_OK;
+    } catch (const Error& e) {
+        std::fprintf(stderr, "pbfmm_test_tc_pair_info: %s\n", e.what());
+        return e.code;
+    }
+}
+
 extern "C" int pbfmm_selftest_m2l_tc(int nrows, int npad, const float* Q, const float* Op, float* D) {
     try {
         int ns_, ks_;
@@ -676,12 +1038,30 @@ extern "C" int pbfmm_selftest_m2l_tc(int nrows, int npad, const float* Q, const 
         T.m2l_pairs.nitems = (int)items.size();
         T.m2l_pairs.items.alloc(items.size(), st);
         PB_CUDA(cudaMemcpyAsync(T.m2l_pairs.items.p, items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice, st));
-        m2l_tc_launch(&T, O, q.p, d.p, e.p, st);
-        int herr = 0;
-        PB_CUDA(cudaMemcpyAsync(&herr, e.p, 4, cudaMemcpyDeviceToHost, st));
-        PB_CUDA(cudaMemcpyAsync(D, d.p, (size_t)nrows * npad * 4, cudaMemcpyDeviceToHost, st));
-        PB_CUDA(cudaStreamSynchronize(st));
-        return herr ? PB_ETIMEOUT : PB_OK;
+        // progress markers of the CTA-pair kernel in host-mapped memory
+        int* trace_h = nullptr;
+        int* trace_d = nullptr;
+        PB_CUDA(cudaHostAlloc((void**)&trace_h, 16 * sizeof(int), cudaHostAllocMapped));
+        std::unique_ptr<int, void (*)(int*)> trace_guard(trace_h, [](int* p) { cudaFreeHost(p); });
+        for (int i = 0; i < 16; ++i) trace_h[i] = 0;
+        PB_CUDA(cudaHostGetDevicePointer((void**)&trace_d, trace_h, 0));
+        try {
+            TcSets sets{{O.m2l_tc.p, nullptr}, {q.p, nullptr}, {d.p, nullptr}, {O.m2l_tc_single ? 1 : 0, 0}, 0,
+                        trace_d};
+            if (!tc_dispatch(O.npad, T.m2l_pairs.items.p, T.m2l_pairs.nitems, T.m2l_pairs.tgt.p, T.m2l_pairs.src.p,
+                             sets, 1, e.p, st, true))
+                return PB_EINVAL;
+            int herr = 0;
+            PB_CUDA(cudaMemcpyAsync(&herr, e.p, 4, cudaMemcpyDeviceToHost, st));
+            PB_CUDA(cudaMemcpyAsync(D, d.p, (size_t)nrows * npad * 4, cudaMemcpyDeviceToHost, st));
+            PB_CUDA(cudaStreamSynchronize(st));
+            return herr ? PB_ETIMEOUT : PB_OK;
+        } catch (const Error& ex) {
+            std::fprintf(stderr, "pbfmm_selftest_m2l_tc: %s; pair-kernel markers:", ex.what());
+            for (int i = 0; i < 16; ++i) std::fprintf(stderr, " %d", ((volatile int*)trace_h)[i]);
+            std::fprintf(stderr, "\n");
+            throw;
+        }
     } catch (const Error& e) {
         return e.code;
     }

@@ -14,7 +14,8 @@
 // UC2UE / DC2DE themselves are needed where raw check potentials are
 // converted (P2M at leaves, P2L of X lists): in FP64 for the all-FP64 path,
 // and for the FP32 path in factored form, pinv = V D V^T K^T with
-// K^T K = V diag(mu) V^T (cyclic Jacobi, FP64, on the host) and
+// K^T K = V diag(mu) V^T (Householder tridiagonalisation and implicit
+// symmetric QR, FP64, on the host) and
 // D = diag(1 / (mu + lam)): W1 = D V^T K^T and W2 = V are well scaled, and the
 // FP32 rounding of W1 x is amplified only along eigenvectors of small mu,
 // whose equivalent densities produce correspondingly small fields away from
@@ -109,50 +110,112 @@ __global__ void k_chol_solve(int n, const double* __restrict__ L, const double* 
     }
 }
 
-// Symmetric eigendecomposition A = V diag(w) V^T by the cyclic Jacobi method
-// (plane rotations that annihilate one off-diagonal entry each, with the
-// rotation angle from theta = (a_qq - a_pp) / (2 a_pq), t = sgn(theta) /
-// (|theta| + sqrt(theta^2 + 1))). A (n x n, row-major) is overwritten.
-static void jacobi_eig(int n, std::vector<double>& A, std::vector<double>& V, std::vector<double>& w) {
-    V.assign((size_t)n * n, 0.0);
-    for (int i = 0; i < n; ++i) V[(size_t)i * n + i] = 1.0;
-    for (int sweep = 0; sweep < 60; ++sweep) {
-        double off = 0.0, dg = 0.0;
-        for (int i = 0; i < n; ++i) {
-            dg += A[(size_t)i * n + i] * A[(size_t)i * n + i];
-            for (int j = i + 1; j < n; ++j) off += A[(size_t)i * n + j] * A[(size_t)i * n + j];
+// Symmetric eigendecomposition A = V diag(w) V^T (A n x n, row-major,
+// overwritten; V[k * n + j] = component k of eigenvector j) in two stages:
+//  1. Householder tridiagonalisation Q^T A Q = T: reflection k maps the part
+//     of column k below the diagonal onto its first entry; the trailing
+//     block is updated as S - v w^T - w v^T with p = beta S v,
+//     w = p - (beta / 2)(v . p) v; Q^T = H_{n-3} ... H_0 is accumulated.
+//  2. Implicit symmetric QR steps with the Wilkinson shift (the eigenvalue
+//     of the trailing 2 x 2 block of the unreduced part nearer its last
+//     diagonal entry) on T, chasing the bulge with Givens rotations that
+//     are applied to the rows of Q^T as well; off-diagonal entries below
+//     eps (|d_i| + |d_i+1|) are set to zero and split the problem.
+// O(n^3) in all with unit-stride inner loops.
+static void sym_eig(int n, std::vector<double>& A, std::vector<double>& V, std::vector<double>& w) {
+    std::vector<double> d(n, 0.0), e(std::max(n - 1, 1), 0.0), Zt((size_t)n * n, 0.0), vv(n), pv(n), wv(n);
+    for (int i = 0; i < n; ++i) Zt[(size_t)i * n + i] = 1.0;
+    // 1. tridiagonalisation
+    for (int k = 0; k + 2 < n; ++k) {
+        const int m = n - k - 1;                  // trailing size
+        const double* row = &A[(size_t)k * n + k + 1];   // column k below the diagonal (symmetric)
+        double xn = 0.0;
+        for (int i = 0; i < m; ++i) xn += row[i] * row[i];
+        xn = std::sqrt(xn);
+        d[k] = A[(size_t)k * n + k];
+        if (xn == 0.0) { e[k] = 0.0; continue; }
+        const double alpha = row[0] > 0 ? -xn : xn;
+        for (int i = 0; i < m; ++i) vv[i] = row[i];
+        vv[0] -= alpha;
+        double vn2 = 0.0;
+        for (int i = 0; i < m; ++i) vn2 += vv[i] * vv[i];
+        e[k] = alpha;
+        if (vn2 == 0.0) continue;
+        const double beta = 2.0 / vn2;
+        // p = beta S v, S = A[k+1.., k+1..]
+        for (int i = 0; i < m; ++i) {
+            const double* Si = &A[(size_t)(k + 1 + i) * n + k + 1];
+            double acc = 0.0;
+            for (int j = 0; j < m; ++j) acc += Si[j] * vv[j];
+            pv[i] = beta * acc;
         }
-        if (off <= 1e-32 * dg) break;
-        for (int p = 0; p < n - 1; ++p)
-            for (int q = p + 1; q < n; ++q) {
-                const double apq = A[(size_t)p * n + q];
-                const double app = A[(size_t)p * n + p], aqq = A[(size_t)q * n + q];
-                if (std::fabs(apq) <= 1e-18 * std::sqrt(std::fabs(app * aqq))) {
-                    A[(size_t)p * n + q] = A[(size_t)q * n + p] = 0.0;
-                    continue;
-                }
-                const double th = (aqq - app) / (2.0 * apq);
-                const double t = (th >= 0 ? 1.0 : -1.0) / (std::fabs(th) + std::sqrt(th * th + 1.0));
-                const double c = 1.0 / std::sqrt(t * t + 1.0), sn = t * c;
-                for (int k = 0; k < n; ++k) {
-                    const double akp = A[(size_t)k * n + p], akq = A[(size_t)k * n + q];
-                    A[(size_t)k * n + p] = c * akp - sn * akq;
-                    A[(size_t)k * n + q] = sn * akp + c * akq;
-                }
-                for (int k = 0; k < n; ++k) {
-                    const double apk = A[(size_t)p * n + k], aqk = A[(size_t)q * n + k];
-                    A[(size_t)p * n + k] = c * apk - sn * aqk;
-                    A[(size_t)q * n + k] = sn * apk + c * aqk;
-                }
-                for (int k = 0; k < n; ++k) {
-                    const double vkp = V[(size_t)k * n + p], vkq = V[(size_t)k * n + q];
-                    V[(size_t)k * n + p] = c * vkp - sn * vkq;
-                    V[(size_t)k * n + q] = sn * vkp + c * vkq;
-                }
-            }
+        double vp = 0.0;
+        for (int i = 0; i < m; ++i) vp += vv[i] * pv[i];
+        const double K = 0.5 * beta * vp;
+        for (int i = 0; i < m; ++i) wv[i] = pv[i] - K * vv[i];
+        for (int i = 0; i < m; ++i) {
+            double* Si = &A[(size_t)(k + 1 + i) * n + k + 1];
+            const double vi = vv[i], wi = wv[i];
+            for (int j = 0; j < m; ++j) Si[j] -= vi * wv[j] + wi * vv[j];
+        }
+        // Q^T <- H_k Q^T: rows k+1 .. n-1 of Zt
+        for (int j = 0; j < n; ++j) pv[j] = 0.0;
+        for (int i = 0; i < m; ++i) {
+            const double* Zi = &Zt[(size_t)(k + 1 + i) * n];
+            const double vi = vv[i];
+            for (int j = 0; j < n; ++j) pv[j] += vi * Zi[j];
+        }
+        for (int i = 0; i < m; ++i) {
+            double* Zi = &Zt[(size_t)(k + 1 + i) * n];
+            const double f = beta * vv[i];
+            for (int j = 0; j < n; ++j) Zi[j] -= f * pv[j];
+        }
     }
-    w.resize(n);
-    for (int i = 0; i < n; ++i) w[i] = A[(size_t)i * n + i];
+    if (n >= 2) {
+        d[n - 2] = A[(size_t)(n - 2) * n + n - 2];
+        e[n - 2] = A[(size_t)(n - 1) * n + n - 2];
+    }
+    d[n - 1] = A[(size_t)(n - 1) * n + n - 1];
+    // 2. implicit symmetric QR with Wilkinson shifts
+    const double eps = 2.220446049250313e-16;
+    auto small = [&](int i) { return std::fabs(e[i]) <= eps * (std::fabs(d[i]) + std::fabs(d[i + 1])); };
+    int hi = n - 1, guard = 0;
+    while (hi > 0 && guard < 60 * n) {
+        if (small(hi - 1)) { e[hi - 1] = 0.0; --hi; continue; }
+        int lo = hi - 1;
+        while (lo > 0 && !small(lo - 1)) --lo;
+        ++guard;
+        // shift: eigenvalue of [[d_{hi-1}, e_{hi-1}], [e_{hi-1}, d_hi]] nearer d_hi
+        const double b = e[hi - 1], delta = 0.5 * (d[hi - 1] - d[hi]);
+        const double den = delta + (delta >= 0 ? 1.0 : -1.0) * std::hypot(delta, b);
+        const double mu = d[hi] - b * b / den;
+        double x = d[lo] - mu, z = e[lo];
+        for (int k = lo; k < hi; ++k) {
+            const double r = std::hypot(x, z);
+            const double c = r > 0 ? x / r : 1.0, sn = r > 0 ? z / r : 0.0;
+            if (k > lo) e[k - 1] = r;
+            const double dk = d[k], dk1 = d[k + 1], ek = e[k];
+            d[k] = c * c * dk + 2.0 * c * sn * ek + sn * sn * dk1;
+            d[k + 1] = sn * sn * dk - 2.0 * c * sn * ek + c * c * dk1;
+            e[k] = c * sn * (dk1 - dk) + (c * c - sn * sn) * ek;
+            if (k + 1 < hi) {
+                z = sn * e[k + 1];               // bulge at (k + 2, k)
+                e[k + 1] *= c;
+                x = e[k];
+            }
+            double* Zk = &Zt[(size_t)k * n];
+            double* Zk1 = &Zt[(size_t)(k + 1) * n];
+            for (int j = 0; j < n; ++j) {
+                const double a0 = Zk[j], a1 = Zk1[j];
+                Zk[j] = c * a0 + sn * a1;
+                Zk1[j] = -sn * a0 + c * a1;
+            }
+        }
+    }
+    w = d;
+    V.assign((size_t)n * n, 0.0);
+    for (int j = 0; j < n; ++j)
+        for (int k = 0; k < n; ++k) V[(size_t)k * n + j] = Zt[(size_t)j * n + k];
 }
 
 // Factored Tikhonov pseudo-inverse of K(check surface at scale tscale,
@@ -160,7 +223,7 @@ static void jacobi_eig(int n, std::vector<double>& A, std::vector<double>& V, st
 // W1 = D V^T K^T and W2 = V, written padded to npad x npad in FP32.
 static void factored_pinv(int n, int npad, int kernel, double kappa, const std::vector<double>& surf, double tscale,
                           double sscale, float* W1, float* W2) {
-    std::vector<double> K((size_t)n * n), G((size_t)n * n), V, mu;
+    std::vector<double> K((size_t)n * n), G((size_t)n * n, 0.0), V, mu, KV((size_t)n * n, 0.0);
     double fro = 0.0;
     for (int i = 0; i < n; ++i)
         for (int j = 0; j < n; ++j) {
@@ -173,23 +236,33 @@ static void factored_pinv(int n, int npad, int kernel, double kappa, const std::
             K[(size_t)i * n + j] = g;
             fro += g * g;
         }
-    for (int i = 0; i < n; ++i)
-        for (int j = i; j < n; ++j) {
-            double a = 0.0;
-            for (int k = 0; k < n; ++k) a += K[(size_t)k * n + i] * K[(size_t)k * n + j];
-            G[(size_t)i * n + j] = G[(size_t)j * n + i] = a;
+    // G = K^T K (upper triangle by rows of K, then mirrored)
+    for (int k = 0; k < n; ++k) {
+        const double* Kk = &K[(size_t)k * n];
+        for (int i = 0; i < n; ++i) {
+            const double a = Kk[i];
+            double* Gi = &G[(size_t)i * n];
+            for (int j = i; j < n; ++j) Gi[j] += a * Kk[j];
         }
-    jacobi_eig(n, G, V, mu);
+    }
+    for (int i = 0; i < n; ++i)
+        for (int j = 0; j < i; ++j) G[(size_t)i * n + j] = G[(size_t)j * n + i];
+    sym_eig(n, G, V, mu);
     const double lam = 1e-14 * fro;
+    // KV = K V
+    for (int i = 0; i < n; ++i) {
+        double* KVi = &KV[(size_t)i * n];
+        for (int k = 0; k < n; ++k) {
+            const double a = K[(size_t)i * n + k];
+            const double* Vk = &V[(size_t)k * n];
+            for (int j = 0; j < n; ++j) KVi[j] += a * Vk[j];
+        }
+    }
     std::fill(W1, W1 + (size_t)npad * npad, 0.f);
     std::fill(W2, W2 + (size_t)npad * npad, 0.f);
     for (int j = 0; j < n; ++j) {
-        const double d = 1.0 / (std::max(mu[j], 0.0) + lam);
-        for (int i = 0; i < n; ++i) {
-            double a = 0.0;
-            for (int k = 0; k < n; ++k) a += K[(size_t)i * n + k] * V[(size_t)k * n + j];
-            W1[(size_t)j * npad + i] = (float)(d * a);
-        }
+        const double dj = 1.0 / (std::max(mu[j], 0.0) + lam);
+        for (int i = 0; i < n; ++i) W1[(size_t)j * npad + i] = (float)(dj * KV[(size_t)i * n + j]);
     }
     for (int i = 0; i < n; ++i)
         for (int j = 0; j < n; ++j) W2[(size_t)i * npad + j] = (float)V[(size_t)i * n + j];
@@ -461,3 +534,14 @@ std::shared_ptr<Operators> get_operators(fmm_tree* T, int kernel, double kappa, 
 }
 
 }  // namespace pbfmm
+
+// test hook (include/pbfmm_testing.h): the host eigensolver of the factored
+// pseudo-inverses; no GPU involved
+extern "C" int pbfmm_test_sym_eig(int n, const double* A, double* w, double* V) {
+    if (n < 1 || !A || !w || !V) return PB_EINVAL;
+    std::vector<double> a(A, A + (size_t)n * n), vv, ww;
+    pbfmm::sym_eig(n, a, vv, ww);
+    std::copy(ww.begin(), ww.end(), w);
+    std::copy(vv.begin(), vv.end(), V);
+    return PB_OK;
+}

@@ -106,7 +106,11 @@ def test_tcgen05_m2l_kernel(pb, npad, nrows):
     rng = np.random.default_rng(npad + nrows)
     Q = rng.uniform(-1, 1, (nrows, npad)).astype(np.float32)
     Op = rng.uniform(-1, 1, (npad, npad)).astype(np.float32)
-    D = pb._selftest_m2l_tc(Q, Op)
+    prev = pb._test_tc_pair(0)             # the single-CTA kernel
+    try:
+        D = pb._selftest_m2l_tc(Q, Op)
+    finally:
+        pb._test_tc_pair(prev)
     ref = Q.astype(np.float64) @ Op.astype(np.float64).T
     absum = np.abs(Q.astype(np.float64)) @ np.abs(Op.astype(np.float64)).T
     err = np.abs(D - ref)
@@ -117,6 +121,41 @@ def test_tcgen05_m2l_kernel(pb, npad, nrows):
     # statistically far inside the bound: the per-term errors have random
     # signs, so the measured error sits near 2^-22 of the absolute sum
     assert np.max(err / absum) < 4 * 2.0 ** -22
+
+
+# operator sizes with the CTA-pair (cta_group::2) variant of the kernel
+PAIR_NPADS = (128, 160, 320, 512)
+
+
+@pytest.mark.parametrize("npad,nrows", [(npad, nrows) for npad in PAIR_NPADS for nrows in (1, 257, 2500)])
+def test_tcgen05_pair_kernel(pb, npad, nrows):
+    """The CTA-pair variant (clusters of two CTAs, M = 256 MMAs whose A rows
+    and B columns come from both CTAs): D = Q Op^T within the same 3xTF32
+    bound as the single-CTA kernel, and equal to it up to the FP32
+    accumulation order (one pair, a ragged half tile, several items)."""
+    info = pb._test_tc_pair_info()
+    print(f"CTA-pair kernel: {info}")
+    assert info["max_active_clusters"] > 0
+    rng = np.random.default_rng(7 * npad + nrows)
+    Q = rng.uniform(-1, 1, (nrows, npad)).astype(np.float32)
+    Op = rng.uniform(-1, 1, (npad, npad)).astype(np.float32)
+    prev = pb._test_tc_pair(1)
+    try:
+        D = pb._selftest_m2l_tc(Q, Op)
+    finally:
+        pb._test_tc_pair(0)
+    try:
+        D1 = pb._selftest_m2l_tc(Q, Op)
+    finally:
+        pb._test_tc_pair(prev)
+    ref = Q.astype(np.float64) @ Op.astype(np.float64).T
+    absum = np.abs(Q.astype(np.float64)) @ np.abs(Op.astype(np.float64)).T
+    err = np.abs(D - ref)
+    print(f"tcgen05 pair npad={npad} rows={nrows}: max err / bound {np.max(err / (split3_bound(npad) * absum)):.3f}, "
+          f"max |pair - single| / sum|q||o| {np.max(np.abs(D - D1) / absum):.3e}")
+    assert np.all(err <= split3_bound(npad) * absum)
+    assert np.max(err / absum) < 4 * 2.0 ** -22
+    assert np.all(np.abs(D - D1) <= split3_bound(npad) * absum)
 
 
 def fmm_case(n, seed=0):
@@ -406,6 +445,25 @@ def test_pair_equals_two_applies_low_order(pb, ctx, case20k, p):
     assert rel_l2(oL, sL) < 1e-6 and rel_l2(oY, sY) < 1e-6
 
 
+@pytest.mark.parametrize("p", [5, 6, 8, 10])
+def test_pair_mode_apply(pb, ctx, case20k, p):
+    """A whole paired apply with the CTA-pair box-operator kernel (M2L, M2M,
+    L2L and the check -> equivalent solves) gives the single-CTA results
+    and the same distance to the direct sum."""
+    x, nrm, q, d, h = case20k
+    prev = pb._test_tc_pair(1)
+    try:
+        oL, oY = run_pair(pb, ctx, h, 0.125, p, qL=q, qY=q, d=d, sn=nrm, nt=len(x))
+    finally:
+        pb._test_tc_pair(0)
+    try:
+        sL, sY = run_pair(pb, ctx, h, 0.125, p, qL=q, qY=q, d=d, sn=nrm, nt=len(x))
+    finally:
+        pb._test_tc_pair(prev)
+    print(f"pair-mode apply p={p}: rel L2 vs single-CTA {rel_l2(oL, sL):.2e} / {rel_l2(oY, sY):.2e}")
+    assert rel_l2(oL, sL) < 1e-6 and rel_l2(oY, sY) < 1e-6
+
+
 # ---------------------------------------------------------------------------
 # the expansion orders and leaf sizes of the 4M-point sweep, on the 20k case
 # ---------------------------------------------------------------------------
@@ -434,8 +492,8 @@ def ref20k(case20k):
 @pytest.mark.parametrize("p", [4, 5, 6, 8, 10])
 def test_pair_orders_vs_direct(pb, ctx, case20k, ref20k, p, prec):
     """Paired apply (SL + DL, both kernels) at every order of the sweep, in
-    both precisions (p <= 6 mixed: tensor-core box operators; p = 8, 10
-    mixed: the CUDA-core M2L), against the FP64 direct sum."""
+    both precisions (mixed: tensor-core box operators at every order; FP64:
+    the CUDA-core kernels), against the FP64 direct sum."""
     x, nrm, q, d, h = case20k
     oL, oY = run_pair(pb, ctx, h, 0.125, p, qL=q, qY=q, d=d, sn=nrm, nt=len(x), fp64=prec == "fp64")
     err = max(rel_l2(oL, ref20k[0]), rel_l2(oY, ref20k[1]))
