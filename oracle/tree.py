@@ -10,8 +10,9 @@ the kernel-independent FMM it cites (Ying, Biros, Zorin 2004).
 
 Readings (the paper is silent on these):
   * cube: centre = midpoint of the coordinate min/max (FP32 values promoted
-    to FP64); half-width R = (0.5 * max extent) * (1 + 2^-20); R = 1 if all
-    points coincide.
+    to FP64); half-width R = the smallest power of two >= (0.5 * max
+    extent) * (1 + 2^-20), so that trees of similar size share their boxes'
+    sizes (and translation operators); R = 1 if all points coincide.
   * Morton integer per axis: floor((x - lo) * (2^21 / (2R))), clamped to
     [0, 2^21 - 1], every step a correctly rounded FP64 operation.
   * keys interleave x, y, z bits from the most significant bit (63 bits);
@@ -22,6 +23,8 @@ Readings (the paper is silent on these):
   * adjacency = the closed cubes intersect.
 """
 from __future__ import annotations
+
+import math
 
 import numpy as np
 
@@ -37,8 +40,9 @@ def bounding_cube(points_list):
     ext = float((hi - lo).max())
     R = (0.5 * ext) * (1.0 + 2.0 ** -20)
     if R == 0.0:
-        R = 1.0
-    return c, R
+        return c, 1.0
+    m, e = math.frexp(R)            # R = m 2^e, 0.5 <= m < 1 (exact)
+    return c, (R if m == 0.5 else math.ldexp(1.0, e))
 
 
 def morton_keys(points, c, R):

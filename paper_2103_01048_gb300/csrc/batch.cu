@@ -10,8 +10,9 @@
 // index from device memory, so the same graph is replayed every iteration;
 // a system that converges marks itself done on the device and its Arnoldi
 // kernels return at once.  The host launches the graph, reads the systems'
-// done flags (one synchronisation per iteration) and re-captures the graph
-// without the converged systems, so their mat-vecs stop too.
+// done flags (one synchronisation per iteration) and, once a quarter of the
+// systems in the graph have converged, re-captures it without them, so their
+// mat-vecs stop too.
 #include "bem.cuh"
 #include <algorithm>
 #include <cmath>
@@ -359,11 +360,15 @@ void solve_batch(pb_ctx* ctx, pb_mesh* const* meshes, int nsys, pb_result** resu
                                  (int)std::max<size_t>(48 * 1024, (max_iter + 1) * sizeof(double))));
     int nactive = 0;
     for (auto& Sp : sys) nactive += Sp->active ? 1 : 0;
-    bool rebuild = true;
+    int captured = 0;           // active systems when the graph was captured
     for (int it = 0; it < max_iter && nactive > 0; ++it) {
-        if (rebuild) {
+        // a finished system's Arnoldi kernels return at once, but its
+        // mat-vec still runs: re-capture once a quarter of the captured
+        // systems have finished (not for every one, which at hundreds of
+        // systems would cost more than it saves)
+        if (captured == 0 || 4 * nactive <= 3 * captured) {
             capture();
-            rebuild = false;
+            captured = nactive;
         }
         PB_CUDA(cudaGraphLaunch(exec, origin));
         PB_CUDA(cudaStreamSynchronize(origin));
@@ -377,7 +382,6 @@ void solve_batch(pb_ctx* ctx, pb_mesh* const* meshes, int nsys, pb_result** resu
                 S.j = hflags[s].m;
                 S.status = S.R->residual <= tol ? PB_OK : PB_ENOCONV;
                 --nactive;
-                rebuild = true;
             }
         }
     }

@@ -3,6 +3,9 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string>
+#include <tuple>
+#include <memory>
+#include <map>
 #include <vector>
 #include <cstdio>
 #include <cstring>
@@ -138,6 +141,10 @@ struct pb_ctx {
     // apply; null: everything on `stream`
     cudaStream_t aux = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    // translation-operator sets shared by the context's trees, keyed by
+    // (kernel, kappa, p, root half-width, levels); weak references, so a set
+    // lives as long as some tree uses it
+    std::map<std::tuple<int, double, int, double, int>, std::weak_ptr<void>> op_cache;
 };
 
 namespace pbfmm {

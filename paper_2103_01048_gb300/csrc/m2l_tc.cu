@@ -39,6 +39,7 @@ void radix_sort_pairs(const unsigned* keys_in, const int* vals_in, unsigned* key
 constexpr int kTcRows = 128;           // pairs per row tile (MMA M)
 constexpr int kTcItemPairs = 2048;     // pairs per M2L work item (one operator load each)
 constexpr int kTcSmallItemPairs = 512; // M2M / L2L / check->equivalent items: fewer pairs per operator, more CTAs
+constexpr int kTcOffItemPairs = 8192;  // items of a level-invariant M2L set (one offset, all levels)
 
 // Operator split per padded size: NS parts of the output rows (MMA N =
 // npad / NS) times KS parts of the inner dimension (npad / KS columns,
@@ -128,7 +129,7 @@ __global__ void k_pairs_emit(int nbox, const int* V, const int* V_n, const int* 
         int4 as = anchor[s];
         int o = (as.x - ab.x + 3) * 49 + (as.y - ab.y + 3) * 7 + (as.z - ab.z + 3);
         int e = V_off[b] + i;
-        key[e] = ab.w * kNumOffsets + o;
+        key[e] = o * 32 + ab.w;            // offset-major, then level (< 22)
         tgt[e] = b;
         src[e] = s;
     }
@@ -163,9 +164,9 @@ void build_m2l_pairs(fmm_tree* T) {
     std::vector<int> hidx(np);
     for (long long i = 0; i < np; ++i) hidx[i] = (int)i;
     PB_CUDA(cudaMemcpyAsync(idx.p, hidx.data(), np * sizeof(int), cudaMemcpyHostToDevice, st));
-    // group by (level, offset) keeping each group in box order (stable sort;
-    // level * 343 + offset < 2^13)
-    radix_sort_pairs((const unsigned*)key.p, idx.p, (unsigned*)key_s.p, idx_s.p, np, 13, st);
+    // group by (offset, level) keeping each group in box order (stable sort;
+    // offset * 32 + level < 2^14)
+    radix_sort_pairs((const unsigned*)key.p, idx.p, (unsigned*)key_s.p, idx_s.p, np, 14, st);
     P.tgt.alloc(np, st);
     P.src.alloc(np, st);
     k_gather_int<<<div_up(np, 256), 256, 0, st>>>((int)np, idx_s.p, tgt.p, P.tgt.p);
@@ -174,16 +175,32 @@ void build_m2l_pairs(fmm_tree* T) {
     std::vector<int> hk(np);
     PB_CUDA(cudaMemcpyAsync(hk.data(), key_s.p, np * sizeof(int), cudaMemcpyDeviceToHost, st));
     PB_CUDA(cudaStreamSynchronize(st));
-    // work items: (first pair, pair count <= kTcItemPairs, operator index = level * 343 + offset, 0)
-    std::vector<int4> items;
+    // work items: (first pair, pair count <= kTcItemPairs, operator index =
+    // level * 343 + offset, 0) per (offset, level) group; and per offset
+    // (all levels, <= kTcOffItemPairs pairs, operator index = offset) for a
+    // level-invariant operator set
+    std::vector<int4> items, items_off;
     long long i = 0;
     while (i < np) {
         long long j = i;
         while (j < np && hk[j] == hk[i]) ++j;
+        const int off = hk[i] / 32, lvl = hk[i] % 32;
         for (long long a = i; a < j; a += kTcItemPairs)
-            items.push_back(make_int4((int)a, (int)std::min<long long>(kTcItemPairs, j - a), hk[i], 0));
+            items.push_back(make_int4((int)a, (int)std::min<long long>(kTcItemPairs, j - a), lvl * kNumOffsets + off, 0));
         i = j;
     }
+    i = 0;
+    while (i < np) {
+        long long j = i;
+        while (j < np && hk[j] / 32 == hk[i] / 32) ++j;
+        for (long long a = i; a < j; a += kTcOffItemPairs)
+            items_off.push_back(make_int4((int)a, (int)std::min<long long>(kTcOffItemPairs, j - a), hk[i] / 32, 0));
+        i = j;
+    }
+    P.nitems_off = (int)items_off.size();
+    P.items_off.alloc(items_off.size(), st);
+    PB_CUDA(cudaMemcpyAsync(P.items_off.p, items_off.data(), items_off.size() * sizeof(int4), cudaMemcpyHostToDevice,
+                            st));
     P.nitems = (int)items.size();
     P.items.alloc(items.size(), st);
     PB_CUDA(cudaMemcpyAsync(P.items.p, items.data(), items.size() * sizeof(int4), cudaMemcpyHostToDevice, st));
@@ -314,6 +331,7 @@ struct TcSets {
     int single[2];           // 1: the set holds one level of M2L operators, indexed by offset alone
     long long wait_limit;    // cycles a role waits on a barrier before giving up (set at launch)
     int* trace;              // optional progress markers of the CTA-pair kernel (host-mapped), or null
+    int ncols;               // output columns that can be nonzero (n_e; the rest is padding); 0: all
 };
 
 // progress marker of the CTA-pair kernel (self-test diagnostics): slot k of
@@ -607,6 +625,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     const int opi = sets.single[blockIdx.z] ? it.z % kNumOffsets : it.z;
     const int ntile = (npairs + TILE - 1) / TILE;
     const int rofs = (int)rank * kTcRows;            // this CTA's rows of a tile
+    const int ncols = sets.ncols > 0 ? sets.ncols : NPAD;
+    static_assert(NP % (2 * kTcEpiLd) == 0, "epilogue chunks");
 
     if (tid == 0) {
         mbar_init(&S->barB, 1);
@@ -706,22 +726,37 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             if (!__all_sync(0xffffffffu, ok)) break;
             tc_fence_after();
             float (*buf)[kTcEpiStride] = S->epi[q];
-#pragma unroll 1
-            for (int c0 = 0; c0 < NP; c0 += kTcEpiLd) {
-                float v[kTcEpiLd];
-                tmem_ld16(taddr + ((uint32_t)(q * 32) << 16) + a * ACOLS + c0, v);
+            const uint32_t tbase = taddr + ((uint32_t)(q * 32) << 16) + a * ACOLS;
+            // one 16-column chunk: transpose through shared memory so that a
+            // reduction instruction covers 8 rows x 64 B, skip padding columns
+            auto drain = [&](const uint32_t* r, int c0) {
 #pragma unroll
                 for (int cc = 0; cc < kTcEpiLd; cc += 4)
-                    *(float4*)&buf[lane][cc] = make_float4(v[cc], v[cc + 1], v[cc + 2], v[cc + 3]);
+                    *(float4*)&buf[lane][cc] = make_float4(__uint_as_float(r[cc]), __uint_as_float(r[cc + 1]),
+                                                           __uint_as_float(r[cc + 2]), __uint_as_float(r[cc + 3]));
                 __syncwarp();
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
                     const int rr = j * 8 + (lane >> 2), cc = (lane & 3) * 4;
                     const float4 x = *(const float4*)&buf[rr][cc];
                     const int tr = __shfl_sync(0xffffffffu, t, rr);
-                    if (tr >= 0) red_add_v4(Qd + (size_t)tr * NPAD + nsp * NP + c0 + cc, x.x, x.y, x.z, x.w);
+                    const int col = nsp * NP + c0 + cc;
+                    if (tr >= 0 && col < ncols) red_add_v4(Qd + (size_t)tr * NPAD + col, x.x, x.y, x.z, x.w);
                 }
                 __syncwarp();
+            };
+            // the next chunk's TMEM load runs while the current one drains
+            uint32_t ra[kTcEpiLd], rb[kTcEpiLd];
+            tmem_ld16_issue(tbase, ra);
+            tmem_wait16(ra);
+#pragma unroll 1
+            for (int c0 = 0; c0 < NP; c0 += 2 * kTcEpiLd) {        // NP is a multiple of 32
+                tmem_ld16_issue(tbase + c0 + kTcEpiLd, rb);
+                drain(ra, c0);
+                tmem_wait16(rb);
+                if (c0 + 2 * kTcEpiLd < NP) tmem_ld16_issue(tbase + c0 + 2 * kTcEpiLd, ra);
+                drain(rb, c0 + kTcEpiLd);
+                if (c0 + 2 * kTcEpiLd < NP) tmem_wait16(ra);
             }
             tc_fence_before();
             __syncwarp();
@@ -949,10 +984,23 @@ bool m2l_tc_launch2(const fmm_tree* T, const Operators& O, const Operators* O2, 
                     const float* Qu2, float* Qd2, int* err, cudaStream_t st) {
     if (!tc_ok(O) || (O2 && (!tc_ok(*O2) || O2->npad != O.npad))) return false;
     if (T->m2l_pairs.nitems == 0) return true;
-    TcSets sets{{O.m2l_tc.p, O2 ? O2->m2l_tc.p : nullptr}, {Qu, Qu2}, {Qd, Qd2},
-                {O.m2l_tc_single ? 1 : 0, (O2 && O2->m2l_tc_single) ? 1 : 0}, 0};
-    return tc_dispatch(O.npad, T->m2l_pairs.items.p, T->m2l_pairs.nitems, T->m2l_pairs.tgt.p, T->m2l_pairs.src.p,
-                       sets, O2 ? 2 : 1, err, st, true);
+    const auto& P = T->m2l_pairs;
+    const bool single1 = O.m2l_tc_single, single2 = O2 && O2->m2l_tc_single;
+    if (!single1 && !single2) {
+        // both sets per (level, offset): one launch, grid z selects the set
+        TcSets sets{{O.m2l_tc.p, O2 ? O2->m2l_tc.p : nullptr}, {Qu, Qu2}, {Qd, Qd2}, {0, 0}, 0, nullptr, O.ne};
+        return tc_dispatch(O.npad, P.items.p, P.nitems, P.tgt.p, P.src.p, sets, O2 ? 2 : 1, err, st, true);
+    }
+    // a level-invariant set takes the per-offset items (every level of an
+    // offset under one operator load); the other set its per-level items
+    auto one = [&](const Operators& o, const float* X, float* Y) {
+        TcSets sets{{o.m2l_tc.p, nullptr}, {X, nullptr}, {Y, nullptr}, {o.m2l_tc_single ? 1 : 0, 0}, 0, nullptr, o.ne};
+        if (o.m2l_tc_single && P.nitems_off > 0)
+            return tc_dispatch(o.npad, P.items_off.p, P.nitems_off, P.tgt.p, P.src.p, sets, 1, err, st, true);
+        return tc_dispatch(o.npad, P.items.p, P.nitems, P.tgt.p, P.src.p, sets, 1, err, st, true);
+    };
+    if (!one(O, Qu, Qd)) return false;
+    return O2 ? one(*O2, Qu2, Qd2) : true;
 }
 
 bool m2l_tc_launch(const fmm_tree* T, const Operators& O, const float* Qu, float* Qd, int* err, cudaStream_t st) {

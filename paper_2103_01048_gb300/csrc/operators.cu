@@ -403,6 +403,18 @@ std::shared_ptr<Operators> get_operators(fmm_tree* T, int kernel, double kappa, 
     auto key = std::make_tuple(kernel, kernel == FMM_YUKAWA ? kappa : 0.0, p, T->nlev);
     auto it = T->ops.find(key);
     if (it != T->ops.end() && (!need_fp64 || it->second->have_d)) return it->second;
+    // another tree of the context with the same box sizes may hold the set
+    const auto gkey = std::make_tuple(kernel, kernel == FMM_YUKAWA ? kappa : 0.0, p, T->R, T->nlev);
+    {
+        auto g = T->ctx->op_cache.find(gkey);
+        if (g != T->ctx->op_cache.end()) {
+            auto sp = std::static_pointer_cast<Operators>(g->second.lock());
+            if (sp && (!need_fp64 || sp->have_d)) {
+                T->ops[key] = sp;
+                return sp;
+            }
+        }
+    }
     cudaStream_t st = T->ctx->stream;
     auto O = std::make_shared<Operators>();
     O->kernel = kernel;
@@ -530,6 +542,9 @@ std::shared_ptr<Operators> get_operators(fmm_tree* T, int kernel, double kappa, 
     pack_m2l_tc(*O, st);
     PB_CUDA(cudaStreamSynchronize(st));
     T->ops[key] = O;
+    auto& cache = T->ctx->op_cache;
+    for (auto g = cache.begin(); g != cache.end();) g = g->second.expired() ? cache.erase(g) : std::next(g);
+    cache[gkey] = std::static_pointer_cast<void>(O);
     return O;
 }
 

@@ -435,8 +435,17 @@ void build_tree(fmm_tree* T, const float* src, const float* tgt) {
         T->c[a] = (lo + hi) * 0.5;
         ext = std::max(ext, hi - lo);
     }
+    // half-width: the smallest power of two >= half the extent (slightly
+    // enlarged), so that trees of similar size share box sizes and hence
+    // translation operators
     T->R = (0.5 * ext) * (1.0 + 1.0 / 1048576.0);
-    if (T->R == 0.0) T->R = 1.0;
+    if (T->R == 0.0) {
+        T->R = 1.0;
+    } else {
+        int e = 0;
+        const double m = std::frexp(T->R, &e);     // R = m 2^e, 0.5 <= m < 1 (exact)
+        if (m != 0.5) T->R = std::ldexp(1.0, e);
+    }
     const double lo3[3] = {T->c[0] - T->R, T->c[1] - T->R, T->c[2] - T->R};
     const double scale = (double)(1 << kMaxLevel) / (2.0 * T->R);
 

@@ -35,6 +35,10 @@ struct M2LPairs {
     long long npairs = 0;
     DBuf<int4> items32;        // the same groups in chunks of at most 32 pairs (CUDA-core M2L)
     int nitems32 = 0;
+    // items of a level-invariant operator set (Laplace): all levels of one
+    // offset together (the pairs are ordered by offset, then level)
+    DBuf<int4> items_off;
+    int nitems_off = 0;
 };
 
 // Parent-child pairs (children of level >= 3) grouped by (level, octant) for

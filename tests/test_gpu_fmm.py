@@ -554,3 +554,34 @@ def test_radix_sort_stable(pb, n):
     ko, vo = pb._test_radix_sort(small, vals, 13)
     order = np.argsort(small, kind="stable")
     assert np.array_equal(ko, small[order]) and np.array_equal(vo, vals[order])
+
+
+def test_operators_shared_between_trees(pb, ctx, case20k, ref20k):
+    """Trees of one context with the same box sizes (root half-widths are
+    powers of two) share their translation operators: the first apply on a
+    translated copy of the points makes far fewer device allocations than
+    the first apply on the original, and both agree with the direct sum."""
+    x, nrm, q, d, _ = case20k
+    xB = (x + np.array([3.0, -1.0, 2.0])).astype(x.dtype)
+    hA = pb.fmm_tree_build(ctx, dev(x), 64)
+    hB = pb.fmm_tree_build(ctx, dev(xB), 64)
+    try:
+        assert pb.fmm_tree_info(hA).n_levels == pb.fmm_tree_info(hB).n_levels
+        n0 = pb._test_alloc_count()
+        oA = run_pair(pb, ctx, hA, 0.0625, 6, qL=q, qY=q, d=d, sn=nrm, nt=len(x))
+        nA = pb._test_alloc_count() - n0
+        n1 = pb._test_alloc_count()
+        oB = run_pair(pb, ctx, hB, 0.0625, 6, qL=q, qY=q, d=d, sn=nrm, nt=len(x))
+        nB = pb._test_alloc_count() - n1
+    finally:
+        pb.fmm_tree_destroy(hA)
+        pb.fmm_tree_destroy(hB)
+    print(f"first-apply allocations: tree A {nA}, tree B (shared operators) {nB}")
+    assert nB + 10 < nA
+    # each tree against the direct sum over its own FP32 coordinates (the
+    # rounding of x + shift moves near-coincident points enough to change
+    # the double-layer sums by ~1e-2)
+    for o, pts in ((oA, x), (oB, xB)):
+        refL = direct_sum(LAPLACE, 0.0, pts, q=q, dip=d, src_n=nrm)
+        refY = direct_sum(YUKAWA, 0.0625, pts, q=q, dip=d, src_n=nrm)
+        assert rel_l2(o[0], refL) < TOL and rel_l2(o[1], refY) < TOL

@@ -140,6 +140,19 @@ def test_cube_rules():
     pts = np.array([[0, 0, 0], [1, 2, 0.5]], dtype=np.float32)
     c, R = ot.bounding_cube([pts])
     assert np.allclose(c, [0.5, 1.0, 0.25])
-    assert R == 1.0 * (1 + 2.0 ** -20)
+    # half the extent is 1, enlarged by 2^-20, rounded up to a power of two
+    assert R == 2.0
     c1, R1 = ot.bounding_cube([np.ones((3, 3), dtype=np.float32)])
     assert R1 == 1.0
+    # an extent whose enlarged half is already a power of two keeps it, and
+    # every cube encloses its points with R a power of two
+    _, R2 = ot.bounding_cube([np.array([[0, 0, 0], [2.0 / (1 + 2.0 ** -20), 0, 0]])])
+    assert R2 == 1.0
+    rng = np.random.default_rng(3)
+    for _ in range(20):
+        p = rng.uniform(-5, 5, (50, 3)).astype(np.float32) * rng.uniform(0.01, 100)
+        c3, R3 = ot.bounding_cube([p])
+        m, e = np.frexp(R3)
+        assert m == 0.5
+        assert np.all(np.abs(p.astype(np.float64) - c3) <= R3)
+        assert R3 < 2 * 0.5 * np.ptp(p.astype(np.float64), axis=0).max() * (1 + 2.0 ** -20) + 1e-300
