@@ -85,6 +85,8 @@ def parse():
     ap.add_argument("--binding", type=int, default=0, metavar="N",
                     help="batched binding energies of N synthetic complexes (receptor 500-2,000 atoms, ligand "
                          "20-300 atoms; 3N meshes) in one pb_solve_batch")
+    ap.add_argument("--binding-form", choices=["exterior", "direct"], default="direct",
+                    help="formulation of --binding: exterior derivative (P1, Eq. lu) or direct (P0)")
     ap.add_argument("--kirkwood", action="store_true",
                     help="off-centre-charge sphere refinement study (512 ... 131,072 elements)")
     return ap.parse_args()
@@ -298,13 +300,20 @@ def run_binding(args):
     import paper_2103_01048_gb300 as pb
     C = 332.0637
     ctx = pb.pb_create(0, None)
+    # singular entries with the FP32 4-level rule for every mesh (the FP64
+    # 5-level rule, the default below 262,144 triangles, runs at the FP64
+    # rate); its effect on dG is measured on one ligand below
+    pb.pb_set_option(ctx, pb.PB_OPT_SINGULAR, 2)
+    ext = args.binding_form == "exterior"
+    form = pb.PB_FORM_EXTERIOR if ext else pb.PB_FORM_DIRECT
+    basis = pb.PB_P1 if ext else pb.PB_P0
     meshes, atoms_l, q_l, coul = [], [], [], []
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     for spec, cx in gen:
         for k in ("cplx", "rec", "lig"):
             V, T = cx["surf"][k]
-            meshes.append(pb.pb_mesh_setup(ctx, V, T.astype(np.int32), 3, 6, 64))
+            meshes.append(pb.pb_mesh_setup(ctx, V, T.astype(np.int32), 3, 6, 64, basis=basis))
             atoms_l.append(cx[k][0]); q_l.append(cx[k][2])
         xr, xl = cx["rec"][0], cx["lig"][0]
         r = np.linalg.norm(xr[:, None, :] - xl[None, :, :], axis=2)
@@ -312,15 +321,20 @@ def run_binding(args):
     torch.cuda.synchronize()
     t_mesh = time.perf_counter() - t0
     ntri = [pb.pb_mesh_info(m)[0] for m in meshes]
-    max_iter = 150
+    max_iter = 400
+    # set-up: one preconditioned mat-vec per mesh builds its singular
+    # entries, tree lists and (shared) operator sets
     t0 = time.perf_counter()
-    res_l, sts, rc = pb.pb_solve_batch(ctx, meshes, atoms_l, q_l, 4.0, 80.0, 0.125, 1e-5, max_iter)
-    t_first = time.perf_counter() - t0
-    for r_ in res_l:
-        pb.pb_result_destroy(r_)
+    for m in meshes:
+        nu = pb.pb_mesh_unknowns(m)
+        xv = torch.zeros(2 * nu, dtype=torch.float64, device="cuda")
+        yv = torch.empty_like(xv)
+        pb.pb_mesh_matvec(ctx, m, xv, yv, 4.0, 80.0, 0.125, precond=True, formulation=form)
     torch.cuda.synchronize()
+    t_first = time.perf_counter() - t0
     t0 = time.perf_counter()
-    res_l, sts, rc = pb.pb_solve_batch(ctx, meshes, atoms_l, q_l, 4.0, 80.0, 0.125, 1e-5, max_iter)
+    res_l, sts, rc = pb.pb_solve_batch(ctx, meshes, atoms_l, q_l, 4.0, 80.0, 0.125, 1e-5, max_iter,
+                                       formulation=form)
     t_batch = time.perf_counter() - t0
     eb = [pb.pb_solvation_energy(ctx, r_) for r_ in res_l]
     iters = [int(pb.pb_result_get(r_)[0]) for r_ in res_l]
@@ -328,13 +342,26 @@ def run_binding(args):
         pb.pb_result_destroy(r_)
     n = len(gen)
     dgb = [eb[3 * c] - eb[3 * c + 1] - eb[3 * c + 2] - coul[c] for c in range(n)]
+    # the FP32 singular rule against the FP64 one on the smallest mesh
+    k = int(np.argmin(ntri))
+    pb.pb_set_option(ctx, pb.PB_OPT_SINGULAR, 1)
+    r64, _ = pb.pb_solve(ctx, meshes[k], atoms_l[k], q_l[k], 4.0, 80.0, 0.125, 1e-5, max_iter, formulation=form)
+    e64 = pb.pb_solvation_energy(ctx, r64)
+    pb.pb_result_destroy(r64)
+    sing = {"mesh_triangles": ntri[k], "dG_fp32_rule": eb[k], "dG_fp64_rule": e64,
+            "rel_diff": abs(eb[k] - e64) / abs(e64)}
     line = {"metric": "batched binding energies, ms per mesh", "value": t_batch * 1e3 / len(meshes),
             "unit": "ms/mesh", "higher_is_better": False, "n_gpus": 1, "dtype": "f32+f64", "data": "synthetic",
             "config": {"workload": f"{n} synthetic complexes (receptor 500-2,000 atoms, ligand 20-300) x (complex, "
                                    f"receptor, ligand) = {len(meshes)} meshes, {min(ntri)}-{max(ntri)} triangles "
-                                   f"({sum(ntri)} in all), P0, p = 6, mixed, tol 1e-5, one pb_solve_batch"},
+                                   f"({sum(ntri)} in all), "
+                                   + ("exterior derivative formulation (Eq. lu), P1" if ext else
+                                      "direct formulation, P0")
+                                   + ", p = 6, mixed, tol 1e-5, eps 4/80, kappa 0.125, FP32 singular rule, "
+                                     "one pb_solve_batch"},
+            "singular_rule_check": sing,
                "host_generation_s": t_gen, "mesh_setup_s": t_mesh,
-               "first_batch_s_incl_singular_and_operators": t_first, "batched_solve_s": t_batch,
+               "setup_s_singular_lists_operators": t_first, "batched_solve_s": t_batch, "max_iter": max_iter,
                "status_ok": int(sum(1 for s_ in sts if s_ == pb.PB_OK)), "rc": int(rc),
                "iterations": {"min": min(iters), "median": float(np.median(iters)), "max": max(iters)},
                "dG_bind_kcal_mol": {"min": float(min(dgb)), "median": float(np.median(dgb)), "max": float(max(dgb))},

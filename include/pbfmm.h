@@ -372,7 +372,8 @@ int pb_solve(pb_ctx* ctx, pb_mesh* mesh, const double* atoms, const double* q, i
  * pb_solvation_energy converts to the interior fields (phi_1 = phi_2,
  * dphi_1/dn = (eps_out/eps_in) dphi_2/dn) for Eq. phi_reac.  For P1 meshes
  * the charge <-> surface sums are always direct FP64 sums.
- * pb_energy_grad and pb_solve_batch take direct-formulation P0 systems only.
+ * pb_energy_grad takes direct-formulation P0 systems only; pb_solve_batch_ex
+ * takes any formulation with its basis.
  * Errors: as pb_solve, and PB_EINVAL for a derivative formulation on a P0
  * mesh. */
 int pb_solve_ex(pb_ctx* ctx, pb_mesh* mesh, const double* atoms, const double* q, int64_t na, double eps_in,
@@ -392,19 +393,32 @@ int pb_result_get(const pb_result* res, int* iterations, double* residual, doubl
 int pb_solvation_energy(pb_ctx* ctx, pb_result* res, double* dG_kcal_per_mol, double* phi_reac);
 
 /* Solve several systems together (same eps_in, eps_out, kappa, tol,
- * max_iter, precision; each its own mesh, charges and positions): the
- * GMRES iterations run in lockstep, one CUDA stream per system, each
- * system's preconditioned mat-vec captured once as a CUDA graph and replayed
- * every iteration; one host synchronisation per iteration for all systems.
- * meshes[nsys] must be distinct.  atoms[s] (double [na[s]][3]) and
- * charges[s] (double [na[s]]) are host or device arrays.  out[nsys]
- * receives one result per system (free each with pb_result_destroy),
- * status[nsys] PB_OK or PB_ENOCONV per system.  Returns PB_OK if every system
- * converged, else PB_ENOCONV.  Synchronous.  The results match pb_solve up to
- * the FMM's run-dependent summation order. */
+ * max_iter, precision; each its own mesh, charges and positions), direct
+ * formulation (Eq. direct) on P0 meshes: the GMRES iterations of all systems
+ * run in lockstep, one lockstep iteration of every active system (its
+ * preconditioned mat-vec on its own stream, the Gram-Schmidt passes, the
+ * Givens update and the convergence test on the device) is one CUDA graph
+ * replayed every iteration, with one host synchronisation per iteration for
+ * all systems; the graph is re-captured without the converged systems once a
+ * quarter of them have finished.  meshes[nsys] must be distinct.  atoms[s]
+ * (double [na[s]][3]) and charges[s] (double [na[s]]) are host or device
+ * arrays.  out[nsys] receives one result per system (free each with
+ * pb_result_destroy), status[nsys] PB_OK or PB_ENOCONV per system.  Returns
+ * PB_OK if every system converged, else PB_ENOCONV.  Synchronous.  The
+ * results match pb_solve up to the FMM's run-dependent summation order. */
 int pb_solve_batch(pb_ctx* ctx, pb_mesh* const* meshes, int nsys, const double* const* atoms,
                    const double* const* charges, const int64_t* na, double eps_in, double eps_out, double kappa,
                    double tol, int max_iter, int precision, pb_result** out, int* status);
+
+/* pb_solve_batch with a formulation (PB_FORM_DIRECT, PB_FORM_EXTERIOR or
+ * PB_FORM_INTERIOR, as pb_solve_ex): the derivative formulations need PB_P1
+ * meshes (all systems of the batch; PB_EINVAL otherwise), whose GMRES
+ * iteration counts stay flat under refinement (Sec. "Matrix conditioning of
+ * two derivative formulations"), so a batch of large meshes needs far fewer
+ * Krylov vectors than with the direct formulation. */
+int pb_solve_batch_ex(pb_ctx* ctx, pb_mesh* const* meshes, int nsys, const double* const* atoms,
+                      const double* const* charges, const int64_t* na, double eps_in, double eps_out, double kappa,
+                      double tol, int max_iter, int precision, int formulation, pb_result** out, int* status);
 
 /* Autotuner for the leaf size: for each candidate ncrit, build the octree of
  * the points xyz (host or device, float [n][3]) and time one Laplace and one

@@ -97,6 +97,8 @@ _sig("pb_solvation_energy", [_P, _P, ctypes.POINTER(_D), _P])
 _sig("pb_solvation_energy_noalloc", [_P, _P, _P])
 _sig("pb_energy_grad", [_P, _P, _D, ctypes.c_int, _P, _P])
 _sig("pb_solve_batch", [_P, _P, ctypes.c_int, _P, _P, _P, _D, _D, _D, _D, ctypes.c_int, ctypes.c_int, _P, _P])
+_sig("pb_solve_batch_ex", [_P, _P, ctypes.c_int, _P, _P, _P, _D, _D, _D, _D, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                           _P, _P])
 _sig("pb_tune_ncrit", [_P, _P, _I64, ctypes.c_int, _P, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                        ctypes.POINTER(_D)])
 
@@ -119,7 +121,7 @@ def exported_symbols():
             "fmm_apply", "fmm_apply_pair", "pb_mesh_setup", "pb_mesh_destroy", "pb_mesh_info", "pb_mesh_export_singular",
             "pb_mesh_matvec", "pb_mesh_matvec_ex", "pb_mesh_unknowns", "pb_solve", "pb_solve_ex",
             "pb_result_destroy", "pb_result_get", "pb_solvation_energy",
-            "pb_solvation_energy_noalloc", "pb_energy_grad", "pb_solve_batch", "pb_tune_ncrit"]
+            "pb_solvation_energy_noalloc", "pb_energy_grad", "pb_solve_batch", "pb_solve_batch_ex", "pb_tune_ncrit"]
 
 
 def ptr(x):
@@ -352,8 +354,10 @@ def pb_energy_grad(ctx, res, na, tol=1e-8, max_iter=500):
 
 
 def pb_solve_batch(ctx, meshes, atoms_list, charges_list, eps_in, eps_out, kappa, tol, max_iter=500,
-                   precision=PB_MIXED):
-    """Solve len(meshes) systems together; returns (results, statuses, rc)."""
+                   precision=PB_MIXED, formulation=None):
+    """Solve len(meshes) systems together; returns (results, statuses, rc).
+    formulation (PB_FORM_*; None: the direct formulation through
+    pb_solve_batch) selects pb_solve_batch_ex."""
     ns = len(meshes)
     A = [np.ascontiguousarray(a, dtype=np.float64) for a in atoms_list]
     Q = [np.ascontiguousarray(q, dtype=np.float64) for q in charges_list]
@@ -363,8 +367,13 @@ def pb_solve_batch(ctx, meshes, atoms_list, charges_list, eps_in, eps_out, kappa
     na = np.array([len(q) for q in Q], dtype=np.int64)
     out = (_P * ns)()
     st = np.zeros(ns, dtype=np.int32)
-    rc = _lib.pb_solve_batch(ctx, mesh_arr, ns, a_arr, q_arr, ptr(na), float(eps_in), float(eps_out),
-                             float(kappa), float(tol), int(max_iter), int(precision), out, ptr(st))
+    if formulation is None:
+        rc = _lib.pb_solve_batch(ctx, mesh_arr, ns, a_arr, q_arr, ptr(na), float(eps_in), float(eps_out),
+                                 float(kappa), float(tol), int(max_iter), int(precision), out, ptr(st))
+    else:
+        rc = _lib.pb_solve_batch_ex(ctx, mesh_arr, ns, a_arr, q_arr, ptr(na), float(eps_in), float(eps_out),
+                                    float(kappa), float(tol), int(max_iter), int(precision), int(formulation), out,
+                                    ptr(st))
     if rc not in (PB_OK, PB_ENOCONV):
         _check(rc, ctx)
     return [_P(out[i]) for i in range(ns)], st, rc

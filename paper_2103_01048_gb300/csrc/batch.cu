@@ -224,10 +224,11 @@ void solve_batch(pb_ctx* ctx, pb_mesh* const* meshes, int nsys, pb_result** resu
         S->R = results[s];
         pb_mesh* M = S->M;
         pb_result* R = S->R;
-        ensure_singular_public(M, R->kappa);
+        const bool p1 = M->basis == PB_P1;
+        if (!p1) ensure_singular_public(M, R->kappa);
         const int nt = (int)M->nt, nq = M->nq;
         const long long np = (long long)nt * nq;
-        S->n = 2LL * nt;
+        S->n = 2LL * M->nunk;
         S->kmax = max_iter;
         S->nb = (int)std::min<long long>(kDotBlocksB, (S->n + 255) / 256);
         S->ub = (int)std::min<long long>(4LL * ctx->sm_count, (S->n + 255) / 256);
@@ -237,16 +238,22 @@ void solve_batch(pb_ctx* ctx, pb_mesh* const* meshes, int nsys, pb_result** resu
         S->H.alloc((size_t)(S->kmax + 1) * S->kmax, main);
         S->cs.alloc(S->kmax + 1, main); S->sn.alloc(S->kmax + 1, main); S->g.alloc(S->kmax + 2, main);
         S->nrm2.alloc(1, main); S->resid.alloc(1, main); S->yv.alloc(S->kmax + 1, main);
-        S->xin.alloc(S->n, main); S->xout.alloc(S->n, main); S->b.alloc(S->n, main); S->f.alloc(np, main);
+        S->xin.alloc(S->n, main); S->xout.alloc(S->n, main); S->b.alloc(S->n, main);
         S->g.zero(main);
         S->xin.zero(main);
         R->x.alloc(S->n, main);
         R->x.zero(main);
-        coulomb_at_points(M, R, S->f.p);
-        k_rhs<<<div_up(nt, 128), 128, 0, main>>>(nt, nq, S->f.p, M->qw_d.p, M->adj_off.p, M->adj_ids.p, M->S_d.p,
-                                                 M->area.p, R->eps_in / R->eps_out, 1, S->b.p);
-        PB_CHECK_LAUNCH();
-        mesh_matvec(M, R->eps_in, R->eps_out, R->kappa, R->precision, S->xin.p, S->xout.p, 1);
+        if (p1) {
+            rhs_p1(M, R, S->b.p);              // the formulation's right-hand side (P1 test functions)
+        } else {
+            S->f.alloc(np, main);
+            coulomb_at_points(M, R, S->f.p);
+            k_rhs<<<div_up(nt, 128), 128, 0, main>>>(nt, nq, S->f.p, M->qw_d.p, M->adj_off.p, M->adj_ids.p,
+                                                     M->S_d.p, M->area.p, R->eps_in / R->eps_out, 1, S->b.p);
+            PB_CHECK_LAUNCH();
+        }
+        // warm mat-vec: singular entries, operators and workspaces exist before the capture
+        mesh_matvec(M, R->eps_in, R->eps_out, R->kappa, R->precision, S->xin.p, S->xout.p, 1, R->formulation);
         PB_CUDA(cudaMallocHost((void**)&S->host, 2 * sizeof(double)));
         sys[s] = std::move(S);
     }
@@ -329,7 +336,8 @@ void solve_batch(pb_ctx* ctx, pb_mesh* const* meshes, int nsys, pb_result** resu
                 pb_result* R = S.R;
                 k_b_copy_in<<<S.ub, 256, 0, st>>>(S.n, S.V.p, S.dev.p, S.xin.p);
                 PB_CHECK_LAUNCH();
-                mesh_matvec(S.M, R->eps_in, R->eps_out, R->kappa, R->precision, S.xin.p, S.xout.p, 1);
+                mesh_matvec(S.M, R->eps_in, R->eps_out, R->kappa, R->precision, S.xin.p, S.xout.p, 1,
+                            R->formulation);
                 for (int pass = 0; pass < 2; ++pass) {       // CGS2
                     double* hp = pass == 0 ? S.h.p : S.h2.p;
                     k_b_dots<<<S.nb, 256, 0, st>>>(S.n, S.V.p, S.n, S.xout.p, S.partial.p, S.kmax + 1, S.dev.p, 1);

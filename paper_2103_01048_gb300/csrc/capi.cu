@@ -622,6 +622,13 @@ int pb_solvation_energy(pb_ctx* ctx, pb_result* R, double* dG, double* phir) {
 int pb_solve_batch(pb_ctx* ctx, pb_mesh* const* meshes, int nsys, const double* const* atoms,
                    const double* const* charges, const int64_t* na, double eps_in, double eps_out, double kappa,
                    double tol, int max_iter, int precision, pb_result** out, int* status) {
+    return pb_solve_batch_ex(ctx, meshes, nsys, atoms, charges, na, eps_in, eps_out, kappa, tol, max_iter, precision,
+                             PB_FORM_DIRECT, out, status);
+}
+
+int pb_solve_batch_ex(pb_ctx* ctx, pb_mesh* const* meshes, int nsys, const double* const* atoms,
+                      const double* const* charges, const int64_t* na, double eps_in, double eps_out, double kappa,
+                      double tol, int max_iter, int precision, int formulation, pb_result** out, int* status) {
     if (!ctx || !meshes || nsys < 1 || !atoms || !charges || !na || !out || !status) return PB_EINVAL;
     for (int s = 0; s < nsys; ++s) out[s] = nullptr;
     int rc = PB_OK;
@@ -629,16 +636,20 @@ int pb_solve_batch(pb_ctx* ctx, pb_mesh* const* meshes, int nsys, const double* 
     PB_REQUIRE(eps_in > 0 && eps_out > 0 && kappa > 0, PB_EINVAL, "pb_solve_batch: eps and kappa must be > 0");
     PB_REQUIRE(tol >= 0 && max_iter >= 1 && max_iter <= 2000, PB_EINVAL, "pb_solve_batch: bad tol or max_iter");
     PB_REQUIRE(precision == PB_MIXED || precision == PB_FP64, PB_EINVAL, "pb_solve_batch: unknown precision");
+    PB_REQUIRE(formulation >= PB_FORM_DIRECT && formulation <= PB_FORM_INTERIOR, PB_EINVAL,
+               "pb_solve_batch: unknown formulation");
     for (int s = 0; s < nsys; ++s) {
         PB_REQUIRE(meshes[s] && atoms[s] && charges[s] && na[s] >= 1, PB_EINVAL, "pb_solve_batch: empty system");
-        PB_REQUIRE(meshes[s]->basis == PB_P0, PB_EINVAL, "pb_solve_batch: P0 meshes (direct formulation) only");
+        PB_REQUIRE(formulation == PB_FORM_DIRECT || meshes[s]->basis == PB_P1, PB_EINVAL,
+                   "pb_solve_batch: the derivative formulations need PB_P1 meshes");
         for (int t = 0; t < s; ++t)
             PB_REQUIRE(meshes[t] != meshes[s], PB_EINVAL, "pb_solve_batch: meshes must be distinct");
     }
     PB_CUDA(cudaSetDevice(ctx->device));
     try {
         for (int s = 0; s < nsys; ++s)
-            out[s] = make_result(ctx, meshes[s], atoms[s], charges[s], na[s], eps_in, eps_out, kappa, precision);
+            out[s] = make_result(ctx, meshes[s], atoms[s], charges[s], na[s], eps_in, eps_out, kappa, precision,
+                                 formulation);
         solve_batch(ctx, meshes, nsys, out, tol, max_iter, status);
         check_device_error(ctx);
     } catch (...) {

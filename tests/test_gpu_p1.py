@@ -191,9 +191,45 @@ def test_p1_argument_checks(pb, ctx):
             pb.pb_solvation_energy_noalloc(ctx, res, out)
         assert e.value.code == pb.PB_EINVAL
         pb.pb_result_destroy(res)
-        with pytest.raises(pb.PBError) as e:
-            pb.pb_solve_batch(ctx, [m1], [np.zeros((1, 3))], [np.array([1.0])], *EPS, 1e-6, 100)
+        with pytest.raises(pb.PBError) as e:       # a derivative formulation on a P0 mesh
+            pb.pb_solve_batch(ctx, [m1, m0], [np.zeros((1, 3))] * 2, [np.array([1.0])] * 2, *EPS, 1e-6, 100,
+                              formulation=FORMS["exterior"])
         assert e.value.code == pb.PB_EINVAL
     finally:
         pb.pb_mesh_destroy(m0)
         pb.pb_mesh_destroy(m1)
+
+
+@pytest.mark.parametrize("form", ["exterior", "direct"])
+def test_p1_batch_vs_single_and_oracle(pb, ctx, oracle_mats, form):
+    """pb_solve_batch_ex on P1 meshes (the two oracle systems and a finer
+    sphere): every energy equals the one-at-a-time pb_solve_ex result up to
+    the FMM's summation order, and the oracle systems match the dense LU
+    oracle within the 1e-4 target."""
+    Vs, Fs = synthetic.icosphere(3, 2.0)
+    xyz, radii, qq = synthetic.fcc_ball_atoms(4, 3.5, 2.85, 0.1, seed=4)
+    systems = [(oracle_mats["sphere320"], np.zeros((1, 3)), np.array([1.0])),
+               (oracle_mats["gaussian648"], xyz, qq),
+               ((Vs, Fs.astype(np.int32), None), np.array([[0.5, -0.3, 0.2]]), np.array([-1.0]))]
+    meshes = [pb.pb_mesh_setup(ctx, V, F, 3, 6, 32, basis=pb.PB_P1) for (V, F, _), _, _ in systems]
+    try:
+        res, st, rc = pb.pb_solve_batch(ctx, meshes, [a for _, a, _ in systems], [q for _, _, q in systems], *EPS,
+                                        1e-9, 500, formulation=FORMS[form])
+        assert rc == pb.PB_OK and all(s_ == pb.PB_OK for s_ in st)
+        eb = [pb.pb_solvation_energy(ctx, r_) for r_ in res]
+        itb = [pb.pb_result_get(r_)[0] for r_ in res]
+        for r_ in res:
+            pb.pb_result_destroy(r_)
+        for k, (m, ((V, F, mats), a, q)) in enumerate(zip(meshes, systems)):
+            r1, s1 = pb.pb_solve(ctx, m, a, q, *EPS, 1e-9, 500, formulation=FORMS[form])
+            e1 = pb.pb_solvation_energy(ctx, r1)
+            it1 = pb.pb_result_get(r1)[0]
+            pb.pb_result_destroy(r1)
+            print(f"P1 batch {form} system {k}: dG {eb[k]:.9f} single {e1:.9f}, iterations {itb[k]} / {it1}")
+            assert abs(eb[k] - e1) < 1e-7 * abs(e1)
+            if mats is not None:
+                e_ref, *_ = bem_p1.solve_energy(V, F, 3, a, q, *EPS, form, mats=mats)
+                assert abs(eb[k] - e_ref) < 1e-4 * abs(e_ref)
+    finally:
+        for m in meshes:
+            pb.pb_mesh_destroy(m)
