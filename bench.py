@@ -83,8 +83,8 @@ def parse():
                     help="tensor-core box-operator kernel: CTA pairs (cta_group::2) or one CTA per operator part "
                          "(default: the library's choice)")
     ap.add_argument("--binding", type=int, default=0, metavar="N",
-                    help="batched binding energies of N synthetic complexes (receptor 500-2,000 atoms, ligand "
-                         "20-300 atoms; 3N meshes) in one pb_solve_batch")
+                    help="batched binding energies of N synthetic complexes (compact receptor 500-5,000 atoms, "
+                         "ligand 20-300 atoms; 3N meshes) in one pb_solve_batch")
     ap.add_argument("--binding-form", choices=["exterior", "direct"], default="direct",
                     help="formulation of --binding: exterior derivative (P1, Eq. lu) or direct (P0)")
     ap.add_argument("--kirkwood", action="store_true",
@@ -277,21 +277,21 @@ def run_virus(args):
 def _gen_complex(spec):
     import synthetic as syn
     n_rec, n_lig, seed = spec
-    return spec, syn.binding_complex(n_rec, n_lig, seed=seed)
+    return spec, syn.binding_complex(n_rec, n_lig, seed=seed, dense=True)
 
 
 def run_binding(args):
     """Batched binding energies (Eq. bind) at scale: N seeded synthetic
-    complexes (receptor 500-2,000 atoms, ligand 20-300 atoms, the generator
-    of the binding tests), the complex, receptor and ligand surfaces of each
-    (3N meshes, 20k-300k triangles) solved together by one pb_solve_batch
+    complexes (compact receptor of 500-5,000 atoms, ligand of 20-300 atoms,
+    atom centres 4.5 A apart at the closest), the complex, receptor and
+    ligand surfaces of each (3N meshes) solved together by one pb_solve_batch
     (mixed precision, p = 6, tol 1e-5, eps 4/80, kappa 0.125).  Reports the
     host mesh generation, the library set-up (mesh set-up, singular entries,
     operators shared between trees of equal box sizes), the batched solve
     and the binding energies; one JSON line."""
     import multiprocessing as mp
     rng = np.random.default_rng(2021)
-    specs = [(int(rng.integers(500, 2001)), int(rng.integers(20, 301)), 5000 + c) for c in range(args.binding)]
+    specs = [(int(rng.integers(500, 5001)), int(rng.integers(20, 301)), 5000 + c) for c in range(args.binding)]
     t0 = time.perf_counter()
     with mp.get_context("spawn").Pool(max(1, min(len(specs), host_cores()))) as pool:
         gen = pool.map(_gen_complex, specs)
@@ -307,6 +307,22 @@ def run_binding(args):
     ext = args.binding_form == "exterior"
     form = pb.PB_FORM_EXTERIOR if ext else pb.PB_FORM_DIRECT
     basis = pb.PB_P1 if ext else pb.PB_P0
+    max_iter = 250
+    # keep the complexes whose estimated footprint fits: Krylov basis
+    # (max_iter + 1) x 2 n doubles plus ~7 KB per triangle of singular
+    # entries, trees and workspaces (measured: 33.7 GB for 2.58M triangles
+    # at max_iter 400)
+    free, _ = torch.cuda.mem_get_info()
+    per_tri = 16 * (max_iter + 1) * (0.5 if ext else 1.0) + 7000
+    keep, used = [], 0.0
+    for spec, cx in gen:
+        need = per_tri * sum(len(cx["surf"][k][1]) for k in ("cplx", "rec", "lig"))
+        if used + need > 0.75 * free:
+            break
+        keep.append((spec, cx))
+        used += need
+    dropped = len(gen) - len(keep)
+    gen = keep
     meshes, atoms_l, q_l, coul = [], [], [], []
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -321,7 +337,6 @@ def run_binding(args):
     torch.cuda.synchronize()
     t_mesh = time.perf_counter() - t0
     ntri = [pb.pb_mesh_info(m)[0] for m in meshes]
-    max_iter = 400
     # set-up: one preconditioned mat-vec per mesh builds its singular
     # entries, tree lists and (shared) operator sets
     t0 = time.perf_counter()
@@ -352,14 +367,15 @@ def run_binding(args):
             "rel_diff": abs(eb[k] - e64) / abs(e64)}
     line = {"metric": "batched binding energies, ms per mesh", "value": t_batch * 1e3 / len(meshes),
             "unit": "ms/mesh", "higher_is_better": False, "n_gpus": 1, "dtype": "f32+f64", "data": "synthetic",
-            "config": {"workload": f"{n} synthetic complexes (receptor 500-2,000 atoms, ligand 20-300) x (complex, "
+            "config": {"workload": f"{n} synthetic complexes (compact receptor 500-5,000 atoms, ligand 20-300) x (complex, "
                                    f"receptor, ligand) = {len(meshes)} meshes, {min(ntri)}-{max(ntri)} triangles "
                                    f"({sum(ntri)} in all), "
                                    + ("exterior derivative formulation (Eq. lu), P1" if ext else
                                       "direct formulation, P0")
                                    + ", p = 6, mixed, tol 1e-5, eps 4/80, kappa 0.125, FP32 singular rule, "
                                      "one pb_solve_batch"},
-            "singular_rule_check": sing,
+            "singular_rule_check": sing, "complexes_generated": n + dropped,
+            "complexes_dropped_for_memory": dropped, "device_free_gb_at_start": free / 1e9,
                "host_generation_s": t_gen, "mesh_setup_s": t_mesh,
                "setup_s_singular_lists_operators": t_first, "batched_solve_s": t_batch, "max_iter": max_iter,
                "status_ok": int(sum(1 for s_ in sts if s_ == pb.PB_OK)), "rc": int(rc),

@@ -295,17 +295,38 @@ def synthetic_protein(natoms=2000, target_tris=80000, seed=3, ball_radius=20.0):
     return V, T, xyz, radii, q, h
 
 
-def binding_complex(n_rec, n_lig, seed=0, gap=4.5, spacing=0.7):
+def fcc_fill_radius(natoms, nn_dist=2.85, step=0.05):
+    """Ball radius (a multiple of `step`, at most `step` beyond the
+    natoms-th nearest site) whose FCC lattice of nearest-neighbour distance
+    nn_dist holds at least natoms sites."""
+    a = nn_dist * 2.0 ** 0.5
+    r = (3 * natoms * (a ** 3 / 4) / (4 * np.pi)) ** (1 / 3) * 0.9
+    m = int(np.ceil(2 * r / a)) + 2
+    g = np.arange(-m, m + 1, dtype=np.float64)
+    X, Y, Z = np.meshgrid(g, g, g, indexing="ij")
+    base = np.stack([X.ravel(), Y.ravel(), Z.ravel()], axis=1) * a
+    offs = np.array([[0, 0, 0], [0.5, 0.5, 0], [0.5, 0, 0.5], [0, 0.5, 0.5]]) * a
+    rho = np.sort(np.linalg.norm((base[:, None, :] + offs[None, :, :]).reshape(-1, 3), axis=1))
+    return float((np.floor(rho[natoms - 1] / step) + 1) * step)      # strictly beyond the natoms-th site
+
+
+def binding_complex(n_rec, n_lig, seed=0, gap=4.5, spacing=0.7, dense=False):
     """A synthetic receptor-ligand complex: receptor atoms on a jittered FCC
     lattice in a ball sized for n_rec atoms, ligand in a small ball placed
     along a seeded random direction so that the closest receptor-ligand
     atom-centre distance is `gap` A.  Returns dict with the atoms, radii and
     charges of the receptor, the ligand and the complex, and the three
-    Gaussian surfaces (verts, tris)."""
+    Gaussian surfaces (verts, tris).  dense=False: balls 10% wider than the
+    atoms need (a porous receptor, ~60% of the sites taken); dense=True: the
+    smallest balls that hold the atoms (compact bodies like the synthetic
+    protein's)."""
     rng = np.random.default_rng(seed)
     per_atom = 2.85 ** 3 / 2 ** 0.5          # FCC volume per site
-    rr = (3 * n_rec * per_atom / (4 * np.pi)) ** (1 / 3) * 1.1 + 1.0
-    rl = (3 * n_lig * per_atom / (4 * np.pi)) ** (1 / 3) * 1.1 + 1.0
+    if dense:
+        rr, rl = fcc_fill_radius(n_rec), fcc_fill_radius(n_lig)
+    else:
+        rr = (3 * n_rec * per_atom / (4 * np.pi)) ** (1 / 3) * 1.1 + 1.0
+        rl = (3 * n_lig * per_atom / (4 * np.pi)) ** (1 / 3) * 1.1 + 1.0
     xr, radr, qr = fcc_ball_atoms(n_rec, rr, 2.85, 0.1, seed=seed + 1)
     xl, radl, ql = fcc_ball_atoms(n_lig, rl, 2.85, 0.1, seed=seed + 2)
     u = rng.standard_normal(3)

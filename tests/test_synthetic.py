@@ -1,6 +1,8 @@
 """Seeded input generators (no method arithmetic): the sphere meshes used by
 the refinement study, the Born ion and the virus-scale shell are closed,
 2-manifold, outward oriented and of the stated sizes."""
+import os
+
 import numpy as np
 import pytest
 
@@ -43,3 +45,37 @@ def test_cube_sphere_counts_and_closure():
     assert len(F) == 12 * 6 * 6
     assert np.allclose(np.linalg.norm(V, axis=1), 3.0)
     _check_closed_outward(V, F, 0.8 * 4.0 / 3.0 * np.pi * 3.0 ** 3)
+
+
+def test_binding_complex_default_meshes_match_golden():
+    """The default (porous) complexes are unchanged: their meshes hash to
+    the values recorded with the oracle's binding energies."""
+    import hashlib
+    import json
+    gold = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "binding_small.json")))
+    c = gold["complexes"][0]
+    cx = synthetic.binding_complex(c["n_rec"], c["n_lig"], seed=10 + c["n_rec"], spacing=1.0)
+    for k in ("cplx", "rec", "lig"):
+        V, T = cx["surf"][k]
+        h = hashlib.sha256()
+        h.update(np.ascontiguousarray(V, np.float64).tobytes())
+        h.update(np.ascontiguousarray(T, np.int32).tobytes())
+        assert len(T) == c[k]["triangles"]
+        assert h.hexdigest()[:16] == c[k]["mesh_sha256_16"], k
+
+
+@pytest.mark.parametrize("n", [5, 20, 500, 2000])
+def test_fcc_fill_radius(n):
+    """The dense complexes' balls: a radius at most 0.05 A beyond the n-th
+    nearest FCC site, so the ball holds the n atoms with (almost) no empty
+    sites."""
+    r = synthetic.fcc_fill_radius(n)
+    xyz, _, _ = synthetic.fcc_ball_atoms(n, r, 2.85, 0.0, seed=1)
+    assert len(xyz) == n
+    # brute force: distance of the n-th nearest FCC site (a = 2.85 sqrt 2)
+    a = 2.85 * 2 ** 0.5
+    g = np.arange(-12, 13)
+    base = np.stack(np.meshgrid(g, g, g, indexing="ij"), -1).reshape(-1, 3) * a
+    offs = np.array([[0, 0, 0], [0.5, 0.5, 0], [0.5, 0, 0.5], [0, 0.5, 0.5]]) * a
+    rho = np.sort(np.linalg.norm((base[:, None] + offs[None]).reshape(-1, 3), axis=1))
+    assert rho[n - 1] < r <= rho[n - 1] + 0.05 + 1e-12
