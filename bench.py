@@ -307,13 +307,15 @@ def run_binding(args):
     ext = args.binding_form == "exterior"
     form = pb.PB_FORM_EXTERIOR if ext else pb.PB_FORM_DIRECT
     basis = pb.PB_P1 if ext else pb.PB_P0
-    max_iter = 250
-    # keep the complexes whose estimated footprint fits: Krylov basis
-    # (max_iter + 1) x 2 n doubles plus ~7 KB per triangle of singular
-    # entries, trees and workspaces (measured: 33.7 GB for 2.58M triangles
-    # at max_iter 400)
+    # GMRES(200) with up to 800 iterations in all: 201 Krylov vectors per
+    # system; keep the complexes whose estimated footprint fits: the basis
+    # (201 x 2 n doubles) plus ~7 KB per triangle of singular entries, trees
+    # and workspaces (an overestimate: 139 GB measured for 18.7M triangles
+    # with 251 vectors)
+    max_iter, restart = 800, 200
+    pb.pb_set_option(ctx, pb.PB_OPT_RESTART, restart)
     free, _ = torch.cuda.mem_get_info()
-    per_tri = 16 * (max_iter + 1) * (0.5 if ext else 1.0) + 7000
+    per_tri = 16 * (restart + 1) * (0.5 if ext else 1.0) + 7000
     keep, used = [], 0.0
     for spec, cx in gen:
         need = per_tri * sum(len(cx["surf"][k][1]) for k in ("cplx", "rec", "lig"))
@@ -352,7 +354,10 @@ def run_binding(args):
                                        formulation=form)
     t_batch = time.perf_counter() - t0
     eb = [pb.pb_solvation_energy(ctx, r_) for r_ in res_l]
-    iters = [int(pb.pb_result_get(r_)[0]) for r_ in res_l]
+    got = [pb.pb_result_get(r_)[:2] for r_ in res_l]
+    iters = [int(g_[0]) for g_ in got]
+    unconv = [{"triangles": ntri[i], "iterations": iters[i], "residual": float(got[i][1])}
+              for i in range(len(res_l)) if sts[i] != pb.PB_OK]
     for r_ in res_l:
         pb.pb_result_destroy(r_)
     n = len(gen)
@@ -372,12 +377,13 @@ def run_binding(args):
                                    f"({sum(ntri)} in all), "
                                    + ("exterior derivative formulation (Eq. lu), P1" if ext else
                                       "direct formulation, P0")
-                                   + ", p = 6, mixed, tol 1e-5, eps 4/80, kappa 0.125, FP32 singular rule, "
-                                     "one pb_solve_batch"},
+                                   + ", p = 6, mixed, GMRES(200) to tol 1e-5, eps 4/80, kappa 0.125, FP32 "
+                                     "singular rule, one pb_solve_batch"},
             "singular_rule_check": sing, "complexes_generated": n + dropped,
             "complexes_dropped_for_memory": dropped, "device_free_gb_at_start": free / 1e9,
                "host_generation_s": t_gen, "mesh_setup_s": t_mesh,
                "setup_s_singular_lists_operators": t_first, "batched_solve_s": t_batch, "max_iter": max_iter,
+               "gmres_restart": restart, "unconverged": unconv,
                "status_ok": int(sum(1 for s_ in sts if s_ == pb.PB_OK)), "rc": int(rc),
                "iterations": {"min": min(iters), "median": float(np.median(iters)), "max": max(iters)},
                "dG_bind_kcal_mol": {"min": float(min(dgb)), "median": float(np.median(dgb)), "max": float(max(dgb))},

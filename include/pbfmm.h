@@ -140,8 +140,15 @@ int pb_profile(pb_ctx* ctx, int enable);
  *                         4M-point p = 6 workload it does not pay: the
  *                         tensor-core kernels cannot share an SM with the
  *                         near-field CTAs (shared memory).
+ *   PB_OPT_RESTART        GMRES restart length m of pb_solve_batch(_ex):
+ *                         0 (default): no restart (max_iter + 1 Krylov
+ *                         vectors per system); m >= 1: GMRES(m), at most
+ *                         m + 1 vectors per system, max_iter still bounding
+ *                         the total iterations.  A system whose cycle ends
+ *                         unconverged takes its update, recomputes its
+ *                         residual with one mat-vec and starts a new cycle.
  * Errors: PB_EINVAL for an unknown option or value. */
-enum { PB_OPT_COUPLING = 1, PB_OPT_DETERMINISTIC = 2, PB_OPT_SINGULAR = 3, PB_OPT_OVERLAP = 4 };
+enum { PB_OPT_COUPLING = 1, PB_OPT_DETERMINISTIC = 2, PB_OPT_SINGULAR = 3, PB_OPT_OVERLAP = 4, PB_OPT_RESTART = 5 };
 int pb_set_option(pb_ctx* ctx, int option, int value);
 int pb_profile_read(pb_ctx* ctx, int phase, double* ms, int64_t* calls);
 

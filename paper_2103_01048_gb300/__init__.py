@@ -166,7 +166,7 @@ PHASES = ["gather", "p2m", "m2m", "p2l", "m2l", "down", "leaf", "scatter", "bem"
 PB_PH_LAUNCHES = 100
 
 
-PB_OPT_COUPLING, PB_OPT_DETERMINISTIC, PB_OPT_SINGULAR, PB_OPT_OVERLAP = 1, 2, 3, 4
+PB_OPT_COUPLING, PB_OPT_DETERMINISTIC, PB_OPT_SINGULAR, PB_OPT_OVERLAP, PB_OPT_RESTART = 1, 2, 3, 4, 5
 
 
 def pb_set_option(ctx, option, value):

@@ -154,6 +154,13 @@ __global__ void k_b_givens(int kmax, const double* __restrict__ h, const double*
     }
 }
 
+// r = b - w (the residual of a restart)
+__global__ void k_b_residual(long long n, const double* __restrict__ b, const double* __restrict__ w,
+                             double* __restrict__ r) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        r[i] = b[i] - w[i];
+}
+
 // V[j] = w / ||w|| (j already advanced by k_b_givens); skipped once done
 __global__ void k_b_scale(long long n, const double* __restrict__ w, const double* __restrict__ nrm2,
                           double* __restrict__ V, const BatchDev* __restrict__ d) {
@@ -176,8 +183,9 @@ struct BatchSystem {
     DBuf<double> V, w, partial, h, h2, H, cs, sn, g, nrm2, resid, yv, xin, xout, b, f;
     double* host = nullptr;           // pinned: [0] residual, [1] ||b||^2
     DBuf<BatchDev> dev;               // iteration state on the device
-    double beta = 0.0;
+    double beta = 0.0;                // ||P^-1 b||: the convergence test is relative to it in every cycle
     int j = 0;
+    int tot = 0;                      // iterations of the completed (restarted) cycles
     bool active = true;
     int status = PB_ENOCONV;
     ~BatchSystem() {
@@ -229,7 +237,7 @@ void solve_batch(pb_ctx* ctx, pb_mesh* const* meshes, int nsys, pb_result** resu
         const int nt = (int)M->nt, nq = M->nq;
         const long long np = (long long)nt * nq;
         S->n = 2LL * M->nunk;
-        S->kmax = max_iter;
+        S->kmax = ctx->restart > 0 ? std::min(ctx->restart, max_iter) : max_iter;   // vectors of one cycle
         S->nb = (int)std::min<long long>(kDotBlocksB, (S->n + 255) / 256);
         S->ub = (int)std::min<long long>(4LL * ctx->sm_count, (S->n + 255) / 256);
         S->V.alloc((size_t)(S->kmax + 1) * S->n, main);
@@ -365,10 +373,28 @@ void solve_batch(pb_ctx* ctx, pb_mesh* const* meshes, int nsys, pb_result** resu
     };
     // k_b_update stages up to kmax + 1 coefficients in shared memory
     PB_CUDA(cudaFuncSetAttribute(k_b_update, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 (int)std::max<size_t>(48 * 1024, (max_iter + 1) * sizeof(double))));
+                                 (int)std::max<size_t>(48 * 1024, (sys[0]->kmax + 1) * sizeof(double))));
+    // end of an unconverged cycle of GMRES(m): x += V y, r = P^-1 b - P^-1 A x,
+    // V[0] = r / ||r||, g[0] = ||r||, j = 0 (the captured graph stays valid)
+    auto restart = [&](BatchSystem& S, int m) {
+        cudaStream_t st = S.sub.stream;
+        pb_result* R = S.R;
+        k_backsolve<<<1, 1, 0, st>>>(m, S.kmax, S.H.p, S.g.p, S.yv.p);
+        k_axpy_basis<<<S.ub, 256, m * sizeof(double), st>>>(S.n, S.V.p, S.n, m, S.yv.p, R->x.p);
+        PB_CHECK_LAUNCH();
+        mesh_matvec(S.M, R->eps_in, R->eps_out, R->kappa, R->precision, R->x.p, S.xout.p, 1, R->formulation);
+        k_b_residual<<<S.ub, 256, 0, st>>>(S.n, S.b.p, S.xout.p, S.xin.p);
+        PB_CHECK_LAUNCH();
+        batch_dots(S, S.xin.p, 1, S.xin.p, S.nrm2.p, 0);
+        k_scale<<<S.ub, 256, 0, st>>>(S.n, S.xin.p, S.nrm2.p, S.V.p);
+        k_set_g0<<<1, 1, 0, st>>>(S.nrm2.p, S.g.p);
+        PB_CHECK_LAUNCH();
+        PB_CUDA(cudaMemsetAsync(S.dev.p, 0, sizeof(BatchDev), st));
+    };
     int nactive = 0;
     for (auto& Sp : sys) nactive += Sp->active ? 1 : 0;
     int captured = 0;           // active systems when the graph was captured
+    bool restarted = false;
     for (int it = 0; it < max_iter && nactive > 0; ++it) {
         // a finished system's Arnoldi kernels return at once, but its
         // mat-vec still runs: re-capture once a quarter of the captured
@@ -386,11 +412,25 @@ void solve_batch(pb_ctx* ctx, pb_mesh* const* meshes, int nsys, pb_result** resu
             S.j = hflags[s].j;
             S.R->residual = hflags[s].resid / S.beta;
             if (hflags[s].done) {
-                S.active = false;
-                S.j = hflags[s].m;
-                S.status = S.R->residual <= tol ? PB_OK : PB_ENOCONV;
-                --nactive;
+                const int m = hflags[s].m;
+                const bool conv = S.R->residual <= tol;
+                if (conv || S.tot + m >= max_iter) {
+                    S.active = false;
+                    S.j = m;
+                    S.status = conv ? PB_OK : PB_ENOCONV;
+                    --nactive;
+                } else {
+                    restart(S, m);
+                    S.tot += m;
+                    S.j = 0;
+                    restarted = true;
+                }
             }
+        }
+        // the next graph launch (on `origin`) must see the restarts' work
+        if (restarted) {
+            for (auto& Sp : sys) PB_CUDA(cudaStreamSynchronize(Sp->sub.stream));
+            restarted = false;
         }
     }
     for (int s = 0; s < nsys; ++s) {
@@ -402,7 +442,7 @@ void solve_batch(pb_ctx* ctx, pb_mesh* const* meshes, int nsys, pb_result** resu
             k_axpy_basis<<<S.ub, 256, m * sizeof(double), st>>>(S.n, S.V.p, S.n, m, S.yv.p, S.R->x.p);
             PB_CHECK_LAUNCH();
         }
-        S.R->iterations = m;
+        S.R->iterations = S.tot + m;
         S.R->status = S.status;
         if (m == 0) S.R->residual = 0.0;
         status[s] = S.status;

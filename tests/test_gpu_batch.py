@@ -62,6 +62,44 @@ def test_batch_matches_single_solves(pb):
         pb.pb_destroy(ctx)
 
 
+@pytest.mark.parametrize("m", [5, 12])
+def test_batch_restarted_gmres(pb, m):
+    """GMRES(m) in the batch (PB_OPT_RESTART): every system converges to
+    the same energy as the unrestarted batch (the restart recomputes the
+    true residual, so the final residual is the true one at tol), with at
+    least as many iterations, and restarts run within max_iter."""
+    ctx = pb.pb_create(0, None)
+    sysl = systems()
+    meshes = [pb.pb_mesh_setup(ctx, V, F.astype(np.int32), 3, 6, 64) for V, F, _, _ in sysl]
+    try:
+        args = ([s[2] for s in sysl], [s[3] for s in sysl], *EPS, 1e-7, 400)
+        full, sts, rc = pb.pb_solve_batch(ctx, meshes, *args)
+        assert rc == pb.PB_OK
+        ref = [(pb.pb_solvation_energy(ctx, r_), pb.pb_result_get(r_)[0]) for r_ in full]
+        for r_ in full:
+            pb.pb_result_destroy(r_)
+        pb.pb_set_option(ctx, pb.PB_OPT_RESTART, m)
+        res, sts, rc = pb.pb_solve_batch(ctx, meshes, *args)
+        assert rc == pb.PB_OK and np.all(sts == pb.PB_OK)
+        for r_, (e_ref, it_ref) in zip(res, ref):
+            e = pb.pb_solvation_energy(ctx, r_)
+            it, rr, _ = pb.pb_result_get(r_)
+            print(f"GMRES({m}): {it} iterations (full GMRES {it_ref}), dG {e:.9f} vs {e_ref:.9f}")
+            assert rr <= 1e-7 and it >= it_ref
+            assert abs(e - e_ref) <= 1e-5 * abs(e_ref)
+            pb.pb_result_destroy(r_)
+        # a cap below the need: PB_ENOCONV with the iterations at the cap
+        res, sts, rc = pb.pb_solve_batch(ctx, meshes, [s[2] for s in sysl], [s[3] for s in sysl], *EPS, 1e-12, 2 * m)
+        assert rc == pb.PB_ENOCONV
+        for r_ in res:
+            assert pb.pb_result_get(r_)[0] <= 2 * m
+            pb.pb_result_destroy(r_)
+    finally:
+        for mm in meshes:
+            pb.pb_mesh_destroy(mm)
+        pb.pb_destroy(ctx)
+
+
 def test_ncrit_autotuner(pb):
     ctx = pb.pb_create(0, None)
     try:
