@@ -559,10 +559,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_m2l_tc(const int4* __restrict
 // and each CTA's tensor memory receives its own 128 rows x 2 NH columns.
 // Against the single-CTA kernel every source row is gathered once instead
 // of once per row part, and each A tile feeds twice the columns.
-//   producers: arrive (one per warp) on the even CTA's `full` barrier;
-//   MMA issuer (even CTA): commits to `empty` / `accf` of both CTAs;
-//   epilogues: arrive (one per warp) on the even CTA's `acce` barrier;
-//   the odd CTA relays the arrival of its operator part (`barBp`).
+//   producers and epilogues arrive (one per warp) on their own CTA's
+//   barriers; the odd CTA's warp 12 relays each completed event (operator
+//   part, full A stage, drained accumulator) to the even CTA's barrier with
+//   one cluster-scope arrival;
+//   MMA issuer (even CTA): commits to `empty` / `accf` of both CTAs.
 // Cluster barriers after the set-up and before the teardown keep every
 // remote arrival and MMA inside the lifetime of both CTAs.
 // ---------------------------------------------------------------------------
@@ -570,6 +571,7 @@ template <int STAGES>
 struct TcPairSmem {
     alignas(16) float epi[kTcEpiWarps][32][kTcEpiStride];
     uint64_t barB, barBp, full[STAGES], empty[STAGES], accf[2], acce[2];
+    uint64_t pfull[STAGES], pacce[2];     // odd CTA: its warps' arrivals, relayed to the even CTA
     uint32_t tmem_slot;
     int failed;
 };
@@ -631,13 +633,16 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     if (tid == 0) {
         mbar_init(&S->barB, 1);
         mbar_init(&S->barBp, 1);
+        // even CTA: its own warps arrive locally, the odd CTA's relay once
         for (int q = 0; q < kTcStages; ++q) {
-            mbar_init(&S->full[q], 2 * kTcProdWarps);
+            mbar_init(&S->full[q], kTcProdWarps + 1);
             mbar_init(&S->empty[q], 1);
+            mbar_init(&S->pfull[q], kTcProdWarps);
         }
         for (int q = 0; q < 2; ++q) {
             mbar_init(&S->accf[q], 1);
-            mbar_init(&S->acce[q], 2 * kTcEpiWarps);
+            mbar_init(&S->acce[q], kTcEpiWarps + 1);
+            mbar_init(&S->pacce[q], kTcEpiWarps);
         }
         S->failed = 0;
         fence_mbar_init();
@@ -701,7 +706,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 }
                 fence_proxy_async();
                 __syncwarp();
-                if (lane == 0) mbar_arrive_cluster(mapa_shared(smem_u32(&S->full[s]), 0));
+                if (lane == 0) mbar_arrive(rank == 0 ? &S->full[s] : &S->pfull[s]);
                 if (tid == 0) tc_mark(sets.trace, rank, 5, g + 1);
 #pragma unroll
                 for (int i = 0; i < 4; ++i) {
@@ -760,7 +765,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             }
             tc_fence_before();
             __syncwarp();
-            if (lane == 0) mbar_arrive_cluster(mapa_shared(smem_u32(&S->acce[a]), 0));
+            if (lane == 0) mbar_arrive(rank == 0 ? &S->acce[a] : &S->pacce[a]);
             if (warp == kTcProdWarps && lane == 0) tc_mark(sets.trace, rank, 4, tile + 1);
         }
         __syncwarp();
@@ -804,11 +809,25 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         }
         __syncwarp();
     } else {
-        // ---- odd CTA: tell the issuer that this CTA's operator part has landed
+        // ---- odd CTA relays (one cluster-scope arrival per event instead
+        // of one per warp): lane 0 its operator part and its full A stages,
+        // lane 1 its drained accumulators, in the order the issuer needs them
         if (lane == 0) {
-            const bool ok = mbar_wait_cta(&S->barB, 0, failed, wl);
+            bool ok = mbar_wait_cta(&S->barB, 0, failed, wl);
             if (ok) mbar_arrive_cluster(mapa_shared(smem_u32(&S->barBp), 0));
             tc_mark(sets.trace, rank, 2, ok ? 1 : -1);
+            for (int g = 0; ok && g < ntile * KB; ++g) {
+                const int s = g % kTcStages, n = g / kTcStages;
+                if ((ok = mbar_wait_cta(&S->pfull[s], n & 1, failed, wl)))
+                    mbar_arrive_cluster(mapa_shared(smem_u32(&S->full[s]), 0));
+            }
+        } else if (lane == 1) {
+            bool ok = true;
+            for (int tile = 0; ok && tile < ntile; ++tile) {
+                const int a = tile & 1, u = tile >> 1;
+                if ((ok = mbar_wait_cta(&S->pacce[a], u & 1, failed, wl)))
+                    mbar_arrive_cluster(mapa_shared(smem_u32(&S->acce[a]), 0));
+            }
         }
         __syncwarp();
     }
