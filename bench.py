@@ -89,6 +89,10 @@ def parse():
                     help="formulation of --binding: exterior derivative (P1, Eq. lu) or direct (P0)")
     ap.add_argument("--kirkwood", action="store_true",
                     help="off-centre-charge sphere refinement study (512 ... 131,072 elements)")
+    ap.add_argument("--leaf-nt", type=int, default=0, choices=[0, 2, 4],
+                    help="targets per thread of the leaf kernel (PB_OPT_LEAF_NT; 0: the library's default)")
+    ap.add_argument("--leaf-scalar", action="store_true",
+                    help="scalar FP32 leaf kernel instead of the packed f32x2 one (PB_OPT_LEAF_PACKED 0)")
     return ap.parse_args()
 
 
@@ -549,6 +553,8 @@ def main():
 
     stream = torch.cuda.Stream()
     ctx = pb.pb_create(local, stream)
+    pb.pb_set_option(ctx, pb.PB_OPT_LEAF_NT, args.leaf_nt)
+    pb.pb_set_option(ctx, pb.PB_OPT_LEAF_PACKED, 0 if args.leaf_scalar else 1)
     X = torch.from_numpy(x).cuda()
     Nr = torch.from_numpy(nrm).cuda()
     Q = torch.from_numpy(q).cuda()

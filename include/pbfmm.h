@@ -147,8 +147,19 @@ int pb_profile(pb_ctx* ctx, int enable);
  *                         the total iterations.  A system whose cycle ends
  *                         unconverged takes its update, recomputes its
  *                         residual with one mat-vec and starts a new cycle.
+ *   PB_OPT_LEAF_NT        targets per thread of the leaf (P2P + M2P + L2P)
+ *                         kernel of fmm_apply_pair: 0 (default): 4 in FP32,
+ *                         2 in FP64; 2 or 4.  A tile-shape knob of the
+ *                         autotuner (pb_tune_ncrit); results differ only by
+ *                         the summation order of each target's partial sums.
+ *   PB_OPT_LEAF_PACKED    1 (default): the FP32 leaf kernel of fmm_apply_pair
+ *                         without target-normal derivatives takes two sources
+ *                         per packed instruction (add/mul/fma .f32x2); 0: one
+ *                         source per scalar instruction.  Same arithmetic per
+ *                         pair, summation order of the partial sums differs.
  * Errors: PB_EINVAL for an unknown option or value. */
-enum { PB_OPT_COUPLING = 1, PB_OPT_DETERMINISTIC = 2, PB_OPT_SINGULAR = 3, PB_OPT_OVERLAP = 4, PB_OPT_RESTART = 5 };
+enum { PB_OPT_COUPLING = 1, PB_OPT_DETERMINISTIC = 2, PB_OPT_SINGULAR = 3, PB_OPT_OVERLAP = 4, PB_OPT_RESTART = 5,
+       PB_OPT_LEAF_NT = 6, PB_OPT_LEAF_PACKED = 7 };
 int pb_set_option(pb_ctx* ctx, int option, int value);
 int pb_profile_read(pb_ctx* ctx, int phase, double* ms, int64_t* calls);
 

@@ -192,6 +192,8 @@ int pb_set_option(pb_ctx* ctx, int option, int value) {
     if (option == PB_OPT_DETERMINISTIC && (value == 0 || value == 1)) { ctx->deterministic = value; return PB_OK; }
     if (option == PB_OPT_SINGULAR && value >= 0 && value <= 2) { ctx->singular = value; return PB_OK; }
     if (option == PB_OPT_OVERLAP && (value == 0 || value == 1)) { ctx->overlap = value; return PB_OK; }
+    if (option == PB_OPT_LEAF_NT && (value == 0 || value == 2 || value == 4)) { ctx->leaf_nt = value; return PB_OK; }
+    if (option == PB_OPT_LEAF_PACKED && (value == 0 || value == 1)) { ctx->leaf_packed = value; return PB_OK; }
     if (option == PB_OPT_RESTART && value >= 0 && value <= 2000) { ctx->restart = value; return PB_OK; }
     ctx->last_error = "pb_set_option: unknown option or value";
     return PB_EINVAL;

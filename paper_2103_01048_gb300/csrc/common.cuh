@@ -137,6 +137,8 @@ struct pb_ctx {
     int deterministic = 0;     // 1: no run-dependent reductions (SIMT M2L/M2M/L2L)
     int singular = 0;          // singular entries: 0 auto, 1 FP64 (depth 5), 2 FP32 (depth 4)
     int overlap = 0;           // 1: near field of the paired apply on `aux`, beside the far field
+    int leaf_nt = 0;           // targets per thread of the paired leaf kernel (0: by precision)
+    int leaf_packed = 1;       // FP32 paired leaf kernel with packed (f32x2) arithmetic
     int restart = 0;           // GMRES restart length of the batched solves (0: none)
     // second stream (and fork / join events) for the near field of the paired
     // apply; null: everything on `stream`

@@ -235,6 +235,24 @@ __global__ void __launch_bounds__(256) k_p2check(int nbox, const int* __restrict
     }
 }
 
+// ---- staging of a leaf's source stream in shared memory
+// 16-byte asynchronous global -> shared copy (no register round trip; the
+// CTA waits once per staged window instead of once per source box).
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+template <typename V>
+__device__ __forceinline__ void cp_async_v(V* smem, const V* gmem) {
+    static_assert(sizeof(V) % 16 == 0, "16-byte pieces");
+#pragma unroll
+    for (int i = 0; i < (int)(sizeof(V) / 16); ++i)
+        cp_async16(reinterpret_cast<char*>(smem) + 16 * i, reinterpret_cast<const char*>(gmem) + 16 * i);
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
+
 // P2M / P2L of the paired apply: Laplace and Yukawa check potentials of the
 // same sources in one pass (sm carries the dipole and the Yukawa monopole).
 template <typename T, bool DL, int MAXP>
@@ -642,8 +660,50 @@ __global__ void __launch_bounds__(128) k_leaf_eval(const int* __restrict__ leave
     }
 }
 
-// Leaf evaluation of the paired apply: the same work split as k_leaf_eval,
-// with the Laplace and the Yukawa sums of every pair taken together.
+// Position in a U list taken in the order "the leaf itself first, then the
+// others in list order" (selfpos = the leaf's index in the list, or -1).
+__device__ __forceinline__ int u_at(int vi, int selfpos) {
+    return selfpos < 0 ? vi : (vi == 0 ? selfpos : (vi <= selfpos ? vi - 1 : vi));
+}
+
+// Copies the next window (at most CAP points) of the concatenated sources of
+// the U-list boxes into s_q (and s_m if WITH_M), advancing the cursor
+// (vi = box in self-first order, off = points of that box already staged).
+// Returns the number of points staged; the caller synchronises the CTA.
+template <typename V, bool WITH_M, int CAP>
+__device__ __forceinline__ int stage_near(V* s_q, V* s_m, const V* __restrict__ sq, const V* __restrict__ sm,
+                                          const int* __restrict__ ul, int nu, int selfpos,
+                                          const int* __restrict__ sb, const int* __restrict__ se, int& vi,
+                                          int& off) {
+    int filled = 0;
+    while (filled < CAP && vi < nu) {
+        const int a = ul[u_at(vi, selfpos)];
+        const int j0 = sb[a] + off, len = se[a] - j0;
+        const int take = min(len, CAP - filled);
+        for (int e = threadIdx.x; e < take; e += blockDim.x) {
+            cp_async_v(s_q + filled + e, sq + j0 + e);
+            if (WITH_M) cp_async_v(s_m + filled + e, sm + j0 + e);
+        }
+        filled += take;
+        if (take == len) { ++vi; off = 0; } else off += take;
+    }
+    cp_async_wait_all();
+    return filled;
+}
+
+// Leaf evaluation of the paired apply (Laplace and Yukawa sums of every pair
+// taken together), one 128-thread CTA per target leaf.  Targets: NT per
+// thread in slots = ceil(n_t / NT) threads; the CTA holds G = 128 / slots
+// groups of slots threads.  Sources: the leaf's whole near field (the
+// U-list boxes, the leaf itself first, concatenated) is staged in windows
+// of CAP points with asynchronous copies, then the far field (W-list upward
+// and the leaf's own downward equivalent surfaces) in windows of generated
+// points; group g takes the points g, g + G, g + 2G, ... of a window, so
+// the lanes of a warp read neighbouring points (no bank conflicts) and
+// every group has the same count to within one.  Only the leaf's own box
+// can hold a coincident pair (equal points share a Morton key), so only its
+// points take the r = 0 guard.  The G partial sums of each target are
+// added in a fixed order at the end.
 // PART 0: everything; 1: the near field (P2P) only, writing the outputs;
 // 2: the far field (M2P, L2P) only, adding to the outputs of a PART 1 launch.
 template <typename T, bool DL, bool DN, int NT, int PART>
@@ -664,120 +724,130 @@ __global__ void __launch_bounds__(128) k_leaf_pair(const int* __restrict__ leave
                                                    T* __restrict__ dnL_out, T* __restrict__ dnY_out) {
     using V = typename V4<T>::type;
     constexpr int CH = 128;
+    constexpr int CAP = 16384 / (int)sizeof(V);     // points per window: 16 KB per array
     constexpr int NR = DN ? 4 : 2;
-    __shared__ V s_q[CH];
-    __shared__ V s_m[CH];
-    __shared__ T s_red[NR][NT * CH];
-    int li = blockIdx.x;
+    static_assert(NR * NT * CH * (int)sizeof(T) <= CAP * (int)sizeof(V), "reduction fits the staging buffer");
+    __shared__ __align__(16) V s_q[CAP];
+    __shared__ __align__(16) V s_m[CAP];
+    __shared__ int s_self;
+    T* s_red = reinterpret_cast<T*>(s_q);            // [NR][NT * CH], after the last window
+    T* s_qy = reinterpret_cast<T*>(s_m);             // far windows: the Yukawa densities
+    const int li = blockIdx.x;
     if (li >= nleaf) return;
     const int b = leaves[li];
     const int t0 = tb[b], t1 = te[b];
     const int slots = min(CH, max(4, (t1 - t0 + NT - 1) / NT));
     const int G = CH / slots;
     const int tloc = threadIdx.x % slots, g = threadIdx.x / slots;
+    const bool active = g < G;
+    const int* ul = U_ids + U_off[b];
+    const int nu = U_off[b + 1] - U_off[b];
     const int nw = W_off[b + 1] - W_off[b];
     const int nsrcbox = nw + (level[b] >= 2 ? 1 : 0);
+    const int nf = nsrcbox * ne;
+    const double4 cb = center[b];
     const T kl2 = -kappa * T(kLog2E);
+    if (threadIdx.x == 0) s_self = -1;
+    __syncthreads();
+    for (int i = threadIdx.x; i < nu; i += CH)
+        if (ul[i] == b) s_self = i;
+    __syncthreads();
+    const int selfpos = s_self;
+    const int nself = selfpos >= 0 ? se[b] - sb[b] : 0;
     for (int tc = t0; tc < t1; tc += NT * slots) {
         int ti[NT];
         bool vt[NT];
-        float4 xt[NT];
+        T xt[NT], yt[NT], zt[NT];
         T nx[NT], ny[NT], nz[NT], pL[NT], pY[NT], dL[NT], dY[NT];
 #pragma unroll
         for (int u = 0; u < NT; ++u) {
             ti[u] = tc + tloc + u * slots;
             vt[u] = ti[u] < t1;
-            xt[u] = vt[u] ? tpos[ti[u]] : make_float4(0, 0, 0, 0);
+            const float4 x = vt[u] ? tpos[ti[u]] : make_float4(0, 0, 0, 0);
+            xt[u] = x.x; yt[u] = x.y; zt[u] = x.z;
             nx[u] = ny[u] = nz[u] = T(0);
             if (DN && vt[u]) { V nn = tn[ti[u]]; nx[u] = nn.x; ny[u] = nn.y; nz[u] = nn.z; }
             pL[u] = pY[u] = dL[u] = dY[u] = T(0);
         }
-        // P2P
-        for (int ui = U_off[b]; PART != 2 && ui < U_off[b + 1]; ++ui) {
-            const int a = U_ids[ui];
-            const int j0 = sb[a], j1 = se[a];
-            for (int jc = j0; jc < j1; jc += CH) {
-                int j = jc + threadIdx.x;
+        // P2P over the staged windows of the near field
+        if (PART != 2) {
+            int vi = 0, off = 0;
+            while (vi < nu) {
+                const int self_left = (selfpos >= 0 && vi == 0) ? nself - off : 0;
+                const int n = stage_near<V, true, CAP>(s_q, s_m, sq, sm, ul, nu, selfpos, sb, se, vi, off);   // sm.w: Yukawa monopole
                 __syncthreads();
-                if (j < j1) {
-                    s_q[threadIdx.x] = sq[j];
-                    s_m[threadIdx.x] = sm[j];
-                }
-                __syncthreads();
-                const int cnt = min(CH, j1 - jc);
-                // group g takes a contiguous share of the chunk
-                const int per = (cnt + G - 1) / G;
-                const int k0 = g * per, k1 = min(cnt, k0 + per);
-                if (a == b) {
-#pragma unroll 2
-                    for (int k = k0; k < k1; ++k) {
-                        V s = s_q[k], mm = s_m[k];
+                const int selfhi = min(self_left, n);
+                int k = g;
+                for (; active && k < selfhi; k += G) {
+                    const V s = s_q[k], mm = s_m[k];
 #pragma unroll
-                        for (int u = 0; u < NT; ++u)
-                            interact_pair<T, DL, DN, true>((T)xt[u].x - s.x, (T)xt[u].y - s.y, (T)xt[u].z - s.z, s.w,
-                                                           mm.w, mm.x, mm.y, mm.z, nx[u], ny[u], nz[u], kappa, kl2,
-                                                           pL[u], pY[u], dL[u], dY[u]);
-                    }
-                } else {
+                    for (int u = 0; u < NT; ++u)
+                        interact_pair<T, DL, DN, true>(xt[u] - s.x, yt[u] - s.y, zt[u] - s.z, s.w, mm.w, mm.x, mm.y,
+                                                       mm.z, nx[u], ny[u], nz[u], kappa, kl2, pL[u], pY[u], dL[u],
+                                                       dY[u]);
+                }
 #pragma unroll 4
-                    for (int k = k0; k < k1; ++k) {
-                        V s = s_q[k], mm = s_m[k];
+                for (; active && k < n; k += G) {
+                    const V s = s_q[k], mm = s_m[k];
 #pragma unroll
-                        for (int u = 0; u < NT; ++u)
-                            interact_pair<T, DL, DN, false>((T)xt[u].x - s.x, (T)xt[u].y - s.y, (T)xt[u].z - s.z,
-                                                            s.w, mm.w, mm.x, mm.y, mm.z, nx[u], ny[u], nz[u], kappa,
-                                                            kl2, pL[u], pY[u], dL[u], dY[u]);
-                    }
+                    for (int u = 0; u < NT; ++u)
+                        interact_pair<T, DL, DN, false>(xt[u] - s.x, yt[u] - s.y, zt[u] - s.z, s.w, mm.w, mm.x,
+                                                        mm.y, mm.z, nx[u], ny[u], nz[u], kappa, kl2, pL[u], pY[u],
+                                                        dL[u], dY[u]);
                 }
+                __syncthreads();
             }
         }
-        // M2P (W list) and L2P (own downward equivalent)
-        for (int wi = 0; PART != 1 && wi < nsrcbox; ++wi) {
-            const int a = (wi < nw) ? W_ids[W_off[b] + wi] : b;
-            const T* QL = (wi < nw) ? QuL : QdL;
-            const T* QY = (wi < nw) ? QuY : QdY;
-            const double4 ca = center[a];
-            const T alpha = T(wi < nw ? kAlphaInner : kAlphaOuter) * (T)ca.w;
+        // M2P (W list, upward equivalents) and L2P (own downward equivalent),
+        // in coordinates relative to the leaf's centre
+        if (PART != 1 && nf > 0) {
             T rx[NT], ry[NT], rz[NT];
 #pragma unroll
             for (int u = 0; u < NT; ++u) {
-                rx[u] = (T)((double)xt[u].x - ca.x);
-                ry[u] = (T)((double)xt[u].y - ca.y);
-                rz[u] = (T)((double)xt[u].z - ca.z);
+                rx[u] = (T)((double)xt[u] - cb.x);
+                ry[u] = (T)((double)yt[u] - cb.y);
+                rz[u] = (T)((double)zt[u] - cb.z);
             }
-            for (int jc = 0; jc < ne; jc += CH) {
-                int j = jc + threadIdx.x;
-                __syncthreads();
-                if (j < ne) {
-                    float4 s = surf[j];
-                    s_q[threadIdx.x] = {alpha * (T)s.x, alpha * (T)s.y, alpha * (T)s.z, QL[(size_t)a * npad + j]};
-                    s_m[threadIdx.x].w = QY[(size_t)a * npad + j];
+            for (int w0 = 0; w0 < nf; w0 += CAP) {
+                const int n = min(CAP, nf - w0);
+                for (int e = threadIdx.x; e < n; e += CH) {
+                    const int v = w0 + e, i = v / ne, j = v - i * ne;
+                    const bool isw = i < nw;
+                    const int a = isw ? W_ids[W_off[b] + i] : b;
+                    const double4 ca = center[a];
+                    const T alpha = T(isw ? kAlphaInner : kAlphaOuter) * (T)ca.w;
+                    const float4 s = surf[j];
+                    const size_t o = (size_t)a * npad + j;
+                    V w;
+                    w.x = (T)(ca.x - cb.x) + alpha * (T)s.x;
+                    w.y = (T)(ca.y - cb.y) + alpha * (T)s.y;
+                    w.z = (T)(ca.z - cb.z) + alpha * (T)s.z;
+                    w.w = isw ? QuL[o] : QdL[o];
+                    s_q[e] = w;
+                    s_qy[e] = isw ? QuY[o] : QdY[o];
                 }
                 __syncthreads();
-                const int cnt = min(CH, ne - jc);
-                const int per = (cnt + G - 1) / G;
-                const int k0 = g * per, k1 = min(cnt, k0 + per);
 #pragma unroll 4
-                for (int k = k0; k < k1; ++k) {
-                    V s = s_q[k];
-                    T qy = s_m[k].w;
+                for (int k = g; active && k < n; k += G) {
+                    const V s = s_q[k];
+                    const T qy = s_qy[k];
 #pragma unroll
                     for (int u = 0; u < NT; ++u)
                         interact_pair<T, false, DN, false>(rx[u] - s.x, ry[u] - s.y, rz[u] - s.z, s.w, qy, 0, 0, 0,
                                                            nx[u], ny[u], nz[u], kappa, kl2, pL[u], pY[u], dL[u],
                                                            dY[u]);
                 }
+                __syncthreads();
             }
         }
-        // combine the G partial sums of each target
-        __syncthreads();
+        // combine the G partial sums of each target (the staging buffer is free)
 #pragma unroll
         for (int u = 0; u < NT; ++u) {
-            s_red[0][u * CH + threadIdx.x] = pL[u];
-            s_red[1][u * CH + threadIdx.x] = pY[u];
+            s_red[(0 * NT + u) * CH + threadIdx.x] = pL[u];
+            s_red[(1 * NT + u) * CH + threadIdx.x] = pY[u];
             if (DN) {
-                s_red[NR - 2][u * CH + threadIdx.x] = dL[u];
-                s_red[NR - 1][u * CH + threadIdx.x] = dY[u];
+                s_red[((NR - 2) * NT + u) * CH + threadIdx.x] = dL[u];
+                s_red[((NR - 1) * NT + u) * CH + threadIdx.x] = dY[u];
             }
         }
         __syncthreads();
@@ -787,9 +857,9 @@ __global__ void __launch_bounds__(128) k_leaf_pair(const int* __restrict__ leave
                 T a0 = 0, a1 = 0, a2 = 0, a3 = 0;
                 for (int q = 0; q < G; ++q) {
                     const int o = u * CH + tloc + q * slots;
-                    a0 += s_red[0][o];
-                    a1 += s_red[1][o];
-                    if (DN) { a2 += s_red[NR - 2][o]; a3 += s_red[NR - 1][o]; }
+                    a0 += s_red[0 * NT * CH + o];
+                    a1 += s_red[1 * NT * CH + o];
+                    if (DN) { a2 += s_red[(NR - 2) * NT * CH + o]; a3 += s_red[(NR - 1) * NT * CH + o]; }
                 }
                 if (vt[u]) {
                     if (PART == 2) {          // after the near-field launch (each target has one thread)
@@ -810,6 +880,311 @@ __global__ void __launch_bounds__(128) k_leaf_pair(const int* __restrict__ leave
                 }
             }
         }
+        __syncthreads();              // s_red is the next chunk's staging buffer
+    }
+}
+
+// ---- packed FP32: two sources per instruction
+// add / sub / mul / fma .rn.f32x2 on 64-bit register pairs {lo, hi}: one
+// issue slot for two lanes' worth of FP32 work (the FMA pipe time is the
+// same as two scalar instructions; the freed issue slots take the MUFU,
+// shared-memory and loop instructions of an issue-bound kernel).
+typedef unsigned long long f32x2;
+__device__ __forceinline__ f32x2 x2_add(f32x2 a, f32x2 b) {
+    f32x2 d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f32x2 x2_sub(f32x2 a, f32x2 b) {
+    f32x2 d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f32x2 x2_mul(f32x2 a, f32x2 b) {
+    f32x2 d;
+    asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ f32x2 x2_fma(f32x2 a, f32x2 b, f32x2 c) {
+    f32x2 d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ f32x2 x2_pack(float lo, float hi) {
+    f32x2 d;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(d) : "f"(lo), "f"(hi));
+    return d;
+}
+__device__ __forceinline__ float x2_lo(f32x2 a) {
+    float l, h;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(l), "=f"(h) : "l"(a));
+    return l;
+}
+__device__ __forceinline__ float x2_hi(f32x2 a) {
+    float l, h;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(l), "=f"(h) : "l"(a));
+    return h;
+}
+template <bool GUARD>
+__device__ __forceinline__ f32x2 x2_rsqrt(f32x2 a) {
+    const float l = x2_lo(a), h = x2_hi(a);
+    if (GUARD) return x2_pack(l > 0.f ? rsqrt_t<float>(l) : 0.f, h > 0.f ? rsqrt_t<float>(h) : 0.f);
+    return x2_pack(rsqrt_t<float>(l), rsqrt_t<float>(h));
+}
+__device__ __forceinline__ f32x2 x2_exp2(f32x2 a) { return x2_pack(exp2_t<float>(x2_lo(a)), exp2_t<float>(x2_hi(a))); }
+
+// interact_pair for one target (coordinates in both halves) and two sources
+// (one per half), the same grouping of the arithmetic.  Source pair layout:
+// A = {x, y}, B = {z, qL}, C = {mx, my}, D = {mz, qY}, each a pair.
+template <bool DL, bool GUARD>
+__device__ __forceinline__ void interact_x2(f32x2 X, f32x2 Y, f32x2 Z, const ulonglong2& A, const ulonglong2& B,
+                                            const ulonglong2& C, const ulonglong2& D, f32x2 kap, f32x2 kl2,
+                                            f32x2 one, f32x2& pL, f32x2& pY) {
+    const f32x2 dx = x2_sub(X, A.x), dy = x2_sub(Y, A.y), dz = x2_sub(Z, B.x);
+    const f32x2 r2 = x2_fma(dx, dx, x2_fma(dy, dy, x2_mul(dz, dz)));
+    const f32x2 rinv = x2_rsqrt<GUARD>(r2);
+    const f32x2 r = x2_mul(r2, rinv);
+    const f32x2 er = x2_mul(x2_exp2(x2_mul(kl2, r)), rinv);        // e^{-kr} / r
+    if (DL) {
+        const f32x2 rinv2 = x2_mul(rinv, rinv);
+        const f32x2 u = x2_fma(kap, r, one);
+        const f32x2 w = x2_mul(x2_fma(dx, C.x, x2_fma(dy, C.y, x2_mul(dz, D.x))), rinv2);
+        pL = x2_fma(rinv, x2_add(w, B.y), pL);
+        pY = x2_fma(er, x2_fma(w, u, D.y), pY);
+    } else {
+        pL = x2_fma(rinv, B.y, pL);
+        pY = x2_fma(er, D.y, pY);
+    }
+}
+
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+
+// Copies source j (sq = {x, y, z, qL}, sm = {mx, my, mz, qY}) into half
+// e & 1 of pair slot e >> 1 of the packed window with 4-byte asynchronous
+// copies (the dipole only if DL).
+template <bool DL>
+__device__ __forceinline__ void copy_src_x2(ulonglong2* sA, ulonglong2* sB, ulonglong2* sC, ulonglong2* sD, int e,
+                                            const float4* __restrict__ sq, const float4* __restrict__ sm,
+                                            int j) {
+    const int p = e >> 1, h = e & 1;
+    float* a = reinterpret_cast<float*>(sA + p);
+    float* b = reinterpret_cast<float*>(sB + p);
+    float* c = reinterpret_cast<float*>(sC + p);
+    float* d = reinterpret_cast<float*>(sD + p);
+    const float* q = reinterpret_cast<const float*>(sq + j);
+    const float* m = reinterpret_cast<const float*>(sm + j);
+    cp_async4(a + h, q);
+    cp_async4(a + 2 + h, q + 1);
+    cp_async4(b + h, q + 2);
+    cp_async4(b + 2 + h, q + 3);
+    if (DL) {
+        cp_async4(c + h, m);
+        cp_async4(c + 2 + h, m + 1);
+        cp_async4(d + h, m + 2);
+    }
+    cp_async4(d + 2 + h, m + 3);
+}
+
+// Writes one source (or equivalent point) into half h of pair slot p of the
+// packed window (A..D as above).
+__device__ __forceinline__ void put_src_x2(ulonglong2* sA, ulonglong2* sB, ulonglong2* sC, ulonglong2* sD, int e,
+                                           float x, float y, float z, float qL, float mx, float my, float mz,
+                                           float qY) {
+    const int p = e >> 1, h = e & 1;
+    float* a = reinterpret_cast<float*>(sA + p);
+    float* b = reinterpret_cast<float*>(sB + p);
+    float* c = reinterpret_cast<float*>(sC + p);
+    float* d = reinterpret_cast<float*>(sD + p);
+    a[h] = x; a[2 + h] = y;
+    b[h] = z; b[2 + h] = qL;
+    c[h] = mx; c[2 + h] = my;
+    d[h] = mz; d[2 + h] = qY;
+}
+
+// The paired leaf kernel in packed FP32 (no target-normal derivatives): the
+// work split of k_leaf_pair (NT targets per thread, G groups, the near field
+// in windows of the concatenated U-list sources, the leaf itself first, then
+// the far field in windows of generated equivalent points), with each window
+// stored as pairs of points, every value pair one 64-bit half of a 16-byte
+// vector, so that group g takes the pairs g, g + G, ... and one packed
+// instruction serves two sources.  An odd window is padded with a point of
+// zero weight 1e10 away (its terms are exactly 0).
+template <bool DL, int NT, int PART>
+__global__ void __launch_bounds__(128, 5) k_leaf_pair_x2(const int* __restrict__ leaves, int nleaf,
+                                                      const int* __restrict__ tb, const int* __restrict__ te,
+                                                      const int* __restrict__ sb, const int* __restrict__ se,
+                                                      const int* __restrict__ U_off, const int* __restrict__ U_ids,
+                                                      const int* __restrict__ W_off, const int* __restrict__ W_ids,
+                                                      const int* __restrict__ level,
+                                                      const double4* __restrict__ center,
+                                                      const float4* __restrict__ tpos, const float4* __restrict__ sq,
+                                                      const float4* __restrict__ sm, const float* __restrict__ QuL,
+                                                      const float* __restrict__ QdL, const float* __restrict__ QuY,
+                                                      const float* __restrict__ QdY, const float4* __restrict__ surf,
+                                                      int ne, int npad, float kappa, float* __restrict__ potL_out,
+                                                      float* __restrict__ potY_out) {
+    constexpr int CH = 128;
+    constexpr int CAP = 1024;                    // points per window (512 pairs, 32 KB)
+    constexpr int CP = CAP / 2;
+    static_assert(2 * NT * CH * 4 <= CP * 16, "reduction fits one staging array");
+    __shared__ ulonglong2 sA[CP], sB[CP], sC[CP], sD[CP];
+    __shared__ int s_self;
+    __shared__ float4 s_box[CH];                 // far window: box centre relative to the leaf's, radius
+    __shared__ int s_boxid[CH];                  // box id (W list) or -1 - id (own downward)
+    float* s_red = reinterpret_cast<float*>(sA);
+    const int li = blockIdx.x;
+    if (li >= nleaf) return;
+    const int b = leaves[li];
+    const int t0 = tb[b], t1 = te[b];
+    const int slots = min(CH, max(4, (t1 - t0 + NT - 1) / NT));
+    const int G = CH / slots;
+    const int tloc = threadIdx.x % slots, g = threadIdx.x / slots;
+    const bool active = g < G;
+    const int* ul = U_ids + U_off[b];
+    const int nu = U_off[b + 1] - U_off[b];
+    const int nw = W_off[b + 1] - W_off[b];
+    const int nsrcbox = nw + (level[b] >= 2 ? 1 : 0);
+    const int nf = nsrcbox * ne;
+    const double4 cb = center[b];
+    const float kl2s = -kappa * float(kLog2E);
+    const f32x2 kap = x2_pack(kappa, kappa), kl2 = x2_pack(kl2s, kl2s), one = x2_pack(1.f, 1.f);
+    if (threadIdx.x == 0) s_self = -1;
+    __syncthreads();
+    for (int i = threadIdx.x; i < nu; i += CH)
+        if (ul[i] == b) s_self = i;
+    __syncthreads();
+    const int selfpos = s_self;
+    const int nself = selfpos >= 0 ? se[b] - sb[b] : 0;
+    for (int tc = t0; tc < t1; tc += NT * slots) {
+        int ti[NT];
+        bool vt[NT];
+        f32x2 X[NT], Y[NT], Z[NT], pL[NT], pY[NT];
+        float xs[NT], ys[NT], zs[NT];
+#pragma unroll
+        for (int u = 0; u < NT; ++u) {
+            ti[u] = tc + tloc + u * slots;
+            vt[u] = ti[u] < t1;
+            const float4 x = vt[u] ? tpos[ti[u]] : make_float4(0, 0, 0, 0);
+            xs[u] = x.x; ys[u] = x.y; zs[u] = x.z;
+            X[u] = x2_pack(x.x, x.x); Y[u] = x2_pack(x.y, x.y); Z[u] = x2_pack(x.z, x.z);
+            pL[u] = pY[u] = 0ull;
+        }
+        if (PART != 2) {
+            int vi = 0, off = 0;
+            while (vi < nu) {
+                const int self_left = (selfpos >= 0 && vi == 0) ? nself - off : 0;
+                int filled = 0;
+                while (filled < CAP && vi < nu) {
+                    const int a = ul[u_at(vi, selfpos)];
+                    const int j0 = sb[a] + off, len = se[a] - j0;
+                    const int take = min(len, CAP - filled);
+                    for (int e = threadIdx.x; e < take; e += CH)
+                        copy_src_x2<DL>(sA, sB, sC, sD, filled + e, sq, sm, j0 + e);
+                    filled += take;
+                    if (take == len) { ++vi; off = 0; } else off += take;
+                }
+                if ((filled & 1) && threadIdx.x == 0)
+                    put_src_x2(sA, sB, sC, sD, filled, 1e10f, 1e10f, 1e10f, 0.f, 0.f, 0.f, 0.f, 0.f);
+                cp_async_wait_all();
+                __syncthreads();
+                const int np = (filled + 1) >> 1;
+                const int selfp = (min(self_left, filled) + 1) >> 1;      // pairs holding a point of the leaf
+                int k = g;
+                for (; active && k < selfp; k += G) {
+                    const ulonglong2 A = sA[k], B = sB[k], C = DL ? sC[k] : make_ulonglong2(0, 0), D = sD[k];
+#pragma unroll
+                    for (int u = 0; u < NT; ++u)
+                        interact_x2<DL, true>(X[u], Y[u], Z[u], A, B, C, D, kap, kl2, one, pL[u], pY[u]);
+                }
+#pragma unroll 2
+                for (; active && k < np; k += G) {
+                    const ulonglong2 A = sA[k], B = sB[k], C = DL ? sC[k] : make_ulonglong2(0, 0), D = sD[k];
+#pragma unroll
+                    for (int u = 0; u < NT; ++u)
+                        interact_x2<DL, false>(X[u], Y[u], Z[u], A, B, C, D, kap, kl2, one, pL[u], pY[u]);
+                }
+                __syncthreads();
+            }
+        }
+        if (PART != 1 && nf > 0) {
+#pragma unroll
+            for (int u = 0; u < NT; ++u) {
+                const float rx = (float)((double)xs[u] - cb.x), ry = (float)((double)ys[u] - cb.y),
+                            rz = (float)((double)zs[u] - cb.z);
+                X[u] = x2_pack(rx, rx); Y[u] = x2_pack(ry, ry); Z[u] = x2_pack(rz, rz);
+            }
+            const int nbw = CAP / ne;                    // whole boxes per window (ne <= CAP: host)
+            for (int i0 = 0; i0 < nsrcbox; i0 += nbw) {
+                const int nb = min(nbw, nsrcbox - i0), n = nb * ne;
+                if (threadIdx.x < nb) {
+                    const int i = i0 + threadIdx.x;
+                    const bool isw = i < nw;
+                    const int a = isw ? W_ids[W_off[b] + i] : b;
+                    const double4 ca = center[a];
+                    s_box[threadIdx.x] = make_float4((float)(ca.x - cb.x), (float)(ca.y - cb.y),
+                                                     (float)(ca.z - cb.z),
+                                                     float(isw ? kAlphaInner : kAlphaOuter) * (float)ca.w);
+                    s_boxid[threadIdx.x] = isw ? a : -1 - a;
+                }
+                __syncthreads();
+                for (int i = 0; i < nb; ++i) {
+                    const float4 bx = s_box[i];
+                    const int code = s_boxid[i];
+                    const bool isw = code >= 0;
+                    const size_t base = (size_t)(isw ? code : -1 - code) * npad;
+                    const float* QL = isw ? QuL : QdL;
+                    const float* QY = isw ? QuY : QdY;
+                    for (int j = threadIdx.x; j < ne; j += CH) {
+                        const float4 sf = surf[j];
+                        put_src_x2(sA, sB, sC, sD, i * ne + j, bx.x + bx.w * sf.x, bx.y + bx.w * sf.y,
+                                   bx.z + bx.w * sf.z, QL[base + j], 0.f, 0.f, 0.f, QY[base + j]);
+                    }
+                }
+                if ((n & 1) && threadIdx.x == 0)
+                    put_src_x2(sA, sB, sC, sD, n, 1e10f, 1e10f, 1e10f, 0.f, 0.f, 0.f, 0.f, 0.f);
+                __syncthreads();
+                const int np = (n + 1) >> 1;
+                const ulonglong2 C0 = make_ulonglong2(0, 0);
+#pragma unroll 2
+                for (int k = g; active && k < np; k += G) {
+                    const ulonglong2 A = sA[k], B = sB[k], D = sD[k];
+#pragma unroll
+                    for (int u = 0; u < NT; ++u)
+                        interact_x2<false, false>(X[u], Y[u], Z[u], A, B, C0, D, kap, kl2, one, pL[u], pY[u]);
+                }
+                __syncthreads();
+            }
+        }
+        // combine: the two halves of each accumulator, then the G groups
+#pragma unroll
+        for (int u = 0; u < NT; ++u) {
+            s_red[u * CH + threadIdx.x] = x2_lo(pL[u]) + x2_hi(pL[u]);
+            s_red[(NT + u) * CH + threadIdx.x] = x2_lo(pY[u]) + x2_hi(pY[u]);
+        }
+        __syncthreads();
+        if (g == 0) {
+#pragma unroll
+            for (int u = 0; u < NT; ++u) {
+                float a0 = 0.f, a1 = 0.f;
+                for (int q = 0; q < G; ++q) {
+                    a0 += s_red[u * CH + tloc + q * slots];
+                    a1 += s_red[(NT + u) * CH + tloc + q * slots];
+                }
+                if (vt[u]) {
+                    if (PART == 2) {
+                        potL_out[ti[u]] += a0 * float(kInv4PiD);
+                        potY_out[ti[u]] += a1 * float(kInv4PiD);
+                    } else {
+                        potL_out[ti[u]] = a0 * float(kInv4PiD);
+                        potY_out[ti[u]] = a1 * float(kInv4PiD);
+                    }
+                }
+            }
+        }
+        __syncthreads();
     }
 }
 
@@ -1168,8 +1543,22 @@ static void launch_leaf_pair(cudaStream_t st, fmm_tree* Tr, Work<T>& WL, Work<T>
     const float4* tpos = Tr->same ? Tr->pos_s.p : Tr->pos_t.p;
     const int* tb = Tr->same ? Tr->sb.p : Tr->tb.p;
     const int* te = Tr->same ? Tr->se.p : Tr->te.p;
-    constexpr int NT = 2;
-    k_leaf_pair<T, DL, DN, NT, PART><<<Tr->n_tleaf, 128, 0, st>>>(
+    const int nt_opt = Tr->ctx->leaf_nt;
+    if constexpr (std::is_same<T, float>::value && !DN) {
+        if (Tr->ctx->leaf_packed && O.ne <= 1024) {
+            const int NT = nt_opt ? nt_opt : 4;
+            auto k = NT == 4 ? k_leaf_pair_x2<DL, 4, PART> : k_leaf_pair_x2<DL, 2, PART>;
+            k<<<Tr->n_tleaf, 128, 0, st>>>(Tr->leaf_ids.p, Tr->n_tleaf, tb, te, Tr->sb.p, Tr->se.p, Tr->U_off.p,
+                                           Tr->U_ids.p, Tr->W_off.p, Tr->W_ids.p, Tr->level.p, Tr->center.p, tpos,
+                                           WL.sq.p, WL.sm.p, WL.Qu.p, WL.Qd.p, WY.Qu.p, WY.Qd.p,
+                                           (const float4*)O.surf_f.p, O.ne, O.npad, kappa, WL.pot.p, WY.pot.p);
+            PB_CHECK_LAUNCH();
+            return;
+        }
+    }
+    const int NT = nt_opt ? nt_opt : (sizeof(T) == 4 ? 4 : 2);
+    auto k = NT == 4 ? k_leaf_pair<T, DL, DN, 4, PART> : k_leaf_pair<T, DL, DN, 2, PART>;
+    k<<<Tr->n_tleaf, 128, 0, st>>>(
         Tr->leaf_ids.p, Tr->n_tleaf, tb, te, Tr->sb.p, Tr->se.p, Tr->U_off.p, Tr->U_ids.p, Tr->W_off.p, Tr->W_ids.p,
         Tr->level.p, Tr->center.p, tpos, WL.tn.p, WL.sq.p, WL.sm.p, WL.Qu.p, WL.Qd.p, WY.Qu.p, WY.Qd.p,
         (const float4*)O.surf_f.p, O.ne, O.npad, kappa, WL.pot.p, WY.pot.p, WL.dn.p, WY.dn.p);
