@@ -150,16 +150,21 @@ int pb_profile(pb_ctx* ctx, int enable);
  *   PB_OPT_LEAF_NT        targets per thread of the leaf (P2P + M2P + L2P)
  *                         kernel of fmm_apply_pair: 0 (default): 4 in FP32,
  *                         2 in FP64; 2 or 4.  A tile-shape knob of the
- *                         autotuner (pb_tune_ncrit); results differ only by
+ *                         autotuner (pb_tune); results differ only by
  *                         the summation order of each target's partial sums.
  *   PB_OPT_LEAF_PACKED    1 (default): the FP32 leaf kernel of fmm_apply_pair
  *                         without target-normal derivatives takes two sources
  *                         per packed instruction (add/mul/fma .f32x2); 0: one
  *                         source per scalar instruction.  Same arithmetic per
  *                         pair, summation order of the partial sums differs.
+ *   PB_OPT_M2L_TILE       row tile of the tensor-core M2L: 0 (default): 256
+ *                         pairs per MMA on CTA pairs (tcgen05 cta_group::2)
+ *                         where the operator size allows (n_pad >= 128), else
+ *                         128; 1: 128 pairs per MMA, one CTA per operator
+ *                         part.  A tile-shape knob of the autotuner (pb_tune).
  * Errors: PB_EINVAL for an unknown option or value. */
 enum { PB_OPT_COUPLING = 1, PB_OPT_DETERMINISTIC = 2, PB_OPT_SINGULAR = 3, PB_OPT_OVERLAP = 4, PB_OPT_RESTART = 5,
-       PB_OPT_LEAF_NT = 6, PB_OPT_LEAF_PACKED = 7 };
+       PB_OPT_LEAF_NT = 6, PB_OPT_LEAF_PACKED = 7, PB_OPT_M2L_TILE = 8 };
 int pb_set_option(pb_ctx* ctx, int option, int value);
 int pb_profile_read(pb_ctx* ctx, int phase, double* ms, int64_t* calls);
 
@@ -445,6 +450,20 @@ int pb_solve_batch_ex(pb_ctx* ctx, pb_mesh* const* meshes, int nsys, const doubl
  * (may be NULL) its time.  Synchronous. */
 int pb_tune_ncrit(pb_ctx* ctx, const float* xyz, int64_t n, int p, const int32_t* candidates, int ncand,
                   int* best_ncrit, double* best_ms);
+
+/* Autotuner for the leaf size and the tile shapes of the two hot kernels,
+ * on the work of one direct-formulation mat-vec: for each candidate ncrit
+ * it builds the octree of xyz (host or device, float [n][3]) and times the
+ * paired Laplace + Yukawa (kappa 0.125) single+double-layer apply
+ * (fmm_apply_pair, mixed precision, order p; mean of 3 after a warm run,
+ * CUDA events) with every combination of PB_OPT_LEAF_NT (2, 4) and
+ * PB_OPT_M2L_TILE (0, 1).  On return the context's PB_OPT_LEAF_NT and
+ * PB_OPT_M2L_TILE hold the fastest combination (on an error they keep their
+ * values from before the call); *best_ncrit, *best_leaf_nt, *best_m2l_tile
+ * and *best_ms (any of the last three may be NULL) receive it.  The tile
+ * options change the summation order of partial sums only.  Synchronous. */
+int pb_tune(pb_ctx* ctx, const float* xyz, int64_t n, int p, const int32_t* candidates, int ncand, int* best_ncrit,
+            int* best_leaf_nt, int* best_m2l_tile, double* best_ms);
 
 /* Gradient of the polar solvation energy of a solved system (kcal/mol per e
  * and per A) with respect to the atomic charges and positions, by one

@@ -101,6 +101,8 @@ _sig("pb_solve_batch_ex", [_P, _P, ctypes.c_int, _P, _P, _P, _D, _D, _D, _D, cty
                            _P, _P])
 _sig("pb_tune_ncrit", [_P, _P, _I64, ctypes.c_int, _P, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
                        ctypes.POINTER(_D)])
+_sig("pb_tune", [_P, _P, _I64, ctypes.c_int, _P, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                 ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int), ctypes.POINTER(_D)])
 
 
 class PBError(RuntimeError):
@@ -121,7 +123,8 @@ def exported_symbols():
             "fmm_apply", "fmm_apply_pair", "pb_mesh_setup", "pb_mesh_destroy", "pb_mesh_info", "pb_mesh_export_singular",
             "pb_mesh_matvec", "pb_mesh_matvec_ex", "pb_mesh_unknowns", "pb_solve", "pb_solve_ex",
             "pb_result_destroy", "pb_result_get", "pb_solvation_energy",
-            "pb_solvation_energy_noalloc", "pb_energy_grad", "pb_solve_batch", "pb_solve_batch_ex", "pb_tune_ncrit"]
+            "pb_solvation_energy_noalloc", "pb_energy_grad", "pb_solve_batch", "pb_solve_batch_ex", "pb_tune_ncrit",
+            "pb_tune"]
 
 
 def ptr(x):
@@ -167,7 +170,7 @@ PB_PH_LAUNCHES = 100
 
 
 PB_OPT_COUPLING, PB_OPT_DETERMINISTIC, PB_OPT_SINGULAR, PB_OPT_OVERLAP, PB_OPT_RESTART = 1, 2, 3, 4, 5
-PB_OPT_LEAF_NT, PB_OPT_LEAF_PACKED = 6, 7
+PB_OPT_LEAF_NT, PB_OPT_LEAF_PACKED, PB_OPT_M2L_TILE = 6, 7, 8
 
 
 def pb_set_option(ctx, option, value):
@@ -389,6 +392,18 @@ def pb_tune_ncrit(ctx, xyz, p, candidates):
     _check(_lib.pb_tune_ncrit(ctx, ptr(xyz), n, int(p), ptr(cand), len(cand), ctypes.byref(best), ctypes.byref(ms)),
            ctx)
     return best.value, ms.value
+
+
+def pb_tune(ctx, xyz, p, candidates):
+    """(best ncrit, leaf targets per thread, M2L tile option, its ms) for the
+    paired Laplace + Yukawa SL+DL apply; the context keeps the best tile options."""
+    cand = np.ascontiguousarray(candidates, dtype=np.int32)
+    best, nt, tile = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    ms = _D()
+    n = int(np.prod(xyz.shape)) // 3
+    _check(_lib.pb_tune(ctx, ptr(xyz), n, int(p), ptr(cand), len(cand), ctypes.byref(best), ctypes.byref(nt),
+                        ctypes.byref(tile), ctypes.byref(ms)), ctx)
+    return best.value, nt.value, tile.value, ms.value
 
 
 # test hooks (include/pbfmm_testing.h; not part of the solver's interface)

@@ -501,4 +501,70 @@ void tune_ncrit(pb_ctx* ctx, const float* xyz_dev, long long n, int p, const int
     if (best_ms) *best_ms = bestv;
 }
 
+// time the paired apply (the FMM work of one direct-formulation mat-vec) for
+// every candidate ncrit and every leaf / M2L tile shape; leave the fastest
+// tile shapes set on the context
+void tune_fmm(pb_ctx* ctx, const float* xyz_dev, long long n, int p, const int* cand, int ncand, int* best,
+              int* best_nt, int* best_tile, double* best_ms) {
+    cudaStream_t st = ctx->stream;
+    const int nt0 = ctx->leaf_nt, tile0 = ctx->m2l_tile;
+    DBuf<float> q, nrm, outL, outY;
+    q.alloc(n, st); nrm.alloc(3 * n, st); outL.alloc(n, st); outY.alloc(n, st);
+    k_fill<<<div_up(n, 256), 256, 0, st>>>(n, 1.0f, q.p);
+    k_fill<<<div_up(3 * n, 256), 256, 0, st>>>(3 * n, 0.57735026f, nrm.p);
+    PB_CHECK_LAUNCH();
+    cudaEvent_t a, b;
+    PB_CUDA(cudaEventCreate(&a));
+    PB_CUDA(cudaEventCreate(&b));
+    double bestv = 1e300;
+    int bc = cand[0], bnt = 4, btile = 0;
+    try {
+        for (int c = 0; c < ncand; ++c) {
+            fmm_tree T;
+            T.ctx = ctx;
+            T.ns = n;
+            T.nt = n;
+            T.same = true;
+            T.ncrit = cand[c];
+            build_tree(&T, xyz_dev, nullptr);
+            for (int nt : {2, 4})
+                for (int tile : {0, 1}) {
+                    ctx->leaf_nt = nt;
+                    ctx->m2l_tile = tile;
+                    auto run = [&]() {
+                        fmm_apply_pair_impl(&T, 0.125, p, PB_MIXED, q.p, q.p, q.p, nrm.p, nullptr, outL.p, outY.p,
+                                            nullptr, nullptr);
+                    };
+                    run();
+                    PB_CUDA(cudaStreamSynchronize(st));
+                    float ms = 0.f, tot = 0.f;
+                    for (int r = 0; r < 3; ++r) {
+                        PB_CUDA(cudaEventRecord(a, st));
+                        run();
+                        PB_CUDA(cudaEventRecord(b, st));
+                        PB_CUDA(cudaEventSynchronize(b));
+                        PB_CUDA(cudaEventElapsedTime(&ms, a, b));
+                        tot += ms;
+                    }
+                    if (tot / 3 < bestv) { bestv = tot / 3; bc = cand[c]; bnt = nt; btile = tile; }
+                }
+            PB_CUDA(cudaStreamSynchronize(st));
+        }
+    } catch (...) {
+        ctx->leaf_nt = nt0;
+        ctx->m2l_tile = tile0;
+        cudaEventDestroy(a);
+        cudaEventDestroy(b);
+        throw;
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    ctx->leaf_nt = bnt;
+    ctx->m2l_tile = btile;
+    *best = bc;
+    if (best_nt) *best_nt = bnt;
+    if (best_tile) *best_tile = btile;
+    if (best_ms) *best_ms = bestv;
+}
+
 }  // namespace pbfmm

@@ -22,6 +22,8 @@ void solve_batch(pb_ctx* ctx, pb_mesh* const* meshes, int nsys, pb_result** resu
                  int* status);
 void tune_ncrit(pb_ctx* ctx, const float* xyz_dev, long long n, int p, const int* cand, int ncand, int* best,
                 double* best_ms);
+void tune_fmm(pb_ctx* ctx, const float* xyz_dev, long long n, int p, const int* cand, int ncand, int* best,
+              int* best_nt, int* best_tile, double* best_ms);
 
 // A result object for the charges of one system (atoms as (x, y, z, q) on the device).
 pb_result* make_result(pb_ctx* ctx, pb_mesh* M, const double* atoms, const double* q, int64_t na, double eps_in,
@@ -194,6 +196,7 @@ int pb_set_option(pb_ctx* ctx, int option, int value) {
     if (option == PB_OPT_OVERLAP && (value == 0 || value == 1)) { ctx->overlap = value; return PB_OK; }
     if (option == PB_OPT_LEAF_NT && (value == 0 || value == 2 || value == 4)) { ctx->leaf_nt = value; return PB_OK; }
     if (option == PB_OPT_LEAF_PACKED && (value == 0 || value == 1)) { ctx->leaf_packed = value; return PB_OK; }
+    if (option == PB_OPT_M2L_TILE && (value == 0 || value == 1)) { ctx->m2l_tile = value; return PB_OK; }
     if (option == PB_OPT_RESTART && value >= 0 && value <= 2000) { ctx->restart = value; return PB_OK; }
     ctx->last_error = "pb_set_option: unknown option or value";
     return PB_EINVAL;
@@ -682,6 +685,20 @@ int pb_tune_ncrit(pb_ctx* ctx, const float* xyz, int64_t n, int p, const int32_t
     Staged s;
     s.in(xyz, (size_t)n * 3 * sizeof(float), ctx->stream);
     tune_ncrit(ctx, (const float*)s.dev, n, p, cand, ncand, best, best_ms);
+    check_device_error(ctx);
+    PB_API_END(ctx)
+}
+
+int pb_tune(pb_ctx* ctx, const float* xyz, int64_t n, int p, const int32_t* cand, int ncand, int* best,
+            int* best_nt, int* best_tile, double* best_ms) {
+    if (!ctx || !xyz || n < 1 || !cand || ncand < 1 || !best) return PB_EINVAL;
+    PB_API_BEGIN
+    PB_REQUIRE(p >= 2 && p <= 10, PB_EINVAL, "pb_tune: p must be in [2, 10]");
+    for (int c = 0; c < ncand; ++c) PB_REQUIRE(cand[c] >= 1, PB_EINVAL, "pb_tune: ncrit must be >= 1");
+    PB_CUDA(cudaSetDevice(ctx->device));
+    Staged s;
+    s.in(xyz, (size_t)n * 3 * sizeof(float), ctx->stream);
+    tune_fmm(ctx, (const float*)s.dev, n, p, cand, ncand, best, best_nt, best_tile, best_ms);
     check_device_error(ctx);
     PB_API_END(ctx)
 }

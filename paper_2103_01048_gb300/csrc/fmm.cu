@@ -1188,6 +1188,109 @@ __global__ void __launch_bounds__(128, 5) k_leaf_pair_x2(const int* __restrict__
     }
 }
 
+// P2M / P2L of the paired apply in packed FP32 (two sources per
+// instruction), for the FP32 path.  One 128-thread CTA per box: NP check
+// points per thread in slots = ceil(ne / NP) threads, G = 128 / slots groups
+// taking the source pairs g, g + G, ...  Coordinates relative to the box:
+// with cf = the centre rounded to FP32, a source at s enters as s - cf (an
+// FP32 difference of two nearby numbers, exact up to the rounding of the
+// difference itself) and a check point as alpha u + (c - cf), so that no
+// digit of the absolute coordinates is lost.  Windows of CAP sources (B's
+// own for P2M, its X-list boxes' for P2L), odd windows padded with a point
+// of zero weight 1e10 away.
+template <bool DL, int NP>
+__global__ void __launch_bounds__(128) k_p2check_pair_x2(int nbox, const int* __restrict__ boxes, int mode,
+                                                         const double4* __restrict__ center,
+                                                         const int* __restrict__ sb, const int* __restrict__ se,
+                                                         const int* __restrict__ X, const int* __restrict__ X_n,
+                                                         const float4* __restrict__ sq, const float4* __restrict__ sm,
+                                                         const float4* __restrict__ surf, int ne, int npad,
+                                                         float kappa, float* __restrict__ chkL,
+                                                         float* __restrict__ chkY) {
+    constexpr int CH = 128;
+    constexpr int CAP = 512;
+    constexpr int CP = CAP / 2;
+    static_assert(2 * NP * CH * 4 <= 4 * CP * 16, "reduction fits the staging arrays");
+    __shared__ ulonglong2 sA[CP], sB[CP], sC[CP], sD[CP];
+    float* s_red = reinterpret_cast<float*>(sA);     // [2][NP][CH], spans sA..sD
+    const int bi = blockIdx.x;
+    if (bi >= nbox) return;
+    const int b = boxes[bi];
+    const double4 c = center[b];
+    const float cfx = (float)c.x, cfy = (float)c.y, cfz = (float)c.z;
+    const float ox = (float)(c.x - (double)cfx), oy = (float)(c.y - (double)cfy), oz = (float)(c.z - (double)cfz);
+    const float alpha = float(mode == 0 ? kAlphaOuter : kAlphaInner) * (float)c.w;
+    const int slots = (ne + NP - 1) / NP;            // <= 128 (host)
+    const int G = CH / slots;
+    const int tloc = threadIdx.x % slots, g = threadIdx.x / slots;
+    const bool active = g < G;
+    const float kl2s = -kappa * float(kLog2E);
+    const f32x2 kap = x2_pack(kappa, kappa), kl2 = x2_pack(kl2s, kl2s), one = x2_pack(1.f, 1.f);
+    f32x2 PX[NP], PY[NP], PZ[NP], aL[NP], aY[NP];
+#pragma unroll
+    for (int m = 0; m < NP; ++m) {
+        const int i = tloc + m * slots;
+        const float4 u = (i < ne) ? surf[i] : make_float4(0, 0, 0, 0);
+        const float px = alpha * u.x + ox, py = alpha * u.y + oy, pz = alpha * u.z + oz;
+        PX[m] = x2_pack(px, px); PY[m] = x2_pack(py, py); PZ[m] = x2_pack(pz, pz);
+        aL[m] = aY[m] = 0ull;
+    }
+    const int nlist = (mode == 0) ? 1 : X_n[b];
+    const int* xl = X + (long long)b * kXCap;
+    int ui = 0, off = 0;
+    while (ui < nlist) {
+        int filled = 0;
+        while (filled < CAP && ui < nlist) {
+            const int a = (mode == 0) ? b : xl[ui];
+            const int j0 = sb[a] + off, len = se[a] - j0;
+            const int take = min(len, CAP - filled);
+            for (int e = threadIdx.x; e < take; e += CH) {
+                const float4 q = sq[j0 + e], m = sm[j0 + e];
+                put_src_x2(sA, sB, sC, sD, filled + e, q.x - cfx, q.y - cfy, q.z - cfz, q.w, m.x, m.y, m.z, m.w);
+            }
+            filled += take;
+            if (take == len) { ++ui; off = 0; } else off += take;
+        }
+        if ((filled & 1) && threadIdx.x == 0)
+            put_src_x2(sA, sB, sC, sD, filled, 1e10f, 1e10f, 1e10f, 0.f, 0.f, 0.f, 0.f, 0.f);
+        __syncthreads();
+        const int np = (filled + 1) >> 1;
+#pragma unroll 2
+        for (int k = g; active && k < np; k += G) {
+            const ulonglong2 A = sA[k], B = sB[k], C = DL ? sC[k] : make_ulonglong2(0, 0), D = sD[k];
+#pragma unroll
+            for (int m = 0; m < NP; ++m)
+                interact_x2<DL, false>(PX[m], PY[m], PZ[m], A, B, C, D, kap, kl2, one, aL[m], aY[m]);
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int m = 0; m < NP; ++m) {
+        s_red[m * CH + threadIdx.x] = x2_lo(aL[m]) + x2_hi(aL[m]);
+        s_red[(NP + m) * CH + threadIdx.x] = x2_lo(aY[m]) + x2_hi(aY[m]);
+    }
+    __syncthreads();
+    if (g == 0) {
+#pragma unroll
+        for (int m = 0; m < NP; ++m) {
+            const int i = tloc + m * slots;
+            float sL = 0.f, sY = 0.f;
+            for (int q = 0; q < G; ++q) {
+                sL += s_red[m * CH + tloc + q * slots];
+                sY += s_red[(NP + m) * CH + tloc + q * slots];
+            }
+            if (i < ne) {
+                chkL[(long long)b * npad + i] = sL * float(kInv4PiD);
+                chkY[(long long)b * npad + i] = sY * float(kInv4PiD);
+            }
+        }
+    }
+    for (int i = ne + threadIdx.x; i < npad; i += CH) {
+        chkL[(long long)b * npad + i] = 0.f;
+        chkY[(long long)b * npad + i] = 0.f;
+    }
+}
+
 // ---------------------------------------------------------------------------
 // host driver
 // ---------------------------------------------------------------------------
@@ -1524,6 +1627,33 @@ template <typename T, bool DL>
 static void launch_p2check_pair(cudaStream_t st, int nbox, const int* boxes, int mode, fmm_tree* Tr, Work<T>& WL,
                                 Work<T>& WY, const Operators& O, T kappa) {
     if (nbox <= 0) return;
+    // P2L (the X-list sources of a box, often several hundred) in packed
+    // groups; P2M (at most n_crit sources) keeps one thread per check point,
+    // which measured faster for so little work per box
+    if constexpr (std::is_same<T, float>::value) {
+        if (Tr->ctx->leaf_packed && mode == 1) {
+            // check points per thread: the choice that leaves the fewest lanes idle
+            // (p = 4: 4 -> 9 groups of 14 threads; p = 6: 4 -> 3 x 38; p = 8: 8 -> 3 x 37; p = 10: 4 -> 1 x 122)
+            int best = 0;
+            double best_eff = 0.0;
+            for (int np : {2, 4, 8}) {
+                const int slots = (O.ne + np - 1) / np;
+                if (slots > 128) continue;
+                const int warps = (128 / slots * slots + 31) / 32;
+                const double eff = double(O.ne) / (double(slots) * np) * (128 / slots) * slots / (32.0 * warps);
+                if (eff > best_eff + 1e-9) { best_eff = eff; best = np; }
+            }
+            if (best) {
+                auto k = best == 2 ? k_p2check_pair_x2<DL, 2>
+                                   : (best == 4 ? k_p2check_pair_x2<DL, 4> : k_p2check_pair_x2<DL, 8>);
+                k<<<nbox, 128, 0, st>>>(nbox, boxes, mode, Tr->center.p, Tr->sb.p, Tr->se.p, Tr->X.p, Tr->X_n.p,
+                                        WL.sq.p, WL.sm.p, (const float4*)O.surf_f.p, O.ne, O.npad, kappa,
+                                        WL.chk.p, WY.chk.p);
+                PB_CHECK_LAUNCH();
+                return;
+            }
+        }
+    }
     if (O.npad <= 256)
         k_p2check_pair<T, DL, 1><<<nbox, O.npad, 0, st>>>(nbox, boxes, mode, Tr->center.p, Tr->sb.p, Tr->se.p,
                                                           Tr->X.p, Tr->X_n.p, WL.sq.p, WL.sm.p,

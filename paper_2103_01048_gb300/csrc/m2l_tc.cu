@@ -1004,19 +1004,20 @@ bool m2l_tc_launch2(const fmm_tree* T, const Operators& O, const Operators* O2, 
     if (!tc_ok(O) || (O2 && (!tc_ok(*O2) || O2->npad != O.npad))) return false;
     if (T->m2l_pairs.nitems == 0) return true;
     const auto& P = T->m2l_pairs;
+    const bool pair = T->ctx->m2l_tile == 0;       // PB_OPT_M2L_TILE: 256-pair tiles on CTA pairs
     const bool single1 = O.m2l_tc_single, single2 = O2 && O2->m2l_tc_single;
     if (!single1 && !single2) {
         // both sets per (level, offset): one launch, grid z selects the set
         TcSets sets{{O.m2l_tc.p, O2 ? O2->m2l_tc.p : nullptr}, {Qu, Qu2}, {Qd, Qd2}, {0, 0}, 0, nullptr, O.ne};
-        return tc_dispatch(O.npad, P.items.p, P.nitems, P.tgt.p, P.src.p, sets, O2 ? 2 : 1, err, st, true);
+        return tc_dispatch(O.npad, P.items.p, P.nitems, P.tgt.p, P.src.p, sets, O2 ? 2 : 1, err, st, pair);
     }
     // a level-invariant set takes the per-offset items (every level of an
     // offset under one operator load); the other set its per-level items
     auto one = [&](const Operators& o, const float* X, float* Y) {
         TcSets sets{{o.m2l_tc.p, nullptr}, {X, nullptr}, {Y, nullptr}, {o.m2l_tc_single ? 1 : 0, 0}, 0, nullptr, o.ne};
         if (o.m2l_tc_single && P.nitems_off > 0)
-            return tc_dispatch(o.npad, P.items_off.p, P.nitems_off, P.tgt.p, P.src.p, sets, 1, err, st, true);
-        return tc_dispatch(o.npad, P.items.p, P.nitems, P.tgt.p, P.src.p, sets, 1, err, st, true);
+            return tc_dispatch(o.npad, P.items_off.p, P.nitems_off, P.tgt.p, P.src.p, sets, 1, err, st, pair);
+        return tc_dispatch(o.npad, P.items.p, P.nitems, P.tgt.p, P.src.p, sets, 1, err, st, pair);
     };
     if (!one(O, Qu, Qd)) return false;
     return O2 ? one(*O2, Qu2, Qd2) : true;

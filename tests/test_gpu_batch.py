@@ -108,3 +108,45 @@ def test_ncrit_autotuner(pb):
         assert best in (32, 64, 128, 256) and ms > 0
     finally:
         pb.pb_destroy(ctx)
+
+
+def test_tile_autotuner(pb):
+    """pb_tune picks ncrit and the leaf / M2L tile shapes on the paired apply,
+    leaves the winning tile options on the context, and an apply with them
+    still matches the FP64 direct sum."""
+    ctx = pb.pb_create(0, None)
+    try:
+        x, nrm = synthetic.bumpy_sphere_points(200000, seed=1)
+        X = torch.from_numpy(x).cuda()
+        best, nt, tile, ms = pb.pb_tune(ctx, X, 6, [64, 128])
+        assert best in (64, 128) and nt in (2, 4) and tile in (0, 1) and ms > 0
+        # the options on the context are the tuner's choice: setting them again is accepted
+        pb.pb_set_option(ctx, pb.PB_OPT_LEAF_NT, nt)
+        pb.pb_set_option(ctx, pb.PB_OPT_M2L_TILE, tile)
+        with pytest.raises(pb.PBError):
+            pb.pb_set_option(ctx, pb.PB_OPT_M2L_TILE, 2)
+        # parity of every tile combination on a 20k-point case
+        xs, ns = synthetic.bumpy_sphere_points(20000, seed=3)
+        q = synthetic.uniform_densities(len(xs), seed=4)
+        d = synthetic.uniform_densities(len(xs), seed=5)
+        from oracle import kernels as ok
+        refL = ok.direct_sum(ok.LAPLACE, 0.0, xs, q=q, dip=d, src_n=ns)
+        refY = ok.direct_sum(ok.YUKAWA, 0.125, xs, q=q, dip=d, src_n=ns)
+        h = pb.fmm_tree_build(ctx, torch.from_numpy(xs).cuda(), 64)
+        try:
+            for nt_ in (2, 4):
+                for tile_ in (0, 1):
+                    pb.pb_set_option(ctx, pb.PB_OPT_LEAF_NT, nt_)
+                    pb.pb_set_option(ctx, pb.PB_OPT_M2L_TILE, tile_)
+                    oL = torch.empty(len(xs), device="cuda")
+                    oY = torch.empty(len(xs), device="cuda")
+                    Q = torch.from_numpy(q).cuda()
+                    pb.fmm_apply_pair(ctx, h, 0.125, 6, oL, oY, q_lap=Q, q_yuk=Q, dip=torch.from_numpy(d).cuda(),
+                                      src_n=torch.from_numpy(ns).cuda())
+                    pb.pb_sync(ctx)
+                    for o, r in ((oL.cpu().numpy(), refL), (oY.cpu().numpy(), refY)):
+                        assert np.linalg.norm(o - r) / np.linalg.norm(r) < 1e-5
+        finally:
+            pb.fmm_tree_destroy(h)
+    finally:
+        pb.pb_destroy(ctx)
