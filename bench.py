@@ -77,6 +77,8 @@ def parse():
     ap.add_argument("--virus", action="store_true", help="virus-scale shell solve only (10M triangles, 1.6M atoms)")
     ap.add_argument("--virus-face", type=int, default=645, help="cube-sphere subdivision (12 n^2 triangles per wall)")
     ap.add_argument("--virus-atoms", type=int, default=1_600_000)
+    ap.add_argument("--virus-fp64", action="store_true",
+                    help="with --virus: also solve the shell with the all-FP64 GPU path and compare dG")
     ap.add_argument("--sweep", action="store_true", help="p x ncrit grid of the 4M-point apply")
     ap.add_argument("--profile", action="store_true",
                     help="bracket the timed steps with cudaProfilerStart/Stop (for ncu --profile-from-start off)")
@@ -273,6 +275,20 @@ def run_virus(args):
             "device_gb_in_use_after": (total - free1) / 1e9, "device_gb_in_use_before": (total - free0) / 1e9,
             "paper_context": "Zika (~10M elements, direct): GMRES 9470.9 s, 105 iterations, 109.7 GB, "
                              "dual 20-core Xeon Gold 6148"}
+    if args.virus_fp64:
+        # the same mesh, charges and tolerance on the all-FP64 path (FP64
+        # FMM, operators and GMRES): dG agreement of the mixed path at scale
+        t0 = time.perf_counter()
+        res64, st64 = pb.pb_solve(ctx, mesh, xyz, q, 4.0, 80.0, 0.125, 1e-4, 300, precision=pb.PB_FP64)
+        t64 = time.perf_counter() - t0
+        e64 = pb.pb_solvation_energy(ctx, res64)
+        it64, rr64, _ = pb.pb_result_get(res64)
+        line["fp64"] = {"status": int(st64), "iterations": it64, "residual": rr64, "dG_kcal_mol": e64,
+                        "solve_s": t64}
+        line["mixed_vs_fp64_rel_dG"] = abs(e - e64) / abs(e64)
+        line["speedup_mixed_over_fp64"] = t64 / t_solve
+        note(f"FP64 solve: {t64:.1f} s, rel dG {line['mixed_vs_fp64_rel_dG']:.2e}")
+        pb.pb_result_destroy(res64)
     print(json.dumps(line), flush=True)
     pb.pb_result_destroy(res)
     pb.pb_mesh_destroy(mesh)
