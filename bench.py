@@ -34,9 +34,8 @@ METRIC = "FMM apply points/s (4M-point surface, Laplace+Yukawa SL+DL, p=6)"
 UNIT = "points/s"
 # dram__bytes_read.sum + dram__bytes_write.sum of one leaf launch
 # (k_leaf_pair_x2) on this workload (4M points, p = 6, ncrit = 128), from one
-# ncu capture of the current kernel (544.6 + 27.2 MB); None once the kernel
-# changes
-LEAF_TRAFFIC_BYTES = 571.8e6
+# ncu capture of the current kernel; None once the kernel changes
+LEAF_TRAFFIC_BYTES = None
 # Arithmetic of one source-target pair in the paired (Laplace + Yukawa)
 # evaluation, FMA = 2 FLOPs, MUFU counted apart: SL+DL of both kernels
 # 30 FLOPs + 2 MUFU (rsqrt, ex2); monopole-only pairs of equivalent
@@ -55,6 +54,27 @@ def max_over_ranks(ms, dist):
     t = torch.tensor([ms], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def list_work(ex, ne, direct_w, direct_x):
+    """Pair counts of the leaf kernel when the adaptive-list pairs are taken
+    directly where that is less work (PB_OPT_LIST_DIRECT): W-list boxes of at
+    most ne // 2 sources, and the X list of a leaf of at most ne targets.
+    Returns (direct W pairs, direct X pairs, M2P targets left, P2L sources
+    left)."""
+    nchild = ex["nchild"]
+    ns = (ex["src_end"] - ex["src_begin"]).astype(np.int64)
+    nt = (ex["tgt_end"] - ex["tgt_begin"]).astype(np.int64)
+    if nt.sum() == 0:                        # targets = sources
+        nt = ns
+    woff, wids = ex["W"]
+    xoff, xids = ex["X"]
+    rw = np.repeat(np.arange(len(nchild)), np.diff(woff))
+    rx = np.repeat(np.arange(len(nchild)), np.diff(xoff))
+    dw = (ns[wids] <= ne // 2) if direct_w else np.zeros(len(wids), bool)
+    dx = ((nchild[rx] == 0) & (nt[rx] <= ne)) if direct_x else np.zeros(len(xids), bool)
+    return (int((nt[rw] * ns[wids])[dw].sum()), int((nt[rx] * ns[xids])[dx].sum()),
+            int(nt[rw][~dw].sum()), int(ns[xids][~dx].sum()))
 
 
 def job_throughput(world, n_points, ms):
@@ -94,6 +114,9 @@ def parse():
                     help="off-centre-charge sphere refinement study (512 ... 131,072 elements)")
     ap.add_argument("--leaf-nt", type=int, default=0, choices=[0, 2, 4],
                     help="targets per thread of the leaf kernel (PB_OPT_LEAF_NT; 0: the library's default)")
+    ap.add_argument("--list-direct", type=int, default=1, choices=[0, 1, 2, 3],
+                    help="PB_OPT_LIST_DIRECT: 0 every W/X pair through the equivalent surfaces, 1 small W boxes "
+                         "and small leaves' X lists directly, 2 X lists only, 3 W boxes only")
     ap.add_argument("--leaf-scalar", action="store_true",
                     help="scalar FP32 leaf kernel instead of the packed f32x2 one (PB_OPT_LEAF_PACKED 0)")
     return ap.parse_args()
@@ -572,6 +595,7 @@ def main():
     ctx = pb.pb_create(local, stream)
     pb.pb_set_option(ctx, pb.PB_OPT_LEAF_NT, args.leaf_nt)
     pb.pb_set_option(ctx, pb.PB_OPT_LEAF_PACKED, 0 if args.leaf_scalar else 1)
+    pb.pb_set_option(ctx, pb.PB_OPT_LIST_DIRECT, args.list_direct)
     X = torch.from_numpy(x).cuda()
     Nr = torch.from_numpy(nrm).cuda()
     Q = torch.from_numpy(q).cuda()
@@ -674,9 +698,13 @@ def main():
     leaf_ms = phases["leaf"][0] / args.steps
     p = args.p
     ne = 6 * (p - 1) ** 2 + 2
-    far = (info.m2p_targets + info.l2p_targets) * ne
-    leaf_flops = info.p2p_pairs * FLOPS_PAIR["pair_sd"] + far * FLOPS_PAIR["pair_m"]
-    leaf_mufu = (info.p2p_pairs + far) * MUFU_PAIR
+    on = not args.leaf_scalar and args.list_direct != 0 and ne <= 1024
+    w_dir, x_dir, m2p_left, p2l_left = list_work(pb.fmm_tree_export(ctx, tree), ne, on and args.list_direct != 2,
+                                                 on and args.list_direct != 3)
+    near = info.p2p_pairs + w_dir + x_dir
+    far = (m2p_left + info.l2p_targets) * ne
+    leaf_flops = near * FLOPS_PAIR["pair_sd"] + far * FLOPS_PAIR["pair_m"]
+    leaf_mufu = (near + far) * MUFU_PAIR
     fma_peak = peaks["fp32_fma_tflops"] * 1e12                        # FLOP/s, measured
     # one rsqrt and one ex2 per pair, on the same MUFU unit: the harmonic mean
     mufu_peak = 2.0 / (1.0 / peaks["mufu_rsqrt_tops"] + 1.0 / peaks["mufu_ex2_tops"]) * 1e12
@@ -865,6 +893,11 @@ def main():
                          "v_pairs": info.n_v, "p2p_pairs": info.p2p_pairs, "m2p_targets": info.m2p_targets,
                          "p2l_sources": info.p2l_sources, "l2p_targets": info.l2p_targets,
                          "build_ms": tree_build_ms,
+                         "direct_w_pairs": w_dir, "direct_x_pairs": x_dir, "m2p_targets_far": m2p_left,
+                         "p2l_sources_far": p2l_left,
+                         "direct_note": "pairs of W-list boxes of at most n_e/2 sources and of the X lists of leaves "
+                                        "of at most n_e targets are summed directly in the leaf kernel "
+                                        "(PB_OPT_LIST_DIRECT); m2p_targets_far / p2l_sources_far are the rest",
                          "build_note": "fmm_tree_build wall time with a device synchronisation, median of 3 "
                                        "after one warm-up build; not part of the timed step (tree cached)"},
                 "paired_step_points_per_s": value / 2,

@@ -170,7 +170,7 @@ PB_PH_LAUNCHES = 100
 
 
 PB_OPT_COUPLING, PB_OPT_DETERMINISTIC, PB_OPT_SINGULAR, PB_OPT_OVERLAP, PB_OPT_RESTART = 1, 2, 3, 4, 5
-PB_OPT_LEAF_NT, PB_OPT_LEAF_PACKED, PB_OPT_M2L_TILE = 6, 7, 8
+PB_OPT_LEAF_NT, PB_OPT_LEAF_PACKED, PB_OPT_M2L_TILE, PB_OPT_LIST_DIRECT = 6, 7, 8, 9
 
 
 def pb_set_option(ctx, option, value):

@@ -197,6 +197,7 @@ int pb_set_option(pb_ctx* ctx, int option, int value) {
     if (option == PB_OPT_LEAF_NT && (value == 0 || value == 2 || value == 4)) { ctx->leaf_nt = value; return PB_OK; }
     if (option == PB_OPT_LEAF_PACKED && (value == 0 || value == 1)) { ctx->leaf_packed = value; return PB_OK; }
     if (option == PB_OPT_M2L_TILE && (value == 0 || value == 1)) { ctx->m2l_tile = value; return PB_OK; }
+    if (option == PB_OPT_LIST_DIRECT && value >= 0 && value <= 3) { ctx->list_direct = value; return PB_OK; }
     if (option == PB_OPT_RESTART && value >= 0 && value <= 2000) { ctx->restart = value; return PB_OK; }
     ctx->last_error = "pb_set_option: unknown option or value";
     return PB_EINVAL;

@@ -140,6 +140,7 @@ struct pb_ctx {
     int leaf_nt = 0;           // targets per thread of the paired leaf kernel (0: by precision)
     int leaf_packed = 1;       // FP32 paired leaf kernel with packed (f32x2) arithmetic
     int m2l_tile = 0;          // 0: M = 256 (CTA pairs) where allowed; 1: M = 128 (one CTA per part)
+    int list_direct = 1;       // small W boxes and small leaves' X lists evaluated directly (packed path)
     int restart = 0;           // GMRES restart length of the batched solves (0: none)
     // second stream (and fork / join events) for the near field of the paired
     // apply; null: everything on `stream`

@@ -9,6 +9,7 @@
 // on the arithmetic type: float (mixed path) and double (all-FP64 path).
 #include "fmm.cuh"
 #include <algorithm>
+#include <climits>
 #include <memory>
 #include <type_traits>
 
@@ -1025,15 +1026,22 @@ __global__ void __launch_bounds__(128, 5) k_leaf_pair_x2(const int* __restrict__
                                                       const float* __restrict__ QdL, const float* __restrict__ QuY,
                                                       const float* __restrict__ QdY, const float4* __restrict__ surf,
                                                       int ne, int npad, float kappa, float* __restrict__ potL_out,
-                                                      float* __restrict__ potY_out) {
+                                                      float* __restrict__ potY_out, const int* __restrict__ Xl,
+                                                      const int* __restrict__ Xn, int thrW, int thrX) {
     constexpr int CH = 128;
     constexpr int CAP = 1024;                    // points per window (512 pairs, 32 KB)
     constexpr int CP = CAP / 2;
     static_assert(2 * NT * CH * 4 <= CP * 16, "reduction fits one staging array");
     __shared__ ulonglong2 sA[CP], sB[CP], sC[CP], sD[CP];
     __shared__ int s_self;
-    __shared__ float4 s_box[CH];                 // far window: box centre relative to the leaf's, radius
-    __shared__ int s_boxid[CH];                  // box id (W list) or -1 - id (own downward)
+    constexpr int VC = 256;                      // near-list entries resolved per chunk
+    constexpr int FC = CH;                       // far candidates resolved per chunk
+    constexpr int kSkip = INT_MIN;               // far candidate evaluated directly instead
+    __shared__ int s_vb[VC], s_vn[VC];           // near entry: first source, sources taken (0: none)
+    __shared__ float4 s_fb[FC];                  // far candidate: centre - the leaf's centre, radius
+    __shared__ int s_fc[FC];                     // box id (W list), -1 - id (own downward) or kSkip
+    __shared__ int s_sel[CH];                    // far window: the candidates it takes
+    __shared__ int s_nb, s_fcur;
     float* s_red = reinterpret_cast<float*>(sA);
     const int li = blockIdx.x;
     if (li >= nleaf) return;
@@ -1047,7 +1055,11 @@ __global__ void __launch_bounds__(128, 5) k_leaf_pair_x2(const int* __restrict__
     const int nu = U_off[b + 1] - U_off[b];
     const int nw = W_off[b + 1] - W_off[b];
     const int nsrcbox = nw + (level[b] >= 2 ? 1 : 0);
-    const int nf = nsrcbox * ne;
+    // near stream: U list, then the W boxes of at most thrW sources, then the
+    // X list when the leaf has at most thrX targets (thr < 0: none)
+    const int nxd = (thrX >= 0 && t1 - t0 <= thrX) ? Xn[b] : 0;
+    const int nvirt = nu + (thrW >= 0 ? nw : 0) + nxd;
+    const int* xl = Xl + (long long)b * kXCap;
     const double4 cb = center[b];
     const float kl2s = -kappa * float(kLog2E);
     const f32x2 kap = x2_pack(kappa, kappa), kl2 = x2_pack(kl2s, kl2s), one = x2_pack(1.f, 1.f);
@@ -1058,7 +1070,52 @@ __global__ void __launch_bounds__(128, 5) k_leaf_pair_x2(const int* __restrict__
     __syncthreads();
     const int selfpos = s_self;
     const int nself = selfpos >= 0 ? se[b] - sb[b] : 0;
+    // list entries resolved in parallel into shared memory (one round of
+    // dependent loads per chunk instead of one per box in the cursor loops)
+    auto load_near = [&](int v0) {
+        for (int v = v0 + threadIdx.x; v < min(nvirt, v0 + VC); v += CH) {
+            int a;
+            bool inc = true;
+            if (v < nu) {
+                a = ul[u_at(v, selfpos)];
+            } else if (thrW >= 0 && v < nu + nw) {
+                a = W_ids[W_off[b] + (v - nu)];
+                inc = se[a] - sb[a] <= thrW;
+            } else {
+                a = xl[v - nu - (thrW >= 0 ? nw : 0)];
+            }
+            s_vb[v - v0] = sb[a];
+            s_vn[v - v0] = inc ? se[a] - sb[a] : 0;
+        }
+    };
+    auto load_far = [&](int f0) {
+        for (int i = f0 + threadIdx.x; i < min(nsrcbox, f0 + FC); i += CH) {
+            int code = -1 - b;
+            if (i < nw) {
+                const int a = W_ids[W_off[b] + i];
+                code = (thrW < 0 || se[a] - sb[a] > thrW) ? a : kSkip;
+            }
+            if (code != kSkip) {
+                const bool isw = code >= 0;
+                const double4 ca = center[isw ? code : -1 - code];
+                s_fb[i - f0] = make_float4((float)(ca.x - cb.x), (float)(ca.y - cb.y), (float)(ca.z - cb.z),
+                                           float(isw ? kAlphaInner : kAlphaOuter) * (float)ca.w);
+            }
+            s_fc[i - f0] = code;
+        }
+    };
+    int vbase = 0, fbase = 0;
+    load_near(0);
+    load_far(0);
+    __syncthreads();
     for (int tc = t0; tc < t1; tc += NT * slots) {
+        if (vbase != 0 || fbase != 0) {          // a later target chunk: the first list chunks again
+            __syncthreads();
+            vbase = fbase = 0;
+            load_near(0);
+            load_far(0);
+            __syncthreads();
+        }
         int ti[NT];
         bool vt[NT];
         f32x2 X[NT], Y[NT], Z[NT], pL[NT], pY[NT];
@@ -1074,12 +1131,17 @@ __global__ void __launch_bounds__(128, 5) k_leaf_pair_x2(const int* __restrict__
         }
         if (PART != 2) {
             int vi = 0, off = 0;
-            while (vi < nu) {
+            while (vi < nvirt) {
                 const int self_left = (selfpos >= 0 && vi == 0) ? nself - off : 0;
                 int filled = 0;
-                while (filled < CAP && vi < nu) {
-                    const int a = ul[u_at(vi, selfpos)];
-                    const int j0 = sb[a] + off, len = se[a] - j0;
+                while (filled < CAP && vi < nvirt) {
+                    if (vi >= vbase + VC) {      // next chunk of resolved entries
+                        __syncthreads();
+                        vbase += VC;
+                        load_near(vbase);
+                        __syncthreads();
+                    }
+                    const int j0 = s_vb[vi - vbase] + off, len = s_vn[vi - vbase] - off;
                     const int take = min(len, CAP - filled);
                     for (int e = threadIdx.x; e < take; e += CH)
                         copy_src_x2<DL>(sA, sB, sC, sD, filled + e, sq, sm, j0 + e);
@@ -1109,7 +1171,7 @@ __global__ void __launch_bounds__(128, 5) k_leaf_pair_x2(const int* __restrict__
                 __syncthreads();
             }
         }
-        if (PART != 1 && nf > 0) {
+        if (PART != 1 && nsrcbox > 0) {
 #pragma unroll
             for (int u = 0; u < NT; ++u) {
                 const float rx = (float)((double)xs[u] - cb.x), ry = (float)((double)ys[u] - cb.y),
@@ -1117,22 +1179,45 @@ __global__ void __launch_bounds__(128, 5) k_leaf_pair_x2(const int* __restrict__
                 X[u] = x2_pack(rx, rx); Y[u] = x2_pack(ry, ry); Z[u] = x2_pack(rz, rz);
             }
             const int nbw = CAP / ne;                    // whole boxes per window (ne <= CAP: host)
-            for (int i0 = 0; i0 < nsrcbox; i0 += nbw) {
-                const int nb = min(nbw, nsrcbox - i0), n = nb * ne;
-                if (threadIdx.x < nb) {
-                    const int i = i0 + threadIdx.x;
-                    const bool isw = i < nw;
-                    const int a = isw ? W_ids[W_off[b] + i] : b;
-                    const double4 ca = center[a];
-                    s_box[threadIdx.x] = make_float4((float)(ca.x - cb.x), (float)(ca.y - cb.y),
-                                                     (float)(ca.z - cb.z),
-                                                     float(isw ? kAlphaInner : kAlphaOuter) * (float)ca.w);
-                    s_boxid[threadIdx.x] = isw ? a : -1 - a;
+            int fcur = 0;                                // next far candidate: W list, then the leaf's own
+            while (fcur < nsrcbox) {
+                if (fcur >= fbase + FC) {                // next chunk of resolved candidates
+                    __syncthreads();
+                    fbase += FC;
+                    load_far(fbase);
+                    __syncthreads();
+                }
+                // warp 0 picks the window's boxes: up to nbw candidates of this
+                // chunk that are not evaluated directly
+                if (threadIdx.x < 32) {
+                    const int lane = threadIdx.x;
+                    const int cend = min(nsrcbox, fbase + FC);
+                    int nb = 0, c = fcur;
+                    while (nb < nbw && c < cend) {
+                        const int i = c + lane;
+                        const bool ok = i < cend && s_fc[i - fbase] != kSkip;
+                        const unsigned m = __ballot_sync(0xffffffffu, ok);
+                        const int rank = __popc(m & ((1u << lane) - 1u));
+                        const int want = nbw - nb, have = __popc(m);
+                        if (ok && rank < want) s_sel[nb + rank] = i - fbase;
+                        if (have <= want) {
+                            nb += have;
+                            c = min(c + 32, cend);
+                        } else {
+                            const unsigned last = __ballot_sync(0xffffffffu, ok && rank == want - 1);
+                            c += __ffs(last);            // one past the last box taken
+                            nb += want;
+                        }
+                    }
+                    if (lane == 0) { s_nb = nb; s_fcur = c; }
                 }
                 __syncthreads();
+                const int nb = s_nb, n = nb * ne;
+                fcur = s_fcur;
                 for (int i = 0; i < nb; ++i) {
-                    const float4 bx = s_box[i];
-                    const int code = s_boxid[i];
+                    const int slot = s_sel[i];
+                    const float4 bx = s_fb[slot];
+                    const int code = s_fc[slot];
                     const bool isw = code >= 0;
                     const size_t base = (size_t)(isw ? code : -1 - code) * npad;
                     const float* QL = isw ? QuL : QdL;
@@ -1206,7 +1291,9 @@ __global__ void __launch_bounds__(128) k_p2check_pair_x2(int nbox, const int* __
                                                          const float4* __restrict__ sq, const float4* __restrict__ sm,
                                                          const float4* __restrict__ surf, int ne, int npad,
                                                          float kappa, float* __restrict__ chkL,
-                                                         float* __restrict__ chkY) {
+                                                         float* __restrict__ chkY, const int* __restrict__ nchild,
+                                                         const int* __restrict__ tb, const int* __restrict__ te,
+                                                         int thrX) {
     constexpr int CH = 128;
     constexpr int CAP = 512;
     constexpr int CP = CAP / 2;
@@ -1216,6 +1303,14 @@ __global__ void __launch_bounds__(128) k_p2check_pair_x2(int nbox, const int* __
     const int bi = blockIdx.x;
     if (bi >= nbox) return;
     const int b = boxes[bi];
+    if (mode == 1 && thrX >= 0 && nchild[b] == 0 && te[b] - tb[b] <= thrX) {
+        // a leaf of at most thrX targets takes its X list directly in the leaf kernel
+        for (int i = threadIdx.x; i < npad; i += CH) {
+            chkL[(long long)b * npad + i] = 0.f;
+            chkY[(long long)b * npad + i] = 0.f;
+        }
+        return;
+    }
     const double4 c = center[b];
     const float cfx = (float)c.x, cfy = (float)c.y, cfz = (float)c.z;
     const float ox = (float)(c.x - (double)cfx), oy = (float)(c.y - (double)cfy), oz = (float)(c.z - (double)cfz);
@@ -1625,7 +1720,7 @@ static void apply_t(fmm_tree* Tr, const Operators& O, double kappa_d, const In* 
 // ---- paired apply: Laplace (operators OL) and Yukawa (OY) in one traversal
 template <typename T, bool DL>
 static void launch_p2check_pair(cudaStream_t st, int nbox, const int* boxes, int mode, fmm_tree* Tr, Work<T>& WL,
-                                Work<T>& WY, const Operators& O, T kappa) {
+                                Work<T>& WY, const Operators& O, T kappa, int thrX = -1) {
     if (nbox <= 0) return;
     // P2L (the X-list sources of a box, often several hundred) in packed
     // groups; P2M (at most n_crit sources) keeps one thread per check point,
@@ -1648,12 +1743,14 @@ static void launch_p2check_pair(cudaStream_t st, int nbox, const int* boxes, int
                                    : (best == 4 ? k_p2check_pair_x2<DL, 4> : k_p2check_pair_x2<DL, 8>);
                 k<<<nbox, 128, 0, st>>>(nbox, boxes, mode, Tr->center.p, Tr->sb.p, Tr->se.p, Tr->X.p, Tr->X_n.p,
                                         WL.sq.p, WL.sm.p, (const float4*)O.surf_f.p, O.ne, O.npad, kappa,
-                                        WL.chk.p, WY.chk.p);
+                                        WL.chk.p, WY.chk.p, Tr->nchild.p, Tr->same ? Tr->sb.p : Tr->tb.p,
+                                        Tr->same ? Tr->se.p : Tr->te.p, thrX);
                 PB_CHECK_LAUNCH();
                 return;
             }
         }
     }
+    PB_REQUIRE(thrX < 0, PB_EINVAL, "direct X-list evaluation needs the packed check-potential kernel");
     if (O.npad <= 256)
         k_p2check_pair<T, DL, 1><<<nbox, O.npad, 0, st>>>(nbox, boxes, mode, Tr->center.p, Tr->sb.p, Tr->se.p,
                                                           Tr->X.p, Tr->X_n.p, WL.sq.p, WL.sm.p,
@@ -1668,7 +1765,8 @@ static void launch_p2check_pair(cudaStream_t st, int nbox, const int* boxes, int
 }
 
 template <typename T, bool DL, bool DN, int PART>
-static void launch_leaf_pair(cudaStream_t st, fmm_tree* Tr, Work<T>& WL, Work<T>& WY, const Operators& O, T kappa) {
+static void launch_leaf_pair(cudaStream_t st, fmm_tree* Tr, Work<T>& WL, Work<T>& WY, const Operators& O, T kappa,
+                             int thrW = -1, int thrX = -1) {
     if (Tr->n_tleaf <= 0) return;
     const float4* tpos = Tr->same ? Tr->pos_s.p : Tr->pos_t.p;
     const int* tb = Tr->same ? Tr->sb.p : Tr->tb.p;
@@ -1681,11 +1779,13 @@ static void launch_leaf_pair(cudaStream_t st, fmm_tree* Tr, Work<T>& WL, Work<T>
             k<<<Tr->n_tleaf, 128, 0, st>>>(Tr->leaf_ids.p, Tr->n_tleaf, tb, te, Tr->sb.p, Tr->se.p, Tr->U_off.p,
                                            Tr->U_ids.p, Tr->W_off.p, Tr->W_ids.p, Tr->level.p, Tr->center.p, tpos,
                                            WL.sq.p, WL.sm.p, WL.Qu.p, WL.Qd.p, WY.Qu.p, WY.Qd.p,
-                                           (const float4*)O.surf_f.p, O.ne, O.npad, kappa, WL.pot.p, WY.pot.p);
+                                           (const float4*)O.surf_f.p, O.ne, O.npad, kappa, WL.pot.p, WY.pot.p,
+                                           Tr->X.p, Tr->X_n.p, thrW, thrX);
             PB_CHECK_LAUNCH();
             return;
         }
     }
+    PB_REQUIRE(thrW < 0 && thrX < 0, PB_EINVAL, "direct W/X-list evaluation needs the packed leaf kernel");
     const int NT = nt_opt ? nt_opt : (sizeof(T) == 4 ? 4 : 2);
     auto k = NT == 4 ? k_leaf_pair<T, DL, DN, 4, PART> : k_leaf_pair<T, DL, DN, 2, PART>;
     k<<<Tr->n_tleaf, 128, 0, st>>>(
@@ -1693,6 +1793,19 @@ static void launch_leaf_pair(cudaStream_t st, fmm_tree* Tr, Work<T>& WL, Work<T>
         Tr->level.p, Tr->center.p, tpos, WL.tn.p, WL.sq.p, WL.sm.p, WL.Qu.p, WL.Qd.p, WY.Qu.p, WY.Qd.p,
         (const float4*)O.surf_f.p, O.ne, O.npad, kappa, WL.pot.p, WY.pot.p, WL.dn.p, WY.dn.p);
     PB_CHECK_LAUNCH();
+}
+
+// Adaptive-list pairs taken directly (exact) where that is less work than the
+// equivalent surfaces (PB_OPT_LIST_DIRECT, FP32 packed kernels): a W-list box
+// of at most n_e / 2 sources (M2P costs n_e monopole terms per target, a
+// direct pair with a dipole about twice one of them), and the X list of a
+// leaf of at most n_e targets (P2L would put the same sources on n_e check
+// points).  Returns the two thresholds, -1 when off.
+static void list_direct(const fmm_tree* Tr, const Operators& O, bool fp32, bool DN, int& thrW, int& thrX) {
+    const int mode = Tr->ctx->list_direct;         // 0 off, 1 W and X, 2 X only, 3 W only
+    const bool on = fp32 && !DN && Tr->ctx->leaf_packed && mode != 0 && O.ne <= 1024;
+    thrW = on && mode != 2 ? O.ne / 2 : -1;
+    thrX = on && mode != 3 ? O.ne : -1;
 }
 
 template <typename T, typename In>
@@ -1704,6 +1817,8 @@ static void apply_pair_t(fmm_tree* Tr, const Operators& OL, const Operators& OY,
     const T kappa = (T)kappa_d;
     const bool DL = dip != nullptr, DN = dnL != nullptr;
     if (DL && DN) throw Error(PB_EINVAL, "double layer with target-normal derivative is not provided");
+    int thrW, thrX;
+    list_direct(Tr, OL, std::is_same<T, float>::value, DN, thrW, thrX);
     Work<T> WL, WY;
     WL.sq.alloc(ns, st);
     WL.sm.alloc(ns, st);
@@ -1730,9 +1845,9 @@ static void apply_pair_t(fmm_tree* Tr, const Operators& OL, const Operators& OY,
         PB_CUDA(cudaStreamWaitEvent(ctx->aux, ctx->ev_fork, 0));
         {
             PhaseTimer phn(ctx, PB_PH_LEAF, ctx->aux);
-            if (DL) launch_leaf_pair<T, true, false, 1>(ctx->aux, Tr, WL, WY, OL, kappa);
-            else if (DN) launch_leaf_pair<T, false, true, 1>(ctx->aux, Tr, WL, WY, OL, kappa);
-            else launch_leaf_pair<T, false, false, 1>(ctx->aux, Tr, WL, WY, OL, kappa);
+            if (DL) launch_leaf_pair<T, true, false, 1>(ctx->aux, Tr, WL, WY, OL, kappa, thrW, thrX);
+            else if (DN) launch_leaf_pair<T, false, true, 1>(ctx->aux, Tr, WL, WY, OL, kappa, thrW, thrX);
+            else launch_leaf_pair<T, false, false, 1>(ctx->aux, Tr, WL, WY, OL, kappa, thrW, thrX);
         }
         PB_CUDA(cudaEventRecord(ctx->ev_join, ctx->aux));
     }
@@ -1745,8 +1860,8 @@ static void apply_pair_t(fmm_tree* Tr, const Operators& OL, const Operators& OY,
     far_pair_m2m(Tr, OL, OY, WL, WY);
     ph.reset(); ph = std::make_unique<PhaseTimer>(ctx, PB_PH_P2L);
     if (Tr->n_xbox > 0) {
-        if (DL) launch_p2check_pair<T, true>(st, Tr->n_xbox, Tr->xbox_ids.p, 1, Tr, WL, WY, OL, kappa);
-        else launch_p2check_pair<T, false>(st, Tr->n_xbox, Tr->xbox_ids.p, 1, Tr, WL, WY, OL, kappa);
+        if (DL) launch_p2check_pair<T, true>(st, Tr->n_xbox, Tr->xbox_ids.p, 1, Tr, WL, WY, OL, kappa, thrX);
+        else launch_p2check_pair<T, false>(st, Tr->n_xbox, Tr->xbox_ids.p, 1, Tr, WL, WY, OL, kappa, thrX);
         far_pair_c2e(Tr, OL, OY, WL, WY, false);
     }
     ph.reset(); ph = std::make_unique<PhaseTimer>(ctx, PB_PH_M2L);
@@ -1756,13 +1871,13 @@ static void apply_pair_t(fmm_tree* Tr, const Operators& OL, const Operators& OY,
     if (fork) PB_CUDA(cudaStreamWaitEvent(st, ctx->ev_join, 0));
     ph.reset(); ph = std::make_unique<PhaseTimer>(ctx, PB_PH_LEAF);
     if (fork) {
-        if (DL) launch_leaf_pair<T, true, false, 2>(st, Tr, WL, WY, OL, kappa);
-        else if (DN) launch_leaf_pair<T, false, true, 2>(st, Tr, WL, WY, OL, kappa);
-        else launch_leaf_pair<T, false, false, 2>(st, Tr, WL, WY, OL, kappa);
+        if (DL) launch_leaf_pair<T, true, false, 2>(st, Tr, WL, WY, OL, kappa, thrW, thrX);
+        else if (DN) launch_leaf_pair<T, false, true, 2>(st, Tr, WL, WY, OL, kappa, thrW, thrX);
+        else launch_leaf_pair<T, false, false, 2>(st, Tr, WL, WY, OL, kappa, thrW, thrX);
     } else {
-        if (DL) launch_leaf_pair<T, true, false, 0>(st, Tr, WL, WY, OL, kappa);
-        else if (DN) launch_leaf_pair<T, false, true, 0>(st, Tr, WL, WY, OL, kappa);
-        else launch_leaf_pair<T, false, false, 0>(st, Tr, WL, WY, OL, kappa);
+        if (DL) launch_leaf_pair<T, true, false, 0>(st, Tr, WL, WY, OL, kappa, thrW, thrX);
+        else if (DN) launch_leaf_pair<T, false, true, 0>(st, Tr, WL, WY, OL, kappa, thrW, thrX);
+        else launch_leaf_pair<T, false, false, 0>(st, Tr, WL, WY, OL, kappa, thrW, thrX);
     }
     ph.reset(); ph = std::make_unique<PhaseTimer>(ctx, PB_PH_SCATTER);
     const int* pt = Tr->same ? Tr->perm_s.p : Tr->perm_t.p;

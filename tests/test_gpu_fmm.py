@@ -304,9 +304,20 @@ def test_pair_vs_direct(pb, ctx, case20k, kappa):
     assert rel_l2(oY, direct_sum(YUKAWA, kappa, x, q=qY, dip=d, src_n=nrm)) < TOL
 
 
+def pair_surfaces_only(pb, ctx, *args, **kw):
+    """run_pair with every W/X pair through the equivalent surfaces, as the
+    single-kernel apply takes them (the same approximation, so the two agree
+    to rounding)."""
+    pb.pb_set_option(ctx, pb.PB_OPT_LIST_DIRECT, 0)
+    try:
+        return run_pair(pb, ctx, *args, **kw)
+    finally:
+        pb.pb_set_option(ctx, pb.PB_OPT_LIST_DIRECT, 1)
+
+
 def test_pair_equals_two_applies(pb, ctx, case20k):
     x, nrm, q, d, h = case20k
-    oL, oY = run_pair(pb, ctx, h, 0.125, 6, qL=q, qY=q, d=d, sn=nrm, nt=len(x))
+    oL, oY = pair_surfaces_only(pb, ctx, h, 0.125, 6, qL=q, qY=q, d=d, sn=nrm, nt=len(x))
     sL, _ = run_apply(pb, ctx, h, LAPLACE, 0.0, 6, q=q, d=d, sn=nrm, nt=len(x))
     sY, _ = run_apply(pb, ctx, h, YUKAWA, 0.125, 6, q=q, d=d, sn=nrm, nt=len(x))
     assert rel_l2(oL, sL) < 1e-6 and rel_l2(oY, sY) < 1e-6
@@ -439,7 +450,7 @@ def test_pair_equals_two_applies_low_order(pb, ctx, case20k, p):
     operator sizes (npad 32 and 64: p = 3, 4, 5) give the single-kernel
     results."""
     x, nrm, q, d, h = case20k
-    oL, oY = run_pair(pb, ctx, h, 0.125, p, qL=q, qY=q, d=d, sn=nrm, nt=len(x))
+    oL, oY = pair_surfaces_only(pb, ctx, h, 0.125, p, qL=q, qY=q, d=d, sn=nrm, nt=len(x))
     sL, _ = run_apply(pb, ctx, h, LAPLACE, 0.0, p, q=q, d=d, sn=nrm, nt=len(x))
     sY, _ = run_apply(pb, ctx, h, YUKAWA, 0.125, p, q=q, d=d, sn=nrm, nt=len(x))
     assert rel_l2(oL, sL) < 1e-6 and rel_l2(oY, sY) < 1e-6
@@ -585,3 +596,31 @@ def test_operators_shared_between_trees(pb, ctx, case20k, ref20k):
         refL = direct_sum(LAPLACE, 0.0, pts, q=q, dip=d, src_n=nrm)
         refY = direct_sum(YUKAWA, 0.0625, pts, q=q, dip=d, src_n=nrm)
         assert rel_l2(o[0], refL) < TOL and rel_l2(o[1], refY) < TOL
+
+
+@pytest.mark.parametrize("direct", [1, 0])
+def test_pair_list_direct_vs_direct_sum(pb, ctx, direct):
+    """W- and X-list pairs taken directly (PB_OPT_LIST_DIRECT 1) or through
+    the equivalent surfaces (0): both within 1e-5 of the FP64 direct sum on
+    an adaptive tree with many W/X entries (a dense cluster inside a sparse
+    cloud, ncrit 24), at p = 8."""
+    rng = np.random.default_rng(41)
+    x = np.concatenate([rng.normal(0.2, 0.02, (6000, 3)), rng.uniform(-1, 1, (6000, 3))]).astype(np.float32)
+    nrm = rng.standard_normal((len(x), 3))
+    nrm = (nrm / np.linalg.norm(nrm, axis=1)[:, None]).astype(np.float32)
+    q = synthetic.uniform_densities(len(x), seed=42)
+    d = synthetic.uniform_densities(len(x), seed=43)
+    qY = synthetic.uniform_densities(len(x), seed=44)
+    h = pb.fmm_tree_build(ctx, dev(x), 24)
+    try:
+        ex = pb.fmm_tree_export(ctx, h)
+        assert ex["W"][0][-1] > 0 and ex["X"][0][-1] > 0
+        pb.pb_set_option(ctx, pb.PB_OPT_LIST_DIRECT, direct)
+        try:
+            oL, oY = run_pair(pb, ctx, h, 0.3, 8, qL=q, qY=qY, d=d, sn=nrm, nt=len(x))
+        finally:
+            pb.pb_set_option(ctx, pb.PB_OPT_LIST_DIRECT, 1)
+    finally:
+        pb.fmm_tree_destroy(h)
+    assert rel_l2(oL, direct_sum(LAPLACE, 0.0, x, q=q, dip=d, src_n=nrm)) < TOL
+    assert rel_l2(oY, direct_sum(YUKAWA, 0.3, x, q=qY, dip=d, src_n=nrm)) < TOL
