@@ -184,7 +184,8 @@ __global__ void __launch_bounds__(256) k_p2check(int nbox, const int* __restrict
                                                  const typename V4<T>::type* __restrict__ sq,
                                                  const typename V4<T>::type* __restrict__ sm,
                                                  const float4* __restrict__ surf, int ne, int npad, T kappa,
-                                                 T* __restrict__ chk) {
+                                                 T* __restrict__ chk, const int* __restrict__ nchild,
+                                                 const int* __restrict__ tb, const int* __restrict__ te, int thrX) {
     // one (MAXP = 1) or two check points per thread; blockDim.x <= 256
     using V = typename V4<T>::type;
     __shared__ V s_q[256];
@@ -193,6 +194,11 @@ __global__ void __launch_bounds__(256) k_p2check(int nbox, const int* __restrict
     int bi = blockIdx.x;
     if (bi >= nbox) return;
     int b = boxes[bi];
+    if (mode == 1 && thrX >= 0 && nchild[b] == 0 && te[b] - tb[b] <= thrX) {
+        // a leaf of at most thrX targets takes its X list directly in the leaf kernel
+        for (int i = threadIdx.x; i < npad; i += CH) chk[(long long)b * npad + i] = T(0);
+        return;
+    }
     double4 c = center[b];
     T alpha = T(mode == 0 ? kAlphaOuter : kAlphaInner) * (T)c.w;
     T px[MAXP], py[MAXP], pz[MAXP], acc[MAXP];
@@ -937,24 +943,35 @@ __device__ __forceinline__ f32x2 x2_exp2(f32x2 a) { return x2_pack(exp2_t<float>
 // interact_pair for one target (coordinates in both halves) and two sources
 // (one per half), the same grouping of the arithmetic.  Source pair layout:
 // A = {x, y}, B = {z, qL}, C = {mx, my}, D = {mz, qY}, each a pair.
-template <bool DL, bool GUARD>
+// KM: 3 both kernels; 1 Laplace only (density qL, sum pL); 2 Yukawa only
+// (density in the qL slot, sum pY).
+template <bool DL, bool GUARD, int KM = 3>
 __device__ __forceinline__ void interact_x2(f32x2 X, f32x2 Y, f32x2 Z, const ulonglong2& A, const ulonglong2& B,
                                             const ulonglong2& C, const ulonglong2& D, f32x2 kap, f32x2 kl2,
                                             f32x2 one, f32x2& pL, f32x2& pY) {
     const f32x2 dx = x2_sub(X, A.x), dy = x2_sub(Y, A.y), dz = x2_sub(Z, B.x);
     const f32x2 r2 = x2_fma(dx, dx, x2_fma(dy, dy, x2_mul(dz, dz)));
     const f32x2 rinv = x2_rsqrt<GUARD>(r2);
+    if (KM == 1) {
+        if (DL) {
+            const f32x2 w = x2_mul(x2_fma(dx, C.x, x2_fma(dy, C.y, x2_mul(dz, D.x))), x2_mul(rinv, rinv));
+            pL = x2_fma(rinv, x2_add(w, B.y), pL);
+        } else {
+            pL = x2_fma(rinv, B.y, pL);
+        }
+        return;
+    }
     const f32x2 r = x2_mul(r2, rinv);
     const f32x2 er = x2_mul(x2_exp2(x2_mul(kl2, r)), rinv);        // e^{-kr} / r
     if (DL) {
         const f32x2 rinv2 = x2_mul(rinv, rinv);
         const f32x2 u = x2_fma(kap, r, one);
         const f32x2 w = x2_mul(x2_fma(dx, C.x, x2_fma(dy, C.y, x2_mul(dz, D.x))), rinv2);
-        pL = x2_fma(rinv, x2_add(w, B.y), pL);
-        pY = x2_fma(er, x2_fma(w, u, D.y), pY);
+        if (KM == 3) pL = x2_fma(rinv, x2_add(w, B.y), pL);
+        pY = x2_fma(er, x2_fma(w, u, KM == 3 ? D.y : B.y), pY);
     } else {
-        pL = x2_fma(rinv, B.y, pL);
-        pY = x2_fma(er, D.y, pY);
+        if (KM == 3) pL = x2_fma(rinv, B.y, pL);
+        pY = x2_fma(er, KM == 3 ? D.y : B.y, pY);
     }
 }
 
@@ -965,8 +982,8 @@ __device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
 
 // Copies source j (sq = {x, y, z, qL}, sm = {mx, my, mz, qY}) into half
 // e & 1 of pair slot e >> 1 of the packed window with 4-byte asynchronous
-// copies (the dipole only if DL).
-template <bool DL>
+// copies (the dipole only if DL, the Yukawa monopole only if QY).
+template <bool DL, bool QY = true>
 __device__ __forceinline__ void copy_src_x2(ulonglong2* sA, ulonglong2* sB, ulonglong2* sC, ulonglong2* sD, int e,
                                             const float4* __restrict__ sq, const float4* __restrict__ sm,
                                             int j) {
@@ -986,7 +1003,7 @@ __device__ __forceinline__ void copy_src_x2(ulonglong2* sA, ulonglong2* sB, ulon
         cp_async4(c + 2 + h, m + 1);
         cp_async4(d + h, m + 2);
     }
-    cp_async4(d + 2 + h, m + 3);
+    if (QY) cp_async4(d + 2 + h, m + 3);
 }
 
 // Writes one source (or equivalent point) into half h of pair slot p of the
@@ -1013,7 +1030,7 @@ __device__ __forceinline__ void put_src_x2(ulonglong2* sA, ulonglong2* sB, ulong
 // vector, so that group g takes the pairs g, g + G, ... and one packed
 // instruction serves two sources.  An odd window is padded with a point of
 // zero weight 1e10 away (its terms are exactly 0).
-template <bool DL, int NT, int PART>
+template <bool DL, int NT, int PART, int KM = 3>
 __global__ void __launch_bounds__(128, 5) k_leaf_pair_x2(const int* __restrict__ leaves, int nleaf,
                                                       const int* __restrict__ tb, const int* __restrict__ te,
                                                       const int* __restrict__ sb, const int* __restrict__ se,
@@ -1144,7 +1161,7 @@ __global__ void __launch_bounds__(128, 5) k_leaf_pair_x2(const int* __restrict__
                     const int j0 = s_vb[vi - vbase] + off, len = s_vn[vi - vbase] - off;
                     const int take = min(len, CAP - filled);
                     for (int e = threadIdx.x; e < take; e += CH)
-                        copy_src_x2<DL>(sA, sB, sC, sD, filled + e, sq, sm, j0 + e);
+                        copy_src_x2<DL, KM == 3>(sA, sB, sC, sD, filled + e, sq, sm, j0 + e);
                     filled += take;
                     if (take == len) { ++vi; off = 0; } else off += take;
                 }
@@ -1159,14 +1176,14 @@ __global__ void __launch_bounds__(128, 5) k_leaf_pair_x2(const int* __restrict__
                     const ulonglong2 A = sA[k], B = sB[k], C = DL ? sC[k] : make_ulonglong2(0, 0), D = sD[k];
 #pragma unroll
                     for (int u = 0; u < NT; ++u)
-                        interact_x2<DL, true>(X[u], Y[u], Z[u], A, B, C, D, kap, kl2, one, pL[u], pY[u]);
+                        interact_x2<DL, true, KM>(X[u], Y[u], Z[u], A, B, C, D, kap, kl2, one, pL[u], pY[u]);
                 }
 #pragma unroll 2
                 for (; active && k < np; k += G) {
                     const ulonglong2 A = sA[k], B = sB[k], C = DL ? sC[k] : make_ulonglong2(0, 0), D = sD[k];
 #pragma unroll
                     for (int u = 0; u < NT; ++u)
-                        interact_x2<DL, false>(X[u], Y[u], Z[u], A, B, C, D, kap, kl2, one, pL[u], pY[u]);
+                        interact_x2<DL, false, KM>(X[u], Y[u], Z[u], A, B, C, D, kap, kl2, one, pL[u], pY[u]);
                 }
                 __syncthreads();
             }
@@ -1225,7 +1242,7 @@ __global__ void __launch_bounds__(128, 5) k_leaf_pair_x2(const int* __restrict__
                     for (int j = threadIdx.x; j < ne; j += CH) {
                         const float4 sf = surf[j];
                         put_src_x2(sA, sB, sC, sD, i * ne + j, bx.x + bx.w * sf.x, bx.y + bx.w * sf.y,
-                                   bx.z + bx.w * sf.z, QL[base + j], 0.f, 0.f, 0.f, QY[base + j]);
+                                   bx.z + bx.w * sf.z, QL[base + j], 0.f, 0.f, 0.f, KM == 3 ? QY[base + j] : 0.f);
                     }
                 }
                 if ((n & 1) && threadIdx.x == 0)
@@ -1238,7 +1255,7 @@ __global__ void __launch_bounds__(128, 5) k_leaf_pair_x2(const int* __restrict__
                     const ulonglong2 A = sA[k], B = sB[k], D = sD[k];
 #pragma unroll
                     for (int u = 0; u < NT; ++u)
-                        interact_x2<false, false>(X[u], Y[u], Z[u], A, B, C0, D, kap, kl2, one, pL[u], pY[u]);
+                        interact_x2<false, false, KM>(X[u], Y[u], Z[u], A, B, C0, D, kap, kl2, one, pL[u], pY[u]);
                 }
                 __syncthreads();
             }
@@ -1260,11 +1277,11 @@ __global__ void __launch_bounds__(128, 5) k_leaf_pair_x2(const int* __restrict__
                 }
                 if (vt[u]) {
                     if (PART == 2) {
-                        potL_out[ti[u]] += a0 * float(kInv4PiD);
-                        potY_out[ti[u]] += a1 * float(kInv4PiD);
+                        if (KM & 1) potL_out[ti[u]] += a0 * float(kInv4PiD);
+                        if (KM & 2) potY_out[ti[u]] += a1 * float(kInv4PiD);
                     } else {
-                        potL_out[ti[u]] = a0 * float(kInv4PiD);
-                        potY_out[ti[u]] = a1 * float(kInv4PiD);
+                        if (KM & 1) potL_out[ti[u]] = a0 * float(kInv4PiD);
+                        if (KM & 2) potY_out[ti[u]] = a1 * float(kInv4PiD);
                     }
                 }
             }
@@ -1426,16 +1443,19 @@ static void gemm_dispatch(int npad, cudaStream_t st, int nblocks, const GemmArgs
 
 template <typename T, bool YUK, bool DL>
 static void launch_p2check(cudaStream_t st, int nbox, const int* boxes, int mode, fmm_tree* Tr, Work<T>& W,
-                           const Operators& O, T kappa) {
+                           const Operators& O, T kappa, int thrX = -1) {
     if (nbox <= 0) return;
+    const int* tb = Tr->same ? Tr->sb.p : Tr->tb.p;
+    const int* te = Tr->same ? Tr->se.p : Tr->te.p;
     if (O.npad <= 256)
         k_p2check<T, YUK, DL, 1><<<nbox, O.npad, 0, st>>>(nbox, boxes, mode, Tr->center.p, Tr->sb.p, Tr->se.p,
                                                           Tr->X.p, Tr->X_n.p, W.sq.p, W.sm.p,
-                                                          (const float4*)O.surf_f.p, O.ne, O.npad, kappa, W.chk.p);
+                                                          (const float4*)O.surf_f.p, O.ne, O.npad, kappa, W.chk.p,
+                                                          Tr->nchild.p, tb, te, thrX);
     else
         k_p2check<T, YUK, DL, 2><<<nbox, 256, 0, st>>>(nbox, boxes, mode, Tr->center.p, Tr->sb.p, Tr->se.p, Tr->X.p,
                                                        Tr->X_n.p, W.sq.p, W.sm.p, (const float4*)O.surf_f.p, O.ne,
-                                                       O.npad, kappa, W.chk.p);
+                                                       O.npad, kappa, W.chk.p, Tr->nchild.p, tb, te, thrX);
     PB_CHECK_LAUNCH();
 }
 
@@ -1460,11 +1480,29 @@ void check2equiv<double>(const Operators& O, int level, bool up, cudaStream_t st
 }
 
 template <typename T, bool YUK, bool DL, bool DN>
-static void launch_leaf(cudaStream_t st, fmm_tree* Tr, Work<T>& W, const Operators& O, T kappa) {
+static void launch_leaf(cudaStream_t st, fmm_tree* Tr, Work<T>& W, const Operators& O, T kappa, int thrW = -1,
+                        int thrX = -1) {
     if (Tr->n_tleaf <= 0) return;
     const float4* tpos = Tr->same ? Tr->pos_s.p : Tr->pos_t.p;
     const int* tb = Tr->same ? Tr->sb.p : Tr->tb.p;
     const int* te = Tr->same ? Tr->se.p : Tr->te.p;
+    if constexpr (std::is_same<T, float>::value && !DN) {
+        if (Tr->ctx->leaf_packed && O.ne <= 1024) {
+            // the packed leaf kernel for one kernel (KM 1: Laplace, 2: Yukawa)
+            constexpr int KM = YUK ? 2 : 1;
+            const int NT = Tr->ctx->leaf_nt ? Tr->ctx->leaf_nt : 4;
+            auto k = NT == 4 ? k_leaf_pair_x2<DL, 4, 0, KM> : k_leaf_pair_x2<DL, 2, 0, KM>;
+            k<<<Tr->n_tleaf, 128, 0, st>>>(Tr->leaf_ids.p, Tr->n_tleaf, tb, te, Tr->sb.p, Tr->se.p, Tr->U_off.p,
+                                           Tr->U_ids.p, Tr->W_off.p, Tr->W_ids.p, Tr->level.p, Tr->center.p, tpos,
+                                           W.sq.p, W.sm.p, W.Qu.p, W.Qd.p, nullptr, nullptr,
+                                           (const float4*)O.surf_f.p, O.ne, O.npad, kappa,
+                                           YUK ? nullptr : W.pot.p, YUK ? W.pot.p : nullptr, Tr->X.p, Tr->X_n.p,
+                                           thrW, thrX);
+            PB_CHECK_LAUNCH();
+            return;
+        }
+    }
+    PB_REQUIRE(thrW < 0 && thrX < 0, PB_EINVAL, "direct W/X-list evaluation needs the packed leaf kernel");
     constexpr int NT = 2;     // 4 measured slower (register pressure)
     k_leaf_eval<T, YUK, DL, DN, NT><<<Tr->n_tleaf, 128, 0, st>>>(
         Tr->leaf_ids.p, Tr->n_tleaf, tb, te, Tr->sb.p, Tr->se.p, Tr->U_off.p, Tr->U_ids.p, Tr->W_off.p, Tr->W_ids.p,
@@ -1666,6 +1704,10 @@ static void apply_t(fmm_tree* Tr, const Operators& O, double kappa_d, const In* 
     const T kappa = (T)kappa_d;
     const bool DL = dip != nullptr, DN = out_dn != nullptr;
     if (DL && DN) throw Error(PB_EINVAL, "double layer with target-normal derivative is not provided");
+    // small W boxes and small leaves' X lists summed directly (see list_direct)
+    const int ldm = Tr->ctx->list_direct;
+    const bool ld = std::is_same<T, float>::value && !DN && Tr->ctx->leaf_packed && ldm != 0 && O.ne <= 1024;
+    const int thrW = ld && ldm != 2 ? O.ne / 2 : -1, thrX = ld && ldm != 3 ? O.ne : -1;
     Work<T> W;
     W.sq.alloc(ns, st);
     if (DL) W.sm.alloc(ns, st);
@@ -1694,8 +1736,8 @@ static void apply_t(fmm_tree* Tr, const Operators& O, double kappa_d, const In* 
     // ---- far field into downward equivalent densities.
     // P2L: X-list sources -> downward check -> DC2DE, per level
     if (Tr->n_xbox > 0) {
-        if (DL) launch_p2check<T, YUK, true>(st, Tr->n_xbox, Tr->xbox_ids.p, 1, Tr, W, O, kappa);
-        else launch_p2check<T, YUK, false>(st, Tr->n_xbox, Tr->xbox_ids.p, 1, Tr, W, O, kappa);
+        if (DL) launch_p2check<T, YUK, true>(st, Tr->n_xbox, Tr->xbox_ids.p, 1, Tr, W, O, kappa, thrX);
+        else launch_p2check<T, YUK, false>(st, Tr->n_xbox, Tr->xbox_ids.p, 1, Tr, W, O, kappa, thrX);
         far_dc2de_x(Tr, O, W);
     }
     ph.reset(); ph = std::make_unique<PhaseTimer>(ctx, PB_PH_M2L);
@@ -1705,9 +1747,9 @@ static void apply_t(fmm_tree* Tr, const Operators& O, double kappa_d, const In* 
     far_l2l(Tr, O, W);
     ph.reset(); ph = std::make_unique<PhaseTimer>(ctx, PB_PH_LEAF);
     // ---- leaves: P2P + M2P + L2P
-    if (DL) launch_leaf<T, YUK, true, false>(st, Tr, W, O, kappa);
-    else if (DN) launch_leaf<T, YUK, false, true>(st, Tr, W, O, kappa);
-    else launch_leaf<T, YUK, false, false>(st, Tr, W, O, kappa);
+    if (DL) launch_leaf<T, YUK, true, false>(st, Tr, W, O, kappa, thrW, thrX);
+    else if (DN) launch_leaf<T, YUK, false, true>(st, Tr, W, O, kappa, thrW, thrX);
+    else launch_leaf<T, YUK, false, false>(st, Tr, W, O, kappa, thrW, thrX);
     ph.reset(); ph = std::make_unique<PhaseTimer>(ctx, PB_PH_SCATTER);
     const int* pt = Tr->same ? Tr->perm_s.p : Tr->perm_t.p;
     k_scatter<T, In><<<div_up(nt, 256), 256, 0, st>>>(nt, pt, W.pot.p, out);

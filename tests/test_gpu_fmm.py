@@ -6,6 +6,8 @@ with oracle/tree.py; fmm_apply is compared with the FP64 direct sum
 seeded target sample (the 4M-point workload).  Tolerance: 1e-5 relative L2,
 the bound the FMM apply must meet at an expansion order chosen for it.
 """
+import contextlib
+
 import numpy as np
 import pytest
 
@@ -304,22 +306,24 @@ def test_pair_vs_direct(pb, ctx, case20k, kappa):
     assert rel_l2(oY, direct_sum(YUKAWA, kappa, x, q=qY, dip=d, src_n=nrm)) < TOL
 
 
-def pair_surfaces_only(pb, ctx, *args, **kw):
-    """run_pair with every W/X pair through the equivalent surfaces, as the
-    single-kernel apply takes them (the same approximation, so the two agree
-    to rounding)."""
+@contextlib.contextmanager
+def surfaces_only(pb, ctx):
+    """Every W/X pair through the equivalent surfaces (PB_OPT_LIST_DIRECT 0)
+    in both the paired and the single-kernel apply: the same approximation,
+    so the two agree to rounding."""
     pb.pb_set_option(ctx, pb.PB_OPT_LIST_DIRECT, 0)
     try:
-        return run_pair(pb, ctx, *args, **kw)
+        yield
     finally:
         pb.pb_set_option(ctx, pb.PB_OPT_LIST_DIRECT, 1)
 
 
 def test_pair_equals_two_applies(pb, ctx, case20k):
     x, nrm, q, d, h = case20k
-    oL, oY = pair_surfaces_only(pb, ctx, h, 0.125, 6, qL=q, qY=q, d=d, sn=nrm, nt=len(x))
-    sL, _ = run_apply(pb, ctx, h, LAPLACE, 0.0, 6, q=q, d=d, sn=nrm, nt=len(x))
-    sY, _ = run_apply(pb, ctx, h, YUKAWA, 0.125, 6, q=q, d=d, sn=nrm, nt=len(x))
+    with surfaces_only(pb, ctx):
+        oL, oY = run_pair(pb, ctx, h, 0.125, 6, qL=q, qY=q, d=d, sn=nrm, nt=len(x))
+        sL, _ = run_apply(pb, ctx, h, LAPLACE, 0.0, 6, q=q, d=d, sn=nrm, nt=len(x))
+        sY, _ = run_apply(pb, ctx, h, YUKAWA, 0.125, 6, q=q, d=d, sn=nrm, nt=len(x))
     assert rel_l2(oL, sL) < 1e-6 and rel_l2(oY, sY) < 1e-6
 
 
@@ -450,9 +454,10 @@ def test_pair_equals_two_applies_low_order(pb, ctx, case20k, p):
     operator sizes (npad 32 and 64: p = 3, 4, 5) give the single-kernel
     results."""
     x, nrm, q, d, h = case20k
-    oL, oY = pair_surfaces_only(pb, ctx, h, 0.125, p, qL=q, qY=q, d=d, sn=nrm, nt=len(x))
-    sL, _ = run_apply(pb, ctx, h, LAPLACE, 0.0, p, q=q, d=d, sn=nrm, nt=len(x))
-    sY, _ = run_apply(pb, ctx, h, YUKAWA, 0.125, p, q=q, d=d, sn=nrm, nt=len(x))
+    with surfaces_only(pb, ctx):
+        oL, oY = run_pair(pb, ctx, h, 0.125, p, qL=q, qY=q, d=d, sn=nrm, nt=len(x))
+        sL, _ = run_apply(pb, ctx, h, LAPLACE, 0.0, p, q=q, d=d, sn=nrm, nt=len(x))
+        sY, _ = run_apply(pb, ctx, h, YUKAWA, 0.125, p, q=q, d=d, sn=nrm, nt=len(x))
     assert rel_l2(oL, sL) < 1e-6 and rel_l2(oY, sY) < 1e-6
 
 
@@ -601,7 +606,8 @@ def test_operators_shared_between_trees(pb, ctx, case20k, ref20k):
 @pytest.mark.parametrize("direct", [1, 0])
 def test_pair_list_direct_vs_direct_sum(pb, ctx, direct):
     """W- and X-list pairs taken directly (PB_OPT_LIST_DIRECT 1) or through
-    the equivalent surfaces (0): both within 1e-5 of the FP64 direct sum on
+    the equivalent surfaces (0), paired and single-kernel applies: all
+    within 1e-5 of the FP64 direct sum on
     an adaptive tree with many W/X entries (a dense cluster inside a sparse
     cloud, ncrit 24), at p = 8."""
     rng = np.random.default_rng(41)
@@ -618,9 +624,13 @@ def test_pair_list_direct_vs_direct_sum(pb, ctx, direct):
         pb.pb_set_option(ctx, pb.PB_OPT_LIST_DIRECT, direct)
         try:
             oL, oY = run_pair(pb, ctx, h, 0.3, 8, qL=q, qY=qY, d=d, sn=nrm, nt=len(x))
+            sL, _ = run_apply(pb, ctx, h, LAPLACE, 0.0, 8, q=q, d=d, sn=nrm, nt=len(x))
+            sY, _ = run_apply(pb, ctx, h, YUKAWA, 0.3, 8, q=qY, d=d, sn=nrm, nt=len(x))
         finally:
             pb.pb_set_option(ctx, pb.PB_OPT_LIST_DIRECT, 1)
     finally:
         pb.fmm_tree_destroy(h)
-    assert rel_l2(oL, direct_sum(LAPLACE, 0.0, x, q=q, dip=d, src_n=nrm)) < TOL
-    assert rel_l2(oY, direct_sum(YUKAWA, 0.3, x, q=qY, dip=d, src_n=nrm)) < TOL
+    rL = direct_sum(LAPLACE, 0.0, x, q=q, dip=d, src_n=nrm)
+    rY = direct_sum(YUKAWA, 0.3, x, q=qY, dip=d, src_n=nrm)
+    for a, r in ((oL, rL), (oY, rY), (sL, rL), (sY, rY)):
+        assert rel_l2(a, r) < TOL
