@@ -19,14 +19,17 @@ bool m2l_tc_launch(const fmm_tree* T, const Operators& O, const float* Qu, float
 bool pc_tc_launch(const fmm_tree* T, const Operators& O, int child_level, bool up, float* Q, int* err,
                   cudaStream_t st);
 bool c2e_tc_launch(const fmm_tree* T, const Operators& O, bool up, const float* X, float* Y, float* tmp, int* err,
-                   cudaStream_t st);
+                   cudaStream_t st, bool xfar = false);
 // two operator sets (Laplace, Yukawa) in the same launches
 bool m2l_tc_launch2(const fmm_tree* T, const Operators& O, const Operators* O2, const float* Qu, float* Qd,
                     const float* Qu2, float* Qd2, int* err, cudaStream_t st);
 bool pc_tc_launch2(const fmm_tree* T, const Operators& O, const Operators* O2, int child_level, bool up, float* Q,
                    float* Q2, int* err, cudaStream_t st);
 bool c2e_tc_launch2(const fmm_tree* T, const Operators& O, const Operators* O2, bool up, const float* X, float* Y,
-                    float* tmp, const float* X2, float* Y2, float* tmp2, int* err, cudaStream_t st);
+                    float* tmp, const float* X2, float* Y2, float* tmp2, int* err, cudaStream_t st, bool xfar = false);
+// X-list boxes that keep P2L when small leaves sum their X lists directly
+bool c2e_tc_ok(const Operators& O);
+void build_xbox_far(fmm_tree* T, int thrX);
 
 constexpr double kInv4PiD = 0.07957747154594767;
 constexpr double kLog2E = 1.4426950408889634;     // log2(e)
@@ -1567,10 +1570,11 @@ static void far_m2m(fmm_tree* Tr, const Operators& O, Work<T>& W) {
 // DC2DE at every X-list box (downward check potentials of P2L in W.chk);
 // writes Qd of those boxes before the M2L accumulates
 template <typename T>
-static void far_dc2de_x(fmm_tree* Tr, const Operators& O, Work<T>& W) {
+static void far_dc2de_x(fmm_tree* Tr, const Operators& O, Work<T>& W, bool xfar = false) {
     if constexpr (std::is_same<T, float>::value) {
-        if (c2e_tc_launch(Tr, O, false, W.chk.p, W.Qd.p, W.tmp.p, Tr->ctx->dev_err, Tr->ctx->stream)) return;
+        if (c2e_tc_launch(Tr, O, false, W.chk.p, W.Qd.p, W.tmp.p, Tr->ctx->dev_err, Tr->ctx->stream, xfar)) return;
     }
+    PB_REQUIRE(!xfar, PB_EINVAL, "reduced X-box list without the tensor-core solve");
     GemmArgs ga = tree_gemm_args<T>(Tr);
     for (int l = 0; l < Tr->nlev; ++l) {
         int a0 = Tr->xbox_lvl_off[l], a1 = Tr->xbox_lvl_off[l + 1];
@@ -1634,12 +1638,14 @@ static void far_l2l(fmm_tree* Tr, const Operators& O, Work<T>& W) {
 // ---- the far-field steps of the paired apply: both kernels in one
 // tensor-core launch where that path applies, else one kernel after the other
 template <typename T>
-static void far_pair_c2e(fmm_tree* Tr, const Operators& OL, const Operators& OY, Work<T>& WL, Work<T>& WY, bool up) {
+static void far_pair_c2e(fmm_tree* Tr, const Operators& OL, const Operators& OY, Work<T>& WL, Work<T>& WY, bool up,
+                         bool xfar = false) {
     if constexpr (std::is_same<T, float>::value) {
         if (c2e_tc_launch2(Tr, OL, &OY, up, WL.chk.p, up ? WL.Qu.p : WL.Qd.p, WL.tmp.p, WY.chk.p,
-                           up ? WY.Qu.p : WY.Qd.p, WY.tmp.p, Tr->ctx->dev_err, Tr->ctx->stream))
+                           up ? WY.Qu.p : WY.Qd.p, WY.tmp.p, Tr->ctx->dev_err, Tr->ctx->stream, xfar))
             return;
     }
+    PB_REQUIRE(!xfar, PB_EINVAL, "reduced X-box list without the tensor-core solve");
     if (up) { far_uc2ue(Tr, OL, WL); far_uc2ue(Tr, OY, WY); }
     else { far_dc2de_x(Tr, OL, WL); far_dc2de_x(Tr, OY, WY); }
 }
@@ -1736,9 +1742,14 @@ static void apply_t(fmm_tree* Tr, const Operators& O, double kappa_d, const In* 
     // ---- far field into downward equivalent densities.
     // P2L: X-list sources -> downward check -> DC2DE, per level
     if (Tr->n_xbox > 0) {
-        if (DL) launch_p2check<T, YUK, true>(st, Tr->n_xbox, Tr->xbox_ids.p, 1, Tr, W, O, kappa, thrX);
-        else launch_p2check<T, YUK, false>(st, Tr->n_xbox, Tr->xbox_ids.p, 1, Tr, W, O, kappa, thrX);
-        far_dc2de_x(Tr, O, W);
+        bool xfar = false;
+        if constexpr (std::is_same<T, float>::value) xfar = thrX >= 0 && c2e_tc_ok(O);
+        if (xfar) build_xbox_far(Tr, thrX);
+        const int nx = xfar ? Tr->n_xfar : Tr->n_xbox;
+        const int* xids = xfar ? Tr->xfar_ids.p : Tr->xbox_ids.p;
+        if (DL) launch_p2check<T, YUK, true>(st, nx, xids, 1, Tr, W, O, kappa, thrX);
+        else launch_p2check<T, YUK, false>(st, nx, xids, 1, Tr, W, O, kappa, thrX);
+        far_dc2de_x(Tr, O, W, xfar);
     }
     ph.reset(); ph = std::make_unique<PhaseTimer>(ctx, PB_PH_M2L);
     far_m2l(Tr, O, W);
@@ -1902,9 +1913,16 @@ static void apply_pair_t(fmm_tree* Tr, const Operators& OL, const Operators& OY,
     far_pair_m2m(Tr, OL, OY, WL, WY);
     ph.reset(); ph = std::make_unique<PhaseTimer>(ctx, PB_PH_P2L);
     if (Tr->n_xbox > 0) {
-        if (DL) launch_p2check_pair<T, true>(st, Tr->n_xbox, Tr->xbox_ids.p, 1, Tr, WL, WY, OL, kappa, thrX);
-        else launch_p2check_pair<T, false>(st, Tr->n_xbox, Tr->xbox_ids.p, 1, Tr, WL, WY, OL, kappa, thrX);
-        far_pair_c2e(Tr, OL, OY, WL, WY, false);
+        // with the small leaves' X lists summed in the leaf kernel, P2L and its
+        // solve run on the other X-list boxes only (tensor-core solve path)
+        bool xfar = false;
+        if constexpr (std::is_same<T, float>::value) xfar = thrX >= 0 && c2e_tc_ok(OL) && c2e_tc_ok(OY);
+        if (xfar) build_xbox_far(Tr, thrX);
+        const int nx = xfar ? Tr->n_xfar : Tr->n_xbox;
+        const int* xids = xfar ? Tr->xfar_ids.p : Tr->xbox_ids.p;
+        if (DL) launch_p2check_pair<T, true>(st, nx, xids, 1, Tr, WL, WY, OL, kappa, thrX);
+        else launch_p2check_pair<T, false>(st, nx, xids, 1, Tr, WL, WY, OL, kappa, thrX);
+        far_pair_c2e(Tr, OL, OY, WL, WY, false, xfar);
     }
     ph.reset(); ph = std::make_unique<PhaseTimer>(ctx, PB_PH_M2L);
     far_pair_m2l(Tr, OL, OY, WL, WY);

@@ -972,14 +972,48 @@ bool pc_tc_launch(const fmm_tree* T, const Operators& O, int child_level, bool u
 // result does not depend on the order of the reductions). Y rows of those
 // boxes must be zero on entry. One operator set, or two (O2, X2, Y2, tmp2)
 // in the same launches. False when the tensor-core path does not apply.
+bool c2e_tc_ok(const Operators& O) { return tc_ok(O) && O.uc2ue_w1_tc.p; }
+
+// The X-list boxes that keep P2L at a direct-list threshold (see the
+// field comment in fmm_tree), with their check -> equivalent items; once per
+// tree and threshold, on the host (the first apply runs uncaptured).
+void build_xbox_far(fmm_tree* T, int thrX) {
+    if (T->xfar_thr == thrX) return;
+    cudaStream_t st = T->ctx->stream;
+    const int nb = T->nbox, nx = T->n_xbox;
+    std::vector<int> ids(std::max(nx, 1)), nch(nb), b0(nb), b1(nb);
+    if (nx) PB_CUDA(cudaMemcpyAsync(ids.data(), T->xbox_ids.p, nx * sizeof(int), cudaMemcpyDeviceToHost, st));
+    PB_CUDA(cudaMemcpyAsync(nch.data(), T->nchild.p, nb * sizeof(int), cudaMemcpyDeviceToHost, st));
+    PB_CUDA(cudaMemcpyAsync(b0.data(), T->same ? T->sb.p : T->tb.p, nb * sizeof(int), cudaMemcpyDeviceToHost, st));
+    PB_CUDA(cudaMemcpyAsync(b1.data(), T->same ? T->se.p : T->te.p, nb * sizeof(int), cudaMemcpyDeviceToHost, st));
+    PB_CUDA(cudaStreamSynchronize(st));
+    std::vector<int> far;
+    far.reserve(nx);
+    for (int i = 0; i < nx; ++i) {
+        const int b = ids[i];
+        if (!(nch[b] == 0 && b1[b] - b0[b] <= thrX)) far.push_back(b);
+    }
+    std::vector<int> lvl(T->nlev + 1, 0);
+    for (int l = 0; l <= T->nlev; ++l)
+        lvl[l] = (int)(std::lower_bound(far.begin(), far.end(), T->lvl_off[l]) - far.begin());
+    T->xfar_ids.alloc(std::max<size_t>(far.size(), 1), st);
+    if (!far.empty())
+        PB_CUDA(cudaMemcpyAsync(T->xfar_ids.p, far.data(), far.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+    T->n_xfar = (int)far.size();
+    T->n_c2e_xfar = 0;
+    level_items(lvl, T->nlev, T->c2e_items_xfar, T->n_c2e_xfar, st);
+    T->xfar_thr = thrX;
+}
+
 bool c2e_tc_launch2(const fmm_tree* T, const Operators& O, const Operators* O2, bool up, const float* X, float* Y,
-                    float* tmp, const float* X2, float* Y2, float* tmp2, int* err, cudaStream_t st) {
+                    float* tmp, const float* X2, float* Y2, float* tmp2, int* err, cudaStream_t st, bool xfar) {
     if (!tc_ok(O) || !O.uc2ue_w1_tc.p) return false;
     if (O2 && (!tc_ok(*O2) || !O2->uc2ue_w1_tc.p || O2->npad != O.npad)) return false;
-    const int nitems = up ? T->n_c2e_up : T->n_c2e_dn;
+    const bool far = !up && xfar;
+    const int nitems = up ? T->n_c2e_up : (far ? T->n_c2e_xfar : T->n_c2e_dn);
     if (nitems == 0) return true;
-    const int4* items = up ? T->c2e_items_up.p : T->c2e_items_dn.p;
-    const int* ids = up ? T->sleaf_ids.p : T->xbox_ids.p;
+    const int4* items = up ? T->c2e_items_up.p : (far ? T->c2e_items_xfar.p : T->c2e_items_dn.p);
+    const int* ids = up ? T->sleaf_ids.p : (far ? T->xfar_ids.p : T->xbox_ids.p);
     auto w1 = [&](const Operators& o) { return up ? o.uc2ue_w1_tc.p : o.dc2de_w1_tc.p; };
     auto w2 = [&](const Operators& o) { return up ? o.uc2ue_w2_tc.p : o.dc2de_w2_tc.p; };
     const size_t bytes = (size_t)T->nbox * O.npad * sizeof(float);
@@ -993,8 +1027,8 @@ bool c2e_tc_launch2(const fmm_tree* T, const Operators& O, const Operators* O2, 
 }
 
 bool c2e_tc_launch(const fmm_tree* T, const Operators& O, bool up, const float* X, float* Y, float* tmp, int* err,
-                   cudaStream_t st) {
-    return c2e_tc_launch2(T, O, nullptr, up, X, Y, tmp, nullptr, nullptr, nullptr, err, st);
+                   cudaStream_t st, bool xfar) {
+    return c2e_tc_launch2(T, O, nullptr, up, X, Y, tmp, nullptr, nullptr, nullptr, err, st, xfar);
 }
 
 // M2L on the tensor cores for one or two operator sets; false when the

@@ -94,6 +94,14 @@ struct fmm_tree {
     // level) over sleaf_ids (upward) and xbox_ids (downward), one box per row
     pbfmm::DBuf<int4> c2e_items_up, c2e_items_dn;
     int n_c2e_up = 0, n_c2e_dn = 0;
+    // X-list boxes whose X lists the leaf kernel does not sum directly (it
+    // does for leaves of at most xfar_thr targets): P2L and its solve run on
+    // these only.  Built on first use for a threshold (-1: not built).
+    int xfar_thr = -1;
+    pbfmm::DBuf<int> xfar_ids;
+    int n_xfar = 0;
+    pbfmm::DBuf<int4> c2e_items_xfar;
+    int n_c2e_xfar = 0;
 
     std::map<std::tuple<int, double, int, int>, std::shared_ptr<pbfmm::Operators>> ops;
 };
