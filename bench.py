@@ -34,9 +34,9 @@ METRIC = "FMM apply points/s (4M-point surface, Laplace+Yukawa SL+DL, p=6)"
 UNIT = "points/s"
 # dram__bytes_read.sum + dram__bytes_write.sum of one leaf launch
 # (k_leaf_pair_x2) on this workload (4M points, p = 6, ncrit = 128), from one
-# ncu capture of the current kernel (506.6 + 27.1 MB, direct W/X lists on);
+# ncu capture of the current kernel (505.6 + 27.2 MB, direct W/X lists on);
 # None once the kernel changes
-LEAF_TRAFFIC_BYTES = 533.7e6
+LEAF_TRAFFIC_BYTES = 532.8e6
 # Arithmetic of one source-target pair in the paired (Laplace + Yukawa)
 # evaluation, FMA = 2 FLOPs, MUFU counted apart: SL+DL of both kernels
 # 30 FLOPs + 2 MUFU (rsqrt, ex2); monopole-only pairs of equivalent
