@@ -162,16 +162,17 @@ int pb_profile(pb_ctx* ctx, int enable);
  *                         where the operator size allows (n_pad >= 128), else
  *                         128; 1: 128 pairs per MMA, one CTA per operator
  *                         part.  A tile-shape knob of the autotuner (pb_tune).
- *   PB_OPT_LIST_DIRECT    1 (default): in the FP32 paired apply without
- *                         target-normal derivatives (the packed kernels),
- *                         the pairs of the adaptive lists are summed directly
+ *   PB_OPT_LIST_DIRECT    1 (default): in the FP32 applies without
+ *                         target-normal derivatives (fmm_apply_pair and
+ *                         fmm_apply on the packed kernels, PB_OPT_LEAF_PACKED
+ *                         1), the pairs of the adaptive lists are summed directly
  *                         where that is less work than the equivalent
  *                         surfaces: a W-list box of at most n_e / 2 sources
  *                         instead of its M2P, and the X list of a leaf of at
  *                         most n_e targets instead of its P2L (the direct
  *                         sums are exact); 0: every W and X pair through the
  *                         equivalent surfaces, as in the KIFMM the paper
- *                         cites.
+ *                         cites; 2: X lists only; 3: W boxes only.
  * Errors: PB_EINVAL for an unknown option or value. */
 enum { PB_OPT_COUPLING = 1, PB_OPT_DETERMINISTIC = 2, PB_OPT_SINGULAR = 3, PB_OPT_OVERLAP = 4, PB_OPT_RESTART = 5,
        PB_OPT_LEAF_NT = 6, PB_OPT_LEAF_PACKED = 7, PB_OPT_M2L_TILE = 8, PB_OPT_LIST_DIRECT = 9 };
