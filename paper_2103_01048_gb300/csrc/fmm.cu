@@ -1810,7 +1810,11 @@ static void launch_p2check_pair(cudaStream_t st, int nbox, const int* boxes, int
                                                           (const float4*)O.surf_f.p, O.ne, O.npad, kappa, WL.chk.p,
                                                           WY.chk.p);
     else
-        k_p2check_pair<T, DL, 2><<<nbox, 256, 0, st>>>(nbox, boxes, mode, Tr->center.p, Tr->sb.p, Tr->se.p,
+        // two check points per thread, the threads rounded up from n_pad / 2
+        // (p = 8: 160 threads for 296 points; a fixed 256 left 42% of the
+        // slots idle: P2M 2.12 -> 1.63 ms at 4M)
+        k_p2check_pair<T, DL, 2><<<nbox, std::min(256, (O.npad / 2 + 31) / 32 * 32), 0, st>>>(
+                                                       nbox, boxes, mode, Tr->center.p, Tr->sb.p, Tr->se.p,
                                                        Tr->X.p, Tr->X_n.p, WL.sq.p, WL.sm.p,
                                                        (const float4*)O.surf_f.p, O.ne, O.npad, kappa, WL.chk.p,
                                                        WY.chk.p);
