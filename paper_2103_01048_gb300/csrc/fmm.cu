@@ -1455,8 +1455,9 @@ static void launch_p2check(cudaStream_t st, int nbox, const int* boxes, int mode
                                                           Tr->X.p, Tr->X_n.p, W.sq.p, W.sm.p,
                                                           (const float4*)O.surf_f.p, O.ne, O.npad, kappa, W.chk.p,
                                                           Tr->nchild.p, tb, te, thrX);
-    else
-        k_p2check<T, YUK, DL, 2><<<nbox, 256, 0, st>>>(nbox, boxes, mode, Tr->center.p, Tr->sb.p, Tr->se.p, Tr->X.p,
+    else       // two check points per thread, threads rounded up from n_pad / 2
+        k_p2check<T, YUK, DL, 2><<<nbox, std::min(256, (O.npad / 2 + 31) / 32 * 32), 0, st>>>(
+                                                       nbox, boxes, mode, Tr->center.p, Tr->sb.p, Tr->se.p, Tr->X.p,
                                                        Tr->X_n.p, W.sq.p, W.sm.p, (const float4*)O.surf_f.p, O.ne,
                                                        O.npad, kappa, W.chk.p, Tr->nchild.p, tb, te, thrX);
     PB_CHECK_LAUNCH();
